@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+The paper prints no worked numerical example of the layer, so the oracle is
+pinned by: brute force on tiny inputs (plain Python loops), closed forms and
+invariants that the definition fixes (constant output, the linear-target
+identity, the eps limits, the global window), special cases that reduce to
+library routines (torch's clipped average pool and bilinear interpolate in
+FP64, He's textbook guided filter written with uncentred moments), torch
+autograd on that independent composition, adjoint dot-product identities and
+FP64 central finite differences.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from tests import torch_composition as TC
+
+pytestmark = pytest.mark.filterwarnings("ignore::UserWarning")
+
+
+def rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- box filter
+
+@pytest.mark.parametrize("h,w,r", [(1, 1, 0), (1, 7, 2), (5, 7, 1), (6, 4, 3), (9, 13, 2)])
+def test_window_count_closed_form(h, w, r):
+    N = O.window_count(h, w, r)
+    for i in range(h):
+        for j in range(w):
+            cy = min(i + r, h - 1) - max(i - r, 0) + 1
+            cx = min(j + r, w - 1) - max(j - r, 0) + 1
+            assert N[i, j] == cy * cx
+
+
+@pytest.mark.parametrize("h,w,r", [(5, 7, 1), (4, 9, 2), (3, 3, 4)])
+def test_window_sum_brute_force(h, w, r):
+    x = rng(1).normal(size=(h, w))
+    S = O.window_sum(x, r)
+    for i in range(h):
+        for j in range(w):
+            ref = 0.0
+            for a in range(h):
+                for b in range(w):
+                    if abs(a - i) <= r and abs(b - j) <= r:
+                        ref += x[a, b]
+            assert abs(S[i, j] - ref) < 1e-12
+
+
+@pytest.mark.parametrize("h,w,r", [(8, 11, 1), (16, 9, 2), (7, 7, 3), (5, 12, 5)])
+def test_box_mean_matches_avg_pool(h, w, r):
+    x = rng(2).uniform(size=(h, w))
+    ref = TC.box(torch.from_numpy(x), r).numpy()
+    np.testing.assert_allclose(O.box_mean(x, r), ref, rtol=0, atol=1e-14)
+
+
+def test_box_mean_global_window():
+    x = rng(3).uniform(size=(6, 9))
+    M = O.box_mean(x, 9)
+    np.testing.assert_allclose(M, np.full_like(x, x.mean()), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("h,w,r", [(6, 9, 1), (10, 7, 2), (4, 4, 5)])
+def test_box_mean_transpose_identity(h, w, r):
+    R = rng(4)
+    x, y = R.normal(size=(h, w)), R.normal(size=(h, w))
+    lhs = np.sum(O.box_mean(x, r) * y)
+    rhs = np.sum(x * O.box_mean_T(y, r))
+    assert abs(lhs - rhs) <= 1e-13 * max(1.0, abs(lhs))
+
+
+# ------------------------------------------------------------ window stats
+
+@pytest.mark.parametrize("h,w,r", [(5, 6, 1), (7, 5, 2), (3, 4, 3)])
+def test_window_stats_against_numpy_var_cov(h, w, r):
+    R = rng(5)
+    G, P = R.uniform(size=(h, w)), R.uniform(size=(h, w))
+    mu, nu, var, cov = O.window_stats(G, P, r)
+    for i in range(h):
+        for j in range(w):
+            gs = G[max(i - r, 0):i + r + 1, max(j - r, 0):j + r + 1].ravel()
+            ps = P[max(i - r, 0):i + r + 1, max(j - r, 0):j + r + 1].ravel()
+            assert abs(mu[i, j] - gs.mean()) < 1e-14
+            assert abs(nu[i, j] - ps.mean()) < 1e-14
+            assert abs(var[i, j] - np.var(gs)) < 1e-14
+            c = np.cov(np.stack([gs, ps]), bias=True) if gs.size > 1 else np.zeros((2, 2))
+            assert abs(cov[i, j] - c[0, 1]) < 1e-14
+
+
+# --------------------------------------------------------------- upsampler
+
+@pytest.mark.parametrize("hl,wl,h,w", [(4, 4, 16, 16), (5, 3, 16, 13), (1, 2, 4, 9),
+                                       (7, 7, 7, 7), (3, 8, 24, 64)])
+def test_upsample_matches_torch_interpolate(hl, wl, h, w):
+    X = rng(6).normal(size=(hl, wl))
+    ref = TC.up(torch.from_numpy(X), h, w).numpy()
+    np.testing.assert_allclose(O.upsample(X, h, w), ref, rtol=0, atol=1e-14)
+
+
+def test_upsample_constant_and_ramp():
+    # constants are reproduced exactly; a ramp exactly away from the clamped border
+    X = np.full((5, 6), 0.375)
+    assert np.all(O.upsample(X, 20, 24) == 0.375)
+    f = 4
+    ramp = np.tile(np.arange(6, dtype=float), (5, 1))  # value = column index j
+    U = O.upsample(ramp, 20, 24)
+    for x in range(24):
+        t = (x + 0.5) / f - 0.5
+        if 0.0 <= t <= 5.0:
+            assert abs(U[3, x] - t) < 1e-14
+
+
+@pytest.mark.parametrize("f", [2, 4, 8])
+def test_bilinear_weights_f_periodic(f):
+    n_in = 6
+    W = O.bilinear_matrix(n_in * f, n_in)
+    for k in range(f, (n_in - 1) * f):
+        t = (k + 0.5) / f - 0.5
+        i0 = math.floor(t)
+        lam = t - i0
+        assert abs(W[k, i0] - (1 - lam)) < 1e-15 and abs(W[k, i0 + 1] - lam) < 1e-15
+        assert abs(W[k].sum() - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("hl,wl,h,w", [(4, 5, 16, 20), (5, 3, 17, 11)])
+def test_upsample_transpose_identity(hl, wl, h, w):
+    R = rng(7)
+    X, Z = R.normal(size=(hl, wl)), R.normal(size=(h, w))
+    lhs = np.sum(O.upsample(X, h, w) * Z)
+    rhs = np.sum(X * O.upsample_T(Z, hl, wl))
+    assert abs(lhs - rhs) <= 1e-13 * max(1.0, abs(lhs))
+
+
+# ----------------------------------------------------------- whole forward
+
+CASES = [  # N, C, h_l, w_l, h, w, r, eps
+    (1, 1, 8, 8, 32, 32, 1, 1e-2),
+    (2, 3, 6, 9, 24, 36, 2, 1e-3),
+    (1, 2, 5, 7, 17, 23, 1, 1e-4),
+    (1, 1, 4, 4, 32, 32, 8, 1e-4),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_forward_matches_torch_composition(case):
+    N, C, hl, wl, h, w, r, eps = case
+    d = synth.ragged_case(11, N, C, hl, wl, h, w)
+    out = O.forward(d["p_l"], d["I_l"], d["I_h"], r, eps)
+    ref = TC.gf(d["p_l"], d["I_l"], d["I_h"], r, eps).numpy()
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-10)
+
+
+def test_f1_reduces_to_textbook_guided_filter():
+    # With h = h_l the layer is He's guided filter with q = mean(a) I + mean(b).
+    d = synth.ragged_case(12, 1, 1, 12, 10, 12, 10)
+    G, P = d["I_l"][0, 0].numpy(), d["p_l"][0, 0].numpy()
+    r, eps = 2, 1e-3
+    Gt, Pt = torch.from_numpy(G), torch.from_numpy(P)
+    mean_I = TC.box(Gt, r)
+    mean_p = TC.box(Pt, r)
+    a = (TC.box(Gt * Pt, r) - mean_I * mean_p) / (TC.box(Gt * Gt, r) - mean_I ** 2 + eps)
+    b = mean_p - a * mean_I
+    q = TC.box(a, r) * Gt + TC.box(b, r)
+    out = O.forward_plane(P, G, G, r, eps)
+    np.testing.assert_allclose(out, q.numpy(), rtol=0, atol=1e-12)
+
+
+def test_constant_target_is_reproduced_exactly():
+    d = synth.ragged_case(13, 1, 2, 9, 7, 36, 28)
+    p = np.full((1, 2, 9, 7), 0.5)
+    out = O.forward(p, d["I_l"], d["I_h"], 2, 1e-3)
+    assert np.all(out == 0.5)
+
+
+def test_linear_target_closed_form():
+    # p = alpha G + beta  =>  A = alpha var/(var+eps), b = beta + alpha mu eps/(var+eps)
+    d = synth.ragged_case(14, 1, 1, 10, 12, 40, 48)
+    G = d["I_l"][0, 0].numpy()
+    alpha, beta, eps, r = 0.7, 0.1, 1e-3, 1
+    P = alpha * G + beta
+    mu, _, var, _ = O.window_stats(G, P, r)
+    A, b = O.coefficients(G, P, r, eps)
+    np.testing.assert_allclose(A, alpha * var / (var + eps), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(b, beta + alpha * mu * eps / (var + eps), rtol=1e-12, atol=1e-14)
+    # eps -> 0: the layer reproduces alpha G_h + beta
+    Gh = d["I_h"][0, 0].numpy()
+    out = O.forward_plane(P, G, Gh, r, 1e-14)
+    np.testing.assert_allclose(out, alpha * Gh + beta, rtol=0, atol=1e-9)
+
+
+def test_large_eps_limit():
+    # eps -> inf: A -> 0, so O_h -> f_up(f_mu(f_mu(p)))
+    d = synth.ragged_case(15, 1, 1, 8, 9, 32, 27)
+    G, P, Gh = d["I_l"][0, 0].numpy(), d["p_l"][0, 0].numpy(), d["I_h"][0, 0].numpy()
+    r = 1
+    out = O.forward_plane(P, G, Gh, r, 1e12)
+    ref = O.upsample(O.box_mean(O.box_mean(P, r), r), 32, 27)
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-11)
+
+
+def test_global_window_is_one_ridge_regression():
+    # r >= image size: a single scalar A (1-D ridge regression) for the whole image
+    d = synth.ragged_case(16, 1, 1, 5, 6, 20, 24)
+    G, P = d["I_l"][0, 0].numpy(), d["p_l"][0, 0].numpy()
+    eps = 1e-3
+    A, b = O.coefficients(G, P, 10, eps)
+    g, p = G.ravel(), P.ravel()
+    A_ref = np.mean((g - g.mean()) * (p - p.mean())) / (np.var(g) + eps)
+    b_ref = p.mean() - A_ref * g.mean()
+    np.testing.assert_allclose(A, A_ref, rtol=1e-12)
+    np.testing.assert_allclose(b, b_ref, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("case", CASES)
+def test_backward_matches_torch_autograd(case):
+    N, C, hl, wl, h, w, r, eps = case
+    d = synth.ragged_case(21, N, C, hl, wl, h, w)
+    R = synth.upstream_grad(1, d["I_h"].shape)
+    p = d["p_l"].clone().requires_grad_(True)
+    gl = d["I_l"].clone().requires_grad_(True)
+    gh = d["I_h"].clone().requires_grad_(True)
+    (TC.gf(p, gl, gh, r, eps) * R).sum().backward()
+    dp, dIl, dIh = O.backward(R, d["p_l"], d["I_l"], d["I_h"], r, eps)
+    for got, ref in ((dp, p.grad), (dIl, gl.grad), (dIh, gh.grad)):
+        ref = ref.numpy()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 1e-10, err
+
+
+def _fd_check(fun, x, grad, n_probe=None, seed=0):
+    """Central differences of the scalar fun at x against grad (norm-wise)."""
+    idx = list(np.ndindex(*x.shape))
+    if n_probe is not None and n_probe < len(idx):
+        sel = np.random.default_rng(seed).choice(len(idx), n_probe, replace=False)
+        idx = [idx[i] for i in sel]
+    fd = np.empty(len(idx))
+    an = np.empty(len(idx))
+    for k, i in enumerate(idx):
+        # step ~ cube root of FP64 epsilon balances truncation and rounding error
+        hstep = 5e-6 * max(1.0, abs(x[i]))
+        x0 = x[i]
+        x[i] = x0 + hstep
+        fp = fun()
+        x[i] = x0 - hstep
+        fm = fun()
+        x[i] = x0
+        fd[k] = (fp - fm) / (2 * hstep)
+        an[k] = grad[i]
+    return np.linalg.norm(fd - an) / np.linalg.norm(an)
+
+
+@pytest.mark.parametrize("hl,wl,h,w,r,eps", [(4, 4, 16, 16, 1, 1e-2), (8, 8, 16, 16, 2, 1e-3),
+                                             (5, 6, 16, 16, 1, 1e-2)])
+def test_backward_finite_differences(hl, wl, h, w, r, eps):
+    d = synth.ragged_case(31, 1, 1, hl, wl, h, w)
+    P = d["p_l"][0, 0].numpy().copy()
+    Gl = d["I_l"][0, 0].numpy().copy()
+    Gh = d["I_h"][0, 0].numpy().copy()
+    R = synth.upstream_grad(2, (h, w)).numpy()
+    dP, dGl, dGh = O.backward_plane(R, P, Gl, Gh, r, eps)
+
+    def loss():
+        return float(np.sum(O.forward_plane(P, Gl, Gh, r, eps) * R))
+
+    assert _fd_check(loss, P, dP) < 1e-6
+    assert _fd_check(loss, Gl, dGl) < 1e-6
+    assert _fd_check(loss, Gh, dGh, n_probe=64) < 1e-6
+
+
+# ------------------------------------------------------- guidance transform
+
+def test_guided_forward_and_backward_match_torch():
+    N, C, f, hl, wl, r, eps = 2, 3, 4, 4, 5, 1, 1e-3
+    d = synth.photo_like(41, N, C, hl, wl, f)
+    g = synth.guide_weights(3)
+    R = synth.upstream_grad(4, d["I_h"].shape)
+    out = O.forward_guided(d["p_l"], d["I_h"], g["w1"], g["w2"], g["b2"], r, eps)
+    p = d["p_l"].clone().requires_grad_(True)
+    ih = d["I_h"].clone().requires_grad_(True)
+    w1 = g["w1"].clone().requires_grad_(True)
+    w2 = g["w2"].clone().requires_grad_(True)
+    b2 = g["b2"].clone().requires_grad_(True)
+    ref = TC.gf_guided(p, ih, w1, w2, b2, r, eps)
+    np.testing.assert_allclose(out, ref.detach().numpy(), rtol=0, atol=1e-12)
+    (ref * R).sum().backward()
+    got = O.backward_guided(R, d["p_l"], d["I_h"], g["w1"], g["w2"], g["b2"], r, eps)
+    for a, b in zip(got[:4], (p.grad, ih.grad, w1.grad, w2.grad)):
+        b = b.numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-10
+    # Adding a constant to the guide leaves the layer unchanged (b absorbs it:
+    # b -> b - A c, so Abar_h c - f_up(f_mu(A c)) = 0), hence dL/db2 = 0.
+    assert np.max(np.abs(got[4])) < 1e-12 and np.max(np.abs(b2.grad.numpy())) < 1e-12
+
+
+def test_guided_backward_finite_differences():
+    C, f, hl, wl, r, eps = 3, 4, 4, 4, 1, 1e-2
+    d = synth.photo_like(42, 1, C, hl, wl, f)
+    Ih = d["I_h"].numpy().copy()
+    # keep away from the leaky-ReLU kink so central differences are valid:
+    # draw weight seeds until no hidden pre-activation is within 1e-4 of 0
+    for seed in range(5, 200):
+        g = {k: v.numpy().copy() for k, v in synth.guide_weights(seed).items()}
+        _, Z = O.guide_apply(Ih[0], g["w1"], g["w2"], g["b2"])
+        if np.min(np.abs(Z)) > 1e-4:
+            break
+    assert np.min(np.abs(Z)) > 1e-4
+    P = d["p_l"].numpy().copy()
+    R = synth.upstream_grad(6, Ih.shape).numpy()
+    dP, dI, dw1, dw2, db2 = O.backward_guided(R, P, Ih, g["w1"], g["w2"], g["b2"], r, eps)
+
+    def loss():
+        return float(np.sum(O.forward_guided(P, Ih, g["w1"], g["w2"], g["b2"], r, eps) * R))
+
+    assert _fd_check(loss, P, dP) < 1e-6
+    assert _fd_check(loss, Ih, dI, n_probe=48) < 1e-6
+    assert _fd_check(loss, g["w1"], dw1) < 1e-6
+    assert _fd_check(loss, g["w2"], dw2) < 1e-6
+    assert np.max(np.abs(db2)) < 1e-12  # guide-shift invariance
+
+
+# ------------------------------------------------ planted mistakes (pins bite)
+
+def test_pins_catch_a_dropped_mean_of_coefficients(monkeypatch):
+    # Planting the paper-literal variant (no box mean of A, b) must fail the
+    # torch-composition pin, which proves that pin sees that step.
+    case = CASES[1]
+    N, C, hl, wl, h, w, r, eps = case
+    d = synth.ragged_case(11, N, C, hl, wl, h, w)
+    monkeypatch.setattr(O.dgf_oracle, "mean_coefficients",
+                        lambda G, P, r, eps: O.dgf_oracle.coefficients(G, P, r, eps))
+    out = O.forward(d["p_l"], d["I_l"], d["I_h"], r, eps)
+    ref = TC.gf(d["p_l"], d["I_l"], d["I_h"], r, eps).numpy()
+    assert np.max(np.abs(out - ref)) > 1e-4
+
+
+def test_pins_catch_a_sign_error_in_the_adjoint(monkeypatch):
+    d = synth.ragged_case(31, 1, 1, 4, 4, 16, 16)
+    P = d["p_l"][0, 0].numpy().copy()
+    Gl = d["I_l"][0, 0].numpy().copy()
+    Gh = d["I_h"][0, 0].numpy().copy()
+    R = synth.upstream_grad(2, (16, 16)).numpy()
+    good = O.backward_plane(R, P, Gl, Gh, 1, 1e-2)[1]
+    real_T = O.dgf_oracle.box_mean_T
+    calls = {"n": 0}
+
+    def flipped(y, r):
+        calls["n"] += 1
+        out = real_T(y, r)
+        return -out if calls["n"] == 6 else out  # the f_mu^T of d Sigma_G
+    monkeypatch.setattr(O.dgf_oracle, "box_mean_T", flipped)
+    bad = O.backward_plane(R, P, Gl, Gh, 1, 1e-2)[1]
+    assert np.linalg.norm(bad - good) / np.linalg.norm(good) > 1e-3
