@@ -1,0 +1,514 @@
+"""Benchmark of the guided filtering layer's hot path on GB300.
+
+One step = forward + backward of the layer (low-res statistics -> A, b ->
+box mean -> bilinear upsampling + affine; then the transposed upsampler,
+the recomputed statistics and Algorithm 1's low-res gradients) over one
+batch, through the C ABI, inputs resident in HBM.
+
+Default workload: 4 images x 3 channels, low-res 512 x 512, high-res
+2048 x 2048, r = 1, eps = 1e-4, FP32 storage (the plain FP32 configuration;
+blobs + edges + noise photo stand-in with a tone-curve target).  The same
+JSON line also reports the forward alone, the BF16 4K batch (2 x 3 x
+3840 x 2160, r = 2, eps = 1e-3), the per-kernel roofline, an end-to-end
+figure with host buffers, and the FP64 oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank runs its own batch (images are
+independent; no collective on the data path) and the time is the max over
+ranks; the value is the pixels of all ranks over that time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "high-res Mpix/s fwd & fwd+bwd, BF16-batched vs FP32-plain; % of HBM roofline"
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    # name: N, C, h_l, w_l, f, r, eps, dtype, recipe
+    "fp32_plain_4x3x2048": dict(N=4, C=3, h_l=512, w_l=512, f=4, r=1, eps=1e-4, dtype="f32", recipe="blobs"),
+    "bf16_4k_2x3x3840x2160": dict(N=2, C=3, h_l=540, w_l=960, f=4, r=2, eps=1e-3, dtype="bf16",
+                                  recipe="photo"),
+}
+MAIN = "fp32_plain_4x3x2048"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed loop only (no roofline pass, e2e, extras or oracle): for profiler runs")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ inputs
+def make_inputs(spec, device, seed=0):
+    import torch
+
+    import synth
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[spec["dtype"]]
+    if spec["recipe"] == "blobs":
+        d = synth.blobs_tone_curve(seed, spec["N"], spec["C"], spec["h_l"], spec["w_l"], spec["f"],
+                                   device=str(device))
+    else:
+        d = synth.photo_like(seed, spec["N"], spec["C"], spec["h_l"], spec["w_l"], spec["f"])
+    g = {k: v.to(dt).to(device) for k, v in d.items()}
+    g["R"] = synth.upstream_grad(seed + 1, g["I_h"].shape).to(dt).to(device)
+    return g, dt
+
+
+class Step:
+    """Pre-marshalled forward + backward calls through the C ABI."""
+
+    def __init__(self, g, spec, device):
+        import torch
+
+        from paper_1803_05619_gb300 import _lib as L
+        from paper_1803_05619_gb300.layer import dtype_code, workspace
+        self.L = L
+        lib = L.lib()
+        N, C, h, w = g["I_h"].shape
+        h_l, w_l = g["p_l"].shape[2:]
+        self.shape = (N, C, h_l, w_l, h, w)
+        self.r, self.eps = spec["r"], spec["eps"]
+        self.dt = dtype_code(g["I_h"])
+        self.g = g
+        self.O = torch.empty_like(g["I_h"])
+        self.dp = torch.empty_like(g["p_l"])
+        self.dIl = torch.empty_like(g["p_l"])
+        self.dIh = torch.empty_like(g["I_h"])
+        nb = L.dgf_workspace_size(N, C, h_l, w_l, h, w, self.r, self.dt, None)
+        self.ws = workspace(nb, device)
+        self.stream = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+        P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self.fwd_args = (P(g["p_l"]), P(g["I_l"]), P(g["I_h"]), P(self.O), N, C, h_l, w_l, h, w, self.r,
+                         ctypes.c_float(self.eps), self.dt, None, P(self.ws), self.ws.numel(), self.stream)
+        self.bwd_args = (P(g["R"]), P(g["p_l"]), P(g["I_l"]), P(g["I_h"]), P(self.dp), P(self.dIl),
+                         P(self.dIh), None, N, C, h_l, w_l, h, w, self.r, ctypes.c_float(self.eps), self.dt,
+                         None, P(self.ws), self.ws.numel(), self.stream)
+        self._f = lib.dgf_forward
+        self._b = lib.dgf_backward
+
+    def forward(self):
+        st = self._f(*self.fwd_args)
+        if st != 0:
+            raise RuntimeError(self.L.dgf_last_error())
+
+    def backward(self):
+        st = self._b(*self.bwd_args)
+        if st != 0:
+            raise RuntimeError(self.L.dgf_last_error())
+
+    def __call__(self):
+        self.forward()
+        self.backward()
+
+
+# ------------------------------------------------------------------ timing
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", rank=rank, world_size=ws, device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws, device):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed loop runs."""
+
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        import datetime
+        rows = []
+        t0, t1 = getattr(self, "start", None), getattr(self, "stop", None)
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                row = (float(parts[1]), float(parts[2]), parts[5:9], parts[4], float(parts[3]))
+            except ValueError:
+                continue
+            if t0 is not None and t1 is not None and not (t0 <= ts <= t1):
+                continue
+            rows.append(row)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(r[4] for r in rows)}
+
+
+def time_loop(fn, steps, warmup, ws, device, clock=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    if clock is not None:
+        clock.mark("start")
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    if clock is not None:
+        clock.mark("stop")
+    barrier(ws)
+    ms = a.elapsed_time(b) / steps
+    return max_over_ranks(ms, ws, device)
+
+
+# --------------------------------------------------------------- roofline
+def algorithmic_bytes(kernel, shape, esz):
+    """Minimum DRAM bytes one launch must move (inputs read once, outputs written once)."""
+    N, C, h_l, w_l, h, w = shape
+    hi = N * C * h * w
+    lo = N * C * h_l * w_l
+    return {
+        "k2_hires_apply": hi * 2 * esz,               # read I_h, write O_h
+        "k3_hires_bwd": hi * 3 * esz,                 # read dO_h, I_h; write dI_h
+        "k1_lowres_coef": lo * (2 * esz + 8),         # read I_l, p_l; write Abar, bbar (FP32)
+        "k4_lowres_bwd": lo * (2 * esz + 8 + 2 * esz),  # read I_l, p_l, dAbar/dbbar; write dp_l, dI_l
+    }.get(kernel)
+
+
+def peaks():
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1803_05619_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def roofline(step, spec, steps, warmup, workload):
+    import torch
+    L = step.L
+    L.dgf_profile_reset()
+    L.dgf_profile_enable(True)
+    try:
+        for _ in range(max(3, warmup // 4)):
+            step()
+        L.dgf_profile_reset()
+        for _ in range(steps):
+            step()
+        torch.cuda.synchronize()
+        prof = L.dgf_profile_read()
+    finally:
+        L.dgf_profile_enable(False)
+    esz = 4 if spec["dtype"] == "f32" else 2
+    total = sum(v[0] for v in prof.values())
+    per = {}
+    for k, (ms, n) in prof.items():
+        ab = algorithmic_bytes(k, step.shape, esz)
+        avg = ms / max(n, 1)
+        per[k] = {"avg_us": round(avg * 1e3, 2), "share": round(ms / total, 4),
+                  "gbs": round(ab / (avg * 1e-3) / 1e9, 1) if ab else None}
+    top = max(prof, key=lambda k: prof[k][0])
+    ms, n = prof[top]
+    avg_s = ms / n * 1e-3
+    ab = algorithmic_bytes(top, step.shape, esz)
+    peak, src = peaks()
+    ach = ab / avg_s / 1e9
+    return {"kernel": top, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "peak_source": src,
+            "frac_of_nominal_8TBs": round(ach / NOMINAL_HBM_GBS, 4),
+            "traffic": ncu_traffic(top, workload), "algorithmic_bytes": ab,
+            "avg_launch_us": round(avg_s * 1e6, 2), "kernels": per}
+
+
+# ------------------------------------------------------------- end to end
+def e2e(step, steps, warmup, device):
+    """Same step with host buffers: H2D of the inputs and D2H of every output inside the timed region."""
+    import torch
+    g = step.g
+    ins = [g["p_l"], g["I_l"], g["I_h"], g["R"]]
+    outs = [step.O, step.dp, step.dIl, step.dIh]
+    h_in = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in ins]
+    h_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+    for h, t in zip(h_in, ins):
+        h.copy_(t)
+
+    def once():
+        for h, t in zip(h_in, ins):
+            t.copy_(h, non_blocking=True)
+        step()
+        for h, t in zip(h_out, outs):
+            h.copy_(t, non_blocking=True)
+
+    n = max(3, min(steps, 50))
+    ms = time_loop(once, n, max(2, warmup // 4), 1, device)
+    bi = sum(t.numel() * t.element_size() for t in ins)
+    bo = sum(t.numel() * t.element_size() for t in outs)
+    return ms, bi, bo, n
+
+
+# ------------------------------------------------------------ CPU oracle
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle, synth
+spec = json.loads({spec!r})
+if spec["recipe"] == "blobs":
+    d = synth.blobs_tone_curve(0, 1, 1, spec["h_l"], spec["w_l"], spec["f"])
+else:
+    d = synth.photo_like(0, 1, 1, spec["h_l"], spec["w_l"], spec["f"])
+R = synth.upstream_grad(1, d["I_h"].shape).numpy()
+p, il, ih = (d[k].numpy() for k in ("p_l", "I_l", "I_h"))
+reps = int(spec.get("reps", 1))
+oracle.forward(p, il, ih, spec["r"], spec["eps"])  # warm-up
+t0 = time.perf_counter()
+for _ in range(reps):
+    oracle.forward(p, il, ih, spec["r"], spec["eps"])
+    oracle.backward(R, p, il, ih, spec["r"], spec["eps"])
+dt = (time.perf_counter() - t0) / reps
+print(json.dumps({{"seconds_per_plane": dt}}))
+"""
+
+
+def cpu_oracle(spec, reps=1):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    s = dict(spec)
+    s["reps"] = reps
+    code = ORACLE_SNIPPET.format(root=ROOT, spec=json.dumps(s))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    sec = json.loads(out.stdout.strip().splitlines()[-1])["seconds_per_plane"]
+    pix = spec["h_l"] * spec["f"] * spec["w_l"] * spec["f"] / spec["C"]  # one plane = 1/C of an image
+    return pix / sec / 1e6, sec
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec = WORKLOADS[MAIN]
+    steps = max(1, min(args.steps, 30))  # each step ~0.6 s of CPU work; bounded to keep the run short
+    t0 = time.perf_counter()
+    value, sec = cpu_oracle(spec, reps=steps)
+    wall = time.perf_counter() - t0
+    sample = (f"one plane (1 of {spec['N'] * spec['C']}) of {MAIN} per step: forward + backward, "
+              f"{spec['h_l']}x{spec['w_l']} -> {spec['h_l'] * spec['f']}x{spec['w_l'] * spec['f']}, "
+              f"{sec:.2f} s per plane, single-threaded numpy FP64")
+    pix_total = spec["N"] * spec["h_l"] * spec["f"] * spec["w_l"] * spec["f"]
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpix/s",
+            "n_gpus": args.gpus, "steps": steps, "warmup": 1,
+            "ms_per_step": round(pix_total / value / 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": MAIN, **{k: spec[k] for k in spec}},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- main
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    from paper_1803_05619_gb300 import build as B
+    rank, ws, local = dist_setup()
+    if rank == 0:
+        B.build()
+    barrier(ws)
+    from paper_1803_05619_gb300 import _lib as L
+    device = torch.device("cuda", local)
+    spec = WORKLOADS[MAIN]
+    g, dt = make_inputs(spec, device, seed=1000 * rank)
+    step = Step(g, spec, device)
+    N, C, h_l, w_l, h, w = step.shape
+    pix = N * h * w
+
+    n0 = L.dgf_launch_count()
+    step()
+    per_step = L.dgf_launch_count() - n0
+    with ClockSampler(local) as clk:
+        ms = time_loop(step, args.steps, args.warmup, ws, device, clock=clk)
+    launches = per_step * args.steps
+    value = ws * pix / (ms * 1e-3) / 1e6
+    fwd_ms = time_loop(step.forward, max(10, args.steps // 2), args.warmup, ws, device)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic (seeded; blobs+edges+noise photo "
+        "stand-in, tone-curve target, N(0,1) upstream gradient)",
+        "config": {"workload": MAIN, "step": "forward+backward", "N": N, "C": C, "h_l": h_l, "w_l": w_l,
+                   "h": h, "w": w, "r": spec["r"], "eps": spec["eps"],
+                   "l2": "inputs larger than L2 (each high-res tensor %d MB > 129 MB)"
+                         % (N * C * h * w * g["I_h"].element_size() // 10**6),
+                   "parallelism": f"images sharded over {ws} GPU(s), no collective"},
+        "fwd": {"value": round(ws * pix / (fwd_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
+                "ms_per_step": round(fwd_ms, 5)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and args.quick:
+        print(json.dumps(line), flush=True)
+    elif rank == 0:
+        line["roofline"] = roofline(step, spec, min(args.steps, 200), args.warmup, MAIN)
+        e_ms, bi, bo, n_e2e = e2e(step, args.steps, args.warmup, device)
+        line["e2e"] = {"value": round(pix / (e_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
+                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": n_e2e,
+                       "ms_per_step": round(e_ms, 4)}
+        if not args.no_extra:
+            line["bf16_4k"] = bench_bf16_4k(args, device)
+        if not args.no_oracle:
+            reps = 15
+            cv, csec = cpu_oracle(spec, reps=reps)
+            line["cpu_baseline"] = {"value": round(cv, 4), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"{reps} x one plane (1 of {N * C}) of {MAIN}, forward + "
+                                              f"backward, {csec:.2f} s per plane, single-threaded numpy FP64"}
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def bench_bf16_4k(args, device):
+    """BF16 4K batch: single-call fwd+bwd (both images per launch) and the
+    graph-replayed batched forward."""
+    import torch
+
+    from paper_1803_05619_gb300 import _lib as L
+    from paper_1803_05619_gb300.layer import gf_forward_batched
+    name = "bf16_4k_2x3x3840x2160"
+    spec = WORKLOADS[name]
+    g, dt = make_inputs(spec, device, seed=7)
+    step = Step(g, spec, device)
+    N, C, h_l, w_l, h, w = step.shape
+    pix = N * h * w
+    steps = max(20, min(args.steps, 1000))
+    ms = time_loop(step, steps, args.warmup, 1, device)
+    fwd_ms = time_loop(step.forward, steps, args.warmup, 1, device)
+    images = [{"p_l": g["p_l"][i], "I_l": g["I_l"][i], "I_h": g["I_h"][i], "r": spec["r"],
+               "eps": spec["eps"]} for i in range(N)]
+    outs = [torch.empty_like(g["I_h"][i]) for i in range(N)]
+    bat_ms = time_loop(lambda: gf_forward_batched(images, out=outs), steps, args.warmup, 1, device)
+    rl = roofline(step, spec, min(steps, 200), args.warmup, name)
+    esz = 2
+    fb_bytes = pix * C * esz * (2 + 3) + N * C * h_l * w_l * esz * (2 + 2 + 2)
+    return {"workload": name, "fwd_bwd_mpix_s": round(pix / (ms * 1e-3) / 1e6, 2),
+            "fwd_mpix_s": round(pix / (fwd_ms * 1e-3) / 1e6, 2),
+            "batched_graph_fwd_mpix_s": round(pix / (bat_ms * 1e-3) / 1e6, 2),
+            "ms_fwd_bwd": round(ms, 5), "fwd_bwd_frac_of_nominal_8TBs": round(
+                fb_bytes / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4),
+            "fwd_bwd_algorithmic_bytes": fb_bytes, "roofline": rl}
+
+
+if __name__ == "__main__":
+    main()

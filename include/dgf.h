@@ -1,0 +1,187 @@
+/*
+ * dgf.h - C ABI of the fast guided filtering layer on sm_103a.
+ *
+ * The layer (Wu et al., "Fast End-to-End Trainable Guided Filter") maps a
+ * low-resolution target p_l (the paper's O_l), a low-resolution guide I_l
+ * and a high-resolution guide I_h, with window radius r and ridge eps, to
+ * the high-resolution output O_h (Sec. 3.1-3.3):
+ *
+ *   mean_I, mean_p, var_I, cov_Ip over every (2r+1)^2 window of the
+ *   low-resolution grid, clipped to the image and divided by the number of
+ *   in-image pixels;  A = cov_Ip / (var_I + eps),  b = mean_p - A mean_I
+ *   (Eq. 1);  Abar, bbar = box means of A and b;  Abar_h, bbar_h = bilinear
+ *   upsampling to h x w with half-pixel centres (align_corners = False);
+ *   O_h = Abar_h * I_h + bbar_h  (Eq. 2).
+ *
+ * dgf_backward returns the gradients of Algorithm 1 (with respect to p_l,
+ * I_l and I_h, extended through the box mean of A and b).  With a guidance
+ * transform F (Sec. 3.4: 1x1 conv, leaky ReLU, 1x1 conv) the guides become
+ * G_h = F(I_h) and G_l = the f x f block mean of G_h, and the weight
+ * gradients are returned as well.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout:    every image tensor is NCHW, contiguous, planes back to back:
+ *            element (n, c, y, x) of an N x C x H x W tensor is at
+ *            ((n*C + c)*H + y)*W + x.
+ * Memory:    every tensor pointer is DEVICE memory owned by the caller.  The
+ *            library allocates no tensor memory; it uses the caller's
+ *            workspace (dgf_workspace_size bytes, 256-byte aligned) for its
+ *            FP32 intermediates.
+ * Precision: storage is FP32, BF16 or FP16 (dgf_dtype); every sum and every
+ *            product is formed in FP32; stores round to nearest even.
+ * Streams:   calls enqueue kernels on `stream` and return without waiting.
+ *            A workspace may be reused by calls on the same stream; calls
+ *            that overlap on the device need separate workspaces.  Calls
+ *            that pass a guidance transform stage its 93 weights in the
+ *            library's constant memory, so such calls must not overlap on
+ *            the device (serialise them on one stream).
+ * Errors:    arguments are validated on the host before anything is
+ *            enqueued; a bad argument returns DGF_ERR_INVALID (or
+ *            DGF_ERR_UNSUPPORTED / DGF_ERR_WORKSPACE) and enqueues nothing.
+ *            A CUDA error at launch returns DGF_ERR_CUDA.  dgf_last_error()
+ *            gives a message for the calling thread's last non-OK status.
+ *            No entry point aborts, traps or prints.
+ * Sizes:     1 <= h_l <= h and 1 <= w_l <= w; the scale is the size ratio,
+ *            so non-integer ratios are accepted.  r >= 0, eps > 0 and
+ *            finite, N >= 0, C >= 1 (C = 3 when a guidance transform is
+ *            given).  N = 0 is a valid empty call.
+ */
+#ifndef DGF_H
+#define DGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* dgf_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum { DGF_F32 = 0, DGF_BF16 = 1, DGF_F16 = 2 } dgf_dtype;
+
+typedef enum {
+    DGF_OK = 0,
+    DGF_ERR_INVALID = 1,     /* bad pointer, size, radius, eps or dtype   */
+    DGF_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. C != 3 with a guide) */
+    DGF_ERR_CUDA = 3,        /* a CUDA runtime call failed                */
+    DGF_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out        */
+    DGF_ERR_WORKSPACE = 5    /* workspace missing, misaligned or too small */
+} dgf_status;
+
+/*
+ * Guidance transform F of Sec. 3.4 / Table 1 (1x1 convolutions, no
+ * normalisation): hidden = w1 . x (no bias), leaky ReLU with `slope`,
+ * G = w2 . lrelu(hidden) + b2, per pixel, C = 3 in and out.
+ * w1: hidden x 3 row-major, w2: 3 x hidden row-major, b2: 3; all FP32
+ * DEVICE pointers.  1 <= hidden <= 16.  A NULL dgf_guide* means F = identity.
+ */
+typedef struct {
+    const float* w1;
+    const float* w2;
+    const float* b2;
+    int hidden;
+    float slope;
+} dgf_guide;
+
+/* One image of a batched call (per-image sizes, radius, eps; C channels). */
+typedef struct {
+    const void* p_l; /* C x h_l x w_l */
+    const void* I_l; /* C x h_l x w_l */
+    const void* I_h; /* C x h x w     */
+    void* O_h;       /* C x h x w     */
+    int C, h_l, w_l, h, w, r;
+    float eps;
+} dgf_image;
+
+/*
+ * Bytes of workspace that dgf_forward and dgf_backward need for these sizes
+ * (the larger of the two; FP32 Abar/bbar, their gradients, the low-res
+ * guide when g != NULL, and weight-gradient partials).  Returns 0 for
+ * invalid sizes.  Pure host function.
+ */
+size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r,
+                          dgf_dtype dt, const dgf_guide* g);
+
+/*
+ * Forward pass, Eq. 1-2 with the box mean of A and b (Sec. 3.2-3.3).
+ * p_l, I_l: N x C x h_l x w_l; I_h, O_h: N x C x h x w; all of dtype dt.
+ * With g != NULL, I_l is ignored (may be NULL): the low-resolution guide is
+ * the f x f block mean of F(I_h), which requires h = f*h_l and w = f*w_l.
+ */
+dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* O_h,
+                       int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
+                       dgf_dtype dt, const dgf_guide* g,
+                       void* workspace, size_t ws_bytes, dgf_stream_t stream);
+
+/*
+ * Backward pass, Algorithm 1 extended through the box mean of A and b.
+ * dO_h is the upstream gradient dL/dO_h (N x C x h x w, dtype dt).  Outputs
+ * (each nullable = not wanted): dp_l, dI_l (N x C x h_l x w_l, dtype dt),
+ * dI_h (N x C x h x w, dtype dt), and with g != NULL dW: 3*hidden + 3*hidden
+ * + 3 FP32 values laid out [dw1 | dw2 | db2], OVERWRITTEN with the sum over
+ * the batch.  With g != NULL, dI_l must be NULL (I_l is not an input).
+ * Every statistic is recomputed from the inputs; nothing from the forward
+ * call is needed.
+ */
+dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, const void* I_h,
+                        void* dp_l, void* dI_l, void* dI_h, float* dW,
+                        int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
+                        dgf_dtype dt, const dgf_guide* g,
+                        void* workspace, size_t ws_bytes, dgf_stream_t stream);
+
+/* Workspace bytes for dgf_forward_batched on this list (0 if invalid). */
+size_t dgf_workspace_size_batched(const dgf_image* imgs, int n, dgf_dtype dt);
+
+/*
+ * Forward pass of n images of different sizes, radii and scale factors
+ * (same dtype, F = identity) in one persistent launch per stage, replayed
+ * from a CUDA graph that the library builds once per (dtype, device) and
+ * updates in place on later calls.  Each image is computed exactly as
+ * dgf_forward computes it with the same tile configuration, so results are
+ * bitwise identical to per-image calls.  n <= DGF_MAX_BATCH.
+ * The image table is read on the host during the call; it need not outlive it.
+ */
+#define DGF_MAX_BATCH 128
+dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtype dt,
+                               void* workspace, size_t ws_bytes, dgf_stream_t stream);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char* dgf_last_error(void);
+
+/*
+ * Optional per-kernel timing with CUDA events recorded on the launch stream
+ * around every kernel the library enqueues (for benchmarks).  While enabled,
+ * each call synchronises its stream before returning, to read the events.
+ * dgf_profile_read fills up to `cap` entries of names/milliseconds/launches
+ * accumulated since the last reset and returns the number of kernel kinds.
+ */
+void dgf_profile_enable(int on);
+void dgf_profile_reset(void);
+int dgf_profile_read(const char** names, double* total_ms, long long* launches, int cap);
+
+/* Number of kernels this process has enqueued through the library. */
+long long dgf_launch_count(void);
+
+/*
+ * Reads and clears the library's device status word on the current device
+ * (synchronous).  0 = no device-side error since the last read;
+ * bit 0 = a bounded wait for a TMA copy ran out (the result of that call is
+ * invalid, DGF_ERR_TIMEOUT); -1 = the word could not be read.
+ */
+int dgf_device_status(void);
+
+/* Allows (1, default) or forbids (0) TMA staging of the low-resolution
+ * tiles; with 0 every tile is staged with plain loads.  Results are
+ * identical either way; this exists for testing the two paths. */
+void dgf_set_tma(int on);
+
+/* Releases cached graphs and tuning state (idempotent). */
+void dgf_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGF_H */

@@ -1,0 +1,688 @@
+// C ABI of the guided filtering layer (include/dgf.h): argument validation,
+// workspace layout, tile planning, kernel sequencing, the graph-replayed
+// batched path, launch counting and optional per-kernel event timing.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dgf.h"
+#include "batch.cuh"
+#include "kernels.h"
+#include "tma.cuh"
+
+namespace dgf {
+
+// -------------------------------------------------------------- errors
+static thread_local std::string t_err;
+
+static dgf_status fail(dgf_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+static dgf_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(DGF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------- launch count + profiling
+static std::atomic<long long> g_launches{0};
+
+struct ProfEntry {
+    double ms = 0.0;
+    long long n = 0;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::map<std::string, ProfEntry> g_prof;
+
+struct Pending {
+    const char* name;
+    cudaEvent_t a, b;
+};
+
+class Launcher {
+   public:
+    explicit Launcher(cudaStream_t s) : s_(s) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        prof_ = g_prof_on;
+    }
+    template <class Fn>
+    cudaError_t run(const char* name, Fn&& fn) {
+        g_launches.fetch_add(1);
+        if (!prof_) return fn();
+        Pending p{name, nullptr, nullptr};
+        cudaEventCreate(&p.a);
+        cudaEventCreate(&p.b);
+        cudaEventRecord(p.a, s_);
+        cudaError_t e = fn();
+        cudaEventRecord(p.b, s_);
+        pend_.push_back(p);
+        return e;
+    }
+    ~Launcher() {
+        if (pend_.empty()) return;
+        cudaStreamSynchronize(s_);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (auto& p : pend_) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                ProfEntry& e = g_prof[p.name];
+                e.ms += ms;
+                e.n += 1;
+            }
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+    }
+
+   private:
+    cudaStream_t s_;
+    bool prof_ = false;
+    std::vector<Pending> pend_;
+};
+
+// --------------------------------------------------------------- status word
+// Device-side error bits (bounded waits that ran out); read by dgf_device_status.
+__device__ uint32_t g_status_word;
+
+static uint32_t* status_ptr() {
+    static uint32_t* p[64] = {nullptr};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (p[dev] == nullptr) {
+        void* a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_status_word) != cudaSuccess) return nullptr;
+        p[dev] = static_cast<uint32_t*>(a);
+    }
+    return p[dev];
+}
+
+// ------------------------------------------------------------------ sizes
+static size_t esize(dgf_dtype dt) { return dt == DGF_F32 ? 4 : 2; }
+static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+constexpr int kMaxRadius = 16;
+
+struct Layout {
+    size_t coef, dcoef, gl, dgl, partials, total;
+};
+
+static Layout layout(int N, int C, int h_l, int w_l, bool guided) {
+    const size_t lo = (size_t)N * C * h_l * w_l;
+    Layout L{};
+    size_t off = 0;
+    L.coef = off;
+    off += align256(lo * sizeof(float2));
+    L.dcoef = off;
+    off += align256(lo * sizeof(float2));
+    if (guided) {
+        L.gl = off;
+        off += align256(lo * sizeof(float));
+        L.dgl = off;
+        off += align256(lo * sizeof(float));
+        L.partials = off;
+        off += align256((size_t)kMaxK6Blocks * kWGradPadded * sizeof(float));
+    }
+    L.total = off;
+    return L;
+}
+
+static bool bad_eps(float eps) { return !(eps > 0.f) || !std::isfinite(eps); }
+
+static int integer_factor(int h_l, int w_l, int h, int w) {
+    if (h % h_l != 0 || w % w_l != 0) return 0;
+    const int fy = h / h_l, fx = w / w_l;
+    return fy == fx ? fy : 0;
+}
+
+// Vector width (elements) of the high-res passes: 16-byte vectors, else
+// 8-byte vectors, else scalars; the width must divide w and keep every
+// pointer aligned.
+static int pick_vec(dgf_dtype dt, int w, std::initializer_list<const void*> ptrs) {
+    const int esz = (int)esize(dt);
+    for (int v = 16 / esz; v >= 8 / esz; v >>= 1) {
+        if (w % v != 0) continue;
+        bool ok = true;
+        for (const void* p : ptrs)
+            if (p != nullptr && (reinterpret_cast<uintptr_t>(p) % (size_t)(v * esz)) != 0) ok = false;
+        if (ok) return v;
+    }
+    return 1;
+}
+
+static bool aligned16(std::initializer_list<const void*> ptrs) {
+    for (const void* p : ptrs)
+        if (p != nullptr && reinterpret_cast<uintptr_t>(p) % 16 != 0) return false;
+    return true;
+}
+
+struct Plan {
+    int F = 0;      // integer factor (0 = general ratio)
+    int vec = 1;    // K2 / K3 vector width
+    int k1_ty = 32, k1_tx = 32;
+    int k4_ty = 16, k4_tx = 16;
+    int k2_th = 32;
+    int k3_lth = 8;
+    bool k3_fast = false;
+};
+
+static size_t g_smem_optin = 0;
+static size_t smem_limit() {
+    if (g_smem_optin == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+            v = 227 * 1024;
+        g_smem_optin = (size_t)v;
+    }
+    return g_smem_optin;
+}
+
+static bool pick_lowres_tiles(int r, Plan& p) {
+    const size_t lim = smem_limit();
+    static const int cand[] = {32, 16, 8};
+    bool ok1 = false, ok4 = false;
+    for (int t : cand)
+        if (k1_smem_bytes(r, t, t) <= lim) {
+            p.k1_ty = p.k1_tx = t;
+            ok1 = true;
+            break;
+        }
+    for (int t : cand) {
+        if (t > 16) continue;
+        if (k4_smem_bytes(r, t, t) <= lim) {
+            p.k4_ty = p.k4_tx = t;
+            ok4 = true;
+            break;
+        }
+    }
+    return ok1 && ok4;
+}
+
+static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r,
+                      std::initializer_list<const void*> hires_ptrs) {
+    Plan p;
+    p.F = integer_factor(h_l, w_l, h, w);
+    p.vec = pick_vec(dt, w, hires_ptrs);
+    pick_lowres_tiles(r, p);
+    p.k3_fast = p.F > 0 && k3_fast_ok(p.vec, p.F);
+    p.k3_lth = p.F >= 8 ? 4 : (p.F >= 4 ? 8 : 16);
+    return p;
+}
+
+// --------------------------------------------------------------- TMA maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+static bool g_tma_allowed = true;
+
+// One plane stack (planes x h x w of element size esz) for a K1 tile of
+// TY x TX with radius r.  False when the TMA alignment rules do not hold.
+static bool make_tma(TmaPlane& tp, const void* base, CUtensorMapDataType ty, int esz, int planes, int h, int w,
+                     int r, int TY, int TX) {
+    EncodeTiledFn enc = encode_fn();
+    if (enc == nullptr) return false;
+    const int U = 16 / esz;  // elements per 16 bytes
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
+    if (((size_t)w * esz) % 16 != 0) return false;
+    if (TX % U != 0) return false;
+    const int lead = (2 * r + U - 1) / U * U;  // box starts on a 16-byte column boundary
+    tp.off = lead - 2 * r;
+    tp.bx = (tp.off + TX + 4 * r + U - 1) / U * U;
+    tp.by = TY + 4 * r;
+    tp.esize = esz;
+    if (tp.bx > 256 || tp.by > 256) return false;
+    cuuint64_t gdim[3] = {(cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)planes};
+    cuuint64_t gstride[2] = {(cuuint64_t)w * esz, (cuuint64_t)w * h * esz};
+    cuuint32_t box[3] = {(cuuint32_t)tp.bx, (cuuint32_t)tp.by, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult rc = enc(&tp.map, ty, 3, const_cast<void*>(base), gdim, gstride, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return rc == CUDA_SUCCESS;
+}
+
+static CUtensorMapDataType tma_type(dgf_dtype dt) {
+    return dt == DGF_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                         : (dt == DGF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+}
+
+// TMA pair for K1's (G, P) staging; also checks that the landing buffers fit.
+static TmaPair make_tma_pair(const void* G, dgf_dtype dg, const void* P, dgf_dtype dp, int planes, int h, int w,
+                             int r, int TY, int TX) {
+    TmaPair t;
+    memset(&t, 0, sizeof t);
+    t.enabled = 0;
+    if (!g_tma_allowed) return t;
+    if (!make_tma(t.a, G, tma_type(dg), (int)esize(dg), planes, h, w, r, TY, TX)) return t;
+    if (!make_tma(t.b, P, tma_type(dp), (int)esize(dp), planes, h, w, r, TY, TX)) return t;
+    // landing buffers live in K1's row-statistics region (4 EY2 EX1 floats)
+    const size_t region = (size_t)4 * (TY + 4 * r) * (TX + 2 * r) * sizeof(float);
+    const size_t need = (size_t)t.a.bx * t.a.by * t.a.esize + (size_t)t.b.bx * t.b.by * t.b.esize + 256;
+    if (need > region + tma_extra_bytes(r, TY, TX)) return t;
+    t.enabled = 1;
+    return t;
+}
+
+// --------------------------------------------------------------- validation
+static dgf_status check_sizes(int N, int C, int h_l, int w_l, int h, int w, int r, float eps, dgf_dtype dt) {
+    if ((int)dt < 0 || (int)dt > 2) return fail(DGF_ERR_INVALID, "dtype %d is not FP32, BF16 or FP16", (int)dt);
+    if (N < 0) return fail(DGF_ERR_INVALID, "N = %d < 0", N);
+    if (C < 1) return fail(DGF_ERR_INVALID, "C = %d < 1", C);
+    if (h_l < 1 || w_l < 1 || h < 1 || w < 1)
+        return fail(DGF_ERR_INVALID, "sizes must be >= 1 (h_l=%d w_l=%d h=%d w=%d)", h_l, w_l, h, w);
+    if (h_l > h || w_l > w) return fail(DGF_ERR_INVALID, "low-res %dx%d larger than high-res %dx%d", h_l, w_l, h, w);
+    if (r < 0) return fail(DGF_ERR_INVALID, "radius r = %d < 0", r);
+    if (r > kMaxRadius) return fail(DGF_ERR_UNSUPPORTED, "radius r = %d > %d", r, kMaxRadius);
+    if (bad_eps(eps)) return fail(DGF_ERR_INVALID, "eps must be finite and > 0");
+    if ((long long)N * C > 65535) return fail(DGF_ERR_UNSUPPORTED, "N*C = %lld planes > 65535", (long long)N * C);
+    if ((long long)h * w >= (1LL << 40)) return fail(DGF_ERR_UNSUPPORTED, "plane too large");
+    return DGF_OK;
+}
+
+static dgf_status check_guide(const dgf_guide* g, int C, int h_l, int w_l, int h, int w, dgf_dtype dt) {
+    if (g == nullptr) return DGF_OK;
+    if (g->w1 == nullptr || g->w2 == nullptr || g->b2 == nullptr)
+        return fail(DGF_ERR_INVALID, "guide weights must be non-NULL");
+    if (g->hidden < 1 || g->hidden > 16) return fail(DGF_ERR_INVALID, "guide hidden = %d not in [1, 16]", g->hidden);
+    if (!std::isfinite(g->slope)) return fail(DGF_ERR_INVALID, "guide slope not finite");
+    if (C != 3) return fail(DGF_ERR_UNSUPPORTED, "guidance transform needs C = 3 (got %d)", C);
+    const int F = integer_factor(h_l, w_l, h, w);
+    if (F == 0) return fail(DGF_ERR_INVALID, "guidance transform needs h = f h_l and w = f w_l");
+    if (!guided_supported(dt, w, F))
+        return fail(DGF_ERR_UNSUPPORTED, "guidance transform: factor %d with width %d not supported", F, w);
+    return DGF_OK;
+}
+
+static dgf_status check_ws(void* ws, size_t ws_bytes, size_t need) {
+    if (need == 0) return DGF_OK;
+    if (ws == nullptr) return fail(DGF_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", need);
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(DGF_ERR_WORKSPACE, "workspace not 256-byte aligned");
+    if (ws_bytes < need) return fail(DGF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    return DGF_OK;
+}
+
+static cudaError_t run_k1(Launcher& L, dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef,
+                          int planes, int h_l, int w_l, int r, float eps, const Plan& p, cudaStream_t s) {
+    TmaPair tma = make_tma_pair(G, gf32 ? DGF_F32 : dt, P, dt, planes, h_l, w_l, r, p.k1_ty, p.k1_tx);
+    uint32_t* st = status_ptr();
+    return L.run("k1_lowres_coef", [&] {
+        return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, p.k1_ty, p.k1_tx, tma, st, s);
+    });
+}
+
+}  // namespace dgf
+
+// ------------------------------------------------------------------ batched
+namespace dgf {
+
+struct BatchGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t n1 = nullptr, n2 = nullptr;
+};
+
+std::mutex g_batch_mu;
+std::map<std::pair<int, int>, BatchGraph> g_batch;  // (device, dtype)
+
+struct BatchPrep {
+    BatchParams bp;
+    size_t smem1 = 0, smem2 = 0;
+    size_t ws = 0;
+};
+
+dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_base, BatchPrep& out) {
+    if (n < 0 || n > DGF_MAX_BATCH) return fail(DGF_ERR_INVALID, "batch size %d not in [0, %d]", n, DGF_MAX_BATCH);
+    if (n > 0 && imgs == nullptr) return fail(DGF_ERR_INVALID, "image table is NULL");
+    BatchParams& bp = out.bp;
+    memset(&bp, 0, sizeof bp);
+    bp.n = n;
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const dgf_image& im = imgs[i];
+        dgf_status st = check_sizes(1, im.C, im.h_l, im.w_l, im.h, im.w, im.r, im.eps, dt);
+        if (st != DGF_OK) return fail(st, "image %d: %s", i, t_err.c_str());
+        if (ws_base != nullptr &&
+            (im.p_l == nullptr || im.I_l == nullptr || im.I_h == nullptr || im.O_h == nullptr))
+            return fail(DGF_ERR_INVALID, "image %d: NULL pointer", i);
+        BatchImage& b = bp.img[i];
+        b.p_l = im.p_l;
+        b.I_l = im.I_l;
+        b.I_h = im.I_h;
+        b.O_h = im.O_h;
+        b.C = im.C;
+        b.h_l = im.h_l;
+        b.w_l = im.w_l;
+        b.h = im.h;
+        b.w = im.w;
+        b.r = im.r;
+        b.eps = im.eps;
+        Plan p = make_plan(dt, im.h_l, im.w_l, im.h, im.w, im.r, {im.I_h, im.O_h});
+        // the persistent K2 has fast paths for factors 4 and 8 only
+        b.F = (p.F == 4 || p.F == 8) ? p.F : 0;
+        b.vec = p.vec;
+        b.k1_ty = p.k1_ty;
+        b.k1_tx = p.k1_tx;
+        b.k2_th = p.k2_th;
+        b.k1_nx = (im.w_l + b.k1_tx - 1) / b.k1_tx;
+        b.k1_ny = (im.h_l + b.k1_ty - 1) / b.k1_ty;
+        b.k2_nx = (im.w + 32 * b.vec - 1) / (32 * b.vec);
+        b.k2_ny = (im.h + b.k2_th - 1) / b.k2_th;
+        b.coef = ws_base ? reinterpret_cast<float2*>(ws_base + off) : nullptr;
+        off += align256((size_t)im.C * im.h_l * im.w_l * sizeof(float2));
+        bp.k1_start[i + 1] = bp.k1_start[i] + b.k1_nx * b.k1_ny * im.C;
+        bp.k2_start[i + 1] = bp.k2_start[i] + b.k2_nx * b.k2_ny * im.C;
+        out.smem1 = std::max(out.smem1, k1_smem_bytes(b.r, b.k1_ty, b.k1_tx));
+        out.smem2 = std::max(out.smem2, k2_smem_bytes(b.vec, b.F, b.w_l, b.w, b.k2_th));
+    }
+    bp.k1_total = bp.k1_start[n];
+    bp.k2_total = bp.k2_start[n];
+    out.ws = off;
+    return DGF_OK;
+}
+
+}  // namespace dgf
+
+
+using namespace dgf;
+
+// ====================================================================== ABI
+extern "C" {
+
+size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt, const dgf_guide* g) {
+    if (check_sizes(N, C, h_l, w_l, h, w, r, 1.f, dt) != DGF_OK) return 0;
+    return layout(N, C, h_l, w_l, g != nullptr).total;
+}
+
+dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
+                       int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
+                       size_t ws_bytes, dgf_stream_t stream) {
+    dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
+    if (st != DGF_OK) return st;
+    if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
+    if (N == 0) return DGF_OK;
+    if (p_l == nullptr || I_h == nullptr || O_h == nullptr || (g == nullptr && I_l == nullptr))
+        return fail(DGF_ERR_INVALID, "NULL input or output pointer");
+    const Layout lay = layout(N, C, h_l, w_l, g != nullptr);
+    if ((st = check_ws(workspace, ws_bytes, lay.total)) != DGF_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
+    const int planes = N * C;
+    Plan p = make_plan(dt, h_l, w_l, h, w, r, {I_h, O_h});
+    Launcher L(s);
+    cudaError_t e;
+    if (g == nullptr) {
+        e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+        if (e != cudaSuccess) return cuda_fail(e, "k1");
+        e = L.run("k2_hires_apply", [&] {
+            return launch_k2(dt, 0, coef, I_h, O_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k2");
+        return DGF_OK;
+    }
+    float* G_l = reinterpret_cast<float*>(ws + lay.gl);
+    if (!aligned16({I_h, O_h})) return fail(DGF_ERR_UNSUPPORTED, "guidance transform needs 16-byte aligned I_h, O_h");
+    e = guide_upload(g->w1, g->w2, g->b2, g->hidden, s);
+    if (e != cudaSuccess) return cuda_fail(e, "guide weights");
+    e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "k5");
+    e = run_k1(L, dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k1");
+    e = L.run("k2_hires_apply_guided", [&] {
+        return launch_k2_guided(dt, coef, I_h, O_h, N, h_l, w_l, h, w, p.F, 8, g->slope, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "k2g");
+    return DGF_OK;
+}
+
+dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l, void* dI_l,
+                        void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
+                        dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes, dgf_stream_t stream) {
+    dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
+    if (st != DGF_OK) return st;
+    if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
+    if (g != nullptr && dI_l != nullptr) return fail(DGF_ERR_INVALID, "dI_l must be NULL with a guidance transform");
+    if (g == nullptr && dW != nullptr) return fail(DGF_ERR_INVALID, "dW needs a guidance transform");
+    if (N == 0) {
+        if (g != nullptr && dW != nullptr) {
+            cudaError_t e = cudaMemsetAsync(dW, 0, sizeof(float) * (6 * g->hidden + 3),
+                                            reinterpret_cast<cudaStream_t>(stream));
+            if (e != cudaSuccess) return cuda_fail(e, "memset dW");
+        }
+        return DGF_OK;
+    }
+    if (dO_h == nullptr || p_l == nullptr || I_h == nullptr || (g == nullptr && I_l == nullptr))
+        return fail(DGF_ERR_INVALID, "NULL input pointer");
+    const Layout lay = layout(N, C, h_l, w_l, g != nullptr);
+    if ((st = check_ws(workspace, ws_bytes, lay.total)) != DGF_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
+    float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
+    const int planes = N * C;
+    Plan p = make_plan(dt, h_l, w_l, h, w, r, {dO_h, I_h, dI_h});
+    Launcher L(s);
+    cudaError_t e;
+    if (g == nullptr) {
+        if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
+        // coefficients are recomputed, not saved from the forward call
+        if (dI_h != nullptr) {
+            e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+            if (e != cudaSuccess) return cuda_fail(e, "k1");
+        }
+        if (p.k3_fast) {
+            e = L.run("k3_hires_bwd", [&] {
+                return launch_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, p.k3_lth, s);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "k3");
+        } else {
+            if (dI_h != nullptr) {
+                e = L.run("k2_hires_scale", [&] {
+                    return launch_k2(dt, 1, coef, dO_h, dI_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
+                });
+                if (e != cudaSuccess) return cuda_fail(e, "k2 scale");
+            }
+            e = L.run("k3_gather_general", [&] {
+                return launch_k3_general(dt, dO_h, I_h, dcoef, planes, h_l, w_l, h, w, s);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "k3 general");
+        }
+        if (dp_l != nullptr || dI_l != nullptr) {
+            e = L.run("k4_lowres_bwd", [&] {
+                return launch_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4_ty,
+                                 p.k4_tx, s);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "k4");
+        }
+        return DGF_OK;
+    }
+    // with the guidance transform
+    float* G_l = reinterpret_cast<float*>(ws + lay.gl);
+    float* dG_l = reinterpret_cast<float*>(ws + lay.dgl);
+    float* partials = reinterpret_cast<float*>(ws + lay.partials);
+    const bool need_hi = dI_h != nullptr || dW != nullptr;
+    if (!aligned16({dO_h, I_h, dI_h}))
+        return fail(DGF_ERR_UNSUPPORTED, "guidance transform needs 16-byte aligned dO_h, I_h, dI_h");
+    e = guide_upload(g->w1, g->w2, g->b2, g->hidden, s);
+    if (e != cudaSuccess) return cuda_fail(e, "guide weights");
+    e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "k5");
+    e = run_k1(L, dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k1");
+    e = L.run("k3_hires_bwd_guided", [&] {
+        return launch_k3_guided(dt, dO_h, I_h, dcoef, N, h_l, w_l, h, w, p.F, g->slope, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "k3g");
+    if (dp_l != nullptr || need_hi) {
+        e = L.run("k4_lowres_bwd", [&] {
+            return launch_k4(dt, true, G_l, p_l, dcoef, dp_l, need_hi ? dG_l : nullptr, planes, h_l, w_l, r, eps,
+                             p.k4_ty, p.k4_tx, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k4");
+    }
+    if (need_hi) {
+        const int nb = k6_blocks(N, h, w);
+        e = L.run("k6_guide_bwd", [&] {
+            return launch_k6(dt, coef, dG_l, dO_h, I_h, dI_h, partials, N, h_l, w_l, h, w, p.F, g->slope, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k6");
+        if (dW != nullptr) {
+            e = L.run("k6_weight_reduce", [&] { return launch_wreduce(partials, nb, dW, g->hidden, s); });
+            if (e != cudaSuccess) return cuda_fail(e, "k6 reduce");
+        }
+    }
+    return DGF_OK;
+}
+
+extern "C" size_t dgf_workspace_size_batched(const dgf_image* imgs, int n, dgf_dtype dt) {
+    static thread_local BatchPrep prep;
+    if (prepare_batch(imgs, n, dt, nullptr, prep) != DGF_OK) return 0;
+    return prep.ws;
+}
+
+extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtype dt, void* workspace,
+                                          size_t ws_bytes, dgf_stream_t stream) {
+    static thread_local BatchPrep prep;
+    if ((int)dt < 0 || (int)dt > 2) return fail(DGF_ERR_INVALID, "dtype %d", (int)dt);
+    dgf_status st = prepare_batch(imgs, n, dt, nullptr, prep);
+    if (st != DGF_OK) return st;
+    if (n == 0) return DGF_OK;
+    if ((st = check_ws(workspace, ws_bytes, prep.ws)) != DGF_OK) return st;
+    st = prepare_batch(imgs, n, dt, static_cast<char*>(workspace), prep);
+    if (st != DGF_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaError_t e = k1_batched_kernel(dt, prep.smem1, &f1);
+    if (e != cudaSuccess) return cuda_fail(e, "k1 batched attr");
+    e = k2_batched_kernel(dt, prep.smem2, &f2);
+    if (e != cudaSuccess) return cuda_fail(e, "k2 batched attr");
+    int dev = 0, sms = 0, occ1 = 0, occ2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, f1, kThreads, prep.smem1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, f2, kThreads, prep.smem2);
+    const int g1 = std::max(1, std::min(prep.bp.k1_total, sms * std::max(occ1, 1)));
+    const int g2 = std::max(1, std::min(prep.bp.k2_total, sms * std::max(occ2, 1)));
+    uint32_t* stw = status_ptr();
+    void* args1[] = {&prep.bp, &stw};
+    void* args2[] = {&prep.bp};
+    cudaKernelNodeParams p1{}, p2{};
+    p1.func = f1;
+    p1.gridDim = dim3(g1);
+    p1.blockDim = dim3(kThreads);
+    p1.sharedMemBytes = (unsigned)prep.smem1;
+    p1.kernelParams = args1;
+    p2.func = f2;
+    p2.gridDim = dim3(g2);
+    p2.blockDim = dim3(kThreads);
+    p2.sharedMemBytes = (unsigned)prep.smem2;
+    p2.kernelParams = args2;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchGraph& bg = g_batch[{dev, (int)dt}];
+    if (bg.exec == nullptr) {
+        if ((e = cudaGraphCreate(&bg.graph, 0)) != cudaSuccess) return cuda_fail(e, "graph create");
+        if ((e = cudaGraphAddKernelNode(&bg.n1, bg.graph, nullptr, 0, &p1)) != cudaSuccess)
+            return cuda_fail(e, "graph node k1");
+        if ((e = cudaGraphAddKernelNode(&bg.n2, bg.graph, &bg.n1, 1, &p2)) != cudaSuccess)
+            return cuda_fail(e, "graph node k2");
+        if ((e = cudaGraphInstantiate(&bg.exec, bg.graph, 0)) != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    } else {
+        if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n1, &p1)) != cudaSuccess)
+            return cuda_fail(e, "graph update k1");
+        if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n2, &p2)) != cudaSuccess)
+            return cuda_fail(e, "graph update k2");
+    }
+    Launcher L(s);
+    e = L.run("batched_graph(k1,k2)", [&] {
+        g_launches.fetch_add(1);  // two kernels per replay
+        return cudaGraphLaunch(bg.exec, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    return DGF_OK;
+}
+
+extern "C" const char* dgf_last_error(void) { return t_err.c_str(); }
+
+extern "C" void dgf_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+}
+
+extern "C" void dgf_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.clear();
+}
+
+extern "C" int dgf_profile_read(const char** names, double* total_ms, long long* launches, int cap) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int i = 0;
+    for (auto& kv : g_prof) {
+        if (i < cap) {
+            if (names) names[i] = kv.first.c_str();
+            if (total_ms) total_ms[i] = kv.second.ms;
+            if (launches) launches[i] = kv.second.n;
+        }
+        ++i;
+    }
+    return i;
+}
+
+extern "C" long long dgf_launch_count(void) { return g_launches.load(); }
+
+extern "C" int dgf_device_status(void) {
+    uint32_t* p = status_ptr();
+    if (p == nullptr) return -1;
+    uint32_t v = 0;
+    if (cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    const uint32_t z = 0;
+    cudaMemcpy(p, &z, sizeof z, cudaMemcpyHostToDevice);
+    return (int)v;
+}
+
+extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
+
+extern "C" void dgf_shutdown(void) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto& kv : g_batch) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    g_batch.clear();
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Shared device helpers of the guided-filtering kernels: storage-type
+// conversion, vector access and the bilinear source coordinate.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgf {
+
+constexpr int kThreads = 256;  // threads per CTA of every tiled kernel
+constexpr int kWarps = kThreads / 32;
+
+// ---------------------------------------------------------------- storage
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+// VEC consecutive elements moved as one aligned access (16, 8, 4 or 2 bytes).
+template <typename T, int VEC>
+struct __align__(sizeof(T) * VEC) Vec {
+    T v[VEC];
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, float (&out)[VEC]) {
+    Vec<T, VEC> x = *reinterpret_cast<const Vec<T, VEC>*>(p);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) out[k] = to_f32<T>(x.v[k]);
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void store_vec(T* __restrict__ p, const float (&in)[VEC]) {
+    Vec<T, VEC> x;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) x.v[k] = from_f32<T>(in[k]);
+    *reinterpret_cast<Vec<T, VEC>*>(p) = x;
+}
+
+// ------------------------------------------------------------- upsampler
+// Bilinear source position of output sample y when n_in samples are
+// stretched over n_out (half-pixel centres, align_corners = False):
+// t = (y + 1/2) n_in / n_out - 1/2, clamped below at 0.  `i0` is floor(t);
+// the second tap is i0 + 1, which callers clamp to n_in - 1 by replicating
+// the last sample.  Exact integer arithmetic for i0; lam = remainder / (2 n_out).
+struct Tap {
+    int i0;
+    float lam;
+};
+
+__device__ __forceinline__ Tap tap_general(int y, int n_in, int n_out) {
+    long long num = (long long)(2 * y + 1) * n_in - n_out;  // = 2 n_out t
+    Tap t;
+    if (num <= 0) {
+        t.i0 = 0;
+        t.lam = 0.f;
+        return t;
+    }
+    long long den = 2LL * n_out;
+    long long i0 = num / den;
+    t.i0 = (int)i0;
+    t.lam = (float)(num - i0 * den) / (float)den;
+    return t;
+}
+
+// Integer factor F (n_out = F n_in): y = F j + q gives t = j + (2q + 1 - F) / (2F).
+// i0 may be -1 at the left border; callers replicate sample 0 there, which is
+// the same as clamping t at 0.
+template <int F>
+__device__ __forceinline__ Tap tap_int(int y) {
+    const int j = y / F, q = y - (y / F) * F;
+    const int t2 = 2 * q + 1 - F;
+    Tap t;
+    if (t2 < 0) {
+        t.i0 = j - 1;
+        t.lam = (float)(t2 + 2 * F) / (float)(2 * F);
+    } else {
+        t.i0 = j;
+        t.lam = (float)t2 / (float)(2 * F);
+    }
+    return t;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ float lerp(float a, float b, float lam) { return fmaf(lam, b - a, a); }
+
+}  // namespace dgf

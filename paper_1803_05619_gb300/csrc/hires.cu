@@ -1,0 +1,267 @@
+// High-resolution kernels: K2 (bilinear upsampling of Abar, bbar and the
+// affine step, Eq. 2) and K3 (the transposed upsampler of Algorithm 1's
+// first two lines as a gather, plus d I_h = d O_h * Abar_h).
+#include "batch.cuh"
+#include "common.cuh"
+#include "hires.cuh"
+#include "kernels.h"
+
+namespace dgf {
+
+template <typename T, int VEC, int F, int MODE>
+__global__ void __launch_bounds__(kThreads) k2_apply(const float2* __restrict__ coef, const T* __restrict__ in,
+                                                     T* __restrict__ out, int h_l, int w_l, int h, int w,
+                                                     int TH, int pitch) {
+    extern __shared__ __align__(128) float2 sAB[];
+    const size_t plane = blockIdx.z;
+    apply_tile<T, VEC, F, MODE>(coef + plane * h_l * w_l, in + plane * h * w, out + plane * h * w, h_l,
+                                w_l, h, w, blockIdx.y * TH, blockIdx.x * 32 * VEC, TH, pitch, sAB);
+}
+
+template <typename T, int VEC, int F>
+__global__ void __launch_bounds__(kThreads) k3_hires_bwd(const float2* __restrict__ coef, const T* __restrict__ R,
+                                                         const T* __restrict__ G, T* __restrict__ dG,
+                                                         float2* __restrict__ dcoef, int h_l, int w_l,
+                                                         int h, int w, int LTH) {
+    extern __shared__ __align__(128) float smem[];
+    const size_t plane = blockIdx.z;
+    const size_t hw = (size_t)h * w, lw = (size_t)h_l * w_l;
+    hires_bwd_tile<T, VEC, F>(coef + plane * lw, R + plane * hw, G + plane * hw,
+                              dG ? dG + plane * hw : nullptr, dcoef + plane * lw, h_l, w_l, h, w,
+                              blockIdx.y * LTH, blockIdx.x * K3Shape<VEC, F>::LTW, LTH, smem);
+}
+
+// -------------------------------------------------- K3 general (any ratio)
+// One thread per low-res (i, j): sum over the high-res rows/columns whose
+// (clamped) taps include it.  Slow but exact for every size; the fast tile
+// above covers integer factors.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k3_gather_general(const T* __restrict__ R, const T* __restrict__ G,
+                                                              float2* __restrict__ dcoef, int h_l, int w_l,
+                                                              int h, int w) {
+    const size_t plane = blockIdx.z;
+    const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int i = blockIdx.y * kWarps + (threadIdx.x >> 5);
+    if (i >= h_l || j >= w_l) return;
+    R += plane * h * w;
+    G += plane * h * w;
+    const long long ylo_ll = ((long long)(i - 1) * h) / h_l - 2;
+    const long long yhi_ll = ((long long)(i + 2) * h) / h_l + 2;
+    const long long xlo_ll = ((long long)(j - 1) * w) / w_l - 2;
+    const long long xhi_ll = ((long long)(j + 2) * w) / w_l + 2;
+    const int ylo = (int)max(ylo_ll, 0LL), yhi = (int)min(yhi_ll, (long long)h - 1);
+    const int xlo = (int)max(xlo_ll, 0LL), xhi = (int)min(xhi_ll, (long long)w - 1);
+    float su = 0.f, sv = 0.f;
+    for (int y = ylo; y <= yhi; ++y) {
+        const Tap ty = tap_general(y, h_l, h);
+        const int a0 = min(ty.i0, h_l - 1), a1 = min(ty.i0 + 1, h_l - 1);
+        const float wy = (a0 == i ? 1.f - ty.lam : 0.f) + (a1 == i ? ty.lam : 0.f);
+        if (wy == 0.f) continue;
+        float ru = 0.f, rv = 0.f;
+        for (int x = xlo; x <= xhi; ++x) {
+            const Tap tx = tap_general(x, w_l, w);
+            const int b0 = min(tx.i0, w_l - 1), b1 = min(tx.i0 + 1, w_l - 1);
+            const float wx = (b0 == j ? 1.f - tx.lam : 0.f) + (b1 == j ? tx.lam : 0.f);
+            if (wx == 0.f) continue;
+            const float r = to_f32<T>(R[(size_t)y * w + x]);
+            ru = fmaf(wx, r * to_f32<T>(G[(size_t)y * w + x]), ru);
+            rv = fmaf(wx, r, rv);
+        }
+        su = fmaf(wy, ru, su);
+        sv = fmaf(wy, rv, sv);
+    }
+    dcoef[plane * h_l * w_l + (size_t)i * w_l + j] = make_float2(su, sv);
+}
+
+// ------------------------------------------------------- batched K2 (persistent)
+template <typename T, int VEC, int F>
+__device__ __forceinline__ void apply_batched_tile(const BatchImage& im, int local, float2* sAB) {
+    const int per_plane = im.k2_nx * im.k2_ny;
+    const int plane = local / per_plane;
+    const int tp = local - plane * per_plane;
+    const int ty = tp / im.k2_nx, tx = tp - ty * im.k2_nx;
+    const size_t hw = (size_t)im.h * im.w, lw = (size_t)im.h_l * im.w_l;
+    const int pitch = k2_pitch(VEC, F, im.w_l, im.w);
+    apply_tile<T, VEC, F, 0>(im.coef + plane * lw, static_cast<const T*>(im.I_h) + plane * hw,
+                             static_cast<T*>(im.O_h) + plane * hw, im.h_l, im.w_l, im.h, im.w,
+                             ty * im.k2_th, tx * 32 * VEC, im.k2_th, pitch, sAB);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_apply_batched(const __grid_constant__ BatchParams bp) {
+    extern __shared__ __align__(128) float2 sAB[];
+    constexpr int VW = 16 / sizeof(T);  // 16-byte vectors
+    constexpr int VH = 8 / sizeof(T);   // 8-byte vectors
+    for (int tile = blockIdx.x; tile < bp.k2_total; tile += gridDim.x) {
+        const int i = batch_find(bp.k2_start, bp.n, tile);
+        const BatchImage& im = bp.img[i];
+        const int local = tile - bp.k2_start[i];
+        if (im.vec == VW) {
+            if (im.F == 4) apply_batched_tile<T, VW, 4>(im, local, sAB);
+            else if (im.F == 8) apply_batched_tile<T, VW, 8>(im, local, sAB);
+            else apply_batched_tile<T, VW, 0>(im, local, sAB);
+        } else if (im.vec == VH) {
+            if (im.F == 4) apply_batched_tile<T, VH, 4>(im, local, sAB);
+            else if (im.F == 8) apply_batched_tile<T, VH, 8>(im, local, sAB);
+            else apply_batched_tile<T, VH, 0>(im, local, sAB);
+        } else {
+            apply_batched_tile<T, 1, 0>(im, local, sAB);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+size_t k2_smem_bytes(int vec, int F, int w_l, int w, int TH) {
+    return (size_t)TH * k2_pitch(vec, F, w_l, w) * sizeof(float2);
+}
+
+int k3_ltw(int vec, int F) {
+    const int K = vec / F;
+    return K == 1 ? 29 : 30 * K;
+}
+
+size_t k3_smem_bytes(int vec, int F, int LTH) {
+    const int SXP = k3_ltw(vec, F) + 2;
+    return (size_t)F * (LTH + 1) * SXP * sizeof(float2) + (size_t)F * LTH * SXP * sizeof(float);
+}
+
+bool k3_fast_ok(int vec, int F) {
+    return (vec == 8 && (F == 4 || F == 8)) || (vec == 4 && (F == 4 || F == 2)) ||
+           (vec == 2 && F == 2);
+}
+
+template <typename K>
+static cudaError_t prep(K kernel, size_t smem) {
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+template <typename T, int VEC, int F, int MODE>
+static cudaError_t k2_go(const float2* coef, const void* in, void* out, int planes, int h_l, int w_l,
+                         int h, int w, int TH, cudaStream_t s) {
+    const int pitch = k2_pitch(VEC, F, w_l, w);
+    const size_t smem = (size_t)TH * pitch * sizeof(float2);
+    auto kern = k2_apply<T, VEC, F, MODE>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((w + 32 * VEC - 1) / (32 * VEC), (h + TH - 1) / TH, planes);
+    kern<<<grid, kThreads, smem, s>>>(coef, static_cast<const T*>(in), static_cast<T*>(out), h_l, w_l, h,
+                                      w, TH, pitch);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+static cudaError_t k2_dispatch(const float2* coef, const void* in, void* out, int planes, int h_l,
+                               int w_l, int h, int w, int vec, int F, int TH, cudaStream_t s) {
+    constexpr int VW = 16 / sizeof(T), VH = 8 / sizeof(T);
+    if (vec == VW) {
+        if (F == 4) return k2_go<T, VW, 4, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        if (F == 8) return k2_go<T, VW, 8, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        return k2_go<T, VW, 0, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+    }
+    if (vec == VH) {
+        if (F == 4) return k2_go<T, VH, 4, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        if (F == 8) return k2_go<T, VH, 8, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        return k2_go<T, VH, 0, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+    }
+    return k2_go<T, 1, 0, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+}
+
+cudaError_t launch_k2(dgf_dtype dt, int mode, const float2* coef, const void* in, void* out, int planes,
+                      int h_l, int w_l, int h, int w, int vec, int F, int TH, cudaStream_t s) {
+    if (planes == 0) return cudaSuccess;
+    switch (dt) {
+        case DGF_F32:
+            return mode == 0 ? k2_dispatch<float, 0>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s)
+                             : k2_dispatch<float, 1>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s);
+        case DGF_BF16:
+            return mode == 0 ? k2_dispatch<__nv_bfloat16, 0>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s)
+                             : k2_dispatch<__nv_bfloat16, 1>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s);
+        case DGF_F16:
+            return mode == 0 ? k2_dispatch<__half, 0>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s)
+                             : k2_dispatch<__half, 1>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int VEC, int F>
+static cudaError_t k3_go(const float2* coef, const void* R, const void* G, void* dG, float2* dcoef,
+                         int planes, int h_l, int w_l, int h, int w, int LTH, cudaStream_t s) {
+    const size_t smem = k3_smem_bytes(VEC, F, LTH);
+    auto kern = k3_hires_bwd<T, VEC, F>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    constexpr int LTW = K3Shape<VEC, F>::LTW;
+    dim3 grid((w_l + LTW - 1) / LTW, (h_l + LTH - 1) / LTH, planes);
+    kern<<<grid, kThreads, smem, s>>>(coef, static_cast<const T*>(R), static_cast<const T*>(G),
+                                      static_cast<T*>(dG), dcoef, h_l, w_l, h, w, LTH);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t k3_dispatch(const float2* coef, const void* R, const void* G, void* dG, float2* dcoef,
+                               int planes, int h_l, int w_l, int h, int w, int vec, int F, int LTH,
+                               cudaStream_t s) {
+    if (sizeof(T) == 2) {
+        if (vec == 8 && F == 4) return k3_go<T, 8, 4>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
+        if (vec == 8 && F == 8) return k3_go<T, 8, 8>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
+        if (vec == 4 && F == 4) return k3_go<T, 4, 4>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
+        if (vec == 4 && F == 2) return k3_go<T, 4, 2>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
+    } else {
+        if (vec == 4 && F == 4) return k3_go<T, 4, 4>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
+        if (vec == 4 && F == 2) return k3_go<T, 4, 2>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
+        if (vec == 2 && F == 2) return k3_go<T, 2, 2>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_k3(dgf_dtype dt, const float2* coef, const void* R, const void* G, void* dG,
+                      float2* dcoef, int planes, int h_l, int w_l, int h, int w, int vec, int F, int LTH,
+                      cudaStream_t s) {
+    if (planes == 0) return cudaSuccess;
+    switch (dt) {
+        case DGF_F32: return k3_dispatch<float>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, vec, F, LTH, s);
+        case DGF_BF16: return k3_dispatch<__nv_bfloat16>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, vec, F, LTH, s);
+        case DGF_F16: return k3_dispatch<__half>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, vec, F, LTH, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t k3g_go(const void* R, const void* G, float2* dcoef, int planes, int h_l, int w_l, int h,
+                          int w, cudaStream_t s) {
+    dim3 grid((w_l + 31) / 32, (h_l + kWarps - 1) / kWarps, planes);
+    k3_gather_general<T><<<grid, kThreads, 0, s>>>(static_cast<const T*>(R), static_cast<const T*>(G), dcoef,
+                                                   h_l, w_l, h, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_k3_general(dgf_dtype dt, const void* R, const void* G, float2* dcoef, int planes,
+                              int h_l, int w_l, int h, int w, cudaStream_t s) {
+    if (planes == 0) return cudaSuccess;
+    switch (dt) {
+        case DGF_F32: return k3g_go<float>(R, G, dcoef, planes, h_l, w_l, h, w, s);
+        case DGF_BF16: return k3g_go<__nv_bfloat16>(R, G, dcoef, planes, h_l, w_l, h, w, s);
+        case DGF_F16: return k3g_go<__half>(R, G, dcoef, planes, h_l, w_l, h, w, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t k2b_prep(size_t smem) {
+    return prep(k2_apply_batched<T>, smem);
+}
+
+cudaError_t k2_batched_kernel(dgf_dtype dt, size_t smem, void** fn) {
+    cudaError_t e = cudaSuccess;
+    switch (dt) {
+        case DGF_F32: e = k2b_prep<float>(smem); *fn = (void*)k2_apply_batched<float>; break;
+        case DGF_BF16: e = k2b_prep<__nv_bfloat16>(smem); *fn = (void*)k2_apply_batched<__nv_bfloat16>; break;
+        case DGF_F16: e = k2b_prep<__half>(smem); *fn = (void*)k2_apply_batched<__half>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    return e;
+}
+
+}  // namespace dgf

@@ -1,0 +1,292 @@
+// Device tile functions of the high-resolution stage (shared by the
+// identity-guide kernels and the guidance-transform kernels).
+//
+// Both stream the high-resolution planes with aligned vector accesses of
+// VEC elements (16 or 8 bytes), one warp per row segment of 32*VEC pixels.
+// The low-resolution coefficients a tile needs are first interpolated along
+// y into shared memory (one row per high-res row, one column per low-res
+// column plus a replicated border column on each side, which makes the
+// clamp of the bilinear taps free); each pixel then needs one lerp along x.
+#pragma once
+
+#include "common.cuh"
+
+namespace dgf {
+
+// ----------------------------------------------------------------- K2 tile
+// F > 0: integer factor (w = F w_l, h = F h_l); F = 0: any ratio.
+// MODE 0: out = Abar_h * in + bbar_h (O_h);  MODE 1: out = Abar_h * in (d I_h).
+template <int F>
+__device__ __forceinline__ void col_tap(int pos, int& c, float& lam) {
+    // pos = position of the pixel inside the tile (tile origin is a multiple of F)
+    const int q = pos % F, j = pos / F;
+    const int t2 = 2 * q + 1 - F;
+    c = j + (t2 >= 0 ? 1 : 0);  // smem column of the first tap (column 0 = low-res jlo)
+    lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
+}
+
+template <typename T, int VEC, int F, int MODE>
+__device__ void apply_tile(const float2* __restrict__ coef, const T* __restrict__ in,
+                           T* __restrict__ out, int h_l, int w_l, int h, int w, int Y0, int X0, int TH,
+                           int pitch, float2* sAB) {
+    constexpr int TW = 32 * VEC;
+    int jlo;
+    int ncol;
+    if (F > 0) {
+        jlo = X0 / F - 1;
+        ncol = TW / F + 2;
+    } else {
+        const int xl = min(X0 + TW, w) - 1;
+        jlo = tap_general(X0, w_l, w).i0;
+        ncol = tap_general(xl, w_l, w).i0 - jlo + 2;
+    }
+    const int nst = TH * ncol;
+    for (int idx = threadIdx.x; idx < nst; idx += kThreads) {
+        const int i = idx / ncol, c = idx - i * ncol;
+        const int y = Y0 + i;
+        if (y >= h) continue;
+        Tap ty;
+        if (F > 0) {
+            const int q = y % F, j = y / F, t2 = 2 * q + 1 - F;
+            ty.i0 = t2 < 0 ? j - 1 : j;
+            ty.lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
+        } else {
+            ty = tap_general(y, h_l, h);
+        }
+        const int r0 = clampi(ty.i0, 0, h_l - 1), r1 = clampi(ty.i0 + 1, 0, h_l - 1);
+        const int jj = clampi(jlo + c, 0, w_l - 1);
+        const float2 a = coef[(size_t)r0 * w_l + jj];
+        const float2 b = coef[(size_t)r1 * w_l + jj];
+        sAB[i * pitch + c] = make_float2(lerp(a.x, b.x, ty.lam), lerp(a.y, b.y, ty.lam));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int xs = X0 + lane * VEC;
+    if (xs < w) {
+        // column taps of this lane's VEC pixels (same for every row)
+        int cc[VEC];
+        float ll[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            if (F > 0) {
+                col_tap<(F > 0 ? F : 1)>(lane * VEC + k, cc[k], ll[k]);
+            } else {
+                const Tap tx = tap_general(xs + k, w_l, w);
+                cc[k] = tx.i0 - jlo;
+                ll[k] = tx.lam;
+            }
+        }
+        constexpr int U = 4;  // rows in flight per thread
+        for (int i0 = warp; i0 < TH; i0 += kWarps * U) {
+            float g[U][VEC];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * kWarps, y = Y0 + i;
+                if (i < TH && y < h) load_vec<T, VEC>(in + (size_t)y * w + xs, g[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * kWarps, y = Y0 + i;
+                if (i < TH && y < h) {
+                    const float2* row = sAB + i * pitch;
+                    float o[VEC];
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) {
+                        const float2 s0 = row[cc[k]], s1 = row[cc[k] + 1];
+                        const float A = lerp(s0.x, s1.x, ll[k]);
+                        if (MODE == 0) {
+                            const float B = lerp(s0.y, s1.y, ll[k]);
+                            o[k] = fmaf(A, g[u][k], B);
+                        } else {
+                            o[k] = A * g[u][k];
+                        }
+                    }
+                    store_vec<T, VEC>(out + (size_t)y * w + xs, o);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// -------------------------------------------------------- K3 tile (integer F)
+// The tile owns low-res rows [i0, i0 + LTH) and columns [j0, j0 + LTW) and
+// gathers, for each owned (i, j), the transposed bilinear weights of every
+// high-res pixel whose taps include it:
+//   d Abar(i, j) = sum_y,x wy(y, i) wx(x, j) R(y, x) G(y, x),
+//   d bbar(i, j) = sum_y,x wy(y, i) wx(x, j) R(y, x),
+// so every output is written once and no atomics are needed.  Pixels whose
+// tap falls outside the image (virtual low-res row/column -1 or h_l / w_l)
+// fold into the border row/column, as the clamp in the forward does.
+// The row sums along x are formed in registers and combined across lanes
+// with warp shuffles; the column sums along y read them from shared memory.
+template <int VEC, int F>
+struct K3Shape {
+    static constexpr int K = VEC / F;                     // low-res columns per lane
+    static constexpr int H0 = F / 2;                      // first q with a right-hand tap
+    static constexpr int LTW = (K == 1) ? 29 : 30 * K;    // owned low-res columns
+    static constexpr int SXP = LTW + 2;                   // shared-memory pitch
+};
+
+// Row partials of one warp-row: each lane's VEC pixels (values u = R G and
+// v = R) weighted onto the K + 2 low-res columns they tap, then combined
+// across lanes so that lane l holds the complete row sums of the K columns
+// jb(l) .. jb(l) + K - 1 it owns (jb(l) = first tap of its first pixel);
+// those land in shared-memory columns (l - 1) K + c.
+template <int VEC, int F>
+__device__ __forceinline__ void k3_row_to_smem(const float (&u)[VEC], const float (&v)[VEC], int lane,
+                                               float2* sx_row) {
+    using S = K3Shape<VEC, F>;
+    constexpr int K = S::K, SXP = S::SXP, NC = K + 2;
+    float pu[NC], pv[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) pu[c] = pv[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        const int q = k % F, jr = k / F, t2 = 2 * q + 1 - F;
+        const int cl = jr + (t2 >= 0 ? 1 : 0);
+        const float lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
+        pu[cl] = fmaf(1.f - lam, u[k], pu[cl]);
+        pv[cl] = fmaf(1.f - lam, v[k], pv[cl]);
+        pu[cl + 1] = fmaf(lam, u[k], pu[cl + 1]);
+        pv[cl + 1] = fmaf(lam, v[k], pv[cl + 1]);
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        float su = pu[c], sv = pv[c];
+#pragma unroll
+        for (int m = 1; m <= 2; ++m) {
+            if (c + m * K <= K + 1) {
+                constexpr int dummy = 0;
+                (void)dummy;
+                const int src = (c + m * K <= K + 1) ? c + m * K : 0;
+                const float tu = __shfl_up_sync(0xffffffffu, pu[src], m);
+                const float tv = __shfl_up_sync(0xffffffffu, pv[src], m);
+                if (lane >= m) {
+                    su += tu;
+                    sv += tv;
+                }
+            }
+        }
+        const int idx = (lane - 1) * K + c;
+        if (idx >= 0 && idx < SXP) sx_row[idx] = make_float2(su, sv);
+    }
+}
+
+// Column pass: for each owned low-res (i, j) sum the row sums of the 2F
+// high-res rows whose taps include row i, with their y weights.  Virtual
+// taps outside the image fold into the border row/column.
+template <int VEC, int F>
+__device__ __forceinline__ void k3_gather_columns(const float2* Sx, int i0, int j0, int LTH, int h_l,
+                                                  int w_l, float2* __restrict__ dcoef) {
+    using S = K3Shape<VEC, F>;
+    constexpr int H0 = S::H0, LTW = S::LTW, SXP = S::SXP;
+    const int yf0 = F * (i0 - 1) + H0;
+    const int nown = LTH * LTW;
+    for (int idx = threadIdx.x; idx < nown; idx += kThreads) {
+        const int li = idx / LTW, lj = idx - li * LTW;
+        const int i = i0 + li, j = j0 + lj;
+        if (i >= h_l || j >= w_l) continue;
+        const int c = lj + 1;
+        const bool left = (j == 0), right = (j == w_l - 1);
+        float su = 0.f, sv = 0.f;
+#pragma unroll
+        for (int tt = 0; tt < 2 * F; ++tt) {
+            // tt < F: rows whose first tap is i; tt >= F: rows whose second tap is i
+            const int t = tt % F;
+            const int y = (tt < F) ? F * i + H0 + t : F * (i - 1) + H0 + t;
+            const int q = (H0 + t) % F;
+            const int t2 = 2 * q + 1 - F;
+            const float lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
+            float wgt;
+            if (tt < F) wgt = (i == h_l - 1) ? 1.f : 1.f - lam;
+            else wgt = (i == 0) ? 1.f : lam;
+            const float2* row = Sx + (y - yf0) * SXP;
+            float2 v = row[c];
+            if (left) { v.x += row[0].x; v.y += row[0].y; }
+            if (right) { v.x += row[c + 1].x; v.y += row[c + 1].y; }
+            su = fmaf(wgt, v.x, su);
+            sv = fmaf(wgt, v.y, sv);
+        }
+        dcoef[(size_t)i * w_l + j] = make_float2(su, sv);
+    }
+}
+
+// Vertical lerp of Abar for the tile's interior high-res rows
+// [F i0, F (i0 + LTH)), columns j0-1 .. j0+LTW (clamped), into SA.
+template <int VEC, int F>
+__device__ __forceinline__ void k3_stage_abar(const float2* __restrict__ coef, int i0, int j0, int LTH,
+                                              int h_l, int w_l, int h, float* SA) {
+    constexpr int SXP = K3Shape<VEC, F>::SXP;
+    const int nst = F * LTH * SXP;
+    for (int idx = threadIdx.x; idx < nst; idx += kThreads) {
+        const int ri = idx / SXP, c = idx - ri * SXP;
+        const int y = F * i0 + ri;
+        if (y >= h) continue;
+        const int q = y % F, j = y / F, t2 = 2 * q + 1 - F;
+        const int yi0 = t2 < 0 ? j - 1 : j;
+        const float lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
+        const int r0 = clampi(yi0, 0, h_l - 1), r1 = clampi(yi0 + 1, 0, h_l - 1);
+        const int jj = clampi(j0 - 1 + c, 0, w_l - 1);
+        SA[idx] = lerp(coef[(size_t)r0 * w_l + jj].x, coef[(size_t)r1 * w_l + jj].x, lam);
+    }
+}
+
+// Abar_h of pixel k of lane `lane` in an interior row of SA (row pointer).
+template <int VEC, int F>
+__device__ __forceinline__ float k3_abar_at(const float* row, int lane, int k) {
+    constexpr int K = K3Shape<VEC, F>::K;
+    const int q = k % F, jr = k / F, t2 = 2 * q + 1 - F;
+    const int c = (lane - 1) * K + jr + (t2 >= 0 ? 1 : 0);
+    const float lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
+    return lerp(row[c], row[c + 1], lam);
+}
+
+template <typename T, int VEC, int F>
+__device__ void hires_bwd_tile(const float2* __restrict__ coef, const T* __restrict__ R,
+                               const T* __restrict__ G, T* __restrict__ dG, float2* __restrict__ dcoef,
+                               int h_l, int w_l, int h, int w, int i0, int j0, int LTH, float* smem) {
+    using S = K3Shape<VEC, F>;
+    constexpr int K = S::K, H0 = S::H0, LTW = S::LTW, SXP = S::SXP;
+    const int FR = F * (LTH + 1);
+    const int yf0 = F * (i0 - 1) + H0;
+    const int XS = F * j0 - VEC;
+    float2* Sx = reinterpret_cast<float2*>(smem);
+    float* SA = reinterpret_cast<float*>(Sx + FR * SXP);
+    if (dG != nullptr) {
+        k3_stage_abar<VEC, F>(coef, i0, j0, LTH, h_l, w_l, h, SA);
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int xs = XS + lane * VEC;
+    const bool col_ok = xs >= 0 && xs < w;
+    const bool interior = lane >= 1 && lane <= LTW / K;
+    for (int fr = warp; fr < FR; fr += kWarps) {
+        const int y = yf0 + fr;
+        const bool ok = col_ok && y >= 0 && y < h;
+        float rv[VEC], gv[VEC];
+        if (ok) {
+            load_vec<T, VEC>(R + (size_t)y * w + xs, rv);
+            load_vec<T, VEC>(G + (size_t)y * w + xs, gv);
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) rv[k] = gv[k] = 0.f;
+        }
+        if (dG != nullptr && ok && interior && y >= F * i0 && y < F * (i0 + LTH)) {
+            const float* row = SA + (y - F * i0) * SXP;
+            float o[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) o[k] = rv[k] * k3_abar_at<VEC, F>(row, lane, k);
+            store_vec<T, VEC>(dG + (size_t)y * w + xs, o);
+        }
+        float u[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) u[k] = rv[k] * gv[k];
+        k3_row_to_smem<VEC, F>(u, rv, lane, Sx + fr * SXP);
+    }
+    __syncthreads();
+    k3_gather_columns<VEC, F>(Sx, i0, j0, LTH, h_l, w_l, dcoef);
+    __syncthreads();
+}
+
+}  // namespace dgf

@@ -1,0 +1,67 @@
+// Host-side launchers of the guided-filtering kernels (internal interface
+// between the C ABI in api.cu and the kernel translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "../../include/dgf.h"
+
+namespace dgf {
+
+struct TmaPair;
+
+// Shared-memory pitch (float2 columns) of a K2 tile row.
+__host__ __device__ inline int k2_pitch(int vec, int F, int w_l, int w) {
+    const int TW = 32 * vec;
+    if (F > 0) return TW / F + 2;
+    const long long span = ((long long)TW * w_l + w - 1) / w;
+    return (int)span + 3;
+}
+
+size_t k1_smem_bytes(int r, int TY, int TX);
+size_t k4_smem_bytes(int r, int TY, int TX);
+size_t k2_smem_bytes(int vec, int F, int w_l, int w, int TH);
+size_t k3_smem_bytes(int vec, int F, int LTH);
+int k3_ltw(int vec, int F);
+bool k3_fast_ok(int vec, int F);
+
+cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P, float2* coef,
+                      int planes, int h, int w, int r, float eps, int TY, int TX, const TmaPair& tma,
+                      uint32_t* status, cudaStream_t s);
+cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P, const float2* dcoef,
+                      void* dP, void* dG, int planes, int h, int w, int r, float eps, int TY, int TX,
+                      cudaStream_t s);
+cudaError_t launch_k2(dgf_dtype dt, int mode, const float2* coef, const void* in, void* out, int planes,
+                      int h_l, int w_l, int h, int w, int vec, int F, int TH, cudaStream_t s);
+cudaError_t launch_k3(dgf_dtype dt, const float2* coef, const void* R, const void* G, void* dG,
+                      float2* dcoef, int planes, int h_l, int w_l, int h, int w, int vec, int F, int LTH,
+                      cudaStream_t s);
+cudaError_t launch_k3_general(dgf_dtype dt, const void* R, const void* G, float2* dcoef, int planes,
+                              int h_l, int w_l, int h, int w, cudaStream_t s);
+
+// Guidance transform (Sec. 3.4): weights staged to constant memory first.
+constexpr int kMaxK6Blocks = 1024;   // rows of weight-gradient partials
+constexpr int kWGradPadded = 99;     // padded [dw1 16x3 | dw2 3x16 | db2 3]
+cudaError_t guide_upload(const float* w1, const float* w2, const float* b2, int hidden, cudaStream_t s);
+bool guided_supported(dgf_dtype dt, int w, int F);
+cudaError_t launch_k5(dgf_dtype dt, const void* I_h, float* G_l, int N, int h_l, int w_l, int h, int w,
+                      int F, float slope, cudaStream_t s);
+cudaError_t launch_k2_guided(dgf_dtype dt, const float2* coef, const void* I_h, void* O_h, int N,
+                             int h_l, int w_l, int h, int w, int F, int TH, float slope, cudaStream_t s);
+cudaError_t launch_k3_guided(dgf_dtype dt, const void* R, const void* I_h, float2* dcoef, int N,
+                             int h_l, int w_l, int h, int w, int F, float slope, cudaStream_t s);
+int k6_blocks(int N, int h, int w);
+cudaError_t launch_k6(dgf_dtype dt, const float2* coef, const float* dG_l, const void* R, const void* I_h,
+                      void* dI_h, float* partials, int N, int h_l, int w_l, int h, int w, int F, float slope,
+                      cudaStream_t s);
+cudaError_t launch_wreduce(const float* partials, int nblocks, float* dW, int hidden, cudaStream_t s);
+
+// Persistent batched kernels (function pointers for graph nodes).
+cudaError_t k1_batched_kernel(dgf_dtype dt, size_t smem, void** fn);
+cudaError_t k2_batched_kernel(dgf_dtype dt, size_t smem, void** fn);
+
+}  // namespace dgf

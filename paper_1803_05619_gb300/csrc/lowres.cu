@@ -1,0 +1,400 @@
+// Low-resolution kernels: K1 (statistics -> A, b -> Abar, bbar) and K4
+// (recompute + Algorithm 1's low-resolution gradients).
+#include "batch.cuh"
+#include "kernels.h"
+#include "lowres.cuh"
+#include "tma.cuh"
+
+namespace dgf {
+
+// --------------------------------------------------------------------- K1
+// Eq. 1 (least-squares A, b per window, Sec. 3.2) followed by the box mean
+// of A and b (Sec. 3.3's f_mu applied once more at low resolution).
+template <typename TG, typename TP>
+__device__ void coef_tile(const TG* __restrict__ G, const TP* __restrict__ P,
+                          float2* __restrict__ coef, const LowresTile& t, float* smem,
+                          const TmaPlane* tg, const TmaPlane* tp, int plane, uint32_t* status) {
+    const int n2 = t.EY2 * t.EX2;
+    float* sG = smem;
+    float* sP = sG + n2;
+    float* hbuf = sP + n2;
+    bool staged = false;
+    if (tg != nullptr && tp != nullptr)
+        staged = tma_stage_pair<TG, TP>(tg, tp, plane, t, sG, sP, hbuf, status);
+    if (!staged) {
+        stage_plane<TG>(G, sG, t);
+        stage_plane<TP>(P, sP, t);
+    }
+    __syncthreads();
+    const int nh = t.EY2 * t.EX1;
+    stats_rows(sG, sP, hbuf, hbuf + nh, hbuf + 2 * nh, hbuf + 3 * nh, t);
+    __syncthreads();
+    // A, b on E1 (zero outside the image); the staged inputs are dead now
+    const int n1 = t.EY1 * t.EX1;
+    float* sA = smem;
+    float* sB = smem + n1;
+    for (int idx = threadIdx.x; idx < n1; idx += kThreads) {
+        const int ey1 = idx / t.EX1, ex = idx - ey1 * t.EX1;
+        const int gy = t.ty0 - t.r + ey1, gx = t.tx0 - t.r + ex;
+        float A = 0.f, b = 0.f;
+        if (gy >= 0 && gy < t.h && gx >= 0 && gx < t.w) {
+            const Moments m = stats_window(hbuf, hbuf + nh, hbuf + 2 * nh, hbuf + 3 * nh, ey1, ex, t);
+            A = m.cov / (m.var + t.eps);
+            b = fmaf(-A, m.mu, m.nu);
+        }
+        sA[idx] = A;
+        sB[idx] = b;
+    }
+    __syncthreads();
+    float* rA = hbuf;
+    float* rB = hbuf + t.EY1 * t.TX;
+    box_rows(sA, t.EX1, t.EY1, t.tx0 - t.r, rA, t.TX, t.tx0, t.TX, t.w, t.r);
+    box_rows(sB, t.EX1, t.EY1, t.tx0 - t.r, rB, t.TX, t.tx0, t.TX, t.w, t.r);
+    __syncthreads();
+    const int n0 = t.TY * t.TX;
+    for (int idx = threadIdx.x; idx < n0; idx += kThreads) {
+        const int y = idx / t.TX, x = idx - y * t.TX;
+        const int gy = t.ty0 + y, gx = t.tx0 + x;
+        if (gy >= t.h || gx >= t.w) continue;
+        const int lo = max(gy - t.r, 0), hi = min(gy + t.r, t.h - 1);
+        float sa = 0.f, sb = 0.f;
+        for (int k = lo; k <= hi; ++k) {
+            const int o = (k - (t.ty0 - t.r)) * t.TX + x;
+            sa += rA[o];
+            sb += rB[o];
+        }
+        const float n = (float)((hi - lo + 1) * t.cnt(gx, t.w));
+        coef[(size_t)gy * t.w + gx] = make_float2(sa / n, sb / n);
+    }
+    __syncthreads();
+}
+
+template <typename TG, typename TP>
+__global__ void __launch_bounds__(kThreads) k1_coef(const TG* __restrict__ G, const TP* __restrict__ P,
+                                                    float2* __restrict__ coef, int h, int w, int r,
+                                                    float eps, int TY, int TX,
+                                                    const __grid_constant__ TmaPair tma,
+                                                    uint32_t* status) {
+    extern __shared__ __align__(128) float smem[];
+    LowresTile t;
+    t.init(h, w, r, eps, blockIdx.y * TY, blockIdx.x * TX, TY, TX);
+    const size_t plane = blockIdx.z;
+    const size_t hw = (size_t)h * w;
+    coef_tile<TG, TP>(G + plane * hw, P + plane * hw, coef + plane * hw, t, smem,
+                      tma.enabled ? &tma.a : nullptr, tma.enabled ? &tma.b : nullptr, (int)plane,
+                      status);
+}
+
+// ---------------------------------------------------------------------- K4
+// Algorithm 1 at low resolution.  With d Abar, d bbar from the high-res
+// pass: dA = f_mu^T(d Abar), db = f_mu^T(d bbar); per window m
+//   alpha = dA - db mu, gamma = alpha / (var + eps)   (d Sigma_GO),
+//   beta = -gamma A                                   (d Sigma_G);
+// then, summing over the windows m that contain pixel i, in centred form,
+//   dP_i = sum [gamma (G_i - mu) + db] / N_m,
+//   dG_i = sum [gamma (P_i - nu) + 2 beta (G_i - mu) - db A] / N_m,
+// which equals Algorithm 1's d O_l and d G_l (the uncentred terms
+// -d Sigma_GO Gbar etc. regroup into the differences).  Every sum is a
+// separable window pass; G and P are shifted by the tile mean first.
+template <typename TG, typename TP, typename TD>
+__device__ void lowres_bwd_tile(const TG* __restrict__ G, const TP* __restrict__ P,
+                                const float2* __restrict__ dcoef, TP* __restrict__ dP,
+                                TD* __restrict__ dG, const LowresTile& t, float* smem) {
+    const int n2 = t.EY2 * t.EX2, n1 = t.EY1 * t.EX1;
+    const int nh = max(4 * t.EY2 * t.EX1, 7 * t.EY1 * t.TX);
+    float* sG = smem;
+    float* sP = sG + n2;
+    float* sDA = sP + n2;
+    float* sDB = sDA + n2;
+    float* hbuf = sDB + n2;
+    float* e1 = hbuf + nh;  // mu, nu, var+eps, A, dA, db on E1
+    float* q = e1 + 6 * n1;  // the seven quantities whose window sums form dP, dG
+    float* red = q + 7 * n1;
+
+    stage_plane<TG>(G, sG, t);
+    stage_plane<TP>(P, sP, t);
+    for (int idx = threadIdx.x; idx < n2; idx += kThreads) {
+        const int ey = idx / t.EX2, ex = idx - ey * t.EX2;
+        const int gy = t.ty0 - 2 * t.r + ey, gx = t.tx0 - 2 * t.r + ex;
+        float a = 0.f, b = 0.f;
+        if (gy >= 0 && gy < t.h && gx >= 0 && gx < t.w) {
+            const float2 c = dcoef[(size_t)gy * t.w + gx];
+            const float n = (float)(t.cnt(gy, t.h) * t.cnt(gx, t.w));
+            a = c.x / n;
+            b = c.y / n;
+        }
+        sDA[idx] = a;
+        sDB[idx] = b;
+    }
+    __syncthreads();
+    // tile shift K = mean of the in-image output pixels (conditioning only)
+    {
+        float sg = 0.f, sp = 0.f, c = 0.f;
+        for (int idx = threadIdx.x; idx < t.TY * t.TX; idx += kThreads) {
+            const int y = idx / t.TX, x = idx - y * t.TX;
+            if (t.ty0 + y < t.h && t.tx0 + x < t.w) {
+                const int o = (y + 2 * t.r) * t.EX2 + x + 2 * t.r;
+                sg += sG[o];
+                sp += sP[o];
+                c += 1.f;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sg += __shfl_down_sync(0xffffffffu, sg, off);
+            sp += __shfl_down_sync(0xffffffffu, sp, off);
+            c += __shfl_down_sync(0xffffffffu, c, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[(threadIdx.x >> 5) * 3 + 0] = sg;
+            red[(threadIdx.x >> 5) * 3 + 1] = sp;
+            red[(threadIdx.x >> 5) * 3 + 2] = c;
+        }
+    }
+    const int nhr = t.EY2 * t.EX1;
+    stats_rows(sG, sP, hbuf, hbuf + nhr, hbuf + 2 * nhr, hbuf + 3 * nhr, t);
+    __syncthreads();
+    float KG = 0.f, KP = 0.f;
+    {
+        float sg = 0.f, sp = 0.f, c = 0.f;
+        for (int k = 0; k < kWarps; ++k) {
+            sg += red[k * 3 + 0];
+            sp += red[k * 3 + 1];
+            c += red[k * 3 + 2];
+        }
+        if (c > 0.f) {
+            KG = sg / c;
+            KP = sp / c;
+        }
+    }
+    float* eMU = e1;
+    float* eNU = e1 + n1;
+    float* eVE = e1 + 2 * n1;
+    float* eA = e1 + 3 * n1;
+    float* eDA = e1 + 4 * n1;
+    float* eDB = e1 + 5 * n1;
+    for (int idx = threadIdx.x; idx < n1; idx += kThreads) {
+        const int ey1 = idx / t.EX1, ex = idx - ey1 * t.EX1;
+        const int gy = t.ty0 - t.r + ey1, gx = t.tx0 - t.r + ex;
+        float mu = 0.f, nu = 0.f, ve = 1.f, A = 0.f;
+        if (gy >= 0 && gy < t.h && gx >= 0 && gx < t.w) {
+            const Moments m = stats_window(hbuf, hbuf + nhr, hbuf + 2 * nhr, hbuf + 3 * nhr, ey1, ex, t);
+            mu = m.mu;
+            nu = m.nu;
+            ve = m.var + t.eps;
+            A = m.cov / ve;
+        }
+        eMU[idx] = mu; eNU[idx] = nu; eVE[idx] = ve; eA[idx] = A;
+    }
+    __syncthreads();
+    // dA = f_mu^T(d Abar), db = f_mu^T(d bbar) on E1: window sums of (d/N)
+    box_rows(sDA, t.EX2, t.EY2, t.tx0 - 2 * t.r, hbuf, t.EX1, t.tx0 - t.r, t.EX1, t.w, t.r);
+    box_rows(sDB, t.EX2, t.EY2, t.tx0 - 2 * t.r, hbuf + nhr, t.EX1, t.tx0 - t.r, t.EX1, t.w, t.r);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n1; idx += kThreads) {
+        const int ey1 = idx / t.EX1, ex = idx - ey1 * t.EX1;
+        const int gy = t.ty0 - t.r + ey1, gx = t.tx0 - t.r + ex;
+        float da = 0.f, db = 0.f;
+        if (gy >= 0 && gy < t.h && gx >= 0 && gx < t.w) {
+            const int lo = max(gy - t.r, 0), hi = min(gy + t.r, t.h - 1);
+            for (int k = lo; k <= hi; ++k) {
+                const int o = (k - (t.ty0 - 2 * t.r)) * t.EX1 + ex;
+                da += hbuf[o];
+                db += hbuf[nhr + o];
+            }
+        }
+        eDA[idx] = da;
+        eDB[idx] = db;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n1; idx += kThreads) {
+        const int ey1 = idx / t.EX1, ex = idx - ey1 * t.EX1;
+        const int gy = t.ty0 - t.r + ey1, gx = t.tx0 - t.r + ex;
+        float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (gy >= 0 && gy < t.h && gx >= 0 && gx < t.w) {
+            const float n = (float)(t.cnt(gy, t.h) * t.cnt(gx, t.w));
+            const float db = eDB[idx], A = eA[idx];
+            const float mus = eMU[idx] - KG, nus = eNU[idx] - KP;
+            const float alpha = fmaf(-db, eMU[idx], eDA[idx]);
+            const float gamma = alpha / eVE[idx];
+            const float beta = -gamma * A;
+            v[0] = gamma / n;
+            v[1] = gamma * mus / n;
+            v[2] = gamma * nus / n;
+            v[3] = beta / n;
+            v[4] = beta * mus / n;
+            v[5] = db / n;
+            v[6] = db * A / n;
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) q[k * n1 + idx] = v[k];
+    }
+    __syncthreads();
+    const int nq = t.EY1 * t.TX;
+#pragma unroll 1
+    for (int k = 0; k < 7; ++k)
+        box_rows(q + k * n1, t.EX1, t.EY1, t.tx0 - t.r, hbuf + k * nq, t.TX, t.tx0, t.TX, t.w, t.r);
+    __syncthreads();
+    const int n0 = t.TY * t.TX;
+    for (int idx = threadIdx.x; idx < n0; idx += kThreads) {
+        const int y = idx / t.TX, x = idx - y * t.TX;
+        const int gy = t.ty0 + y, gx = t.tx0 + x;
+        if (gy >= t.h || gx >= t.w) continue;
+        const int lo = max(gy - t.r, 0), hi = min(gy + t.r, t.h - 1);
+        float S[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = lo; k <= hi; ++k) {
+            const int o = (k - (t.ty0 - t.r)) * t.TX + x;
+#pragma unroll
+            for (int m = 0; m < 7; ++m) S[m] += hbuf[m * nq + o];
+        }
+        const int o2 = (y + 2 * t.r) * t.EX2 + x + 2 * t.r;
+        const float g = sG[o2] - KG, p = sP[o2] - KP;
+        const size_t go = (size_t)gy * t.w + gx;
+        if (dP != nullptr) dP[go] = from_f32<TP>(fmaf(g, S[0], S[5] - S[1]));
+        if (dG != nullptr) {
+            const float v = fmaf(p, S[0], -S[2]) + 2.f * fmaf(g, S[3], -S[4]) - S[6];
+            dG[go] = from_f32<TD>(v);
+        }
+    }
+    __syncthreads();
+}
+
+template <typename TG, typename TP, typename TD>
+__global__ void __launch_bounds__(kThreads) k4_lowres_bwd(const TG* __restrict__ G, const TP* __restrict__ P,
+                                                          const float2* __restrict__ dcoef,
+                                                          TP* __restrict__ dP, TD* __restrict__ dG,
+                                                          int h, int w, int r, float eps, int TY, int TX) {
+    extern __shared__ __align__(128) float smem[];
+    LowresTile t;
+    t.init(h, w, r, eps, blockIdx.y * TY, blockIdx.x * TX, TY, TX);
+    const size_t plane = blockIdx.z;
+    const size_t hw = (size_t)h * w;
+    lowres_bwd_tile<TG, TP, TD>(G + plane * hw, P + plane * hw, dcoef + plane * hw,
+                                dP ? dP + plane * hw : nullptr, dG ? dG + plane * hw : nullptr, t,
+                                smem);
+}
+
+// ------------------------------------------------------- batched K1 (persistent)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k1_coef_batched(const __grid_constant__ BatchParams bp,
+                                                            uint32_t* status) {
+    extern __shared__ __align__(128) float smem[];
+    for (int tile = blockIdx.x; tile < bp.k1_total; tile += gridDim.x) {
+        const int i = batch_find(bp.k1_start, bp.n, tile);
+        const BatchImage& im = bp.img[i];
+        const int local = tile - bp.k1_start[i];
+        const int per_plane = im.k1_nx * im.k1_ny;
+        const int plane = local / per_plane;
+        const int tp = local - plane * per_plane;
+        const int ty = tp / im.k1_nx, tx = tp - ty * im.k1_nx;
+        LowresTile t;
+        t.init(im.h_l, im.w_l, im.r, im.eps, ty * im.k1_ty, tx * im.k1_tx, im.k1_ty, im.k1_tx);
+        const size_t hw = (size_t)im.h_l * im.w_l;
+        coef_tile<T, T>(static_cast<const T*>(im.I_l) + plane * hw,
+                        static_cast<const T*>(im.p_l) + plane * hw, im.coef + plane * hw, t, smem,
+                        nullptr, nullptr, plane, status);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+size_t k1_smem_bytes(int r, int TY, int TX) {
+    const size_t EY2 = TY + 4 * r, EX2 = TX + 4 * r, EX1 = TX + 2 * r;
+    size_t floats = 2 * EY2 * EX2 + 4 * EY2 * EX1;
+    // TMA staging adds a raw landing buffer for 16-bit inputs; bounded by the same region
+    return floats * sizeof(float) + tma_extra_bytes(r, TY, TX);
+}
+
+size_t k4_smem_bytes(int r, int TY, int TX) {
+    const size_t EY2 = TY + 4 * r, EX2 = TX + 4 * r, EY1 = TY + 2 * r, EX1 = TX + 2 * r;
+    const size_t n2 = EY2 * EX2, n1 = EY1 * EX1;
+    const size_t nh = std::max(4 * EY2 * EX1, 7 * EY1 * (size_t)TX);
+    return (4 * n2 + nh + 13 * n1 + 3 * kWarps) * sizeof(float);
+}
+
+template <typename K>
+static cudaError_t prep(K kernel, size_t smem) {
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+template <typename TG, typename TP>
+static cudaError_t k1_go(const void* G, const void* P, float2* coef, int planes, int h, int w, int r,
+                         float eps, int TY, int TX, const TmaPair& tma, uint32_t* status,
+                         cudaStream_t s) {
+    const size_t smem = k1_smem_bytes(r, TY, TX);
+    auto kern = k1_coef<TG, TP>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY, planes);
+    kern<<<grid, kThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), coef, h,
+                                      w, r, eps, TY, TX, tma, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P, float2* coef,
+                      int planes, int h, int w, int r, float eps, int TY, int TX, const TmaPair& tma,
+                      uint32_t* status, cudaStream_t s) {
+    if (planes == 0) return cudaSuccess;
+    switch (dt) {
+        case DGF_F32:
+            return k1_go<float, float>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s);
+        case DGF_BF16:
+            return guide_f32 ? k1_go<float, __nv_bfloat16>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s)
+                             : k1_go<__nv_bfloat16, __nv_bfloat16>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s);
+        case DGF_F16:
+            return guide_f32 ? k1_go<float, __half>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s)
+                             : k1_go<__half, __half>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename TG, typename TP, typename TD>
+static cudaError_t k4_go(const void* G, const void* P, const float2* dcoef, void* dP, void* dG,
+                         int planes, int h, int w, int r, float eps, int TY, int TX, cudaStream_t s) {
+    const size_t smem = k4_smem_bytes(r, TY, TX);
+    auto kern = k4_lowres_bwd<TG, TP, TD>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY, planes);
+    kern<<<grid, kThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef,
+                                      static_cast<TP*>(dP), static_cast<TD*>(dG), h, w, r, eps, TY, TX);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P, const float2* dcoef,
+                      void* dP, void* dG, int planes, int h, int w, int r, float eps, int TY, int TX,
+                      cudaStream_t s) {
+    if (planes == 0) return cudaSuccess;
+    switch (dt) {
+        case DGF_F32:
+            return k4_go<float, float, float>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s);
+        case DGF_BF16:
+            return guide_f32
+                       ? k4_go<float, __nv_bfloat16, float>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s)
+                       : k4_go<__nv_bfloat16, __nv_bfloat16, __nv_bfloat16>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s);
+        case DGF_F16:
+            return guide_f32
+                       ? k4_go<float, __half, float>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s)
+                       : k4_go<__half, __half, __half>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t k1b_prep(size_t smem) {
+    return prep(k1_coef_batched<T>, smem);
+}
+
+cudaError_t k1_batched_kernel(dgf_dtype dt, size_t smem, void** fn) {
+    cudaError_t e = cudaSuccess;
+    switch (dt) {
+        case DGF_F32: e = k1b_prep<float>(smem); *fn = (void*)k1_coef_batched<float>; break;
+        case DGF_BF16: e = k1b_prep<__nv_bfloat16>(smem); *fn = (void*)k1_coef_batched<__nv_bfloat16>; break;
+        case DGF_F16: e = k1b_prep<__half>(smem); *fn = (void*)k1_coef_batched<__half>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    return e;
+}
+
+}  // namespace dgf

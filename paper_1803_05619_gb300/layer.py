@@ -1,0 +1,217 @@
+"""Torch-facing side of the guided filtering layer: tensor checks and
+marshalling onto the C ABI, a ``torch.autograd.Function`` whose backward is
+the library's hand-written adjoint (Algorithm 1), and ``nn.Module`` wrappers.
+
+PyTorch provides device memory and the current stream only; every step of
+the layer runs in libdgf.so's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+_DT = {torch.float32: L.DGF_F32, torch.bfloat16: L.DGF_BF16, torch.float16: L.DGF_F16}
+
+
+def dtype_code(t: torch.Tensor) -> int:
+    if t.dtype not in _DT:
+        raise TypeError(f"unsupported dtype {t.dtype}; use float32, bfloat16 or float16")
+    return _DT[t.dtype]
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check(*ts):
+    dev = None
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("tensors must be CUDA tensors (the layer has no CPU path)")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous NCHW")
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError("tensors on different devices")
+    return dev
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    ws = torch.empty(max(int(nbytes), 256) + 256, dtype=torch.uint8, device=device)
+    off = (-ws.data_ptr()) % 256
+    return ws[off:off + max(int(nbytes), 256)]
+
+
+def _guide_struct(w1, w2, b2, slope):
+    if w1 is None:
+        return None
+    for t in (w1, w2, b2):
+        if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError("guide weights must be contiguous float32 CUDA tensors")
+    hidden = w1.shape[0]
+    if tuple(w1.shape) != (hidden, 3) or tuple(w2.shape) != (3, hidden) or tuple(b2.shape) != (3,):
+        raise ValueError("guide weights: w1 (hidden, 3), w2 (3, hidden), b2 (3,)")
+    return L.dgf_guide(w1.data_ptr(), w2.data_ptr(), b2.data_ptr(), hidden, float(slope))
+
+
+def _sizes(p_l, I_h):
+    N, C, h, w = I_h.shape
+    h_l, w_l = p_l.shape[2], p_l.shape[3]
+    if p_l.shape[0] != N or p_l.shape[1] != C:
+        raise ValueError("p_l and I_h disagree on N or C")
+    return N, C, h_l, w_l, h, w
+
+
+def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2, out=None):
+    """O_h of the fast guided filtering layer (Eq. 1-2, box mean of A and b)."""
+    dev = _check(p_l, I_l, I_h, w1, w2, b2)
+    N, C, h_l, w_l, h, w = _sizes(p_l, I_h)
+    dt = dtype_code(I_h)
+    if p_l.dtype != I_h.dtype or (I_l is not None and I_l.dtype != I_h.dtype):
+        raise TypeError("p_l, I_l and I_h must share one dtype")
+    g = _guide_struct(w1, w2, b2, slope)
+    gp = ctypes.byref(g) if g is not None else None
+    if out is None:
+        out = torch.empty_like(I_h)
+    nb = L.dgf_workspace_size(N, C, h_l, w_l, h, w, r, dt, gp)
+    ws = workspace(nb, dev)
+    with torch.cuda.device(dev):
+        L.check(L.dgf_forward(_ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(out), N, C, h_l, w_l, h, w, r,
+                              float(eps), dt, gp, _ptr(ws), ws.numel(), _stream(dev)))
+    return out
+
+
+def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2,
+                need_p=True, need_Il=True, need_Ih=True, need_w=True):
+    """(dp_l, dI_l, dI_h, (dw1, dw2, db2)) by the library's adjoint kernels."""
+    dev = _check(dO_h, p_l, I_l, I_h, w1, w2, b2)
+    N, C, h_l, w_l, h, w = _sizes(p_l, I_h)
+    dt = dtype_code(I_h)
+    g = _guide_struct(w1, w2, b2, slope)
+    gp = ctypes.byref(g) if g is not None else None
+    dO_h = dO_h.to(I_h.dtype).contiguous()
+    dp = torch.empty_like(p_l) if need_p else None
+    dIl = torch.empty_like(p_l) if (need_Il and g is None) else None
+    dIh = torch.empty_like(I_h) if need_Ih else None
+    dW = None
+    if g is not None and need_w:
+        dW = torch.empty(6 * g.hidden + 3, dtype=torch.float32, device=dev)
+    nb = L.dgf_workspace_size(N, C, h_l, w_l, h, w, r, dt, gp)
+    ws = workspace(nb, dev)
+    with torch.cuda.device(dev):
+        L.check(L.dgf_backward(_ptr(dO_h), _ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(dp), _ptr(dIl),
+                               _ptr(dIh), _ptr(dW), N, C, h_l, w_l, h, w, r, float(eps), dt, gp,
+                               _ptr(ws), ws.numel(), _stream(dev)))
+    dws = None
+    if dW is not None:
+        hid = g.hidden
+        dws = (dW[:3 * hid].view(hid, 3), dW[3 * hid:6 * hid].view(3, hid), dW[6 * hid:])
+    return dp, dIl, dIh, dws
+
+
+def gf_forward_batched(images, out=None):
+    """Uneven batch in one graph-replayed persistent launch per stage.
+
+    ``images``: list of dicts with p_l, I_l, I_h (C x h x w tensors, one
+    dtype), r, eps.  Returns the list of O_h.
+    """
+    n = len(images)
+    if n == 0:
+        return []
+    dt = dtype_code(images[0]["I_h"])
+    dev = images[0]["I_h"].device
+    arr = (L.dgf_image * n)()
+    outs = []
+    for i, im in enumerate(images):
+        _check(im["p_l"], im["I_l"], im["I_h"])
+        o = out[i] if out is not None else torch.empty_like(im["I_h"])
+        outs.append(o)
+        C, h, w = im["I_h"].shape
+        h_l, w_l = im["p_l"].shape[1:]
+        arr[i] = L.dgf_image(im["p_l"].data_ptr(), im["I_l"].data_ptr(), im["I_h"].data_ptr(),
+                             o.data_ptr(), C, h_l, w_l, h, w, int(im["r"]), float(im["eps"]))
+    nb = L.dgf_workspace_size_batched(arr, n, dt)
+    if nb == 0:
+        raise L.DGFError(1, L.dgf_last_error())
+    ws = workspace(nb, dev)
+    with torch.cuda.device(dev):
+        L.check(L.dgf_forward_batched(arr, n, dt, _ptr(ws), ws.numel(), _stream(dev)))
+    return outs
+
+
+class GuidedFilterFn(torch.autograd.Function):
+    """O_h = GF(p_l, I_l, I_h); backward = Algorithm 1 in libdgf.so."""
+
+    @staticmethod
+    def forward(ctx, p_l, I_l, I_h, r, eps):
+        p_l, I_l, I_h = p_l.contiguous(), I_l.contiguous(), I_h.contiguous()
+        ctx.save_for_backward(p_l, I_l, I_h)
+        ctx.r, ctx.eps = r, eps
+        return gf_forward(p_l, I_l, I_h, r, eps)
+
+    @staticmethod
+    def backward(ctx, dO_h):
+        p_l, I_l, I_h = ctx.saved_tensors
+        dp, dIl, dIh, _ = gf_backward(dO_h.contiguous(), p_l, I_l, I_h, ctx.r, ctx.eps,
+                                      need_p=ctx.needs_input_grad[0],
+                                      need_Il=ctx.needs_input_grad[1],
+                                      need_Ih=ctx.needs_input_grad[2])
+        return dp, dIl, dIh, None, None
+
+
+class GuidedFilterTransformFn(torch.autograd.Function):
+    """O_h with the trainable guidance transform F (Sec. 3.4)."""
+
+    @staticmethod
+    def forward(ctx, p_l, I_h, w1, w2, b2, r, eps, slope):
+        p_l, I_h = p_l.contiguous(), I_h.contiguous()
+        w1, w2, b2 = w1.contiguous(), w2.contiguous(), b2.contiguous()
+        ctx.save_for_backward(p_l, I_h, w1, w2, b2)
+        ctx.r, ctx.eps, ctx.slope = r, eps, slope
+        return gf_forward(p_l, None, I_h, r, eps, w1, w2, b2, slope)
+
+    @staticmethod
+    def backward(ctx, dO_h):
+        p_l, I_h, w1, w2, b2 = ctx.saved_tensors
+        need_w = any(ctx.needs_input_grad[2:5])
+        dp, _, dIh, dws = gf_backward(dO_h.contiguous(), p_l, None, I_h, ctx.r, ctx.eps, w1, w2, b2,
+                                      ctx.slope, need_p=ctx.needs_input_grad[0], need_Il=False,
+                                      need_Ih=ctx.needs_input_grad[1], need_w=need_w)
+        dw1, dw2, db2 = dws if dws is not None else (None, None, None)
+        return dp, dIh, dw1, dw2, db2, None, None, None
+
+
+class GuidedFilter(torch.nn.Module):
+    """Fast guided filtering layer, F = identity (DGF_b with n_I = n_O)."""
+
+    def __init__(self, r: int = 1, eps: float = 1e-8):
+        super().__init__()
+        self.r, self.eps = int(r), float(eps)
+
+    def forward(self, p_l, I_l, I_h):
+        return GuidedFilterFn.apply(p_l, I_l, I_h, self.r, self.eps)
+
+
+class GuidedFilterWithTransform(torch.nn.Module):
+    """Guided filtering layer with the learnable guidance map F(I) (Sec. 3.4)."""
+
+    def __init__(self, r: int = 1, eps: float = 1e-8, hidden: int = 16, slope: float = 0.2):
+        super().__init__()
+        self.r, self.eps, self.slope = int(r), float(eps), float(slope)
+        self.w1 = torch.nn.Parameter(torch.randn(hidden, 3) * 0.1)
+        self.w2 = torch.nn.Parameter(torch.randn(3, hidden) * 0.1)
+        self.b2 = torch.nn.Parameter(torch.zeros(3))
+
+    def forward(self, p_l, I_h):
+        return GuidedFilterTransformFn.apply(p_l, I_h, self.w1, self.w2, self.b2, self.r, self.eps,
+                                             self.slope)

@@ -1,0 +1,103 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol
+include/dgf.h declares, and its host-side validation rejects bad arguments
+before anything touches CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1803_05619_gb300 import _lib as L
+from paper_1803_05619_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dgf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(dgf_[a-z_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ("dgf_forward", "dgf_backward", "dgf_forward_batched", "dgf_workspace_size"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_workspace_size_is_host_only(lib):
+    n = L.dgf_workspace_size(4, 3, 512, 512, 2048, 2048, 1, L.DGF_F32, None)
+    lo = 4 * 3 * 512 * 512
+    assert n >= 2 * lo * 8
+    assert L.dgf_workspace_size(1, 1, 8, 8, 4, 4, 1, L.DGF_F32, None) == 0  # h_l > h
+    assert L.dgf_workspace_size(1, 1, 8, 8, 32, 32, -1, L.DGF_F32, None) == 0
+
+
+def _fwd(**kw):
+    a = dict(p_l=1024, I_l=2048, I_h=4096, O_h=8192, N=1, C=1, h_l=8, w_l=8, h=32, w=32, r=1,
+             eps=1e-3, dt=L.DGF_F32, g=None, ws=None, ws_bytes=0, stream=None)
+    a.update(kw)
+    return L.dgf_forward(*(ctypes.c_void_p(a[k]) if k in ("p_l", "I_l", "I_h", "O_h", "ws") and a[k]
+                           else a[k] for k in a))
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(r=-1), 1), (dict(eps=0.0), 1), (dict(eps=float("nan")), 1), (dict(eps=float("inf")), 1),
+    (dict(h_l=64), 1), (dict(C=0), 1), (dict(N=-1), 1), (dict(dt=7), 1), (dict(r=17), 2),
+    (dict(p_l=0), 1), (dict(O_h=0), 1), (dict(ws=None), 5), (dict(ws=4096 + 8, ws_bytes=1 << 20), 5),
+    (dict(ws=4096, ws_bytes=16), 5),
+])
+def test_forward_rejects_bad_arguments_on_host(lib, bad, status):
+    assert _fwd(**bad) == status
+    assert L.dgf_last_error() != ""
+
+
+def test_empty_batch_is_ok(lib):
+    assert _fwd(N=0) == 0
+
+
+def test_guide_validation(lib):
+    g = L.dgf_guide(16, 32, 48, 0, 0.2)  # hidden = 0
+    assert _fwd(C=3, g=ctypes.byref(g)) == 1
+    g = L.dgf_guide(16, 32, 48, 15, 0.2)
+    assert _fwd(C=1, g=ctypes.byref(g)) == 2  # needs C = 3
+    assert _fwd(C=3, h=33, g=ctypes.byref(g)) == 1  # needs an integer factor
+
+
+def test_backward_validation(lib):
+    z = ctypes.c_void_p(4096)
+    st = L.dgf_backward(z, z, z, z, z, z, z, None, 1, 1, 8, 8, 32, 32, 1, -1.0, L.DGF_F32, None, None,
+                        0, None)
+    assert st == 1
+    # dW without a guidance transform
+    st = L.dgf_backward(z, z, z, z, z, z, z, ctypes.c_void_p(8192), 1, 1, 8, 8, 32, 32, 1, 1e-3,
+                        L.DGF_F32, None, None, 0, None)
+    assert st == 1
+
+
+def test_batched_validation(lib):
+    arr = (L.dgf_image * 2)()
+    arr[0] = L.dgf_image(16, 32, 48, 64, 3, 8, 8, 32, 32, 1, 1e-3)
+    arr[1] = L.dgf_image(16, 32, 48, 64, 3, 8, 8, 32, 32, -2, 1e-3)
+    assert L.dgf_workspace_size_batched(arr, 2, L.DGF_BF16) == 0
+    assert L.dgf_workspace_size_batched(arr, 1, L.DGF_BF16) > 0
+    assert L.dgf_forward_batched(arr, 1, L.DGF_BF16, None, 0, None) == 5
+    assert L.dgf_forward_batched(arr, 200, L.DGF_BF16, None, 0, None) == 1

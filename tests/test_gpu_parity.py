@@ -1,0 +1,210 @@
+"""CUDA path vs the FP64 oracle, element by element (needs a GPU).
+
+Sizes span several tiles of every kernel and end in ragged tails; the
+cases cover integer factors 2, 4, 8, non-integer ratios, odd widths (scalar
+path), r from 0 to 16, FP32/BF16/FP16 storage.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from paper_1803_05619_gb300 import _lib as L
+from paper_1803_05619_gb300.layer import gf_backward, gf_forward, gf_forward_batched
+from tests.helpers import (assert_fwd, assert_grad, f64, make_case, oracle_backward, oracle_forward,
+                           to_storage)
+
+pytestmark = pytest.mark.gpu
+
+F32, BF16, F16 = torch.float32, torch.bfloat16, torch.float16
+
+# kind, N, C, h_l, w_l, h, w, r, eps
+FWD_CASES = [
+    ("photo", 1, 1, 64, 64, 256, 256, 1, 1e-2),     # configuration-1 shape
+    ("photo", 2, 3, 70, 90, 280, 360, 1, 1e-3),     # several tiles + ragged tails, f = 4
+    ("photo", 1, 2, 40, 44, 320, 352, 2, 1e-3),     # f = 8
+    ("photo", 1, 1, 33, 47, 66, 94, 4, 1e-3),       # f = 2
+    ("ragged", 1, 2, 37, 53, 150, 211, 1, 1e-3),    # non-integer ratio, odd width
+    ("ragged", 2, 1, 19, 23, 61, 92, 2, 1e-3),      # non-integer, even width
+    ("photo", 1, 1, 48, 40, 192, 160, 8, 1e-3),     # r = 8
+    ("photo", 1, 1, 20, 24, 80, 96, 16, 1e-2),      # r = 16 > image half-size
+    ("photo", 1, 1, 30, 36, 120, 144, 0, 1e-2),     # r = 0
+    ("blobs", 1, 3, 64, 72, 256, 288, 1, 1e-4),     # configuration-2 recipe, eps = 1e-4
+    ("ragged", 1, 1, 1, 1, 7, 5, 1, 1e-3),          # single low-res pixel
+    ("ragged", 1, 1, 3, 1, 9, 4, 1, 1e-3),          # one column
+    ("ragged", 1, 1, 5, 6, 5, 6, 1, 1e-3),          # f = 1 (plain guided filter)
+]
+
+
+def _ids(cases):
+    return ["-".join(str(v) for v in c) for c in cases]
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16, F16], ids=["f32", "bf16", "f16"])
+@pytest.mark.parametrize("case", FWD_CASES, ids=_ids(FWD_CASES))
+def test_forward_parity(case, dtype):
+    kind, N, C, hl, wl, h, w, r, eps = case
+    st = to_storage(make_case(kind, 100 + r, N, C, hl, wl, h, w), dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    out = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps)
+    torch.cuda.synchronize()
+    ref = oracle_forward(st, r, eps)
+    assert_fwd(f64(out), ref, dtype, eps)
+    assert L.dgf_device_status() == 0
+
+
+BWD_CASES = [c for c in FWD_CASES if c[0] != "ragged" or c[3] > 1] + [
+    ("photo", 1, 1, 48, 64, 384, 512, 2, 1e-3),     # f = 8 with an even low-res width
+]
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16, F16], ids=["f32", "bf16", "f16"])
+@pytest.mark.parametrize("case", BWD_CASES, ids=_ids(BWD_CASES))
+def test_backward_parity(case, dtype):
+    kind, N, C, hl, wl, h, w, r, eps = case
+    st = to_storage(make_case(kind, 200 + r, N, C, hl, wl, h, w), dtype)
+    R = synth.upstream_grad(7, st["I_h"].shape).to(dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    dp, dIl, dIh, _ = gf_backward(R.cuda(), g["p_l"], g["I_l"], g["I_h"], r, eps)
+    torch.cuda.synchronize()
+    rp, rIl, rIh = oracle_backward(R, st, r, eps)
+    if dtype == F32 and eps < 1e-3:
+        pass  # same gate: relative L2 <= 1e-4
+    assert_grad(f64(dp), rp, dtype, "dp_l")
+    assert_grad(f64(dIl), rIl, dtype, "dI_l")
+    assert_grad(f64(dIh), rIh, dtype, "dI_h")
+
+
+def test_autograd_function_matches_oracle():
+    from paper_1803_05619_gb300 import GuidedFilter
+    st = to_storage(make_case("photo", 5, 2, 3, 24, 40, 96, 160), F32)
+    R = synth.upstream_grad(9, st["I_h"].shape).float()
+    p = st["p_l"].cuda().requires_grad_(True)
+    il = st["I_l"].cuda().requires_grad_(True)
+    ih = st["I_h"].cuda().requires_grad_(True)
+    out = GuidedFilter(r=2, eps=1e-3)(p, il, ih)
+    (out * R.cuda()).sum().backward()
+    rp, rIl, rIh = oracle_backward(R, st, 2, 1e-3)
+    assert_grad(f64(p.grad), rp, F32, "dp_l")
+    assert_grad(f64(il.grad), rIl, F32, "dI_l")
+    assert_grad(f64(ih.grad), rIh, F32, "dI_h")
+
+
+def test_tma_and_plain_staging_identical():
+    st = to_storage(make_case("photo", 3, 2, 3, 64, 96, 256, 384), BF16)
+    g = {k: v.cuda() for k, v in st.items()}
+    L.dgf_set_tma(True)
+    a = gf_forward(g["p_l"], g["I_l"], g["I_h"], 2, 1e-3)
+    L.dgf_set_tma(False)
+    b = gf_forward(g["p_l"], g["I_l"], g["I_h"], 2, 1e-3)
+    L.dgf_set_tma(True)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_deterministic():
+    st = to_storage(make_case("photo", 4, 2, 3, 40, 48, 160, 192), F32)
+    g = {k: v.cuda() for k, v in st.items()}
+    R = synth.upstream_grad(3, st["I_h"].shape).float().cuda()
+    o1 = gf_forward(g["p_l"], g["I_l"], g["I_h"], 1, 1e-3)
+    o2 = gf_forward(g["p_l"], g["I_l"], g["I_h"], 1, 1e-3)
+    a = gf_backward(R, g["p_l"], g["I_l"], g["I_h"], 1, 1e-3)
+    b = gf_backward(R, g["p_l"], g["I_l"], g["I_h"], 1, 1e-3)
+    assert torch.equal(o1, o2)
+    for x, y in zip(a[:3], b[:3]):
+        assert torch.equal(x, y)
+
+
+def test_guard_regions_untouched():
+    # outputs written into the middle of sentinel-filled buffers
+    N, C, hl, wl, h, w = 1, 3, 30, 50, 120, 200
+    st = to_storage(make_case("photo", 6, N, C, hl, wl, h, w), F32)
+    g = {k: v.cuda() for k, v in st.items()}
+    guard = 4096
+    big = torch.full((guard * 2 + N * C * h * w,), 12345.0, device="cuda")
+    out = big[guard:guard + N * C * h * w].view(N, C, h, w)
+    gf_forward(g["p_l"], g["I_l"], g["I_h"], 1, 1e-3, out=out)
+    torch.cuda.synchronize()
+    assert torch.all(big[:guard] == 12345.0) and torch.all(big[-guard:] == 12345.0)
+    assert_fwd(f64(out), oracle_forward(st, 1, 1e-3), F32, 1e-3)
+
+
+def test_constant_target_gives_constant_output():
+    st = to_storage(make_case("photo", 8, 1, 2, 40, 40, 160, 160), F32)
+    st["p_l"] = torch.full_like(st["p_l"], 0.5)
+    g = {k: v.cuda() for k, v in st.items()}
+    out = gf_forward(g["p_l"], g["I_l"], g["I_h"], 2, 1e-3)
+    assert torch.all(out == 0.5)
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
+def test_batched_matches_single_bitwise(dtype):
+    specs = synth.mixed_sizes(seed=3, n=9, long_lo=96, long_hi=520)
+    images = []
+    for i, s in enumerate(specs):
+        d = to_storage(synth.photo_like(50 + i, 1, 3, s.h_l, s.w_l, s.f), dtype)
+        images.append({"p_l": d["p_l"][0].cuda(), "I_l": d["I_l"][0].cuda(), "I_h": d["I_h"][0].cuda(),
+                       "r": s.r, "eps": 1e-3, "_st": d})
+    for rep in range(2):  # second call replays the updated graph
+        outs = gf_forward_batched(images)
+        torch.cuda.synchronize()
+        for im, o in zip(images, outs):
+            single = gf_forward(im["p_l"][None], im["I_l"][None], im["I_h"][None], im["r"], im["eps"])
+            assert torch.equal(o, single[0])
+    # and against the oracle
+    for im, o in zip(images, outs):
+        ref = oracle_forward(im["_st"], im["r"], im["eps"])
+        assert_fwd(f64(o)[None], ref, dtype, im["eps"])
+
+
+def test_invalid_arguments_report_status():
+    st = to_storage(make_case("photo", 9, 1, 1, 8, 8, 32, 32), F32)
+    g = {k: v.cuda() for k, v in st.items()}
+    with pytest.raises(L.DGFError) as e:
+        gf_forward(g["p_l"], g["I_l"], g["I_h"], -1, 1e-3)
+    assert e.value.status == 1
+    with pytest.raises(L.DGFError) as e:
+        gf_forward(g["p_l"], g["I_l"], g["I_h"], 1, 0.0)
+    assert e.value.status == 1
+    with pytest.raises(L.DGFError) as e:
+        gf_forward(g["p_l"], g["I_l"], g["I_h"], 17, 1e-3)
+    assert e.value.status == 2
+
+
+# ------------------------------------------------------ guidance transform
+GUIDED_CASES = [  # N, h_l, w_l, f, r, eps, dtype
+    (2, 24, 20, 4, 1, 1e-3, F32),
+    (1, 20, 30, 8, 2, 1e-4, BF16),
+    (2, 16, 29, 8, 8, 1e-4, BF16),   # r = 8 as in the training configuration; ragged K3 tile
+    (1, 26, 18, 4, 1, 1e-3, F16),
+]
+
+
+@pytest.mark.parametrize("case", GUIDED_CASES, ids=_ids(GUIDED_CASES))
+def test_guided_forward_backward_parity(case):
+    N, hl, wl, f, r, eps, dtype = case
+    d = synth.photo_like(60 + r, N, 3, hl, wl, f)
+    st = to_storage(d, dtype)
+    gw = synth.guide_weights(11)
+    w = {k: v.float() for k, v in gw.items()}
+    R = synth.upstream_grad(12, st["I_h"].shape).to(dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    wc = {k: v.cuda() for k, v in w.items()}
+    out = gf_forward(g["p_l"], None, g["I_h"], r, eps, wc["w1"], wc["w2"], wc["b2"], 0.2)
+    dp, _, dIh, dws = gf_backward(R.cuda(), g["p_l"], None, g["I_h"], r, eps, wc["w1"], wc["w2"],
+                                  wc["b2"], 0.2)
+    torch.cuda.synchronize()
+    w64 = {k: v.double().numpy() for k, v in w.items()}
+    ref = O.forward_guided(f64(st["p_l"]), f64(st["I_h"]), w64["w1"], w64["w2"], w64["b2"], r, eps)
+    assert_fwd(f64(out), ref, dtype, eps if dtype != F32 else max(eps, 1e-3))
+    rp, rI, rw1, rw2, rb2 = O.backward_guided(f64(R), f64(st["p_l"]), f64(st["I_h"]), w64["w1"],
+                                              w64["w2"], w64["b2"], r, eps)
+    assert_grad(f64(dp), rp, dtype, "dp_l")
+    assert_grad(f64(dIh), rI, dtype, "dI_h")
+    wtol = 1e-3 if dtype == F32 else 2e-2
+    for got, refw, name in ((dws[0], rw1, "dw1"), (dws[1], rw2, "dw2")):
+        err = float(np.linalg.norm(f64(got) - refw) / np.linalg.norm(refw))
+        assert err <= wtol, f"{name}: rel L2 {err:.3e}"
+    # the guide-shift invariance makes db2 vanish; compare on the scale of dw2
+    assert float(np.max(np.abs(f64(dws[2])))) <= 1e-3 * float(np.max(np.abs(rw2)))
