@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="workload of the timed loop (default: the FP32 plain configuration)")
     ap.add_argument("--quick", action="store_true",
                     help="timed loop only (no roofline pass, e2e, extras or oracle): for profiler runs")
     return ap.parse_args()
@@ -427,7 +429,8 @@ def main():
     barrier(ws)
     from paper_1803_05619_gb300 import _lib as L
     device = torch.device("cuda", local)
-    spec = WORKLOADS[MAIN]
+    main_name = args.workload or MAIN
+    spec = WORKLOADS[main_name]
     g, dt = make_inputs(spec, device, seed=1000 * rank)
     step = Step(g, spec, device)
     N, C, h_l, w_l, h, w = step.shape
@@ -446,7 +449,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic (seeded; blobs+edges+noise photo "
         "stand-in, tone-curve target, N(0,1) upstream gradient)",
-        "config": {"workload": MAIN, "step": "forward+backward", "N": N, "C": C, "h_l": h_l, "w_l": w_l,
+        "config": {"workload": main_name, "step": "forward+backward", "N": N, "C": C, "h_l": h_l, "w_l": w_l,
                    "h": h, "w": w, "r": spec["r"], "eps": spec["eps"],
                    "l2": "inputs larger than L2 (each high-res tensor %d MB > 129 MB)"
                          % (N * C * h * w * g["I_h"].element_size() // 10**6),

@@ -175,8 +175,8 @@ static bool aligned16(std::initializer_list<const void*> ptrs) {
 struct Plan {
     int F = 0;      // integer factor (0 = general ratio)
     int vec = 1;    // K2 / K3 vector width
-    int k1_ty = 32, k1_tx = 32;
-    int k4_ty = 16, k4_tx = 16;
+    LowCfg k1{0, 32, 32};
+    LowCfg k4{0, 16, 16};
     int k2_th = 32;
     int k3_lth = 8;
     bool k3_fast = false;
@@ -194,22 +194,38 @@ static size_t smem_limit() {
     return g_smem_optin;
 }
 
+// Default low-resolution tiles: the column-walking kernels for r in
+// {1, 2, 4, 8} (CW columns x EY1 rows of coefficients per CTA), else the
+// generic tile kernels with the largest square tile that fits.
 static bool pick_lowres_tiles(int r, Plan& p) {
     const size_t lim = smem_limit();
-    static const int cand[] = {32, 16, 8};
     bool ok1 = false, ok4 = false;
-    for (int t : cand)
-        if (k1_smem_bytes(r, t, t) <= lim) {
-            p.k1_ty = p.k1_tx = t;
+    if (low_fast_radius(r)) {
+        const LowCfg k1 = r <= 2 ? LowCfg{1, 64, 32} : LowCfg{1, 128, 32};
+        const LowCfg k4 = r == 1 ? LowCfg{1, 64, 16} : (r == 2 ? LowCfg{1, 64, 32}
+                                                              : (r == 4 ? LowCfg{1, 128, 16} : LowCfg{1, 64, 32}));
+        if (k1_cfg_smem(k1, r, 0) <= lim) {
+            p.k1 = k1;
             ok1 = true;
-            break;
         }
-    for (int t : cand) {
-        if (t > 16) continue;
-        if (k4_smem_bytes(r, t, t) <= lim) {
-            p.k4_ty = p.k4_tx = t;
+        if (k4_cfg_smem(k4, r) <= lim) {
+            p.k4 = k4;
             ok4 = true;
-            break;
+        }
+    }
+    static const int cand[] = {32, 16, 8};
+    for (int t : cand) {
+        if (ok1) break;
+        if (k1_smem_bytes(r, t, t) <= lim) {
+            p.k1 = LowCfg{0, t, t};
+            ok1 = true;
+        }
+    }
+    for (int t : cand) {
+        if (ok4) break;
+        if (t <= 16 && k4_smem_bytes(r, t, t) <= lim) {
+            p.k4 = LowCfg{0, t, t};
+            ok4 = true;
         }
     }
     return ok1 && ok4;
@@ -249,25 +265,23 @@ static EncodeTiledFn encode_fn() {
 
 static bool g_tma_allowed = true;
 
-// One plane stack (planes x h x w of element size esz) for a K1 tile of
-// TY x TX with radius r.  False when the TMA alignment rules do not hold.
+// Tensor map over one plane stack (planes x h x w, element size esz) with
+// a bx x by box.  False when the TMA alignment rules do not hold.
 static bool make_tma(TmaPlane& tp, const void* base, CUtensorMapDataType ty, int esz, int planes, int h, int w,
-                     int r, int TY, int TX) {
+                     int bx, int by, int off) {
     EncodeTiledFn enc = encode_fn();
     if (enc == nullptr) return false;
-    const int U = 16 / esz;  // elements per 16 bytes
     if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
     if (((size_t)w * esz) % 16 != 0) return false;
-    if (TX % U != 0) return false;
-    const int lead = (2 * r + U - 1) / U * U;  // box starts on a 16-byte column boundary
-    tp.off = lead - 2 * r;
-    tp.bx = (tp.off + TX + 4 * r + U - 1) / U * U;
-    tp.by = TY + 4 * r;
+    if (((size_t)bx * esz) % 16 != 0) return false;
+    if (bx > 256 || by > 256 || bx < 1 || by < 1) return false;
+    tp.off = off;
+    tp.bx = bx;
+    tp.by = by;
     tp.esize = esz;
-    if (tp.bx > 256 || tp.by > 256) return false;
     cuuint64_t gdim[3] = {(cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)planes};
     cuuint64_t gstride[2] = {(cuuint64_t)w * esz, (cuuint64_t)w * h * esz};
-    cuuint32_t box[3] = {(cuuint32_t)tp.bx, (cuuint32_t)tp.by, 1};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult rc = enc(&tp.map, ty, 3, const_cast<void*>(base), gdim, gstride, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -280,19 +294,50 @@ static CUtensorMapDataType tma_type(dgf_dtype dt) {
                          : (dt == DGF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
 }
 
-// TMA pair for K1's (G, P) staging; also checks that the landing buffers fit.
+// Box of one input for K1's halo tile.  Generic tiles start on a 16-byte
+// column boundary (TX a multiple of the 16-byte unit), so the offset is a
+// constant; column-walking tiles start anywhere, so the box is one unit
+// wider and the kernel computes the offset per tile.
+static bool k1_box(const LowCfg& c, int r, int esz, int& bx, int& by, int& off) {
+    const int U = 16 / esz;
+    if (c.fast) {
+        const int EX2 = c.a + 2 * r;
+        bx = (EX2 + U - 1 + U - 1) / U * U;
+        by = c.b + 2 * r;
+        off = 0;
+        return true;
+    }
+    const int TY = c.a, TX = c.b;
+    if (TX % U != 0) return false;
+    const int lead = (2 * r + U - 1) / U * U;  // box starts on a 16-byte column boundary
+    off = lead - 2 * r;
+    bx = (off + TX + 4 * r + U - 1) / U * U;
+    by = TY + 4 * r;
+    return true;
+}
+
+// TMA pair for K1's (G, P) staging; `landing` returns the bytes the two
+// landing buffers need (with alignment slack).
 static TmaPair make_tma_pair(const void* G, dgf_dtype dg, const void* P, dgf_dtype dp, int planes, int h, int w,
-                             int r, int TY, int TX) {
+                             int r, const LowCfg& c, size_t& landing) {
     TmaPair t;
     memset(&t, 0, sizeof t);
     t.enabled = 0;
+    landing = 0;
     if (!g_tma_allowed) return t;
-    if (!make_tma(t.a, G, tma_type(dg), (int)esize(dg), planes, h, w, r, TY, TX)) return t;
-    if (!make_tma(t.b, P, tma_type(dp), (int)esize(dp), planes, h, w, r, TY, TX)) return t;
-    // landing buffers live in K1's row-statistics region (4 EY2 EX1 floats)
-    const size_t region = (size_t)4 * (TY + 4 * r) * (TX + 2 * r) * sizeof(float);
-    const size_t need = (size_t)t.a.bx * t.a.by * t.a.esize + (size_t)t.b.bx * t.b.by * t.b.esize + 256;
-    if (need > region + tma_extra_bytes(r, TY, TX)) return t;
+    int bxa, bya, offa, bxb, byb, offb;
+    if (!k1_box(c, r, (int)esize(dg), bxa, bya, offa) || !k1_box(c, r, (int)esize(dp), bxb, byb, offb)) return t;
+    if (!make_tma(t.a, G, tma_type(dg), (int)esize(dg), planes, h, w, bxa, bya, offa)) return t;
+    if (!make_tma(t.b, P, tma_type(dp), (int)esize(dp), planes, h, w, bxb, byb, offb)) return t;
+    const size_t need = (size_t)bxa * bya * esize(dg) + (size_t)bxb * byb * esize(dp) + 256;
+    if (c.fast) {
+        if (k1_fast_smem_bytes(r, c.a, c.b, need) > smem_limit()) return t;
+        landing = need;
+    } else {
+        // landing buffers live in the generic K1's row-statistics region (4 EY2 EX1 floats)
+        const size_t region = (size_t)4 * (c.a + 4 * r) * (c.b + 2 * r) * sizeof(float);
+        if (need > region + tma_extra_bytes(r, c.a, c.b)) return t;
+    }
     t.enabled = 1;
     return t;
 }
@@ -337,10 +382,12 @@ static dgf_status check_ws(void* ws, size_t ws_bytes, size_t need) {
 
 static cudaError_t run_k1(Launcher& L, dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef,
                           int planes, int h_l, int w_l, int r, float eps, const Plan& p, cudaStream_t s) {
-    TmaPair tma = make_tma_pair(G, gf32 ? DGF_F32 : dt, P, dt, planes, h_l, w_l, r, p.k1_ty, p.k1_tx);
+    size_t landing = 0;
+    TmaPair tma = make_tma_pair(G, gf32 ? DGF_F32 : dt, P, dt, planes, h_l, w_l, r, p.k1, landing);
+    const size_t smem = k1_cfg_smem(p.k1, r, tma.enabled ? landing : 0);
     uint32_t* st = status_ptr();
     return L.run("k1_lowres_coef", [&] {
-        return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, p.k1_ty, p.k1_tx, tma, st, s);
+        return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, st, s);
     });
 }
 
@@ -394,19 +441,19 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
         // the persistent K2 has fast paths for factors 4 and 8 only
         b.F = (p.F == 4 || p.F == 8) ? p.F : 0;
         b.vec = p.vec;
-        b.k1_ty = p.k1_ty;
-        b.k1_tx = p.k1_tx;
+        b.k1_fast = p.k1.fast;
+        b.k1_ty = p.k1.fast ? p.k1.b : p.k1.a;  // fast: EY1; generic: TY
+        b.k1_tx = p.k1.fast ? p.k1.a : p.k1.b;  // fast: CW;  generic: TX
         b.k2_th = p.k2_th;
-        b.k1_nx = (im.w_l + b.k1_tx - 1) / b.k1_tx;
-        b.k1_ny = (im.h_l + b.k1_ty - 1) / b.k1_ty;
+        low_grid(p.k1, im.r, im.h_l, im.w_l, b.k1_nx, b.k1_ny);
         b.k2_nx = (im.w + 32 * b.vec - 1) / (32 * b.vec);
         b.k2_ny = (im.h + b.k2_th - 1) / b.k2_th;
         b.coef = ws_base ? reinterpret_cast<float2*>(ws_base + off) : nullptr;
         off += align256((size_t)im.C * im.h_l * im.w_l * sizeof(float2));
         bp.k1_start[i + 1] = bp.k1_start[i] + b.k1_nx * b.k1_ny * im.C;
         bp.k2_start[i + 1] = bp.k2_start[i] + b.k2_nx * b.k2_ny * im.C;
-        out.smem1 = std::max(out.smem1, k1_smem_bytes(b.r, b.k1_ty, b.k1_tx));
-        out.smem2 = std::max(out.smem2, k2_smem_bytes(b.vec, b.F, b.w_l, b.w, b.k2_th));
+        out.smem1 = std::max(out.smem1, k1_cfg_smem(p.k1, b.r, 0));
+        out.smem2 = std::max(out.smem2, k2_smem_bytes(b.vec, b.F, b.h_l, b.h, b.w_l, b.w, b.k2_th));
     }
     bp.k1_total = bp.k1_start[n];
     bp.k2_total = bp.k2_start[n];
@@ -523,8 +570,7 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
         }
         if (dp_l != nullptr || dI_l != nullptr) {
             e = L.run("k4_lowres_bwd", [&] {
-                return launch_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4_ty,
-                                 p.k4_tx, s);
+                return launch_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4, s);
             });
             if (e != cudaSuccess) return cuda_fail(e, "k4");
         }
@@ -550,7 +596,7 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
     if (dp_l != nullptr || need_hi) {
         e = L.run("k4_lowres_bwd", [&] {
             return launch_k4(dt, true, G_l, p_l, dcoef, dp_l, need_hi ? dG_l : nullptr, planes, h_l, w_l, r, eps,
-                             p.k4_ty, p.k4_tx, s);
+                             p.k4, s);
         });
         if (e != cudaSuccess) return cuda_fail(e, "k4");
     }

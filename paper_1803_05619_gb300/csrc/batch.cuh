@@ -17,6 +17,7 @@ struct BatchImage {
     float eps;
     int F;            // integer upsampling factor, 0 = general ratio
     int vec;          // elements per vector access of the high-res pass
+    int k1_fast;      // 1: column-walking kernel (k1_ty = EY1, k1_tx = CW), 0: generic tile
     int k1_ty, k1_tx; // low-res tile
     int k2_th;        // high-res rows per tile
     int k1_nx, k1_ny; // low-res tiles per plane

@@ -40,6 +40,18 @@ __device__ __forceinline__ void load_vec(const T* __restrict__ p, float (&out)[V
     for (int k = 0; k < VEC; ++k) out[k] = to_f32<T>(x.v[k]);
 }
 
+// Raw vector load through the read-only path (kept packed until used).
+template <typename T, int VEC>
+__device__ __forceinline__ Vec<T, VEC> ldg_vec(const T* __restrict__ p) {
+    return *reinterpret_cast<const Vec<T, VEC>*>(p);
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void unpack_vec(const Vec<T, VEC>& x, float (&out)[VEC]) {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) out[k] = to_f32<T>(x.v[k]);
+}
+
 template <typename T, int VEC>
 __device__ __forceinline__ void store_vec(T* __restrict__ p, const float (&in)[VEC]) {
     Vec<T, VEC> x;
@@ -79,6 +91,7 @@ __device__ __forceinline__ Tap tap_general(int y, int n_in, int n_out) {
 // the same as clamping t at 0.
 template <int F>
 __device__ __forceinline__ Tap tap_int(int y) {
+    static_assert(F > 0, "integer factor");
     const int j = y / F, q = y - (y / F) * F;
     const int t2 = 2 * q + 1 - F;
     Tap t;

@@ -111,8 +111,14 @@ __global__ void __launch_bounds__(kThreads) k2_apply_batched(const __grid_consta
 }
 
 // ------------------------------------------------------------------ host side
-size_t k2_smem_bytes(int vec, int F, int w_l, int w, int TH) {
-    return (size_t)TH * k2_pitch(vec, F, w_l, w) * sizeof(float2);
+// rows of the raw low-res coefficient block a K2 tile of TH rows touches
+static int k2_raw_rows(int F, int h_l, int h, int TH) {
+    if (F > 0) return TH / F + 3;
+    return (int)(((long long)TH * h_l + h - 1) / h) + 3;
+}
+
+size_t k2_smem_bytes(int vec, int F, int h_l, int h, int w_l, int w, int TH) {
+    return (size_t)(TH + k2_raw_rows(F, h_l, h, TH)) * k2_pitch(vec, F, w_l, w) * sizeof(float2);
 }
 
 int k3_ltw(int vec, int F) {
@@ -122,7 +128,8 @@ int k3_ltw(int vec, int F) {
 
 size_t k3_smem_bytes(int vec, int F, int LTH) {
     const int SXP = k3_ltw(vec, F) + 2;
-    return (size_t)F * (LTH + 1) * SXP * sizeof(float2) + (size_t)F * LTH * SXP * sizeof(float);
+    return (size_t)F * (LTH + 1) * SXP * sizeof(float2) + (size_t)F * LTH * SXP * sizeof(float) +
+           (size_t)(LTH + 2) * SXP * sizeof(float);
 }
 
 bool k3_fast_ok(int vec, int F) {
@@ -141,7 +148,7 @@ template <typename T, int VEC, int F, int MODE>
 static cudaError_t k2_go(const float2* coef, const void* in, void* out, int planes, int h_l, int w_l,
                          int h, int w, int TH, cudaStream_t s) {
     const int pitch = k2_pitch(VEC, F, w_l, w);
-    const size_t smem = (size_t)TH * pitch * sizeof(float2);
+    const size_t smem = k2_smem_bytes(VEC, F, h_l, h, w_l, w, TH);
     auto kern = k2_apply<T, VEC, F, MODE>;
     cudaError_t e = prep(kern, smem);
     if (e != cudaSuccess) return e;

@@ -30,64 +30,98 @@ __device__ void apply_tile(const float2* __restrict__ coef, const T* __restrict_
                            T* __restrict__ out, int h_l, int w_l, int h, int w, int Y0, int X0, int TH,
                            int pitch, float2* sAB) {
     constexpr int TW = 32 * VEC;
+    constexpr int U = 4;  // rows in flight per thread
+    constexpr int FF = F > 0 ? F : 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int xs = X0 + lane * VEC;
+    const bool col_ok = xs < w;
+    // issue the first rows' loads before staging, so both latencies overlap
+    Vec<T, VEC> raw[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int i = warp + u * kWarps, y = Y0 + i;
+        if (col_ok && i < TH && y < h) raw[u] = ldg_vec<T, VEC>(in + (size_t)y * w + xs);
+    }
     int jlo;
     int ncol;
     if (F > 0) {
-        jlo = X0 / F - 1;
-        ncol = TW / F + 2;
+        jlo = X0 / FF - 1;
+        ncol = TW / FF + 2;
     } else {
         const int xl = min(X0 + TW, w) - 1;
         jlo = tap_general(X0, w_l, w).i0;
         ncol = tap_general(xl, w_l, w).i0 - jlo + 2;
     }
+    // low-res rows the tile's taps reach, clamped to the image
+    const int ylast = min(Y0 + TH, h) - 1;
+    const Tap tfirst = F > 0 ? tap_int<FF>(Y0) : tap_general(Y0, h_l, h);
+    const Tap tlast = F > 0 ? tap_int<FF>(ylast) : tap_general(ylast, h_l, h);
+    const int rlo = clampi(tfirst.i0, 0, h_l - 1);
+    const int rhi = clampi(tlast.i0 + 1, 0, h_l - 1);
+    const int nrows = rhi - rlo + 1;
+    float2* sRaw = sAB + TH * pitch;  // nrows x ncol raw coefficients
+    // phase 1: every low-res coefficient the tile needs, loaded once (8 loads in flight per thread)
+    {
+        const int n = nrows * ncol;
+        for (int base = threadIdx.x; base < n; base += 8 * kThreads) {
+            float2 v[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int idx = base + b * kThreads;
+                if (idx < n) {
+                    const int rr = idx / ncol, c = idx - rr * ncol;
+                    v[b] = coef[(size_t)(rlo + rr) * w_l + clampi(jlo + c, 0, w_l - 1)];
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int idx = base + b * kThreads;
+                if (idx < n) sRaw[idx] = v[b];
+            }
+        }
+    }
+    __syncthreads();
+    // phase 2: interpolate along y, one row per high-res row of the tile
     const int nst = TH * ncol;
     for (int idx = threadIdx.x; idx < nst; idx += kThreads) {
         const int i = idx / ncol, c = idx - i * ncol;
         const int y = Y0 + i;
         if (y >= h) continue;
-        Tap ty;
-        if (F > 0) {
-            const int q = y % F, j = y / F, t2 = 2 * q + 1 - F;
-            ty.i0 = t2 < 0 ? j - 1 : j;
-            ty.lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
-        } else {
-            ty = tap_general(y, h_l, h);
-        }
-        const int r0 = clampi(ty.i0, 0, h_l - 1), r1 = clampi(ty.i0 + 1, 0, h_l - 1);
-        const int jj = clampi(jlo + c, 0, w_l - 1);
-        const float2 a = coef[(size_t)r0 * w_l + jj];
-        const float2 b = coef[(size_t)r1 * w_l + jj];
+        const Tap ty = F > 0 ? tap_int<FF>(y) : tap_general(y, h_l, h);
+        const int r0 = clampi(ty.i0, 0, h_l - 1) - rlo, r1 = clampi(ty.i0 + 1, 0, h_l - 1) - rlo;
+        const float2 a = sRaw[r0 * ncol + c];
+        const float2 b = sRaw[r1 * ncol + c];
         sAB[i * pitch + c] = make_float2(lerp(a.x, b.x, ty.lam), lerp(a.y, b.y, ty.lam));
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int xs = X0 + lane * VEC;
-    if (xs < w) {
+    if (col_ok) {
         // column taps of this lane's VEC pixels (same for every row)
         int cc[VEC];
         float ll[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) {
             if (F > 0) {
-                col_tap<(F > 0 ? F : 1)>(lane * VEC + k, cc[k], ll[k]);
+                col_tap<FF>(lane * VEC + k, cc[k], ll[k]);
             } else {
                 const Tap tx = tap_general(xs + k, w_l, w);
                 cc[k] = tx.i0 - jlo;
                 ll[k] = tx.lam;
             }
         }
-        constexpr int U = 4;  // rows in flight per thread
         for (int i0 = warp; i0 < TH; i0 += kWarps * U) {
-            float g[U][VEC];
+            if (i0 != warp) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = i0 + u * kWarps, y = Y0 + i;
-                if (i < TH && y < h) load_vec<T, VEC>(in + (size_t)y * w + xs, g[u]);
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * kWarps, y = Y0 + i;
+                    if (i < TH && y < h) raw[u] = ldg_vec<T, VEC>(in + (size_t)y * w + xs);
+                }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int i = i0 + u * kWarps, y = Y0 + i;
                 if (i < TH && y < h) {
+                    float g[VEC];
+                    unpack_vec<T, VEC>(raw[u], g);
                     const float2* row = sAB + i * pitch;
                     float o[VEC];
 #pragma unroll
@@ -96,9 +130,9 @@ __device__ void apply_tile(const float2* __restrict__ coef, const T* __restrict_
                         const float A = lerp(s0.x, s1.x, ll[k]);
                         if (MODE == 0) {
                             const float B = lerp(s0.y, s1.y, ll[k]);
-                            o[k] = fmaf(A, g[u][k], B);
+                            o[k] = fmaf(A, g[k], B);
                         } else {
-                            o[k] = A * g[u][k];
+                            o[k] = A * g[k];
                         }
                     }
                     store_vec<T, VEC>(out + (size_t)y * w + xs, o);
@@ -216,8 +250,28 @@ __device__ __forceinline__ void k3_gather_columns(const float2* Sx, int i0, int 
 // [F i0, F (i0 + LTH)), columns j0-1 .. j0+LTW (clamped), into SA.
 template <int VEC, int F>
 __device__ __forceinline__ void k3_stage_abar(const float2* __restrict__ coef, int i0, int j0, int LTH,
-                                              int h_l, int w_l, int h, float* SA) {
+                                              int h_l, int w_l, int h, float* SA, float* sRaw) {
     constexpr int SXP = K3Shape<VEC, F>::SXP;
+    // raw Abar rows i0-1 .. i0+LTH (clamped), loaded once, 8 loads in flight per thread
+    const int nraw = (LTH + 2) * SXP;
+    for (int base = threadIdx.x; base < nraw; base += 8 * kThreads) {
+        float v[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int idx = base + b * kThreads;
+            if (idx < nraw) {
+                const int rr = idx / SXP, c = idx - rr * SXP;
+                const int row = clampi(i0 - 1 + rr, 0, h_l - 1), jj = clampi(j0 - 1 + c, 0, w_l - 1);
+                v[b] = coef[(size_t)row * w_l + jj].x;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int idx = base + b * kThreads;
+            if (idx < nraw) sRaw[idx] = v[b];
+        }
+    }
+    __syncthreads();
     const int nst = F * LTH * SXP;
     for (int idx = threadIdx.x; idx < nst; idx += kThreads) {
         const int ri = idx / SXP, c = idx - ri * SXP;
@@ -226,9 +280,9 @@ __device__ __forceinline__ void k3_stage_abar(const float2* __restrict__ coef, i
         const int q = y % F, j = y / F, t2 = 2 * q + 1 - F;
         const int yi0 = t2 < 0 ? j - 1 : j;
         const float lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
-        const int r0 = clampi(yi0, 0, h_l - 1), r1 = clampi(yi0 + 1, 0, h_l - 1);
-        const int jj = clampi(j0 - 1 + c, 0, w_l - 1);
-        SA[idx] = lerp(coef[(size_t)r0 * w_l + jj].x, coef[(size_t)r1 * w_l + jj].x, lam);
+        // raw row index = clamped low-res row - (i0 - 1); clamping matches the load above
+        const int r0 = clampi(yi0, 0, h_l - 1) - (i0 - 1), r1 = clampi(yi0 + 1, 0, h_l - 1) - (i0 - 1);
+        SA[idx] = lerp(sRaw[r0 * SXP + c], sRaw[r1 * SXP + c], lam);
     }
 }
 
@@ -248,41 +302,62 @@ __device__ void hires_bwd_tile(const float2* __restrict__ coef, const T* __restr
                                int h_l, int w_l, int h, int w, int i0, int j0, int LTH, float* smem) {
     using S = K3Shape<VEC, F>;
     constexpr int K = S::K, H0 = S::H0, LTW = S::LTW, SXP = S::SXP;
+    constexpr int U = 5;  // footprint rows per warp held in flight (F (LTH + 1) <= 40 rows)
     const int FR = F * (LTH + 1);
     const int yf0 = F * (i0 - 1) + H0;
     const int XS = F * j0 - VEC;
     float2* Sx = reinterpret_cast<float2*>(smem);
     float* SA = reinterpret_cast<float*>(Sx + FR * SXP);
-    if (dG != nullptr) {
-        k3_stage_abar<VEC, F>(coef, i0, j0, LTH, h_l, w_l, h, SA);
-        __syncthreads();
-    }
+    float* sRaw = SA + F * LTH * SXP;  // (LTH + 2) x SXP
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int xs = XS + lane * VEC;
     const bool col_ok = xs >= 0 && xs < w;
     const bool interior = lane >= 1 && lane <= LTW / K;
-    for (int fr = warp; fr < FR; fr += kWarps) {
-        const int y = yf0 + fr;
-        const bool ok = col_ok && y >= 0 && y < h;
-        float rv[VEC], gv[VEC];
-        if (ok) {
-            load_vec<T, VEC>(R + (size_t)y * w + xs, rv);
-            load_vec<T, VEC>(G + (size_t)y * w + xs, gv);
-        } else {
+    Vec<T, VEC> rr[U], gg[U];
+    auto load_chunk = [&](int f0) {
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) rv[k] = gv[k] = 0.f;
+        for (int u = 0; u < U; ++u) {
+            const int fr = f0 + u * kWarps, y = yf0 + fr;
+            if (fr < FR && col_ok && y >= 0 && y < h) {
+                rr[u] = ldg_vec<T, VEC>(R + (size_t)y * w + xs);
+                gg[u] = ldg_vec<T, VEC>(G + (size_t)y * w + xs);
+            }
         }
-        if (dG != nullptr && ok && interior && y >= F * i0 && y < F * (i0 + LTH)) {
-            const float* row = SA + (y - F * i0) * SXP;
-            float o[VEC];
+    };
+    load_chunk(warp);  // first rows in flight before the staging below
+    if (dG != nullptr) {
+        // Abar along y for the interior rows, once per tile
+        k3_stage_abar<VEC, F>(coef, i0, j0, LTH, h_l, w_l, h, SA, sRaw);
+        __syncthreads();
+    }
+    for (int f0 = warp; f0 < FR; f0 += kWarps * U) {
+        if (f0 != warp) load_chunk(f0);
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) o[k] = rv[k] * k3_abar_at<VEC, F>(row, lane, k);
-            store_vec<T, VEC>(dG + (size_t)y * w + xs, o);
+        for (int u = 0; u < U; ++u) {
+            const int fr = f0 + u * kWarps, y = yf0 + fr;
+            if (fr < FR) {  // uniform across the warp: every lane takes part in the shuffles
+                const bool ok = col_ok && y >= 0 && y < h;
+                float rv[VEC], gv[VEC];
+                if (ok) {
+                    unpack_vec<T, VEC>(rr[u], rv);
+                    unpack_vec<T, VEC>(gg[u], gv);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) rv[k] = gv[k] = 0.f;
+                }
+                if (dG != nullptr && ok && interior && y >= F * i0 && y < F * (i0 + LTH)) {
+                    const float* row = SA + (y - F * i0) * SXP;
+                    float o[VEC];
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) o[k] = rv[k] * k3_abar_at<VEC, F>(row, lane, k);
+                    store_vec<T, VEC>(dG + (size_t)y * w + xs, o);
+                }
+                float u2[VEC];
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) u2[k] = rv[k] * gv[k];
+                k3_row_to_smem<VEC, F>(u2, rv, lane, Sx + fr * SXP);
+            }
         }
-        float u[VEC];
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) u[k] = rv[k] * gv[k];
-        k3_row_to_smem<VEC, F>(u, rv, lane, Sx + fr * SXP);
     }
     __syncthreads();
     k3_gather_columns<VEC, F>(Sx, i0, j0, LTH, h_l, w_l, dcoef);

@@ -22,18 +22,32 @@ __host__ __device__ inline int k2_pitch(int vec, int F, int w_l, int w) {
     return (int)span + 3;
 }
 
+// Low-resolution tile configuration: fast = column-walking kernels (r in
+// {1, 2, 4, 8}; a = CW columns, b = EY1 rows of the coefficient region),
+// else the generic tile kernels (a = TY, b = TX output tile).
+struct LowCfg {
+    int fast;
+    int a, b;
+};
+
 size_t k1_smem_bytes(int r, int TY, int TX);
 size_t k4_smem_bytes(int r, int TY, int TX);
-size_t k2_smem_bytes(int vec, int F, int w_l, int w, int TH);
+bool low_fast_radius(int r);
+size_t k1_fast_smem_bytes(int r, int CW, int EY1, size_t tma_landing);
+size_t k4_fast_smem_bytes(int r, int CW, int EY1);
+size_t k1_cfg_smem(const LowCfg& c, int r, size_t tma_landing);
+size_t k4_cfg_smem(const LowCfg& c, int r);
+void low_grid(const LowCfg& c, int r, int h, int w, int& gx, int& gy);
+size_t k2_smem_bytes(int vec, int F, int h_l, int h, int w_l, int w, int TH);
 size_t k3_smem_bytes(int vec, int F, int LTH);
 int k3_ltw(int vec, int F);
 bool k3_fast_ok(int vec, int F);
 
-cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P, float2* coef,
-                      int planes, int h, int w, int r, float eps, int TY, int TX, const TmaPair& tma,
+cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P, float2* coef, int planes,
+                      int h, int w, int r, float eps, const LowCfg& c, const TmaPair& tma, size_t smem,
                       uint32_t* status, cudaStream_t s);
 cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P, const float2* dcoef,
-                      void* dP, void* dG, int planes, int h, int w, int r, float eps, int TY, int TX,
+                      void* dP, void* dG, int planes, int h, int w, int r, float eps, const LowCfg& c,
                       cudaStream_t s);
 cudaError_t launch_k2(dgf_dtype dt, int mode, const float2* coef, const void* in, void* out, int planes,
                       int h_l, int w_l, int h, int w, int vec, int F, int TH, cudaStream_t s);
@@ -59,6 +73,31 @@ cudaError_t launch_k6(dgf_dtype dt, const float2* coef, const float* dG_l, const
                       void* dI_h, float* partials, int N, int h_l, int w_l, int h, int w, int F, float slope,
                       cudaStream_t s);
 cudaError_t launch_wreduce(const float* partials, int nblocks, float* dW, int hidden, cudaStream_t s);
+
+// Column-walking low-resolution kernels, one translation unit per radius.
+template <int R>
+cudaError_t launch_k1_fast(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes,
+                           int h, int w, float eps, const LowCfg& c, const TmaPair& tma, size_t smem,
+                           uint32_t* status, cudaStream_t s);
+template <int R>
+cudaError_t launch_k4_fast(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP,
+                           void* dG, int planes, int h, int w, float eps, const LowCfg& c, cudaStream_t s);
+extern template cudaError_t launch_k1_fast<1>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
+                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+extern template cudaError_t launch_k1_fast<2>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
+                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+extern template cudaError_t launch_k1_fast<4>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
+                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+extern template cudaError_t launch_k1_fast<8>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
+                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+extern template cudaError_t launch_k4_fast<1>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*,
+                                              int, int, int, float, const LowCfg&, cudaStream_t);
+extern template cudaError_t launch_k4_fast<2>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*,
+                                              int, int, int, float, const LowCfg&, cudaStream_t);
+extern template cudaError_t launch_k4_fast<4>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*,
+                                              int, int, int, float, const LowCfg&, cudaStream_t);
+extern template cudaError_t launch_k4_fast<8>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*,
+                                              int, int, int, float, const LowCfg&, cudaStream_t);
 
 // Persistent batched kernels (function pointers for graph nodes).
 cudaError_t k1_batched_kernel(dgf_dtype dt, size_t smem, void** fn);

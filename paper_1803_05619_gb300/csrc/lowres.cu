@@ -2,72 +2,10 @@
 // (recompute + Algorithm 1's low-resolution gradients).
 #include "batch.cuh"
 #include "kernels.h"
-#include "lowres.cuh"
-#include "tma.cuh"
+#include "lowres_fast.cuh"
+#include "lowres_generic.cuh"
 
 namespace dgf {
-
-// --------------------------------------------------------------------- K1
-// Eq. 1 (least-squares A, b per window, Sec. 3.2) followed by the box mean
-// of A and b (Sec. 3.3's f_mu applied once more at low resolution).
-template <typename TG, typename TP>
-__device__ void coef_tile(const TG* __restrict__ G, const TP* __restrict__ P,
-                          float2* __restrict__ coef, const LowresTile& t, float* smem,
-                          const TmaPlane* tg, const TmaPlane* tp, int plane, uint32_t* status) {
-    const int n2 = t.EY2 * t.EX2;
-    float* sG = smem;
-    float* sP = sG + n2;
-    float* hbuf = sP + n2;
-    bool staged = false;
-    if (tg != nullptr && tp != nullptr)
-        staged = tma_stage_pair<TG, TP>(tg, tp, plane, t, sG, sP, hbuf, status);
-    if (!staged) {
-        stage_plane<TG>(G, sG, t);
-        stage_plane<TP>(P, sP, t);
-    }
-    __syncthreads();
-    const int nh = t.EY2 * t.EX1;
-    stats_rows(sG, sP, hbuf, hbuf + nh, hbuf + 2 * nh, hbuf + 3 * nh, t);
-    __syncthreads();
-    // A, b on E1 (zero outside the image); the staged inputs are dead now
-    const int n1 = t.EY1 * t.EX1;
-    float* sA = smem;
-    float* sB = smem + n1;
-    for (int idx = threadIdx.x; idx < n1; idx += kThreads) {
-        const int ey1 = idx / t.EX1, ex = idx - ey1 * t.EX1;
-        const int gy = t.ty0 - t.r + ey1, gx = t.tx0 - t.r + ex;
-        float A = 0.f, b = 0.f;
-        if (gy >= 0 && gy < t.h && gx >= 0 && gx < t.w) {
-            const Moments m = stats_window(hbuf, hbuf + nh, hbuf + 2 * nh, hbuf + 3 * nh, ey1, ex, t);
-            A = m.cov / (m.var + t.eps);
-            b = fmaf(-A, m.mu, m.nu);
-        }
-        sA[idx] = A;
-        sB[idx] = b;
-    }
-    __syncthreads();
-    float* rA = hbuf;
-    float* rB = hbuf + t.EY1 * t.TX;
-    box_rows(sA, t.EX1, t.EY1, t.tx0 - t.r, rA, t.TX, t.tx0, t.TX, t.w, t.r);
-    box_rows(sB, t.EX1, t.EY1, t.tx0 - t.r, rB, t.TX, t.tx0, t.TX, t.w, t.r);
-    __syncthreads();
-    const int n0 = t.TY * t.TX;
-    for (int idx = threadIdx.x; idx < n0; idx += kThreads) {
-        const int y = idx / t.TX, x = idx - y * t.TX;
-        const int gy = t.ty0 + y, gx = t.tx0 + x;
-        if (gy >= t.h || gx >= t.w) continue;
-        const int lo = max(gy - t.r, 0), hi = min(gy + t.r, t.h - 1);
-        float sa = 0.f, sb = 0.f;
-        for (int k = lo; k <= hi; ++k) {
-            const int o = (k - (t.ty0 - t.r)) * t.TX + x;
-            sa += rA[o];
-            sb += rB[o];
-        }
-        const float n = (float)((hi - lo + 1) * t.cnt(gx, t.w));
-        coef[(size_t)gy * t.w + gx] = make_float2(sa / n, sb / n);
-    }
-    __syncthreads();
-}
 
 template <typename TG, typename TP>
 __global__ void __launch_bounds__(kThreads) k1_coef(const TG* __restrict__ G, const TP* __restrict__ P,
@@ -274,33 +212,11 @@ __global__ void __launch_bounds__(kThreads) k4_lowres_bwd(const TG* __restrict__
                                 smem);
 }
 
-// ------------------------------------------------------- batched K1 (persistent)
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k1_coef_batched(const __grid_constant__ BatchParams bp,
-                                                            uint32_t* status) {
-    extern __shared__ __align__(128) float smem[];
-    for (int tile = blockIdx.x; tile < bp.k1_total; tile += gridDim.x) {
-        const int i = batch_find(bp.k1_start, bp.n, tile);
-        const BatchImage& im = bp.img[i];
-        const int local = tile - bp.k1_start[i];
-        const int per_plane = im.k1_nx * im.k1_ny;
-        const int plane = local / per_plane;
-        const int tp = local - plane * per_plane;
-        const int ty = tp / im.k1_nx, tx = tp - ty * im.k1_nx;
-        LowresTile t;
-        t.init(im.h_l, im.w_l, im.r, im.eps, ty * im.k1_ty, tx * im.k1_tx, im.k1_ty, im.k1_tx);
-        const size_t hw = (size_t)im.h_l * im.w_l;
-        coef_tile<T, T>(static_cast<const T*>(im.I_l) + plane * hw,
-                        static_cast<const T*>(im.p_l) + plane * hw, im.coef + plane * hw, t, smem,
-                        nullptr, nullptr, plane, status);
-    }
-}
-
 // ------------------------------------------------------------------ host side
 size_t k1_smem_bytes(int r, int TY, int TX) {
     const size_t EY2 = TY + 4 * r, EX2 = TX + 4 * r, EX1 = TX + 2 * r;
     size_t floats = 2 * EY2 * EX2 + 4 * EY2 * EX1;
-    // TMA staging adds a raw landing buffer for 16-bit inputs; bounded by the same region
+    // TMA staging lands inside the row-statistics region, plus alignment slack
     return floats * sizeof(float) + tma_extra_bytes(r, TY, TX);
 }
 
@@ -309,6 +225,44 @@ size_t k4_smem_bytes(int r, int TY, int TX) {
     const size_t n2 = EY2 * EX2, n1 = EY1 * EX1;
     const size_t nh = std::max(4 * EY2 * EX1, 7 * EY1 * (size_t)TX);
     return (4 * n2 + nh + 13 * n1 + 3 * kWarps) * sizeof(float);
+}
+
+bool low_fast_radius(int r) { return r == 1 || r == 2 || r == 4 || r == 8; }
+
+size_t k1_fast_smem_bytes(int r, int CW, int EY1, size_t tma_landing) {
+    const size_t e2 = (size_t)(CW + 2 * r) * (EY1 + 2 * r), e1 = (size_t)CW * EY1;
+    size_t floats = 2 * e2 + 2 * e1;
+    if (r > 2) floats += (size_t)4 * (EY1 + 2 * r) * CW;  // row statistics of the staged walk
+    const size_t base = floats * sizeof(float);
+    // the TMA landing buffers overlap sA, sB (and what follows) and may extend past them
+    const size_t land_end = 2 * e2 * sizeof(float) + tma_landing;
+    return std::max(base, land_end);
+}
+
+size_t k4_fast_smem_bytes(int r, int CW, int EY1) {
+    const size_t e2 = (size_t)(CW + 2 * r) * (EY1 + 2 * r), e1 = (size_t)CW * EY1;
+    size_t floats = 4 * e2 + 7 * e1 + 3 * (kLowThreads / 32);
+    if (r > 2) floats += 8 + std::max((size_t)6 * (EY1 + 2 * r) * CW, 7 * e1);
+    return floats * sizeof(float);
+}
+
+size_t k1_cfg_smem(const LowCfg& c, int r, size_t tma_landing) {
+    return c.fast ? k1_fast_smem_bytes(r, c.a, c.b, tma_landing) : k1_smem_bytes(r, c.a, c.b);
+}
+
+size_t k4_cfg_smem(const LowCfg& c, int r) {
+    return c.fast ? k4_fast_smem_bytes(r, c.a, c.b) : k4_smem_bytes(r, c.a, c.b);
+}
+
+void low_grid(const LowCfg& c, int r, int h, int w, int& gx, int& gy) {
+    if (c.fast) {
+        const int TX = c.a - 2 * r, TY = c.b - 2 * r;
+        gx = (w + TX - 1) / TX;
+        gy = (h + TY - 1) / TY;
+    } else {
+        gx = (w + c.b - 1) / c.b;
+        gy = (h + c.a - 1) / c.a;
+    }
 }
 
 template <typename K>
@@ -320,81 +274,97 @@ static cudaError_t prep(K kernel, size_t smem) {
 
 template <typename TG, typename TP>
 static cudaError_t k1_go(const void* G, const void* P, float2* coef, int planes, int h, int w, int r,
-                         float eps, int TY, int TX, const TmaPair& tma, uint32_t* status,
+                         float eps, const LowCfg& c, const TmaPair& tma, size_t smem, uint32_t* status,
                          cudaStream_t s) {
-    const size_t smem = k1_smem_bytes(r, TY, TX);
     auto kern = k1_coef<TG, TP>;
     cudaError_t e = prep(kern, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY, planes);
-    kern<<<grid, kThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), coef, h,
-                                      w, r, eps, TY, TX, tma, status);
+    int gx, gy;
+    low_grid(c, r, h, w, gx, gy);
+    kern<<<dim3(gx, gy, planes), kThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), coef,
+                                                      h, w, r, eps, c.a, c.b, tma, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P, float2* coef,
-                      int planes, int h, int w, int r, float eps, int TY, int TX, const TmaPair& tma,
+cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P, float2* coef, int planes,
+                      int h, int w, int r, float eps, const LowCfg& c, const TmaPair& tma, size_t smem,
                       uint32_t* status, cudaStream_t s) {
     if (planes == 0) return cudaSuccess;
+    if (c.fast) {
+        switch (r) {
+            case 1: return launch_k1_fast<1>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
+            case 2: return launch_k1_fast<2>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
+            case 4: return launch_k1_fast<4>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
+            case 8: return launch_k1_fast<8>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (dt) {
         case DGF_F32:
-            return k1_go<float, float>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s);
+            return k1_go<float, float>(G, P, coef, planes, h, w, r, eps, c, tma, smem, status, s);
         case DGF_BF16:
-            return guide_f32 ? k1_go<float, __nv_bfloat16>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s)
-                             : k1_go<__nv_bfloat16, __nv_bfloat16>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s);
+            return guide_f32 ? k1_go<float, __nv_bfloat16>(G, P, coef, planes, h, w, r, eps, c, tma, smem, status, s)
+                             : k1_go<__nv_bfloat16, __nv_bfloat16>(G, P, coef, planes, h, w, r, eps, c, tma, smem, status, s);
         case DGF_F16:
-            return guide_f32 ? k1_go<float, __half>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s)
-                             : k1_go<__half, __half>(G, P, coef, planes, h, w, r, eps, TY, TX, tma, status, s);
+            return guide_f32 ? k1_go<float, __half>(G, P, coef, planes, h, w, r, eps, c, tma, smem, status, s)
+                             : k1_go<__half, __half>(G, P, coef, planes, h, w, r, eps, c, tma, smem, status, s);
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename TG, typename TP, typename TD>
 static cudaError_t k4_go(const void* G, const void* P, const float2* dcoef, void* dP, void* dG,
-                         int planes, int h, int w, int r, float eps, int TY, int TX, cudaStream_t s) {
-    const size_t smem = k4_smem_bytes(r, TY, TX);
+                         int planes, int h, int w, int r, float eps, const LowCfg& c, cudaStream_t s) {
+    const size_t smem = k4_smem_bytes(r, c.a, c.b);
     auto kern = k4_lowres_bwd<TG, TP, TD>;
     cudaError_t e = prep(kern, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY, planes);
-    kern<<<grid, kThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef,
-                                      static_cast<TP*>(dP), static_cast<TD*>(dG), h, w, r, eps, TY, TX);
+    int gx, gy;
+    low_grid(c, r, h, w, gx, gy);
+    kern<<<dim3(gx, gy, planes), kThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef,
+                                                      static_cast<TP*>(dP), static_cast<TD*>(dG), h, w, r, eps,
+                                                      c.a, c.b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P, const float2* dcoef,
-                      void* dP, void* dG, int planes, int h, int w, int r, float eps, int TY, int TX,
+                      void* dP, void* dG, int planes, int h, int w, int r, float eps, const LowCfg& c,
                       cudaStream_t s) {
     if (planes == 0) return cudaSuccess;
+    if (c.fast) {
+        switch (r) {
+            case 1: return launch_k4_fast<1>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
+            case 2: return launch_k4_fast<2>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
+            case 4: return launch_k4_fast<4>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
+            case 8: return launch_k4_fast<8>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (dt) {
         case DGF_F32:
-            return k4_go<float, float, float>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s);
+            return k4_go<float, float, float>(G, P, dcoef, dP, dG, planes, h, w, r, eps, c, s);
         case DGF_BF16:
             return guide_f32
-                       ? k4_go<float, __nv_bfloat16, float>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s)
-                       : k4_go<__nv_bfloat16, __nv_bfloat16, __nv_bfloat16>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s);
+                       ? k4_go<float, __nv_bfloat16, float>(G, P, dcoef, dP, dG, planes, h, w, r, eps, c, s)
+                       : k4_go<__nv_bfloat16, __nv_bfloat16, __nv_bfloat16>(G, P, dcoef, dP, dG, planes, h, w, r, eps, c, s);
         case DGF_F16:
             return guide_f32
-                       ? k4_go<float, __half, float>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s)
-                       : k4_go<__half, __half, __half>(G, P, dcoef, dP, dG, planes, h, w, r, eps, TY, TX, s);
+                       ? k4_go<float, __half, float>(G, P, dcoef, dP, dG, planes, h, w, r, eps, c, s)
+                       : k4_go<__half, __half, __half>(G, P, dcoef, dP, dG, planes, h, w, r, eps, c, s);
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename T>
-static cudaError_t k1b_prep(size_t smem) {
-    return prep(k1_coef_batched<T>, smem);
-}
+cudaError_t k1_batched_kernel_t(size_t smem, void** fn);
 
 cudaError_t k1_batched_kernel(dgf_dtype dt, size_t smem, void** fn) {
-    cudaError_t e = cudaSuccess;
     switch (dt) {
-        case DGF_F32: e = k1b_prep<float>(smem); *fn = (void*)k1_coef_batched<float>; break;
-        case DGF_BF16: e = k1b_prep<__nv_bfloat16>(smem); *fn = (void*)k1_coef_batched<__nv_bfloat16>; break;
-        case DGF_F16: e = k1b_prep<__half>(smem); *fn = (void*)k1_coef_batched<__half>; break;
-        default: return cudaErrorInvalidValue;
+        case DGF_F32: return k1_batched_kernel_t<float>(smem, fn);
+        case DGF_BF16: return k1_batched_kernel_t<__nv_bfloat16>(smem, fn);
+        case DGF_F16: return k1_batched_kernel_t<__half>(smem, fn);
     }
-    return e;
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace dgf

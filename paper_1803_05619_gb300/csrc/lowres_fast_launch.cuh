@@ -1,0 +1,109 @@
+// Column-walking low-resolution kernels (see lowres_fast.cuh) and their
+// launchers, templated on the radius.  Each radius is instantiated in its
+// own translation unit (lowres_k1_r*.cu, lowres_k4_r*.cu) so the build
+// compiles them in parallel.
+#pragma once
+
+#include "kernels.h"
+#include "lowres_fast.cuh"
+
+namespace dgf {
+
+template <typename TG, typename TP, int R>
+__global__ void __launch_bounds__(kLowThreads) k1_coef_fast(const TG* __restrict__ G, const TP* __restrict__ P,
+                                                            float2* __restrict__ coef, int h, int w, float eps,
+                                                            int CW, int EY1, const __grid_constant__ TmaPair tma,
+                                                            uint32_t* status) {
+    extern __shared__ __align__(128) float smem[];
+    FastTile t;
+    t.h = h; t.w = w; t.CW = CW; t.EY1 = EY1; t.log2cw = ilog2(CW); t.eps = eps;
+    t.TX = CW - 2 * R; t.TY = EY1 - 2 * R;
+    t.tx0 = blockIdx.x * t.TX; t.ty0 = blockIdx.y * t.TY;
+    const size_t plane = blockIdx.z, hw = (size_t)h * w;
+    coef_tile_fast<TG, TP, R>(G + plane * hw, P + plane * hw, coef + plane * hw, t, smem,
+                              tma.enabled ? &tma.a : nullptr, tma.enabled ? &tma.b : nullptr, (int)plane, status);
+}
+
+template <typename TG, typename TP, typename TD, int R>
+__global__ void __launch_bounds__(kLowThreads) k4_lowres_bwd_fast(const TG* __restrict__ G, const TP* __restrict__ P,
+                                                                  const float2* __restrict__ dcoef,
+                                                                  TP* __restrict__ dP, TD* __restrict__ dG, int h,
+                                                                  int w, float eps, int CW, int EY1) {
+    extern __shared__ __align__(128) float smem[];
+    FastTile t;
+    t.h = h; t.w = w; t.CW = CW; t.EY1 = EY1; t.log2cw = ilog2(CW); t.eps = eps;
+    t.TX = CW - 2 * R; t.TY = EY1 - 2 * R;
+    t.tx0 = blockIdx.x * t.TX; t.ty0 = blockIdx.y * t.TY;
+    const size_t plane = blockIdx.z, hw = (size_t)h * w;
+    lowres_bwd_tile_fast<TG, TP, TD, R>(G + plane * hw, P + plane * hw, dcoef + plane * hw,
+                                        dP ? dP + plane * hw : nullptr, dG ? dG + plane * hw : nullptr, t, smem);
+}
+
+
+template <typename K>
+static inline cudaError_t fast_prep(K kernel, size_t smem) {
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+template <typename TG, typename TP, int R>
+static cudaError_t k1f_go(const void* G, const void* P, float2* coef, int planes, int h, int w, float eps,
+                          const LowCfg& c, const TmaPair& tma, size_t smem, uint32_t* status, cudaStream_t s) {
+    auto kern = k1_coef_fast<TG, TP, R>;
+    cudaError_t e = fast_prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    int gx, gy;
+    low_grid(c, R, h, w, gx, gy);
+    kern<<<dim3(gx, gy, planes), kLowThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P),
+                                                         coef, h, w, eps, c.a, c.b, tma, status);
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_k1_fast(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes,
+                           int h, int w, float eps, const LowCfg& c, const TmaPair& tma, size_t smem,
+                           uint32_t* status, cudaStream_t s) {
+    switch (dt) {
+        case DGF_F32: return k1f_go<float, float, R>(G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
+        case DGF_BF16:
+            return gf32 ? k1f_go<float, __nv_bfloat16, R>(G, P, coef, planes, h, w, eps, c, tma, smem, status, s)
+                        : k1f_go<__nv_bfloat16, __nv_bfloat16, R>(G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
+        case DGF_F16:
+            return gf32 ? k1f_go<float, __half, R>(G, P, coef, planes, h, w, eps, c, tma, smem, status, s)
+                        : k1f_go<__half, __half, R>(G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename TG, typename TP, typename TD, int R>
+static cudaError_t k4f_go(const void* G, const void* P, const float2* dcoef, void* dP, void* dG, int planes,
+                          int h, int w, float eps, const LowCfg& c, cudaStream_t s) {
+    const size_t smem = k4_fast_smem_bytes(R, c.a, c.b);
+    auto kern = k4_lowres_bwd_fast<TG, TP, TD, R>;
+    cudaError_t e = fast_prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    int gx, gy;
+    low_grid(c, R, h, w, gx, gy);
+    kern<<<dim3(gx, gy, planes), kLowThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P),
+                                                         dcoef, static_cast<TP*>(dP), static_cast<TD*>(dG), h, w,
+                                                         eps, c.a, c.b);
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_k4_fast(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP,
+                           void* dG, int planes, int h, int w, float eps, const LowCfg& c, cudaStream_t s) {
+    switch (dt) {
+        case DGF_F32: return k4f_go<float, float, float, R>(G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
+        case DGF_BF16:
+            return gf32 ? k4f_go<float, __nv_bfloat16, float, R>(G, P, dcoef, dP, dG, planes, h, w, eps, c, s)
+                        : k4f_go<__nv_bfloat16, __nv_bfloat16, __nv_bfloat16, R>(G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
+        case DGF_F16:
+            return gf32 ? k4f_go<float, __half, float, R>(G, P, dcoef, dP, dG, planes, h, w, eps, c, s)
+                        : k4f_go<__half, __half, __half, R>(G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dgf

@@ -1,0 +1,7 @@
+// K1 (low-resolution coefficients), column-walking form, radius 4.
+#include "lowres_fast_launch.cuh"
+
+namespace dgf {
+template cudaError_t launch_k1_fast<4>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int, float,
+                                       const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+}  // namespace dgf

@@ -1,0 +1,7 @@
+// K4 (low-resolution backward), column-walking form, radius 1.
+#include "lowres_fast_launch.cuh"
+
+namespace dgf {
+template cudaError_t launch_k4_fast<1>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*, int,
+                                       int, int, float, const LowCfg&, cudaStream_t);
+}  // namespace dgf

@@ -30,6 +30,9 @@ FWD_CASES = [
     ("photo", 1, 1, 48, 40, 192, 160, 8, 1e-3),     # r = 8
     ("photo", 1, 1, 20, 24, 80, 96, 16, 1e-2),      # r = 16 > image half-size
     ("photo", 1, 1, 30, 36, 120, 144, 0, 1e-2),     # r = 0
+    ("photo", 1, 2, 50, 70, 200, 280, 3, 1e-3),     # r = 3 (generic-radius tile kernels)
+    ("photo", 2, 1, 36, 300, 144, 1200, 4, 1e-3),   # r = 4, wide: several column-walking tiles
+    ("photo", 1, 1, 70, 40, 560, 320, 8, 1e-4),     # r = 8 over several tiles, eps = 1e-4
     ("blobs", 1, 3, 64, 72, 256, 288, 1, 1e-4),     # configuration-2 recipe, eps = 1e-4
     ("ragged", 1, 1, 1, 1, 7, 5, 1, 1e-3),          # single low-res pixel
     ("ragged", 1, 1, 3, 1, 9, 4, 1, 1e-3),          # one column
