@@ -177,6 +177,21 @@ int dgf_device_status(void);
  * identical either way; this exists for testing the two paths. */
 void dgf_set_tma(int on);
 
+/*
+ * Tile-shape autotuner.  When enabled (here, or DGF_AUTOTUNE=1 in the
+ * environment), the first call for a new key (kernel, storage type, radius
+ * or factor, vector width) times each candidate tile shape on that call's
+ * own buffers and keeps the fastest; that call synchronises its stream and
+ * must not be under stream capture (tuning is skipped while capturing).
+ * Chosen shapes are used by every later call with the same key, tuned or
+ * not, and are saved to the file DGF_TUNE_CACHE names (if any); unreadable
+ * lines in that file are ignored.  Results never depend on the shape beyond
+ * FP32 rounding order.
+ */
+void dgf_autotune(int on);
+int dgf_autotune_entries(void);
+void dgf_autotune_reset(void);
+
 /* Releases cached graphs and tuning state (idempotent). */
 void dgf_shutdown(void);
 

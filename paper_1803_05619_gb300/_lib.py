@@ -57,6 +57,9 @@ _SIGS = {
     "dgf_device_status": (_I, []),
     "dgf_set_tma": (None, [_I]),
     "dgf_shutdown": (None, []),
+    "dgf_autotune": (None, [_I]),
+    "dgf_autotune_entries": (_I, []),
+    "dgf_autotune_reset": (None, []),
 }
 
 
@@ -142,3 +145,15 @@ def dgf_set_tma(on: bool) -> None:
 
 def dgf_shutdown() -> None:
     lib().dgf_shutdown()
+
+
+def dgf_autotune(on: bool) -> None:
+    lib().dgf_autotune(1 if on else 0)
+
+
+def dgf_autotune_entries() -> int:
+    return lib().dgf_autotune_entries()
+
+
+def dgf_autotune_reset() -> None:
+    lib().dgf_autotune_reset()

@@ -19,6 +19,7 @@
 #include "batch.cuh"
 #include "kernels.h"
 #include "tma.cuh"
+#include "tune.h"
 
 namespace dgf {
 
@@ -231,15 +232,45 @@ static bool pick_lowres_tiles(int r, Plan& p) {
     return ok1 && ok4;
 }
 
-static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r,
+static int default_k3_lth(int F) { return F >= 8 ? 4 : (F >= 4 ? 8 : 16); }
+
+// Shapes from the autotuner's table override the defaults (whether or not
+// tuning is enabled now), so every call with the same key uses one shape.
+static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool gf32,
                       std::initializer_list<const void*> hires_ptrs) {
     Plan p;
     p.F = integer_factor(h_l, w_l, h, w);
     p.vec = pick_vec(dt, w, hires_ptrs);
     pick_lowres_tiles(r, p);
     p.k3_fast = p.F > 0 && k3_fast_ok(p.vec, p.F);
-    p.k3_lth = p.F >= 8 ? 4 : (p.F >= 4 ? 8 : 16);
+    p.k3_lth = default_k3_lth(p.F);
+    int a, b;
+    if (low_fast_radius(r)) {
+        if (tune_lookup(TuneKey{1, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b) &&
+            k1_fast_smem_bytes(r, a, b, 0) <= smem_limit())
+            p.k1 = LowCfg{1, a, b};
+        if (tune_lookup(TuneKey{4, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b) && k4_fast_smem_bytes(r, a, b) <= smem_limit())
+            p.k4 = LowCfg{1, a, b};
+    }
+    if (tune_lookup(TuneKey{2, (int)dt, 0, p.F, p.vec, 0}, a, b)) p.k2_th = a;
+    if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b) &&
+        k3_smem_bytes(p.vec, p.F, a) <= smem_limit())
+        p.k3_lth = a;
     return p;
+}
+
+static std::vector<LowCfg> low_candidates(int r, bool k4) {
+    std::vector<LowCfg> v;
+    if (!low_fast_radius(r)) return v;
+    static const int cws[] = {64, 128, 256};
+    static const int eys[] = {16, 32, 64};
+    for (int cw : cws)
+        for (int ey : eys) {
+            if (cw <= 2 * r + 1 || ey <= 2 * r + 1) continue;
+            const size_t sm = k4 ? k4_fast_smem_bytes(r, cw, ey) : k1_fast_smem_bytes(r, cw, ey, 0);
+            if (sm <= smem_limit()) v.push_back(LowCfg{1, cw, ey});
+        }
+    return v;
 }
 
 // --------------------------------------------------------------- TMA maps
@@ -380,6 +411,104 @@ static dgf_status check_ws(void* ws, size_t ws_bytes, size_t need) {
     return DGF_OK;
 }
 
+// ---------------------------------------------------------------- autotune
+// Each helper times its candidates on the call's own buffers (the real
+// launch that follows overwrites every output) and records the fastest.
+static void tune_k1(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes, int h_l,
+                    int w_l, int r, float eps, cudaStream_t s, Plan& p) {
+    TuneKey key{1, (int)dt, r, 0, 0, gf32 ? 1 : 0};
+    int a, b;
+    if (tune_lookup(key, a, b)) return;
+    float best = 1e30f;
+    LowCfg bc = p.k1;
+    for (const LowCfg& c : low_candidates(r, false)) {
+        size_t landing = 0;
+        TmaPair tma = make_tma_pair(G, gf32 ? DGF_F32 : dt, P, dt, planes, h_l, w_l, r, c, landing);
+        const size_t smem = k1_cfg_smem(c, r, tma.enabled ? landing : 0);
+        const float ms = time_launch(s, [&] {
+            return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, c, tma, smem, status_ptr(), s);
+        }, 3);
+        if (ms > 0.f && ms < best) {
+            best = ms;
+            bc = c;
+        }
+    }
+    if (best < 1e30f) {
+        tune_store(key, bc.a, bc.b);
+        p.k1 = bc;
+    }
+}
+
+static void tune_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP, void* dG,
+                    int planes, int h_l, int w_l, int r, float eps, cudaStream_t s, Plan& p) {
+    TuneKey key{4, (int)dt, r, 0, 0, gf32 ? 1 : 0};
+    int a, b;
+    if (tune_lookup(key, a, b)) return;
+    float best = 1e30f;
+    LowCfg bc = p.k4;
+    for (const LowCfg& c : low_candidates(r, true)) {
+        const float ms = time_launch(s, [&] {
+            return launch_k4(dt, gf32, G, P, dcoef, dP, dG, planes, h_l, w_l, r, eps, c, s);
+        }, 3);
+        if (ms > 0.f && ms < best) {
+            best = ms;
+            bc = c;
+        }
+    }
+    if (best < 1e30f) {
+        tune_store(key, bc.a, bc.b);
+        p.k4 = bc;
+    }
+}
+
+static void tune_k2(dgf_dtype dt, const float2* coef, const void* in, void* out, int planes, int h_l, int w_l,
+                    int h, int w, cudaStream_t s, Plan& p) {
+    TuneKey key{2, (int)dt, 0, p.F, p.vec, 0};
+    int a, b;
+    if (tune_lookup(key, a, b)) return;
+    float best = 1e30f;
+    int bt = p.k2_th;
+    for (int th : {8, 16, 32, 64}) {
+        if (k2_smem_bytes(p.vec, p.F, h_l, h, w_l, w, th) > smem_limit()) continue;
+        const float ms = time_launch(s, [&] {
+            return launch_k2(dt, 0, coef, in, out, planes, h_l, w_l, h, w, p.vec, p.F, th, s);
+        }, 3);
+        if (ms > 0.f && ms < best) {
+            best = ms;
+            bt = th;
+        }
+    }
+    if (best < 1e30f) {
+        tune_store(key, bt, 0);
+        p.k2_th = bt;
+    }
+}
+
+static void tune_k3(dgf_dtype dt, const float2* coef, const void* R, const void* G, void* dG, float2* dcoef,
+                    int planes, int h_l, int w_l, int h, int w, cudaStream_t s, Plan& p) {
+    if (!p.k3_fast) return;
+    TuneKey key{3, (int)dt, 0, p.F, p.vec, 0};
+    int a, b;
+    if (tune_lookup(key, a, b)) return;
+    float best = 1e30f;
+    int bl = p.k3_lth;
+    const int d = default_k3_lth(p.F);
+    for (int lth : {d / 2, d, 2 * d}) {
+        if (lth < 1 || k3_smem_bytes(p.vec, p.F, lth) > smem_limit()) continue;
+        const float ms = time_launch(s, [&] {
+            return launch_k3(dt, coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, lth, s);
+        }, 3);
+        if (ms > 0.f && ms < best) {
+            best = ms;
+            bl = lth;
+        }
+    }
+    if (best < 1e30f) {
+        tune_store(key, bl, 0);
+        p.k3_lth = bl;
+    }
+}
+
 static cudaError_t run_k1(Launcher& L, dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef,
                           int planes, int h_l, int w_l, int r, float eps, const Plan& p, cudaStream_t s) {
     size_t landing = 0;
@@ -437,7 +566,7 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
         b.w = im.w;
         b.r = im.r;
         b.eps = im.eps;
-        Plan p = make_plan(dt, im.h_l, im.w_l, im.h, im.w, im.r, {im.I_h, im.O_h});
+        Plan p = make_plan(dt, im.h_l, im.w_l, im.h, im.w, im.r, false, {im.I_h, im.O_h});
         // the persistent K2 has fast paths for factors 4 and 8 only
         b.F = (p.F == 4 || p.F == 8) ? p.F : 0;
         b.vec = p.vec;
@@ -489,12 +618,15 @@ dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* 
     char* ws = static_cast<char*>(workspace);
     float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
     const int planes = N * C;
-    Plan p = make_plan(dt, h_l, w_l, h, w, r, {I_h, O_h});
+    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr, {I_h, O_h});
     Launcher L(s);
     cudaError_t e;
+    const bool tuning = tune_enabled() && !stream_capturing(s);
     if (g == nullptr) {
+        if (tuning) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
         e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
         if (e != cudaSuccess) return cuda_fail(e, "k1");
+        if (tuning) tune_k2(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, s, p);
         e = L.run("k2_hires_apply", [&] {
             return launch_k2(dt, 0, coef, I_h, O_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
         });
@@ -541,17 +673,20 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
     float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
     float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
     const int planes = N * C;
-    Plan p = make_plan(dt, h_l, w_l, h, w, r, {dO_h, I_h, dI_h});
+    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr, {dO_h, I_h, dI_h});
     Launcher L(s);
     cudaError_t e;
     if (g == nullptr) {
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
+        const bool tuning = tune_enabled() && !stream_capturing(s);
         // coefficients are recomputed, not saved from the forward call
         if (dI_h != nullptr) {
+            if (tuning) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
             e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
             if (e != cudaSuccess) return cuda_fail(e, "k1");
         }
         if (p.k3_fast) {
+            if (tuning) tune_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, s, p);
             e = L.run("k3_hires_bwd", [&] {
                 return launch_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, p.k3_lth, s);
             });
@@ -569,6 +704,7 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
             if (e != cudaSuccess) return cuda_fail(e, "k3 general");
         }
         if (dp_l != nullptr || dI_l != nullptr) {
+            if (tuning) tune_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, s, p);
             e = L.run("k4_lowres_bwd", [&] {
                 return launch_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4, s);
             });
@@ -721,6 +857,12 @@ extern "C" int dgf_device_status(void) {
 }
 
 extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
+
+extern "C" void dgf_autotune(int on) { tune_set_enabled(on != 0); }
+
+extern "C" int dgf_autotune_entries(void) { return tune_count(); }
+
+extern "C" void dgf_autotune_reset(void) { tune_clear(); }
 
 extern "C" void dgf_shutdown(void) {
     std::lock_guard<std::mutex> lk(g_batch_mu);

@@ -24,6 +24,15 @@ namespace dgf {
 
 constexpr int kLowThreads = 256;
 
+// Per window m the backward needs four window sums over the windows that
+// contain each pixel i (all divided by N_m; G' = G - K_G, P' = P - K_P,
+// mu' = mu - K_G, nu' = nu - K_P for the tile shift K):
+//   q0 = gamma, q1 = beta, q2 = db - gamma mu', q3 = gamma nu' + 2 beta mu' + db A,
+// and then dP_i = G'_i S0 + S2,  dG_i = P'_i S0 + 2 G'_i S1 - S3,
+// the regrouping of sum_m [gamma (G_i - mu) + db] / N_m and
+// sum_m [gamma (P_i - nu) + 2 beta (G_i - mu) - db A] / N_m.
+constexpr int kNQ = 4;
+
 __host__ __device__ inline int ilog2(int v) {
     int l = 0;
     while ((1 << l) < v) ++l;
@@ -405,7 +414,7 @@ __device__ __forceinline__ void bwd_stage_and_shift(const TG* __restrict__ G, co
 // db = f_mu^T(d bbar), gamma = (dA - db mu)/(var + eps), beta = -gamma A,
 // and the seven quantities whose window sums give dP and dG; pass B sums
 // them over the windows containing each output pixel.
-// smem: sG, sP, sDA, sDB (E2), sQ (7 x E1), red (3 x warps).
+// smem: sG, sP, sDA, sDB (E2), sQ (4 x E1), red (3 x warps).
 template <typename TG, typename TP, typename TD, int R, bool INT>
 __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restrict__ P,
                                      const float2* __restrict__ dcoef, TP* __restrict__ dP, TD* __restrict__ dG,
@@ -417,7 +426,7 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
     float* sDA = sP + EX2 * EY2;
     float* sDB = sDA + EX2 * EY2;
     float* sQ = sDB + EX2 * EY2;
-    float* red = sQ + 7 * n1;
+    float* red = sQ + kNQ * n1;
     float KG, KP;
     bwd_stage_and_shift<TG, TP, R, INT>(G, P, dcoef, t, sG, sP, sDA, sDB, red, KG, KP);
     const int c = threadIdx.x & (t.CW - 1), rg = threadIdx.x >> t.log2cw;
@@ -473,7 +482,7 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         hdb[slot] = b;
                     }
                     const int gy = t.ty0 - R + e1;
-                    float q[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    float q[kNQ] = {0.f, 0.f, 0.f, 0.f};
                     if (INT || (colin && gy >= 0 && gy < t.h)) {
                         const float ny = INT ? (float)W : (float)seg_count(gy, t.h, R);
                         const float iny = INT ? 1.f / (float)W : __frcp_rn(ny);
@@ -494,15 +503,12 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         const float beta = -gamma * A;
                         const float mus = mu - KG, nus = nu - KP;
                         q[0] = gamma * inn;
-                        q[1] = gamma * mus * inn;
-                        q[2] = gamma * nus * inn;
-                        q[3] = beta * inn;
-                        q[4] = beta * mus * inn;
-                        q[5] = db * inn;
-                        q[6] = db * A * inn;
+                        q[1] = beta * inn;
+                        q[2] = fmaf(-gamma, mus, db) * inn;
+                        q[3] = fmaf(gamma, nus, fmaf(2.f * beta, mus, db * A)) * inn;
                     }
 #pragma unroll
-                    for (int k = 0; k < 7; ++k) sQ[k * n1 + e1 * EX1 + c] = q[k];
+                    for (int k = 0; k < kNQ; ++k) sQ[k * n1 + e1 * EX1 + c] = q[k];
                 }
             }
         }
@@ -512,11 +518,11 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
     if (c < t.TX) {
         const int gx = t.tx0 + c;
         const int ya = (rg * t.TY) / ngroups, yb = ((rg + 1) * t.TY) / ngroups;
-        float hq[7][W];
+        float hq[kNQ][W];
 #pragma unroll
         for (int s = 0; s < 2 * R; ++s) {
 #pragma unroll
-            for (int m = 0; m < 7; ++m) {
+            for (int m = 0; m < kNQ; ++m) {
                 const float* pq = sQ + m * n1 + (ya + s) * EX1 + c;
                 float a = 0.f;
 #pragma unroll
@@ -531,7 +537,7 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                 if (y < yb) {
                     const int slot = (s + 2 * R) % W;
 #pragma unroll
-                    for (int m = 0; m < 7; ++m) {
+                    for (int m = 0; m < kNQ; ++m) {
                         const float* pq = sQ + m * n1 + (y + 2 * R) * EX1 + c;
                         float a = 0.f;
 #pragma unroll
@@ -540,9 +546,9 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                     }
                     const int gy = t.ty0 + y;
                     if (INT || (gx < t.w && gy < t.h)) {
-                        float S[7];
+                        float S[kNQ];
 #pragma unroll
-                        for (int m = 0; m < 7; ++m) {
+                        for (int m = 0; m < kNQ; ++m) {
                             float a = 0.f;
 #pragma unroll
                             for (int k = 0; k < W; ++k) a += hq[m][k];
@@ -551,9 +557,8 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         const int o = (y + 2 * R) * EX2 + c + 2 * R;
                         const float g = sG[o] - KG, p = sP[o] - KP;
                         const size_t go = (size_t)gy * t.w + gx;
-                        if (dP != nullptr) dP[go] = from_f32<TP>(fmaf(g, S[0], S[5] - S[1]));
-                        if (dG != nullptr)
-                            dG[go] = from_f32<TD>(fmaf(p, S[0], -S[2]) + 2.f * fmaf(g, S[3], -S[4]) - S[6]);
+                        if (dP != nullptr) dP[go] = from_f32<TP>(fmaf(g, S[0], S[2]));
+                        if (dG != nullptr) dG[go] = from_f32<TD>(fmaf(p, S[0], fmaf(2.f * g, S[1], -S[3])));
                     }
                 }
             }
@@ -711,8 +716,8 @@ __device__ void lowres_bwd_tile_staged(const TG* __restrict__ G, const TP* __res
     float* sDA = sP + EX2 * EY2;
     float* sDB = sDA + EX2 * EY2;
     float* sQ = sDB + EX2 * EY2;
-    float* red = sQ + 7 * n1;
-    float* H = red + 3 * (kLowThreads / 32) + 8;  // max(6 x EY2 x CW, 7 x EY1 x CW)
+    float* red = sQ + kNQ * n1;
+    float* H = red + 3 * (kLowThreads / 32) + 8;  // max(6 x EY2 x CW, kNQ x EY1 x CW)
     float KG, KP;
     bwd_stage_and_shift<TG, TP, R>(G, P, dcoef, t, sG, sP, sDA, sDB, red, KG, KP);
     const int c = threadIdx.x & (CW - 1), rg = threadIdx.x >> t.log2cw;
@@ -740,7 +745,7 @@ __device__ void lowres_bwd_tile_staged(const TG* __restrict__ G, const TP* __res
     __syncthreads();
     for (int e1 = rg; e1 < t.EY1; e1 += ngroups) {
         const int gy = t.ty0 - R + e1;
-        float q[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float q[kNQ] = {0.f, 0.f, 0.f, 0.f};
         if (colin && gy >= 0 && gy < t.h) {
             const float ny = (float)seg_count(gy, t.h, R);
             float mu, nu, var, cov;
@@ -760,21 +765,18 @@ __device__ void lowres_bwd_tile_staged(const TG* __restrict__ G, const TP* __res
             const float inn = __frcp_rn(nx * ny);
             const float mus = mu - KG, nus = nu - KP;
             q[0] = gamma * inn;
-            q[1] = gamma * mus * inn;
-            q[2] = gamma * nus * inn;
-            q[3] = beta * inn;
-            q[4] = beta * mus * inn;
-            q[5] = db * inn;
-            q[6] = db * A * inn;
+            q[1] = beta * inn;
+            q[2] = fmaf(-gamma, mus, db) * inn;
+            q[3] = fmaf(gamma, nus, fmaf(2.f * beta, mus, db * A)) * inn;
         }
 #pragma unroll
-        for (int k = 0; k < 7; ++k) sQ[k * n1 + e1 * CW + c] = q[k];
+        for (int k = 0; k < kNQ; ++k) sQ[k * n1 + e1 * CW + c] = q[k];
     }
     __syncthreads();
     if (c < t.TX) {
         for (int e1 = rg; e1 < t.EY1; e1 += ngroups) {
 #pragma unroll
-            for (int m = 0; m < 7; ++m) {
+            for (int m = 0; m < kNQ; ++m) {
                 float a = 0.f;
 #pragma unroll
                 for (int k = 0; k < W; ++k) a += sQ[m * n1 + e1 * CW + c + k];
@@ -788,9 +790,9 @@ __device__ void lowres_bwd_tile_staged(const TG* __restrict__ G, const TP* __res
         for (int y = rg; y < t.TY; y += ngroups) {
             const int gy = t.ty0 + y;
             if (gx >= t.w || gy >= t.h) continue;
-            float S[7];
+            float S[kNQ];
 #pragma unroll
-            for (int m = 0; m < 7; ++m) {
+            for (int m = 0; m < kNQ; ++m) {
                 float a = 0.f;
 #pragma unroll
                 for (int k = 0; k < W; ++k) a += H[m * n1 + (y + k) * CW + c];
@@ -799,8 +801,8 @@ __device__ void lowres_bwd_tile_staged(const TG* __restrict__ G, const TP* __res
             const int o = (y + 2 * R) * EX2 + c + 2 * R;
             const float g = sG[o] - KG, p = sP[o] - KP;
             const size_t go = (size_t)gy * t.w + gx;
-            if (dP != nullptr) dP[go] = from_f32<TP>(fmaf(g, S[0], S[5] - S[1]));
-            if (dG != nullptr) dG[go] = from_f32<TD>(fmaf(p, S[0], -S[2]) + 2.f * fmaf(g, S[3], -S[4]) - S[6]);
+            if (dP != nullptr) dP[go] = from_f32<TP>(fmaf(g, S[0], S[2]));
+            if (dG != nullptr) dG[go] = from_f32<TD>(fmaf(p, S[0], fmaf(2.f * g, S[1], -S[3])));
         }
     }
     __syncthreads();

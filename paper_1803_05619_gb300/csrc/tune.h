@@ -1,0 +1,28 @@
+// Tile-shape autotuner (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <functional>
+
+namespace dgf {
+
+// kind: 1 = K1 low-res coefficients, 2 = K2 high-res apply, 3 = K3 high-res
+// backward, 4 = K4 low-res backward.  The value (a, b) is the kernel's
+// shape: K1/K4 (fast, a, b) packed as a = CW (or TY) and b = EY1 (or TX),
+// with b negative never stored; K2: a = rows per tile; K3: a = low-res rows.
+struct TuneKey {
+    int kind, dt, r, F, vec, gf32;
+};
+
+bool tune_enabled();
+void tune_set_enabled(bool on);
+bool tune_lookup(const TuneKey& k, int& a, int& b);
+void tune_store(const TuneKey& k, int a, int b);
+void tune_clear();
+int tune_count();
+bool stream_capturing(cudaStream_t s);
+// Average milliseconds of `reps` launches after one warm-up; -1 on error.
+float time_launch(cudaStream_t s, const std::function<cudaError_t()>& fn, int reps);
+
+}  // namespace dgf
