@@ -192,6 +192,32 @@ void dgf_autotune(int on);
 int dgf_autotune_entries(void);
 void dgf_autotune_reset(void);
 
+/*
+ * Forward pass that allocates nothing and takes no workspace.  The paper
+ * has no counterpart; this exists for callers that cannot allocate device
+ * memory when they call the layer (cudaMalloc may synchronise the device or
+ * fail under memory pressure, so real-time loops and host frameworks that
+ * own all device memory forbid it).  Same computation, arguments and
+ * results as dgf_forward with F = identity (g = NULL), without the
+ * workspace arguments.
+ * Scratch: a fixed device array inside the library, dgf_noalloc_max_pairs()
+ * low-resolution (Abar, bbar) pairs (8 MiB), held by every device that
+ * loads the library until the process exits.  N*C*h_l*w_l above that
+ * maximum returns DGF_ERR_UNSUPPORTED and enqueues nothing.
+ * Set-up: the first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture on the device.
+ * Sharing: every call uses the same array and leaves its last contents
+ * there; each call overwrites all of it that it reads, so nothing needs
+ * clearing, but calls whose kernels overlap on the device (different
+ * streams, or different host threads) race on the array and must be
+ * serialised by the caller.
+ */
+dgf_status dgf_forward_noalloc(const void* p_l, const void* I_l, const void* I_h, void* O_h,
+                               int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
+                               dgf_dtype dt, dgf_stream_t stream);
+size_t dgf_noalloc_max_pairs(void);
+
 /* Releases cached graphs and tuning state (idempotent). */
 void dgf_shutdown(void);
 

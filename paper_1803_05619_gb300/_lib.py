@@ -60,6 +60,8 @@ _SIGS = {
     "dgf_autotune": (None, [_I]),
     "dgf_autotune_entries": (_I, []),
     "dgf_autotune_reset": (None, []),
+    "dgf_forward_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _F, _I, _P]),
+    "dgf_noalloc_max_pairs": (_S, []),
 }
 
 
@@ -157,3 +159,11 @@ def dgf_autotune_entries() -> int:
 
 def dgf_autotune_reset() -> None:
     lib().dgf_autotune_reset()
+
+
+def dgf_forward_noalloc(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, stream) -> int:
+    return lib().dgf_forward_noalloc(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, stream)
+
+
+def dgf_noalloc_max_pairs() -> int:
+    return lib().dgf_noalloc_max_pairs()

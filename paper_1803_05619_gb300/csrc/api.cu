@@ -874,3 +874,73 @@ extern "C" void dgf_shutdown(void) {
 }
 
 }  // extern "C"
+
+// =========================================== forward pass without allocation
+// Some callers cannot allocate device memory at call time: cudaMalloc may
+// synchronise the device and may fail under memory pressure, so latency-
+// critical loops and host frameworks that own every byte of device memory
+// forbid it, and such callers cannot provide the workspace dgf_forward
+// needs.  dgf_forward_noalloc keeps its FP32 (Abar, bbar) scratch in a
+// fixed device array of this translation unit instead; the caller still
+// passes inputs and outputs.
+namespace dgf {
+
+constexpr size_t kNoAllocPairs = size_t(1) << 20;  // (Abar, bbar) pairs: 8 MiB per device
+static __device__ __align__(256) float2 g_noalloc_coef[kNoAllocPairs];
+static std::mutex g_noalloc_mu;
+static float2* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch on the current device; resolved once per
+// device (host code cannot pass the array's name to a kernel: on the host
+// it only stands in for the symbol).
+static dgf_status noalloc_scratch(float2** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(DGF_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_coef);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[dev] = static_cast<float2*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return DGF_OK;
+}
+
+}  // namespace dgf
+
+extern "C" size_t dgf_noalloc_max_pairs(void) { return kNoAllocPairs; }
+
+extern "C" dgf_status dgf_forward_noalloc(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N,
+                                          int C, int h_l, int w_l, int h, int w, int r, float eps, dgf_dtype dt,
+                                          dgf_stream_t stream) {
+    dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
+    if (st != DGF_OK) return st;
+    if (N == 0) return DGF_OK;
+    if (p_l == nullptr || I_l == nullptr || I_h == nullptr || O_h == nullptr)
+        return fail(DGF_ERR_INVALID, "NULL input or output pointer");
+    const size_t pairs = (size_t)N * C * h_l * w_l;
+    if (pairs > kNoAllocPairs)
+        return fail(DGF_ERR_UNSUPPORTED,
+                    "N*C*h_l*w_l = %zu exceeds the fixed scratch of %zu low-resolution pixels (8 MiB); "
+                    "use dgf_forward with a workspace", pairs, kNoAllocPairs);
+    float2* coef = nullptr;
+    if ((st = noalloc_scratch(&coef)) != DGF_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int planes = N * C;
+    const Plan p = make_plan(dt, h_l, w_l, h, w, r, false, {I_h, O_h});
+    // K1 overwrites every scratch entry the call reads, so stale contents
+    // from an earlier call never reach the output.
+    size_t landing = 0;
+    TmaPair tma = make_tma_pair(I_l, dt, p_l, dt, planes, h_l, w_l, r, p.k1, landing);
+    const size_t smem = k1_cfg_smem(p.k1, r, tma.enabled ? landing : 0);
+    g_launches.fetch_add(1);
+    cudaError_t e = launch_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, status_ptr(), s);
+    if (e != cudaSuccess) return cuda_fail(e, "k1");
+    g_launches.fetch_add(1);
+    e = launch_k2(dt, 0, coef, I_h, O_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k2");
+    return DGF_OK;
+}
