@@ -146,6 +146,7 @@ def barrier(ws):
 
 
 def max_over_ranks(v, ws, device):
+    """Slowest rank's time (the job's time); `device` is where the collective runs."""
     if ws == 1:
         return v
     import torch
@@ -153,6 +154,19 @@ def max_over_ranks(v, ws, device):
     t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard(n_units, rank, world):
+    """Contiguous share of n_units independent images for one rank (weak scaling
+    gives every rank the full per-GPU batch; this split serves a fixed total)."""
+    base, extra = divmod(n_units, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def job_value(pixels_per_rank, world, ms_max):
+    """Whole-job Mpix/s: every rank's pixels over the slowest rank's time."""
+    return world * pixels_per_rank / (ms_max * 1e-3) / 1e6
 
 
 class ClockSampler:
@@ -443,7 +457,7 @@ def main():
     with ClockSampler(local) as clk:
         ms = time_loop(step, args.steps, args.warmup, ws, device, clock=clk)
     launches = per_step * args.steps
-    value = ws * pix / (ms * 1e-3) / 1e6
+    value = job_value(pix, ws, ms)
     fwd_ms = time_loop(step.forward, max(10, args.steps // 2), args.warmup, ws, device)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
@@ -471,6 +485,8 @@ def main():
                        "ms_per_step": round(e_ms, 4)}
         if not args.no_extra:
             line["bf16_4k"] = bench_bf16_4k(args, device)
+            line["batched_64_uneven"] = bench_batched_64(args, device)
+            line["guided_train_8x2048"] = bench_guided(args, device)
         if not args.no_oracle:
             reps = 15
             cv, csec = cpu_oracle(spec, reps=reps)
@@ -513,6 +529,67 @@ def bench_bf16_4k(args, device):
             "ms_fwd_bwd": round(ms, 5), "fwd_bwd_frac_of_nominal_8TBs": round(
                 fb_bytes / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4),
             "fwd_bwd_algorithmic_bytes": fb_bytes, "roofline": rl}
+
+
+def bench_batched_64(args, device):
+    """64 uneven BF16 images (long side 512..4096, factor 4 or 8, r in {1,2,4})
+    in one graph-replayed persistent launch per stage: forward Mpix/s."""
+    import torch
+
+    import synth
+    from paper_1803_05619_gb300.layer import gf_forward_batched
+    specs = synth.mixed_sizes(seed=0, n=64)
+    images, outs = [], []
+    for i, s in enumerate(specs):
+        d = synth.photo_like(1000 + i, 1, 3, s.h_l, s.w_l, s.f)
+        st = {k: v.to(torch.bfloat16)[0].to(device) for k, v in d.items()}
+        images.append({"p_l": st["p_l"], "I_l": st["I_l"], "I_h": st["I_h"], "r": s.r, "eps": 1e-3})
+        outs.append(torch.empty_like(st["I_h"]))
+    pix = sum(s.h * s.w for s in specs)
+    steps = max(10, min(args.steps // 10, 200))
+    ms = time_loop(lambda: gf_forward_batched(images, out=outs), steps, max(3, args.warmup // 4), 1, device)
+    byts = sum(3 * 2 * (2 * s.h * s.w + 2 * s.h_l * s.w_l) for s in specs)
+    peak, src = peaks()
+    return {"workload": "64 images, long side U[512,4096], aspect U[0.5,2], f in {4,8}, r in {1,2,4}, BF16",
+            "mpix": round(pix / 1e6, 1), "fwd_mpix_s": round(pix / (ms * 1e-3) / 1e6, 1),
+            "ms_fwd": round(ms, 4), "fwd_algorithmic_bytes": byts,
+            "fwd_frac_of_measured_hbm": round(byts / (ms * 1e-3) / 1e9 / peak, 4),
+            "fwd_frac_of_nominal_8TBs": round(byts / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4)}
+
+
+def bench_guided(args, device):
+    """Training step with the guidance transform: BF16 8 x 3 x 256^2 -> 2048^2,
+    r = 8, eps = 1e-4, forward + backward including the weight gradients."""
+    import torch
+
+    import synth
+    from paper_1803_05619_gb300 import _lib as L
+    from paper_1803_05619_gb300.layer import gf_backward, gf_forward
+    d = synth.photo_like(21, 8, 3, 256, 256, 8)
+    g = {k: v.to(torch.bfloat16).to(device) for k, v in d.items()}
+    w = {k: v.float().to(device) for k, v in synth.guide_weights(22).items()}
+    R = synth.upstream_grad(23, g["I_h"].shape).to(torch.bfloat16).to(device)
+
+    def step():
+        gf_forward(g["p_l"], None, g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2)
+        gf_backward(R, g["p_l"], None, g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2)
+
+    steps = max(10, min(args.steps // 10, 100))
+    ms = time_loop(step, steps, max(3, args.warmup // 4), 1, device)
+    L.dgf_profile_reset()
+    L.dgf_profile_enable(True)
+    try:
+        for _ in range(5):
+            step()
+        torch.cuda.synchronize()
+        prof = L.dgf_profile_read()
+    finally:
+        L.dgf_profile_enable(False)
+    pix = 8 * 2048 * 2048
+    return {"workload": "guided_train_8x3x2048 (BF16, r=8, eps=1e-4, F: 3->15->3)",
+            "fwd_bwd_mpix_s": round(pix / (ms * 1e-3) / 1e6, 1), "ms_fwd_bwd": round(ms, 4),
+            "bound": "alu (FP32 FMA of the 1x1 convolutions)",
+            "kernels_avg_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in prof.items()}}
 
 
 if __name__ == "__main__":

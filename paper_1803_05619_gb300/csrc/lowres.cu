@@ -241,7 +241,7 @@ size_t k1_fast_smem_bytes(int r, int CW, int EY1, size_t tma_landing) {
 
 size_t k4_fast_smem_bytes(int r, int CW, int EY1) {
     const size_t e2 = (size_t)(CW + 2 * r) * (EY1 + 2 * r), e1 = (size_t)CW * EY1;
-    size_t floats = 4 * e2 + kNQ * e1 + 3 * (kLowThreads / 32);
+    size_t floats = 4 * e2 + (r <= 2 ? kNQD : kNQ) * e1 + 3 * (kLowThreads / 32);
     if (r > 2) floats += 8 + std::max((size_t)6 * (EY1 + 2 * r) * CW, (size_t)kNQ * e1);
     return floats * sizeof(float);
 }

@@ -33,6 +33,12 @@ constexpr int kLowThreads = 256;
 // sum_m [gamma (P_i - nu) + 2 beta (G_i - mu) - db A] / N_m.
 constexpr int kNQ = 4;
 
+// The ring form (r <= 2) keeps the centred differences exact instead: per
+// window it stores gamma~, beta~, mu, nu, db~ and (db A)~ (six planes) and
+// forms gamma~ (G_i - mu_m) etc. per pixel, so large gamma in flat regions
+// cannot cancel catastrophically.
+constexpr int kNQD = 6;
+
 __host__ __device__ inline int ilog2(int v) {
     int l = 0;
     while ((1 << l) < v) ++l;
@@ -426,7 +432,7 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
     float* sDA = sP + EX2 * EY2;
     float* sDB = sDA + EX2 * EY2;
     float* sQ = sDB + EX2 * EY2;
-    float* red = sQ + kNQ * n1;
+    float* red = sQ + kNQD * n1;
     float KG, KP;
     bwd_stage_and_shift<TG, TP, R, INT>(G, P, dcoef, t, sG, sP, sDA, sDB, red, KG, KP);
     const int c = threadIdx.x & (t.CW - 1), rg = threadIdx.x >> t.log2cw;
@@ -482,7 +488,7 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         hdb[slot] = b;
                     }
                     const int gy = t.ty0 - R + e1;
-                    float q[kNQ] = {0.f, 0.f, 0.f, 0.f};
+                    float q[kNQD] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     if (INT || (colin && gy >= 0 && gy < t.h)) {
                         const float ny = INT ? (float)W : (float)seg_count(gy, t.h, R);
                         const float iny = INT ? 1.f / (float)W : __frcp_rn(ny);
@@ -501,64 +507,73 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         const float alpha = fmaf(-db, mu, dA);
                         const float gamma = alpha * ive;
                         const float beta = -gamma * A;
-                        const float mus = mu - KG, nus = nu - KP;
                         q[0] = gamma * inn;
                         q[1] = beta * inn;
-                        q[2] = fmaf(-gamma, mus, db) * inn;
-                        q[3] = fmaf(gamma, nus, fmaf(2.f * beta, mus, db * A)) * inn;
+                        q[2] = mu;
+                        q[3] = nu;
+                        q[4] = db * inn;
+                        q[5] = db * A * inn;
                     }
 #pragma unroll
-                    for (int k = 0; k < kNQ; ++k) sQ[k * n1 + e1 * EX1 + c] = q[k];
+                    for (int k = 0; k < kNQD; ++k) sQ[k * n1 + e1 * EX1 + c] = q[k];
                 }
             }
         }
     }
     __syncthreads();
-    // ---- pass B
+    // ---- pass B: exactly centred sums over the windows m containing pixel i,
+    //   dP_i = sum gamma~_m (G_i - mu_m) + sum db~_m,
+    //   dG_i = sum [gamma~_m (P_i - nu_m) + 2 beta~_m (G_i - mu_m)] - sum (db A)~_m,
+    // (~ = divided by N_m).  The window data of the last 2R + 1 rows sit in a
+    // register ring (W rows x W columns); only the two plain sums are separable.
     if (c < t.TX) {
         const int gx = t.tx0 + c;
         const int ya = (rg * t.TY) / ngroups, yb = ((rg + 1) * t.TY) / ngroups;
-        float hq[kNQ][W];
+        float rg_[W][W], rb_[W][W], rm[W][W], rn[W][W], hd[W], he[W];
+        auto load_row = [&](int e1, float (&g_)[W], float (&b_)[W], float (&m_)[W], float (&n_)[W], float& d_,
+                            float& e_) {
+            const float* q0 = sQ + e1 * EX1 + c;
+            float sd = 0.f, se = 0.f;
 #pragma unroll
-        for (int s = 0; s < 2 * R; ++s) {
-#pragma unroll
-            for (int m = 0; m < kNQ; ++m) {
-                const float* pq = sQ + m * n1 + (ya + s) * EX1 + c;
-                float a = 0.f;
-#pragma unroll
-                for (int k = 0; k < W; ++k) a += pq[k];
-                hq[m][s] = a;
+            for (int k = 0; k < W; ++k) {
+                g_[k] = q0[k];
+                b_[k] = q0[n1 + k];
+                m_[k] = q0[2 * n1 + k];
+                n_[k] = q0[3 * n1 + k];
+                sd += q0[4 * n1 + k];
+                se += q0[5 * n1 + k];
             }
-        }
+            d_ = sd;
+            e_ = se;
+        };
+#pragma unroll
+        for (int s = 0; s < 2 * R; ++s) load_row(ya + s, rg_[s], rb_[s], rm[s], rn[s], hd[s], he[s]);
         for (int base = ya; base < yb; base += W) {
 #pragma unroll
             for (int s = 0; s < W; ++s) {
                 const int y = base + s;
                 if (y < yb) {
                     const int slot = (s + 2 * R) % W;
-#pragma unroll
-                    for (int m = 0; m < kNQ; ++m) {
-                        const float* pq = sQ + m * n1 + (y + 2 * R) * EX1 + c;
-                        float a = 0.f;
-#pragma unroll
-                        for (int k = 0; k < W; ++k) a += pq[k];
-                        hq[m][slot] = a;
-                    }
+                    load_row(y + 2 * R, rg_[slot], rb_[slot], rm[slot], rn[slot], hd[slot], he[slot]);
                     const int gy = t.ty0 + y;
                     if (INT || (gx < t.w && gy < t.h)) {
-                        float S[kNQ];
-#pragma unroll
-                        for (int m = 0; m < kNQ; ++m) {
-                            float a = 0.f;
-#pragma unroll
-                            for (int k = 0; k < W; ++k) a += hq[m][k];
-                            S[m] = a;
-                        }
                         const int o = (y + 2 * R) * EX2 + c + 2 * R;
-                        const float g = sG[o] - KG, p = sP[o] - KP;
+                        const float g = sG[o], p = sP[o];
+                        float aP = 0.f, aG = 0.f, sd = 0.f, se = 0.f;
+#pragma unroll
+                        for (int j = 0; j < W; ++j) {
+                            sd += hd[j];
+                            se += he[j];
+#pragma unroll
+                            for (int k = 0; k < W; ++k) {
+                                const float dg = g - rm[j][k], dp = p - rn[j][k];
+                                aP = fmaf(rg_[j][k], dg, aP);
+                                aG = fmaf(rg_[j][k], dp, fmaf(2.f * rb_[j][k], dg, aG));
+                            }
+                        }
                         const size_t go = (size_t)gy * t.w + gx;
-                        if (dP != nullptr) dP[go] = from_f32<TP>(fmaf(g, S[0], S[2]));
-                        if (dG != nullptr) dG[go] = from_f32<TD>(fmaf(p, S[0], fmaf(2.f * g, S[1], -S[3])));
+                        if (dP != nullptr) dP[go] = from_f32<TP>(aP + sd);
+                        if (dG != nullptr) dG[go] = from_f32<TD>(aG - se);
                     }
                 }
             }
@@ -829,8 +844,11 @@ __device__ __forceinline__ void lowres_bwd_tile_fast(const TG* __restrict__ G, c
                                                      const float2* __restrict__ dcoef, TP* __restrict__ dP,
                                                      TD* __restrict__ dG, const FastTile& t, float* smem) {
     if constexpr (R <= 2) {
-        const bool interior = t.tx0 - 2 * R >= 0 && t.ty0 - 2 * R >= 0 && t.tx0 + t.CW <= t.w &&
-                              t.ty0 + t.EY1 <= t.h;
+        // interior here also needs full window counts at every staged position
+        // (d Abar / N is divided by the count of the window centred there), so
+        // the staged region must stay R pixels inside the image
+        const bool interior = t.tx0 - 3 * R >= 0 && t.ty0 - 3 * R >= 0 && t.tx0 + t.CW + R <= t.w &&
+                              t.ty0 + t.EY1 + R <= t.h;
         if (interior)
             lowres_bwd_tile_ring<TG, TP, TD, R, true>(G, P, dcoef, dP, dG, t, smem);
         else

@@ -59,6 +59,8 @@ def test_forward_parity(case, dtype):
 
 BWD_CASES = [c for c in FWD_CASES if c[0] != "ragged" or c[3] > 1] + [
     ("photo", 1, 1, 48, 64, 384, 512, 2, 1e-3),     # f = 8 with an even low-res width
+    ("blobs", 1, 1, 256, 256, 1024, 1024, 1, 1e-4),  # large flat regions: gamma ~ 1/eps
+    ("blobs", 1, 1, 200, 240, 800, 960, 2, 1e-4),
 ]
 
 
