@@ -193,6 +193,24 @@ int dgf_autotune_entries(void);
 void dgf_autotune_reset(void);
 
 /*
+ * Pin one entry of the autotuner's table, as if tuning had chosen it: later
+ * calls with that key use the shape (whether tuning is enabled or not).
+ * Keys and shapes as the table stores them:
+ *   kind 1 (K1 low-res coefficients) and 4 (K4 low-res backward): r = radius,
+ *     F = vec = 0; guide_f32 = 1 for the guidance-transform path (FP32 guide);
+ *     tiles: a = columns, b = rows of the coefficient region (a power of two
+ *     in {64, 128, 256} and one of {16, 32, 64}); K1 with r <= 2 also takes
+ *     warp strips: a = rows per segment in {16, 32, 64}, b = 0.
+ *   kind 2 (K2 high-res apply): r = 0, F = integer factor (0: non-integer),
+ *     vec = elements per vector; a = high-res rows per tile, b = 0.
+ *   kind 3 (K3 high-res backward): as kind 2; a = low-res rows per tile.
+ * A shape the kernels are not built for is stored but ignored at plan time
+ * (the default shape is used).  Returns DGF_ERR_INVALID for a key or shape
+ * outside these ranges.  No counterpart in the paper: tuning machinery.
+ */
+dgf_status dgf_autotune_pin(int kind, dgf_dtype dt, int r, int F, int vec, int guide_f32, int a, int b);
+
+/*
  * Forward pass that allocates nothing and takes no workspace.  The paper
  * has no counterpart; this exists for callers that cannot allocate device
  * memory when they call the layer (cudaMalloc may synchronise the device or

@@ -60,6 +60,7 @@ _SIGS = {
     "dgf_autotune": (None, [_I]),
     "dgf_autotune_entries": (_I, []),
     "dgf_autotune_reset": (None, []),
+    "dgf_autotune_pin": (_I, [_I, _I, _I, _I, _I, _I, _I, _I]),
     "dgf_forward_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _F, _I, _P]),
     "dgf_noalloc_max_pairs": (_S, []),
 }
@@ -159,6 +160,10 @@ def dgf_autotune_entries() -> int:
 
 def dgf_autotune_reset() -> None:
     lib().dgf_autotune_reset()
+
+
+def dgf_autotune_pin(kind, dt, r, F, vec, guide_f32, a, b) -> int:
+    return lib().dgf_autotune_pin(kind, dt, r, F, vec, guide_f32, a, b)
 
 
 def dgf_forward_noalloc(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, stream) -> int:

@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
+#include <tuple>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -202,7 +204,7 @@ static bool pick_lowres_tiles(int r, Plan& p) {
     const size_t lim = smem_limit();
     bool ok1 = false, ok4 = false;
     if (low_fast_radius(r)) {
-        const LowCfg k1 = r <= 2 ? LowCfg{1, 64, 32} : LowCfg{1, 128, 32};
+        const LowCfg k1 = r <= 2 ? LowCfg{2, 32, 0} : LowCfg{1, 128, 32};
         const LowCfg k4 = r == 1 ? LowCfg{1, 64, 16} : (r == 2 ? LowCfg{1, 64, 32}
                                                               : (r == 4 ? LowCfg{1, 128, 16} : LowCfg{1, 64, 32}));
         if (k1_cfg_smem(k1, r, 0) <= lim) {
@@ -234,6 +236,13 @@ static bool pick_lowres_tiles(int r, Plan& p) {
 
 static int default_k3_lth(int F) { return F >= 8 ? 4 : (F >= 4 ? 8 : 16); }
 
+static std::vector<LowCfg> low_candidates(int r, bool k4);
+static bool in_candidates(const LowCfg& c, int r, bool k4) {
+    for (const LowCfg& x : low_candidates(r, k4))
+        if (x.fast == c.fast && x.a == c.a && x.b == c.b) return true;
+    return false;
+}
+
 // Shapes from the autotuner's table override the defaults (whether or not
 // tuning is enabled now), so every call with the same key uses one shape.
 static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool gf32,
@@ -245,15 +254,18 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     p.k3_fast = p.F > 0 && k3_fast_ok(p.vec, p.F);
     p.k3_lth = default_k3_lth(p.F);
     int a, b;
+    // a table entry (tuned, pinned or read from a cache file) is used only if
+    // it is one of the shapes the kernels are built for
     if (low_fast_radius(r)) {
-        if (tune_lookup(TuneKey{1, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b) &&
-            k1_fast_smem_bytes(r, a, b, 0) <= smem_limit())
-            p.k1 = LowCfg{1, a, b};
-        if (tune_lookup(TuneKey{4, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b) && k4_fast_smem_bytes(r, a, b) <= smem_limit())
+        if (tune_lookup(TuneKey{1, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b)) {
+            const LowCfg c{b == 0 ? 2 : 1, a, b};
+            if (in_candidates(c, r, false)) p.k1 = c;
+        }
+        if (tune_lookup(TuneKey{4, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b) && in_candidates(LowCfg{1, a, b}, r, true))
             p.k4 = LowCfg{1, a, b};
     }
-    if (tune_lookup(TuneKey{2, (int)dt, 0, p.F, p.vec, 0}, a, b)) p.k2_th = a;
-    if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b) &&
+    if (tune_lookup(TuneKey{2, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256) p.k2_th = a;
+    if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 64 &&
         k3_smem_bytes(p.vec, p.F, a) <= smem_limit())
         p.k3_lth = a;
     return p;
@@ -262,6 +274,8 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
 static std::vector<LowCfg> low_candidates(int r, bool k4) {
     std::vector<LowCfg> v;
     if (!low_fast_radius(r)) return v;
+    if (!k4 && r <= 2)
+        for (int seg : {16, 32, 64}) v.push_back(LowCfg{2, seg, 0});
     static const int cws[] = {64, 128, 256};
     static const int eys[] = {16, 32, 64};
     for (int cw : cws)
@@ -331,6 +345,7 @@ static CUtensorMapDataType tma_type(dgf_dtype dt) {
 // wider and the kernel computes the offset per tile.
 static bool k1_box(const LowCfg& c, int r, int esz, int& bx, int& by, int& off) {
     const int U = 16 / esz;
+    if (c.fast == 2) return false;  // warp strips load rows directly
     if (c.fast) {
         const int EX2 = c.a + 2 * r;
         bx = (EX2 + U - 1 + U - 1) / U * U;
@@ -525,14 +540,18 @@ static cudaError_t run_k1(Launcher& L, dgf_dtype dt, bool gf32, const void* G, c
 // ------------------------------------------------------------------ batched
 namespace dgf {
 
+// One K1 node per radius present in the batch (each with the shared memory
+// and grid of its own tile shape, so small radii keep full occupancy), all
+// feeding one K2 node.  Keyed by (device, dtype, radii present).
 struct BatchGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t n1 = nullptr, n2 = nullptr;
+    std::vector<cudaGraphNode_t> n1, n2;
 };
 
 std::mutex g_batch_mu;
-std::map<std::pair<int, int>, BatchGraph> g_batch;  // (device, dtype)
+// key: device, dtype, K1 classes (radius), K2 classes (vector width * 100 + factor)
+std::map<std::tuple<int, int, std::vector<int>, std::vector<int>>, BatchGraph> g_batch;
 
 struct BatchPrep {
     BatchParams bp;
@@ -571,8 +590,8 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
         b.F = (p.F == 4 || p.F == 8) ? p.F : 0;
         b.vec = p.vec;
         b.k1_fast = p.k1.fast;
-        b.k1_ty = p.k1.fast ? p.k1.b : p.k1.a;  // fast: EY1; generic: TY
-        b.k1_tx = p.k1.fast ? p.k1.a : p.k1.b;  // fast: CW;  generic: TX
+        b.k1_ty = p.k1.fast ? p.k1.b : p.k1.a;  // tiles: EY1; generic: TY; strips: 0
+        b.k1_tx = p.k1.fast ? p.k1.a : p.k1.b;  // tiles: CW;  generic: TX; strips: rows per segment
         b.k2_th = p.k2_th;
         low_grid(p.k1, im.r, im.h_l, im.w_l, b.k1_nx, b.k1_ny);
         b.k2_nx = (im.w + 32 * b.vec - 1) / (32 * b.vec);
@@ -767,51 +786,114 @@ extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtyp
     st = prepare_batch(imgs, n, dt, static_cast<char*>(workspace), prep);
     if (st != DGF_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    void* f1 = nullptr;
-    void* f2 = nullptr;
-    cudaError_t e = k1_batched_kernel(dt, prep.smem1, &f1);
-    if (e != cudaSuccess) return cuda_fail(e, "k1 batched attr");
-    e = k2_batched_kernel(dt, prep.smem2, &f2);
-    if (e != cudaSuccess) return cuda_fail(e, "k2 batched attr");
-    int dev = 0, sms = 0, occ1 = 0, occ2 = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, f1, kThreads, prep.smem1);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, f2, kThreads, prep.smem2);
-    const int g1 = std::max(1, std::min(prep.bp.k1_total, sms * std::max(occ1, 1)));
-    const int g2 = std::max(1, std::min(prep.bp.k2_total, sms * std::max(occ2, 1)));
+    // Node classes: K1 by (radius, kernel form), one tile shape each,
+    // K2 by (vector width, factor).  Every node is a persistent kernel
+    // specialised for its class, so it keeps the registers and occupancy of
+    // the single-call kernel; its images keep their workspace slots.
+    std::vector<int> c1, c2;
+    auto k1class = [](const BatchImage& im) { return im.r * 4 + im.k1_fast; };
+    auto k2class = [](const BatchImage& im) { return im.vec * 100 + im.F; };
+    for (int i = 0; i < n; ++i) {
+        const BatchImage& im = prep.bp.img[i];
+        if (std::find(c1.begin(), c1.end(), k1class(im)) == c1.end()) c1.push_back(k1class(im));
+        if (std::find(c2.begin(), c2.end(), k2class(im)) == c2.end()) c2.push_back(k2class(im));
+    }
+    std::sort(c1.begin(), c1.end());
+    std::sort(c2.begin(), c2.end());
+    static thread_local std::vector<BatchParams> bp1, bp2;
+    bp1.resize(c1.size());
+    bp2.resize(c2.size());
+    std::vector<size_t> sm1(c1.size(), 0), sm2(c2.size(), 0);
+    std::vector<int> fast1(c1.size(), 0);
+    for (size_t q = 0; q < c1.size(); ++q) {
+        BatchParams& b = bp1[q];
+        memset(&b, 0, sizeof b);
+        for (int i = 0; i < n; ++i) {
+            const BatchImage& im = prep.bp.img[i];
+            if (k1class(im) != c1[q]) continue;
+            const int j = b.n++;
+            b.img[j] = im;
+            b.k1_start[j + 1] = b.k1_start[j] + im.k1_nx * im.k1_ny * im.C;
+            const LowCfg c{im.k1_fast, im.k1_fast ? im.k1_tx : im.k1_ty, im.k1_fast ? im.k1_ty : im.k1_tx};
+            sm1[q] = std::max(sm1[q], k1_cfg_smem(c, im.r, 0));
+            fast1[q] = im.k1_fast;
+        }
+        b.k1_total = b.k1_start[b.n];
+    }
+    for (size_t q = 0; q < c2.size(); ++q) {
+        BatchParams& b = bp2[q];
+        memset(&b, 0, sizeof b);
+        for (int i = 0; i < n; ++i) {
+            const BatchImage& im = prep.bp.img[i];
+            if (k2class(im) != c2[q]) continue;
+            const int j = b.n++;
+            b.img[j] = im;
+            b.k2_start[j + 1] = b.k2_start[j] + im.k2_nx * im.k2_ny * im.C;
+            sm2[q] = std::max(sm2[q], k2_smem_bytes(im.vec, im.F, im.h_l, im.h, im.w_l, im.w, im.k2_th));
+        }
+        b.k2_total = b.k2_start[b.n];
+    }
     uint32_t* stw = status_ptr();
-    void* args1[] = {&prep.bp, &stw};
-    void* args2[] = {&prep.bp};
-    cudaKernelNodeParams p1{}, p2{};
-    p1.func = f1;
-    p1.gridDim = dim3(g1);
-    p1.blockDim = dim3(kThreads);
-    p1.sharedMemBytes = (unsigned)prep.smem1;
-    p1.kernelParams = args1;
-    p2.func = f2;
-    p2.gridDim = dim3(g2);
-    p2.blockDim = dim3(kThreads);
-    p2.sharedMemBytes = (unsigned)prep.smem2;
-    p2.kernelParams = args2;
+    cudaError_t e;
+    std::vector<cudaKernelNodeParams> p1(c1.size()), p2(c2.size());
+    std::vector<std::array<void*, 2>> a1(c1.size());
+    std::vector<std::array<void*, 1>> a2(c2.size());
+    for (size_t q = 0; q < c1.size(); ++q) {
+        void* f = nullptr;
+        if ((e = k1_batched_kernel(dt, c1[q] / 4, fast1[q], sm1[q], &f)) != cudaSuccess)
+            return cuda_fail(e, "k1 batched attr");
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, sm1[q]);
+        a1[q] = {&bp1[q], &stw};
+        p1[q] = cudaKernelNodeParams{};
+        p1[q].func = f;
+        p1[q].gridDim = dim3(std::max(1, std::min(bp1[q].k1_total, sms * std::max(occ, 1))));
+        p1[q].blockDim = dim3(kThreads);
+        p1[q].sharedMemBytes = (unsigned)sm1[q];
+        p1[q].kernelParams = a1[q].data();
+    }
+    for (size_t q = 0; q < c2.size(); ++q) {
+        void* f = nullptr;
+        if ((e = k2_batched_kernel(dt, c2[q] / 100, c2[q] % 100, sm2[q], &f)) != cudaSuccess)
+            return cuda_fail(e, "k2 batched attr");
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, sm2[q]);
+        a2[q] = {&bp2[q]};
+        p2[q] = cudaKernelNodeParams{};
+        p2[q].func = f;
+        p2[q].gridDim = dim3(std::max(1, std::min(bp2[q].k2_total, sms * std::max(occ, 1))));
+        p2[q].blockDim = dim3(kThreads);
+        p2[q].sharedMemBytes = (unsigned)sm2[q];
+        p2[q].kernelParams = a2[q].data();
+    }
     std::lock_guard<std::mutex> lk(g_batch_mu);
-    BatchGraph& bg = g_batch[{dev, (int)dt}];
+    BatchGraph& bg = g_batch[std::make_tuple(dev, (int)dt, c1, c2)];
     if (bg.exec == nullptr) {
         if ((e = cudaGraphCreate(&bg.graph, 0)) != cudaSuccess) return cuda_fail(e, "graph create");
-        if ((e = cudaGraphAddKernelNode(&bg.n1, bg.graph, nullptr, 0, &p1)) != cudaSuccess)
-            return cuda_fail(e, "graph node k1");
-        if ((e = cudaGraphAddKernelNode(&bg.n2, bg.graph, &bg.n1, 1, &p2)) != cudaSuccess)
-            return cuda_fail(e, "graph node k2");
+        bg.n1.resize(c1.size());
+        bg.n2.resize(c2.size());
+        for (size_t q = 0; q < c1.size(); ++q)
+            if ((e = cudaGraphAddKernelNode(&bg.n1[q], bg.graph, nullptr, 0, &p1[q])) != cudaSuccess)
+                return cuda_fail(e, "graph node k1");
+        // the stage boundary: every K2 node waits for every K1 node
+        for (size_t q = 0; q < c2.size(); ++q)
+            if ((e = cudaGraphAddKernelNode(&bg.n2[q], bg.graph, bg.n1.data(), bg.n1.size(), &p2[q])) != cudaSuccess)
+                return cuda_fail(e, "graph node k2");
         if ((e = cudaGraphInstantiate(&bg.exec, bg.graph, 0)) != cudaSuccess) return cuda_fail(e, "graph instantiate");
     } else {
-        if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n1, &p1)) != cudaSuccess)
-            return cuda_fail(e, "graph update k1");
-        if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n2, &p2)) != cudaSuccess)
-            return cuda_fail(e, "graph update k2");
+        for (size_t q = 0; q < c1.size(); ++q)
+            if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n1[q], &p1[q])) != cudaSuccess)
+                return cuda_fail(e, "graph update k1");
+        for (size_t q = 0; q < c2.size(); ++q)
+            if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n2[q], &p2[q])) != cudaSuccess)
+                return cuda_fail(e, "graph update k2");
     }
     Launcher L(s);
     e = L.run("batched_graph(k1,k2)", [&] {
-        g_launches.fetch_add(1);  // two kernels per replay
+        g_launches.fetch_add((long long)(c1.size() + c2.size()) - 1);  // every node of the replay
         return cudaGraphLaunch(bg.exec, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "graph launch");
@@ -861,6 +943,15 @@ extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
 extern "C" void dgf_autotune(int on) { tune_set_enabled(on != 0); }
 
 extern "C" int dgf_autotune_entries(void) { return tune_count(); }
+
+extern "C" dgf_status dgf_autotune_pin(int kind, dgf_dtype dt, int r, int F, int vec, int guide_f32, int a,
+                                       int b) {
+    if (kind < 1 || kind > 4 || (int)dt < 0 || (int)dt > 2 || r < 0 || F < 0 || vec < 0 || a <= 0 || a > 4096 || b < 0 ||
+        b > 4096 || (guide_f32 != 0 && guide_f32 != 1))
+        return fail(DGF_ERR_INVALID, "autotune_pin: bad key or shape");
+    tune_store(TuneKey{kind, (int)dt, r, F, vec, guide_f32}, a, b);
+    return DGF_OK;
+}
 
 extern "C" void dgf_autotune_reset(void) { tune_clear(); }
 

@@ -7,10 +7,13 @@
 #include "kernels.h"
 #include "lowres_fast.cuh"
 #include "lowres_generic.cuh"
+#include "lowres_strip.cuh"
 
 namespace dgf {
 
-template <typename T>
+// MODE 2: warp strips of radius R (a work item is 8 strip segments, one per
+// warp); MODE 1: column-walking tiles of radius R; MODE 0: generic tiles.
+template <typename T, int R, int MODE>
 __global__ void __launch_bounds__(kThreads) k1_coef_batched(const __grid_constant__ BatchParams bp,
                                                             uint32_t* status) {
     extern __shared__ __align__(128) float smem[];
@@ -18,6 +21,24 @@ __global__ void __launch_bounds__(kThreads) k1_coef_batched(const __grid_constan
         const int i = batch_find(bp.k1_start, bp.n, tile);
         const BatchImage& im = bp.img[i];
         const int local = tile - bp.k1_start[i];
+        if constexpr (MODE == 2) {
+            const int nstrip = (im.w_l + (32 - 4 * R) - 1) / (32 - 4 * R);
+            const int nseg = (im.h_l + im.k1_tx - 1) / im.k1_tx;
+            const int plane = local / im.k1_nx;
+            const int item = (local - plane * im.k1_nx) * kStripWarps + (threadIdx.x >> 5);
+            if (item < nstrip * nseg) {  // warp-uniform; no barrier follows
+                StripGeom sg;
+                sg.h = im.h_l;
+                sg.w = im.w_l;
+                sg.x0 = (item % nstrip) * (32 - 4 * R) - 2 * R;
+                sg.y0 = (item / nstrip) * im.k1_tx;
+                sg.seg = im.k1_tx;
+                const size_t hw = (size_t)im.h_l * im.w_l;
+                coef_strip<T, T, R>(static_cast<const T*>(im.I_l) + plane * hw,
+                                    static_cast<const T*>(im.p_l) + plane * hw, im.coef + plane * hw, sg, im.eps);
+            }
+            continue;
+        }
         const int per_plane = im.k1_nx * im.k1_ny;
         const int plane = local / per_plane;
         const int tp = local - plane * per_plane;
@@ -25,17 +46,12 @@ __global__ void __launch_bounds__(kThreads) k1_coef_batched(const __grid_constan
         const size_t hw = (size_t)im.h_l * im.w_l;
         const T* G = static_cast<const T*>(im.I_l) + plane * hw;
         const T* P = static_cast<const T*>(im.p_l) + plane * hw;
-        if (im.k1_fast) {
+        if constexpr (MODE == 1) {
             FastTile f;
             f.h = im.h_l; f.w = im.w_l; f.CW = im.k1_tx; f.EY1 = im.k1_ty; f.log2cw = ilog2(im.k1_tx);
-            f.eps = im.eps; f.TX = im.k1_tx - 2 * im.r; f.TY = im.k1_ty - 2 * im.r;
+            f.eps = im.eps; f.TX = im.k1_tx - 2 * R; f.TY = im.k1_ty - 2 * R;
             f.tx0 = tx * f.TX; f.ty0 = ty * f.TY;
-            switch (im.r) {
-                case 1: coef_tile_fast<T, T, 1>(G, P, im.coef + plane * hw, f, smem, nullptr, nullptr, plane, status); break;
-                case 2: coef_tile_fast<T, T, 2>(G, P, im.coef + plane * hw, f, smem, nullptr, nullptr, plane, status); break;
-                case 4: coef_tile_fast<T, T, 4>(G, P, im.coef + plane * hw, f, smem, nullptr, nullptr, plane, status); break;
-                default: coef_tile_fast<T, T, 8>(G, P, im.coef + plane * hw, f, smem, nullptr, nullptr, plane, status); break;
-            }
+            coef_tile_fast<T, T, R>(G, P, im.coef + plane * hw, f, smem, nullptr, nullptr, plane, status);
         } else {
             LowresTile t;
             t.init(im.h_l, im.w_l, im.r, im.eps, ty * im.k1_ty, tx * im.k1_tx, im.k1_ty, im.k1_tx);
@@ -44,13 +60,30 @@ __global__ void __launch_bounds__(kThreads) k1_coef_batched(const __grid_constan
     }
 }
 
+template <typename T, int R, int MODE>
+static cudaError_t k1b_get(size_t smem, void** fn) {
+    *fn = (void*)k1_coef_batched<T, R, MODE>;
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute(k1_coef_batched<T, R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    return cudaSuccess;
+}
 
 template <typename T>
-cudaError_t k1_batched_kernel_t(size_t smem, void** fn) {
-    *fn = (void*)k1_coef_batched<T>;
-    if (smem > 48 * 1024)
-        return cudaFuncSetAttribute(k1_coef_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaSuccess;
+cudaError_t k1_batched_kernel_t(int r, int mode, size_t smem, void** fn) {
+    if (mode == 2) {
+        if (r == 1) return k1b_get<T, 1, 2>(smem, fn);
+        if (r == 2) return k1b_get<T, 2, 2>(smem, fn);
+    }
+    if (mode == 1) {
+        switch (r) {
+            case 1: return k1b_get<T, 1, 1>(smem, fn);
+            case 2: return k1b_get<T, 2, 1>(smem, fn);
+            case 4: return k1b_get<T, 4, 1>(smem, fn);
+            case 8: return k1b_get<T, 8, 1>(smem, fn);
+        }
+    }
+    return k1b_get<T, 0, 0>(smem, fn);
 }
 
 }  // namespace dgf

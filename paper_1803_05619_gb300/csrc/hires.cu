@@ -87,26 +87,14 @@ __device__ __forceinline__ void apply_batched_tile(const BatchImage& im, int loc
                              ty * im.k2_th, tx * 32 * VEC, im.k2_th, pitch, sAB);
 }
 
-template <typename T>
+// One persistent kernel per (storage type, vector width, factor) class:
+// each graph node walks the flat tile list of the images of its class.
+template <typename T, int VEC, int F>
 __global__ void __launch_bounds__(kThreads) k2_apply_batched(const __grid_constant__ BatchParams bp) {
     extern __shared__ __align__(128) float2 sAB[];
-    constexpr int VW = 16 / sizeof(T);  // 16-byte vectors
-    constexpr int VH = 8 / sizeof(T);   // 8-byte vectors
     for (int tile = blockIdx.x; tile < bp.k2_total; tile += gridDim.x) {
         const int i = batch_find(bp.k2_start, bp.n, tile);
-        const BatchImage& im = bp.img[i];
-        const int local = tile - bp.k2_start[i];
-        if (im.vec == VW) {
-            if (im.F == 4) apply_batched_tile<T, VW, 4>(im, local, sAB);
-            else if (im.F == 8) apply_batched_tile<T, VW, 8>(im, local, sAB);
-            else apply_batched_tile<T, VW, 0>(im, local, sAB);
-        } else if (im.vec == VH) {
-            if (im.F == 4) apply_batched_tile<T, VH, 4>(im, local, sAB);
-            else if (im.F == 8) apply_batched_tile<T, VH, 8>(im, local, sAB);
-            else apply_batched_tile<T, VH, 0>(im, local, sAB);
-        } else {
-            apply_batched_tile<T, 1, 0>(im, local, sAB);
-        }
+        apply_batched_tile<T, VEC, F>(bp.img[i], tile - bp.k2_start[i], sAB);
     }
 }
 
@@ -128,8 +116,7 @@ int k3_ltw(int vec, int F) {
 
 size_t k3_smem_bytes(int vec, int F, int LTH) {
     const int SXP = k3_ltw(vec, F) + 2;
-    return (size_t)F * (LTH + 1) * SXP * sizeof(float2) + (size_t)F * LTH * SXP * sizeof(float) +
-           (size_t)(LTH + 2) * SXP * sizeof(float);
+    return (size_t)F * (LTH + 1) * SXP * sizeof(float2) + (size_t)(LTH + 2) * SXP * sizeof(float);
 }
 
 bool k3_fast_ok(int vec, int F) {
@@ -255,20 +242,35 @@ cudaError_t launch_k3_general(dgf_dtype dt, const void* R, const void* G, float2
     return cudaErrorInvalidValue;
 }
 
-template <typename T>
-static cudaError_t k2b_prep(size_t smem) {
-    return prep(k2_apply_batched<T>, smem);
+template <typename T, int VEC, int F>
+static cudaError_t k2b_get(size_t smem, void** fn) {
+    *fn = (void*)k2_apply_batched<T, VEC, F>;
+    return prep(k2_apply_batched<T, VEC, F>, smem);
 }
 
-cudaError_t k2_batched_kernel(dgf_dtype dt, size_t smem, void** fn) {
-    cudaError_t e = cudaSuccess;
-    switch (dt) {
-        case DGF_F32: e = k2b_prep<float>(smem); *fn = (void*)k2_apply_batched<float>; break;
-        case DGF_BF16: e = k2b_prep<__nv_bfloat16>(smem); *fn = (void*)k2_apply_batched<__nv_bfloat16>; break;
-        case DGF_F16: e = k2b_prep<__half>(smem); *fn = (void*)k2_apply_batched<__half>; break;
-        default: return cudaErrorInvalidValue;
+template <typename T>
+static cudaError_t k2b_dispatch(int vec, int F, size_t smem, void** fn) {
+    constexpr int VW = 16 / sizeof(T), VH = 8 / sizeof(T);
+    if (vec == VW) {
+        if (F == 4) return k2b_get<T, VW, 4>(smem, fn);
+        if (F == 8) return k2b_get<T, VW, 8>(smem, fn);
+        return k2b_get<T, VW, 0>(smem, fn);
     }
-    return e;
+    if (vec == VH) {
+        if (F == 4) return k2b_get<T, VH, 4>(smem, fn);
+        if (F == 8) return k2b_get<T, VH, 8>(smem, fn);
+        return k2b_get<T, VH, 0>(smem, fn);
+    }
+    return k2b_get<T, 1, 0>(smem, fn);
+}
+
+cudaError_t k2_batched_kernel(dgf_dtype dt, int vec, int F, size_t smem, void** fn) {
+    switch (dt) {
+        case DGF_F32: return k2b_dispatch<float>(vec, F, smem, fn);
+        case DGF_BF16: return k2b_dispatch<__nv_bfloat16>(vec, F, smem, fn);
+        case DGF_F16: return k2b_dispatch<__half>(vec, F, smem, fn);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace dgf

@@ -216,84 +216,86 @@ __device__ __forceinline__ void k3_gather_columns(const float2* Sx, int i0, int 
     using S = K3Shape<VEC, F>;
     constexpr int H0 = S::H0, LTW = S::LTW, SXP = S::SXP;
     const int yf0 = F * (i0 - 1) + H0;
-    const int nown = LTH * LTW;
-    for (int idx = threadIdx.x; idx < nown; idx += kThreads) {
-        const int li = idx / LTW, lj = idx - li * LTW;
-        const int i = i0 + li, j = j0 + lj;
-        if (i >= h_l || j >= w_l) continue;
-        const int c = lj + 1;
-        const bool left = (j == 0), right = (j == w_l - 1);
-        float su = 0.f, sv = 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int li = warp; li < LTH; li += kWarps) {
+        const int i = i0 + li;
+        if (i >= h_l) break;
+        const bool top = (i == 0), bottom = (i == h_l - 1);
+        for (int lj = lane; lj < LTW; lj += 32) {
+            const int j = j0 + lj;
+            if (j >= w_l) break;
+            const int c = lj + 1;
+            const bool left = (j == 0), right = (j == w_l - 1);
+            float su = 0.f, sv = 0.f;
 #pragma unroll
-        for (int tt = 0; tt < 2 * F; ++tt) {
-            // tt < F: rows whose first tap is i; tt >= F: rows whose second tap is i
-            const int t = tt % F;
-            const int y = (tt < F) ? F * i + H0 + t : F * (i - 1) + H0 + t;
-            const int q = (H0 + t) % F;
-            const int t2 = 2 * q + 1 - F;
-            const float lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
-            float wgt;
-            if (tt < F) wgt = (i == h_l - 1) ? 1.f : 1.f - lam;
-            else wgt = (i == 0) ? 1.f : lam;
-            const float2* row = Sx + (y - yf0) * SXP;
-            float2 v = row[c];
-            if (left) { v.x += row[0].x; v.y += row[0].y; }
-            if (right) { v.x += row[c + 1].x; v.y += row[c + 1].y; }
-            su = fmaf(wgt, v.x, su);
-            sv = fmaf(wgt, v.y, sv);
+            for (int tt = 0; tt < 2 * F; ++tt) {
+                // tt < F: rows whose first tap is i; tt >= F: rows whose second tap is i
+                const int t = tt % F;
+                const int y = (tt < F) ? F * i + H0 + t : F * (i - 1) + H0 + t;
+                const int q = (H0 + t) % F;
+                const int t2 = 2 * q + 1 - F;
+                const float lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
+                float wgt;
+                if (tt < F) wgt = bottom ? 1.f : 1.f - lam;
+                else wgt = top ? 1.f : lam;
+                const float2* row = Sx + (y - yf0) * SXP;
+                float2 v = row[c];
+                if (left) { v.x += row[0].x; v.y += row[0].y; }
+                if (right) { v.x += row[c + 1].x; v.y += row[c + 1].y; }
+                su = fmaf(wgt, v.x, su);
+                sv = fmaf(wgt, v.y, sv);
+            }
+            dcoef[(size_t)i * w_l + j] = make_float2(su, sv);
         }
-        dcoef[(size_t)i * w_l + j] = make_float2(su, sv);
     }
 }
 
-// Vertical lerp of Abar for the tile's interior high-res rows
-// [F i0, F (i0 + LTH)), columns j0-1 .. j0+LTW (clamped), into SA.
+// Raw Abar rows the tile's interior high-res rows tap
+// (low-res rows i0-1 .. i0+LTH, columns j0-1 .. j0+LTW, clamped) into sRaw.
 template <int VEC, int F>
 __device__ __forceinline__ void k3_stage_abar(const float2* __restrict__ coef, int i0, int j0, int LTH,
-                                              int h_l, int w_l, int h, float* SA, float* sRaw) {
+                                              int h_l, int w_l, float* sRaw) {
     constexpr int SXP = K3Shape<VEC, F>::SXP;
-    // raw Abar rows i0-1 .. i0+LTH (clamped), loaded once, 8 loads in flight per thread
-    const int nraw = (LTH + 2) * SXP;
-    for (int base = threadIdx.x; base < nraw; base += 8 * kThreads) {
-        float v[8];
+    // raw Abar rows i0-1 .. i0+LTH (clamped), columns j0-1 .. j0+LTW (clamped), loaded once
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rr = warp; rr < LTH + 2; rr += kWarps) {
+        const float2* src = coef + (size_t)clampi(i0 - 1 + rr, 0, h_l - 1) * w_l;
+        float v[(SXP + 31) / 32];
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const int idx = base + b * kThreads;
-            if (idx < nraw) {
-                const int rr = idx / SXP, c = idx - rr * SXP;
-                const int row = clampi(i0 - 1 + rr, 0, h_l - 1), jj = clampi(j0 - 1 + c, 0, w_l - 1);
-                v[b] = coef[(size_t)row * w_l + jj].x;
-            }
+        for (int b = 0; b < (SXP + 31) / 32; ++b) {
+            const int c = lane + 32 * b;
+            if (c < SXP) v[b] = src[clampi(j0 - 1 + c, 0, w_l - 1)].x;
         }
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const int idx = base + b * kThreads;
-            if (idx < nraw) sRaw[idx] = v[b];
+        for (int b = 0; b < (SXP + 31) / 32; ++b) {
+            const int c = lane + 32 * b;
+            if (c < SXP) sRaw[rr * SXP + c] = v[b];
         }
-    }
-    __syncthreads();
-    const int nst = F * LTH * SXP;
-    for (int idx = threadIdx.x; idx < nst; idx += kThreads) {
-        const int ri = idx / SXP, c = idx - ri * SXP;
-        const int y = F * i0 + ri;
-        if (y >= h) continue;
-        const int q = y % F, j = y / F, t2 = 2 * q + 1 - F;
-        const int yi0 = t2 < 0 ? j - 1 : j;
-        const float lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
-        // raw row index = clamped low-res row - (i0 - 1); clamping matches the load above
-        const int r0 = clampi(yi0, 0, h_l - 1) - (i0 - 1), r1 = clampi(yi0 + 1, 0, h_l - 1) - (i0 - 1);
-        SA[idx] = lerp(sRaw[r0 * SXP + c], sRaw[r1 * SXP + c], lam);
     }
 }
 
-// Abar_h of pixel k of lane `lane` in an interior row of SA (row pointer).
+// Abar_h of this lane's VEC pixels in high-res row y (interior rows only):
+// the K + 2 low-res columns the lane taps are interpolated along y first,
+// then each pixel along x.
 template <int VEC, int F>
-__device__ __forceinline__ float k3_abar_at(const float* row, int lane, int k) {
-    constexpr int K = K3Shape<VEC, F>::K;
-    const int q = k % F, jr = k / F, t2 = 2 * q + 1 - F;
-    const int c = (lane - 1) * K + jr + (t2 >= 0 ? 1 : 0);
-    const float lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
-    return lerp(row[c], row[c + 1], lam);
+__device__ __forceinline__ void k3_abar_row(const float* sRaw, int y, int i0, int h_l, int lane, float (&A)[VEC]) {
+    using S = K3Shape<VEC, F>;
+    constexpr int K = S::K, SXP = S::SXP, NCOL = K + 2;
+    const int q = y % F, j = y / F, t2 = 2 * q + 1 - F;
+    const int yi0 = t2 < 0 ? j - 1 : j;
+    const float lamy = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
+    const float* r0 = sRaw + (clampi(yi0, 0, h_l - 1) - (i0 - 1)) * SXP + (lane - 1) * K;
+    const float* r1 = sRaw + (clampi(yi0 + 1, 0, h_l - 1) - (i0 - 1)) * SXP + (lane - 1) * K;
+    float v[NCOL];
+#pragma unroll
+    for (int cc = 0; cc < NCOL; ++cc) v[cc] = lerp(r0[cc], r1[cc], lamy);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        const int qx = k % F, t2x = 2 * qx + 1 - F;
+        const int cl = k / F + (t2x >= 0 ? 1 : 0);
+        const float lamx = (float)(t2x < 0 ? t2x + 2 * F : t2x) / (float)(2 * F);
+        A[k] = lerp(v[cl], v[cl + 1], lamx);
+    }
 }
 
 template <typename T, int VEC, int F>
@@ -307,8 +309,7 @@ __device__ void hires_bwd_tile(const float2* __restrict__ coef, const T* __restr
     const int yf0 = F * (i0 - 1) + H0;
     const int XS = F * j0 - VEC;
     float2* Sx = reinterpret_cast<float2*>(smem);
-    float* SA = reinterpret_cast<float*>(Sx + FR * SXP);
-    float* sRaw = SA + F * LTH * SXP;  // (LTH + 2) x SXP
+    float* sRaw = reinterpret_cast<float*>(Sx + FR * SXP);  // (LTH + 2) x SXP raw Abar rows
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int xs = XS + lane * VEC;
     const bool col_ok = xs >= 0 && xs < w;
@@ -327,7 +328,7 @@ __device__ void hires_bwd_tile(const float2* __restrict__ coef, const T* __restr
     load_chunk(warp);  // first rows in flight before the staging below
     if (dG != nullptr) {
         // Abar along y for the interior rows, once per tile
-        k3_stage_abar<VEC, F>(coef, i0, j0, LTH, h_l, w_l, h, SA, sRaw);
+        k3_stage_abar<VEC, F>(coef, i0, j0, LTH, h_l, w_l, sRaw);
         __syncthreads();
     }
     for (int f0 = warp; f0 < FR; f0 += kWarps * U) {
@@ -346,10 +347,10 @@ __device__ void hires_bwd_tile(const float2* __restrict__ coef, const T* __restr
                     for (int k = 0; k < VEC; ++k) rv[k] = gv[k] = 0.f;
                 }
                 if (dG != nullptr && ok && interior && y >= F * i0 && y < F * (i0 + LTH)) {
-                    const float* row = SA + (y - F * i0) * SXP;
-                    float o[VEC];
+                    float A[VEC], o[VEC];
+                    k3_abar_row<VEC, F>(sRaw, y, i0, h_l, lane, A);
 #pragma unroll
-                    for (int k = 0; k < VEC; ++k) o[k] = rv[k] * k3_abar_at<VEC, F>(row, lane, k);
+                    for (int k = 0; k < VEC; ++k) o[k] = rv[k] * A[k];
                     store_vec<T, VEC>(dG + (size_t)y * w + xs, o);
                 }
                 float u2[VEC];

@@ -13,6 +13,7 @@
 namespace dgf {
 
 struct TmaPair;
+constexpr int kStripWarpsPerCta = 8;
 
 // Shared-memory pitch (float2 columns) of a K2 tile row.
 __host__ __device__ inline int k2_pitch(int vec, int F, int w_l, int w) {
@@ -22,9 +23,10 @@ __host__ __device__ inline int k2_pitch(int vec, int F, int w_l, int w) {
     return (int)span + 3;
 }
 
-// Low-resolution tile configuration: fast = column-walking kernels (r in
-// {1, 2, 4, 8}; a = CW columns, b = EY1 rows of the coefficient region),
-// else the generic tile kernels (a = TY, b = TX output tile).
+// Low-resolution tile configuration: fast = 1: column-walking tile kernels
+// (r in {1, 2, 4, 8}; a = CW columns, b = EY1 rows of the coefficient
+// region); fast = 2: warp-strip K1 (r in {1, 2}; a = rows per segment,
+// b = 0); fast = 0: generic tile kernels (a = TY, b = TX output tile).
 struct LowCfg {
     int fast;
     int a, b;
@@ -100,7 +102,7 @@ extern template cudaError_t launch_k4_fast<8>(dgf_dtype, bool, const void*, cons
                                               int, int, int, float, const LowCfg&, cudaStream_t);
 
 // Persistent batched kernels (function pointers for graph nodes).
-cudaError_t k1_batched_kernel(dgf_dtype dt, size_t smem, void** fn);
-cudaError_t k2_batched_kernel(dgf_dtype dt, size_t smem, void** fn);
+cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn);
+cudaError_t k2_batched_kernel(dgf_dtype dt, int vec, int F, size_t smem, void** fn);
 
 }  // namespace dgf

@@ -4,6 +4,7 @@
 #include "kernels.h"
 #include "lowres_fast.cuh"
 #include "lowres_generic.cuh"
+#include "lowres_strip.cuh"
 
 namespace dgf {
 
@@ -241,12 +242,13 @@ size_t k1_fast_smem_bytes(int r, int CW, int EY1, size_t tma_landing) {
 
 size_t k4_fast_smem_bytes(int r, int CW, int EY1) {
     const size_t e2 = (size_t)(CW + 2 * r) * (EY1 + 2 * r), e1 = (size_t)CW * EY1;
-    size_t floats = 4 * e2 + (r <= 2 ? kNQD : kNQ) * e1 + 3 * (kLowThreads / 32);
+    size_t floats = 4 * e2 + (r == 1 ? kNQD : kNQ) * e1 + 3 * (kLowThreads / 32);
     if (r > 2) floats += 8 + std::max((size_t)6 * (EY1 + 2 * r) * CW, (size_t)kNQ * e1);
     return floats * sizeof(float);
 }
 
 size_t k1_cfg_smem(const LowCfg& c, int r, size_t tma_landing) {
+    if (c.fast == 2) return 0;  // warp strips keep everything in registers
     return c.fast ? k1_fast_smem_bytes(r, c.a, c.b, tma_landing) : k1_smem_bytes(r, c.a, c.b);
 }
 
@@ -255,6 +257,13 @@ size_t k4_cfg_smem(const LowCfg& c, int r) {
 }
 
 void low_grid(const LowCfg& c, int r, int h, int w, int& gx, int& gy) {
+    if (c.fast == 2) {
+        // work items of 8 warp strips (one CTA) per plane, in one row
+        const int nstrip = (w + (32 - 4 * r) - 1) / (32 - 4 * r), nseg = (h + c.a - 1) / c.a;
+        gx = (nstrip * nseg + kStripWarps - 1) / kStripWarps;
+        gy = 1;
+        return;
+    }
     if (c.fast) {
         const int TX = c.a - 2 * r, TY = c.b - 2 * r;
         gx = (w + TX - 1) / TX;
@@ -356,13 +365,13 @@ cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P
 }
 
 template <typename T>
-cudaError_t k1_batched_kernel_t(size_t smem, void** fn);
+cudaError_t k1_batched_kernel_t(int r, int mode, size_t smem, void** fn);
 
-cudaError_t k1_batched_kernel(dgf_dtype dt, size_t smem, void** fn) {
+cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn) {
     switch (dt) {
-        case DGF_F32: return k1_batched_kernel_t<float>(smem, fn);
-        case DGF_BF16: return k1_batched_kernel_t<__nv_bfloat16>(smem, fn);
-        case DGF_F16: return k1_batched_kernel_t<__half>(smem, fn);
+        case DGF_F32: return k1_batched_kernel_t<float>(r, mode, smem, fn);
+        case DGF_BF16: return k1_batched_kernel_t<__nv_bfloat16>(r, mode, smem, fn);
+        case DGF_F16: return k1_batched_kernel_t<__half>(r, mode, smem, fn);
     }
     return cudaErrorInvalidValue;
 }

@@ -325,7 +325,7 @@ __device__ void coef_tile_ring(const TG* __restrict__ G, const TP* __restrict__ 
 
 // Stage G, P and d Abar / N, d bbar / N (E2, zero outside the image), and
 // compute the tile shift K = mean of the in-image output pixels.
-template <typename TG, typename TP, int R, bool INT = false>
+template <typename TG, typename TP, int R, bool INT = false, bool SHIFT = true>
 __device__ __forceinline__ void bwd_stage_and_shift(const TG* __restrict__ G, const TP* __restrict__ P,
                                                     const float2* __restrict__ dcoef, const FastTile& t, float* sG,
                                                     float* sP, float* sDA, float* sDB, float* red, float& KG_out,
@@ -376,7 +376,7 @@ __device__ __forceinline__ void bwd_stage_and_shift(const TG* __restrict__ G, co
     __syncthreads();
     // tile shift K = mean of the in-image output pixels (conditioning only)
     float KG = 0.f, KP = 0.f;
-    {
+    if (SHIFT) {
         float sg = 0.f, sp = 0.f, cn = 0.f;
         const int cw = t.CW;
         const int c0 = threadIdx.x & (cw - 1), r0 = threadIdx.x >> t.log2cw, rstep = kLowThreads >> t.log2cw;
@@ -432,9 +432,13 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
     float* sDA = sP + EX2 * EY2;
     float* sDB = sDA + EX2 * EY2;
     float* sQ = sDB + EX2 * EY2;
-    float* red = sQ + kNQD * n1;
+    float* red = sQ + (R == 1 ? kNQD : kNQ) * n1;
+    // r = 1: every difference G_i - mu_m is formed exactly (9 windows per pixel);
+    // r = 2: the four separable window sums, with G and P shifted by the tile mean
+    constexpr bool DIRECT = (R == 1);
+    constexpr int NQ = DIRECT ? kNQD : kNQ;
     float KG, KP;
-    bwd_stage_and_shift<TG, TP, R, INT>(G, P, dcoef, t, sG, sP, sDA, sDB, red, KG, KP);
+    bwd_stage_and_shift<TG, TP, R, INT, !DIRECT>(G, P, dcoef, t, sG, sP, sDA, sDB, red, KG, KP);
     const int c = threadIdx.x & (t.CW - 1), rg = threadIdx.x >> t.log2cw;
     const int ngroups = kLowThreads >> t.log2cw;
     // ---- pass A
@@ -488,7 +492,9 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         hdb[slot] = b;
                     }
                     const int gy = t.ty0 - R + e1;
-                    float q[kNQD] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    float q[NQ];
+#pragma unroll
+                    for (int k = 0; k < NQ; ++k) q[k] = 0.f;
                     if (INT || (colin && gy >= 0 && gy < t.h)) {
                         const float ny = INT ? (float)W : (float)seg_count(gy, t.h, R);
                         const float iny = INT ? 1.f / (float)W : __frcp_rn(ny);
@@ -509,24 +515,81 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         const float beta = -gamma * A;
                         q[0] = gamma * inn;
                         q[1] = beta * inn;
-                        q[2] = mu;
-                        q[3] = nu;
-                        q[4] = db * inn;
-                        q[5] = db * A * inn;
+                        if constexpr (DIRECT) {
+                            q[2] = mu;
+                            q[3] = nu;
+                            q[4] = db * inn;
+                            q[5] = db * A * inn;
+                        } else {
+                            const float mus = mu - KG, nus = nu - KP;
+                            q[2] = fmaf(-gamma, mus, db) * inn;
+                            q[3] = fmaf(gamma, nus, fmaf(2.f * beta, mus, db * A)) * inn;
+                        }
                     }
 #pragma unroll
-                    for (int k = 0; k < kNQD; ++k) sQ[k * n1 + e1 * EX1 + c] = q[k];
+                    for (int k = 0; k < NQ; ++k) sQ[k * n1 + e1 * EX1 + c] = q[k];
                 }
             }
         }
     }
     __syncthreads();
+    // ---- pass B (r = 2): four separable window sums; dP = G' S0 + S2,
+    //   dG = P' S0 + 2 G' S1 - S3 (see kNQ)
+    if (!DIRECT && c < t.TX) {
+        const int gx = t.tx0 + c;
+        const int ya = (rg * t.TY) / ngroups, yb = ((rg + 1) * t.TY) / ngroups;
+        float hq[kNQ][W];
+#pragma unroll
+        for (int s = 0; s < 2 * R; ++s) {
+#pragma unroll
+            for (int m = 0; m < kNQ; ++m) {
+                const float* pq = sQ + m * n1 + (ya + s) * EX1 + c;
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < W; ++k) a += pq[k];
+                hq[m][s] = a;
+            }
+        }
+        for (int base = ya; base < yb; base += W) {
+#pragma unroll
+            for (int s = 0; s < W; ++s) {
+                const int y = base + s;
+                if (y < yb) {
+                    const int slot = (s + 2 * R) % W;
+#pragma unroll
+                    for (int m = 0; m < kNQ; ++m) {
+                        const float* pq = sQ + m * n1 + (y + 2 * R) * EX1 + c;
+                        float a = 0.f;
+#pragma unroll
+                        for (int k = 0; k < W; ++k) a += pq[k];
+                        hq[m][slot] = a;
+                    }
+                    const int gy = t.ty0 + y;
+                    if (INT || (gx < t.w && gy < t.h)) {
+                        float S[kNQ];
+#pragma unroll
+                        for (int m = 0; m < kNQ; ++m) {
+                            float a = 0.f;
+#pragma unroll
+                            for (int k = 0; k < W; ++k) a += hq[m][k];
+                            S[m] = a;
+                        }
+                        const int o = (y + 2 * R) * EX2 + c + 2 * R;
+                        const float g = sG[o] - KG, p = sP[o] - KP;
+                        const size_t go = (size_t)gy * t.w + gx;
+                        if (dP != nullptr) dP[go] = from_f32<TP>(fmaf(g, S[0], S[2]));
+                        if (dG != nullptr) dG[go] = from_f32<TD>(fmaf(p, S[0], fmaf(2.f * g, S[1], -S[3])));
+                    }
+                }
+            }
+        }
+    }
     // ---- pass B: exactly centred sums over the windows m containing pixel i,
     //   dP_i = sum gamma~_m (G_i - mu_m) + sum db~_m,
     //   dG_i = sum [gamma~_m (P_i - nu_m) + 2 beta~_m (G_i - mu_m)] - sum (db A)~_m,
     // (~ = divided by N_m).  The window data of the last 2R + 1 rows sit in a
     // register ring (W rows x W columns); only the two plain sums are separable.
-    if (c < t.TX) {
+    if (DIRECT && c < t.TX) {
         const int gx = t.tx0 + c;
         const int ya = (rg * t.TY) / ngroups, yb = ((rg + 1) * t.TY) / ngroups;
         float rg_[W][W], rb_[W][W], rm[W][W], rn[W][W], hd[W], he[W];

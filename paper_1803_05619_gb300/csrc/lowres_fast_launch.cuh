@@ -6,6 +6,7 @@
 
 #include "kernels.h"
 #include "lowres_fast.cuh"
+#include "lowres_strip.cuh"
 
 namespace dgf {
 
@@ -40,6 +41,26 @@ __global__ void __launch_bounds__(kLowThreads) k4_lowres_bwd_fast(const TG* __re
 }
 
 
+// Warp-strip K1 (R = 1, 2): warp w of the grid owns strip (w % nstrip) of
+// row segment (w / nstrip) % nseg of plane w / (nstrip nseg).
+template <typename TG, typename TP, int R>
+__global__ void __launch_bounds__(kStripWarps * 32) k1_coef_strip(const TG* __restrict__ G, const TP* __restrict__ P,
+                                                                   float2* __restrict__ coef, int h, int w, float eps,
+                                                                   int seg, int nstrip, int nseg, int planes) {
+    const int gw = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
+    if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
+    const int strip = gw % nstrip, rest = gw / nstrip;
+    const int sg = rest % nseg, plane = rest / nseg;
+    StripGeom s;
+    s.h = h;
+    s.w = w;
+    s.x0 = strip * (32 - 4 * R) - 2 * R;
+    s.y0 = sg * seg;
+    s.seg = seg;
+    const size_t hw = (size_t)h * w;
+    coef_strip<TG, TP, R>(G + plane * hw, P + plane * hw, coef + plane * hw, s, eps);
+}
+
 template <typename K>
 static inline cudaError_t fast_prep(K kernel, size_t smem) {
     if (smem > 48 * 1024)
@@ -50,6 +71,16 @@ static inline cudaError_t fast_prep(K kernel, size_t smem) {
 template <typename TG, typename TP, int R>
 static cudaError_t k1f_go(const void* G, const void* P, float2* coef, int planes, int h, int w, float eps,
                           const LowCfg& c, const TmaPair& tma, size_t smem, uint32_t* status, cudaStream_t s) {
+    if constexpr (R <= 2) {
+        if (c.fast == 2) {
+            const int seg = c.a, nstrip = (w + (32 - 4 * R) - 1) / (32 - 4 * R), nseg = (h + seg - 1) / seg;
+            const long long warps = (long long)nstrip * nseg * planes;
+            const int ctas = (int)((warps + kStripWarps - 1) / kStripWarps);
+            k1_coef_strip<TG, TP, R><<<ctas, kStripWarps * 32, 0, s>>>(
+                static_cast<const TG*>(G), static_cast<const TP*>(P), coef, h, w, eps, seg, nstrip, nseg, planes);
+            return cudaGetLastError();
+        }
+    }
     auto kern = k1_coef_fast<TG, TP, R>;
     cudaError_t e = fast_prep(kern, smem);
     if (e != cudaSuccess) return e;

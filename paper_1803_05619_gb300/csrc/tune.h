@@ -9,8 +9,8 @@ namespace dgf {
 
 // kind: 1 = K1 low-res coefficients, 2 = K2 high-res apply, 3 = K3 high-res
 // backward, 4 = K4 low-res backward.  The value (a, b) is the kernel's
-// shape: K1/K4 (fast, a, b) packed as a = CW (or TY) and b = EY1 (or TX),
-// with b negative never stored; K2: a = rows per tile; K3: a = low-res rows.
+// shape: K1/K4 tiles as a = CW and b = EY1; K1 warp strips as a = rows per
+// segment and b = 0; K2: a = rows per tile; K3: a = low-res rows.
 struct TuneKey {
     int kind, dt, r, F, vec, gf32;
 };

@@ -96,7 +96,60 @@ def test_autograd_function_matches_oracle():
     assert_grad(f64(ih.grad), rIh, F32, "dI_h")
 
 
-def test_tma_and_plain_staging_identical():
+@pytest.fixture
+def pin():
+    """Pin autotuner table entries for one test; the table is cleared after."""
+    L.dgf_autotune_reset()
+    yield lambda *args: L.check(L.dgf_autotune_pin(*args))
+    L.dgf_autotune_reset()
+
+
+# K1 kernel forms for r <= 2: warp strips (a = rows per segment, b = 0) and
+# column-walking tiles (a = columns, b = rows of the coefficient region)
+K1_FORMS = [(1, 16, 0), (1, 64, 0), (1, 64, 32), (1, 128, 16), (2, 32, 0), (2, 16, 0), (2, 64, 32),
+            (2, 128, 64)]
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("form", K1_FORMS, ids=_ids(K1_FORMS))
+def test_k1_forms_match_oracle(form, dtype, pin):
+    r, a, b = form
+    dt = L.DGF_F32 if dtype == F32 else L.DGF_BF16
+    pin(1, dt, r, 0, 0, 0, a, b)
+    # ragged against strips of 28 / 24 columns and segments of 16..64 rows
+    st = to_storage(make_case("photo", 30 + r, 1, 2, 77, 131, 308, 524), dtype)
+    R = synth.upstream_grad(31, st["I_h"].shape).to(dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    out = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, 1e-3)
+    dp, dIl, dIh, _ = gf_backward(R.cuda(), g["p_l"], g["I_l"], g["I_h"], r, 1e-3)
+    torch.cuda.synchronize()
+    assert_fwd(f64(out), oracle_forward(st, r, 1e-3), dtype, 1e-3)
+    rp, rIl, rIh = oracle_backward(R, st, r, 1e-3)
+    assert_grad(f64(dp), rp, dtype, "dp_l")
+    assert_grad(f64(dIl), rIl, dtype, "dI_l")
+    assert_grad(f64(dIh), rIh, dtype, "dI_h")
+    assert L.dgf_device_status() == 0
+
+
+def test_autotune_pin_rejects_bad_keys():
+    with pytest.raises(L.DGFError):
+        L.check(L.dgf_autotune_pin(0, L.DGF_F32, 1, 0, 0, 0, 64, 32))
+    with pytest.raises(L.DGFError):
+        L.check(L.dgf_autotune_pin(1, L.DGF_F32, 1, 0, 0, 0, -4, 32))
+
+
+def test_unbuilt_pinned_shape_falls_back_to_default(pin):
+    st = to_storage(make_case("photo", 5, 1, 1, 40, 52, 160, 208), F32)
+    g = {k: v.cuda() for k, v in st.items()}
+    ref = gf_forward(g["p_l"], g["I_l"], g["I_h"], 1, 1e-3)
+    pin(1, L.DGF_F32, 1, 0, 0, 0, 100, 7)  # not a built shape: ignored at plan time
+    out = gf_forward(g["p_l"], g["I_l"], g["I_h"], 1, 1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+
+
+def test_tma_and_plain_staging_identical(pin):
+    pin(1, L.DGF_BF16, 2, 0, 0, 0, 64, 32)  # tile form (the one that stages by TMA)
     st = to_storage(make_case("photo", 3, 2, 3, 64, 96, 256, 384), BF16)
     g = {k: v.cuda() for k, v in st.items()}
     L.dgf_set_tma(True)
@@ -143,8 +196,13 @@ def test_constant_target_gives_constant_output():
     assert torch.all(out == 0.5)
 
 
+@pytest.mark.parametrize("k1_form", ["default", "tiles"])
 @pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
-def test_batched_matches_single_bitwise(dtype):
+def test_batched_matches_single_bitwise(dtype, k1_form, pin):
+    if k1_form == "tiles":
+        dt = L.DGF_F32 if dtype == F32 else L.DGF_BF16
+        pin(1, dt, 1, 0, 0, 0, 64, 32)
+        pin(1, dt, 2, 0, 0, 0, 128, 32)
     specs = synth.mixed_sizes(seed=3, n=9, long_lo=96, long_hi=520)
     images = []
     for i, s in enumerate(specs):
