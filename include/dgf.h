@@ -43,9 +43,11 @@
  *            gives a message for the calling thread's last non-OK status.
  *            No entry point aborts, traps or prints.
  * Sizes:     1 <= h_l <= h and 1 <= w_l <= w; the scale is the size ratio,
- *            so non-integer ratios are accepted.  r >= 0, eps > 0 and
- *            finite, N >= 0, C >= 1 (C = 3 when a guidance transform is
- *            given).  N = 0 is a valid empty call.
+ *            so non-integer ratios are accepted.  r >= 0, eps finite and
+ *            at least FLT_MIN (the smallest normal float; 1/(var + eps) is
+ *            taken with the hardware's approximate reciprocal), N >= 0,
+ *            C >= 1 (C = 3 when a guidance transform is given).  N = 0 is a
+ *            valid empty call.
  */
 #ifndef DGF_H
 #define DGF_H
@@ -200,7 +202,7 @@ void dgf_autotune_reset(void);
  *     F = vec = 0; guide_f32 = 1 for the guidance-transform path (FP32 guide);
  *     tiles: a = columns, b = rows of the coefficient region (a power of two
  *     in {64, 128, 256} and one of {16, 32, 64}); K1 with r <= 2 also takes
- *     warp strips: a = rows per segment in {16, 32, 64}, b = 0.
+ *     warp strips: a = rows per segment in {8, 16, 32, 64, 128}, b = 0.
  *   kind 2 (K2 high-res apply): r = 0, F = integer factor (0: non-integer),
  *     vec = elements per vector; a = high-res rows per tile, b = 0.
  *   kind 3 (K3 high-res backward): as kind 2; a = low-res rows per tile.

@@ -8,6 +8,7 @@
 #include <array>
 #include <atomic>
 #include <tuple>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -146,7 +147,7 @@ static Layout layout(int N, int C, int h_l, int w_l, bool guided) {
     return L;
 }
 
-static bool bad_eps(float eps) { return !(eps > 0.f) || !std::isfinite(eps); }
+static bool bad_eps(float eps) { return !(eps >= FLT_MIN) || !std::isfinite(eps); }
 
 static int integer_factor(int h_l, int w_l, int h, int w) {
     if (h % h_l != 0 || w % w_l != 0) return 0;
@@ -275,7 +276,7 @@ static std::vector<LowCfg> low_candidates(int r, bool k4) {
     std::vector<LowCfg> v;
     if (!low_fast_radius(r)) return v;
     if (!k4 && r <= 2)
-        for (int seg : {16, 32, 64}) v.push_back(LowCfg{2, seg, 0});
+        for (int seg : {8, 16, 32, 64, 128}) v.push_back(LowCfg{2, seg, 0});
     static const int cws[] = {64, 128, 256};
     static const int eys[] = {16, 32, 64};
     for (int cw : cws)
@@ -398,7 +399,7 @@ static dgf_status check_sizes(int N, int C, int h_l, int w_l, int h, int w, int 
     if (h_l > h || w_l > w) return fail(DGF_ERR_INVALID, "low-res %dx%d larger than high-res %dx%d", h_l, w_l, h, w);
     if (r < 0) return fail(DGF_ERR_INVALID, "radius r = %d < 0", r);
     if (r > kMaxRadius) return fail(DGF_ERR_UNSUPPORTED, "radius r = %d > %d", r, kMaxRadius);
-    if (bad_eps(eps)) return fail(DGF_ERR_INVALID, "eps must be finite and > 0");
+    if (bad_eps(eps)) return fail(DGF_ERR_INVALID, "eps must be finite and >= FLT_MIN (the smallest normal float)");
     if ((long long)N * C > 65535) return fail(DGF_ERR_UNSUPPORTED, "N*C = %lld planes > 65535", (long long)N * C);
     if ((long long)h * w >= (1LL << 40)) return fail(DGF_ERR_UNSUPPORTED, "plane too large");
     return DGF_OK;

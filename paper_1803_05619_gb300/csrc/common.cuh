@@ -12,6 +12,32 @@ namespace dgf {
 constexpr int kThreads = 256;  // threads per CTA of every tiled kernel
 constexpr int kWarps = kThreads / 32;
 
+// ------------------------------------------------------------ reciprocals
+// 1/x from the special-function unit (PTX rcp.approx.ftz.f32: relative error
+// within about one unit in the last place; subnormal arguments flush to
+// zero).  Used for 1/(var + eps): var >= 0 and eps >= FLT_MIN (checked at the
+// entry points) keep the argument normal.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Correctly rounded 1/k for window counts k = 1 .. kInvCountMax (the largest
+// clipped window, (2 r + 1)^2 at r = 16), built by the compiler.  Entry 0 is
+// unused.  Window counts come from integer clipping, so a table load replaces
+// a division.
+constexpr int kInvCountMax = 33 * 33;
+struct InvCountTable {
+    float v[kInvCountMax + 1];
+    constexpr InvCountTable() : v() {
+        for (int k = 1; k <= kInvCountMax; ++k) v[k] = 1.f / (float)k;
+    }
+};
+static __constant__ InvCountTable kInvCount = InvCountTable();
+__device__ __forceinline__ float inv_count(int k) { return kInvCount.v[k]; }
+__device__ __forceinline__ float inv_countf(float k) { return kInvCount.v[(int)k]; }  // k integral
+
 // ---------------------------------------------------------------- storage
 template <typename T> __device__ __forceinline__ float to_f32(T v);
 template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }

@@ -228,7 +228,7 @@ __device__ void coef_tile_ring(const TG* __restrict__ G, const TP* __restrict__ 
             mk[k] = (INT || (x >= 0 && x < t.w)) ? 1.f : 0.f;
         }
         const float nx = INT ? (float)W : (colin ? (float)seg_count(gx, t.w, R) : 1.f);
-        const float inx = INT ? 1.f / (float)W : __frcp_rn(nx);
+        const float inx = INT ? 1.f / (float)W : inv_countf(nx);
         const int ra = (rg * t.EY1) / ngroups, rb = ((rg + 1) * t.EY1) / ngroups;
         float mg[W], mp[W], sgg[W], sgp[W], vr[W];
         // warm-up: E2 rows ra .. ra + 2R - 1 into slots 0 .. 2R - 1
@@ -257,10 +257,10 @@ __device__ void coef_tile_ring(const TG* __restrict__ G, const TP* __restrict__ 
                     if (INT || (colin && gy >= 0 && gy < t.h)) {
                         float mu, nu, var, cov;
                         const float ny = INT ? (float)W : (float)seg_count(gy, t.h, R);
-                        const float iny = INT ? 1.f / (float)W : __frcp_rn(ny);
-                        const float inn = INT ? 1.f / (float)(W * W) : __frcp_rn(nx * ny);
+                        const float iny = INT ? 1.f / (float)W : inv_countf(ny);
+                        const float inn = INT ? 1.f / (float)(W * W) : inv_countf(nx * ny);
                         fast_window<R>(mg, mp, sgg, sgp, vr, nx, iny, inn, mu, nu, var, cov);
-                        A = cov * __frcp_rn(var + t.eps);
+                        A = cov * rcp_approx(var + t.eps);
                         b = fmaf(-A, mu, nu);
                     }
                     sA[e1 * EX1 + c] = A;
@@ -313,7 +313,7 @@ __device__ void coef_tile_ring(const TG* __restrict__ G, const TP* __restrict__ 
                             sa += ha[k];
                             sb += hb[k];
                         }
-                        const float inn = INT ? 1.f / (float)(W * W) : __frcp_rn(nx * (float)seg_count(gy, t.h, R));
+                        const float inn = INT ? 1.f / (float)(W * W) : inv_countf(nx * (float)seg_count(gy, t.h, R));
                         coef[(size_t)gy * t.w + gx] = make_float2(sa * inn, sb * inn);
                     }
                 }
@@ -341,7 +341,7 @@ __device__ __forceinline__ void bwd_stage_and_shift(const TG* __restrict__ G, co
             if (INT || (gy >= 0 && gy < t.h && gx >= 0 && gx < t.w)) {
                 const float2 v = dcoef[(size_t)gy * t.w + gx];
                 const float inn = INT ? 1.f / (float)((2 * R + 1) * (2 * R + 1))
-                                      : __frcp_rn((float)seg_count(gy, t.h, R) * (float)seg_count(gx, t.w, R));
+                                      : inv_countf((float)seg_count(gy, t.h, R) * (float)seg_count(gx, t.w, R));
                 return make_float2(v.x * inn, v.y * inn);
             }
             return make_float2(0.f, 0.f);
@@ -452,7 +452,7 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
             mk[k] = (INT || (x >= 0 && x < t.w)) ? 1.f : 0.f;
         }
         const float nx = INT ? (float)W : (colin ? (float)seg_count(gx, t.w, R) : 1.f);
-        const float inx = INT ? 1.f / (float)W : __frcp_rn(nx);
+        const float inx = INT ? 1.f / (float)W : inv_countf(nx);
         const int ra = (rg * t.EY1) / ngroups, rb = ((rg + 1) * t.EY1) / ngroups;
         float mg[W], mp[W], sgg[W], sgp[W], vr[W], hda[W], hdb[W];
 #pragma unroll
@@ -497,12 +497,12 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                     for (int k = 0; k < NQ; ++k) q[k] = 0.f;
                     if (INT || (colin && gy >= 0 && gy < t.h)) {
                         const float ny = INT ? (float)W : (float)seg_count(gy, t.h, R);
-                        const float iny = INT ? 1.f / (float)W : __frcp_rn(ny);
-                        const float inn = INT ? 1.f / (float)(W * W) : __frcp_rn(nx * ny);
+                        const float iny = INT ? 1.f / (float)W : inv_countf(ny);
+                        const float inn = INT ? 1.f / (float)(W * W) : inv_countf(nx * ny);
                         float mu, nu, var, cov;
                         fast_window<R>(mg, mp, sgg, sgp, vr, nx, iny, inn, mu, nu, var, cov);
                         const float ve = var + t.eps;
-                        const float ive = __frcp_rn(ve);
+                        const float ive = rcp_approx(ve);
                         const float A = cov * ive;
                         float dA = 0.f, db = 0.f;
 #pragma unroll
@@ -662,7 +662,7 @@ __device__ __forceinline__ void fast_col_setup(const FastTile& t, int c, float (
         mk[k] = (x >= 0 && x < t.w) ? 1.f : 0.f;
     }
     nx = colin ? (float)seg_count(gx, t.w, R) : 1.f;
-    inx = __frcp_rn(nx);
+    inx = inv_countf(nx);
 }
 
 // Window moments of E1 row e1, column c, from the row statistics stored in
@@ -684,7 +684,7 @@ __device__ __forceinline__ void staged_window(const float* H, int plane_stride, 
         a += hgg[o];
         cc += hgp[o];
     }
-    const float iny = __frcp_rn(ny);
+    const float iny = inv_countf(ny);
     mu = s1 * iny;
     nu = s2 * iny;
     float dgg = 0.f, dgp = 0.f;
@@ -697,7 +697,7 @@ __device__ __forceinline__ void staged_window(const float* H, int plane_stride, 
         dgg = fmaf(dg, dg, dgg);
         dgp = fmaf(dg, hmp[o] - nu, dgp);
     }
-    const float inn = __frcp_rn(nx * ny);
+    const float inn = inv_countf(nx * ny);
     var = fmaf(nx, dgg, a) * inn;
     cov = fmaf(nx, dgp, cc) * inn;
 }
@@ -742,7 +742,7 @@ __device__ void coef_tile_staged(const TG* __restrict__ G, const TP* __restrict_
         if (colin && gy >= 0 && gy < t.h) {
             float mu, nu, var, cov;
             staged_window<R>(H, hs, CW, e1, c, t, nx, (float)seg_count(gy, t.h, R), mu, nu, var, cov);
-            A = cov * __frcp_rn(var + t.eps);
+            A = cov * rcp_approx(var + t.eps);
             b = fmaf(-A, mu, nu);
         }
         sA[e1 * CW + c] = A;
@@ -776,7 +776,7 @@ __device__ void coef_tile_staged(const TG* __restrict__ G, const TP* __restrict_
                 sa += HA[(y + k) * CW + c];
                 sb += HB[(y + k) * CW + c];
             }
-            const float inn = __frcp_rn(nx0 * (float)seg_count(gy, t.h, R));
+            const float inn = inv_countf(nx0 * (float)seg_count(gy, t.h, R));
             coef[(size_t)gy * t.w + gx] = make_float2(sa * inn, sb * inn);
         }
     }
@@ -829,7 +829,7 @@ __device__ void lowres_bwd_tile_staged(const TG* __restrict__ G, const TP* __res
             float mu, nu, var, cov;
             staged_window<R>(H, hs, CW, e1, c, t, nx, ny, mu, nu, var, cov);
             const float ve = var + t.eps;
-            const float ive = __frcp_rn(ve);
+            const float ive = rcp_approx(ve);
             const float A = cov * ive;
             float dA = 0.f, db = 0.f;
 #pragma unroll
@@ -840,7 +840,7 @@ __device__ void lowres_bwd_tile_staged(const TG* __restrict__ G, const TP* __res
             const float alpha = fmaf(-db, mu, dA);
             const float gamma = alpha * ive;
             const float beta = -gamma * A;
-            const float inn = __frcp_rn(nx * ny);
+            const float inn = inv_countf(nx * ny);
             const float mus = mu - KG, nus = nu - KP;
             q[0] = gamma * inn;
             q[1] = beta * inn;

@@ -5,10 +5,16 @@
 // from the neighbouring lanes by warp shuffles, vertical window terms from a
 // register ring of the last 2R + 1 rows (the walk is unrolled by 2R + 1 so
 // every ring slot is a fixed register).  No shared memory, no barriers: the
-// row loads of a whole ring period are issued before that period is
+// row loads of the next ring period are issued before the current one is
 // processed.  Lanes [2R, 32 - 2R) produce outputs; the 2R lanes on each side
 // are the strip's halo (neighbouring strips overlap by 4R columns), and the
 // first 4R rows of a segment only fill the rings.
+//
+// A ring period whose rows and columns are all far enough from the image
+// border takes the interior form: every window is full, so the masks and
+// clipped counts drop out and the counts' reciprocals are constants.  Both
+// forms use the same correctly rounded count reciprocals, so a pixel's result
+// does not depend on which form produced it.
 //
 // Statistics are exactly centred as in the tile kernels: each row segment is
 // centred on its own mean and rows are combined with Chan's update.
@@ -40,6 +46,111 @@ struct StripGeom {
     int seg;      // output rows of the segment
 };
 
+// Register rings of one strip: level 1 holds per-row statistics of the last
+// 2R + 1 input rows, level 2 the horizontal box sums of A, b of the last
+// 2R + 1 window rows.
+template <int R>
+struct StripRing {
+    static constexpr int W = 2 * R + 1;
+    float mg[W], mp[W], sgg[W], sgp[W], vr[W], ha[W], hb[W];
+};
+
+// Per-lane facts of the generic form (columns clipped at the image border).
+template <int R>
+struct StripLane {
+    float mk[2 * R + 1];  // 1 where column x - R + k is inside the image
+    int nx;               // clipped window width at this lane's column
+    bool xin, out;        // column inside the image; lane writes an output
+};
+
+// One input row e entering ring slot U.  INT: interior ring period (all rows
+// and columns of every window touched are inside the image and complete).
+template <typename TG, typename TP, int R, bool INT>
+__device__ __forceinline__ void strip_k1_row(StripRing<R>& q, const StripLane<R>& ln, int U, float gvu, float pvu,
+                                             int e, int e_first, int x, float2* __restrict__ coef,
+                                             const StripGeom& s, float eps) {
+    constexpr int W = 2 * R + 1;
+    constexpr float kInvW = 1.f / (float)W;
+    constexpr float kInvW2 = 1.f / (float)(W * W);
+    const int lane = threadIdx.x & 31;
+    // ---- level 1: centred statistics of row e over this lane's window columns
+    float g[W], p[W];
+    g[R] = gvu;
+    p[R] = pvu;
+#pragma unroll
+    for (int d = 1; d <= R; ++d) {
+        g[R - d] = shfl_up(gvu, d);
+        g[R + d] = shfl_dn(gvu, d);
+        p[R - d] = shfl_up(pvu, d);
+        p[R + d] = shfl_dn(pvu, d);
+    }
+    float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        s1 += g[k];
+        s2 += p[k];
+    }
+    const float inx = INT ? kInvW : inv_count(ln.nx);
+    const float m1 = s1 * inx, m2 = s2 * inx;
+    float a = 0.f, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const float dg = INT ? g[k] - m1 : ln.mk[k] * (g[k] - m1);
+        a = fmaf(dg, dg, a);
+        c = fmaf(dg, p[k] - m2, c);
+    }
+    q.mg[U] = m1;
+    q.mp[U] = m2;
+    q.sgg[U] = a;
+    q.sgp[U] = c;
+    q.vr[U] = (INT || (e >= 0 && e < s.h)) ? 1.f : 0.f;
+    // ---- Eq. 1's A, b of window row ce = e - R (rows ce - R .. ce + R = level 1)
+    const int ce = e - R;
+    float A = 0.f, b = 0.f;
+    if (INT || (ln.xin && ce >= 0 && ce < s.h && e - e_first >= 2 * R)) {
+        const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
+        float t1 = 0.f, t2 = 0.f, ta = 0.f, tc = 0.f;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            t1 += q.mg[k];
+            t2 += q.mp[k];
+            ta += q.sgg[k];
+            tc += q.sgp[k];
+        }
+        const float iny = INT ? kInvW : inv_count(ny);
+        const float mu = t1 * iny, nu = t2 * iny;
+        float dgg = 0.f, dgp = 0.f;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const float dg = INT ? q.mg[k] - mu : q.vr[k] * (q.mg[k] - mu);
+            dgg = fmaf(dg, dg, dgg);
+            dgp = fmaf(dg, q.mp[k] - nu, dgp);
+        }
+        const float nxf = INT ? (float)W : (float)ln.nx;
+        const float inn = INT ? kInvW2 : inv_count(ln.nx * ny);
+        const float var = fmaf(nxf, dgg, ta) * inn;
+        const float cov = fmaf(nxf, dgp, tc) * inn;
+        A = cov * rcp_approx(var + eps);
+        b = fmaf(-A, mu, nu);
+    }
+    // ---- level 2: horizontal box sums of A, b, then the vertical sum over the ring
+    q.ha[U] = hsum<R>(A);
+    q.hb[U] = hsum<R>(b);
+    const int co = ce - R;  // output row; level 2 holds window rows co - R .. co + R
+    const bool write = INT ? (lane >= 2 * R && lane < 32 - 2 * R)
+                           : (ln.out && co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
+    if (write) {
+        float sa = 0.f, sb = 0.f;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            sa += q.ha[k];
+            sb += q.hb[k];
+        }
+        const float inn = INT ? kInvW2 : inv_count(ln.nx * (min(co + R, s.h - 1) - max(co - R, 0) + 1));
+        coef[(size_t)co * s.w + x] = make_float2(sa * inn, sb * inn);
+    }
+}
+
 // ------------------------------------------------------------------- K1
 // Eq. 1's least-squares A, b per clipped window, then their box mean, for
 // one strip segment.  Writes Abar, bbar for lanes [2R, 32 - 2R).
@@ -49,111 +160,54 @@ __device__ void coef_strip(const TG* __restrict__ G, const TP* __restrict__ P, f
     constexpr int W = 2 * R + 1;
     const int lane = threadIdx.x & 31;
     const int x = s.x0 + lane;
-    const bool xin = x >= 0 && x < s.w;
-    // column facts of this lane's window (same for every row)
-    float mk[W];
+    StripLane<R> ln;
+    ln.xin = x >= 0 && x < s.w;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
         const int xx = x - R + k;
-        mk[k] = (xx >= 0 && xx < s.w) ? 1.f : 0.f;
+        ln.mk[k] = (xx >= 0 && xx < s.w) ? 1.f : 0.f;
     }
-    const float nx = xin ? (float)(min(x + R, s.w - 1) - max(x - R, 0) + 1) : 1.f;
-    const float inx = __frcp_rn(nx);
-    const bool out_lane = lane >= 2 * R && lane < 32 - 2 * R && xin;
-    // level-1 ring: row statistics of input rows; level-2 ring: horizontal box sums of A, b
-    float mg[W], mp[W], sgg[W], sgp[W], vr[W], ha[W], hb[W];
+    ln.nx = ln.xin ? min(x + R, s.w - 1) - max(x - R, 0) + 1 : 1;
+    ln.out = lane >= 2 * R && lane < 32 - 2 * R && ln.xin;
+    const bool cols_int = s.x0 >= 0 && s.x0 + 32 <= s.w;  // warp-uniform
+    StripRing<R> q;
 #pragma unroll
-    for (int k = 0; k < W; ++k) mg[k] = mp[k] = sgg[k] = sgp[k] = vr[k] = ha[k] = hb[k] = 0.f;
-    // input row e enters ring 1 in slot (e - e_first) % W; the window of row
-    // c = e - R is then complete, and its A, b enter ring 2 in slot (c - c_first) % W;
-    // the output row c - R is complete after that.
+    for (int k = 0; k < W; ++k) q.mg[k] = q.mp[k] = q.sgg[k] = q.sgp[k] = q.vr[k] = q.ha[k] = q.hb[k] = 0.f;
+    // input row e enters level 1 in slot (e - e_first) % W; the window of row
+    // e - R is then complete and enters level 2 in the same slot; the output
+    // row e - 2R is complete after that.
     const int e_first = s.y0 - 2 * R;
-    const int e_last = s.y0 + s.seg + 2 * R;  // exclusive
+    const int e_last = min(s.y0 + s.seg, s.h) + 2 * R;  // exclusive
+    float gn[W], pn[W];
+    auto load = [&](int base) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const int e = base + u;
+            const bool ok = ln.xin && e >= 0 && e < s.h && e < e_last;
+            gn[u] = ok ? to_f32<TG>(G[(size_t)e * s.w + x]) : 0.f;
+            pn[u] = ok ? to_f32<TP>(P[(size_t)e * s.w + x]) : 0.f;
+        }
+    };
+    load(e_first);
     for (int base = e_first; base < e_last; base += W) {
         float gv[W], pv[W];
 #pragma unroll
         for (int u = 0; u < W; ++u) {
-            const int e = base + u;
-            const bool ok = xin && e >= 0 && e < s.h && e < e_last;
-            gv[u] = ok ? to_f32<TG>(G[(size_t)e * s.w + x]) : 0.f;
-            pv[u] = ok ? to_f32<TP>(P[(size_t)e * s.w + x]) : 0.f;
+            gv[u] = gn[u];
+            pv[u] = pn[u];
         }
+        if (base + W < e_last) load(base + W);  // next period in flight while this one computes
+        const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W <= s.h &&
+                             base + W <= e_last;
+        if (row_int) {
 #pragma unroll
-        for (int u = 0; u < W; ++u) {
-            const int e = base + u;
-            if (e >= e_last) break;  // uniform across the warp
-            // ---- level 1: row statistics of input row e at this lane's column
-            float g[W], p[W];
-            g[R] = gv[u];
-            p[R] = pv[u];
+            for (int u = 0; u < W; ++u)
+                strip_k1_row<TG, TP, R, true>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, s, eps);
+        } else {
 #pragma unroll
-            for (int d = 1; d <= R; ++d) {
-                g[R - d] = shfl_up(gv[u], d);
-                g[R + d] = shfl_dn(gv[u], d);
-                p[R - d] = shfl_up(pv[u], d);
-                p[R + d] = shfl_dn(pv[u], d);
-            }
-            float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                s1 += g[k];
-                s2 += p[k];
-            }
-            const float m1 = s1 * inx, m2 = s2 * inx;
-            float a = 0.f, c = 0.f;
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const float dg = mk[k] * (g[k] - m1);
-                a = fmaf(dg, dg, a);
-                c = fmaf(dg, p[k] - m2, c);
-            }
-            mg[u] = m1;
-            mp[u] = m2;
-            sgg[u] = a;
-            sgp[u] = c;
-            vr[u] = (e >= 0 && e < s.h) ? 1.f : 0.f;
-            // ---- window of row ce = e - R (rows ce - R .. ce + R = ring 1)
-            const int ce = e - R;
-            float A = 0.f, b = 0.f;
-            if (xin && ce >= 0 && ce < s.h && e - e_first >= 2 * R) {
-                const float ny = (float)(min(ce + R, s.h - 1) - max(ce - R, 0) + 1);
-                float t1 = 0.f, t2 = 0.f, ta = 0.f, tc = 0.f;
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    t1 += mg[k];
-                    t2 += mp[k];
-                    ta += sgg[k];
-                    tc += sgp[k];
-                }
-                const float iny = __frcp_rn(ny);
-                const float mu = t1 * iny, nu = t2 * iny;
-                float dgg = 0.f, dgp = 0.f;
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    const float dg = vr[k] * (mg[k] - mu);
-                    dgg = fmaf(dg, dg, dgg);
-                    dgp = fmaf(dg, mp[k] - nu, dgp);
-                }
-                const float inn = __frcp_rn(nx * ny);
-                const float var = fmaf(nx, dgg, ta) * inn;
-                const float cov = fmaf(nx, dgp, tc) * inn;
-                A = cov * __frcp_rn(var + eps);
-                b = fmaf(-A, mu, nu);
-            }
-            // ---- level 2: horizontal box sums of A, b; ring 2 over rows ce
-            ha[u] = hsum<R>(A);
-            hb[u] = hsum<R>(b);
-            const int co = ce - R;  // output row, complete once ring 2 holds rows co - R .. co + R
-            if (out_lane && co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R) {
-                float sa = 0.f, sb = 0.f;
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    sa += ha[k];
-                    sb += hb[k];
-                }
-                const float n = nx * (float)(min(co + R, s.h - 1) - max(co - R, 0) + 1);
-                const float inn = __frcp_rn(n);
-                coef[(size_t)co * s.w + x] = make_float2(sa * inn, sb * inn);
+            for (int u = 0; u < W; ++u) {
+                if (base + u >= e_last) break;  // uniform across the warp
+                strip_k1_row<TG, TP, R, false>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, s, eps);
             }
         }
     }
