@@ -205,7 +205,8 @@ void dgf_autotune_reset(void);
  *     warp strips: a = rows per segment in {8, 16, 32, 64, 128}, b = 0.
  *   kind 2 (K2 high-res apply): r = 0, F = integer factor (0: non-integer),
  *     vec = elements per vector; a = high-res rows per tile, b = 0.
- *   kind 3 (K3 high-res backward): as kind 2; a = low-res rows per tile.
+ *   kind 3 (K3 high-res backward): as kind 2; a = low-res rows per segment
+ *     of a warp strip (1 .. 256).
  * A shape the kernels are not built for is stored but ignored at plan time
  * (the default shape is used).  Returns DGF_ERR_INVALID for a key or shape
  * outside these ranges.  No counterpart in the paper: tuning machinery.

@@ -206,8 +206,7 @@ static bool pick_lowres_tiles(int r, Plan& p) {
     bool ok1 = false, ok4 = false;
     if (low_fast_radius(r)) {
         const LowCfg k1 = r <= 2 ? LowCfg{2, 32, 0} : LowCfg{1, 128, 32};
-        const LowCfg k4 = r == 1 ? LowCfg{1, 64, 16} : (r == 2 ? LowCfg{1, 64, 32}
-                                                              : (r == 4 ? LowCfg{1, 128, 16} : LowCfg{1, 64, 32}));
+        const LowCfg k4 = r <= 2 ? LowCfg{2, 32, 0} : (r == 4 ? LowCfg{1, 128, 16} : LowCfg{1, 64, 32});
         if (k1_cfg_smem(k1, r, 0) <= lim) {
             p.k1 = k1;
             ok1 = true;
@@ -235,7 +234,8 @@ static bool pick_lowres_tiles(int r, Plan& p) {
     return ok1 && ok4;
 }
 
-static int default_k3_lth(int F) { return F >= 8 ? 4 : (F >= 4 ? 8 : 16); }
+// K3 strip segments: low-res rows per segment
+static int default_k3_lth(int) { return 32; }
 
 static std::vector<LowCfg> low_candidates(int r, bool k4);
 static bool in_candidates(const LowCfg& c, int r, bool k4) {
@@ -262,12 +262,13 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
             const LowCfg c{b == 0 ? 2 : 1, a, b};
             if (in_candidates(c, r, false)) p.k1 = c;
         }
-        if (tune_lookup(TuneKey{4, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b) && in_candidates(LowCfg{1, a, b}, r, true))
-            p.k4 = LowCfg{1, a, b};
+        if (tune_lookup(TuneKey{4, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b)) {
+            const LowCfg c{b == 0 ? 2 : 1, a, b};
+            if (in_candidates(c, r, true)) p.k4 = c;
+        }
     }
     if (tune_lookup(TuneKey{2, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256) p.k2_th = a;
-    if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 64 &&
-        k3_smem_bytes(p.vec, p.F, a) <= smem_limit())
+    if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256)
         p.k3_lth = a;
     return p;
 }
@@ -275,7 +276,7 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
 static std::vector<LowCfg> low_candidates(int r, bool k4) {
     std::vector<LowCfg> v;
     if (!low_fast_radius(r)) return v;
-    if (!k4 && r <= 2)
+    if (r <= 2)
         for (int seg : {8, 16, 32, 64, 128}) v.push_back(LowCfg{2, seg, 0});
     static const int cws[] = {64, 128, 256};
     static const int eys[] = {16, 32, 64};
@@ -338,6 +339,20 @@ static bool make_tma(TmaPlane& tp, const void* base, CUtensorMapDataType ty, int
 static CUtensorMapDataType tma_type(dgf_dtype dt) {
     return dt == DGF_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                          : (dt == DGF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+}
+
+// K3's tensor maps (d O_h, I_h): box of one strip row (32 vec columns) x F
+// rows.  Only for 16-byte vectors; returns false (plain loads) otherwise or
+// when the maps cannot be made.
+static bool make_k3_maps(K3Maps& m, const void* R, const void* G, dgf_dtype dt, int planes, int h, int w, int vec,
+                         int F) {
+    if (!g_tma_allowed || F <= 0 || vec * (int)esize(dt) != 16) return false;
+    TmaPlane a, b;
+    if (!make_tma(a, R, tma_type(dt), (int)esize(dt), planes, h, w, 32 * vec, F, 0)) return false;
+    if (!make_tma(b, G, tma_type(dt), (int)esize(dt), planes, h, w, 32 * vec, F, 0)) return false;
+    m.r = a.map;
+    m.g = b.map;
+    return true;
 }
 
 // Box of one input for K1's halo tile.  Generic tiles start on a 16-byte
@@ -508,11 +523,12 @@ static void tune_k3(dgf_dtype dt, const float2* coef, const void* R, const void*
     if (tune_lookup(key, a, b)) return;
     float best = 1e30f;
     int bl = p.k3_lth;
-    const int d = default_k3_lth(p.F);
-    for (int lth : {d / 2, d, 2 * d}) {
-        if (lth < 1 || k3_smem_bytes(p.vec, p.F, lth) > smem_limit()) continue;
+    K3Maps maps;
+    const bool tma = make_k3_maps(maps, R, G, dt, planes, h, w, p.vec, p.F);
+    for (int lth : {8, 16, 32, 64}) {
         const float ms = time_launch(s, [&] {
-            return launch_k3(dt, coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, lth, s);
+            return launch_k3(dt, coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, lth,
+                             tma ? &maps : nullptr, status_ptr(), s);
         }, 3);
         if (ms > 0.f && ms < best) {
             best = ms;
@@ -707,8 +723,11 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
         }
         if (p.k3_fast) {
             if (tuning) tune_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, s, p);
+            K3Maps maps;
+            const bool tma = make_k3_maps(maps, dO_h, I_h, dt, planes, h, w, p.vec, p.F);
             e = L.run("k3_hires_bwd", [&] {
-                return launch_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, p.k3_lth, s);
+                return launch_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, p.k3_lth,
+                                 tma ? &maps : nullptr, status_ptr(), s);
             });
             if (e != cudaSuccess) return cuda_fail(e, "k3");
         } else {

@@ -4,6 +4,7 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "hires.cuh"
+#include "hires_strip.cuh"
 #include "kernels.h"
 
 namespace dgf {
@@ -18,17 +19,41 @@ __global__ void __launch_bounds__(kThreads) k2_apply(const float2* __restrict__ 
                                 w_l, h, w, blockIdx.y * TH, blockIdx.x * 32 * VEC, TH, pitch, sAB);
 }
 
+// K3 fast path: warp w of the grid owns strip (w % nstrip) of segment
+// (w / nstrip) % nseg (LS low-res rows each) of plane w / (nstrip nseg).
 template <typename T, int VEC, int F>
 __global__ void __launch_bounds__(kThreads) k3_hires_bwd(const float2* __restrict__ coef, const T* __restrict__ R,
                                                          const T* __restrict__ G, T* __restrict__ dG,
-                                                         float2* __restrict__ dcoef, int h_l, int w_l,
-                                                         int h, int w, int LTH) {
-    extern __shared__ __align__(128) float smem[];
-    const size_t plane = blockIdx.z;
+                                                         float2* __restrict__ dcoef, int h_l, int w_l, int h, int w,
+                                                         int LS, int nstrip, int nseg, int planes) {
+    const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
+    const int strip = gw % nstrip, rest = gw / nstrip;
+    const int sg = rest % nseg, plane = rest / nseg;
     const size_t hw = (size_t)h * w, lw = (size_t)h_l * w_l;
-    hires_bwd_tile<T, VEC, F>(coef + plane * lw, R + plane * hw, G + plane * hw,
-                              dG ? dG + plane * hw : nullptr, dcoef + plane * lw, h_l, w_l, h, w,
-                              blockIdx.y * LTH, blockIdx.x * K3Shape<VEC, F>::LTW, LTH, smem);
+    k3_strip<T, VEC, F>(coef + plane * lw, R + plane * hw, G + plane * hw, dG ? dG + plane * hw : nullptr,
+                        dcoef + plane * lw, h_l, w_l, h, w, strip, sg * LS, min(sg * LS + LS, h_l));
+}
+
+// K3 fast path with TMA staging (16-byte vectors): same decomposition,
+// WPC warps per CTA, each warp's blocks staged through its own slot ring.
+template <typename T, int VEC, int F>
+__global__ void __launch_bounds__(K3Tma<T, VEC, F>::WPC * 32)
+    k3_hires_bwd_tma(const float2* __restrict__ coef, const __grid_constant__ K3Maps maps, T* __restrict__ dG,
+                     float2* __restrict__ dcoef, int h_l, int w_l, int h, int w, int LS, int nstrip, int nseg,
+                     int planes, uint32_t* status) {
+    extern __shared__ __align__(1024) unsigned char k3ring[];
+    using B = K3Tma<T, VEC, F>;
+    const int warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * B::WPC + warp;
+    if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
+    const int strip = gw % nstrip, rest = gw / nstrip;
+    const int sg = rest % nseg, plane = rest / nseg;
+    const size_t hw = (size_t)h * w, lw = (size_t)h_l * w_l;
+    unsigned char* ring = k3ring + (size_t)warp * B::NSB * B::SLOT;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(k3ring + (size_t)B::WPC * B::NSB * B::SLOT) + warp * B::NSB;
+    k3_strip_tma<T, VEC, F>(coef + plane * lw, &maps, dG ? dG + plane * hw : nullptr, dcoef + plane * lw, h_l, w_l,
+                            h, w, strip, sg * LS, min(sg * LS + LS, h_l), plane, ring, bars, status);
 }
 
 // -------------------------------------------------- K3 general (any ratio)
@@ -109,16 +134,6 @@ size_t k2_smem_bytes(int vec, int F, int h_l, int h, int w_l, int w, int TH) {
     return (size_t)(TH + k2_raw_rows(F, h_l, h, TH)) * k2_pitch(vec, F, w_l, w) * sizeof(float2);
 }
 
-int k3_ltw(int vec, int F) {
-    const int K = vec / F;
-    return K == 1 ? 29 : 30 * K;
-}
-
-size_t k3_smem_bytes(int vec, int F, int LTH) {
-    const int SXP = k3_ltw(vec, F) + 2;
-    return (size_t)F * (LTH + 1) * SXP * sizeof(float2) + (size_t)(LTH + 2) * SXP * sizeof(float);
-}
-
 bool k3_fast_ok(int vec, int F) {
     return (vec == 8 && (F == 4 || F == 8)) || (vec == 4 && (F == 4 || F == 2)) ||
            (vec == 2 && F == 2);
@@ -181,43 +196,55 @@ cudaError_t launch_k2(dgf_dtype dt, int mode, const float2* coef, const void* in
 
 template <typename T, int VEC, int F>
 static cudaError_t k3_go(const float2* coef, const void* R, const void* G, void* dG, float2* dcoef,
-                         int planes, int h_l, int w_l, int h, int w, int LTH, cudaStream_t s) {
-    const size_t smem = k3_smem_bytes(VEC, F, LTH);
-    auto kern = k3_hires_bwd<T, VEC, F>;
-    cudaError_t e = prep(kern, smem);
-    if (e != cudaSuccess) return e;
-    constexpr int LTW = K3Shape<VEC, F>::LTW;
-    dim3 grid((w_l + LTW - 1) / LTW, (h_l + LTH - 1) / LTH, planes);
-    kern<<<grid, kThreads, smem, s>>>(coef, static_cast<const T*>(R), static_cast<const T*>(G),
-                                      static_cast<T*>(dG), dcoef, h_l, w_l, h, w, LTH);
+                         int planes, int h_l, int w_l, int h, int w, int LS, const K3Maps* maps, uint32_t* status,
+                         cudaStream_t s) {
+    constexpr int OUT = K3Strip<VEC, F>::OUT;
+    const int nstrip = (w_l + OUT - 1) / OUT, nseg = (h_l + LS - 1) / LS;
+    const long long warps = (long long)nstrip * nseg * planes;
+    if constexpr (VEC * sizeof(T) == 16) {
+        if (maps != nullptr) {
+            using B = K3Tma<T, VEC, F>;
+            auto kern = k3_hires_bwd_tma<T, VEC, F>;
+            cudaError_t e = prep(kern, B::CTA_BYTES);
+            if (e != cudaSuccess) return e;
+            const int ctas = (int)((warps + B::WPC - 1) / B::WPC);
+            kern<<<ctas, B::WPC * 32, B::CTA_BYTES, s>>>(coef, *maps, static_cast<T*>(dG), dcoef, h_l, w_l, h, w,
+                                                          LS, nstrip, nseg, planes, status);
+            return cudaGetLastError();
+        }
+    }
+    const int ctas = (int)((warps + kWarps - 1) / kWarps);
+    k3_hires_bwd<T, VEC, F><<<ctas, kThreads, 0, s>>>(coef, static_cast<const T*>(R), static_cast<const T*>(G),
+                                                      static_cast<T*>(dG), dcoef, h_l, w_l, h, w, LS, nstrip, nseg,
+                                                      planes);
     return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t k3_dispatch(const float2* coef, const void* R, const void* G, void* dG, float2* dcoef,
                                int planes, int h_l, int w_l, int h, int w, int vec, int F, int LTH,
-                               cudaStream_t s) {
-    if (sizeof(T) == 2) {
-        if (vec == 8 && F == 4) return k3_go<T, 8, 4>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
-        if (vec == 8 && F == 8) return k3_go<T, 8, 8>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
-        if (vec == 4 && F == 4) return k3_go<T, 4, 4>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
-        if (vec == 4 && F == 2) return k3_go<T, 4, 2>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
+                               const K3Maps* maps, uint32_t* status, cudaStream_t s) {
+    if constexpr (sizeof(T) == 2) {
+        if (vec == 8 && F == 4) return k3_go<T, 8, 4>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, maps, status, s);
+        if (vec == 8 && F == 8) return k3_go<T, 8, 8>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, maps, status, s);
+        if (vec == 4 && F == 4) return k3_go<T, 4, 4>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, maps, status, s);
+        if (vec == 4 && F == 2) return k3_go<T, 4, 2>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, maps, status, s);
     } else {
-        if (vec == 4 && F == 4) return k3_go<T, 4, 4>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
-        if (vec == 4 && F == 2) return k3_go<T, 4, 2>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
-        if (vec == 2 && F == 2) return k3_go<T, 2, 2>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, s);
+        if (vec == 4 && F == 4) return k3_go<T, 4, 4>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, maps, status, s);
+        if (vec == 4 && F == 2) return k3_go<T, 4, 2>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, maps, status, s);
+        if (vec == 2 && F == 2) return k3_go<T, 2, 2>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, LTH, maps, status, s);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_k3(dgf_dtype dt, const float2* coef, const void* R, const void* G, void* dG,
                       float2* dcoef, int planes, int h_l, int w_l, int h, int w, int vec, int F, int LTH,
-                      cudaStream_t s) {
+                      const K3Maps* maps, uint32_t* status, cudaStream_t s) {
     if (planes == 0) return cudaSuccess;
     switch (dt) {
-        case DGF_F32: return k3_dispatch<float>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, vec, F, LTH, s);
-        case DGF_BF16: return k3_dispatch<__nv_bfloat16>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, vec, F, LTH, s);
-        case DGF_F16: return k3_dispatch<__half>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, vec, F, LTH, s);
+        case DGF_F32: return k3_dispatch<float>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, vec, F, LTH, maps, status, s);
+        case DGF_BF16: return k3_dispatch<__nv_bfloat16>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, vec, F, LTH, maps, status, s);
+        case DGF_F16: return k3_dispatch<__half>(coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, vec, F, LTH, maps, status, s);
     }
     return cudaErrorInvalidValue;
 }

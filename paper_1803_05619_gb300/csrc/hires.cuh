@@ -250,119 +250,4 @@ __device__ __forceinline__ void k3_gather_columns(const float2* Sx, int i0, int 
     }
 }
 
-// Raw Abar rows the tile's interior high-res rows tap
-// (low-res rows i0-1 .. i0+LTH, columns j0-1 .. j0+LTW, clamped) into sRaw.
-template <int VEC, int F>
-__device__ __forceinline__ void k3_stage_abar(const float2* __restrict__ coef, int i0, int j0, int LTH,
-                                              int h_l, int w_l, float* sRaw) {
-    constexpr int SXP = K3Shape<VEC, F>::SXP;
-    // raw Abar rows i0-1 .. i0+LTH (clamped), columns j0-1 .. j0+LTW (clamped), loaded once
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = warp; rr < LTH + 2; rr += kWarps) {
-        const float2* src = coef + (size_t)clampi(i0 - 1 + rr, 0, h_l - 1) * w_l;
-        float v[(SXP + 31) / 32];
-#pragma unroll
-        for (int b = 0; b < (SXP + 31) / 32; ++b) {
-            const int c = lane + 32 * b;
-            if (c < SXP) v[b] = src[clampi(j0 - 1 + c, 0, w_l - 1)].x;
-        }
-#pragma unroll
-        for (int b = 0; b < (SXP + 31) / 32; ++b) {
-            const int c = lane + 32 * b;
-            if (c < SXP) sRaw[rr * SXP + c] = v[b];
-        }
-    }
-}
-
-// Abar_h of this lane's VEC pixels in high-res row y (interior rows only):
-// the K + 2 low-res columns the lane taps are interpolated along y first,
-// then each pixel along x.
-template <int VEC, int F>
-__device__ __forceinline__ void k3_abar_row(const float* sRaw, int y, int i0, int h_l, int lane, float (&A)[VEC]) {
-    using S = K3Shape<VEC, F>;
-    constexpr int K = S::K, SXP = S::SXP, NCOL = K + 2;
-    const int q = y % F, j = y / F, t2 = 2 * q + 1 - F;
-    const int yi0 = t2 < 0 ? j - 1 : j;
-    const float lamy = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
-    const float* r0 = sRaw + (clampi(yi0, 0, h_l - 1) - (i0 - 1)) * SXP + (lane - 1) * K;
-    const float* r1 = sRaw + (clampi(yi0 + 1, 0, h_l - 1) - (i0 - 1)) * SXP + (lane - 1) * K;
-    float v[NCOL];
-#pragma unroll
-    for (int cc = 0; cc < NCOL; ++cc) v[cc] = lerp(r0[cc], r1[cc], lamy);
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-        const int qx = k % F, t2x = 2 * qx + 1 - F;
-        const int cl = k / F + (t2x >= 0 ? 1 : 0);
-        const float lamx = (float)(t2x < 0 ? t2x + 2 * F : t2x) / (float)(2 * F);
-        A[k] = lerp(v[cl], v[cl + 1], lamx);
-    }
-}
-
-template <typename T, int VEC, int F>
-__device__ void hires_bwd_tile(const float2* __restrict__ coef, const T* __restrict__ R,
-                               const T* __restrict__ G, T* __restrict__ dG, float2* __restrict__ dcoef,
-                               int h_l, int w_l, int h, int w, int i0, int j0, int LTH, float* smem) {
-    using S = K3Shape<VEC, F>;
-    constexpr int K = S::K, H0 = S::H0, LTW = S::LTW, SXP = S::SXP;
-    constexpr int U = 5;  // footprint rows per warp held in flight (F (LTH + 1) <= 40 rows)
-    const int FR = F * (LTH + 1);
-    const int yf0 = F * (i0 - 1) + H0;
-    const int XS = F * j0 - VEC;
-    float2* Sx = reinterpret_cast<float2*>(smem);
-    float* sRaw = reinterpret_cast<float*>(Sx + FR * SXP);  // (LTH + 2) x SXP raw Abar rows
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int xs = XS + lane * VEC;
-    const bool col_ok = xs >= 0 && xs < w;
-    const bool interior = lane >= 1 && lane <= LTW / K;
-    Vec<T, VEC> rr[U], gg[U];
-    auto load_chunk = [&](int f0) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int fr = f0 + u * kWarps, y = yf0 + fr;
-            if (fr < FR && col_ok && y >= 0 && y < h) {
-                rr[u] = ldg_vec<T, VEC>(R + (size_t)y * w + xs);
-                gg[u] = ldg_vec<T, VEC>(G + (size_t)y * w + xs);
-            }
-        }
-    };
-    load_chunk(warp);  // first rows in flight before the staging below
-    if (dG != nullptr) {
-        // Abar along y for the interior rows, once per tile
-        k3_stage_abar<VEC, F>(coef, i0, j0, LTH, h_l, w_l, sRaw);
-        __syncthreads();
-    }
-    for (int f0 = warp; f0 < FR; f0 += kWarps * U) {
-        if (f0 != warp) load_chunk(f0);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int fr = f0 + u * kWarps, y = yf0 + fr;
-            if (fr < FR) {  // uniform across the warp: every lane takes part in the shuffles
-                const bool ok = col_ok && y >= 0 && y < h;
-                float rv[VEC], gv[VEC];
-                if (ok) {
-                    unpack_vec<T, VEC>(rr[u], rv);
-                    unpack_vec<T, VEC>(gg[u], gv);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < VEC; ++k) rv[k] = gv[k] = 0.f;
-                }
-                if (dG != nullptr && ok && interior && y >= F * i0 && y < F * (i0 + LTH)) {
-                    float A[VEC], o[VEC];
-                    k3_abar_row<VEC, F>(sRaw, y, i0, h_l, lane, A);
-#pragma unroll
-                    for (int k = 0; k < VEC; ++k) o[k] = rv[k] * A[k];
-                    store_vec<T, VEC>(dG + (size_t)y * w + xs, o);
-                }
-                float u2[VEC];
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) u2[k] = rv[k] * gv[k];
-                k3_row_to_smem<VEC, F>(u2, rv, lane, Sx + fr * SXP);
-            }
-        }
-    }
-    __syncthreads();
-    k3_gather_columns<VEC, F>(Sx, i0, j0, LTH, h_l, w_l, dcoef);
-    __syncthreads();
-}
-
 }  // namespace dgf

@@ -13,6 +13,7 @@
 namespace dgf {
 
 struct TmaPair;
+struct K3Maps;
 constexpr int kStripWarpsPerCta = 8;
 
 // Shared-memory pitch (float2 columns) of a K2 tile row.
@@ -41,8 +42,6 @@ size_t k1_cfg_smem(const LowCfg& c, int r, size_t tma_landing);
 size_t k4_cfg_smem(const LowCfg& c, int r);
 void low_grid(const LowCfg& c, int r, int h, int w, int& gx, int& gy);
 size_t k2_smem_bytes(int vec, int F, int h_l, int h, int w_l, int w, int TH);
-size_t k3_smem_bytes(int vec, int F, int LTH);
-int k3_ltw(int vec, int F);
 bool k3_fast_ok(int vec, int F);
 
 cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P, float2* coef, int planes,
@@ -54,8 +53,8 @@ cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P
 cudaError_t launch_k2(dgf_dtype dt, int mode, const float2* coef, const void* in, void* out, int planes,
                       int h_l, int w_l, int h, int w, int vec, int F, int TH, cudaStream_t s);
 cudaError_t launch_k3(dgf_dtype dt, const float2* coef, const void* R, const void* G, void* dG,
-                      float2* dcoef, int planes, int h_l, int w_l, int h, int w, int vec, int F, int LTH,
-                      cudaStream_t s);
+                      float2* dcoef, int planes, int h_l, int w_l, int h, int w, int vec, int F, int LS,
+                      const K3Maps* maps, uint32_t* status, cudaStream_t s);
 cudaError_t launch_k3_general(dgf_dtype dt, const void* R, const void* G, float2* dcoef, int planes,
                               int h_l, int w_l, int h, int w, cudaStream_t s);
 

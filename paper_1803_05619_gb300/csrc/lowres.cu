@@ -253,6 +253,7 @@ size_t k1_cfg_smem(const LowCfg& c, int r, size_t tma_landing) {
 }
 
 size_t k4_cfg_smem(const LowCfg& c, int r) {
+    if (c.fast == 2) return 0;
     return c.fast ? k4_fast_smem_bytes(r, c.a, c.b) : k4_smem_bytes(r, c.a, c.b);
 }
 

@@ -61,6 +61,27 @@ __global__ void __launch_bounds__(kStripWarps * 32) k1_coef_strip(const TG* __re
     coef_strip<TG, TP, R>(G + plane * hw, P + plane * hw, coef + plane * hw, s, eps);
 }
 
+// Warp-strip K4 (R = 1, 2), same work decomposition as k1_coef_strip.
+template <typename TG, typename TP, typename TD, int R>
+__global__ void __launch_bounds__(kStripWarps * 32)
+    k4_lowres_bwd_strip(const TG* __restrict__ G, const TP* __restrict__ P, const float2* __restrict__ dcoef,
+                        TP* __restrict__ dP, TD* __restrict__ dG, int h, int w, float eps, int seg, int nstrip,
+                        int nseg, int planes) {
+    const int gw = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
+    if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
+    const int strip = gw % nstrip, rest = gw / nstrip;
+    const int sg = rest % nseg, plane = rest / nseg;
+    StripGeom s;
+    s.h = h;
+    s.w = w;
+    s.x0 = strip * (32 - 4 * R) - 2 * R;
+    s.y0 = sg * seg;
+    s.seg = seg;
+    const size_t hw = (size_t)h * w;
+    lowres_bwd_strip<TG, TP, TD, R>(G + plane * hw, P + plane * hw, dcoef + plane * hw,
+                                    dP ? dP + plane * hw : nullptr, dG ? dG + plane * hw : nullptr, s, eps);
+}
+
 template <typename K>
 static inline cudaError_t fast_prep(K kernel, size_t smem) {
     if (smem > 48 * 1024)
@@ -110,6 +131,17 @@ cudaError_t launch_k1_fast(dgf_dtype dt, bool gf32, const void* G, const void* P
 template <typename TG, typename TP, typename TD, int R>
 static cudaError_t k4f_go(const void* G, const void* P, const float2* dcoef, void* dP, void* dG, int planes,
                           int h, int w, float eps, const LowCfg& c, cudaStream_t s) {
+    if constexpr (R <= 2) {
+        if (c.fast == 2) {
+            const int seg = c.a, nstrip = (w + (32 - 4 * R) - 1) / (32 - 4 * R), nseg = (h + seg - 1) / seg;
+            const long long warps = (long long)nstrip * nseg * planes;
+            const int ctas = (int)((warps + kStripWarps - 1) / kStripWarps);
+            k4_lowres_bwd_strip<TG, TP, TD, R><<<ctas, kStripWarps * 32, 0, s>>>(
+                static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef, static_cast<TP*>(dP),
+                static_cast<TD*>(dG), h, w, eps, seg, nstrip, nseg, planes);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = k4_fast_smem_bytes(R, c.a, c.b);
     auto kern = k4_lowres_bwd_fast<TG, TP, TD, R>;
     cudaError_t e = fast_prep(kern, smem);

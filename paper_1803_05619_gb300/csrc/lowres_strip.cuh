@@ -63,17 +63,45 @@ struct StripLane {
     bool xin, out;        // column inside the image; lane writes an output
 };
 
-// One input row e entering ring slot U.  INT: interior ring period (all rows
-// and columns of every window touched are inside the image and complete).
-template <typename TG, typename TP, int R, bool INT>
-__device__ __forceinline__ void strip_k1_row(StripRing<R>& q, const StripLane<R>& ln, int U, float gvu, float pvu,
-                                             int e, int e_first, int x, float2* __restrict__ coef,
-                                             const StripGeom& s, float eps) {
+// Centred statistics (mu, nu, var, cov) of the window of row ce = e - R
+// from the level-1 ring; ny = clipped window height.
+template <int R, bool INT>
+__device__ __forceinline__ void strip_window(const StripRing<R>& q, const StripLane<R>& ln, int ny, float& mu,
+                                             float& nu, float& var, float& cov) {
     constexpr int W = 2 * R + 1;
     constexpr float kInvW = 1.f / (float)W;
     constexpr float kInvW2 = 1.f / (float)(W * W);
-    const int lane = threadIdx.x & 31;
-    // ---- level 1: centred statistics of row e over this lane's window columns
+    float t1 = 0.f, t2 = 0.f, ta = 0.f, tc = 0.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        t1 += q.mg[k];
+        t2 += q.mp[k];
+        ta += q.sgg[k];
+        tc += q.sgp[k];
+    }
+    const float iny = INT ? kInvW : inv_count(ny);
+    mu = t1 * iny;
+    nu = t2 * iny;
+    float dgg = 0.f, dgp = 0.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const float dg = INT ? q.mg[k] - mu : q.vr[k] * (q.mg[k] - mu);
+        dgg = fmaf(dg, dg, dgg);
+        dgp = fmaf(dg, q.mp[k] - nu, dgp);
+    }
+    const float nxf = INT ? (float)W : (float)ln.nx;
+    const float inn = INT ? kInvW2 : inv_count(ln.nx * ny);
+    var = fmaf(nxf, dgg, ta) * inn;
+    cov = fmaf(nxf, dgp, tc) * inn;
+}
+
+// Level 1 for input row e: centred statistics of the row over this lane's
+// window columns, stored in ring slot U.
+template <int R, bool INT>
+__device__ __forceinline__ void strip_row_stats(StripRing<R>& q, const StripLane<R>& ln, int U, float gvu,
+                                                float pvu, bool row_in) {
+    constexpr int W = 2 * R + 1;
+    constexpr float kInvW = 1.f / (float)W;
     float g[W], p[W];
     g[R] = gvu;
     p[R] = pvu;
@@ -103,33 +131,42 @@ __device__ __forceinline__ void strip_k1_row(StripRing<R>& q, const StripLane<R>
     q.mp[U] = m2;
     q.sgg[U] = a;
     q.sgp[U] = c;
-    q.vr[U] = (INT || (e >= 0 && e < s.h)) ? 1.f : 0.f;
+    q.vr[U] = (INT || row_in) ? 1.f : 0.f;
+}
+
+// Per-lane facts of the generic form, for column x.
+template <int R>
+__device__ __forceinline__ StripLane<R> strip_lane(int x, int w) {
+    StripLane<R> ln;
+    const int lane = threadIdx.x & 31;
+    ln.xin = x >= 0 && x < w;
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) {
+        const int xx = x - R + k;
+        ln.mk[k] = (xx >= 0 && xx < w) ? 1.f : 0.f;
+    }
+    ln.nx = ln.xin ? min(x + R, w - 1) - max(x - R, 0) + 1 : 1;
+    ln.out = lane >= 2 * R && lane < 32 - 2 * R && ln.xin;
+    return ln;
+}
+
+// K1 for input row e entering ring slot U.  INT: interior ring period (all
+// rows and columns of every window touched are inside the image and complete).
+template <typename TG, typename TP, int R, bool INT>
+__device__ __forceinline__ void strip_k1_row(StripRing<R>& q, const StripLane<R>& ln, int U, float gvu, float pvu,
+                                             int e, int e_first, int x, float2* __restrict__ coef,
+                                             const StripGeom& s, float eps) {
+    constexpr int W = 2 * R + 1;
+    constexpr float kInvW2 = 1.f / (float)(W * W);
+    const int lane = threadIdx.x & 31;
+    strip_row_stats<R, INT>(q, ln, U, gvu, pvu, e >= 0 && e < s.h);
     // ---- Eq. 1's A, b of window row ce = e - R (rows ce - R .. ce + R = level 1)
     const int ce = e - R;
     float A = 0.f, b = 0.f;
     if (INT || (ln.xin && ce >= 0 && ce < s.h && e - e_first >= 2 * R)) {
         const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
-        float t1 = 0.f, t2 = 0.f, ta = 0.f, tc = 0.f;
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            t1 += q.mg[k];
-            t2 += q.mp[k];
-            ta += q.sgg[k];
-            tc += q.sgp[k];
-        }
-        const float iny = INT ? kInvW : inv_count(ny);
-        const float mu = t1 * iny, nu = t2 * iny;
-        float dgg = 0.f, dgp = 0.f;
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            const float dg = INT ? q.mg[k] - mu : q.vr[k] * (q.mg[k] - mu);
-            dgg = fmaf(dg, dg, dgg);
-            dgp = fmaf(dg, q.mp[k] - nu, dgp);
-        }
-        const float nxf = INT ? (float)W : (float)ln.nx;
-        const float inn = INT ? kInvW2 : inv_count(ln.nx * ny);
-        const float var = fmaf(nxf, dgg, ta) * inn;
-        const float cov = fmaf(nxf, dgp, tc) * inn;
+        float mu, nu, var, cov;
+        strip_window<R, INT>(q, ln, ny, mu, nu, var, cov);
         A = cov * rcp_approx(var + eps);
         b = fmaf(-A, mu, nu);
     }
@@ -158,17 +195,8 @@ template <typename TG, typename TP, int R>
 __device__ void coef_strip(const TG* __restrict__ G, const TP* __restrict__ P, float2* __restrict__ coef,
                            const StripGeom& s, float eps) {
     constexpr int W = 2 * R + 1;
-    const int lane = threadIdx.x & 31;
-    const int x = s.x0 + lane;
-    StripLane<R> ln;
-    ln.xin = x >= 0 && x < s.w;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-        const int xx = x - R + k;
-        ln.mk[k] = (xx >= 0 && xx < s.w) ? 1.f : 0.f;
-    }
-    ln.nx = ln.xin ? min(x + R, s.w - 1) - max(x - R, 0) + 1 : 1;
-    ln.out = lane >= 2 * R && lane < 32 - 2 * R && ln.xin;
+    const int x = s.x0 + (int)(threadIdx.x & 31);
+    const StripLane<R> ln = strip_lane<R>(x, s.w);
     const bool cols_int = s.x0 >= 0 && s.x0 + 32 <= s.w;  // warp-uniform
     StripRing<R> q;
 #pragma unroll
@@ -208,6 +236,169 @@ __device__ void coef_strip(const TG* __restrict__ G, const TP* __restrict__ P, f
             for (int u = 0; u < W; ++u) {
                 if (base + u >= e_last) break;  // uniform across the warp
                 strip_k1_row<TG, TP, R, false>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, s, eps);
+            }
+        }
+    }
+}
+
+
+// ------------------------------------------------------------------- K4
+// Algorithm 1 at low resolution for one strip segment.  Per window m (row
+// ce, this lane's column): the statistics, dA = f_mu^T(d Abar) and
+// db = f_mu^T(d bbar) as box sums of d Abar / N, d bbar / N, then
+//   gamma = (dA - db mu) / (var + eps),  beta = -gamma A,
+// and four quantities whose sums over the windows containing a pixel give
+//   dP = G' S0 + S2,   dG = P' S0 + 2 G' S1 - S3,
+// with S0 = sum gamma / N, S1 = sum beta / N, S2 = sum (db - gamma mu') / N,
+// S3 = sum (gamma nu' + 2 beta mu' + db A) / N.  Primes are shifts by a
+// per-strip constant (the mean of the segment's first output row), which
+// conditions the separable sums; the result is the same in exact arithmetic.
+template <int R>
+struct StripBwdRing {
+    static constexpr int W = 2 * R + 1;
+    float hda[W], hdb[W];               // row box sums of d Abar / N, d bbar / N (input rows)
+    float hq0[W], hq1[W], hq2[W], hq3[W];  // row box sums of the four window quantities (window rows)
+    float rg[W], rp[W];                 // raw G, P of the input rows
+};
+
+template <typename TG, typename TP, typename TD, int R, bool INT>
+__device__ __forceinline__ void strip_k4_row(StripRing<R>& q, StripBwdRing<R>& z, const StripLane<R>& ln, int U,
+                                             float gvu, float pvu, float2 dvu, int e, int e_first, int x,
+                                             TP* __restrict__ dP, TD* __restrict__ dG, const StripGeom& s,
+                                             float eps, float KG, float KP) {
+    constexpr int W = 2 * R + 1;
+    constexpr float kInvW2 = 1.f / (float)(W * W);
+    const int lane = threadIdx.x & 31;
+    const bool row_in = e >= 0 && e < s.h;
+    strip_row_stats<R, INT>(q, ln, U, gvu, pvu, row_in);
+    z.rg[U] = gvu;
+    z.rp[U] = pvu;
+    {
+        // d Abar / N, d bbar / N at (e, x); zero outside the image
+        const float inn = INT ? kInvW2
+                              : ((ln.xin && row_in) ? inv_count(ln.nx * (min(e + R, s.h - 1) - max(e - R, 0) + 1))
+                                                    : 0.f);
+        z.hda[U] = hsum<R>(dvu.x * inn);
+        z.hdb[U] = hsum<R>(dvu.y * inn);
+    }
+    const int ce = e - R;
+    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+    if (INT || (ln.xin && ce >= 0 && ce < s.h && e - e_first >= 2 * R)) {
+        const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
+        float mu, nu, var, cov;
+        strip_window<R, INT>(q, ln, ny, mu, nu, var, cov);
+        float dA = 0.f, db = 0.f;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            dA += z.hda[k];
+            db += z.hdb[k];
+        }
+        const float ive = rcp_approx(var + eps);
+        const float A = cov * ive;
+        const float gamma = fmaf(-db, mu, dA) * ive;
+        const float beta = -gamma * A;
+        const float inn = INT ? kInvW2 : inv_count(ln.nx * ny);
+        const float mus = mu - KG, nus = nu - KP;
+        q0 = gamma * inn;
+        q1 = beta * inn;
+        q2 = fmaf(-gamma, mus, db) * inn;
+        q3 = fmaf(gamma, nus, fmaf(2.f * beta, mus, db * A)) * inn;
+    }
+    z.hq0[U] = hsum<R>(q0);
+    z.hq1[U] = hsum<R>(q1);
+    z.hq2[U] = hsum<R>(q2);
+    z.hq3[U] = hsum<R>(q3);
+    const int co = ce - R;
+    const bool write = INT ? (lane >= 2 * R && lane < 32 - 2 * R)
+                           : (ln.out && co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
+    if (write) {
+        float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            S0 += z.hq0[k];
+            S1 += z.hq1[k];
+            S2 += z.hq2[k];
+            S3 += z.hq3[k];
+        }
+        constexpr int kLag = 1;  // row co = e - 2R sits in slot (U + 1) mod W
+        const int V = (U + kLag) % W;
+        const float g = z.rg[V] - KG, p = z.rp[V] - KP;
+        const size_t o = (size_t)co * s.w + x;
+        if (dP != nullptr) dP[o] = from_f32<TP>(fmaf(g, S0, S2));
+        if (dG != nullptr) dG[o] = from_f32<TD>(fmaf(p, S0, fmaf(2.f * g, S1, -S3)));
+    }
+}
+
+template <typename TG, typename TP, typename TD, int R>
+__device__ void lowres_bwd_strip(const TG* __restrict__ G, const TP* __restrict__ P,
+                                 const float2* __restrict__ dcoef, TP* __restrict__ dP, TD* __restrict__ dG,
+                                 const StripGeom& s, float eps) {
+    constexpr int W = 2 * R + 1;
+    const int lane = threadIdx.x & 31;
+    const int x = s.x0 + lane;
+    const StripLane<R> ln = strip_lane<R>(x, s.w);
+    // interior columns: every lane's column and its count's window inside the image
+    const bool cols_int = s.x0 >= R && s.x0 + 32 + R <= s.w;
+    StripRing<R> q;
+    StripBwdRing<R> z;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        q.mg[k] = q.mp[k] = q.sgg[k] = q.sgp[k] = q.vr[k] = 0.f;
+        z.hda[k] = z.hdb[k] = z.hq0[k] = z.hq1[k] = z.hq2[k] = z.hq3[k] = z.rg[k] = z.rp[k] = 0.f;
+    }
+    const int e_first = s.y0 - 2 * R;
+    const int e_last = min(s.y0 + s.seg, s.h) + 2 * R;
+    float gn[W], pn[W];
+    float2 dn[W];
+    auto load = [&](int base) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const int e = base + u;
+            const bool ok = ln.xin && e >= 0 && e < s.h && e < e_last;
+            const size_t o = (size_t)e * s.w + x;
+            gn[u] = ok ? to_f32<TG>(G[o]) : 0.f;
+            pn[u] = ok ? to_f32<TP>(P[o]) : 0.f;
+            dn[u] = ok ? dcoef[o] : make_float2(0.f, 0.f);
+        }
+    };
+    load(e_first);
+    // shift: mean of row y0 (the last row of the first period) over the output lanes
+    float KG, KP;
+    {
+        const bool use = ln.out;
+        float sg = use ? gn[2 * R] : 0.f, sp = use ? pn[2 * R] : 0.f, cn = use ? 1.f : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sg += __shfl_xor_sync(0xffffffffu, sg, off);
+            sp += __shfl_xor_sync(0xffffffffu, sp, off);
+            cn += __shfl_xor_sync(0xffffffffu, cn, off);
+        }
+        KG = cn > 0.f ? sg / cn : 0.f;
+        KP = cn > 0.f ? sp / cn : 0.f;
+    }
+    for (int base = e_first; base < e_last; base += W) {
+        float gv[W], pv[W];
+        float2 dv[W];
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            gv[u] = gn[u];
+            pv[u] = pn[u];
+            dv[u] = dn[u];
+        }
+        if (base + W < e_last) load(base + W);
+        const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W + R <= s.h &&
+                             base + W <= e_last;
+        if (row_int) {
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+                strip_k4_row<TG, TP, TD, R, true>(q, z, ln, u, gv[u], pv[u], dv[u], base + u, e_first, x, dP, dG,
+                                                  s, eps, KG, KP);
+        } else {
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (base + u >= e_last) break;  // uniform across the warp
+                strip_k4_row<TG, TP, TD, R, false>(q, z, ln, u, gv[u], pv[u], dv[u], base + u, e_first, x, dP,
+                                                   dG, s, eps, KG, KP);
             }
         }
     }

@@ -29,6 +29,12 @@ struct TmaPair {
     int enabled;
 };
 
+// Tensor maps of K3's two high-resolution inputs (d O_h, I_h): 3-D (column,
+// row, plane), box of one strip row segment x one block of rows.
+struct K3Maps {
+    CUtensorMap r, g;  // 64-byte aligned opaque descriptors
+};
+
 constexpr long long kWaitLimit = 1LL << 22;  // try_wait polls before giving up
 constexpr uint32_t kStatusTimeout = 1u;
 

@@ -104,18 +104,21 @@ def pin():
     L.dgf_autotune_reset()
 
 
-# K1 kernel forms for r <= 2: warp strips (a = rows per segment, b = 0) and
-# column-walking tiles (a = columns, b = rows of the coefficient region)
-K1_FORMS = [(1, 16, 0), (1, 64, 0), (1, 64, 32), (1, 128, 16), (2, 32, 0), (2, 16, 0), (2, 64, 32),
-            (2, 128, 64)]
+# Low-res kernel forms for r <= 2 (kind 1 = K1, 4 = K4): warp strips
+# (a = rows per segment, b = 0) and column-walking tiles (a = columns,
+# b = rows of the coefficient region)
+LOW_FORMS = [(1, 1, 16, 0), (1, 1, 64, 0), (1, 1, 64, 32), (1, 1, 128, 16), (1, 2, 32, 0), (1, 2, 16, 0),
+             (1, 2, 64, 32), (1, 2, 128, 64),
+             (4, 1, 8, 0), (4, 1, 32, 0), (4, 1, 128, 0), (4, 1, 64, 16), (4, 2, 16, 0), (4, 2, 64, 0),
+             (4, 2, 64, 32)]
 
 
 @pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
-@pytest.mark.parametrize("form", K1_FORMS, ids=_ids(K1_FORMS))
-def test_k1_forms_match_oracle(form, dtype, pin):
-    r, a, b = form
+@pytest.mark.parametrize("form", LOW_FORMS, ids=_ids(LOW_FORMS))
+def test_lowres_forms_match_oracle(form, dtype, pin):
+    kind, r, a, b = form
     dt = L.DGF_F32 if dtype == F32 else L.DGF_BF16
-    pin(1, dt, r, 0, 0, 0, a, b)
+    pin(kind, dt, r, 0, 0, 0, a, b)
     # ragged against strips of 28 / 24 columns and segments of 16..64 rows
     st = to_storage(make_case("photo", 30 + r, 1, 2, 77, 131, 308, 524), dtype)
     R = synth.upstream_grad(31, st["I_h"].shape).to(dtype)
@@ -148,17 +151,25 @@ def test_unbuilt_pinned_shape_falls_back_to_default(pin):
     assert torch.equal(out, ref)
 
 
-def test_tma_and_plain_staging_identical(pin):
-    pin(1, L.DGF_BF16, 2, 0, 0, 0, 64, 32)  # tile form (the one that stages by TMA)
-    st = to_storage(make_case("photo", 3, 2, 3, 64, 96, 256, 384), BF16)
+@pytest.mark.parametrize("dtype,size", [(BF16, (2, 3, 64, 96, 256, 384)), (F32, (1, 2, 70, 90, 280, 360)),
+                                        (BF16, (1, 1, 40, 44, 320, 352))], ids=["bf16-f4", "f32-f4", "bf16-f8"])
+def test_tma_and_plain_staging_identical(dtype, size, pin):
+    # K1 tile form (stages by TMA) and K3 (TMA slot ring vs register ring)
+    pin(1, L.DGF_F32 if dtype == F32 else L.DGF_BF16, 2, 0, 0, 0, 64, 32)
+    N, C, hl, wl, h, w = size
+    st = to_storage(make_case("photo", 3, N, C, hl, wl, h, w), dtype)
+    R = synth.upstream_grad(4, st["I_h"].shape).to(dtype).cuda()
     g = {k: v.cuda() for k, v in st.items()}
-    L.dgf_set_tma(True)
-    a = gf_forward(g["p_l"], g["I_l"], g["I_h"], 2, 1e-3)
-    L.dgf_set_tma(False)
-    b = gf_forward(g["p_l"], g["I_l"], g["I_h"], 2, 1e-3)
+    res = []
+    for on in (True, False):
+        L.dgf_set_tma(on)
+        out = gf_forward(g["p_l"], g["I_l"], g["I_h"], 2, 1e-3)
+        grads = gf_backward(R, g["p_l"], g["I_l"], g["I_h"], 2, 1e-3)[:3]
+        res.append((out, *grads))
     L.dgf_set_tma(True)
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
 
 
 def test_deterministic():
