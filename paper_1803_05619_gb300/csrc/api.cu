@@ -181,7 +181,9 @@ struct Plan {
     int vec = 1;    // K2 / K3 vector width
     LowCfg k1{0, 32, 32};
     LowCfg k4{0, 16, 16};
-    int k2_th = 32;
+    int k2_th = 32;        // K2 tiles: high-res rows per tile
+    bool k2_strip = false; // K2 as warp strips (integer F in {2, 4, 8} dividing vec)
+    int k2_ls = 8;         // K2 strips: low-res rows per segment
     int k3_lth = 8;
     bool k3_fast = false;
 };
@@ -253,6 +255,7 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     p.vec = pick_vec(dt, w, hires_ptrs);
     pick_lowres_tiles(r, p);
     p.k3_fast = p.F > 0 && k3_fast_ok(p.vec, p.F);
+    p.k2_strip = p.F > 0 && k2_strip_ok(p.vec, p.F);
     p.k3_lth = default_k3_lth(p.F);
     int a, b;
     // a table entry (tuned, pinned or read from a cache file) is used only if
@@ -267,7 +270,12 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
             if (in_candidates(c, r, true)) p.k4 = c;
         }
     }
-    if (tune_lookup(TuneKey{2, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256) p.k2_th = a;
+    if (tune_lookup(TuneKey{2, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256) {
+        if (p.k2_strip)
+            p.k2_ls = a;
+        else
+            p.k2_th = a;
+    }
     if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256)
         p.k3_lth = a;
     return p;
@@ -404,6 +412,27 @@ static TmaPair make_tma_pair(const void* G, dgf_dtype dg, const void* P, dgf_dty
     return t;
 }
 
+// K2's tensor map (I_h), same box as K3's.
+static bool make_k2_map(K2Map& m, const void* in, dgf_dtype dt, int planes, int h, int w, int vec, int F) {
+    if (!g_tma_allowed || F <= 0 || vec * (int)esize(dt) != 16) return false;
+    TmaPlane a;
+    if (!make_tma(a, in, tma_type(dt), (int)esize(dt), planes, h, w, 32 * vec, F, 0)) return false;
+    m.m = a.map;
+    return true;
+}
+
+// K2 (mode 0: O_h = Abar_h I_h + bbar_h) in the plan's form.
+static cudaError_t launch_k2_plan(dgf_dtype dt, const float2* coef, const void* in, void* out, int planes, int h_l,
+                                  int w_l, int h, int w, const Plan& p, int shape, cudaStream_t s) {
+    if (p.k2_strip) {
+        K2Map map;
+        const bool tma = make_k2_map(map, in, dt, planes, h, w, p.vec, p.F);
+        return launch_k2_strip(dt, coef, in, out, planes, h_l, w_l, h, w, p.vec, p.F, shape, tma ? &map : nullptr,
+                               status_ptr(), s);
+    }
+    return launch_k2(dt, 0, coef, in, out, planes, h_l, w_l, h, w, p.vec, p.F, shape, s);
+}
+
 // --------------------------------------------------------------- validation
 static dgf_status check_sizes(int N, int C, int h_l, int w_l, int h, int w, int r, float eps, dgf_dtype dt) {
     if ((int)dt < 0 || (int)dt > 2) return fail(DGF_ERR_INVALID, "dtype %d is not FP32, BF16 or FP16", (int)dt);
@@ -498,11 +527,12 @@ static void tune_k2(dgf_dtype dt, const float2* coef, const void* in, void* out,
     int a, b;
     if (tune_lookup(key, a, b)) return;
     float best = 1e30f;
-    int bt = p.k2_th;
-    for (int th : {8, 16, 32, 64}) {
-        if (k2_smem_bytes(p.vec, p.F, h_l, h, w_l, w, th) > smem_limit()) continue;
+    int bt = p.k2_strip ? p.k2_ls : p.k2_th;
+    const std::initializer_list<int> strip_cand = {4, 8, 16, 32}, tile_cand = {8, 16, 32, 64};
+    for (int th : p.k2_strip ? strip_cand : tile_cand) {
+        if (!p.k2_strip && k2_smem_bytes(p.vec, p.F, h_l, h, w_l, w, th) > smem_limit()) continue;
         const float ms = time_launch(s, [&] {
-            return launch_k2(dt, 0, coef, in, out, planes, h_l, w_l, h, w, p.vec, p.F, th, s);
+            return launch_k2_plan(dt, coef, in, out, planes, h_l, w_l, h, w, p, th, s);
         }, 3);
         if (ms > 0.f && ms < best) {
             best = ms;
@@ -511,7 +541,10 @@ static void tune_k2(dgf_dtype dt, const float2* coef, const void* in, void* out,
     }
     if (best < 1e30f) {
         tune_store(key, bt, 0);
-        p.k2_th = bt;
+        if (p.k2_strip)
+            p.k2_ls = bt;
+        else
+            p.k2_th = bt;
     }
 }
 
@@ -603,22 +636,33 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
         b.r = im.r;
         b.eps = im.eps;
         Plan p = make_plan(dt, im.h_l, im.w_l, im.h, im.w, im.r, false, {im.I_h, im.O_h});
-        // the persistent K2 has fast paths for factors 4 and 8 only
-        b.F = (p.F == 4 || p.F == 8) ? p.F : 0;
+        // the persistent K2 runs strips where the single call does, else tiles
+        // with fast taps for factors 4 and 8 only
+        b.F = p.k2_strip ? p.F : ((p.F == 4 || p.F == 8) ? p.F : 0);
         b.vec = p.vec;
         b.k1_fast = p.k1.fast;
         b.k1_ty = p.k1.fast ? p.k1.b : p.k1.a;  // tiles: EY1; generic: TY; strips: 0
         b.k1_tx = p.k1.fast ? p.k1.a : p.k1.b;  // tiles: CW;  generic: TX; strips: rows per segment
-        b.k2_th = p.k2_th;
         low_grid(p.k1, im.r, im.h_l, im.w_l, b.k1_nx, b.k1_ny);
-        b.k2_nx = (im.w + 32 * b.vec - 1) / (32 * b.vec);
-        b.k2_ny = (im.h + b.k2_th - 1) / b.k2_th;
+        if (p.k2_strip) {
+            // work items of kWarps strip segments (one per warp); k2_th = low-res rows per segment
+            b.k2_th = p.k2_ls;
+            const int K = b.vec / b.F;
+            const int nstrip = (im.w_l + 32 * K - 1) / (32 * K), nseg = (im.h_l + b.k2_th - 1) / b.k2_th;
+            b.k2_nx = (nstrip * nseg + kWarps - 1) / kWarps;
+            b.k2_ny = 1;
+        } else {
+            b.k2_th = p.k2_th;
+            b.k2_nx = (im.w + 32 * b.vec - 1) / (32 * b.vec);
+            b.k2_ny = (im.h + b.k2_th - 1) / b.k2_th;
+        }
         b.coef = ws_base ? reinterpret_cast<float2*>(ws_base + off) : nullptr;
         off += align256((size_t)im.C * im.h_l * im.w_l * sizeof(float2));
         bp.k1_start[i + 1] = bp.k1_start[i] + b.k1_nx * b.k1_ny * im.C;
         bp.k2_start[i + 1] = bp.k2_start[i] + b.k2_nx * b.k2_ny * im.C;
         out.smem1 = std::max(out.smem1, k1_cfg_smem(p.k1, b.r, 0));
-        out.smem2 = std::max(out.smem2, k2_smem_bytes(b.vec, b.F, b.h_l, b.h, b.w_l, b.w, b.k2_th));
+        out.smem2 = std::max(out.smem2, p.k2_strip ? k2_strip_batched_smem((int)esize(dt), b.vec, b.F)
+                                                   : k2_smem_bytes(b.vec, b.F, b.h_l, b.h, b.w_l, b.w, b.k2_th));
     }
     bp.k1_total = bp.k1_start[n];
     bp.k2_total = bp.k2_start[n];
@@ -664,7 +708,7 @@ dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* 
         if (e != cudaSuccess) return cuda_fail(e, "k1");
         if (tuning) tune_k2(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, s, p);
         e = L.run("k2_hires_apply", [&] {
-            return launch_k2(dt, 0, coef, I_h, O_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
+            return launch_k2_plan(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, p, p.k2_strip ? p.k2_ls : p.k2_th, s);
         });
         if (e != cudaSuccess) return cuda_fail(e, "k2");
         return DGF_OK;
@@ -852,7 +896,9 @@ extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtyp
             const int j = b.n++;
             b.img[j] = im;
             b.k2_start[j + 1] = b.k2_start[j] + im.k2_nx * im.k2_ny * im.C;
-            sm2[q] = std::max(sm2[q], k2_smem_bytes(im.vec, im.F, im.h_l, im.h, im.w_l, im.w, im.k2_th));
+            sm2[q] = std::max(sm2[q], (im.F > 0 && k2_strip_ok(im.vec, im.F))
+                                          ? k2_strip_batched_smem((int)esize(dt), im.vec, im.F)
+                                          : k2_smem_bytes(im.vec, im.F, im.h_l, im.h, im.w_l, im.w, im.k2_th));
         }
         b.k2_total = b.k2_start[b.n];
     }
@@ -1051,7 +1097,7 @@ extern "C" dgf_status dgf_forward_noalloc(const void* p_l, const void* I_l, cons
     cudaError_t e = launch_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, status_ptr(), s);
     if (e != cudaSuccess) return cuda_fail(e, "k1");
     g_launches.fetch_add(1);
-    e = launch_k2(dt, 0, coef, I_h, O_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
+    e = launch_k2_plan(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, p, p.k2_strip ? p.k2_ls : p.k2_th, s);
     if (e != cudaSuccess) return cuda_fail(e, "k2");
     return DGF_OK;
 }

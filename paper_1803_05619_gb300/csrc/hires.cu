@@ -5,6 +5,7 @@
 #include "common.cuh"
 #include "hires.cuh"
 #include "hires_strip.cuh"
+#include "tma.cuh"
 #include "kernels.h"
 
 namespace dgf {
@@ -98,9 +99,62 @@ __global__ void __launch_bounds__(kThreads) k3_gather_general(const T* __restric
     dcoef[plane * h_l * w_l + (size_t)i * w_l + j] = make_float2(su, sv);
 }
 
+// K2 strips (integer F dividing VEC): warp w of the grid owns strip
+// (w % nstrip) of segment (w / nstrip) % nseg (LS low-res rows) of plane
+// w / (nstrip nseg).
+template <typename T, int VEC, int F>
+__global__ void __launch_bounds__(kThreads) k2_apply_strip(const float2* __restrict__ coef, const T* __restrict__ in,
+                                                           T* __restrict__ out, int h_l, int w_l, int h, int w, int LS,
+                                                           int nstrip, int nseg, int planes) {
+    extern __shared__ __align__(128) unsigned char k2slots[];
+    const int warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kWarps + warp;
+    if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
+    const int strip = gw % nstrip, rest = gw / nstrip;
+    const int sg = rest % nseg, plane = rest / nseg;
+    const size_t hw = (size_t)h * w, lw = (size_t)h_l * w_l;
+    k2_strip_async<T, VEC, F>(coef + plane * lw, in + plane * hw, out + plane * hw, h_l, w_l, h, w, strip, sg * LS,
+                              min(sg * LS + LS, h_l), k2slots + warp * K2Async<T, VEC, F>::WARP_BYTES);
+}
+
+template <typename T, int VEC, int F>
+__global__ void __launch_bounds__(K2Tma<T, VEC, F>::WPC * 32)
+    k2_apply_strip_tma(const float2* __restrict__ coef, const __grid_constant__ K2Map map, T* __restrict__ out,
+                       int h_l, int w_l, int h, int w, int LS, int nstrip, int nseg, int planes, uint32_t* status) {
+    extern __shared__ __align__(1024) unsigned char k2ring[];
+    using B = K2Tma<T, VEC, F>;
+    const int warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * B::WPC + warp;
+    if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
+    const int strip = gw % nstrip, rest = gw / nstrip;
+    const int sg = rest % nseg, plane = rest / nseg;
+    const size_t hw = (size_t)h * w, lw = (size_t)h_l * w_l;
+    unsigned char* ring = k2ring + (size_t)warp * B::NSB * B::SLOT;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(k2ring + (size_t)B::WPC * B::NSB * B::SLOT) + warp * B::NSB;
+    k2_strip_tma<T, VEC, F>(coef + plane * lw, &map.m, out + plane * hw, h_l, w_l, h, w, strip, sg * LS,
+                            min(sg * LS + LS, h_l), plane, ring, bars, status);
+}
+
 // ------------------------------------------------------- batched K2 (persistent)
 template <typename T, int VEC, int F>
 __device__ __forceinline__ void apply_batched_tile(const BatchImage& im, int local, float2* sAB) {
+    if constexpr (F > 0 && VEC % F == 0) {
+        // strips: a work item is kWarps strip segments, one per warp (k2_th = LS)
+        const int nstrip = (im.w_l + 32 * (VEC / F) - 1) / (32 * (VEC / F));
+        const int nseg = (im.h_l + im.k2_th - 1) / im.k2_th;
+        const int plane = local / im.k2_nx;
+        const int item = (local - plane * im.k2_nx) * kWarps + (threadIdx.x >> 5);
+        if (item < nstrip * nseg) {  // warp-uniform; no barrier follows
+            const int strip = item % nstrip, sg = item / nstrip;
+            const size_t hw = (size_t)im.h * im.w, lw = (size_t)im.h_l * im.w_l;
+            k2_strip_async<T, VEC, F>(im.coef + plane * lw, static_cast<const T*>(im.I_h) + plane * hw,
+                                      static_cast<T*>(im.O_h) + plane * hw, im.h_l, im.w_l, im.h, im.w, strip,
+                                      sg * im.k2_th, min(sg * im.k2_th + im.k2_th, im.h_l),
+                                      reinterpret_cast<unsigned char*>(sAB) +
+                                          (threadIdx.x >> 5) * K2Async<T, VEC, F>::WARP_BYTES);
+        }
+        return;
+    }
     const int per_plane = im.k2_nx * im.k2_ny;
     const int plane = local / per_plane;
     const int tp = local - plane * per_plane;
@@ -146,6 +200,40 @@ static cudaError_t prep(K kernel, size_t smem) {
     return cudaSuccess;
 }
 
+bool k2_strip_ok(int vec, int F) { return (F == 2 || F == 4 || F == 8) && vec >= F && vec % F == 0; }
+
+size_t k2_strip_batched_smem(int esize, int vec, int F) {
+    const int nsb = F == 2 ? 6 : (F == 4 ? 3 : 2);
+    return (size_t)kWarps * nsb * (32 * vec) * F * esize;
+}
+
+template <typename T, int VEC, int F>
+static cudaError_t k2s_go(const float2* coef, const void* in, void* out, int planes, int h_l, int w_l, int h, int w,
+                          int LS, const K2Map* map, uint32_t* status, cudaStream_t s) {
+    const int nstrip = (w_l + 32 * (VEC / F) - 1) / (32 * (VEC / F)), nseg = (h_l + LS - 1) / LS;
+    const long long warps = (long long)nstrip * nseg * planes;
+    if constexpr (VEC * sizeof(T) == 16) {
+        if (map != nullptr) {
+            using B = K2Tma<T, VEC, F>;
+            auto kern = k2_apply_strip_tma<T, VEC, F>;
+            cudaError_t e = prep(kern, B::CTA_BYTES);
+            if (e != cudaSuccess) return e;
+            const int ctas = (int)((warps + B::WPC - 1) / B::WPC);
+            kern<<<ctas, B::WPC * 32, B::CTA_BYTES, s>>>(coef, *map, static_cast<T*>(out), h_l, w_l, h, w, LS, nstrip,
+                                                          nseg, planes, status);
+            return cudaGetLastError();
+        }
+    }
+    const int ctas = (int)((warps + kWarps - 1) / kWarps);
+    constexpr size_t smem = kWarps * K2Async<T, VEC, F>::WARP_BYTES;
+    auto kern = k2_apply_strip<T, VEC, F>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<ctas, kThreads, smem, s>>>(coef, static_cast<const T*>(in), static_cast<T*>(out), h_l, w_l, h, w, LS,
+                                      nstrip, nseg, planes);
+    return cudaGetLastError();
+}
+
 template <typename T, int VEC, int F, int MODE>
 static cudaError_t k2_go(const float2* coef, const void* in, void* out, int planes, int h_l, int w_l,
                          int h, int w, int TH, cudaStream_t s) {
@@ -175,6 +263,34 @@ static cudaError_t k2_dispatch(const float2* coef, const void* in, void* out, in
         return k2_go<T, VH, 0, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
     }
     return k2_go<T, 1, 0, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+}
+
+template <typename T>
+static cudaError_t k2s_dispatch(const float2* coef, const void* in, void* out, int planes, int h_l, int w_l, int h,
+                                int w, int vec, int F, int LS, const K2Map* map, uint32_t* status, cudaStream_t s) {
+    constexpr int VW = 16 / sizeof(T), VH = 8 / sizeof(T);
+#define DGF_K2S(V, FF)                                                                                        \
+    if (vec == V && F == FF) return k2s_go<T, V, FF>(coef, in, out, planes, h_l, w_l, h, w, LS, map, status, s);
+    DGF_K2S(VW, 2)
+    DGF_K2S(VW, 4)
+    if constexpr (VW >= 8) { DGF_K2S(VW, 8) }
+    DGF_K2S(VH, 2)
+    if constexpr (VH >= 4) { DGF_K2S(VH, 4) }
+#undef DGF_K2S
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_k2_strip(dgf_dtype dt, const float2* coef, const void* in, void* out, int planes, int h_l,
+                            int w_l, int h, int w, int vec, int F, int LS, const K2Map* map, uint32_t* status,
+                            cudaStream_t s) {
+    if (planes == 0) return cudaSuccess;
+    switch (dt) {
+        case DGF_F32: return k2s_dispatch<float>(coef, in, out, planes, h_l, w_l, h, w, vec, F, LS, map, status, s);
+        case DGF_BF16:
+            return k2s_dispatch<__nv_bfloat16>(coef, in, out, planes, h_l, w_l, h, w, vec, F, LS, map, status, s);
+        case DGF_F16: return k2s_dispatch<__half>(coef, in, out, planes, h_l, w_l, h, w, vec, F, LS, map, status, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_k2(dgf_dtype dt, int mode, const float2* coef, const void* in, void* out, int planes,
@@ -279,11 +395,13 @@ template <typename T>
 static cudaError_t k2b_dispatch(int vec, int F, size_t smem, void** fn) {
     constexpr int VW = 16 / sizeof(T), VH = 8 / sizeof(T);
     if (vec == VW) {
+        if (F == 2) return k2b_get<T, VW, 2>(smem, fn);
         if (F == 4) return k2b_get<T, VW, 4>(smem, fn);
         if (F == 8) return k2b_get<T, VW, 8>(smem, fn);
         return k2b_get<T, VW, 0>(smem, fn);
     }
     if (vec == VH) {
+        if (F == 2) return k2b_get<T, VH, 2>(smem, fn);
         if (F == 4) return k2b_get<T, VH, 4>(smem, fn);
         if (F == 8) return k2b_get<T, VH, 8>(smem, fn);
         return k2b_get<T, VH, 0>(smem, fn);

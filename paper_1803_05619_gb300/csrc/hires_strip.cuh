@@ -370,4 +370,246 @@ __device__ void k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps
     }
 }
 
+// ------------------------------------------------------------- K2 strip
+// Eq. 2 after the bilinear upsampler, as a strip walk: a lane holds VEC
+// pixels (K = VEC / F cells).  Per low-res row block i (the F high-res rows
+// whose first tap is row i) the lane forms once row i + 1 of Abar and bbar
+// interpolated along x at its pixels (from its K + 2 tap columns, clamped)
+// and the difference to row i; each high-res row of the block then costs one
+// FMA per coefficient and one for the output.  Every lane writes its pixels
+// (no halo).  Rows reach the lanes through per-warp shared-memory slots,
+// filled by TMA (16-byte vectors, single calls) or by per-lane asynchronous
+// copies.
+template <int VEC, int F>
+struct K2Rows {
+    float A1[VEC], B1[VEC];  // row i + 1 (the block's second tap row) along x
+    float DA[VEC], DB[VEC];  // row i + 1 minus row i
+};
+
+template <int VEC, int F>
+__device__ __forceinline__ void k2s_hrow(const float2* __restrict__ coef, int ii, int J, int w_l, float (&HA)[VEC],
+                                         float (&HB)[VEC]) {
+    constexpr int K = VEC / F;
+    const float2* row = coef + (size_t)ii * w_l;
+    float2 tp[K + 2];
+#pragma unroll
+    for (int c = 0; c < K + 2; ++c) tp[c] = row[clampi(J - 1 + c, 0, w_l - 1)];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        HA[k] = lerp(tp[k3s_lo<F>(k)].x, tp[k3s_lo<F>(k) + 1].x, k3s_lam<F>(k));
+        HB[k] = lerp(tp[k3s_lo<F>(k)].y, tp[k3s_lo<F>(k) + 1].y, k3s_lam<F>(k));
+    }
+}
+
+// Before the first block b0: row clamp(b0) becomes the "second tap" row.
+template <int VEC, int F>
+__device__ __forceinline__ void k2s_init(K2Rows<VEC, F>& q, const float2* __restrict__ coef, int b0, int J, int h_l,
+                                         int w_l) {
+    k2s_hrow<VEC, F>(coef, clampi(b0, 0, h_l - 1), J, w_l, q.A1, q.B1);
+}
+
+// Block i begins: taps rows clamp(i) (the previous second row) and clamp(i + 1).
+template <int VEC, int F>
+__device__ __forceinline__ void k2s_block(K2Rows<VEC, F>& q, const float2* __restrict__ coef, int i, int J, int h_l,
+                                          int w_l) {
+    float a[VEC], b[VEC];
+    k2s_hrow<VEC, F>(coef, min(i + 1, h_l - 1), J, w_l, a, b);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        q.DA[k] = a[k] - q.A1[k];
+        q.DB[k] = b[k] - q.B1[k];
+        q.A1[k] = a[k];
+        q.B1[k] = b[k];
+    }
+}
+
+// O_h at row t of the block: lerp along y written from the second row,
+// A1 + (lam_y - 1) DA with lam_y = (2t + 1) / 2F.
+template <int VEC, int F>
+__device__ __forceinline__ void k2s_row(const K2Rows<VEC, F>& q, const float (&g)[VEC], int t, float (&o)[VEC]) {
+    const float lm1 = (float)(2 * t + 1 - 2 * F) / (float)(2 * F);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) o[k] = fmaf(fmaf(lm1, q.DA[k], q.A1[k]), g[k], fmaf(lm1, q.DB[k], q.B1[k]));
+}
+
+struct K2Lane {
+    int J, x0;
+    bool full, any;
+};
+
+template <int VEC, int F>
+__device__ __forceinline__ K2Lane k2s_lane(int strip, int w_l) {
+    constexpr int K = VEC / F;
+    K2Lane L;
+    L.J = 32 * K * strip + (int)(threadIdx.x & 31) * K;
+    L.x0 = F * L.J;
+    L.full = L.J + K <= w_l;
+    L.any = L.J < w_l;
+    return L;
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void k2s_store(T* __restrict__ out, int y, int w, const K2Lane& L, const float (&o)[VEC]) {
+    if (L.full) {
+        store_vec<T, VEC>(out + (size_t)y * w + L.x0, o);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k)
+            if (L.x0 + k < w) out[(size_t)y * w + L.x0 + k] = from_f32<T>(o[k]);
+    }
+}
+
+template <typename T, int VEC, int F>
+struct K2Tma {
+    static constexpr int ROW = 32 * VEC;
+    static constexpr int NSB = F == 2 ? 8 : (F == 4 ? 4 : 2);   // slots (blocks) per warp
+    static constexpr int WPC = 8;                               // warps per CTA
+    static constexpr int SLOT = ROW * F * (int)sizeof(T);
+    static constexpr size_t CTA_BYTES = (size_t)WPC * NSB * SLOT + (size_t)WPC * NSB * 8;
+};
+
+// Same walk with the input rows staged per block by TMA (16-byte vectors).
+template <typename T, int VEC, int F>
+__device__ void k2_strip_tma(const float2* __restrict__ coef, const CUtensorMap* map, T* __restrict__ out, int h_l,
+                             int w_l, int h, int w, int strip, int ia, int ib, int plane, unsigned char* ring,
+                             uint64_t* bars, uint32_t* status) {
+    using B = K2Tma<T, VEC, F>;
+    static_assert(VEC * sizeof(T) == 16, "TMA staging needs 16-byte vectors");
+    constexpr int NSB = B::NSB, H0 = F / 2;
+    const int lane = threadIdx.x & 31;
+    const K2Lane L = k2s_lane<VEC, F>(strip, w_l);
+    const int b0 = ia == 0 ? -1 : ia;
+    const int nblk = ib - b0;
+    const int xs = B::ROW * strip;
+    const uint32_t ring_s = smem_u32(ring), bar_s = smem_u32(bars);
+    auto issue = [&](int m) {  // lane 0: block b0 + m into slot m % NSB
+        const int slot = m % NSB;
+        const uint32_t bar = bar_s + 8u * slot;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)B::SLOT)
+                     : "memory");
+        tma_load_3d(ring_s + (uint32_t)(slot * B::SLOT), map, xs, F * (b0 + m) + H0, plane, bar);
+    };
+    if (lane == 0) {
+        for (int s = 0; s < NSB; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int m = 0; m < min(NSB, nblk); ++m) issue(m);
+    }
+    __syncwarp();
+    K2Rows<VEC, F> q;
+    k2s_init<VEC, F>(q, coef, b0, L.J, h_l, w_l);
+    int m = 0;
+    bool ok = true;
+    for (; m < nblk; ++m) {
+        const int slot = m % NSB;
+        const int i = b0 + m;
+        k2s_block<VEC, F>(q, coef, i, L.J, h_l, w_l);
+        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NSB) & 1), kWaitLimit))) {
+            ok = false;
+            break;
+        }
+        const T* sr = reinterpret_cast<const T*>(ring + slot * B::SLOT) + lane * VEC;
+#pragma unroll
+        for (int t = 0; t < F; ++t) {
+            float g[VEC];
+            unpack_vec<T, VEC>(*reinterpret_cast<const Vec<T, VEC>*>(sr + t * B::ROW), g);
+            if (t == F - 1) {
+                __syncwarp();  // every lane has read the slot
+                if (lane == 0 && m + NSB < nblk) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(m + NSB);
+                }
+            }
+            const int y = F * i + H0 + t;
+            if (L.any && y >= 0 && y < h) {
+                float o[VEC];
+                k2s_row<VEC, F>(q, g, t, o);
+                k2s_store<T, VEC>(out, y, w, L, o);
+            }
+        }
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        for (int qb = m; qb < nblk && qb < m + NSB; ++qb)
+            mbar_wait(bar_s + 8u * (qb % NSB), (uint32_t)((qb / NSB) & 1), kWaitLimit);
+    }
+}
+
+// Same walk with the input rows staged by per-lane asynchronous copies
+// (cp.async, 16 or 8 bytes per lane and row, zero-filled outside the image)
+// into a per-warp ring of NSB blocks, one commit group per block; no tensor
+// map is needed, so the persistent batched kernel uses this form.  Each lane
+// reads back only what it copied, so no barrier is involved.
+template <typename T, int VEC, int F>
+struct K2Async {
+    static constexpr int ROW = 32 * VEC;
+    static constexpr int NSB = F == 2 ? 6 : (F == 4 ? 3 : 2);
+    static constexpr int SLOT = ROW * F * (int)sizeof(T);
+    static constexpr size_t WARP_BYTES = (size_t)NSB * SLOT;
+};
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(uint32_t dst, const void* src, bool ok) {
+    const uint32_t n = ok ? BYTES : 0;  // 0 source bytes: the destination is zero-filled
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(BYTES), "r"(n)
+                 : "memory");
+}
+
+template <typename T, int VEC, int F>
+__device__ void k2_strip_async(const float2* __restrict__ coef, const T* __restrict__ in, T* __restrict__ out,
+                               int h_l, int w_l, int h, int w, int strip, int ia, int ib, unsigned char* ring) {
+    using B = K2Async<T, VEC, F>;
+    constexpr int NSB = B::NSB, H0 = F / 2, VB = VEC * (int)sizeof(T);
+    const int lane = threadIdx.x & 31;
+    const K2Lane L = k2s_lane<VEC, F>(strip, w_l);
+    const int b0 = ia == 0 ? -1 : ia;
+    const int nblk = ib - b0;
+    const uint32_t mine = smem_u32(ring) + (uint32_t)(lane * VB);
+    auto issue = [&](int m) {  // this lane's vectors of block b0 + m (partial lanes copy zeros; handled below)
+        const uint32_t dst = mine + (uint32_t)((m % NSB) * B::SLOT);
+#pragma unroll
+        for (int t = 0; t < F; ++t) {
+            const int y = F * (b0 + m) + H0 + t;
+            const bool ok = L.full && y >= 0 && y < h;
+            cp_async_zfill<VB>(dst + (uint32_t)(t * B::ROW * (int)sizeof(T)),
+                               ok ? (const void*)(in + (size_t)y * w + L.x0) : (const void*)in, ok);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int m = 0; m < NSB; ++m) {
+        if (m < nblk) issue(m);
+        else asm volatile("cp.async.commit_group;" ::: "memory");  // keep the group count uniform
+    }
+    K2Rows<VEC, F> q;
+    k2s_init<VEC, F>(q, coef, b0, L.J, h_l, w_l);
+    for (int m = 0; m < nblk; ++m) {
+        const int i = b0 + m;
+        k2s_block<VEC, F>(q, coef, i, L.J, h_l, w_l);
+        asm volatile("cp.async.wait_group %0;" ::"n"(NSB - 1) : "memory");
+        const T* sr = reinterpret_cast<const T*>(ring + (m % NSB) * B::SLOT) + lane * VEC;
+#pragma unroll
+        for (int t = 0; t < F; ++t) {
+            const int y = F * i + H0 + t;
+            float g[VEC];
+            if (L.full) {
+                unpack_vec<T, VEC>(*reinterpret_cast<const Vec<T, VEC>*>(sr + t * B::ROW), g);
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k)
+                    g[k] = (L.any && y >= 0 && y < h && L.x0 + k < w) ? to_f32<T>(in[(size_t)y * w + L.x0 + k]) : 0.f;
+            }
+            if (L.any && y >= 0 && y < h) {
+                float o[VEC];
+                k2s_row<VEC, F>(q, g, t, o);
+                k2s_store<T, VEC>(out, y, w, L, o);
+            }
+        }
+        // the slot is read: refill it with block m + NSB (or an empty group)
+        if (m + NSB < nblk) issue(m + NSB);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 }  // namespace dgf

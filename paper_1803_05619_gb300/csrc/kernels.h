@@ -14,6 +14,7 @@ namespace dgf {
 
 struct TmaPair;
 struct K3Maps;
+struct K2Map;
 constexpr int kStripWarpsPerCta = 8;
 
 // Shared-memory pitch (float2 columns) of a K2 tile row.
@@ -50,6 +51,14 @@ cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P
 cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P, const float2* dcoef,
                       void* dP, void* dG, int planes, int h, int w, int r, float eps, const LowCfg& c,
                       cudaStream_t s);
+// K2 as warp strips (mode 0, integer F in {2, 4, 8} dividing vec); LS =
+// low-res rows per segment; map: TMA staging of `in` (16-byte vectors) or null.
+bool k2_strip_ok(int vec, int F);
+// shared memory of the persistent batched K2 in strip form (its slot rings)
+size_t k2_strip_batched_smem(int esize, int vec, int F);
+cudaError_t launch_k2_strip(dgf_dtype dt, const float2* coef, const void* in, void* out, int planes, int h_l,
+                            int w_l, int h, int w, int vec, int F, int LS, const K2Map* map, uint32_t* status,
+                            cudaStream_t s);
 cudaError_t launch_k2(dgf_dtype dt, int mode, const float2* coef, const void* in, void* out, int planes,
                       int h_l, int w_l, int h, int w, int vec, int F, int TH, cudaStream_t s);
 cudaError_t launch_k3(dgf_dtype dt, const float2* coef, const void* R, const void* G, void* dG,

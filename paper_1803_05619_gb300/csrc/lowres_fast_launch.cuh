@@ -61,13 +61,15 @@ __global__ void __launch_bounds__(kStripWarps * 32) k1_coef_strip(const TG* __re
     coef_strip<TG, TP, R>(G + plane * hw, P + plane * hw, coef + plane * hw, s, eps);
 }
 
-// Warp-strip K4 (R = 1, 2), same work decomposition as k1_coef_strip.
+// Warp-strip K4 (R = 1, 2), same work decomposition as k1_coef_strip, in
+// CTAs of 4 warps (its register footprint is large, and small CTAs let the
+// SM keep more of them resident).
 template <typename TG, typename TP, typename TD, int R>
-__global__ void __launch_bounds__(kStripWarps * 32)
+__global__ void __launch_bounds__(kK4StripWarps * 32)
     k4_lowres_bwd_strip(const TG* __restrict__ G, const TP* __restrict__ P, const float2* __restrict__ dcoef,
                         TP* __restrict__ dP, TD* __restrict__ dG, int h, int w, float eps, int seg, int nstrip,
                         int nseg, int planes) {
-    const int gw = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
+    const int gw = blockIdx.x * kK4StripWarps + (threadIdx.x >> 5);
     if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
     const int strip = gw % nstrip, rest = gw / nstrip;
     const int sg = rest % nseg, plane = rest / nseg;
@@ -135,8 +137,8 @@ static cudaError_t k4f_go(const void* G, const void* P, const float2* dcoef, voi
         if (c.fast == 2) {
             const int seg = c.a, nstrip = (w + (32 - 4 * R) - 1) / (32 - 4 * R), nseg = (h + seg - 1) / seg;
             const long long warps = (long long)nstrip * nseg * planes;
-            const int ctas = (int)((warps + kStripWarps - 1) / kStripWarps);
-            k4_lowres_bwd_strip<TG, TP, TD, R><<<ctas, kStripWarps * 32, 0, s>>>(
+            const int ctas = (int)((warps + kK4StripWarps - 1) / kK4StripWarps);
+            k4_lowres_bwd_strip<TG, TP, TD, R><<<ctas, kK4StripWarps * 32, 0, s>>>(
                 static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef, static_cast<TP*>(dP),
                 static_cast<TD*>(dG), h, w, eps, seg, nstrip, nseg, planes);
             return cudaGetLastError();

@@ -24,7 +24,8 @@
 
 namespace dgf {
 
-constexpr int kStripWarps = 8;  // warps per CTA (independent strips)
+constexpr int kStripWarps = 8;    // warps per CTA of the K1 strips (independent strips)
+constexpr int kK4StripWarps = 4;  // warps per CTA of the K4 strips
 
 __device__ __forceinline__ float shfl_up(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ float shfl_dn(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }

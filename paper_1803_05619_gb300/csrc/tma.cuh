@@ -35,6 +35,11 @@ struct K3Maps {
     CUtensorMap r, g;  // 64-byte aligned opaque descriptors
 };
 
+// Tensor map of K2's high-resolution input (I_h), boxes as for K3.
+struct K2Map {
+    CUtensorMap m;
+};
+
 constexpr long long kWaitLimit = 1LL << 22;  // try_wait polls before giving up
 constexpr uint32_t kStatusTimeout = 1u;
 
