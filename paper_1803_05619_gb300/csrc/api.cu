@@ -124,7 +124,7 @@ static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr int kMaxRadius = 16;
 
 struct Layout {
-    size_t coef, dcoef, gl, dgl, partials, total;
+    size_t coef, dcoef, stats, gl, dgl, partials, total;
 };
 
 static Layout layout(int N, int C, int h_l, int w_l, bool guided) {
@@ -135,6 +135,8 @@ static Layout layout(int N, int C, int h_l, int w_l, bool guided) {
     off += align256(lo * sizeof(float2));
     L.dcoef = off;
     off += align256(lo * sizeof(float2));
+    L.stats = off;  // window statistics kept from the backward K1 pass for K4
+    off += align256(lo * sizeof(float4));
     if (guided) {
         L.gl = off;
         off += align256(lo * sizeof(float));
@@ -369,7 +371,14 @@ static bool make_k3_maps(K3Maps& m, const void* R, const void* G, dgf_dtype dt, 
 // wider and the kernel computes the offset per tile.
 static bool k1_box(const LowCfg& c, int r, int esz, int& bx, int& by, int& off) {
     const int U = 16 / esz;
-    if (c.fast == 2) return false;  // warp strips load rows directly
+    if (c.fast == 2) {
+        // warp strips: 32 columns plus one 16-byte unit (the strip's first
+        // column is rounded down to it), whole blocks of ring periods
+        bx = 32 + U;
+        by = r == 1 ? 6 : 10;
+        off = 0;
+        return true;
+    }
     if (c.fast) {
         const int EX2 = c.a + 2 * r;
         bx = (EX2 + U - 1 + U - 1) / U * U;
@@ -400,7 +409,9 @@ static TmaPair make_tma_pair(const void* G, dgf_dtype dg, const void* P, dgf_dty
     if (!make_tma(t.a, G, tma_type(dg), (int)esize(dg), planes, h, w, bxa, bya, offa)) return t;
     if (!make_tma(t.b, P, tma_type(dp), (int)esize(dp), planes, h, w, bxb, byb, offb)) return t;
     const size_t need = (size_t)bxa * bya * esize(dg) + (size_t)bxb * byb * esize(dp) + 256;
-    if (c.fast) {
+    if (c.fast == 2) {
+        // the strip kernel sizes its own slot rings (well under the limit)
+    } else if (c.fast) {
         if (k1_fast_smem_bytes(r, c.a, c.b, need) > smem_limit()) return t;
         landing = need;
     } else {
@@ -431,6 +442,32 @@ static cudaError_t launch_k2_plan(dgf_dtype dt, const float2* coef, const void* 
                                status_ptr(), s);
     }
     return launch_k2(dt, 0, coef, in, out, planes, h_l, w_l, h, w, p.vec, p.F, shape, s);
+}
+
+// K4 strips' tensor maps: G, P (box 32 + U columns x RB rows) and d Abar,
+// d bbar as float pairs (box 2 x 34 floats).  Disabled when any map cannot
+// be made (alignment) or for the tile forms.
+static TmaTriple make_k4_maps(const void* G, dgf_dtype dg, const void* P, dgf_dtype dp, const float2* dcoef,
+                              int planes, int h, int w, int r, const LowCfg& c) {
+    TmaTriple t;
+    memset(&t, 0, sizeof t);
+    t.enabled = 0;
+    if (!g_tma_allowed || c.fast != 2) return t;
+    const int rb = r == 1 ? 6 : 10;
+    const int eg = (int)esize(dg), ep = (int)esize(dp);
+    if (!make_tma(t.a, G, tma_type(dg), eg, planes, h, w, 32 + 16 / eg, rb, 0)) return t;
+    if (!make_tma(t.b, P, tma_type(dp), ep, planes, h, w, 32 + 16 / ep, rb, 0)) return t;
+    if (!make_tma(t.c, dcoef, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, planes, h, 2 * w, 2 * 34, rb, 0)) return t;
+    t.enabled = 1;
+    return t;
+}
+
+// stats: window statistics saved by the backward K1 pass (strip forms), or null
+static cudaError_t run_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP,
+                          void* dG, int planes, int h_l, int w_l, int r, float eps, const LowCfg& c, cudaStream_t s,
+                          const float4* stats = nullptr) {
+    const TmaTriple tma = make_k4_maps(G, gf32 ? DGF_F32 : dt, P, dt, dcoef, planes, h_l, w_l, r, c);
+    return launch_k4(dt, gf32, G, P, dcoef, dP, dG, planes, h_l, w_l, r, eps, c, &tma, status_ptr(), stats, s);
 }
 
 // --------------------------------------------------------------- validation
@@ -486,7 +523,7 @@ static void tune_k1(dgf_dtype dt, bool gf32, const void* G, const void* P, float
         TmaPair tma = make_tma_pair(G, gf32 ? DGF_F32 : dt, P, dt, planes, h_l, w_l, r, c, landing);
         const size_t smem = k1_cfg_smem(c, r, tma.enabled ? landing : 0);
         const float ms = time_launch(s, [&] {
-            return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, c, tma, smem, status_ptr(), s);
+            return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, c, tma, smem, status_ptr(), nullptr, s);
         }, 3);
         if (ms > 0.f && ms < best) {
             best = ms;
@@ -500,7 +537,8 @@ static void tune_k1(dgf_dtype dt, bool gf32, const void* G, const void* P, float
 }
 
 static void tune_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP, void* dG,
-                    int planes, int h_l, int w_l, int r, float eps, cudaStream_t s, Plan& p) {
+                    int planes, int h_l, int w_l, int r, float eps, cudaStream_t s, Plan& p,
+                    const float4* stats = nullptr) {
     TuneKey key{4, (int)dt, r, 0, 0, gf32 ? 1 : 0};
     int a, b;
     if (tune_lookup(key, a, b)) return;
@@ -508,7 +546,7 @@ static void tune_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const
     LowCfg bc = p.k4;
     for (const LowCfg& c : low_candidates(r, true)) {
         const float ms = time_launch(s, [&] {
-            return launch_k4(dt, gf32, G, P, dcoef, dP, dG, planes, h_l, w_l, r, eps, c, s);
+            return run_k4(dt, gf32, G, P, dcoef, dP, dG, planes, h_l, w_l, r, eps, c, s, c.fast == 2 ? stats : nullptr);
         }, 3);
         if (ms > 0.f && ms < best) {
             best = ms;
@@ -575,13 +613,14 @@ static void tune_k3(dgf_dtype dt, const float2* coef, const void* R, const void*
 }
 
 static cudaError_t run_k1(Launcher& L, dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef,
-                          int planes, int h_l, int w_l, int r, float eps, const Plan& p, cudaStream_t s) {
+                          int planes, int h_l, int w_l, int r, float eps, const Plan& p, cudaStream_t s,
+                          float4* stats = nullptr) {
     size_t landing = 0;
     TmaPair tma = make_tma_pair(G, gf32 ? DGF_F32 : dt, P, dt, planes, h_l, w_l, r, p.k1, landing);
     const size_t smem = k1_cfg_smem(p.k1, r, tma.enabled ? landing : 0);
     uint32_t* st = status_ptr();
     return L.run("k1_lowres_coef", [&] {
-        return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, st, s);
+        return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, st, stats, s);
     });
 }
 
@@ -759,10 +798,15 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
     if (g == nullptr) {
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
         const bool tuning = tune_enabled() && !stream_capturing(s);
-        // coefficients are recomputed, not saved from the forward call
-        if (dI_h != nullptr) {
-            if (tuning) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
-            e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+        // coefficients are recomputed, not saved from the forward call; with
+        // both low-res stages in strip form the K1 pass also keeps each
+        // window's statistics for K4, which then skips recomputing them
+        const bool need_k4 = dp_l != nullptr || dI_l != nullptr;
+        if (tuning && (dI_h != nullptr || need_k4)) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
+        const bool use_stats = need_k4 && p.k1.fast == 2 && p.k4.fast == 2;
+        float4* stats = use_stats ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr;
+        if (dI_h != nullptr || use_stats) {
+            e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s, stats);
             if (e != cudaSuccess) return cuda_fail(e, "k1");
         }
         if (p.k3_fast) {
@@ -786,10 +830,11 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
             });
             if (e != cudaSuccess) return cuda_fail(e, "k3 general");
         }
-        if (dp_l != nullptr || dI_l != nullptr) {
-            if (tuning) tune_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, s, p);
+        if (need_k4) {
+            if (tuning) tune_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, s, p, stats);
+            const float4* k4_stats = p.k4.fast == 2 ? stats : nullptr;
             e = L.run("k4_lowres_bwd", [&] {
-                return launch_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4, s);
+                return run_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4, s, k4_stats);
             });
             if (e != cudaSuccess) return cuda_fail(e, "k4");
         }
@@ -814,8 +859,8 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
     if (e != cudaSuccess) return cuda_fail(e, "k3g");
     if (dp_l != nullptr || need_hi) {
         e = L.run("k4_lowres_bwd", [&] {
-            return launch_k4(dt, true, G_l, p_l, dcoef, dp_l, need_hi ? dG_l : nullptr, planes, h_l, w_l, r, eps,
-                             p.k4, s);
+            return run_k4(dt, true, G_l, p_l, dcoef, dp_l, need_hi ? dG_l : nullptr, planes, h_l, w_l, r, eps,
+                          p.k4, s);
         });
         if (e != cudaSuccess) return cuda_fail(e, "k4");
     }
@@ -1094,7 +1139,8 @@ extern "C" dgf_status dgf_forward_noalloc(const void* p_l, const void* I_l, cons
     TmaPair tma = make_tma_pair(I_l, dt, p_l, dt, planes, h_l, w_l, r, p.k1, landing);
     const size_t smem = k1_cfg_smem(p.k1, r, tma.enabled ? landing : 0);
     g_launches.fetch_add(1);
-    cudaError_t e = launch_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, status_ptr(), s);
+    cudaError_t e =
+        launch_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, status_ptr(), nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "k1");
     g_launches.fetch_add(1);
     e = launch_k2_plan(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, p, p.k2_strip ? p.k2_ls : p.k2_th, s);

@@ -13,6 +13,7 @@
 namespace dgf {
 
 struct TmaPair;
+struct TmaTriple;
 struct K3Maps;
 struct K2Map;
 constexpr int kStripWarpsPerCta = 8;
@@ -47,10 +48,10 @@ bool k3_fast_ok(int vec, int F);
 
 cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P, float2* coef, int planes,
                       int h, int w, int r, float eps, const LowCfg& c, const TmaPair& tma, size_t smem,
-                      uint32_t* status, cudaStream_t s);
+                      uint32_t* status, float4* stats, cudaStream_t s);
 cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P, const float2* dcoef,
                       void* dP, void* dG, int planes, int h, int w, int r, float eps, const LowCfg& c,
-                      cudaStream_t s);
+                      const TmaTriple* tma, uint32_t* status, const float4* stats, cudaStream_t s);
 // K2 as warp strips (mode 0, integer F in {2, 4, 8} dividing vec); LS =
 // low-res rows per segment; map: TMA staging of `in` (16-byte vectors) or null.
 bool k2_strip_ok(int vec, int F);
@@ -88,26 +89,31 @@ cudaError_t launch_wreduce(const float* partials, int nblocks, float* dW, int hi
 template <int R>
 cudaError_t launch_k1_fast(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes,
                            int h, int w, float eps, const LowCfg& c, const TmaPair& tma, size_t smem,
-                           uint32_t* status, cudaStream_t s);
+                           uint32_t* status, float4* stats, cudaStream_t s);
 template <int R>
 cudaError_t launch_k4_fast(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP,
-                           void* dG, int planes, int h, int w, float eps, const LowCfg& c, cudaStream_t s);
+                           void* dG, int planes, int h, int w, float eps, const LowCfg& c, const TmaTriple* tma,
+                           uint32_t* status, const float4* stats, cudaStream_t s);
 extern template cudaError_t launch_k1_fast<1>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
-                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, float4*, cudaStream_t);
 extern template cudaError_t launch_k1_fast<2>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
-                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, float4*, cudaStream_t);
 extern template cudaError_t launch_k1_fast<4>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
-                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, float4*, cudaStream_t);
 extern template cudaError_t launch_k1_fast<8>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
-                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+                                              float, const LowCfg&, const TmaPair&, size_t, uint32_t*, float4*, cudaStream_t);
 extern template cudaError_t launch_k4_fast<1>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*,
-                                              int, int, int, float, const LowCfg&, cudaStream_t);
+                                              int, int, int, float, const LowCfg&, const TmaTriple*, uint32_t*, const float4*,
+                                              cudaStream_t);
 extern template cudaError_t launch_k4_fast<2>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*,
-                                              int, int, int, float, const LowCfg&, cudaStream_t);
+                                              int, int, int, float, const LowCfg&, const TmaTriple*, uint32_t*, const float4*,
+                                              cudaStream_t);
 extern template cudaError_t launch_k4_fast<4>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*,
-                                              int, int, int, float, const LowCfg&, cudaStream_t);
+                                              int, int, int, float, const LowCfg&, const TmaTriple*, uint32_t*, const float4*,
+                                              cudaStream_t);
 extern template cudaError_t launch_k4_fast<8>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*,
-                                              int, int, int, float, const LowCfg&, cudaStream_t);
+                                              int, int, int, float, const LowCfg&, const TmaTriple*, uint32_t*, const float4*,
+                                              cudaStream_t);
 
 // Persistent batched kernels (function pointers for graph nodes).
 cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn);

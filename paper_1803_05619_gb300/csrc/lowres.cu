@@ -298,14 +298,14 @@ static cudaError_t k1_go(const void* G, const void* P, float2* coef, int planes,
 
 cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P, float2* coef, int planes,
                       int h, int w, int r, float eps, const LowCfg& c, const TmaPair& tma, size_t smem,
-                      uint32_t* status, cudaStream_t s) {
+                      uint32_t* status, float4* stats, cudaStream_t s) {
     if (planes == 0) return cudaSuccess;
     if (c.fast) {
         switch (r) {
-            case 1: return launch_k1_fast<1>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
-            case 2: return launch_k1_fast<2>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
-            case 4: return launch_k1_fast<4>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
-            case 8: return launch_k1_fast<8>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, s);
+            case 1: return launch_k1_fast<1>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, stats, s);
+            case 2: return launch_k1_fast<2>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, stats, s);
+            case 4: return launch_k1_fast<4>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, stats, s);
+            case 8: return launch_k1_fast<8>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, stats, s);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -339,14 +339,14 @@ static cudaError_t k4_go(const void* G, const void* P, const float2* dcoef, void
 
 cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P, const float2* dcoef,
                       void* dP, void* dG, int planes, int h, int w, int r, float eps, const LowCfg& c,
-                      cudaStream_t s) {
+                      const TmaTriple* tma, uint32_t* status, const float4* stats, cudaStream_t s) {
     if (planes == 0) return cudaSuccess;
     if (c.fast) {
         switch (r) {
-            case 1: return launch_k4_fast<1>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
-            case 2: return launch_k4_fast<2>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
-            case 4: return launch_k4_fast<4>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
-            case 8: return launch_k4_fast<8>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, s);
+            case 1: return launch_k4_fast<1>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, tma, status, stats, s);
+            case 2: return launch_k4_fast<2>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, tma, status, stats, s);
+            case 4: return launch_k4_fast<4>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, tma, status, stats, s);
+            case 8: return launch_k4_fast<8>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, tma, status, stats, s);
             default: return cudaErrorInvalidValue;
         }
     }

@@ -3,5 +3,5 @@
 
 namespace dgf {
 template cudaError_t launch_k1_fast<2>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int, float,
-                                       const LowCfg&, const TmaPair&, size_t, uint32_t*, cudaStream_t);
+                                       const LowCfg&, const TmaPair&, size_t, uint32_t*, float4*, cudaStream_t);
 }  // namespace dgf

@@ -3,5 +3,6 @@
 
 namespace dgf {
 template cudaError_t launch_k4_fast<1>(dgf_dtype, bool, const void*, const void*, const float2*, void*, void*, int,
-                                       int, int, float, const LowCfg&, cudaStream_t);
+                                       int, int, float, const LowCfg&, const TmaTriple*, uint32_t*, const float4*,
+                                       cudaStream_t);
 }  // namespace dgf

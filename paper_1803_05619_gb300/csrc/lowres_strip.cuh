@@ -21,6 +21,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace dgf {
 
@@ -153,10 +154,12 @@ __device__ __forceinline__ StripLane<R> strip_lane(int x, int w) {
 
 // K1 for input row e entering ring slot U.  INT: interior ring period (all
 // rows and columns of every window touched are inside the image and complete).
+// With `stats` non-null the window statistics the backward pass needs
+// (mu, nu, 1/(var + eps), A) are written too, for the segment's rows.
 template <typename TG, typename TP, int R, bool INT>
 __device__ __forceinline__ void strip_k1_row(StripRing<R>& q, const StripLane<R>& ln, int U, float gvu, float pvu,
                                              int e, int e_first, int x, float2* __restrict__ coef,
-                                             const StripGeom& s, float eps) {
+                                             float4* __restrict__ stats, const StripGeom& s, float eps) {
     constexpr int W = 2 * R + 1;
     constexpr float kInvW2 = 1.f / (float)(W * W);
     const int lane = threadIdx.x & 31;
@@ -168,8 +171,11 @@ __device__ __forceinline__ void strip_k1_row(StripRing<R>& q, const StripLane<R>
         const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
         float mu, nu, var, cov;
         strip_window<R, INT>(q, ln, ny, mu, nu, var, cov);
-        A = cov * rcp_approx(var + eps);
+        const float ive = rcp_approx(var + eps);
+        A = cov * ive;
         b = fmaf(-A, mu, nu);
+        if (stats != nullptr && ln.out && ce >= s.y0 && ce < s.y0 + s.seg)
+            stats[(size_t)ce * s.w + x] = make_float4(mu, nu, ive, A);
     }
     // ---- level 2: horizontal box sums of A, b, then the vertical sum over the ring
     q.ha[U] = hsum<R>(A);
@@ -194,7 +200,7 @@ __device__ __forceinline__ void strip_k1_row(StripRing<R>& q, const StripLane<R>
 // one strip segment.  Writes Abar, bbar for lanes [2R, 32 - 2R).
 template <typename TG, typename TP, int R>
 __device__ void coef_strip(const TG* __restrict__ G, const TP* __restrict__ P, float2* __restrict__ coef,
-                           const StripGeom& s, float eps) {
+                           const StripGeom& s, float eps, float4* __restrict__ stats = nullptr) {
     constexpr int W = 2 * R + 1;
     const int x = s.x0 + (int)(threadIdx.x & 31);
     const StripLane<R> ln = strip_lane<R>(x, s.w);
@@ -231,17 +237,141 @@ __device__ void coef_strip(const TG* __restrict__ G, const TP* __restrict__ P, f
         if (row_int) {
 #pragma unroll
             for (int u = 0; u < W; ++u)
-                strip_k1_row<TG, TP, R, true>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, s, eps);
+                strip_k1_row<TG, TP, R, true>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, stats, s,
+                                                  eps);
         } else {
 #pragma unroll
             for (int u = 0; u < W; ++u) {
                 if (base + u >= e_last) break;  // uniform across the warp
-                strip_k1_row<TG, TP, R, false>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, s, eps);
+                strip_k1_row<TG, TP, R, false>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, stats, s,
+                                                   eps);
             }
         }
     }
 }
 
+
+// ------------------------------------------------- TMA staging of the strips
+// A warp's rows arrive in blocks of RB rows (whole ring periods) through a
+// ring of NS shared-memory slots, one mbarrier per slot.  Each input is one
+// tiled copy per block: box (32 + U) columns x RB rows starting at the
+// strip's first column rounded down to the 16-byte unit U (the lane reads at
+// its offset inside the box); rows and columns outside the image read as
+// zero, exactly what the plain loads supply.  The warp's lane 0 refills a
+// slot once the warp has read it.  Waits are bounded: on a timeout the warp
+// records it in the status word, waits (bounded) for its copies in flight
+// and stops.
+template <int R>
+struct StripTmaCfg {
+    static constexpr int RB = R == 1 ? 6 : 10;  // rows per block (2 ring periods)
+    static constexpr int NS = 4;                // slots per warp
+};
+
+__host__ __device__ constexpr int strip_box_cols(int esize) { return 32 + 16 / esize; }
+__host__ __device__ constexpr int align128i(int b) { return (b + 127) / 128 * 128; }
+// bytes of one input's box in a slot (rounded to 128) for element size esize
+__host__ __device__ constexpr int strip_box_bytes(int R, int esize, int rows) {
+    return align128i(rows * strip_box_cols(esize) * esize);
+}
+
+__device__ __forceinline__ int floor_to(int x, int u) { return x >= 0 ? x / u * u : -((-x + u - 1) / u) * u; }
+
+template <typename TG, typename TP, int R>
+__device__ void coef_strip_tma(const TmaPair* maps, int plane, float2* __restrict__ coef, float4* __restrict__ stats,
+                               const StripGeom& s, float eps, unsigned char* ring, uint64_t* bars,
+                               uint32_t* status) {
+    constexpr int W = 2 * R + 1, RB = StripTmaCfg<R>::RB, NS = StripTmaCfg<R>::NS, NP = RB / W;
+    constexpr int UG = 16 / (int)sizeof(TG), UP = 16 / (int)sizeof(TP);
+    constexpr int BXG = 32 + UG, BXP = 32 + UP;
+    constexpr int BG = strip_box_bytes(R, (int)sizeof(TG), RB), BP = strip_box_bytes(R, (int)sizeof(TP), RB);
+    constexpr int SLOT = BG + BP;
+    constexpr uint32_t TX = (uint32_t)(RB * BXG * (int)sizeof(TG) + RB * BXP * (int)sizeof(TP));
+    const int lane = threadIdx.x & 31;
+    const int x = s.x0 + lane;
+    const StripLane<R> ln = strip_lane<R>(x, s.w);
+    const bool cols_int = s.x0 >= 0 && s.x0 + 32 <= s.w;
+    StripRing<R> q;
+#pragma unroll
+    for (int k = 0; k < W; ++k) q.mg[k] = q.mp[k] = q.sgg[k] = q.sgp[k] = q.vr[k] = q.ha[k] = q.hb[k] = 0.f;
+    const int e_first = s.y0 - 2 * R;
+    const int e_last = min(s.y0 + s.seg, s.h) + 2 * R;
+    const int nblk = (e_last - e_first + RB - 1) / RB;
+    const int xg = floor_to(s.x0, UG), xp = floor_to(s.x0, UP);
+    const int og = s.x0 - xg + lane, op = s.x0 - xp + lane;
+    const uint32_t ring_s = smem_u32(ring), bar_s = smem_u32(bars);
+    auto issue = [&](int m) {  // lane 0: block m into slot m % NS
+        const int slot = m % NS;
+        const uint32_t bar = bar_s + 8u * slot, dst = ring_s + (uint32_t)(slot * SLOT);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TX) : "memory");
+        tma_load_3d(dst, &maps->a.map, xg, e_first + m * RB, plane, bar);
+        tma_load_3d(dst + BG, &maps->b.map, xp, e_first + m * RB, plane, bar);
+    };
+    if (lane == 0) {
+        for (int k = 0; k < NS; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * k) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int m = 0; m < min(NS, nblk); ++m) issue(m);
+    }
+    __syncwarp();
+    int m = 0;
+    bool ok = true;
+    for (; m < nblk; ++m) {
+        const int slot = m % NS;
+        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NS) & 1), kWaitLimit))) {
+            ok = false;
+            break;
+        }
+        const TG* sg = reinterpret_cast<const TG*>(ring + slot * SLOT) + og;
+        const TP* sp = reinterpret_cast<const TP*>(ring + slot * SLOT + BG) + op;
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+            const int base = e_first + m * RB + pp * W;
+            float gv[W], pv[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                gv[u] = to_f32<TG>(sg[(pp * W + u) * BXG]);
+                pv[u] = to_f32<TP>(sp[(pp * W + u) * BXP]);
+            }
+            if (pp == NP - 1) {
+                __syncwarp();  // every lane has read the slot
+                if (lane == 0 && m + NS < nblk) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(m + NS);
+                }
+            }
+            if (base >= e_last) continue;  // uniform
+            const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W <= s.h &&
+                                 base + W <= e_last;
+            if (row_int) {
+#pragma unroll
+                for (int u = 0; u < W; ++u)
+                    strip_k1_row<TG, TP, R, true>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, stats, s,
+                                                  eps);
+            } else {
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    if (base + u >= e_last) break;  // uniform across the warp
+                    strip_k1_row<TG, TP, R, false>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, stats, s,
+                                                   eps);
+                }
+            }
+        }
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        for (int qb = m; qb < nblk && qb < m + NS; ++qb)
+            mbar_wait(bar_s + 8u * (qb % NS), (uint32_t)((qb / NS) & 1), kWaitLimit);
+    }
+}
+
+// shared memory of one CTA of K1 strips staged by TMA (kStripWarps warps)
+template <typename TG, typename TP, int R>
+__host__ __device__ constexpr int k1_strip_tma_smem() {
+    return kStripWarps * StripTmaCfg<R>::NS *
+               (strip_box_bytes(R, (int)sizeof(TG), StripTmaCfg<R>::RB) +
+                strip_box_bytes(R, (int)sizeof(TP), StripTmaCfg<R>::RB)) +
+           kStripWarps * StripTmaCfg<R>::NS * 8;
+}
 
 // ------------------------------------------------------------------- K4
 // Algorithm 1 at low resolution for one strip segment.  Per window m (row
@@ -400,6 +530,272 @@ __device__ void lowres_bwd_strip(const TG* __restrict__ G, const TP* __restrict_
                 if (base + u >= e_last) break;  // uniform across the warp
                 strip_k4_row<TG, TP, TD, R, false>(q, z, ln, u, gv[u], pv[u], dv[u], base + u, e_first, x, dP,
                                                    dG, s, eps, KG, KP);
+            }
+        }
+    }
+}
+
+
+// K4 strip with TMA staging of G, P and d Abar, d bbar (same slots as K1's,
+// one more box per slot).
+template <typename TG, typename TP, typename TD, int R>
+__device__ void lowres_bwd_strip_tma(const TmaTriple* maps, int plane, TP* __restrict__ dP, TD* __restrict__ dG,
+                                     const StripGeom& s, float eps, unsigned char* ring, uint64_t* bars,
+                                     uint32_t* status) {
+    constexpr int W = 2 * R + 1, RB = StripTmaCfg<R>::RB, NS = StripTmaCfg<R>::NS, NP = RB / W;
+    constexpr int UG = 16 / (int)sizeof(TG), UP = 16 / (int)sizeof(TP);
+    constexpr int BXG = 32 + UG, BXP = 32 + UP, BXD = 2 * (32 + 2);  // d: float pairs
+    constexpr int BG = strip_box_bytes(R, (int)sizeof(TG), RB), BP = strip_box_bytes(R, (int)sizeof(TP), RB);
+    constexpr int BD = align128i(RB * BXD * 4);
+    constexpr int SLOT = BG + BP + BD;
+    constexpr uint32_t TX =
+        (uint32_t)(RB * BXG * (int)sizeof(TG) + RB * BXP * (int)sizeof(TP) + RB * BXD * 4);
+    const int lane = threadIdx.x & 31;
+    const int x = s.x0 + lane;
+    const StripLane<R> ln = strip_lane<R>(x, s.w);
+    const bool cols_int = s.x0 >= R && s.x0 + 32 + R <= s.w;
+    StripRing<R> q;
+    StripBwdRing<R> z;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        q.mg[k] = q.mp[k] = q.sgg[k] = q.sgp[k] = q.vr[k] = 0.f;
+        z.hda[k] = z.hdb[k] = z.hq0[k] = z.hq1[k] = z.hq2[k] = z.hq3[k] = z.rg[k] = z.rp[k] = 0.f;
+    }
+    const int e_first = s.y0 - 2 * R;
+    const int e_last = min(s.y0 + s.seg, s.h) + 2 * R;
+    const int nblk = (e_last - e_first + RB - 1) / RB;
+    const int xg = floor_to(s.x0, UG), xp = floor_to(s.x0, UP), xd = floor_to(s.x0, 2);
+    const int og = s.x0 - xg + lane, op = s.x0 - xp + lane, od = 2 * (s.x0 - xd + lane);
+    const uint32_t ring_s = smem_u32(ring), bar_s = smem_u32(bars);
+    auto issue = [&](int m) {  // lane 0: block m into slot m % NS
+        const int slot = m % NS;
+        const uint32_t bar = bar_s + 8u * slot, dst = ring_s + (uint32_t)(slot * SLOT);
+        const int y = e_first + m * RB;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TX) : "memory");
+        tma_load_3d(dst, &maps->a.map, xg, y, plane, bar);
+        tma_load_3d(dst + BG, &maps->b.map, xp, y, plane, bar);
+        tma_load_3d(dst + BG + BP, &maps->c.map, 2 * xd, y, plane, bar);
+    };
+    if (lane == 0) {
+        for (int k = 0; k < NS; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * k) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int m = 0; m < min(NS, nblk); ++m) issue(m);
+    }
+    __syncwarp();
+    float KG = 0.f, KP = 0.f;
+    int m = 0;
+    bool ok = true;
+    for (; m < nblk; ++m) {
+        const int slot = m % NS;
+        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NS) & 1), kWaitLimit))) {
+            ok = false;
+            break;
+        }
+        const TG* sg = reinterpret_cast<const TG*>(ring + slot * SLOT) + og;
+        const TP* sp = reinterpret_cast<const TP*>(ring + slot * SLOT + BG) + op;
+        const float* sd = reinterpret_cast<const float*>(ring + slot * SLOT + BG + BP) + od;
+        if (m == 0) {
+            // shift: mean of row y0 (row 2R of the first block) over the output lanes
+            const bool use = ln.out;
+            float a = use ? to_f32<TG>(sg[2 * R * BXG]) : 0.f, b = use ? to_f32<TP>(sp[2 * R * BXP]) : 0.f;
+            float cn = use ? 1.f : 0.f;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, off);
+                b += __shfl_xor_sync(0xffffffffu, b, off);
+                cn += __shfl_xor_sync(0xffffffffu, cn, off);
+            }
+            KG = cn > 0.f ? a / cn : 0.f;
+            KP = cn > 0.f ? b / cn : 0.f;
+        }
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+            const int base = e_first + m * RB + pp * W;
+            float gv[W], pv[W];
+            float2 dv[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                gv[u] = to_f32<TG>(sg[(pp * W + u) * BXG]);
+                pv[u] = to_f32<TP>(sp[(pp * W + u) * BXP]);
+                dv[u] = *reinterpret_cast<const float2*>(sd + (pp * W + u) * BXD);
+            }
+            if (pp == NP - 1) {
+                __syncwarp();  // every lane has read the slot
+                if (lane == 0 && m + NS < nblk) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(m + NS);
+                }
+            }
+            if (base >= e_last) continue;  // uniform
+            const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W + R <= s.h &&
+                                 base + W <= e_last;
+            if (row_int) {
+#pragma unroll
+                for (int u = 0; u < W; ++u)
+                    strip_k4_row<TG, TP, TD, R, true>(q, z, ln, u, gv[u], pv[u], dv[u], base + u, e_first, x, dP,
+                                                      dG, s, eps, KG, KP);
+            } else {
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    if (base + u >= e_last) break;  // uniform across the warp
+                    strip_k4_row<TG, TP, TD, R, false>(q, z, ln, u, gv[u], pv[u], dv[u], base + u, e_first, x, dP,
+                                                       dG, s, eps, KG, KP);
+                }
+            }
+        }
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        for (int qb = m; qb < nblk && qb < m + NS; ++qb)
+            mbar_wait(bar_s + 8u * (qb % NS), (uint32_t)((qb / NS) & 1), kWaitLimit);
+    }
+}
+
+// shared memory of one CTA of K4 strips staged by TMA (kK4StripWarps warps)
+template <typename TG, typename TP, int R>
+__host__ __device__ constexpr int k4_strip_tma_smem() {
+    return kK4StripWarps * StripTmaCfg<R>::NS *
+               (strip_box_bytes(R, (int)sizeof(TG), StripTmaCfg<R>::RB) +
+                strip_box_bytes(R, (int)sizeof(TP), StripTmaCfg<R>::RB) +
+                align128i(StripTmaCfg<R>::RB * 2 * (32 + 2) * 4)) +
+           kK4StripWarps * StripTmaCfg<R>::NS * 8;
+}
+
+// K4 strip from saved window statistics: the backward K1 pass wrote
+// (mu, nu, 1/(var + eps), A) of every window, so this pass forms only the
+// box sums of d Abar / N, d bbar / N, the four window quantities and their
+// box sums (same arithmetic as lowres_bwd_strip, without the statistics).
+template <typename TG, typename TP, typename TD, int R, bool INT>
+__device__ __forceinline__ void strip_k4s_row(StripBwdRing<R>& z, const StripLane<R>& ln, int U, float gvu,
+                                              float pvu, float2 dvu, float4 st, int e, int e_first, int x,
+                                              TP* __restrict__ dP, TD* __restrict__ dG, const StripGeom& s, float KG,
+                                              float KP) {
+    constexpr int W = 2 * R + 1;
+    constexpr float kInvW2 = 1.f / (float)(W * W);
+    const int lane = threadIdx.x & 31;
+    const bool row_in = e >= 0 && e < s.h;
+    z.rg[U] = gvu;
+    z.rp[U] = pvu;
+    {
+        const float inn = INT ? kInvW2
+                              : ((ln.xin && row_in) ? inv_count(ln.nx * (min(e + R, s.h - 1) - max(e - R, 0) + 1))
+                                                    : 0.f);
+        z.hda[U] = hsum<R>(dvu.x * inn);
+        z.hdb[U] = hsum<R>(dvu.y * inn);
+    }
+    const int ce = e - R;
+    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+    if (INT || (ln.xin && ce >= 0 && ce < s.h && e - e_first >= 2 * R)) {
+        const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
+        float dA = 0.f, db = 0.f;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            dA += z.hda[k];
+            db += z.hdb[k];
+        }
+        const float mu = st.x, nu = st.y, ive = st.z, A = st.w;
+        const float gamma = fmaf(-db, mu, dA) * ive;
+        const float beta = -gamma * A;
+        const float inn = INT ? kInvW2 : inv_count(ln.nx * ny);
+        const float mus = mu - KG, nus = nu - KP;
+        q0 = gamma * inn;
+        q1 = beta * inn;
+        q2 = fmaf(-gamma, mus, db) * inn;
+        q3 = fmaf(gamma, nus, fmaf(2.f * beta, mus, db * A)) * inn;
+    }
+    z.hq0[U] = hsum<R>(q0);
+    z.hq1[U] = hsum<R>(q1);
+    z.hq2[U] = hsum<R>(q2);
+    z.hq3[U] = hsum<R>(q3);
+    const int co = ce - R;
+    const bool write = INT ? (lane >= 2 * R && lane < 32 - 2 * R)
+                           : (ln.out && co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
+    if (write) {
+        float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            S0 += z.hq0[k];
+            S1 += z.hq1[k];
+            S2 += z.hq2[k];
+            S3 += z.hq3[k];
+        }
+        const int V = (U + 1) % W;  // row co = e - 2R sits in slot (U + 1) mod W
+        const float g = z.rg[V] - KG, p = z.rp[V] - KP;
+        const size_t o = (size_t)co * s.w + x;
+        if (dP != nullptr) dP[o] = from_f32<TP>(fmaf(g, S0, S2));
+        if (dG != nullptr) dG[o] = from_f32<TD>(fmaf(p, S0, fmaf(2.f * g, S1, -S3)));
+    }
+}
+
+template <typename TG, typename TP, typename TD, int R>
+__device__ void lowres_bwd_strip_stats(const TG* __restrict__ G, const TP* __restrict__ P,
+                                       const float2* __restrict__ dcoef, const float4* __restrict__ stats,
+                                       TP* __restrict__ dP, TD* __restrict__ dG, const StripGeom& s) {
+    constexpr int W = 2 * R + 1;
+    const int lane = threadIdx.x & 31;
+    const int x = s.x0 + lane;
+    const StripLane<R> ln = strip_lane<R>(x, s.w);
+    const bool cols_int = s.x0 >= R && s.x0 + 32 + R <= s.w;
+    StripBwdRing<R> z;
+#pragma unroll
+    for (int k = 0; k < W; ++k) z.hda[k] = z.hdb[k] = z.hq0[k] = z.hq1[k] = z.hq2[k] = z.hq3[k] = z.rg[k] = z.rp[k] = 0.f;
+    const int e_first = s.y0 - 2 * R;
+    const int e_last = min(s.y0 + s.seg, s.h) + 2 * R;
+    float gn[W], pn[W];
+    float2 dn[W];
+    float4 sn[W];
+    auto load = [&](int base) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const int e = base + u, ce = e - R;
+            const bool ok = ln.xin && e >= 0 && e < s.h && e < e_last;
+            const size_t o = (size_t)e * s.w + x;
+            gn[u] = ok ? to_f32<TG>(G[o]) : 0.f;
+            pn[u] = ok ? to_f32<TP>(P[o]) : 0.f;
+            dn[u] = ok ? dcoef[o] : make_float2(0.f, 0.f);
+            sn[u] = (ln.xin && ce >= 0 && ce < s.h) ? stats[(size_t)ce * s.w + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    load(e_first);
+    float KG, KP;
+    {
+        const bool use = ln.out;
+        float sg = use ? gn[2 * R] : 0.f, sp = use ? pn[2 * R] : 0.f, cn = use ? 1.f : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sg += __shfl_xor_sync(0xffffffffu, sg, off);
+            sp += __shfl_xor_sync(0xffffffffu, sp, off);
+            cn += __shfl_xor_sync(0xffffffffu, cn, off);
+        }
+        KG = cn > 0.f ? sg / cn : 0.f;
+        KP = cn > 0.f ? sp / cn : 0.f;
+    }
+    for (int base = e_first; base < e_last; base += W) {
+        float gv[W], pv[W];
+        float2 dv[W];
+        float4 sv[W];
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            gv[u] = gn[u];
+            pv[u] = pn[u];
+            dv[u] = dn[u];
+            sv[u] = sn[u];
+        }
+        if (base + W < e_last) load(base + W);
+        const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W + R <= s.h &&
+                             base + W <= e_last;
+        if (row_int) {
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+                strip_k4s_row<TG, TP, TD, R, true>(z, ln, u, gv[u], pv[u], dv[u], sv[u], base + u, e_first, x, dP, dG,
+                                                   s, KG, KP);
+        } else {
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (base + u >= e_last) break;  // uniform across the warp
+                strip_k4s_row<TG, TP, TD, R, false>(z, ln, u, gv[u], pv[u], dv[u], sv[u], base + u, e_first, x, dP,
+                                                    dG, s, KG, KP);
             }
         }
     }

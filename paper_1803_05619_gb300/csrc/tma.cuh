@@ -29,6 +29,13 @@ struct TmaPair {
     int enabled;
 };
 
+// K4 strips: G, P and d Abar, d bbar (the float2 pairs as a float tensor of
+// twice the width).
+struct TmaTriple {
+    TmaPlane a, b, c;
+    int enabled;
+};
+
 // Tensor maps of K3's two high-resolution inputs (d O_h, I_h): 3-D (column,
 // row, plane), box of one strip row segment x one block of rows.
 struct K3Maps {

@@ -13,7 +13,7 @@ import synth
 from paper_1803_05619_gb300 import _lib as L
 from paper_1803_05619_gb300.layer import gf_backward, gf_forward, gf_forward_batched
 from tests.helpers import (assert_fwd, assert_grad, f64, make_case, oracle_backward, oracle_forward,
-                           to_storage)
+                           rel_l2, to_storage)
 
 pytestmark = pytest.mark.gpu
 
@@ -134,6 +134,28 @@ def test_lowres_forms_match_oracle(form, dtype, pin):
     assert L.dgf_device_status() == 0
 
 
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
+def test_k4_saved_statistics_match_recomputed(r, dtype, pin):
+    # K1 strips keep each window's statistics for the K4 strips; with K1 in
+    # tile form K4 recomputes them.  Same formulas; the compiler may contract
+    # a product and a sum into one FMA differently in the two kernels, so the
+    # results agree to rounding (dI_h takes Abar from K1, whose forms differ).
+    dt = L.DGF_F32 if dtype == F32 else L.DGF_BF16
+    st = to_storage(make_case("photo", 40 + r, 2, 2, 75, 133, 300, 532), dtype)
+    R = synth.upstream_grad(41, st["I_h"].shape).to(dtype).cuda()
+    g = {k: v.cuda() for k, v in st.items()}
+    pin(4, dt, r, 0, 0, 0, 32, 0)
+    saved = gf_backward(R, g["p_l"], g["I_l"], g["I_h"], r, 1e-3)
+    pin(1, dt, r, 0, 0, 0, 64, 32)
+    recomputed = gf_backward(R, g["p_l"], g["I_l"], g["I_h"], r, 1e-3)
+    torch.cuda.synchronize()
+    bound = 1e-6 if dtype == F32 else 2e-3
+    for name, a, b in zip(("dp_l", "dI_l"), saved[:2], recomputed[:2]):
+        assert rel_l2(f64(a), f64(b)) <= bound, name
+    assert_grad(f64(saved[2]), f64(recomputed[2]), dtype, "dI_h")
+
+
 def test_autotune_pin_rejects_bad_keys():
     with pytest.raises(L.DGFError):
         L.check(L.dgf_autotune_pin(0, L.DGF_F32, 1, 0, 0, 0, 64, 32))
@@ -153,9 +175,12 @@ def test_unbuilt_pinned_shape_falls_back_to_default(pin):
 
 @pytest.mark.parametrize("dtype,size", [(BF16, (2, 3, 64, 96, 256, 384)), (F32, (1, 2, 70, 90, 280, 360)),
                                         (BF16, (1, 1, 40, 44, 320, 352))], ids=["bf16-f4", "f32-f4", "bf16-f8"])
-def test_tma_and_plain_staging_identical(dtype, size, pin):
-    # K1 tile form (stages by TMA) and K3 (TMA slot ring vs register ring)
-    pin(1, L.DGF_F32 if dtype == F32 else L.DGF_BF16, 2, 0, 0, 0, 64, 32)
+@pytest.mark.parametrize("k1_form", ["tiles", "strips"])
+def test_tma_and_plain_staging_identical(dtype, size, k1_form, pin):
+    # every kernel that stages by TMA (K1 tiles or strips, K2, K3, K4 strips)
+    # against its plain-load form
+    if k1_form == "tiles":
+        pin(1, L.DGF_F32 if dtype == F32 else L.DGF_BF16, 2, 0, 0, 0, 64, 32)
     N, C, hl, wl, h, w = size
     st = to_storage(make_case("photo", 3, N, C, hl, wl, h, w), dtype)
     R = synth.upstream_grad(4, st["I_h"].shape).to(dtype).cuda()
