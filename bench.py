@@ -532,29 +532,42 @@ def bench_bf16_4k(args, device):
 
 
 def bench_batched_64(args, device):
-    """64 uneven BF16 images (long side 512..4096, factor 4 or 8, r in {1,2,4})
-    in one graph-replayed persistent launch per stage: forward Mpix/s."""
+    """64 uneven BF16 images (long side 512..4096, factor 4 or 8, r in {1,2,4}):
+    the forward in one graph-replayed persistent launch per stage, and
+    forward + batched backward (per-image kernel chains run concurrently)."""
     import torch
 
     import synth
-    from paper_1803_05619_gb300.layer import gf_forward_batched
+    from paper_1803_05619_gb300.layer import gf_backward_batched, gf_forward_batched
     specs = synth.mixed_sizes(seed=0, n=64)
-    images, outs = [], []
+    images, outs, grads = [], [], []
     for i, s in enumerate(specs):
         d = synth.photo_like(1000 + i, 1, 3, s.h_l, s.w_l, s.f)
         st = {k: v.to(torch.bfloat16)[0].to(device) for k, v in d.items()}
         images.append({"p_l": st["p_l"], "I_l": st["I_l"], "I_h": st["I_h"], "r": s.r, "eps": 1e-3})
         outs.append(torch.empty_like(st["I_h"]))
+        grads.append(synth.upstream_grad(2000 + i, st["I_h"].shape).to(torch.bfloat16).to(device))
     pix = sum(s.h * s.w for s in specs)
     steps = max(10, min(args.steps // 10, 200))
     ms = time_loop(lambda: gf_forward_batched(images, out=outs), steps, max(3, args.warmup // 4), 1, device)
+
+    def step():
+        gf_forward_batched(images, out=outs)
+        gf_backward_batched(images, grads)
+
+    ms2 = time_loop(step, max(5, steps // 4), max(3, args.warmup // 4), 1, device)
     byts = sum(3 * 2 * (2 * s.h * s.w + 2 * s.h_l * s.w_l) for s in specs)
+    byts_bwd = sum(3 * 2 * (3 * s.h * s.w + 4 * s.h_l * s.w_l) for s in specs)
     peak, src = peaks()
     return {"workload": "64 images, long side U[512,4096], aspect U[0.5,2], f in {4,8}, r in {1,2,4}, BF16",
             "mpix": round(pix / 1e6, 1), "fwd_mpix_s": round(pix / (ms * 1e-3) / 1e6, 1),
             "ms_fwd": round(ms, 4), "fwd_algorithmic_bytes": byts,
             "fwd_frac_of_measured_hbm": round(byts / (ms * 1e-3) / 1e9 / peak, 4),
-            "fwd_frac_of_nominal_8TBs": round(byts / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4)}
+            "fwd_frac_of_nominal_8TBs": round(byts / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4),
+            "fwd_bwd_mpix_s": round(pix / (ms2 * 1e-3) / 1e6, 1), "ms_fwd_bwd": round(ms2, 4),
+            "fwd_bwd_algorithmic_bytes": byts + byts_bwd,
+            "fwd_bwd_frac_of_measured_hbm": round((byts + byts_bwd) / (ms2 * 1e-3) / 1e9 / peak, 4),
+            "fwd_bwd_frac_of_nominal_8TBs": round((byts + byts_bwd) / (ms2 * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4)}
 
 
 def bench_guided(args, device):

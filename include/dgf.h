@@ -180,6 +180,43 @@ int dgf_device_status(void);
 void dgf_set_tma(int on);
 
 /*
+ * One image of a batched backward call: the inputs of dgf_backward for one
+ * image (C channels) and its gradient outputs, each output nullable (not
+ * needed).  No guidance transform in the batched path.
+ */
+typedef struct {
+    const void* dO_h;
+    const void* p_l;
+    const void* I_l;
+    const void* I_h;
+    void* dp_l;
+    void* dI_l;
+    void* dI_h;
+    int C, h_l, w_l, h, w, r;
+    float eps;
+} dgf_image_grad;
+
+/*
+ * Batched backward over images of different sizes, radii and factors
+ * (Algorithm 1 per image, as dgf_backward with N = 1 and no guidance
+ * transform).  Each image's chain of kernels is exactly its single call's,
+ * so the gradients equal the single calls' bit for bit; the chains run
+ * concurrently on library-owned streams forked from and joined back to
+ * `stream` (the call is ordered on `stream` like any other).
+ *   imgs:       n descriptors (host memory), 0 <= n <= DGF_MAX_BATCH;
+ *               all tensors device memory in `dt`, NCHW with N = 1.
+ *   workspace:  device memory of at least
+ *               dgf_workspace_size_batched_backward(imgs, n, dt) bytes
+ *               (0 for an invalid list), 256-byte aligned.
+ * Errors as dgf_backward, with the failing image's index in the message.
+ * Not under stream capture (the fork and join use library events).
+ * No counterpart in the paper (batching machinery).
+ */
+size_t dgf_workspace_size_batched_backward(const dgf_image_grad* imgs, int n, dgf_dtype dt);
+dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dgf_dtype dt, void* workspace,
+                                size_t ws_bytes, dgf_stream_t stream);
+
+/*
  * Tile-shape autotuner.  When enabled (here, or DGF_AUTOTUNE=1 in the
  * environment), the first call for a new key (kernel, storage type, radius
  * or factor, vector width) times each candidate tile shape on that call's

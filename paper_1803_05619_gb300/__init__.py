@@ -5,4 +5,5 @@ include/dgf.h); this package is its Python binding.
 """
 from . import _lib  # noqa: F401
 from .layer import (GuidedFilter, GuidedFilterFn, GuidedFilterTransformFn,  # noqa: F401
-                    GuidedFilterWithTransform, gf_backward, gf_forward, gf_forward_batched)
+                    GuidedFilterWithTransform, gf_backward, gf_backward_batched, gf_forward,
+                    gf_forward_batched)

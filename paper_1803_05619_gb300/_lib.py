@@ -31,6 +31,13 @@ class dgf_image(ctypes.Structure):
                 ("eps", ctypes.c_float)]
 
 
+class dgf_image_grad(ctypes.Structure):
+    _fields_ = [("dO_h", ctypes.c_void_p), ("p_l", ctypes.c_void_p), ("I_l", ctypes.c_void_p),
+                ("I_h", ctypes.c_void_p), ("dp_l", ctypes.c_void_p), ("dI_l", ctypes.c_void_p),
+                ("dI_h", ctypes.c_void_p), ("C", ctypes.c_int), ("h_l", ctypes.c_int), ("w_l", ctypes.c_int),
+                ("h", ctypes.c_int), ("w", ctypes.c_int), ("r", ctypes.c_int), ("eps", ctypes.c_float)]
+
+
 class DGFError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
@@ -48,6 +55,8 @@ _SIGS = {
                           ctypes.POINTER(dgf_guide), _P, _S, _P]),
     "dgf_workspace_size_batched": (_S, [ctypes.POINTER(dgf_image), _I, _I]),
     "dgf_forward_batched": (_I, [ctypes.POINTER(dgf_image), _I, _I, _P, _S, _P]),
+    "dgf_workspace_size_batched_backward": (_S, [ctypes.POINTER(dgf_image_grad), _I, _I]),
+    "dgf_backward_batched": (_I, [ctypes.POINTER(dgf_image_grad), _I, _I, _P, _S, _P]),
     "dgf_last_error": (ctypes.c_char_p, []),
     "dgf_profile_enable": (None, [_I]),
     "dgf_profile_reset": (None, []),
@@ -110,6 +119,14 @@ def dgf_workspace_size_batched(imgs, n, dt) -> int:
 
 def dgf_forward_batched(imgs, n, dt, ws, ws_bytes, stream) -> int:
     return lib().dgf_forward_batched(imgs, n, dt, ws, ws_bytes, stream)
+
+
+def dgf_workspace_size_batched_backward(imgs, n, dt) -> int:
+    return lib().dgf_workspace_size_batched_backward(imgs, n, dt)
+
+
+def dgf_backward_batched(imgs, n, dt, ws, ws_bytes, stream) -> int:
+    return lib().dgf_backward_batched(imgs, n, dt, ws, ws_bytes, stream)
 
 
 def dgf_last_error() -> str:

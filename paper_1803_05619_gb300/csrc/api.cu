@@ -658,7 +658,10 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
     for (int i = 0; i < n; ++i) {
         const dgf_image& im = imgs[i];
         dgf_status st = check_sizes(1, im.C, im.h_l, im.w_l, im.h, im.w, im.r, im.eps, dt);
-        if (st != DGF_OK) return fail(st, "image %d: %s", i, t_err.c_str());
+        if (st != DGF_OK) {
+            const std::string why = t_err;
+            return fail(st, "image %d: %s", i, why.c_str());
+        }
         if (ws_base != nullptr &&
             (im.p_l == nullptr || im.I_l == nullptr || im.I_h == nullptr || im.O_h == nullptr))
             return fail(DGF_ERR_INVALID, "image %d: NULL pointer", i);
@@ -767,6 +770,60 @@ dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* 
     return DGF_OK;
 }
 
+// Backward without the guidance transform for one call (N C planes): K1
+// (coefficients, and the window statistics when both low-res stages are
+// strips) -> K3 -> K4, on stream s, in the workspace slice `ws` laid out by
+// `lay`.  Shared by dgf_backward and dgf_backward_batched.
+static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, const void* p_l, const void* I_l,
+                                 const void* I_h, void* dp_l, void* dI_l, void* dI_h, int planes, int h_l, int w_l,
+                                 int h, int w, int r, float eps, Plan& p, char* ws, const Layout& lay, cudaStream_t s,
+                                 bool tuning) {
+    float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
+    float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
+    cudaError_t e;
+    // coefficients are recomputed, not saved from the forward call; with
+    // both low-res stages in strip form the K1 pass also keeps each
+    // window's statistics for K4, which then skips recomputing them
+    const bool need_k4 = dp_l != nullptr || dI_l != nullptr;
+    if (tuning && (dI_h != nullptr || need_k4)) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
+    const bool use_stats = need_k4 && p.k1.fast == 2 && p.k4.fast == 2;
+    float4* stats = use_stats ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr;
+    if (dI_h != nullptr || use_stats) {
+        e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s, stats);
+        if (e != cudaSuccess) return cuda_fail(e, "k1");
+    }
+    if (p.k3_fast) {
+        if (tuning) tune_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, s, p);
+        K3Maps maps;
+        const bool tma = make_k3_maps(maps, dO_h, I_h, dt, planes, h, w, p.vec, p.F);
+        e = L.run("k3_hires_bwd", [&] {
+            return launch_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, p.k3_lth,
+                             tma ? &maps : nullptr, status_ptr(), s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k3");
+    } else {
+        if (dI_h != nullptr) {
+            e = L.run("k2_hires_scale", [&] {
+                return launch_k2(dt, 1, coef, dO_h, dI_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "k2 scale");
+        }
+        e = L.run("k3_gather_general", [&] {
+            return launch_k3_general(dt, dO_h, I_h, dcoef, planes, h_l, w_l, h, w, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k3 general");
+    }
+    if (need_k4) {
+        if (tuning) tune_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, s, p, stats);
+        const float4* k4_stats = p.k4.fast == 2 ? stats : nullptr;
+        e = L.run("k4_lowres_bwd", [&] {
+            return run_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4, s, k4_stats);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k4");
+    }
+    return DGF_OK;
+}
+
 dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l, void* dI_l,
                         void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
                         dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes, dgf_stream_t stream) {
@@ -798,47 +855,8 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
     if (g == nullptr) {
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
         const bool tuning = tune_enabled() && !stream_capturing(s);
-        // coefficients are recomputed, not saved from the forward call; with
-        // both low-res stages in strip form the K1 pass also keeps each
-        // window's statistics for K4, which then skips recomputing them
-        const bool need_k4 = dp_l != nullptr || dI_l != nullptr;
-        if (tuning && (dI_h != nullptr || need_k4)) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
-        const bool use_stats = need_k4 && p.k1.fast == 2 && p.k4.fast == 2;
-        float4* stats = use_stats ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr;
-        if (dI_h != nullptr || use_stats) {
-            e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s, stats);
-            if (e != cudaSuccess) return cuda_fail(e, "k1");
-        }
-        if (p.k3_fast) {
-            if (tuning) tune_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, s, p);
-            K3Maps maps;
-            const bool tma = make_k3_maps(maps, dO_h, I_h, dt, planes, h, w, p.vec, p.F);
-            e = L.run("k3_hires_bwd", [&] {
-                return launch_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, p.k3_lth,
-                                 tma ? &maps : nullptr, status_ptr(), s);
-            });
-            if (e != cudaSuccess) return cuda_fail(e, "k3");
-        } else {
-            if (dI_h != nullptr) {
-                e = L.run("k2_hires_scale", [&] {
-                    return launch_k2(dt, 1, coef, dO_h, dI_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
-                });
-                if (e != cudaSuccess) return cuda_fail(e, "k2 scale");
-            }
-            e = L.run("k3_gather_general", [&] {
-                return launch_k3_general(dt, dO_h, I_h, dcoef, planes, h_l, w_l, h, w, s);
-            });
-            if (e != cudaSuccess) return cuda_fail(e, "k3 general");
-        }
-        if (need_k4) {
-            if (tuning) tune_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, s, p, stats);
-            const float4* k4_stats = p.k4.fast == 2 ? stats : nullptr;
-            e = L.run("k4_lowres_bwd", [&] {
-                return run_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4, s, k4_stats);
-            });
-            if (e != cudaSuccess) return cuda_fail(e, "k4");
-        }
-        return DGF_OK;
+        return backward_plain(L, dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws,
+                              lay, s, tuning);
     }
     // with the guidance transform
     float* G_l = reinterpret_cast<float*>(ws + lay.gl);
@@ -1011,6 +1029,104 @@ extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtyp
     return DGF_OK;
 }
 
+// ------------------------------------------------------- batched backward
+// Images are independent: each image's backward (K1 -> K3 -> K4, exactly the
+// kernels and shapes of its single call) runs as one chain on one of a few
+// library-owned streams forked from and joined back to the caller's stream,
+// so small images run concurrently and large ones fill the GPU by
+// themselves.  Results are those of the single calls.
+namespace dgf {
+constexpr int kBwdStreams = 8;
+struct BwdPool {
+    int dev = -1;
+    cudaStream_t st[kBwdStreams] = {};
+    cudaEvent_t fork = nullptr, join[kBwdStreams] = {};
+};
+std::mutex g_bwd_mu;
+std::map<int, BwdPool> g_bwd_pools;
+
+static cudaError_t bwd_pool(int dev, BwdPool*& out) {
+    BwdPool& p = g_bwd_pools[dev];
+    if (p.dev < 0) {
+        cudaError_t e;
+        for (int i = 0; i < kBwdStreams; ++i) {
+            if ((e = cudaStreamCreateWithFlags(&p.st[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        p.dev = dev;
+    }
+    out = &p;
+    return cudaSuccess;
+}
+
+static dgf_status check_grad_images(const dgf_image_grad* imgs, int n, dgf_dtype dt, size_t* ws_total) {
+    if ((int)dt < 0 || (int)dt > 2) return fail(DGF_ERR_INVALID, "dtype %d", (int)dt);
+    if (n < 0 || n > DGF_MAX_BATCH) return fail(DGF_ERR_INVALID, "n = %d outside [0, %d]", n, DGF_MAX_BATCH);
+    if (n > 0 && imgs == nullptr) return fail(DGF_ERR_INVALID, "NULL image array");
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const dgf_image_grad& im = imgs[i];
+        dgf_status st = check_sizes(1, im.C, im.h_l, im.w_l, im.h, im.w, im.r, im.eps, dt);
+        if (st != DGF_OK) {
+            const std::string why = t_err;
+            return fail(st, "image %d: %s", i, why.c_str());
+        }
+        if (im.dO_h == nullptr || im.p_l == nullptr || im.I_l == nullptr || im.I_h == nullptr)
+            return fail(DGF_ERR_INVALID, "image %d: NULL input pointer", i);
+        off += align256(layout(1, im.C, im.h_l, im.w_l, false).total);
+    }
+    *ws_total = off;
+    return DGF_OK;
+}
+}  // namespace dgf
+
+extern "C" size_t dgf_workspace_size_batched_backward(const dgf_image_grad* imgs, int n, dgf_dtype dt) {
+    size_t total = 0;
+    if (check_grad_images(imgs, n, dt, &total) != DGF_OK) return 0;
+    return total;
+}
+
+extern "C" dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dgf_dtype dt, void* workspace,
+                                           size_t ws_bytes, dgf_stream_t stream) {
+    size_t total = 0;
+    dgf_status st = check_grad_images(imgs, n, dt, &total);
+    if (st != DGF_OK) return st;
+    if (n == 0) return DGF_OK;
+    if ((st = check_ws(workspace, ws_bytes, total)) != DGF_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_bwd_mu);
+    BwdPool* pool = nullptr;
+    cudaError_t e = bwd_pool(dev, pool);
+    if (e != cudaSuccess) return cuda_fail(e, "backward stream pool");
+    const int ns = std::min(n, kBwdStreams);
+    if ((e = cudaEventRecord(pool->fork, s)) != cudaSuccess) return cuda_fail(e, "fork");
+    for (int k = 0; k < ns; ++k)
+        if ((e = cudaStreamWaitEvent(pool->st[k], pool->fork, 0)) != cudaSuccess) return cuda_fail(e, "fork wait");
+    char* ws = static_cast<char*>(workspace);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const dgf_image_grad& im = imgs[i];
+        cudaStream_t si = pool->st[i % ns];
+        const Layout lay = layout(1, im.C, im.h_l, im.w_l, false);
+        Plan p = make_plan(dt, im.h_l, im.w_l, im.h, im.w, im.r, false, {im.dO_h, im.I_h, im.dI_h});
+        if (im.dp_l != nullptr || im.dI_l != nullptr || im.dI_h != nullptr) {
+            Launcher L(si);
+            st = backward_plain(L, dt, im.dO_h, im.p_l, im.I_l, im.I_h, im.dp_l, im.dI_l, im.dI_h, im.C, im.h_l,
+                                im.w_l, im.h, im.w, im.r, im.eps, p, ws + off, lay, si, false);
+            if (st != DGF_OK) return st;
+        }
+        off += align256(lay.total);
+    }
+    for (int k = 0; k < ns; ++k) {
+        if ((e = cudaEventRecord(pool->join[k], pool->st[k])) != cudaSuccess) return cuda_fail(e, "join");
+        if ((e = cudaStreamWaitEvent(s, pool->join[k], 0)) != cudaSuccess) return cuda_fail(e, "join wait");
+    }
+    return DGF_OK;
+}
+
 extern "C" const char* dgf_last_error(void) { return t_err.c_str(); }
 
 extern "C" void dgf_profile_enable(int on) {
@@ -1067,6 +1183,17 @@ extern "C" dgf_status dgf_autotune_pin(int kind, dgf_dtype dt, int r, int F, int
 extern "C" void dgf_autotune_reset(void) { tune_clear(); }
 
 extern "C" void dgf_shutdown(void) {
+    {
+        std::lock_guard<std::mutex> lk(g_bwd_mu);
+        for (auto& kv : g_bwd_pools) {
+            for (int k = 0; k < kBwdStreams; ++k) {
+                if (kv.second.st[k]) cudaStreamDestroy(kv.second.st[k]);
+                if (kv.second.join[k]) cudaEventDestroy(kv.second.join[k]);
+            }
+            if (kv.second.fork) cudaEventDestroy(kv.second.fork);
+        }
+        g_bwd_pools.clear();
+    }
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (auto& kv : g_batch) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);

@@ -149,6 +149,40 @@ def gf_forward_batched(images, out=None):
     return outs
 
 
+def gf_backward_batched(images, grads):
+    """Batched backward (Algorithm 1 per image, chains run concurrently).
+
+    ``images``: list of dicts with p_l, I_l, I_h (C x h x w tensors, one
+    dtype), r, eps; ``grads``: the matching list of d O_h.  Returns a list
+    of (dp_l, dI_l, dI_h) per image.
+    """
+    n = len(images)
+    if n == 0:
+        return []
+    dt = dtype_code(images[0]["I_h"])
+    dev = images[0]["I_h"].device
+    arr = (L.dgf_image_grad * n)()
+    outs = []
+    for i, (im, R) in enumerate(zip(images, grads)):
+        _check(im["p_l"], im["I_l"], im["I_h"])
+        if R.dtype != im["I_h"].dtype or R.shape != im["I_h"].shape or not R.is_contiguous():
+            raise ValueError("d O_h must match I_h in shape, dtype and layout")
+        dp, dIl, dIh = torch.empty_like(im["p_l"]), torch.empty_like(im["I_l"]), torch.empty_like(im["I_h"])
+        outs.append((dp, dIl, dIh))
+        C, h, w = im["I_h"].shape
+        h_l, w_l = im["p_l"].shape[1:]
+        arr[i] = L.dgf_image_grad(R.data_ptr(), im["p_l"].data_ptr(), im["I_l"].data_ptr(), im["I_h"].data_ptr(),
+                                  dp.data_ptr(), dIl.data_ptr(), dIh.data_ptr(), C, h_l, w_l, h, w, int(im["r"]),
+                                  float(im["eps"]))
+    nb = L.dgf_workspace_size_batched_backward(arr, n, dt)
+    if nb == 0:
+        raise L.DGFError(1, L.dgf_last_error())
+    ws = workspace(nb, dev)
+    with torch.cuda.device(dev):
+        L.check(L.dgf_backward_batched(arr, n, dt, _ptr(ws), ws.numel(), _stream(dev)))
+    return outs
+
+
 class GuidedFilterFn(torch.autograd.Function):
     """O_h = GF(p_l, I_l, I_h); backward = Algorithm 1 in libdgf.so."""
 

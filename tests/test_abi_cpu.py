@@ -101,3 +101,19 @@ def test_batched_validation(lib):
     assert L.dgf_workspace_size_batched(arr, 1, L.DGF_BF16) > 0
     assert L.dgf_forward_batched(arr, 1, L.DGF_BF16, None, 0, None) == 5
     assert L.dgf_forward_batched(arr, 200, L.DGF_BF16, None, 0, None) == 1
+
+
+def test_batched_backward_validation(lib):
+    arr = (L.dgf_image_grad * 3)()
+    arr[0] = L.dgf_image_grad(16, 32, 48, 64, 80, 96, 112, 3, 8, 8, 32, 32, 1, 1e-3)
+    arr[1] = L.dgf_image_grad(16, 32, 48, 64, None, None, 112, 1, 12, 10, 48, 40, 2, 1e-3)
+    arr[2] = L.dgf_image_grad(16, None, 48, 64, 80, 96, 112, 3, 8, 8, 32, 32, 1, 1e-3)  # NULL p_l
+    one = L.dgf_workspace_size_batched_backward(arr, 1, L.DGF_F32)
+    two = L.dgf_workspace_size_batched_backward(arr, 2, L.DGF_F32)
+    assert one > 0 and two > one and one % 256 == 0
+    assert L.dgf_workspace_size_batched_backward(arr, 3, L.DGF_F32) == 0
+    assert "image 2" in L.dgf_last_error()
+    assert L.dgf_workspace_size_batched_backward(arr, 200, L.DGF_F32) == 0
+    assert L.dgf_backward_batched(arr, 3, L.DGF_F32, None, 0, None) == 1
+    assert L.dgf_backward_batched(arr, 2, L.DGF_F32, None, 0, None) == 5  # workspace too small
+    assert L.dgf_backward_batched(arr, 0, L.DGF_F32, None, 0, None) == 0

@@ -5,7 +5,8 @@ shapes chosen by the autotuner as in the benchmark.
 * plain FP32 forward + backward, 4 x 3 x 512^2 -> 2048^2, r = 1, eps = 1e-4
 * BF16 4K batch, 2 x 3 x 540x960 -> 2160x3840, r = 2, eps = 1e-3
 * 64 uneven BF16 images through the batched graph path (long side 512..4096,
-  factor 4 or 8, r in {1, 2, 4}); every image bitwise equal to its single call
+  factor 4 or 8, r in {1, 2, 4}) and the batched backward; every image bitwise
+  equal to its single call
 * the training step with the guidance transform, 8 x 3 x 256^2 -> 2048^2,
   r = 8, eps = 1e-4, BF16, weight gradients included
 """
@@ -16,7 +17,7 @@ import torch
 import oracle as O
 import synth
 from paper_1803_05619_gb300 import _lib as L
-from paper_1803_05619_gb300.layer import gf_backward, gf_forward, gf_forward_batched
+from paper_1803_05619_gb300.layer import gf_backward, gf_backward_batched, gf_forward, gf_forward_batched
 from tests.helpers import assert_fwd, assert_grad, f64, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -102,6 +103,23 @@ def test_batched_64_uneven_fullsize():
     for i in (order[0], order[1], order[len(order) // 2]):
         ref = O.forward(f64(host[i]["p_l"]), f64(host[i]["I_l"]), f64(host[i]["I_h"]), specs[i].r, eps)
         assert_fwd(f64(outs[i])[None], ref, torch.bfloat16, eps, what=f"image {i}")
+    # batched backward: every image bitwise equal to its single call (single
+    # calls first, so any shape the autotuner picks is the batch's too); the
+    # smallest image against the oracle
+    grads = [synth.upstream_grad(2000 + i, im["I_h"].shape).to(torch.bfloat16).cuda() for i, im in enumerate(images)]
+    singles = [gf_backward(R[None], im["p_l"][None], im["I_l"][None], im["I_h"][None], im["r"], im["eps"])
+               for im, R in zip(images, grads)]
+    gouts = gf_backward_batched(images, grads)
+    torch.cuda.synchronize()
+    for go, single in zip(gouts, singles):
+        for a, b in zip(go, single[:3]):
+            assert torch.equal(a, b[0])
+    i = order[0]
+    R = grads[i].cpu()[None]
+    rp, rIl, rIh = O.backward(f64(R), f64(host[i]["p_l"]), f64(host[i]["I_l"]), f64(host[i]["I_h"]), specs[i].r, eps)
+    assert_grad(f64(gouts[i][0])[None], rp, torch.bfloat16, "dp_l")
+    assert_grad(f64(gouts[i][1])[None], rIl, torch.bfloat16, "dI_l")
+    assert_grad(f64(gouts[i][2])[None], rIh, torch.bfloat16, "dI_h")
 
 
 def test_guided_training_step_fullsize():

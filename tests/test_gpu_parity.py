@@ -11,7 +11,7 @@ import torch
 import oracle as O
 import synth
 from paper_1803_05619_gb300 import _lib as L
-from paper_1803_05619_gb300.layer import gf_backward, gf_forward, gf_forward_batched
+from paper_1803_05619_gb300.layer import gf_backward, gf_backward_batched, gf_forward, gf_forward_batched
 from tests.helpers import (assert_fwd, assert_grad, f64, make_case, oracle_backward, oracle_forward,
                            rel_l2, to_storage)
 
@@ -255,6 +255,33 @@ def test_batched_matches_single_bitwise(dtype, k1_form, pin):
     for im, o in zip(images, outs):
         ref = oracle_forward(im["_st"], im["r"], im["eps"])
         assert_fwd(f64(o)[None], ref, dtype, im["eps"])
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
+def test_batched_backward_matches_single_bitwise(dtype):
+    specs = synth.mixed_sizes(seed=5, n=7, long_lo=96, long_hi=520)
+    images, grads, host = [], [], []
+    for i, s in enumerate(specs):
+        d = to_storage(synth.photo_like(70 + i, 1, 3, s.h_l, s.w_l, s.f), dtype)
+        R = synth.upstream_grad(90 + i, d["I_h"].shape).to(dtype)
+        host.append((d, R))
+        images.append({"p_l": d["p_l"][0].cuda(), "I_l": d["I_l"][0].cuda(), "I_h": d["I_h"][0].cuda(),
+                       "r": s.r, "eps": 1e-3})
+        grads.append(R[0].cuda())
+    outs = gf_backward_batched(images, grads)
+    torch.cuda.synchronize()
+    for im, R, o in zip(images, grads, outs):
+        single = gf_backward(R[None], im["p_l"][None], im["I_l"][None], im["I_h"][None], im["r"], im["eps"])
+        for a, b in zip(o, single[:3]):
+            assert torch.equal(a, b[0])
+    # and against the oracle on the two smallest images
+    order = sorted(range(len(specs)), key=lambda i: specs[i].h * specs[i].w)
+    for i in order[:2]:
+        d, R = host[i]
+        rp, rIl, rIh = oracle_backward(R, d, specs[i].r, 1e-3)
+        assert_grad(f64(outs[i][0])[None], rp, dtype, "dp_l")
+        assert_grad(f64(outs[i][1])[None], rIl, dtype, "dI_l")
+        assert_grad(f64(outs[i][2])[None], rIh, dtype, "dI_h")
 
 
 def test_invalid_arguments_report_status():
