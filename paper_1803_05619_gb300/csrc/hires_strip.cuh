@@ -48,16 +48,21 @@ __host__ __device__ constexpr float k3s_lam(int k) {
                            : (float)(2 * (k % F) + 1 - F) / (float)(2 * F);
 }
 
-// Row ii of Abar interpolated along x at the lane's VEC pixels.  Columns
-// clamp to the image as in the forward upsampler.
+// Abar of row ii at the lane's own K cells (columns clamped to the image).
 template <int VEC, int F>
-__device__ __forceinline__ void k3s_hrow(const float2* __restrict__ coef, int ii, int J, int w_l,
-                                         float (&H)[VEC]) {
+__device__ __forceinline__ void k3s_own(const float2* __restrict__ coef, int ii, int J, int w_l,
+                                        float (&own)[VEC / F]) {
     constexpr int K = VEC / F;
     const float* row = reinterpret_cast<const float*>(coef + (size_t)ii * w_l);
-    float own[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) own[c] = row[2 * clampi(J + c, 0, w_l - 1)];
+}
+
+// A row of Abar interpolated along x at the lane's VEC pixels, from the
+// lane's own cells and its neighbours' (columns clamp as in the forward).
+template <int VEC, int F>
+__device__ __forceinline__ void k3s_hrow_from(const float (&own)[VEC / F], int J, int w_l, float (&H)[VEC]) {
+    constexpr int K = VEC / F;
     const float up = __shfl_up_sync(0xffffffffu, own[K - 1], 1);
     const float dn = __shfl_down_sync(0xffffffffu, own[0], 1);
     float tp[K + 2];
@@ -93,6 +98,7 @@ struct K3State {
     static constexpr int K = VEC / F;
     float Hlo[VEC], Hhi[VEC];
     float alu[K], alv[K], ahu[K], ahv[K];
+    float own_next[K];  // Abar cells of the next block's second tap row, loaded a block ahead
 };
 
 struct K3Lane {
@@ -121,7 +127,8 @@ __device__ __forceinline__ void k3s_block_start(K3State<VEC, F>& st, const float
                                                 const K3Lane& L, int h_l, int w_l) {
 #pragma unroll
     for (int k = 0; k < VEC; ++k) st.Hlo[k] = st.Hhi[k];
-    k3s_hrow<VEC, F>(coef, min(i + 1, h_l - 1), L.J, w_l, st.Hhi);
+    k3s_hrow_from<VEC, F>(st.own_next, L.J, w_l, st.Hhi);  // row min(i + 1, h_l - 1)
+    k3s_own<VEC, F>(coef, min(i + 2, h_l - 1), L.J, w_l, st.own_next);
 }
 
 // High-res row y = F i + F/2 + t of block i (t compile-time after unrolling).
@@ -240,7 +247,9 @@ template <int VEC, int F>
 __device__ __forceinline__ void k3s_init(K3State<VEC, F>& st, const float2* __restrict__ coef, int ib0,
                                          const K3Lane& L, int h_l, int w_l) {
     constexpr int K = VEC / F;
-    k3s_hrow<VEC, F>(coef, clampi(ib0, 0, h_l - 1), L.J, w_l, st.Hhi);
+    k3s_own<VEC, F>(coef, clampi(ib0, 0, h_l - 1), L.J, w_l, st.own_next);
+    k3s_hrow_from<VEC, F>(st.own_next, L.J, w_l, st.Hhi);
+    k3s_own<VEC, F>(coef, min(max(ib0, -1) + 1, h_l - 1), L.J, w_l, st.own_next);
 #pragma unroll
     for (int c = 0; c < K; ++c) st.alu[c] = st.alv[c] = st.ahu[c] = st.ahv[c] = 0.f;
 }
@@ -382,18 +391,23 @@ __device__ void k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps
 // copies.
 template <int VEC, int F>
 struct K2Rows {
-    float A1[VEC], B1[VEC];  // row i + 1 (the block's second tap row) along x
-    float DA[VEC], DB[VEC];  // row i + 1 minus row i
+    float A1[VEC], B1[VEC];       // row i + 1 (the block's second tap row) along x
+    float DA[VEC], DB[VEC];       // row i + 1 minus row i
+    float2 next[VEC / F + 2];     // tap columns of the next block's second row, loaded a block ahead
 };
 
+// The lane's K + 2 tap columns of coefficient row ii (clamped to the image).
 template <int VEC, int F>
-__device__ __forceinline__ void k2s_hrow(const float2* __restrict__ coef, int ii, int J, int w_l, float (&HA)[VEC],
-                                         float (&HB)[VEC]) {
+__device__ __forceinline__ void k2s_taps(const float2* __restrict__ coef, int ii, int J, int w_l,
+                                         float2 (&tp)[VEC / F + 2]) {
     constexpr int K = VEC / F;
     const float2* row = coef + (size_t)ii * w_l;
-    float2 tp[K + 2];
 #pragma unroll
     for (int c = 0; c < K + 2; ++c) tp[c] = row[clampi(J - 1 + c, 0, w_l - 1)];
+}
+
+template <int VEC, int F>
+__device__ __forceinline__ void k2s_hrow_from(const float2 (&tp)[VEC / F + 2], float (&HA)[VEC], float (&HB)[VEC]) {
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
         HA[k] = lerp(tp[k3s_lo<F>(k)].x, tp[k3s_lo<F>(k) + 1].x, k3s_lam<F>(k));
@@ -405,7 +419,9 @@ __device__ __forceinline__ void k2s_hrow(const float2* __restrict__ coef, int ii
 template <int VEC, int F>
 __device__ __forceinline__ void k2s_init(K2Rows<VEC, F>& q, const float2* __restrict__ coef, int b0, int J, int h_l,
                                          int w_l) {
-    k2s_hrow<VEC, F>(coef, clampi(b0, 0, h_l - 1), J, w_l, q.A1, q.B1);
+    k2s_taps<VEC, F>(coef, clampi(b0, 0, h_l - 1), J, w_l, q.next);
+    k2s_hrow_from<VEC, F>(q.next, q.A1, q.B1);
+    k2s_taps<VEC, F>(coef, min(max(b0, -1) + 1, h_l - 1), J, w_l, q.next);
 }
 
 // Block i begins: taps rows clamp(i) (the previous second row) and clamp(i + 1).
@@ -413,7 +429,8 @@ template <int VEC, int F>
 __device__ __forceinline__ void k2s_block(K2Rows<VEC, F>& q, const float2* __restrict__ coef, int i, int J, int h_l,
                                           int w_l) {
     float a[VEC], b[VEC];
-    k2s_hrow<VEC, F>(coef, min(i + 1, h_l - 1), J, w_l, a, b);
+    k2s_hrow_from<VEC, F>(q.next, a, b);  // row min(i + 1, h_l - 1)
+    k2s_taps<VEC, F>(coef, min(i + 2, h_l - 1), J, w_l, q.next);
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
         q.DA[k] = a[k] - q.A1[k];
