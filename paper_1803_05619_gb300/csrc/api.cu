@@ -372,9 +372,10 @@ static bool make_k3_maps(K3Maps& m, const void* R, const void* G, dgf_dtype dt, 
 static bool k1_box(const LowCfg& c, int r, int esz, int& bx, int& by, int& off) {
     const int U = 16 / esz;
     if (c.fast == 2) {
-        // warp strips: 32 columns plus one 16-byte unit (the strip's first
-        // column is rounded down to it), whole blocks of ring periods
-        bx = 32 + U;
+        // warp strips (two columns per lane): 64 columns plus one 16-byte
+        // unit (the strip's first column is rounded down to it), whole
+        // blocks of ring periods
+        bx = 64 + U;
         by = r == 1 ? 6 : 10;
         off = 0;
         return true;

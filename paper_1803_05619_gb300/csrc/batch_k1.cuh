@@ -8,6 +8,7 @@
 #include "lowres_fast.cuh"
 #include "lowres_generic.cuh"
 #include "lowres_strip.cuh"
+#include "lowres_strip2.cuh"
 
 namespace dgf {
 
@@ -22,19 +23,19 @@ __global__ void __launch_bounds__(kThreads) k1_coef_batched(const __grid_constan
         const BatchImage& im = bp.img[i];
         const int local = tile - bp.k1_start[i];
         if constexpr (MODE == 2) {
-            const int nstrip = (im.w_l + (32 - 4 * R) - 1) / (32 - 4 * R);
+            const int nstrip = (im.w_l + strip2_out_cols(R) - 1) / strip2_out_cols(R);
             const int nseg = (im.h_l + im.k1_tx - 1) / im.k1_tx;
             const int plane = local / im.k1_nx;
-            const int item = (local - plane * im.k1_nx) * kStripWarps + (threadIdx.x >> 5);
+            const int item = (local - plane * im.k1_nx) * kWarps + (threadIdx.x >> 5);
             if (item < nstrip * nseg) {  // warp-uniform; no barrier follows
                 StripGeom sg;
                 sg.h = im.h_l;
                 sg.w = im.w_l;
-                sg.x0 = (item % nstrip) * (32 - 4 * R) - 2 * R;
+                sg.x0 = (item % nstrip) * strip2_out_cols(R) - 2 * R;
                 sg.y0 = (item / nstrip) * im.k1_tx;
                 sg.seg = im.k1_tx;
                 const size_t hw = (size_t)im.h_l * im.w_l;
-                coef_strip<T, T, R>(static_cast<const T*>(im.I_l) + plane * hw,
+                coef_strip2<T, T, R>(static_cast<const T*>(im.I_l) + plane * hw,
                                     static_cast<const T*>(im.p_l) + plane * hw, im.coef + plane * hw, sg, im.eps);
             }
             continue;

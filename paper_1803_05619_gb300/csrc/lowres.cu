@@ -5,6 +5,7 @@
 #include "lowres_fast.cuh"
 #include "lowres_generic.cuh"
 #include "lowres_strip.cuh"
+#include "lowres_strip2.cuh"
 
 namespace dgf {
 
@@ -260,8 +261,8 @@ size_t k4_cfg_smem(const LowCfg& c, int r) {
 void low_grid(const LowCfg& c, int r, int h, int w, int& gx, int& gy) {
     if (c.fast == 2) {
         // work items of 8 warp strips (one CTA) per plane, in one row
-        const int nstrip = (w + (32 - 4 * r) - 1) / (32 - 4 * r), nseg = (h + c.a - 1) / c.a;
-        gx = (nstrip * nseg + kStripWarps - 1) / kStripWarps;
+        const int nstrip = (w + strip2_out_cols(r) - 1) / strip2_out_cols(r), nseg = (h + c.a - 1) / c.a;
+        gx = (nstrip * nseg + kWarps - 1) / kWarps;  // batched work items: one strip segment per warp of a CTA
         gy = 1;
         return;
     }

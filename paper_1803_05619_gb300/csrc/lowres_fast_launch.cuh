@@ -7,6 +7,7 @@
 #include "kernels.h"
 #include "lowres_fast.cuh"
 #include "lowres_strip.cuh"
+#include "lowres_strip2.cuh"
 
 namespace dgf {
 
@@ -41,8 +42,8 @@ __global__ void __launch_bounds__(kLowThreads) k4_lowres_bwd_fast(const TG* __re
 }
 
 
-// Warp-strip K1 (R = 1, 2): warp w of the grid owns strip (w % nstrip) of
-// row segment (w / nstrip) % nseg of plane w / (nstrip nseg).
+// Warp-strip K1 (R = 1, 2; two columns per lane): warp w of the grid owns
+// strip (w % nstrip) of row segment (w / nstrip) % nseg of plane w / (nstrip nseg).
 template <typename TG, typename TP, int R>
 __global__ void __launch_bounds__(kStripWarps * 32) k1_coef_strip(const TG* __restrict__ G, const TP* __restrict__ P,
                                                                    float2* __restrict__ coef, int h, int w, float eps,
@@ -55,12 +56,12 @@ __global__ void __launch_bounds__(kStripWarps * 32) k1_coef_strip(const TG* __re
     StripGeom s;
     s.h = h;
     s.w = w;
-    s.x0 = strip * (32 - 4 * R) - 2 * R;
+    s.x0 = strip * strip2_out_cols(R) - 2 * R;
     s.y0 = sg * seg;
     s.seg = seg;
     const size_t hw = (size_t)h * w;
-    coef_strip<TG, TP, R>(G + plane * hw, P + plane * hw, coef + plane * hw, s, eps,
-                          stats ? stats + plane * hw : nullptr);
+    coef_strip2<TG, TP, R>(G + plane * hw, P + plane * hw, coef + plane * hw, s, eps,
+                           stats ? stats + plane * hw : nullptr);
 }
 
 // Warp-strip K1 with TMA staging: same decomposition; each warp's rows
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(kStripWarps * 32)
                       int h, int w, float eps, int seg, int nstrip, int nseg, int planes, uint32_t* status) {
     extern __shared__ __align__(1024) unsigned char k1ring[];
     constexpr int NS = StripTmaCfg<R>::NS, RB = StripTmaCfg<R>::RB;
-    constexpr int SLOT = strip_box_bytes(R, (int)sizeof(TG), RB) + strip_box_bytes(R, (int)sizeof(TP), RB);
+    constexpr int SLOT = strip2_box_bytes((int)sizeof(TG), RB) + strip2_box_bytes((int)sizeof(TP), RB);
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * kStripWarps + warp;
     if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
@@ -80,14 +81,14 @@ __global__ void __launch_bounds__(kStripWarps * 32)
     StripGeom s;
     s.h = h;
     s.w = w;
-    s.x0 = strip * (32 - 4 * R) - 2 * R;
+    s.x0 = strip * strip2_out_cols(R) - 2 * R;
     s.y0 = sg * seg;
     s.seg = seg;
     unsigned char* ring = k1ring + (size_t)warp * NS * SLOT;
     uint64_t* bars = reinterpret_cast<uint64_t*>(k1ring + (size_t)kStripWarps * NS * SLOT) + warp * NS;
     const size_t hw = (size_t)h * w;
-    coef_strip_tma<TG, TP, R>(&maps, plane, coef + plane * hw, stats ? stats + plane * hw : nullptr, s, eps, ring,
-                              bars, status);
+    coef_strip2_tma<TG, TP, R>(&maps, plane, coef + plane * hw, stats ? stats + plane * hw : nullptr, s, eps, ring,
+                               bars, status);
 }
 
 // Warp-strip K4 (R = 1, 2), same work decomposition as k1_coef_strip, in
@@ -171,11 +172,11 @@ static cudaError_t k1f_go(const void* G, const void* P, float2* coef, int planes
                           const LowCfg& c, const TmaPair& tma, size_t smem, uint32_t* status, float4* stats, cudaStream_t s) {
     if constexpr (R <= 2) {
         if (c.fast == 2) {
-            const int seg = c.a, nstrip = (w + (32 - 4 * R) - 1) / (32 - 4 * R), nseg = (h + seg - 1) / seg;
+            const int seg = c.a, nstrip = (w + strip2_out_cols(R) - 1) / strip2_out_cols(R), nseg = (h + seg - 1) / seg;
             const long long warps = (long long)nstrip * nseg * planes;
             const int ctas = (int)((warps + kStripWarps - 1) / kStripWarps);
             if (tma.enabled) {
-                constexpr int smem_t = k1_strip_tma_smem<TG, TP, R>();
+                constexpr int smem_t = k1_strip2_tma_smem<TG, TP, R>();
                 auto kern = k1_coef_strip_tma<TG, TP, R>;
                 cudaError_t e = fast_prep(kern, smem_t);
                 if (e != cudaSuccess) return e;

@@ -1,4 +1,6 @@
-// Low-resolution stage as warp-strip column walks (radius R = 1 or 2).
+// Low-resolution stage as warp-strip column walks (radius R = 1 or 2): the
+// shared pieces and the K4 strips (one column per lane); K1 strips hold two
+// columns per lane (lowres_strip2.cuh).
 //
 // One warp owns a strip of 32 consecutive low-res columns and walks down a
 // segment of rows.  Each lane holds one column: horizontal window terms come
@@ -25,7 +27,7 @@
 
 namespace dgf {
 
-constexpr int kStripWarps = 8;    // warps per CTA of the K1 strips (independent strips)
+constexpr int kStripWarps = 4;    // warps per CTA of the single-call K1 strips (independent strips)
 constexpr int kK4StripWarps = 4;  // warps per CTA of the K4 strips
 
 __device__ __forceinline__ float shfl_up(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
@@ -152,105 +154,6 @@ __device__ __forceinline__ StripLane<R> strip_lane(int x, int w) {
     return ln;
 }
 
-// K1 for input row e entering ring slot U.  INT: interior ring period (all
-// rows and columns of every window touched are inside the image and complete).
-// With `stats` non-null the window statistics the backward pass needs
-// (mu, nu, 1/(var + eps), A) are written too, for the segment's rows.
-template <typename TG, typename TP, int R, bool INT>
-__device__ __forceinline__ void strip_k1_row(StripRing<R>& q, const StripLane<R>& ln, int U, float gvu, float pvu,
-                                             int e, int e_first, int x, float2* __restrict__ coef,
-                                             float4* __restrict__ stats, const StripGeom& s, float eps) {
-    constexpr int W = 2 * R + 1;
-    constexpr float kInvW2 = 1.f / (float)(W * W);
-    const int lane = threadIdx.x & 31;
-    strip_row_stats<R, INT>(q, ln, U, gvu, pvu, e >= 0 && e < s.h);
-    // ---- Eq. 1's A, b of window row ce = e - R (rows ce - R .. ce + R = level 1)
-    const int ce = e - R;
-    float A = 0.f, b = 0.f;
-    if (INT || (ln.xin && ce >= 0 && ce < s.h && e - e_first >= 2 * R)) {
-        const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
-        float mu, nu, var, cov;
-        strip_window<R, INT>(q, ln, ny, mu, nu, var, cov);
-        const float ive = rcp_approx(var + eps);
-        A = cov * ive;
-        b = fmaf(-A, mu, nu);
-        if (stats != nullptr && ln.out && ce >= s.y0 && ce < s.y0 + s.seg)
-            stats[(size_t)ce * s.w + x] = make_float4(mu, nu, ive, A);
-    }
-    // ---- level 2: horizontal box sums of A, b, then the vertical sum over the ring
-    q.ha[U] = hsum<R>(A);
-    q.hb[U] = hsum<R>(b);
-    const int co = ce - R;  // output row; level 2 holds window rows co - R .. co + R
-    const bool write = INT ? (lane >= 2 * R && lane < 32 - 2 * R)
-                           : (ln.out && co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
-    if (write) {
-        float sa = 0.f, sb = 0.f;
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            sa += q.ha[k];
-            sb += q.hb[k];
-        }
-        const float inn = INT ? kInvW2 : inv_count(ln.nx * (min(co + R, s.h - 1) - max(co - R, 0) + 1));
-        coef[(size_t)co * s.w + x] = make_float2(sa * inn, sb * inn);
-    }
-}
-
-// ------------------------------------------------------------------- K1
-// Eq. 1's least-squares A, b per clipped window, then their box mean, for
-// one strip segment.  Writes Abar, bbar for lanes [2R, 32 - 2R).
-template <typename TG, typename TP, int R>
-__device__ void coef_strip(const TG* __restrict__ G, const TP* __restrict__ P, float2* __restrict__ coef,
-                           const StripGeom& s, float eps, float4* __restrict__ stats = nullptr) {
-    constexpr int W = 2 * R + 1;
-    const int x = s.x0 + (int)(threadIdx.x & 31);
-    const StripLane<R> ln = strip_lane<R>(x, s.w);
-    const bool cols_int = s.x0 >= 0 && s.x0 + 32 <= s.w;  // warp-uniform
-    StripRing<R> q;
-#pragma unroll
-    for (int k = 0; k < W; ++k) q.mg[k] = q.mp[k] = q.sgg[k] = q.sgp[k] = q.vr[k] = q.ha[k] = q.hb[k] = 0.f;
-    // input row e enters level 1 in slot (e - e_first) % W; the window of row
-    // e - R is then complete and enters level 2 in the same slot; the output
-    // row e - 2R is complete after that.
-    const int e_first = s.y0 - 2 * R;
-    const int e_last = min(s.y0 + s.seg, s.h) + 2 * R;  // exclusive
-    float gn[W], pn[W];
-    auto load = [&](int base) {
-#pragma unroll
-        for (int u = 0; u < W; ++u) {
-            const int e = base + u;
-            const bool ok = ln.xin && e >= 0 && e < s.h && e < e_last;
-            gn[u] = ok ? to_f32<TG>(G[(size_t)e * s.w + x]) : 0.f;
-            pn[u] = ok ? to_f32<TP>(P[(size_t)e * s.w + x]) : 0.f;
-        }
-    };
-    load(e_first);
-    for (int base = e_first; base < e_last; base += W) {
-        float gv[W], pv[W];
-#pragma unroll
-        for (int u = 0; u < W; ++u) {
-            gv[u] = gn[u];
-            pv[u] = pn[u];
-        }
-        if (base + W < e_last) load(base + W);  // next period in flight while this one computes
-        const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W <= s.h &&
-                             base + W <= e_last;
-        if (row_int) {
-#pragma unroll
-            for (int u = 0; u < W; ++u)
-                strip_k1_row<TG, TP, R, true>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, stats, s,
-                                                  eps);
-        } else {
-#pragma unroll
-            for (int u = 0; u < W; ++u) {
-                if (base + u >= e_last) break;  // uniform across the warp
-                strip_k1_row<TG, TP, R, false>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, stats, s,
-                                                   eps);
-            }
-        }
-    }
-}
-
-
 // ------------------------------------------------- TMA staging of the strips
 // A warp's rows arrive in blocks of RB rows (whole ring periods) through a
 // ring of NS shared-memory slots, one mbarrier per slot.  Each input is one
@@ -275,103 +178,6 @@ __host__ __device__ constexpr int strip_box_bytes(int R, int esize, int rows) {
 }
 
 __device__ __forceinline__ int floor_to(int x, int u) { return x >= 0 ? x / u * u : -((-x + u - 1) / u) * u; }
-
-template <typename TG, typename TP, int R>
-__device__ void coef_strip_tma(const TmaPair* maps, int plane, float2* __restrict__ coef, float4* __restrict__ stats,
-                               const StripGeom& s, float eps, unsigned char* ring, uint64_t* bars,
-                               uint32_t* status) {
-    constexpr int W = 2 * R + 1, RB = StripTmaCfg<R>::RB, NS = StripTmaCfg<R>::NS, NP = RB / W;
-    constexpr int UG = 16 / (int)sizeof(TG), UP = 16 / (int)sizeof(TP);
-    constexpr int BXG = 32 + UG, BXP = 32 + UP;
-    constexpr int BG = strip_box_bytes(R, (int)sizeof(TG), RB), BP = strip_box_bytes(R, (int)sizeof(TP), RB);
-    constexpr int SLOT = BG + BP;
-    constexpr uint32_t TX = (uint32_t)(RB * BXG * (int)sizeof(TG) + RB * BXP * (int)sizeof(TP));
-    const int lane = threadIdx.x & 31;
-    const int x = s.x0 + lane;
-    const StripLane<R> ln = strip_lane<R>(x, s.w);
-    const bool cols_int = s.x0 >= 0 && s.x0 + 32 <= s.w;
-    StripRing<R> q;
-#pragma unroll
-    for (int k = 0; k < W; ++k) q.mg[k] = q.mp[k] = q.sgg[k] = q.sgp[k] = q.vr[k] = q.ha[k] = q.hb[k] = 0.f;
-    const int e_first = s.y0 - 2 * R;
-    const int e_last = min(s.y0 + s.seg, s.h) + 2 * R;
-    const int nblk = (e_last - e_first + RB - 1) / RB;
-    const int xg = floor_to(s.x0, UG), xp = floor_to(s.x0, UP);
-    const int og = s.x0 - xg + lane, op = s.x0 - xp + lane;
-    const uint32_t ring_s = smem_u32(ring), bar_s = smem_u32(bars);
-    auto issue = [&](int m) {  // lane 0: block m into slot m % NS
-        const int slot = m % NS;
-        const uint32_t bar = bar_s + 8u * slot, dst = ring_s + (uint32_t)(slot * SLOT);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TX) : "memory");
-        tma_load_3d(dst, &maps->a.map, xg, e_first + m * RB, plane, bar);
-        tma_load_3d(dst + BG, &maps->b.map, xp, e_first + m * RB, plane, bar);
-    };
-    if (lane == 0) {
-        for (int k = 0; k < NS; ++k)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * k) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int m = 0; m < min(NS, nblk); ++m) issue(m);
-    }
-    __syncwarp();
-    int m = 0;
-    bool ok = true;
-    for (; m < nblk; ++m) {
-        const int slot = m % NS;
-        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NS) & 1), kWaitLimit))) {
-            ok = false;
-            break;
-        }
-        const TG* sg = reinterpret_cast<const TG*>(ring + slot * SLOT) + og;
-        const TP* sp = reinterpret_cast<const TP*>(ring + slot * SLOT + BG) + op;
-#pragma unroll
-        for (int pp = 0; pp < NP; ++pp) {
-            const int base = e_first + m * RB + pp * W;
-            float gv[W], pv[W];
-#pragma unroll
-            for (int u = 0; u < W; ++u) {
-                gv[u] = to_f32<TG>(sg[(pp * W + u) * BXG]);
-                pv[u] = to_f32<TP>(sp[(pp * W + u) * BXP]);
-            }
-            if (pp == NP - 1) {
-                __syncwarp();  // every lane has read the slot
-                if (lane == 0 && m + NS < nblk) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue(m + NS);
-                }
-            }
-            if (base >= e_last) continue;  // uniform
-            const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W <= s.h &&
-                                 base + W <= e_last;
-            if (row_int) {
-#pragma unroll
-                for (int u = 0; u < W; ++u)
-                    strip_k1_row<TG, TP, R, true>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, stats, s,
-                                                  eps);
-            } else {
-#pragma unroll
-                for (int u = 0; u < W; ++u) {
-                    if (base + u >= e_last) break;  // uniform across the warp
-                    strip_k1_row<TG, TP, R, false>(q, ln, u, gv[u], pv[u], base + u, e_first, x, coef, stats, s,
-                                                   eps);
-                }
-            }
-        }
-    }
-    if (!ok) {
-        if (lane == 0) atomicOr(status, kStatusTimeout);
-        for (int qb = m; qb < nblk && qb < m + NS; ++qb)
-            mbar_wait(bar_s + 8u * (qb % NS), (uint32_t)((qb / NS) & 1), kWaitLimit);
-    }
-}
-
-// shared memory of one CTA of K1 strips staged by TMA (kStripWarps warps)
-template <typename TG, typename TP, int R>
-__host__ __device__ constexpr int k1_strip_tma_smem() {
-    return kStripWarps * StripTmaCfg<R>::NS *
-               (strip_box_bytes(R, (int)sizeof(TG), StripTmaCfg<R>::RB) +
-                strip_box_bytes(R, (int)sizeof(TP), StripTmaCfg<R>::RB)) +
-           kStripWarps * StripTmaCfg<R>::NS * 8;
-}
 
 // ------------------------------------------------------------------- K4
 // Algorithm 1 at low resolution for one strip segment.  Per window m (row
@@ -609,7 +415,7 @@ __device__ void lowres_bwd_strip_tma(const TmaTriple* maps, int plane, TP* __res
             KG = cn > 0.f ? a / cn : 0.f;
             KP = cn > 0.f ? b / cn : 0.f;
         }
-#pragma unroll
+#pragma unroll 1  // one copy of the period's code (ring slots are fixed within a period)
         for (int pp = 0; pp < NP; ++pp) {
             const int base = e_first + m * RB + pp * W;
             float gv[W], pv[W];
