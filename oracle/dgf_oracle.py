@@ -187,15 +187,22 @@ def upsample_T(Z: np.ndarray, h_l: int, w_l: int) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 def forward_plane(P: np.ndarray, G_l: np.ndarray, G_h: np.ndarray, r: int,
-                  eps: float) -> np.ndarray:
-    """O_h = f_up(Abar) * G_h + f_up(bbar) (Eq. 2 with the mean of A, b)."""
+                  eps: float, mean_ab: bool = True) -> np.ndarray:
+    """O_h = f_up(Abar) * G_h + f_up(bbar) (Eq. 2 with the mean of A, b).
+
+    mean_ab=False is the layer as Sec. 3.2 prints it: A_l, b_l upsampled
+    directly, O_h = f_up(A_l) * G_h + f_up(b_l).
+    """
     h, w = G_h.shape
-    Abar, bbar = mean_coefficients(G_l, P, r, eps)
+    if mean_ab:
+        Abar, bbar = mean_coefficients(G_l, P, r, eps)
+    else:
+        Abar, bbar = coefficients(G_l, P, r, eps)
     return upsample(Abar, h, w) * G_h + upsample(bbar, h, w)
 
 
 def backward_plane(R: np.ndarray, P: np.ndarray, G_l: np.ndarray, G_h: np.ndarray,
-                   r: int, eps: float):
+                   r: int, eps: float, mean_ab: bool = True):
     """Gradients of sum(O_h * R) for one plane, following Algorithm 1.
 
     Returns (dP, dG_l, dG_h).  The steps and names follow Algorithm 1
@@ -203,18 +210,19 @@ def backward_plane(R: np.ndarray, P: np.ndarray, G_l: np.ndarray, G_h: np.ndarra
     d I_h), with two extensions: f_up acts on the box-averaged Abar, bbar,
     so its transpose is followed by f_mu^T; and each ".grad f_mu" of the
     algorithm is the transpose box_mean_T of the clipped mean filter.
+    With mean_ab=False there is no f_mu^T after f_up^T: Algorithm 1 as printed.
     """
     h, w = G_h.shape
     h_l, w_l = P.shape
     mu, nu, var, cov = window_stats(G_l, P, r)        # \bar G_l, \bar O_l, Sigma_G, Sigma_GO
     A = cov / (var + eps)
-    Abar = box_mean(A, r)
+    Abar = box_mean(A, r) if mean_ab else A
     # d b_l = dO_h . grad_{b_l} f_up  (through bbar = f_mu(b))
     d_bbar = upsample_T(R, h_l, w_l)
-    d_b = box_mean_T(d_bbar, r)
+    d_b = box_mean_T(d_bbar, r) if mean_ab else d_bbar
     # d A_l = dO_h * G_h . grad_{A_l} f_up - d b_l * \bar G_l
     d_Abar = upsample_T(R * G_h, h_l, w_l)
-    d_A = box_mean_T(d_Abar, r) - d_b * mu
+    d_A = (box_mean_T(d_Abar, r) if mean_ab else d_Abar) - d_b * mu
     # d Sigma_GO = d A_l / (Sigma_G + eps);  d Sigma_G = -d A_l Sigma_GO / (Sigma_G + eps)^2
     d_cov = d_A / (var + eps)
     d_var = -d_A * cov / (var + eps) ** 2
@@ -242,7 +250,7 @@ def _f64(x) -> np.ndarray:
     return np.asarray(x, dtype=np.float64)
 
 
-def forward(p_l, I_l, I_h, r: int, eps: float, planes=None) -> np.ndarray:
+def forward(p_l, I_l, I_h, r: int, eps: float, planes=None, mean_ab: bool = True) -> np.ndarray:
     """O_h for NCHW inputs; ``planes`` optionally restricts to [(n, c), ...]."""
     p_l, I_l, I_h = _f64(p_l), _f64(I_l), _f64(I_h)
     N, C = I_h.shape[:2]
@@ -251,11 +259,11 @@ def forward(p_l, I_l, I_h, r: int, eps: float, planes=None) -> np.ndarray:
         for c in range(C):
             if planes is not None and (n, c) not in planes:
                 continue
-            out[n, c] = forward_plane(p_l[n, c], I_l[n, c], I_h[n, c], r, eps)
+            out[n, c] = forward_plane(p_l[n, c], I_l[n, c], I_h[n, c], r, eps, mean_ab)
     return out
 
 
-def backward(R, p_l, I_l, I_h, r: int, eps: float, planes=None):
+def backward(R, p_l, I_l, I_h, r: int, eps: float, planes=None, mean_ab: bool = True):
     """(dp_l, dI_l, dI_h) of sum(O_h * R) for NCHW inputs."""
     R, p_l, I_l, I_h = _f64(R), _f64(p_l), _f64(I_l), _f64(I_h)
     N, C = I_h.shape[:2]
@@ -267,7 +275,7 @@ def backward(R, p_l, I_l, I_h, r: int, eps: float, planes=None):
             if planes is not None and (n, c) not in planes:
                 continue
             dp[n, c], dIl[n, c], dIh[n, c] = backward_plane(
-                R[n, c], p_l[n, c], I_l[n, c], I_h[n, c], r, eps)
+                R[n, c], p_l[n, c], I_l[n, c], I_h[n, c], r, eps, mean_ab)
     return dp, dIl, dIh
 
 
@@ -298,7 +306,7 @@ def block_mean(X: np.ndarray, f: int) -> np.ndarray:
 
 
 def forward_guided(p_l, I_h, w1, w2, b2, r: int, eps: float, slope: float = 0.2,
-                   images=None) -> np.ndarray:
+                   images=None, mean_ab: bool = True) -> np.ndarray:
     """O_h with G_h = F(I_h) and G_l = block_mean(G_h, f), per channel c."""
     p_l, I_h = _f64(p_l), _f64(I_h)
     w1, w2, b2 = _f64(w1), _f64(w2), _f64(b2)
@@ -311,12 +319,12 @@ def forward_guided(p_l, I_h, w1, w2, b2, r: int, eps: float, slope: float = 0.2,
         G_h, _ = guide_apply(I_h[n], w1, w2, b2, slope)
         G_l = block_mean(G_h, f)
         for c in range(C):
-            out[n, c] = forward_plane(p_l[n, c], G_l[c], G_h[c], r, eps)
+            out[n, c] = forward_plane(p_l[n, c], G_l[c], G_h[c], r, eps, mean_ab)
     return out
 
 
 def backward_guided(R, p_l, I_h, w1, w2, b2, r: int, eps: float, slope: float = 0.2,
-                    images=None):
+                    images=None, mean_ab: bool = True):
     """(dp_l, dI_h, dw1, dw2, db2) of sum(O_h * R) with the guidance transform.
 
     dG_h collects dO_h * A_h and, through the block mean, dG_l / f^2 on every
@@ -342,7 +350,7 @@ def backward_guided(R, p_l, I_h, w1, w2, b2, r: int, eps: float, slope: float = 
         dG_h = np.zeros_like(G_h)
         for c in range(C):
             dp[n, c], dG_l, dG_h[c] = backward_plane(R[n, c], p_l[n, c], G_l[c],
-                                                     G_h[c], r, eps)
+                                                     G_h[c], r, eps, mean_ab)
             dG_h[c] += np.repeat(np.repeat(dG_l, f, axis=0), f, axis=1) / (f * f)
         dw2 += np.einsum("chw,khw->ck", dG_h, H)
         db2 += dG_h.sum(axis=(1, 2))

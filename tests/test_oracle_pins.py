@@ -326,6 +326,78 @@ def test_guided_backward_finite_differences():
     assert np.max(np.abs(db2)) < 1e-12  # guide-shift invariance
 
 
+# ---------------------------------- the layer as printed (no mean of A, b)
+
+@pytest.mark.parametrize("case", CASES)
+def test_paper_literal_forward_and_backward_match_torch(case):
+    # Sec. 3.2 / Algorithm 1 as printed: A_l, b_l upsampled directly
+    N, C, hl, wl, h, w, r, eps = case
+    d = synth.ragged_case(51, N, C, hl, wl, h, w)
+    R = synth.upstream_grad(5, d["I_h"].shape)
+    out = O.forward(d["p_l"], d["I_l"], d["I_h"], r, eps, mean_ab=False)
+    p = d["p_l"].clone().requires_grad_(True)
+    gl = d["I_l"].clone().requires_grad_(True)
+    gh = d["I_h"].clone().requires_grad_(True)
+    ref = TC.gf(p, gl, gh, r, eps, mean_ab=False)
+    np.testing.assert_allclose(out, ref.detach().numpy(), rtol=0, atol=1e-10)
+    (ref * R).sum().backward()
+    got = O.backward(R, d["p_l"], d["I_l"], d["I_h"], r, eps, mean_ab=False)
+    for a, b in zip(got, (p.grad, gl.grad, gh.grad)):
+        b = b.numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-10
+
+
+def test_paper_literal_differs_from_mean_form_and_agrees_where_it_must():
+    d = synth.ragged_case(52, 1, 1, 9, 11, 36, 44)
+    lit = O.forward(d["p_l"], d["I_l"], d["I_h"], 1, 1e-3, mean_ab=False)
+    mean = O.forward(d["p_l"], d["I_l"], d["I_h"], 1, 1e-3)
+    assert np.max(np.abs(lit - mean)) > 1e-3  # the variants are distinct
+    # r = 0: the box mean is the identity, so the two forms coincide
+    lit0 = O.forward(d["p_l"], d["I_l"], d["I_h"], 0, 1e-3, mean_ab=False)
+    np.testing.assert_allclose(lit0, O.forward(d["p_l"], d["I_l"], d["I_h"], 0, 1e-3), rtol=0, atol=1e-15)
+    # a linear target p = a G + b with eps -> 0: A = a and b exactly per window, both forms
+    G = d["I_l"][0, 0].numpy()
+    P = 0.6 * G + 0.25
+    Gh = d["I_h"][0, 0].numpy()
+    lit_lin = O.forward_plane(P, G, Gh, 1, 1e-14, mean_ab=False)
+    np.testing.assert_allclose(lit_lin, 0.6 * Gh + 0.25, rtol=0, atol=1e-7)
+
+
+def test_paper_literal_finite_differences():
+    d = synth.ragged_case(53, 1, 1, 6, 7, 24, 28)
+    P = d["p_l"][0, 0].numpy().copy()
+    Gl = d["I_l"][0, 0].numpy().copy()
+    Gh = d["I_h"][0, 0].numpy().copy()
+    R = synth.upstream_grad(3, (24, 28)).numpy()
+    dP, dGl, dGh = O.backward_plane(R, P, Gl, Gh, 2, 1e-3, mean_ab=False)
+
+    def loss():
+        return float(np.sum(O.forward_plane(P, Gl, Gh, 2, 1e-3, mean_ab=False) * R))
+
+    assert _fd_check(loss, P, dP) < 1e-6
+    assert _fd_check(loss, Gl, dGl) < 1e-6
+    assert _fd_check(loss, Gh, dGh, n_probe=48) < 1e-6
+
+
+def test_paper_literal_guided_matches_torch():
+    N, C, f, hl, wl, r, eps = 1, 3, 4, 5, 4, 1, 1e-3
+    d = synth.photo_like(54, N, C, hl, wl, f)
+    g = synth.guide_weights(7)
+    R = synth.upstream_grad(8, d["I_h"].shape)
+    out = O.forward_guided(d["p_l"], d["I_h"], g["w1"], g["w2"], g["b2"], r, eps, mean_ab=False)
+    p = d["p_l"].clone().requires_grad_(True)
+    ih = d["I_h"].clone().requires_grad_(True)
+    w1 = g["w1"].clone().requires_grad_(True)
+    w2 = g["w2"].clone().requires_grad_(True)
+    ref = TC.gf_guided(p, ih, w1, w2, g["b2"], r, eps, mean_ab=False)
+    np.testing.assert_allclose(out, ref.detach().numpy(), rtol=0, atol=1e-12)
+    (ref * R).sum().backward()
+    got = O.backward_guided(R, d["p_l"], d["I_h"], g["w1"], g["w2"], g["b2"], r, eps, mean_ab=False)
+    for a, b in zip(got[:4], (p.grad, ih.grad, w1.grad, w2.grad)):
+        b = b.numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-10
+
+
 # ------------------------------------------------ planted mistakes (pins bite)
 
 def test_pins_catch_a_dropped_mean_of_coefficients(monkeypatch):

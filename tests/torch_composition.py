@@ -24,7 +24,7 @@ def up(x: torch.Tensor, h: int, w: int) -> torch.Tensor:
                          align_corners=False)[0, 0]
 
 
-def gf_plane(P, G_l, G_h, r: int, eps: float):
+def gf_plane(P, G_l, G_h, r: int, eps: float, mean_ab: bool = True):
     mu = box(G_l, r)
     nu = box(P, r)
     var = box(G_l * G_l, r) - mu * mu
@@ -32,14 +32,16 @@ def gf_plane(P, G_l, G_h, r: int, eps: float):
     A = cov / (var + eps)
     b = nu - A * mu
     h, w = G_h.shape
+    if not mean_ab:  # the layer as printed: A_l, b_l upsampled directly
+        return up(A, h, w) * G_h + up(b, h, w)
     return up(box(A, r), h, w) * G_h + up(box(b, r), h, w)
 
 
-def gf(p_l, I_l, I_h, r: int, eps: float):
+def gf(p_l, I_l, I_h, r: int, eps: float, mean_ab: bool = True):
     N, C = I_h.shape[:2]
     rows = []
     for n in range(N):
-        rows.append(torch.stack([gf_plane(p_l[n, c], I_l[n, c], I_h[n, c], r, eps)
+        rows.append(torch.stack([gf_plane(p_l[n, c], I_l[n, c], I_h[n, c], r, eps, mean_ab)
                                  for c in range(C)]))
     return torch.stack(rows)
 
@@ -51,8 +53,8 @@ def guide(I, w1, w2, b2, slope=0.2):
     return F.conv2d(hdn, w2[:, :, None, None], b2)
 
 
-def gf_guided(p_l, I_h, w1, w2, b2, r: int, eps: float, slope=0.2):
+def gf_guided(p_l, I_h, w1, w2, b2, r: int, eps: float, slope=0.2, mean_ab: bool = True):
     f = I_h.shape[2] // p_l.shape[2]
     G_h = guide(I_h, w1, w2, b2, slope)
     G_l = F.avg_pool2d(G_h, f, stride=f)
-    return gf(p_l, G_l, G_h, r, eps)
+    return gf(p_l, G_l, G_h, r, eps, mean_ab)
