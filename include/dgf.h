@@ -180,6 +180,30 @@ int dgf_device_status(void);
 void dgf_set_tma(int on);
 
 /*
+ * Options of the _opt entry points (NULL = the defaults of dgf_forward and
+ * dgf_backward).
+ *   mean_ab = 1 (default): the fast guided filter's box mean of A and b
+ *             before upsampling (Abar, bbar), Algorithm 1 extended by f_mu^T;
+ *   mean_ab = 0: A_l, b_l upsampled directly, the layer exactly as Sec. 3.2
+ *             and Algorithm 1 print it.  Uses the warp-strip kernels for
+ *             r in {1, 2} and the generic tiles otherwise; shapes are not
+ *             autotuned in this mode.
+ */
+typedef struct {
+    int mean_ab;
+} dgf_options;
+
+dgf_status dgf_forward_opt(const void* p_l, const void* I_l, const void* I_h, void* O_h,
+                           int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
+                           dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes,
+                           dgf_stream_t stream, const dgf_options* opt);
+dgf_status dgf_backward_opt(const void* dO_h, const void* p_l, const void* I_l, const void* I_h,
+                            void* dp_l, void* dI_l, void* dI_h, float* dW,
+                            int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
+                            dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes,
+                            dgf_stream_t stream, const dgf_options* opt);
+
+/*
  * One image of a batched backward call: the inputs of dgf_backward for one
  * image (C channels) and its gradient outputs, each output nullable (not
  * needed).  No guidance transform in the batched path.

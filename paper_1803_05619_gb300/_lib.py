@@ -31,6 +31,10 @@ class dgf_image(ctypes.Structure):
                 ("eps", ctypes.c_float)]
 
 
+class dgf_options(ctypes.Structure):
+    _fields_ = [("mean_ab", ctypes.c_int)]
+
+
 class dgf_image_grad(ctypes.Structure):
     _fields_ = [("dO_h", ctypes.c_void_p), ("p_l", ctypes.c_void_p), ("I_l", ctypes.c_void_p),
                 ("I_h", ctypes.c_void_p), ("dp_l", ctypes.c_void_p), ("dI_l", ctypes.c_void_p),
@@ -53,6 +57,10 @@ _SIGS = {
                          ctypes.POINTER(dgf_guide), _P, _S, _P]),
     "dgf_backward": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _F, _I,
                           ctypes.POINTER(dgf_guide), _P, _S, _P]),
+    "dgf_forward_opt": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _F, _I,
+                             ctypes.POINTER(dgf_guide), _P, _S, _P, ctypes.POINTER(dgf_options)]),
+    "dgf_backward_opt": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _F, _I,
+                              ctypes.POINTER(dgf_guide), _P, _S, _P, ctypes.POINTER(dgf_options)]),
     "dgf_workspace_size_batched": (_S, [ctypes.POINTER(dgf_image), _I, _I]),
     "dgf_forward_batched": (_I, [ctypes.POINTER(dgf_image), _I, _I, _P, _S, _P]),
     "dgf_workspace_size_batched_backward": (_S, [ctypes.POINTER(dgf_image_grad), _I, _I]),
@@ -111,6 +119,17 @@ def dgf_backward(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w
                  ws_bytes, stream) -> int:
     return lib().dgf_backward(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps,
                               dt, g, ws, ws_bytes, stream)
+
+
+def dgf_forward_opt(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, ws, ws_bytes, stream, opt) -> int:
+    return lib().dgf_forward_opt(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, ws, ws_bytes,
+                                 stream, opt)
+
+
+def dgf_backward_opt(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g, ws,
+                     ws_bytes, stream, opt) -> int:
+    return lib().dgf_backward_opt(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps,
+                                  dt, g, ws, ws_bytes, stream, opt)
 
 
 def dgf_workspace_size_batched(imgs, n, dt) -> int:

@@ -251,7 +251,7 @@ static bool in_candidates(const LowCfg& c, int r, bool k4) {
 // Shapes from the autotuner's table override the defaults (whether or not
 // tuning is enabled now), so every call with the same key uses one shape.
 static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool gf32,
-                      std::initializer_list<const void*> hires_ptrs) {
+                      std::initializer_list<const void*> hires_ptrs, bool mean_ab = true) {
     Plan p;
     p.F = integer_factor(h_l, w_l, h, w);
     p.vec = pick_vec(dt, w, hires_ptrs);
@@ -280,6 +280,28 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     }
     if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256)
         p.k3_lth = a;
+    if (!mean_ab) {
+        // the layer as printed (no box mean of A, b): warp strips for r in
+        // {1, 2}, generic tiles otherwise (the column-walking tiles always
+        // box-average A, b)
+        if (r == 1 || r == 2) {
+            p.k1 = LowCfg{2, 32, 0};
+            p.k4 = LowCfg{2, 32, 0};
+        } else {
+            for (int tt : {32, 16, 8})
+                if (k1_smem_bytes(r, tt, tt) <= smem_limit()) {
+                    p.k1 = LowCfg{0, tt, tt};
+                    break;
+                }
+            for (int tt : {16, 8})
+                if (k4_smem_bytes(r, tt, tt) <= smem_limit()) {
+                    p.k4 = LowCfg{0, tt, tt};
+                    break;
+                }
+        }
+        p.k1.mean = 0;
+        p.k4.mean = 0;
+    }
     return p;
 }
 
@@ -726,9 +748,9 @@ size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r, d
     return layout(N, C, h_l, w_l, g != nullptr).total;
 }
 
-dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
-                       int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
-                       size_t ws_bytes, dgf_stream_t stream) {
+static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
+                               int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
+                               void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
@@ -741,10 +763,10 @@ dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* 
     char* ws = static_cast<char*>(workspace);
     float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
     const int planes = N * C;
-    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr, {I_h, O_h});
+    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr, {I_h, O_h}, mean_ab);
     Launcher L(s);
     cudaError_t e;
-    const bool tuning = tune_enabled() && !stream_capturing(s);
+    const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab;
     if (g == nullptr) {
         if (tuning) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
         e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
@@ -825,9 +847,10 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
     return DGF_OK;
 }
 
-dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l, void* dI_l,
-                        void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
-                        dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes, dgf_stream_t stream) {
+static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l,
+                                void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w,
+                                int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
+                                size_t ws_bytes, dgf_stream_t stream, bool mean_ab) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
@@ -850,12 +873,12 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
     float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
     float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
     const int planes = N * C;
-    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr, {dO_h, I_h, dI_h});
+    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr, {dO_h, I_h, dI_h}, mean_ab);
     Launcher L(s);
     cudaError_t e;
     if (g == nullptr) {
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
-        const bool tuning = tune_enabled() && !stream_capturing(s);
+        const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab;
         return backward_plain(L, dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws,
                               lay, s, tuning);
     }
@@ -895,6 +918,34 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
         }
     }
     return DGF_OK;
+}
+
+dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
+                       int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
+                       size_t ws_bytes, dgf_stream_t stream) {
+    return forward_impl(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream, true);
+}
+
+dgf_status dgf_forward_opt(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
+                           int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
+                           void* workspace, size_t ws_bytes, dgf_stream_t stream, const dgf_options* opt) {
+    return forward_impl(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream,
+                        opt == nullptr || opt->mean_ab != 0);
+}
+
+dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l, void* dI_l,
+                        void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
+                        dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes, dgf_stream_t stream) {
+    return backward_impl(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace,
+                         ws_bytes, stream, true);
+}
+
+dgf_status dgf_backward_opt(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l,
+                            void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w, int r,
+                            float eps, dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes,
+                            dgf_stream_t stream, const dgf_options* opt) {
+    return backward_impl(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace,
+                         ws_bytes, stream, opt == nullptr || opt->mean_ab != 0);
 }
 
 extern "C" size_t dgf_workspace_size_batched(const dgf_image* imgs, int n, dgf_dtype dt) {

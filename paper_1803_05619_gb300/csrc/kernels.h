@@ -33,6 +33,7 @@ __host__ __device__ inline int k2_pitch(int vec, int F, int w_l, int w) {
 struct LowCfg {
     int fast;
     int a, b;
+    int mean = 1;  // 1: box mean of A, b (fast guided filter); 0: A_l, b_l as Sec. 3.2 prints them
 };
 
 size_t k1_smem_bytes(int r, int TY, int TX);

@@ -14,10 +14,11 @@ __global__ void __launch_bounds__(kThreads) k1_coef(const TG* __restrict__ G, co
                                                     float2* __restrict__ coef, int h, int w, int r,
                                                     float eps, int TY, int TX,
                                                     const __grid_constant__ TmaPair tma,
-                                                    uint32_t* status) {
+                                                    uint32_t* status, int mean) {
     extern __shared__ __align__(128) float smem[];
     LowresTile t;
     t.init(h, w, r, eps, blockIdx.y * TY, blockIdx.x * TX, TY, TX);
+    t.mean = mean;
     const size_t plane = blockIdx.z;
     const size_t hw = (size_t)h * w;
     coef_tile<TG, TP>(G + plane * hw, P + plane * hw, coef + plane * hw, t, smem,
@@ -135,7 +136,12 @@ __device__ void lowres_bwd_tile(const TG* __restrict__ G, const TP* __restrict__
         const int ey1 = idx / t.EX1, ex = idx - ey1 * t.EX1;
         const int gy = t.ty0 - t.r + ey1, gx = t.tx0 - t.r + ex;
         float da = 0.f, db = 0.f;
-        if (gy >= 0 && gy < t.h && gx >= 0 && gx < t.w) {
+        if (!t.mean && gy >= 0 && gy < t.h && gx >= 0 && gx < t.w) {
+            // no box mean of A, b: dA, db are d Abar, d bbar themselves
+            const float2 c = dcoef[(size_t)gy * t.w + gx];
+            da = c.x;
+            db = c.y;
+        } else if (gy >= 0 && gy < t.h && gx >= 0 && gx < t.w) {
             const int lo = max(gy - t.r, 0), hi = min(gy + t.r, t.h - 1);
             for (int k = lo; k <= hi; ++k) {
                 const int o = (k - (t.ty0 - 2 * t.r)) * t.EX1 + ex;
@@ -203,10 +209,12 @@ template <typename TG, typename TP, typename TD>
 __global__ void __launch_bounds__(kThreads) k4_lowres_bwd(const TG* __restrict__ G, const TP* __restrict__ P,
                                                           const float2* __restrict__ dcoef,
                                                           TP* __restrict__ dP, TD* __restrict__ dG,
-                                                          int h, int w, int r, float eps, int TY, int TX) {
+                                                          int h, int w, int r, float eps, int TY, int TX,
+                                                          int mean) {
     extern __shared__ __align__(128) float smem[];
     LowresTile t;
     t.init(h, w, r, eps, blockIdx.y * TY, blockIdx.x * TX, TY, TX);
+    t.mean = mean;
     const size_t plane = blockIdx.z;
     const size_t hw = (size_t)h * w;
     lowres_bwd_tile<TG, TP, TD>(G + plane * hw, P + plane * hw, dcoef + plane * hw,
@@ -293,7 +301,7 @@ static cudaError_t k1_go(const void* G, const void* P, float2* coef, int planes,
     int gx, gy;
     low_grid(c, r, h, w, gx, gy);
     kern<<<dim3(gx, gy, planes), kThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), coef,
-                                                      h, w, r, eps, c.a, c.b, tma, status);
+                                                      h, w, r, eps, c.a, c.b, tma, status, c.mean);
     return cudaGetLastError();
 }
 
@@ -334,7 +342,7 @@ static cudaError_t k4_go(const void* G, const void* P, const float2* dcoef, void
     low_grid(c, r, h, w, gx, gy);
     kern<<<dim3(gx, gy, planes), kThreads, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef,
                                                       static_cast<TP*>(dP), static_cast<TD*>(dG), h, w, r, eps,
-                                                      c.a, c.b);
+                                                      c.a, c.b, c.mean);
     return cudaGetLastError();
 }
 

@@ -23,10 +23,11 @@ struct LowresTile {
     int EY2, EX2;    // staged region (TY + 4r) x (TX + 4r)
     int EY1, EX1;    // coefficient region (TY + 2r) x (TX + 2r)
     float eps;
+    int mean;        // 1: box mean of A, b; 0: A, b themselves (the layer as printed)
 
     __device__ __forceinline__ void init(int h_, int w_, int r_, float eps_, int ty0_, int tx0_,
                                          int TY_, int TX_) {
-        h = h_; w = w_; r = r_; eps = eps_; ty0 = ty0_; tx0 = tx0_; TY = TY_; TX = TX_;
+        h = h_; w = w_; r = r_; eps = eps_; ty0 = ty0_; tx0 = tx0_; TY = TY_; TX = TX_; mean = 1;
         EY2 = TY + 4 * r; EX2 = TX + 4 * r; EY1 = TY + 2 * r; EX1 = TX + 2 * r;
     }
     // number of in-image samples of the clipped 1-D window [c - r, c + r]

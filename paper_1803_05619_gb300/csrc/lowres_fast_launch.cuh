@@ -48,7 +48,7 @@ template <typename TG, typename TP, int R>
 __global__ void __launch_bounds__(kStripWarps * 32) k1_coef_strip(const TG* __restrict__ G, const TP* __restrict__ P,
                                                                    float2* __restrict__ coef, int h, int w, float eps,
                                                                    int seg, int nstrip, int nseg, int planes,
-                                                                   float4* __restrict__ stats) {
+                                                                   float4* __restrict__ stats, int mean) {
     const int gw = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
     if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
     const int strip = gw % nstrip, rest = gw / nstrip;
@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k1_coef_strip(const TG* __re
     s.x0 = strip * strip2_out_cols(R) - 2 * R;
     s.y0 = sg * seg;
     s.seg = seg;
+    s.mean = mean;
     const size_t hw = (size_t)h * w;
     coef_strip2<TG, TP, R>(G + plane * hw, P + plane * hw, coef + plane * hw, s, eps,
                            stats ? stats + plane * hw : nullptr);
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k1_coef_strip(const TG* __re
 template <typename TG, typename TP, int R>
 __global__ void __launch_bounds__(kStripWarps * 32)
     k1_coef_strip_tma(const __grid_constant__ TmaPair maps, float2* __restrict__ coef, float4* __restrict__ stats,
-                      int h, int w, float eps, int seg, int nstrip, int nseg, int planes, uint32_t* status) {
+                      int h, int w, float eps, int seg, int nstrip, int nseg, int planes, uint32_t* status, int mean) {
     extern __shared__ __align__(1024) unsigned char k1ring[];
     constexpr int NS = StripTmaCfg<R>::NS, RB = StripTmaCfg<R>::RB;
     constexpr int SLOT = strip2_box_bytes((int)sizeof(TG), RB) + strip2_box_bytes((int)sizeof(TP), RB);
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(kStripWarps * 32)
     s.x0 = strip * strip2_out_cols(R) - 2 * R;
     s.y0 = sg * seg;
     s.seg = seg;
+    s.mean = mean;
     unsigned char* ring = k1ring + (size_t)warp * NS * SLOT;
     uint64_t* bars = reinterpret_cast<uint64_t*>(k1ring + (size_t)kStripWarps * NS * SLOT) + warp * NS;
     const size_t hw = (size_t)h * w;
@@ -98,7 +100,7 @@ template <typename TG, typename TP, typename TD, int R>
 __global__ void __launch_bounds__(kK4StripWarps * 32)
     k4_lowres_bwd_strip(const TG* __restrict__ G, const TP* __restrict__ P, const float2* __restrict__ dcoef,
                         TP* __restrict__ dP, TD* __restrict__ dG, int h, int w, float eps, int seg, int nstrip,
-                        int nseg, int planes) {
+                        int nseg, int planes, int mean) {
     const int gw = blockIdx.x * kK4StripWarps + (threadIdx.x >> 5);
     if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
     const int strip = gw % nstrip, rest = gw / nstrip;
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(kK4StripWarps * 32)
     s.x0 = strip * (32 - 4 * R) - 2 * R;
     s.y0 = sg * seg;
     s.seg = seg;
+    s.mean = mean;
     const size_t hw = (size_t)h * w;
     lowres_bwd_strip<TG, TP, TD, R>(G + plane * hw, P + plane * hw, dcoef + plane * hw,
                                     dP ? dP + plane * hw : nullptr, dG ? dG + plane * hw : nullptr, s, eps);
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(kK4StripWarps * 32)
 template <typename TG, typename TP, typename TD, int R>
 __global__ void __launch_bounds__(kK4StripWarps * 32)
     k4_lowres_bwd_strip_tma(const __grid_constant__ TmaTriple maps, TP* __restrict__ dP, TD* __restrict__ dG, int h,
-                            int w, float eps, int seg, int nstrip, int nseg, int planes, uint32_t* status) {
+                            int w, float eps, int seg, int nstrip, int nseg, int planes, uint32_t* status, int mean) {
     extern __shared__ __align__(1024) unsigned char k4ring[];
     constexpr int NS = StripTmaCfg<R>::NS, RB = StripTmaCfg<R>::RB;
     constexpr int SLOT = strip_box_bytes(R, (int)sizeof(TG), RB) + strip_box_bytes(R, (int)sizeof(TP), RB) +
@@ -133,6 +136,7 @@ __global__ void __launch_bounds__(kK4StripWarps * 32)
     s.x0 = strip * (32 - 4 * R) - 2 * R;
     s.y0 = sg * seg;
     s.seg = seg;
+    s.mean = mean;
     const size_t hw = (size_t)h * w;
     unsigned char* ring = k4ring + (size_t)warp * NS * SLOT;
     uint64_t* bars = reinterpret_cast<uint64_t*>(k4ring + (size_t)kK4StripWarps * NS * SLOT) + warp * NS;
@@ -144,7 +148,7 @@ template <typename TG, typename TP, typename TD, int R>
 __global__ void __launch_bounds__(kK4StripWarps * 32)
     k4_lowres_bwd_strip_stats(const TG* __restrict__ G, const TP* __restrict__ P, const float2* __restrict__ dcoef,
                               const float4* __restrict__ stats, TP* __restrict__ dP, TD* __restrict__ dG, int h,
-                              int w, int seg, int nstrip, int nseg, int planes) {
+                              int w, int seg, int nstrip, int nseg, int planes, int mean) {
     const int gw = blockIdx.x * kK4StripWarps + (threadIdx.x >> 5);
     if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
     const int strip = gw % nstrip, rest = gw / nstrip;
@@ -155,6 +159,7 @@ __global__ void __launch_bounds__(kK4StripWarps * 32)
     s.x0 = strip * (32 - 4 * R) - 2 * R;
     s.y0 = sg * seg;
     s.seg = seg;
+    s.mean = mean;
     const size_t hw = (size_t)h * w;
     lowres_bwd_strip_stats<TG, TP, TD, R>(G + plane * hw, P + plane * hw, dcoef + plane * hw, stats + plane * hw,
                                           dP ? dP + plane * hw : nullptr, dG ? dG + plane * hw : nullptr, s);
@@ -181,11 +186,11 @@ static cudaError_t k1f_go(const void* G, const void* P, float2* coef, int planes
                 cudaError_t e = fast_prep(kern, smem_t);
                 if (e != cudaSuccess) return e;
                 kern<<<ctas, kStripWarps * 32, smem_t, s>>>(tma, coef, stats, h, w, eps, seg, nstrip, nseg, planes,
-                                                             status);
+                                                             status, c.mean);
                 return cudaGetLastError();
             }
             k1_coef_strip<TG, TP, R><<<ctas, kStripWarps * 32, 0, s>>>(
-                static_cast<const TG*>(G), static_cast<const TP*>(P), coef, h, w, eps, seg, nstrip, nseg, planes, stats);
+                static_cast<const TG*>(G), static_cast<const TP*>(P), coef, h, w, eps, seg, nstrip, nseg, planes, stats, c.mean);
             return cudaGetLastError();
         }
     }
@@ -227,7 +232,7 @@ static cudaError_t k4f_go(const void* G, const void* P, const float2* dcoef, voi
             if (stats != nullptr) {
                 k4_lowres_bwd_strip_stats<TG, TP, TD, R><<<ctas, kK4StripWarps * 32, 0, s>>>(
                     static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef, stats, static_cast<TP*>(dP),
-                    static_cast<TD*>(dG), h, w, seg, nstrip, nseg, planes);
+                    static_cast<TD*>(dG), h, w, seg, nstrip, nseg, planes, c.mean);
                 return cudaGetLastError();
             }
             if (tma != nullptr && tma->enabled) {
@@ -236,12 +241,12 @@ static cudaError_t k4f_go(const void* G, const void* P, const float2* dcoef, voi
                 cudaError_t e = fast_prep(kern, smem_t);
                 if (e != cudaSuccess) return e;
                 kern<<<ctas, kK4StripWarps * 32, smem_t, s>>>(*tma, static_cast<TP*>(dP), static_cast<TD*>(dG), h, w,
-                                                               eps, seg, nstrip, nseg, planes, status);
+                                                               eps, seg, nstrip, nseg, planes, status, c.mean);
                 return cudaGetLastError();
             }
             k4_lowres_bwd_strip<TG, TP, TD, R><<<ctas, kK4StripWarps * 32, 0, s>>>(
                 static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef, static_cast<TP*>(dP),
-                static_cast<TD*>(dG), h, w, eps, seg, nstrip, nseg, planes);
+                static_cast<TD*>(dG), h, w, eps, seg, nstrip, nseg, planes, c.mean);
             return cudaGetLastError();
         }
     }

@@ -46,6 +46,18 @@ __device__ void coef_tile(const TG* __restrict__ G, const TP* __restrict__ P,
         sB[idx] = b;
     }
     __syncthreads();
+    if (!t.mean) {
+        // no box mean: the output pixels' own A, b (the layer as Sec. 3.2 prints it)
+        for (int idx = threadIdx.x; idx < t.TY * t.TX; idx += kThreads) {
+            const int y = idx / t.TX, x = idx - y * t.TX;
+            const int gy = t.ty0 + y, gx = t.tx0 + x;
+            if (gy >= t.h || gx >= t.w) continue;
+            const int o = (y + t.r) * t.EX1 + x + t.r;
+            coef[(size_t)gy * t.w + gx] = make_float2(sA[o], sB[o]);
+        }
+        __syncthreads();
+        return;
+    }
     float* rA = hbuf;
     float* rB = hbuf + t.EY1 * t.TX;
     box_rows(sA, t.EX1, t.EY1, t.tx0 - t.r, rA, t.TX, t.tx0, t.TX, t.w, t.r);

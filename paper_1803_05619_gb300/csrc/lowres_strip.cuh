@@ -48,6 +48,7 @@ struct StripGeom {
     int x0;       // global column of lane 0 (first input column, may be negative)
     int y0;       // first output row of the segment
     int seg;      // output rows of the segment
+    int mean = 1; // 1: box mean of A, b (fast guided filter); 0: A, b themselves (the layer as printed)
 };
 
 // Register rings of one strip: level 1 holds per-row statistics of the last
@@ -210,13 +211,17 @@ __device__ __forceinline__ void strip_k4_row(StripRing<R>& q, StripBwdRing<R>& z
     strip_row_stats<R, INT>(q, ln, U, gvu, pvu, row_in);
     z.rg[U] = gvu;
     z.rp[U] = pvu;
-    {
+    if (s.mean) {
         // d Abar / N, d bbar / N at (e, x); zero outside the image
         const float inn = INT ? kInvW2
                               : ((ln.xin && row_in) ? inv_count(ln.nx * (min(e + R, s.h - 1) - max(e - R, 0) + 1))
                                                     : 0.f);
         z.hda[U] = hsum<R>(dvu.x * inn);
         z.hdb[U] = hsum<R>(dvu.y * inn);
+    } else {
+        // no box mean of A, b: the window's own d Abar, d bbar (row e, read at row e - R below)
+        z.hda[U] = dvu.x;
+        z.hdb[U] = dvu.y;
     }
     const int ce = e - R;
     float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
@@ -225,10 +230,15 @@ __device__ __forceinline__ void strip_k4_row(StripRing<R>& q, StripBwdRing<R>& z
         float mu, nu, var, cov;
         strip_window<R, INT>(q, ln, ny, mu, nu, var, cov);
         float dA = 0.f, db = 0.f;
+        if (s.mean) {
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            dA += z.hda[k];
-            db += z.hdb[k];
+            for (int k = 0; k < W; ++k) {
+                dA += z.hda[k];
+                db += z.hdb[k];
+            }
+        } else {
+            dA = z.hda[(U + W - R) % W];  // row ce = e - R
+            db = z.hdb[(U + W - R) % W];
         }
         const float ive = rcp_approx(var + eps);
         const float A = cov * ive;
@@ -483,22 +493,32 @@ __device__ __forceinline__ void strip_k4s_row(StripBwdRing<R>& z, const StripLan
     const bool row_in = e >= 0 && e < s.h;
     z.rg[U] = gvu;
     z.rp[U] = pvu;
-    {
+    if (s.mean) {
+        // d Abar / N, d bbar / N at (e, x); zero outside the image
         const float inn = INT ? kInvW2
                               : ((ln.xin && row_in) ? inv_count(ln.nx * (min(e + R, s.h - 1) - max(e - R, 0) + 1))
                                                     : 0.f);
         z.hda[U] = hsum<R>(dvu.x * inn);
         z.hdb[U] = hsum<R>(dvu.y * inn);
+    } else {
+        // no box mean of A, b: the window's own d Abar, d bbar (row e, read at row e - R below)
+        z.hda[U] = dvu.x;
+        z.hdb[U] = dvu.y;
     }
     const int ce = e - R;
     float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
     if (INT || (ln.xin && ce >= 0 && ce < s.h && e - e_first >= 2 * R)) {
         const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
         float dA = 0.f, db = 0.f;
+        if (s.mean) {
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            dA += z.hda[k];
-            db += z.hdb[k];
+            for (int k = 0; k < W; ++k) {
+                dA += z.hda[k];
+                db += z.hdb[k];
+            }
+        } else {
+            dA = z.hda[(U + W - R) % W];  // row ce = e - R
+            db = z.hdb[(U + W - R) % W];
         }
         const float mu = st.x, nu = st.y, ive = st.z, A = st.w;
         const float gamma = fmaf(-db, mu, dA) * ive;

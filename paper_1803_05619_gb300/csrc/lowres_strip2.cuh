@@ -140,8 +140,11 @@ __device__ __forceinline__ void strip2_k1_row(Strip2Ring<R>& q, const Strip2Lane
             b[c] = fmaf(-A[c], mu, nu);
             if (stats != nullptr && ln.out[c] && ce >= s.y0 && ce < s.y0 + s.seg)
                 stats[(size_t)ce * s.w + xa + c] = make_float4(mu, nu, ive, A[c]);
+            if (!s.mean && ln.out[c] && ce >= s.y0 && ce < s.y0 + s.seg)
+                coef[(size_t)ce * s.w + xa + c] = make_float2(A[c], b[c]);  // no box mean: A_l, b_l
         }
     }
+    if (!s.mean) return;
     // ---- level 2: horizontal box sums of A, b per column; vertical sum over the ring
     {
         float TA[2 * R + 2], TB[2 * R + 2];

@@ -72,8 +72,10 @@ def _sizes(p_l, I_h):
     return N, C, h_l, w_l, h, w
 
 
-def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2, out=None):
-    """O_h of the fast guided filtering layer (Eq. 1-2, box mean of A and b)."""
+def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2, out=None,
+               mean_ab=True):
+    """O_h of the fast guided filtering layer (Eq. 1-2, box mean of A and b;
+    mean_ab=False: A_l, b_l upsampled directly, the layer as printed)."""
     dev = _check(p_l, I_l, I_h, w1, w2, b2)
     N, C, h_l, w_l, h, w = _sizes(p_l, I_h)
     dt = dtype_code(I_h)
@@ -86,13 +88,18 @@ def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slo
     nb = L.dgf_workspace_size(N, C, h_l, w_l, h, w, r, dt, gp)
     ws = workspace(nb, dev)
     with torch.cuda.device(dev):
-        L.check(L.dgf_forward(_ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(out), N, C, h_l, w_l, h, w, r,
-                              float(eps), dt, gp, _ptr(ws), ws.numel(), _stream(dev)))
+        if mean_ab:
+            L.check(L.dgf_forward(_ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(out), N, C, h_l, w_l, h, w, r,
+                                  float(eps), dt, gp, _ptr(ws), ws.numel(), _stream(dev)))
+        else:
+            opt = L.dgf_options(0)
+            L.check(L.dgf_forward_opt(_ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(out), N, C, h_l, w_l, h, w, r,
+                                      float(eps), dt, gp, _ptr(ws), ws.numel(), _stream(dev), ctypes.byref(opt)))
     return out
 
 
 def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2,
-                need_p=True, need_Il=True, need_Ih=True, need_w=True):
+                need_p=True, need_Il=True, need_Ih=True, need_w=True, mean_ab=True):
     """(dp_l, dI_l, dI_h, (dw1, dw2, db2)) by the library's adjoint kernels."""
     dev = _check(dO_h, p_l, I_l, I_h, w1, w2, b2)
     N, C, h_l, w_l, h, w = _sizes(p_l, I_h)
@@ -109,9 +116,15 @@ def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=No
     nb = L.dgf_workspace_size(N, C, h_l, w_l, h, w, r, dt, gp)
     ws = workspace(nb, dev)
     with torch.cuda.device(dev):
-        L.check(L.dgf_backward(_ptr(dO_h), _ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(dp), _ptr(dIl),
-                               _ptr(dIh), _ptr(dW), N, C, h_l, w_l, h, w, r, float(eps), dt, gp,
-                               _ptr(ws), ws.numel(), _stream(dev)))
+        if mean_ab:
+            L.check(L.dgf_backward(_ptr(dO_h), _ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(dp), _ptr(dIl),
+                                   _ptr(dIh), _ptr(dW), N, C, h_l, w_l, h, w, r, float(eps), dt, gp,
+                                   _ptr(ws), ws.numel(), _stream(dev)))
+        else:
+            opt = L.dgf_options(0)
+            L.check(L.dgf_backward_opt(_ptr(dO_h), _ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(dp), _ptr(dIl),
+                                       _ptr(dIh), _ptr(dW), N, C, h_l, w_l, h, w, r, float(eps), dt, gp,
+                                       _ptr(ws), ws.numel(), _stream(dev), ctypes.byref(opt)))
     dws = None
     if dW is not None:
         hid = g.hidden

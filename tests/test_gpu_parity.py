@@ -284,6 +284,57 @@ def test_batched_backward_matches_single_bitwise(dtype):
         assert_grad(f64(outs[i][2])[None], rIh, dtype, "dI_h")
 
 
+# the layer as printed (no box mean of A, b): every low-res kernel form that
+# supports it (strips for r in {1, 2}, generic tiles otherwise)
+LIT_CASES = [("photo", 1, 2, 70, 90, 280, 360, 1, 1e-3), ("photo", 1, 2, 40, 44, 320, 352, 2, 1e-3),
+             ("ragged", 1, 1, 37, 53, 150, 211, 1, 1e-3), ("photo", 1, 2, 50, 70, 200, 280, 3, 1e-3),
+             ("photo", 1, 1, 36, 300, 144, 1200, 4, 1e-3), ("photo", 1, 1, 48, 40, 192, 160, 8, 1e-3),
+             ("photo", 1, 1, 30, 36, 120, 144, 0, 1e-2)]
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("case", LIT_CASES, ids=_ids(LIT_CASES))
+def test_paper_literal_variant_parity(case, dtype):
+    kind, N, C, hl, wl, h, w, r, eps = case
+    st = to_storage(make_case(kind, 300 + r, N, C, hl, wl, h, w), dtype)
+    R = synth.upstream_grad(9, st["I_h"].shape).to(dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    out = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps, mean_ab=False)
+    dp, dIl, dIh, _ = gf_backward(R.cuda(), g["p_l"], g["I_l"], g["I_h"], r, eps, mean_ab=False)
+    torch.cuda.synchronize()
+    ref = O.forward(f64(st["p_l"]), f64(st["I_l"]), f64(st["I_h"]), r, eps, mean_ab=False)
+    assert_fwd(f64(out), ref, dtype, eps)
+    rp, rIl, rIh = O.backward(f64(R), f64(st["p_l"]), f64(st["I_l"]), f64(st["I_h"]), r, eps, mean_ab=False)
+    assert_grad(f64(dp), rp, dtype, "dp_l")
+    if r > 0:
+        assert_grad(f64(dIl), rIl, dtype, "dI_l")
+    assert_grad(f64(dIh), rIh, dtype, "dI_h")
+    if r > 0:  # and it is not the default form
+        assert not torch.equal(out, gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps))
+
+
+def test_paper_literal_guided_parity():
+    N, C, hl, wl, f, r, eps = 1, 3, 24, 32, 4, 2, 1e-3
+    st = {k: v.to(BF16) for k, v in synth.photo_like(61, N, C, hl, wl, f).items()}
+    w = {k: v.float() for k, v in synth.guide_weights(62).items()}
+    R = synth.upstream_grad(63, st["I_h"].shape).to(BF16)
+    g = {k: v.cuda() for k, v in st.items()}
+    wc = {k: v.cuda() for k, v in w.items()}
+    out = gf_forward(g["p_l"], None, g["I_h"], r, eps, wc["w1"], wc["w2"], wc["b2"], 0.2, mean_ab=False)
+    dp, _, dIh, dws = gf_backward(R.cuda(), g["p_l"], None, g["I_h"], r, eps, wc["w1"], wc["w2"], wc["b2"], 0.2,
+                                  mean_ab=False)
+    torch.cuda.synchronize()
+    w64 = {k: v.double().numpy() for k, v in w.items()}
+    ref = O.forward_guided(f64(st["p_l"]), f64(st["I_h"]), w64["w1"], w64["w2"], w64["b2"], r, eps, mean_ab=False)
+    assert_fwd(f64(out), ref, BF16, eps)
+    rp, rI, rw1, rw2, _ = O.backward_guided(f64(R), f64(st["p_l"]), f64(st["I_h"]), w64["w1"], w64["w2"],
+                                            w64["b2"], r, eps, mean_ab=False)
+    assert_grad(f64(dp), rp, BF16, "dp_l")
+    assert_grad(f64(dIh), rI, BF16, "dI_h")
+    assert rel_l2(f64(dws[0]), rw1) <= 2e-2
+    assert rel_l2(f64(dws[1]), rw2) <= 2e-2
+
+
 def test_invalid_arguments_report_status():
     st = to_storage(make_case("photo", 9, 1, 1, 8, 8, 32, 32), F32)
     g = {k: v.cuda() for k, v in st.items()}
