@@ -487,6 +487,7 @@ def main():
             line["bf16_4k"] = bench_bf16_4k(args, device)
             line["batched_64_uneven"] = bench_batched_64(args, device)
             line["guided_train_8x2048"] = bench_guided(args, device)
+            line["paper_literal_fp32_plain"] = bench_paper_literal(args, device)
         if not args.no_oracle:
             reps = 15
             cv, csec = cpu_oracle(spec, reps=reps)
@@ -568,6 +569,26 @@ def bench_batched_64(args, device):
             "fwd_bwd_algorithmic_bytes": byts + byts_bwd,
             "fwd_bwd_frac_of_measured_hbm": round((byts + byts_bwd) / (ms2 * 1e-3) / 1e9 / peak, 4),
             "fwd_bwd_frac_of_nominal_8TBs": round((byts + byts_bwd) / (ms2 * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4)}
+
+
+def bench_paper_literal(args, device):
+    """The layer as Sec. 3.2 / Algorithm 1 print it (no box mean of A, b), on
+    the FP32 plain workload: forward + backward through the library."""
+    from paper_1803_05619_gb300.layer import gf_backward, gf_forward
+    spec = WORKLOADS[MAIN]
+    g, _ = make_inputs(spec, device, seed=0)
+    r, eps = spec["r"], spec["eps"]
+    N, C, h, w = g["I_h"].shape
+
+    def step():
+        gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps, mean_ab=False)
+        gf_backward(g["R"], g["p_l"], g["I_l"], g["I_h"], r, eps, mean_ab=False)
+
+    steps = max(10, min(args.steps // 10, 200))
+    ms = time_loop(step, steps, max(3, args.warmup // 4), 1, device)
+    return {"workload": MAIN + " with mean_ab=0", "fwd_bwd_mpix_s": round(N * h * w / (ms * 1e-3) / 1e6, 1),
+            "ms_fwd_bwd": round(ms, 4),
+            "note": "through the Python binding (allocates outputs and workspace per call)"}
 
 
 def bench_guided(args, device):
