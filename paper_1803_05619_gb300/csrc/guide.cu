@@ -24,6 +24,79 @@ __constant__ float c_b2[3];
 
 __device__ __forceinline__ float lrelu(float z, float slope) { return z > 0.f ? z : slope * z; }
 
+// ---- two pixels per instruction: Blackwell's paired FP32 arithmetic
+// (PTX fma.rn.f32x2 / mul.rn.f32x2 on a register pair).  Each half is the
+// scalar IEEE operation, so a pair gives exactly the two scalar results.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// The weights again as pairs {w, w} (filled from c_w1, c_w2, c_b2 by
+// guide_upload), so a paired instruction takes them straight from the
+// constant bank.
+constexpr int kWPairs = kHid * 3 + 3 * kHid + 3;
+__constant__ f32x2 c_wx2[kWPairs];  // [w1 (k, c) | w2 (c, k) | b2]
+__device__ f32x2 g_wx2_stage[kWPairs];
+
+__global__ void k_splat_weights(const float* __restrict__ w1, const float* __restrict__ w2,
+                                const float* __restrict__ b2, int hidden) {
+    const int i = threadIdx.x;
+    if (i >= kWPairs) return;
+    float v = 0.f;
+    if (i < kHid * 3) {
+        const int k = i / 3, c = i - 3 * k;
+        v = k < hidden ? w1[k * 3 + c] : 0.f;
+    } else if (i < 2 * kHid * 3) {
+        const int c = (i - kHid * 3) / kHid, k = (i - kHid * 3) - c * kHid;
+        v = k < hidden ? w2[c * hidden + k] : 0.f;
+    } else {
+        v = b2[i - 2 * kHid * 3];
+    }
+    g_wx2_stage[i] = f2_pack(v, v);
+}
+
+// guide_eval for two pixels (a, b) at once; per pixel the same operations in
+// the same order as guide_eval.  Used where registers are plentiful (K5):
+// in the high-res kernels that hold VEC pixels per thread the register
+// pairs it needs cost more occupancy than the saved issue slots gain.
+__device__ __forceinline__ void guide_eval2(const float (&xa)[3], const float (&xb)[3], float slope,
+                                            float (&ga)[3], float (&gb)[3]) {
+    const f32x2 x0 = f2_pack(xa[0], xb[0]), x1 = f2_pack(xa[1], xb[1]), x2 = f2_pack(xa[2], xb[2]);
+    const f32x2* w1 = c_wx2;
+    const f32x2* w2 = c_wx2 + kHid * 3;
+    const f32x2* bb = c_wx2 + 2 * kHid * 3;
+    f32x2 g0 = bb[0], g1 = bb[1], g2 = bb[2];
+#pragma unroll
+    for (int k = 0; k < kHid; ++k) {
+        const f32x2 z = f2_fma(w1[k * 3 + 2], x2, f2_fma(w1[k * 3 + 1], x1, f2_mul(w1[k * 3 + 0], x0)));
+        float za, zb;
+        f2_unpack(z, za, zb);
+        const f32x2 hk = f2_pack(lrelu(za, slope), lrelu(zb, slope));
+        g0 = f2_fma(w2[0 * kHid + k], hk, g0);
+        g1 = f2_fma(w2[1 * kHid + k], hk, g1);
+        g2 = f2_fma(w2[2 * kHid + k], hk, g2);
+    }
+    f2_unpack(g0, ga[0], gb[0]);
+    f2_unpack(g1, ga[1], gb[1]);
+    f2_unpack(g2, ga[2], gb[2]);
+}
+
 __device__ __forceinline__ void guide_eval(const float (&x)[3], float slope, float (&g)[3]) {
     g[0] = c_b2[0];
     g[1] = c_b2[1];
@@ -51,7 +124,19 @@ __global__ void __launch_bounds__(kThreads) k5_guide_down(const T* __restrict__ 
     float acc[3] = {0.f, 0.f, 0.f};
     for (int dy = 0; dy < f; ++dy) {
         const size_t row = (size_t)(f * i + dy) * w + (size_t)f * j;
-        for (int dx = 0; dx < f; ++dx) {
+        int dx = 0;
+        for (; dx + 1 < f; dx += 2) {  // two pixels per paired instruction
+            float xa[3], xb[3], ga[3], gb[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xa[c] = to_f32<T>(base[c * hw + row + dx]);
+                xb[c] = to_f32<T>(base[c * hw + row + dx + 1]);
+            }
+            guide_eval2(xa, xb, slope, ga, gb);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[c] += ga[c] + gb[c];
+        }
+        for (; dx < f; ++dx) {
             float x[3], g[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) x[c] = to_f32<T>(base[c * hw + row + dx]);
@@ -337,7 +422,13 @@ cudaError_t guide_upload(const float* w1, const float* w2, const float* b2, int 
             if (e != cudaSuccess) return e;
         }
     }
-    return cudaMemcpyToSymbolAsync(c_b2, b2, sizeof(float) * 3, 0, cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyToSymbolAsync(c_b2, b2, sizeof(float) * 3, 0, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_splat_weights<<<1, 128, 0, s>>>(w1, w2, b2, hidden);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    void* stage = nullptr;
+    if ((e = cudaGetSymbolAddress(&stage, g_wx2_stage)) != cudaSuccess) return e;
+    return cudaMemcpyToSymbolAsync(c_wx2, stage, sizeof(f32x2) * kWPairs, 0, cudaMemcpyDeviceToDevice, s);
 }
 
 template <typename T>
