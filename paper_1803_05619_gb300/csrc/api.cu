@@ -209,8 +209,10 @@ static bool pick_lowres_tiles(int r, Plan& p) {
     const size_t lim = smem_limit();
     bool ok1 = false, ok4 = false;
     if (low_fast_radius(r)) {
-        const LowCfg k1 = r <= 2 ? LowCfg{2, 32, 0} : LowCfg{1, 128, 32};
-        const LowCfg k4 = r <= 2 ? LowCfg{2, 32, 0} : (r == 4 ? LowCfg{1, 128, 16} : LowCfg{1, 64, 32});
+        // defaults from timing every shape on GB300 (BF16, 2 x 3 x 540 x 960 at r = 4,
+        // 8 x 3 x 256^2 at r = 8); the autotuner refines them per call shape
+        const LowCfg k1 = r <= 2 ? LowCfg{2, 32, 0} : (r == 4 ? LowCfg{1, 64, 32} : LowCfg{1, 64, 64});
+        const LowCfg k4 = r <= 2 ? LowCfg{2, 32, 0} : (r == 4 ? LowCfg{1, 64, 16} : LowCfg{1, 64, 32});
         if (k1_cfg_smem(k1, r, 0) <= lim) {
             p.k1 = k1;
             ok1 = true;
