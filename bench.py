@@ -41,6 +41,7 @@ WORKLOADS = {
     "fp32_plain_4x3x2048": dict(N=4, C=3, h_l=512, w_l=512, f=4, r=1, eps=1e-4, dtype="f32", recipe="blobs"),
     "bf16_4k_2x3x3840x2160": dict(N=2, C=3, h_l=540, w_l=960, f=4, r=2, eps=1e-3, dtype="bf16",
                                   recipe="photo"),
+    "fp32_small_1x1x256": dict(N=1, C=1, h_l=64, w_l=64, f=4, r=1, eps=1e-2, dtype="f32", recipe="photo"),
 }
 MAIN = "fp32_plain_4x3x2048"
 
@@ -487,6 +488,7 @@ def main():
             line["bf16_4k"] = bench_bf16_4k(args, device)
             line["batched_64_uneven"] = bench_batched_64(args, device)
             line["guided_train_8x2048"] = bench_guided(args, device)
+            line["small_fp32_1x1x256"] = bench_small(args, device)
             line["paper_literal_fp32_plain"] = bench_paper_literal(args, device)
         if not args.no_oracle:
             reps = 15
@@ -569,6 +571,33 @@ def bench_batched_64(args, device):
             "fwd_bwd_algorithmic_bytes": byts + byts_bwd,
             "fwd_bwd_frac_of_measured_hbm": round((byts + byts_bwd) / (ms2 * 1e-3) / 1e9 / peak, 4),
             "fwd_bwd_frac_of_nominal_8TBs": round((byts + byts_bwd) / (ms2 * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4)}
+
+
+def bench_small(args, device):
+    """The smallest configuration (1 x 1 x 64^2 -> 256^2, FP32, r = 1): bound by
+    launch latency, so reported as microseconds per call and Mpix/s."""
+    name = "fp32_small_1x1x256"
+    spec = WORKLOADS[name]
+    import torch
+    g, _ = make_inputs(spec, device, seed=0)
+    steps = max(50, min(args.steps, 1000))
+    pix = 256 * 256
+    cap = torch.cuda.Stream(device)
+    with torch.cuda.stream(cap):
+        step = Step(g, spec, device)  # calls go to the side stream, so the graph can capture them
+        ms_f = time_loop(step.forward, steps, args.warmup, 1, device)
+        ms_fb = time_loop(step, steps, args.warmup, 1, device)
+        # the same calls captured once in a CUDA graph and replayed (what a
+        # graph-captured training step pays: device time, no host launch cost)
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=cap):
+            step()
+        ms_g = time_loop(graph.replay, steps, args.warmup, 1, device)
+    return {"workload": name, "us_fwd": round(ms_f * 1e3, 2), "us_fwd_bwd": round(ms_fb * 1e3, 2),
+            "fwd_mpix_s": round(pix / (ms_f * 1e-3) / 1e6, 1), "fwd_bwd_mpix_s": round(pix / (ms_fb * 1e-3) / 1e6, 1),
+            "us_fwd_bwd_graph": round(ms_g * 1e3, 2), "fwd_bwd_graph_mpix_s": round(pix / (ms_g * 1e-3) / 1e6, 1),
+            "bound": "launch latency (2 kernels forward, 3 backward; eager calls pay the host launch cost)"}
 
 
 def bench_paper_literal(args, device):

@@ -73,6 +73,7 @@ _SIGS = {
     "dgf_launch_count": (ctypes.c_longlong, []),
     "dgf_device_status": (_I, []),
     "dgf_set_tma": (None, [_I]),
+    "dgf_set_fused": (None, [_I]),
     "dgf_shutdown": (None, []),
     "dgf_autotune": (None, [_I]),
     "dgf_autotune_entries": (_I, []),
@@ -180,6 +181,10 @@ def dgf_device_status() -> int:
 
 def dgf_set_tma(on: bool) -> None:
     lib().dgf_set_tma(1 if on else 0)
+
+
+def dgf_set_fused(on: bool) -> None:
+    lib().dgf_set_fused(1 if on else 0)
 
 
 def dgf_shutdown() -> None:

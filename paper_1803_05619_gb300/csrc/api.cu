@@ -188,7 +188,18 @@ struct Plan {
     int k2_ls = 8;         // K2 strips: low-res rows per segment
     int k3_lth = 8;
     bool k3_fast = false;
+    bool k12 = false;      // forward as the fused K12 kernel
+    bool k12_ok = false;   // K12 can serve this call (the tuner may still prefer K1 + K2)
+    int k12_ls = 32;       // K12: low-res rows per segment
 };
+
+static bool g_fused_allowed = false;
+
+static bool aligned_to(std::initializer_list<const void*> ptrs, int bytes) {
+    for (const void* p : ptrs)
+        if (p != nullptr && reinterpret_cast<uintptr_t>(p) % (uintptr_t)bytes != 0) return false;
+    return true;
+}
 
 static size_t g_smem_optin = 0;
 static size_t smem_limit() {
@@ -282,6 +293,16 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     }
     if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256)
         p.k3_lth = a;
+    // fused forward: plain guide, box mean of A, b, r in {1, 2}, a factor with
+    // one low-res cell per lane; a table entry a = 0 means the tuner found
+    // K1 + K2 faster for this key
+    p.k12_ok = g_fused_allowed && !gf32 && mean_ab && p.F > 0 && k12_supported(dt, r, p.F) &&
+               aligned_to(hires_ptrs, k12_vec_bytes(dt, p.F));
+    p.k12 = p.k12_ok;
+    if (p.k12_ok && tune_lookup(TuneKey{5, (int)dt, r, p.F, 0, 0}, a, b) && a >= 0 && a <= 256) {
+        p.k12 = a > 0;
+        if (a > 0) p.k12_ls = a;
+    }
     if (!mean_ab) {
         // the layer as printed (no box mean of A, b): warp strips for r in
         // {1, 2}, generic tiles otherwise (the column-walking tiles always
@@ -311,7 +332,7 @@ static std::vector<LowCfg> low_candidates(int r, bool k4) {
     std::vector<LowCfg> v;
     if (!low_fast_radius(r)) return v;
     if (r <= 2)
-        for (int seg : {8, 16, 32, 64, 128}) v.push_back(LowCfg{2, seg, 0});
+        for (int seg : {8, 16, 24, 32, 48, 64, 128}) v.push_back(LowCfg{2, seg, 0});
     static const int cws[] = {64, 128, 256};
     static const int eys[] = {16, 32, 64};
     for (int cw : cws)
@@ -637,6 +658,39 @@ static void tune_k3(dgf_dtype dt, const float2* coef, const void* R, const void*
     }
 }
 
+// The fused forward against the two-kernel forward with its tuned shapes:
+// records the fastest K12 segment length, or 0 when K1 + K2 win.
+static void tune_k12(dgf_dtype dt, const void* G, const void* P, float2* coef, const void* in, void* out,
+                     int planes, int h_l, int w_l, int h, int w, int r, float eps, cudaStream_t s, Plan& p) {
+    if (!p.k12_ok) return;
+    TuneKey key{5, (int)dt, r, p.F, 0, 0};
+    int a, b;
+    if (tune_lookup(key, a, b)) return;
+    size_t landing = 0;
+    TmaPair tma = make_tma_pair(G, dt, P, dt, planes, h_l, w_l, r, p.k1, landing);
+    const size_t smem = k1_cfg_smem(p.k1, r, tma.enabled ? landing : 0);
+    float best = time_launch(s, [&] {
+        cudaError_t e = launch_k1(dt, false, G, P, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, status_ptr(),
+                                  nullptr, s);
+        if (e != cudaSuccess) return e;
+        return launch_k2_plan(dt, coef, in, out, planes, h_l, w_l, h, w, p, p.k2_strip ? p.k2_ls : p.k2_th, s);
+    }, 3);
+    if (best <= 0.f) best = 1e30f;
+    int bl = 0;
+    for (int ls : {8, 16, 32, 64}) {
+        const float ms = time_launch(s, [&] {
+            return launch_k12(dt, G, P, in, out, planes, h_l, w_l, h, w, r, p.F, eps, ls, s);
+        }, 3);
+        if (ms > 0.f && ms < best) {
+            best = ms;
+            bl = ls;
+        }
+    }
+    tune_store(key, bl, 0);
+    p.k12 = bl > 0;
+    if (bl > 0) p.k12_ls = bl;
+}
+
 static cudaError_t run_k1(Launcher& L, dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef,
                           int planes, int h_l, int w_l, int r, float eps, const Plan& p, cudaStream_t s,
                           float4* stats = nullptr) {
@@ -770,6 +824,19 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
     cudaError_t e;
     const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab;
     if (g == nullptr) {
+        if (tuning && p.k12_ok) {
+            // shapes of the two-kernel forward first: K12 is timed against it
+            tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
+            tune_k2(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, s, p);
+            tune_k12(dt, I_l, p_l, coef, I_h, O_h, planes, h_l, w_l, h, w, r, eps, s, p);
+        }
+        if (p.k12) {
+            e = L.run("k12_fused_forward", [&] {
+                return launch_k12(dt, I_l, p_l, I_h, O_h, planes, h_l, w_l, h, w, r, p.F, eps, p.k12_ls, s);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "k12");
+            return DGF_OK;
+        }
         if (tuning) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
         e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
         if (e != cudaSuccess) return cuda_fail(e, "k1");
@@ -1220,6 +1287,8 @@ extern "C" int dgf_device_status(void) {
 }
 
 extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
+
+extern "C" void dgf_set_fused(int on) { g_fused_allowed = on != 0; }
 
 extern "C" void dgf_autotune(int on) { tune_set_enabled(on != 0); }
 

@@ -396,14 +396,20 @@ struct K2Rows {
     float2 next[VEC / F + 2];     // tap columns of the next block's second row, loaded a block ahead
 };
 
+// Where K2 reads (Abar, bbar) of row ii, column jj from: the plane's
+// coefficient array.
+struct CoefIn {
+    const float2* __restrict__ coef;
+    int w_l;
+    __device__ __forceinline__ float2 at(int ii, int jj) const { return coef[(size_t)ii * w_l + jj]; }
+};
+
 // The lane's K + 2 tap columns of coefficient row ii (clamped to the image).
-template <int VEC, int F>
-__device__ __forceinline__ void k2s_taps(const float2* __restrict__ coef, int ii, int J, int w_l,
-                                         float2 (&tp)[VEC / F + 2]) {
+template <int VEC, int F, class Src>
+__device__ __forceinline__ void k2s_taps(const Src& coef, int ii, int J, int w_l, float2 (&tp)[VEC / F + 2]) {
     constexpr int K = VEC / F;
-    const float2* row = coef + (size_t)ii * w_l;
 #pragma unroll
-    for (int c = 0; c < K + 2; ++c) tp[c] = row[clampi(J - 1 + c, 0, w_l - 1)];
+    for (int c = 0; c < K + 2; ++c) tp[c] = coef.at(ii, clampi(J - 1 + c, 0, w_l - 1));
 }
 
 template <int VEC, int F>
@@ -416,18 +422,16 @@ __device__ __forceinline__ void k2s_hrow_from(const float2 (&tp)[VEC / F + 2], f
 }
 
 // Before the first block b0: row clamp(b0) becomes the "second tap" row.
-template <int VEC, int F>
-__device__ __forceinline__ void k2s_init(K2Rows<VEC, F>& q, const float2* __restrict__ coef, int b0, int J, int h_l,
-                                         int w_l) {
+template <int VEC, int F, class Src>
+__device__ __forceinline__ void k2s_init(K2Rows<VEC, F>& q, const Src& coef, int b0, int J, int h_l, int w_l) {
     k2s_taps<VEC, F>(coef, clampi(b0, 0, h_l - 1), J, w_l, q.next);
     k2s_hrow_from<VEC, F>(q.next, q.A1, q.B1);
     k2s_taps<VEC, F>(coef, min(max(b0, -1) + 1, h_l - 1), J, w_l, q.next);
 }
 
 // Block i begins: taps rows clamp(i) (the previous second row) and clamp(i + 1).
-template <int VEC, int F>
-__device__ __forceinline__ void k2s_block(K2Rows<VEC, F>& q, const float2* __restrict__ coef, int i, int J, int h_l,
-                                          int w_l) {
+template <int VEC, int F, class Src>
+__device__ __forceinline__ void k2s_block(K2Rows<VEC, F>& q, const Src& coef, int i, int J, int h_l, int w_l) {
     float a[VEC], b[VEC];
     k2s_hrow_from<VEC, F>(q.next, a, b);  // row min(i + 1, h_l - 1)
     k2s_taps<VEC, F>(coef, min(i + 2, h_l - 1), J, w_l, q.next);
@@ -514,13 +518,13 @@ __device__ void k2_strip_tma(const float2* __restrict__ coef, const CUtensorMap*
     }
     __syncwarp();
     K2Rows<VEC, F> q;
-    k2s_init<VEC, F>(q, coef, b0, L.J, h_l, w_l);
+    k2s_init<VEC, F>(q, CoefIn{coef, w_l}, b0, L.J, h_l, w_l);
     int m = 0;
     bool ok = true;
     for (; m < nblk; ++m) {
         const int slot = m % NSB;
         const int i = b0 + m;
-        k2s_block<VEC, F>(q, coef, i, L.J, h_l, w_l);
+        k2s_block<VEC, F>(q, CoefIn{coef, w_l}, i, L.J, h_l, w_l);
         if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NSB) & 1), kWaitLimit))) {
             ok = false;
             break;
@@ -599,10 +603,10 @@ __device__ void k2_strip_async(const float2* __restrict__ coef, const T* __restr
         else asm volatile("cp.async.commit_group;" ::: "memory");  // keep the group count uniform
     }
     K2Rows<VEC, F> q;
-    k2s_init<VEC, F>(q, coef, b0, L.J, h_l, w_l);
+    k2s_init<VEC, F>(q, CoefIn{coef, w_l}, b0, L.J, h_l, w_l);
     for (int m = 0; m < nblk; ++m) {
         const int i = b0 + m;
-        k2s_block<VEC, F>(q, coef, i, L.J, h_l, w_l);
+        k2s_block<VEC, F>(q, CoefIn{coef, w_l}, i, L.J, h_l, w_l);
         asm volatile("cp.async.wait_group %0;" ::"n"(NSB - 1) : "memory");
         const T* sr = reinterpret_cast<const T*>(ring + (m % NSB) * B::SLOT) + lane * VEC;
 #pragma unroll

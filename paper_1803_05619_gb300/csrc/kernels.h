@@ -69,6 +69,14 @@ cudaError_t launch_k3(dgf_dtype dt, const float2* coef, const void* R, const voi
 cudaError_t launch_k3_general(dgf_dtype dt, const void* R, const void* G, float2* dcoef, int planes,
                               int h_l, int w_l, int h, int w, cudaStream_t s);
 
+// Fused forward (K1 + K2 in one kernel per high-res warp strip; r in {1, 2};
+// one low-res cell per lane: F-pixel vectors of 8 or 16 bytes).  LS =
+// low-res rows per segment.  in/out must be aligned to k12_vec_bytes.
+bool k12_supported(dgf_dtype dt, int r, int F);
+int k12_vec_bytes(dgf_dtype dt, int F);
+cudaError_t launch_k12(dgf_dtype dt, const void* G, const void* P, const void* in, void* out, int planes, int h_l,
+                       int w_l, int h, int w, int r, int F, float eps, int LS, cudaStream_t s);
+
 // Guidance transform (Sec. 3.4): weights staged to constant memory first.
 constexpr int kMaxK6Blocks = 1024;   // rows of weight-gradient partials
 constexpr int kWGradPadded = 99;     // padded [dw1 16x3 | dw2 3x16 | db2 3]

@@ -16,7 +16,11 @@
 // border takes the interior form: every window is full, so the masks and
 // clipped counts drop out and the counts' reciprocals are constants.  Both
 // forms use the same correctly rounded count reciprocals, so a pixel's result
-// does not depend on which form produced it.
+// does not depend on which form produced it.  The first periods of a segment,
+// which only fill the rings, take the interior form too when their rows are
+// inside the image: what they compute before the rings are full is never
+// stored (a per-row predicate) and leaves the rings before any stored
+// result reads it.
 //
 // Statistics are exactly centred as in the tile kernels: each row segment is
 // centred on its own mean and rows are combined with Chan's update.
@@ -256,7 +260,7 @@ __device__ __forceinline__ void strip_k4_row(StripRing<R>& q, StripBwdRing<R>& z
     z.hq2[U] = hsum<R>(q2);
     z.hq3[U] = hsum<R>(q3);
     const int co = ce - R;
-    const bool write = INT ? (lane >= 2 * R && lane < 32 - 2 * R)
+    const bool write = INT ? (lane >= 2 * R && lane < 32 - 2 * R && e - e_first >= 4 * R)
                            : (ln.out && co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
     if (write) {
         float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
@@ -333,7 +337,7 @@ __device__ void lowres_bwd_strip(const TG* __restrict__ G, const TP* __restrict_
             dv[u] = dn[u];
         }
         if (base + W < e_last) load(base + W);
-        const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W + R <= s.h &&
+        const bool row_int = cols_int && base >= 3 * R && base + W + R <= s.h &&
                              base + W <= e_last;
         if (row_int) {
 #pragma unroll
@@ -444,7 +448,7 @@ __device__ void lowres_bwd_strip_tma(const TmaTriple* maps, int plane, TP* __res
                 }
             }
             if (base >= e_last) continue;  // uniform
-            const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W + R <= s.h &&
+            const bool row_int = cols_int && base >= 3 * R && base + W + R <= s.h &&
                                  base + W <= e_last;
             if (row_int) {
 #pragma unroll
@@ -535,7 +539,7 @@ __device__ __forceinline__ void strip_k4s_row(StripBwdRing<R>& z, const StripLan
     z.hq2[U] = hsum<R>(q2);
     z.hq3[U] = hsum<R>(q3);
     const int co = ce - R;
-    const bool write = INT ? (lane >= 2 * R && lane < 32 - 2 * R)
+    const bool write = INT ? (lane >= 2 * R && lane < 32 - 2 * R && e - e_first >= 4 * R)
                            : (ln.out && co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
     if (write) {
         float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
@@ -609,7 +613,7 @@ __device__ void lowres_bwd_strip_stats(const TG* __restrict__ G, const TP* __res
             sv[u] = sn[u];
         }
         if (base + W < e_last) load(base + W);
-        const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W + R <= s.h &&
+        const bool row_int = cols_int && base >= 3 * R && base + W + R <= s.h &&
                              base + W <= e_last;
         if (row_int) {
 #pragma unroll

@@ -7,8 +7,12 @@
 // shuffles from each neighbouring lane, so the shuffles, loads and loop
 // overhead are shared by two outputs, and the halo is R lanes per side
 // (2R columns) out of 32: 64 - 4R outputs per strip instead of 32 - 4R.
-// Per column the arithmetic is the one-column strip's, term for term.
+// The two columns run in lock step as the halves of paired FP32
+// instructions (f32x2): per column the arithmetic is the one-column
+// walk's, term for term, at one instruction per pair.
 #pragma once
+
+#include <type_traits>
 
 #include "lowres_strip.cuh"
 
@@ -16,16 +20,19 @@ namespace dgf {
 
 template <int R>
 struct Strip2Lane {
-    float mk[2][2 * R + 1];  // 1 where column xa + c - R + k is inside the image
-    int nx[2];               // clipped window widths of the two columns
-    bool xin[2];             // columns inside the image
-    bool out[2];             // column written by this lane (lanes [R, 32 - R), inside the image)
+    f32x2 mk[2 * R + 1];  // per tap k: 1 where column xa + c - R + k is inside the image (halves c = 0, 1)
+    f32x2 nx, inx;        // clipped window widths of the two columns, and their reciprocals
+    f32x2 xin2;           // 1 for the columns inside the image
+    int nx_i[2];          // the widths as integers (count-table index)
+    bool xin[2];          // columns inside the image
+    bool out[2];          // column written by this lane (lanes [R, 32 - R), inside the image)
 };
 
 template <int R>
 __device__ __forceinline__ Strip2Lane<R> strip2_lane(int xa, int w) {
     Strip2Lane<R> ln;
     const int lane = threadIdx.x & 31;
+    float mk[2][2 * R + 1];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         const int x = xa + c;
@@ -33,177 +40,248 @@ __device__ __forceinline__ Strip2Lane<R> strip2_lane(int xa, int w) {
 #pragma unroll
         for (int k = 0; k < 2 * R + 1; ++k) {
             const int xx = x - R + k;
-            ln.mk[c][k] = (xx >= 0 && xx < w) ? 1.f : 0.f;
+            mk[c][k] = (xx >= 0 && xx < w) ? 1.f : 0.f;
         }
-        ln.nx[c] = ln.xin[c] ? min(x + R, w - 1) - max(x - R, 0) + 1 : 1;
+        ln.nx_i[c] = ln.xin[c] ? min(x + R, w - 1) - max(x - R, 0) + 1 : 1;
         ln.out[c] = lane >= R && lane < 32 - R && ln.xin[c];
     }
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) ln.mk[k] = f2_pack(mk[0][k], mk[1][k]);
+    ln.nx = f2_pack((float)ln.nx_i[0], (float)ln.nx_i[1]);
+    ln.inx = f2_pack(inv_count(ln.nx_i[0]), inv_count(ln.nx_i[1]));
+    ln.xin2 = f2_pack(ln.xin[0] ? 1.f : 0.f, ln.xin[1] ? 1.f : 0.f);
     return ln;
 }
 
+// Register rings of the last 2R + 1 rows, one pair {column xa, column xa + 1}
+// per entry; vr holds {v, v} with v = 1 for rows inside the image.
 template <int R>
 struct Strip2Ring {
     static constexpr int W = 2 * R + 1;
-    float mg[2][W], mp[2][W], sgg[2][W], sgp[2][W], ha[2][W], hb[2][W];
-    float vr[W];
+    f32x2 mg[W], mp[W], sgg[W], sgp[W], ha[W], hb[W], vr[W];
 };
 
-// The 2R + 2 consecutive values a lane's two windows span, from its own pair
-// (v0, v1) and R shuffles from each neighbour: T[c .. c + 2R] are column c's taps.
+// The lane's 2R + 1 tap pairs of one row: Q[k] = {T[k], T[k + 1]} where
+// T[0 .. 2R + 1] are the 2R + 2 consecutive values its two windows span
+// (its own pair (v0, v1) and R shuffles from each neighbouring lane), so
+// Q[k] holds tap k of column xa and of column xa + 1.
 template <int R>
-__device__ __forceinline__ void strip2_taps(float v0, float v1, float (&T)[2 * R + 2]) {
+__device__ __forceinline__ void strip2_pairs(float v0, float v1, f32x2 (&Q)[2 * R + 1]) {
     if constexpr (R == 1) {
-        T[0] = shfl_up(v1, 1);
-        T[1] = v0;
-        T[2] = v1;
-        T[3] = shfl_dn(v0, 1);
+        const float l1 = shfl_up(v1, 1), r0 = shfl_dn(v0, 1);
+        Q[0] = f2_pack(l1, v0);
+        Q[1] = f2_pack(v0, v1);
+        Q[2] = f2_pack(v1, r0);
     } else {
-        T[0] = shfl_up(v0, 1);
-        T[1] = shfl_up(v1, 1);
-        T[2] = v0;
-        T[3] = v1;
-        T[4] = shfl_dn(v0, 1);
-        T[5] = shfl_dn(v1, 1);
+        const float l0 = shfl_up(v0, 1), l1 = shfl_up(v1, 1), r0 = shfl_dn(v0, 1), r1 = shfl_dn(v1, 1);
+        Q[0] = f2_pack(l0, l1);
+        Q[1] = f2_pack(l1, v0);
+        Q[2] = f2_pack(v0, v1);
+        Q[3] = f2_pack(v1, r0);
+        Q[4] = f2_pack(r0, r1);
     }
 }
 
-// K1 for input row e entering ring slot U (both columns).  INT: interior
-// ring period.  stats non-null: also write (mu, nu, 1/(var + eps), A) for the
-// segment's rows.
+// K1 for input row e entering ring slot U, both columns at once in paired
+// FP32 (each half is the one-column arithmetic), in two stages:
+//   stage A: level 1 of row e, then Eq. 1's A, b of window row e - R;
+//   stage B: level 2 (box sums of A, b) and the output row e - 2R.
+// INT: interior ring period.  stats non-null: stage A also writes
+// (mu, nu, 1/(var + eps), A) for the segment's rows.
 template <int R, bool INT>
-__device__ __forceinline__ void strip2_k1_row(Strip2Ring<R>& q, const Strip2Lane<R>& ln, int U, float g0, float g1,
-                                              float p0, float p1, int e, int e_first, int xa,
-                                              float2* __restrict__ coef, float4* __restrict__ stats,
-                                              const StripGeom& s, float eps) {
+__device__ __forceinline__ void strip2_k1_stage_a(Strip2Ring<R>& q, const Strip2Lane<R>& ln, int U, float g0,
+                                                  float g1, float p0, float p1, int e, int e_first, int xa,
+                                                  float2* __restrict__ coef, float4* __restrict__ stats,
+                                                  const StripGeom& s, f32x2 eps2, f32x2& A_out, f32x2& b_out) {
     constexpr int W = 2 * R + 1;
     constexpr float kInvW = 1.f / (float)W;
     constexpr float kInvW2 = 1.f / (float)(W * W);
-    const int lane = threadIdx.x & 31;
     // ---- level 1: centred statistics of row e over each column's window
-    float TG[2 * R + 2], TP[2 * R + 2];
-    strip2_taps<R>(g0, g1, TG);
-    strip2_taps<R>(p0, p1, TP);
+    {
+        f32x2 QG[W], QP[W];
+        strip2_pairs<R>(g0, g1, QG);
+        strip2_pairs<R>(p0, p1, QP);
+        f32x2 s1 = QG[0], s2 = QP[0];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        float s1 = 0.f, s2 = 0.f;
+        for (int k = 1; k < W; ++k) {
+            s1 = f2_add(s1, QG[k]);
+            s2 = f2_add(s2, QP[k]);
+        }
+        const f32x2 inx = INT ? f2_splat(kInvW) : ln.inx;
+        const f32x2 m1 = f2_mul(s1, inx), m2 = f2_mul(s2, inx);
+        f32x2 a = 0ull, cc = 0ull;  // +0.0 in both halves
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            s1 += TG[c + k];
-            s2 += TP[c + k];
+            f32x2 dg = f2_sub(QG[k], m1);
+            if (!INT) dg = f2_mul(ln.mk[k], dg);
+            a = f2_fma(dg, dg, a);
+            cc = f2_fma(dg, f2_sub(QP[k], m2), cc);
         }
-        const float inx = INT ? kInvW : inv_count(ln.nx[c]);
-        const float m1 = s1 * inx, m2 = s2 * inx;
-        float a = 0.f, cc = 0.f;
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            const float dg = INT ? TG[c + k] - m1 : ln.mk[c][k] * (TG[c + k] - m1);
-            a = fmaf(dg, dg, a);
-            cc = fmaf(dg, TP[c + k] - m2, cc);
-        }
-        q.mg[c][U] = m1;
-        q.mp[c][U] = m2;
-        q.sgg[c][U] = a;
-        q.sgp[c][U] = cc;
+        q.mg[U] = m1;
+        q.mp[U] = m2;
+        q.sgg[U] = a;
+        q.sgp[U] = cc;
+        q.vr[U] = (INT || (e >= 0 && e < s.h)) ? f2_splat(1.f) : 0ull;
     }
-    q.vr[U] = (INT || (e >= 0 && e < s.h)) ? 1.f : 0.f;
-    // ---- Eq. 1's A, b of window row ce = e - R for each column
+    // ---- Eq. 1's A, b of window row ce = e - R for both columns
     const int ce = e - R;
-    float A[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
+    f32x2 A2 = 0ull, b2 = 0ull;
     const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
     const bool rows_ok = INT || (ce >= 0 && ce < s.h && e - e_first >= 2 * R);
+    if (rows_ok) {
+        f32x2 t1 = q.mg[0], t2 = q.mp[0], ta = q.sgg[0], tc = q.sgp[0];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        if (INT || (rows_ok && ln.xin[c])) {
-            float t1 = 0.f, t2 = 0.f, ta = 0.f, tc = 0.f;
+        for (int k = 1; k < W; ++k) {
+            t1 = f2_add(t1, q.mg[k]);
+            t2 = f2_add(t2, q.mp[k]);
+            ta = f2_add(ta, q.sgg[k]);
+            tc = f2_add(tc, q.sgp[k]);
+        }
+        const f32x2 iny = f2_splat(INT ? kInvW : inv_count(ny));
+        const f32x2 mu = f2_mul(t1, iny), nu = f2_mul(t2, iny);
+        f32x2 dgg = 0ull, dgp = 0ull;
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                t1 += q.mg[c][k];
-                t2 += q.mp[c][k];
-                ta += q.sgg[c][k];
-                tc += q.sgp[c][k];
-            }
-            const float iny = INT ? kInvW : inv_count(ny);
-            const float mu = t1 * iny, nu = t2 * iny;
-            float dgg = 0.f, dgp = 0.f;
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const float dg = INT ? q.mg[c][k] - mu : q.vr[k] * (q.mg[c][k] - mu);
-                dgg = fmaf(dg, dg, dgg);
-                dgp = fmaf(dg, q.mp[c][k] - nu, dgp);
-            }
-            const float nxf = INT ? (float)W : (float)ln.nx[c];
-            const float inn = INT ? kInvW2 : inv_count(ln.nx[c] * ny);
-            const float var = fmaf(nxf, dgg, ta) * inn;
-            const float cov = fmaf(nxf, dgp, tc) * inn;
-            const float ive = rcp_approx(var + eps);
-            A[c] = cov * ive;
-            b[c] = fmaf(-A[c], mu, nu);
-            if (stats != nullptr && ln.out[c] && ce >= s.y0 && ce < s.y0 + s.seg)
-                stats[(size_t)ce * s.w + xa + c] = make_float4(mu, nu, ive, A[c]);
-            if (!s.mean && ln.out[c] && ce >= s.y0 && ce < s.y0 + s.seg)
-                coef[(size_t)ce * s.w + xa + c] = make_float2(A[c], b[c]);  // no box mean: A_l, b_l
+        for (int k = 0; k < W; ++k) {
+            f32x2 dg = f2_sub(q.mg[k], mu);
+            if (!INT) dg = f2_mul(q.vr[k], dg);
+            dgg = f2_fma(dg, dg, dgg);
+            dgp = f2_fma(dg, f2_sub(q.mp[k], nu), dgp);
+        }
+        const f32x2 nxf = INT ? f2_splat((float)W) : ln.nx;
+        const f32x2 inn = INT ? f2_splat(kInvW2)
+                              : f2_pack(inv_count(ln.nx_i[0] * ny), inv_count(ln.nx_i[1] * ny));
+        const f32x2 var = f2_mul(f2_fma(nxf, dgg, ta), inn);
+        const f32x2 cov = f2_mul(f2_fma(nxf, dgp, tc), inn);
+        float v0, v1;
+        f2_unpack(f2_add(var, eps2), v0, v1);
+        const f32x2 ive = f2_pack(rcp_approx(v0), rcp_approx(v1));
+        A2 = f2_mul(cov, ive);
+        // b = nu - A mu, as fma(-A, mu, nu)
+        b2 = f2_fma(A2 ^ 0x8000000080000000ull, mu, nu);
+        if (!INT) {  // columns outside the image hold A = b = 0
+            A2 = f2_mul(A2, ln.xin2);
+            b2 = f2_mul(b2, ln.xin2);
+        }
+        const bool seg_row = ce >= s.y0 && ce < s.y0 + s.seg;
+        if (stats != nullptr && seg_row) {
+            float mu0, mu1, nu0, nu1, i0, i1, a0, a1;
+            f2_unpack(mu, mu0, mu1);
+            f2_unpack(nu, nu0, nu1);
+            f2_unpack(ive, i0, i1);
+            f2_unpack(A2, a0, a1);
+            if (ln.out[0]) stats[(size_t)ce * s.w + xa] = make_float4(mu0, nu0, i0, a0);
+            if (ln.out[1]) stats[(size_t)ce * s.w + xa + 1] = make_float4(mu1, nu1, i1, a1);
+        }
+        if (!s.mean && seg_row) {  // no box mean: A_l, b_l are the coefficients
+            float a0, a1, bb0, bb1;
+            f2_unpack(A2, a0, a1);
+            f2_unpack(b2, bb0, bb1);
+            if (ln.out[0]) coef[(size_t)ce * s.w + xa] = make_float2(a0, bb0);
+            if (ln.out[1]) coef[(size_t)ce * s.w + xa + 1] = make_float2(a1, bb1);
         }
     }
+    A_out = A2;
+    b_out = b2;
+}
+
+// Where stage B puts (Abar, bbar) of output row co, column x: the plane's
+// coefficient array (row pitch w).
+struct CoefOut {
+    float2* __restrict__ coef;
+    int w;
+    __device__ __forceinline__ void put(int co, int x, float2 v) const { coef[(size_t)co * w + x] = v; }
+};
+
+// Stage B for input row e (ring slot U): A2, b2 are stage A's result for it.
+template <int R, bool INT, class Out = CoefOut>
+__device__ __forceinline__ void strip2_k1_stage_b(Strip2Ring<R>& q, const Strip2Lane<R>& ln, int U, int e,
+                                                  int e_first, int xa, const Out& dst, const StripGeom& s,
+                                                  f32x2 A2, f32x2 b2) {
+    constexpr int W = 2 * R + 1;
+    constexpr float kInvW2 = 1.f / (float)(W * W);
+    const int lane = threadIdx.x & 31;
     if (!s.mean) return;
+    const int ce = e - R;
     // ---- level 2: horizontal box sums of A, b per column; vertical sum over the ring
     {
-        float TA[2 * R + 2], TB[2 * R + 2];
-        strip2_taps<R>(A[0], A[1], TA);
-        strip2_taps<R>(b[0], b[1], TB);
+        float a0, a1, bb0, bb1;
+        f2_unpack(A2, a0, a1);
+        f2_unpack(b2, bb0, bb1);
+        f32x2 QA[W], QB[W];
+        strip2_pairs<R>(a0, a1, QA);
+        strip2_pairs<R>(bb0, bb1, QB);
+        f32x2 sa = QA[0], sb = QB[0];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            float sa = 0.f, sb = 0.f;
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                sa += TA[c + k];
-                sb += TB[c + k];
-            }
-            q.ha[c][U] = sa;
-            q.hb[c][U] = sb;
+        for (int k = 1; k < W; ++k) {
+            sa = f2_add(sa, QA[k]);
+            sb = f2_add(sb, QB[k]);
         }
+        q.ha[U] = sa;
+        q.hb[U] = sb;
     }
     const int co = ce - R;  // output row; level 2 holds window rows co - R .. co + R
-    const bool row_out = INT || (co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
+    // (interior periods include the segment's first periods, whose rows only fill the rings)
+    const bool row_out = INT ? e - e_first >= 4 * R
+                             : (co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
     if (row_out) {
         const int nyo = INT ? W : min(co + R, s.h - 1) - max(co - R, 0) + 1;
-        float2 o[2];
+        f32x2 sa = q.ha[0], sb = q.hb[0];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            float sa = 0.f, sb = 0.f;
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                sa += q.ha[c][k];
-                sb += q.hb[c][k];
-            }
-            const float inn = INT ? kInvW2 : inv_count(ln.nx[c] * nyo);
-            o[c] = make_float2(sa * inn, sb * inn);
+        for (int k = 1; k < W; ++k) {
+            sa = f2_add(sa, q.ha[k]);
+            sb = f2_add(sb, q.hb[k]);
         }
-        float2* dst = coef + (size_t)co * s.w + xa;
+        const f32x2 inn = INT ? f2_splat(kInvW2)
+                              : f2_pack(inv_count(ln.nx_i[0] * nyo), inv_count(ln.nx_i[1] * nyo));
+        float oa0, oa1, ob0, ob1;
+        f2_unpack(f2_mul(sa, inn), oa0, oa1);
+        f2_unpack(f2_mul(sb, inn), ob0, ob1);
         const bool w0 = INT ? (lane >= R && lane < 32 - R) : ln.out[0];
         const bool w1 = INT ? (lane >= R && lane < 32 - R) : ln.out[1];
-        if (w0) dst[0] = o[0];
-        if (w1) dst[1] = o[1];
+        if (w0) dst.put(co, xa, make_float2(oa0, ob0));
+        if (w1) dst.put(co, xa + 1, make_float2(oa1, ob1));
     }
 }
 
 template <typename TG, typename TP, int R>
 __device__ __forceinline__ void strip2_ring_init(Strip2Ring<R>& q) {
 #pragma unroll
-    for (int k = 0; k < 2 * R + 1; ++k) {
-        q.vr[k] = 0.f;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) q.mg[c][k] = q.mp[c][k] = q.sgg[c][k] = q.sgp[c][k] = q.ha[c][k] = q.hb[c][k] = 0.f;
-    }
+    for (int k = 0; k < 2 * R + 1; ++k) q.vr[k] = q.mg[k] = q.mp[k] = q.sgg[k] = q.sgp[k] = q.ha[k] = q.hb[k] = 0ull;
 }
 
 // Strip geometry: x0 = strip (64 - 4R) - 2R, lane columns xa = x0 + 2 lane.
 __host__ __device__ constexpr int strip2_out_cols(int R) { return 64 - 4 * R; }
+
+// One ring period of the walk (rows base .. base + W - 1 with values gv, pv).
+// Stage B's results go to `out` when given (the fused forward's shared-memory
+// rows), else to the plane's coefficient array.
+template <int R, bool INT, class Out = CoefOut>
+__device__ __forceinline__ void strip2_k1_period(Strip2Ring<R>& q, const Strip2Lane<R>& ln,
+                                                 const float (&gv)[2][2 * R + 1], const float (&pv)[2][2 * R + 1],
+                                                 int base, int e_first, int e_last, int xa, float2* __restrict__ coef,
+                                                 float4* __restrict__ stats, const StripGeom& s, f32x2 eps2,
+                                                 const Out* out = nullptr) {
+    constexpr int W = 2 * R + 1;
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        const int e = base + u;
+        if (!INT && e >= e_last) break;  // uniform across the warp
+        f32x2 A, b;
+        strip2_k1_stage_a<R, INT>(q, ln, u, gv[0][u], gv[1][u], pv[0][u], pv[1][u], e, e_first, xa, coef, stats,
+                                  s, eps2, A, b);
+        if constexpr (std::is_same<Out, CoefOut>::value)
+            strip2_k1_stage_b<R, INT>(q, ln, u, e, e_first, xa, CoefOut{coef, s.w}, s, A, b);
+        else
+            strip2_k1_stage_b<R, INT>(q, ln, u, e, e_first, xa, *out, s, A, b);
+    }
+}
 
 // K1 for one strip segment, rows loaded one ring period ahead.
 template <typename TG, typename TP, int R>
 __device__ void coef_strip2(const TG* __restrict__ G, const TP* __restrict__ P, float2* __restrict__ coef,
                             const StripGeom& s, float eps, float4* __restrict__ stats = nullptr) {
     constexpr int W = 2 * R + 1;
+    const f32x2 eps2 = f2_splat(eps);
     const int xa = s.x0 + 2 * (int)(threadIdx.x & 31);
     const Strip2Lane<R> ln = strip2_lane<R>(xa, s.w);
     const bool cols_int = s.x0 >= 0 && s.x0 + 64 <= s.w;
@@ -236,21 +314,11 @@ __device__ void coef_strip2(const TG* __restrict__ G, const TP* __restrict__ P, 
                 pv[c][u] = pn[c][u];
             }
         if (base + W < e_last) load(base + W);  // next period in flight while this one computes
-        const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W <= s.h &&
-                             base + W <= e_last;
-        if (row_int) {
-#pragma unroll
-            for (int u = 0; u < W; ++u)
-                strip2_k1_row<R, true>(q, ln, u, gv[0][u], gv[1][u], pv[0][u], pv[1][u], base + u, e_first, xa, coef,
-                                       stats, s, eps);
-        } else {
-#pragma unroll
-            for (int u = 0; u < W; ++u) {
-                if (base + u >= e_last) break;  // uniform across the warp
-                strip2_k1_row<R, false>(q, ln, u, gv[0][u], gv[1][u], pv[0][u], pv[1][u], base + u, e_first, xa,
-                                        coef, stats, s, eps);
-            }
-        }
+        const bool row_int = cols_int && base >= 3 * R && base + W <= s.h && base + W <= e_last;
+        if (row_int)
+            strip2_k1_period<R, true>(q, ln, gv, pv, base, e_first, e_last, xa, coef, stats, s, eps2);
+        else
+            strip2_k1_period<R, false>(q, ln, gv, pv, base, e_first, e_last, xa, coef, stats, s, eps2);
     }
 }
 
@@ -282,6 +350,7 @@ __device__ void coef_strip2_tma(const TmaPair* maps, int plane, float2* __restri
     const int xg = floor_to(s.x0, UG), xp = floor_to(s.x0, UP);
     const int og = s.x0 - xg + 2 * lane, op = s.x0 - xp + 2 * lane;
     const uint32_t ring_s = smem_u32(ring), bar_s = smem_u32(bars);
+    const f32x2 eps2 = f2_splat(eps);
     auto issue = [&](int m) {  // lane 0: block m into slot m % NS
         const int slot = m % NS;
         const uint32_t bar = bar_s + 8u * slot, dst = ring_s + (uint32_t)(slot * SLOT);
@@ -327,21 +396,11 @@ __device__ void coef_strip2_tma(const TmaPair* maps, int plane, float2* __restri
                 }
             }
             if (base >= e_last) continue;  // uniform
-            const bool row_int = cols_int && base >= 3 * R && base - e_first >= 4 * R && base + W <= s.h &&
-                                 base + W <= e_last;
-            if (row_int) {
-#pragma unroll
-                for (int u = 0; u < W; ++u)
-                    strip2_k1_row<R, true>(q, ln, u, gv[0][u], gv[1][u], pv[0][u], pv[1][u], base + u, e_first, xa,
-                                           coef, stats, s, eps);
-            } else {
-#pragma unroll
-                for (int u = 0; u < W; ++u) {
-                    if (base + u >= e_last) break;  // uniform across the warp
-                    strip2_k1_row<R, false>(q, ln, u, gv[0][u], gv[1][u], pv[0][u], pv[1][u], base + u, e_first,
-                                            xa, coef, stats, s, eps);
-                }
-            }
+            const bool row_int = cols_int && base >= 3 * R && base + W <= s.h && base + W <= e_last;
+            if (row_int)
+                strip2_k1_period<R, true>(q, ln, gv, pv, base, e_first, e_last, xa, coef, stats, s, eps2);
+            else
+                strip2_k1_period<R, false>(q, ln, gv, pv, base, e_first, e_last, xa, coef, stats, s, eps2);
         }
     }
     if (!ok) {
