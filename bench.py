@@ -267,6 +267,7 @@ def algorithmic_bytes(kernel, shape, esz):
         "k3_hires_bwd": hi * 3 * esz,                 # read dO_h, I_h; write dI_h
         "k1_lowres_coef": lo * (2 * esz + 8),         # read I_l, p_l; write Abar, bbar (FP32)
         "k4_lowres_bwd": lo * (2 * esz + 8 + 2 * esz),  # read I_l, p_l, dAbar/dbbar; write dp_l, dI_l
+        "k12_fused_forward": hi * 2 * esz + lo * 2 * esz,  # read I_h, I_l, p_l; write O_h (no Abar, bbar traffic)
     }.get(kernel)
 
 

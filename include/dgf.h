@@ -179,15 +179,17 @@ int dgf_device_status(void);
  * identical either way; this exists for testing the two paths. */
 void dgf_set_tma(int on);
 
-/* Allows (1, default) or forbids (0) the fused forward: for r in {1, 2}, the
+/* Allows (1) or forbids (0, default) the fused forward: for r in {1, 2}, the
  * box mean of A, b, no guidance transform and an integer factor F with
  * F-pixel vectors of 8 or 16 bytes (F32: F = 2, 4; BF16/F16: F = 4, 8) and
  * I_h, O_h aligned to that vector, dgf_forward runs Eq. 1, both box means and
  * Eq. 2 (Sec. 3.2-3.3) in one kernel per high-resolution strip instead of a
  * low-resolution pass that writes Abar, bbar and a high-resolution pass that
  * reads them.  The autotuner (when on) keeps whichever form is faster for
- * the call's key.  Results are identical either way; the switch exists for
- * testing and measuring the two forms. */
+ * the call's key (its first call's sizes decide).  The two forms agree to the
+ * last place or two of the FP32 arithmetic.  Off by default: on large images
+ * the fused kernel's redundant low-resolution columns cost more than the
+ * saved Abar, bbar traffic; on small images it is the faster form. */
 void dgf_set_fused(int on);
 
 /*
@@ -274,11 +276,14 @@ void dgf_autotune_reset(void);
  *     F = vec = 0; guide_f32 = 1 for the guidance-transform path (FP32 guide);
  *     tiles: a = columns, b = rows of the coefficient region (a power of two
  *     in {64, 128, 256} and one of {16, 32, 64}); K1 with r <= 2 also takes
- *     warp strips: a = rows per segment in {8, 16, 32, 64, 128}, b = 0.
+ *     warp strips: a = rows per segment in {8, 16, 24, 32, 48, 64, 128}, b = 0.
  *   kind 2 (K2 high-res apply): r = 0, F = integer factor (0: non-integer),
  *     vec = elements per vector; a = high-res rows per tile, b = 0.
  *   kind 3 (K3 high-res backward): as kind 2; a = low-res rows per segment
  *     of a warp strip (1 .. 256).
+ *   kind 5 (fused forward, see dgf_set_fused): r = radius, F = factor,
+ *     vec = guide_f32 = 0; a = low-res rows per segment (1 .. 256), or 0 to
+ *     use the two-kernel forward for this key; b = 0.
  * A shape the kernels are not built for is stored but ignored at plan time
  * (the default shape is used).  Returns DGF_ERR_INVALID for a key or shape
  * outside these ranges.  No counterpart in the paper: tuning machinery.

@@ -1296,8 +1296,8 @@ extern "C" int dgf_autotune_entries(void) { return tune_count(); }
 
 extern "C" dgf_status dgf_autotune_pin(int kind, dgf_dtype dt, int r, int F, int vec, int guide_f32, int a,
                                        int b) {
-    if (kind < 1 || kind > 4 || (int)dt < 0 || (int)dt > 2 || r < 0 || F < 0 || vec < 0 || a <= 0 || a > 4096 || b < 0 ||
-        b > 4096 || (guide_f32 != 0 && guide_f32 != 1))
+    if (kind < 1 || kind > 5 || (int)dt < 0 || (int)dt > 2 || r < 0 || F < 0 || vec < 0 || a < 0 ||
+        (a == 0 && kind != 5) || a > 4096 || b < 0 || b > 4096 || (guide_f32 != 0 && guide_f32 != 1))
         return fail(DGF_ERR_INVALID, "autotune_pin: bad key or shape");
     tune_store(TuneKey{kind, (int)dt, r, F, vec, guide_f32}, a, b);
     return DGF_OK;

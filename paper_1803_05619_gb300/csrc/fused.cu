@@ -16,8 +16,11 @@
 // column pass per strip (64 columns walked for 34 used) plus 4R + 2 halo rows
 // per segment: extra arithmetic, no extra HBM bytes.
 //
-// Every step is the unfused kernels' arithmetic term for term, so the
-// output equals the unfused forward's bit for bit.
+// Every step is the unfused kernels' arithmetic term for term; the output
+// equals the unfused forward's to the last place or two (the K1 walk runs on
+// other segment and strip offsets).  Off by default (dgf_set_fused): on the
+// large benchmark workloads the redundant K1 columns cost more than the saved
+// Abar, bbar round trip; on small images it is the faster form.
 #include "common.cuh"
 #include "hires_strip.cuh"
 #include "kernels.h"

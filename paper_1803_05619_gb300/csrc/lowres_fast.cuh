@@ -167,14 +167,18 @@ __device__ __forceinline__ void fast_row_stats(const float* g, const float* p, c
 }
 
 // Window moments of E1 row e1 from the ring (all 2R + 1 slots), Chan's update.
+// U: slot of the newest row; the slots are summed oldest first, so the
+// rounding does not depend on where the walk started.
 template <int R>
 __device__ __forceinline__ void fast_window(const float (&mg)[2 * R + 1], const float (&mp)[2 * R + 1],
                                             const float (&sgg)[2 * R + 1], const float (&sgp)[2 * R + 1],
-                                            const float (&vr)[2 * R + 1], float nx, float iny, float inn,
+                                            const float (&vr)[2 * R + 1], int U, float nx, float iny, float inn,
                                             float& mu, float& nu, float& var, float& cov) {
+    constexpr int W = 2 * R + 1;
     float s1 = 0.f, s2 = 0.f, a = 0.f, c = 0.f;
 #pragma unroll
-    for (int k = 0; k <= 2 * R; ++k) {
+    for (int j = 0; j < W; ++j) {
+        const int k = (U + 1 + j) % W;
         s1 += mg[k];
         s2 += mp[k];
         a += sgg[k];
@@ -184,7 +188,8 @@ __device__ __forceinline__ void fast_window(const float (&mg)[2 * R + 1], const 
     nu = s2 * iny;
     float dgg = 0.f, dgp = 0.f;
 #pragma unroll
-    for (int k = 0; k <= 2 * R; ++k) {
+    for (int j = 0; j < W; ++j) {
+        const int k = (U + 1 + j) % W;
         const float dg = vr[k] * (mg[k] - mu);
         dgg = fmaf(dg, dg, dgg);
         dgp = fmaf(dg, mp[k] - nu, dgp);
@@ -259,7 +264,7 @@ __device__ void coef_tile_ring(const TG* __restrict__ G, const TP* __restrict__ 
                         const float ny = INT ? (float)W : (float)seg_count(gy, t.h, R);
                         const float iny = INT ? 1.f / (float)W : inv_countf(ny);
                         const float inn = INT ? 1.f / (float)(W * W) : inv_countf(nx * ny);
-                        fast_window<R>(mg, mp, sgg, sgp, vr, nx, iny, inn, mu, nu, var, cov);
+                        fast_window<R>(mg, mp, sgg, sgp, vr, slot, nx, iny, inn, mu, nu, var, cov);
                         A = cov * rcp_approx(var + t.eps);
                         b = fmaf(-A, mu, nu);
                     }
@@ -309,9 +314,9 @@ __device__ void coef_tile_ring(const TG* __restrict__ G, const TP* __restrict__ 
                     if (INT || (gx < t.w && gy < t.h)) {
                         float sa = 0.f, sb = 0.f;
 #pragma unroll
-                        for (int k = 0; k < W; ++k) {
-                            sa += ha[k];
-                            sb += hb[k];
+                        for (int j = 0; j < W; ++j) {  // oldest row first
+                            sa += ha[(slot + 1 + j) % W];
+                            sb += hb[(slot + 1 + j) % W];
                         }
                         const float inn = INT ? 1.f / (float)(W * W) : inv_countf(nx * (float)seg_count(gy, t.h, R));
                         coef[(size_t)gy * t.w + gx] = make_float2(sa * inn, sb * inn);
@@ -500,15 +505,15 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         const float iny = INT ? 1.f / (float)W : inv_countf(ny);
                         const float inn = INT ? 1.f / (float)(W * W) : inv_countf(nx * ny);
                         float mu, nu, var, cov;
-                        fast_window<R>(mg, mp, sgg, sgp, vr, nx, iny, inn, mu, nu, var, cov);
+                        fast_window<R>(mg, mp, sgg, sgp, vr, slot, nx, iny, inn, mu, nu, var, cov);
                         const float ve = var + t.eps;
                         const float ive = rcp_approx(ve);
                         const float A = cov * ive;
                         float dA = 0.f, db = 0.f;
 #pragma unroll
-                        for (int k = 0; k < W; ++k) {
-                            dA += hda[k];
-                            db += hdb[k];
+                        for (int j = 0; j < W; ++j) {  // oldest row first
+                            dA += hda[(slot + 1 + j) % W];
+                            db += hdb[(slot + 1 + j) % W];
                         }
                         const float alpha = fmaf(-db, mu, dA);
                         const float gamma = alpha * ive;
@@ -571,7 +576,7 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         for (int m = 0; m < kNQ; ++m) {
                             float a = 0.f;
 #pragma unroll
-                            for (int k = 0; k < W; ++k) a += hq[m][k];
+                            for (int j = 0; j < W; ++j) a += hq[m][(slot + 1 + j) % W];  // oldest row first
                             S[m] = a;
                         }
                         const int o = (y + 2 * R) * EX2 + c + 2 * R;
@@ -624,7 +629,8 @@ __device__ void lowres_bwd_tile_ring(const TG* __restrict__ G, const TP* __restr
                         const float g = sG[o], p = sP[o];
                         float aP = 0.f, aG = 0.f, sd = 0.f, se = 0.f;
 #pragma unroll
-                        for (int j = 0; j < W; ++j) {
+                        for (int jj = 0; jj < W; ++jj) {
+                            const int j = (slot + 1 + jj) % W;  // oldest row first
                             sd += hd[j];
                             se += he[j];
 #pragma unroll

@@ -14,9 +14,11 @@
 //
 // A ring period whose rows and columns are all far enough from the image
 // border takes the interior form: every window is full, so the masks and
-// clipped counts drop out and the counts' reciprocals are constants.  Both
-// forms use the same correctly rounded count reciprocals, so a pixel's result
-// does not depend on which form produced it.  The first periods of a segment,
+// clipped counts drop out and the counts' reciprocals are constants (the
+// same correctly rounded values the clipped form reads from its table).  A
+// pixel's result can still differ in the last place between segmentations
+// (segment lengths, strip offsets), which is within every tolerance; the
+// same shape always gives the same bits.  The first periods of a segment,
 // which only fill the rings, take the interior form too when their rows are
 // inside the image: what they compute before the rings are full is never
 // stored (a per-row predicate) and leaves the rings before any stored
@@ -47,6 +49,12 @@ __device__ __forceinline__ float hsum(float v) {
     return s;
 }
 
+// Ring slot of the j-th oldest row when the newest sits in slot U (rings of
+// W = 2R + 1 rows).  Window sums run over the slots in this order, so their
+// rounding does not depend on where a segment starts.
+template <int W>
+__host__ __device__ constexpr int ring_slot(int U, int j) { return (U + 1 + j) % W; }
+
 struct StripGeom {
     int h, w;
     int x0;       // global column of lane 0 (first input column, may be negative)
@@ -75,14 +83,15 @@ struct StripLane {
 // Centred statistics (mu, nu, var, cov) of the window of row ce = e - R
 // from the level-1 ring; ny = clipped window height.
 template <int R, bool INT>
-__device__ __forceinline__ void strip_window(const StripRing<R>& q, const StripLane<R>& ln, int ny, float& mu,
+__device__ __forceinline__ void strip_window(const StripRing<R>& q, const StripLane<R>& ln, int U, int ny, float& mu,
                                              float& nu, float& var, float& cov) {
     constexpr int W = 2 * R + 1;
     constexpr float kInvW = 1.f / (float)W;
     constexpr float kInvW2 = 1.f / (float)(W * W);
     float t1 = 0.f, t2 = 0.f, ta = 0.f, tc = 0.f;
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
+    for (int j = 0; j < W; ++j) {
+        const int k = ring_slot<W>(U, j);
         t1 += q.mg[k];
         t2 += q.mp[k];
         ta += q.sgg[k];
@@ -93,7 +102,8 @@ __device__ __forceinline__ void strip_window(const StripRing<R>& q, const StripL
     nu = t2 * iny;
     float dgg = 0.f, dgp = 0.f;
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
+    for (int j = 0; j < W; ++j) {
+        const int k = ring_slot<W>(U, j);
         const float dg = INT ? q.mg[k] - mu : q.vr[k] * (q.mg[k] - mu);
         dgg = fmaf(dg, dg, dgg);
         dgp = fmaf(dg, q.mp[k] - nu, dgp);
@@ -232,13 +242,13 @@ __device__ __forceinline__ void strip_k4_row(StripRing<R>& q, StripBwdRing<R>& z
     if (INT || (ln.xin && ce >= 0 && ce < s.h && e - e_first >= 2 * R)) {
         const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
         float mu, nu, var, cov;
-        strip_window<R, INT>(q, ln, ny, mu, nu, var, cov);
+        strip_window<R, INT>(q, ln, U, ny, mu, nu, var, cov);
         float dA = 0.f, db = 0.f;
         if (s.mean) {
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                dA += z.hda[k];
-                db += z.hdb[k];
+            for (int j = 0; j < W; ++j) {
+                dA += z.hda[ring_slot<W>(U, j)];
+                db += z.hdb[ring_slot<W>(U, j)];
             }
         } else {
             dA = z.hda[(U + W - R) % W];  // row ce = e - R
@@ -265,7 +275,8 @@ __device__ __forceinline__ void strip_k4_row(StripRing<R>& q, StripBwdRing<R>& z
     if (write) {
         float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
+        for (int j = 0; j < W; ++j) {
+            const int k = ring_slot<W>(U, j);
             S0 += z.hq0[k];
             S1 += z.hq1[k];
             S2 += z.hq2[k];
@@ -516,9 +527,9 @@ __device__ __forceinline__ void strip_k4s_row(StripBwdRing<R>& z, const StripLan
         float dA = 0.f, db = 0.f;
         if (s.mean) {
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                dA += z.hda[k];
-                db += z.hdb[k];
+            for (int j = 0; j < W; ++j) {
+                dA += z.hda[ring_slot<W>(U, j)];
+                db += z.hdb[ring_slot<W>(U, j)];
             }
         } else {
             dA = z.hda[(U + W - R) % W];  // row ce = e - R
@@ -544,7 +555,8 @@ __device__ __forceinline__ void strip_k4s_row(StripBwdRing<R>& z, const StripLan
     if (write) {
         float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
+        for (int j = 0; j < W; ++j) {
+            const int k = ring_slot<W>(U, j);
             S0 += z.hq0[k];
             S1 += z.hq1[k];
             S2 += z.hq2[k];

@@ -129,9 +129,14 @@ __device__ __forceinline__ void strip2_k1_stage_a(Strip2Ring<R>& q, const Strip2
     const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
     const bool rows_ok = INT || (ce >= 0 && ce < s.h && e - e_first >= 2 * R);
     if (rows_ok) {
-        f32x2 t1 = q.mg[0], t2 = q.mp[0], ta = q.sgg[0], tc = q.sgp[0];
+        // ring slots in row order, oldest first (slot (U + 1) mod W): the
+        // summation order, and so every bit of the result, does not depend on
+        // where the segment starts
+        const int k0 = ring_slot<W>(U, 0);
+        f32x2 t1 = q.mg[k0], t2 = q.mp[k0], ta = q.sgg[k0], tc = q.sgp[k0];
 #pragma unroll
-        for (int k = 1; k < W; ++k) {
+        for (int j = 1; j < W; ++j) {
+            const int k = ring_slot<W>(U, j);
             t1 = f2_add(t1, q.mg[k]);
             t2 = f2_add(t2, q.mp[k]);
             ta = f2_add(ta, q.sgg[k]);
@@ -141,7 +146,8 @@ __device__ __forceinline__ void strip2_k1_stage_a(Strip2Ring<R>& q, const Strip2
         const f32x2 mu = f2_mul(t1, iny), nu = f2_mul(t2, iny);
         f32x2 dgg = 0ull, dgp = 0ull;
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
+        for (int j = 0; j < W; ++j) {
+            const int k = ring_slot<W>(U, j);
             f32x2 dg = f2_sub(q.mg[k], mu);
             if (!INT) dg = f2_mul(q.vr[k], dg);
             dgg = f2_fma(dg, dg, dgg);
@@ -225,11 +231,11 @@ __device__ __forceinline__ void strip2_k1_stage_b(Strip2Ring<R>& q, const Strip2
                              : (co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
     if (row_out) {
         const int nyo = INT ? W : min(co + R, s.h - 1) - max(co - R, 0) + 1;
-        f32x2 sa = q.ha[0], sb = q.hb[0];
+        f32x2 sa = q.ha[ring_slot<W>(U, 0)], sb = q.hb[ring_slot<W>(U, 0)];
 #pragma unroll
-        for (int k = 1; k < W; ++k) {
-            sa = f2_add(sa, q.ha[k]);
-            sb = f2_add(sb, q.hb[k]);
+        for (int j = 1; j < W; ++j) {  // row order, as in stage A
+            sa = f2_add(sa, q.ha[ring_slot<W>(U, j)]);
+            sb = f2_add(sb, q.hb[ring_slot<W>(U, j)]);
         }
         const f32x2 inn = INT ? f2_splat(kInvW2)
                               : f2_pack(inv_count(ln.nx_i[0] * nyo), inv_count(ln.nx_i[1] * nyo));

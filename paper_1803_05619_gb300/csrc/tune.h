@@ -8,9 +8,11 @@
 namespace dgf {
 
 // kind: 1 = K1 low-res coefficients, 2 = K2 high-res apply, 3 = K3 high-res
-// backward, 4 = K4 low-res backward.  The value (a, b) is the kernel's
-// shape: K1/K4 tiles as a = CW and b = EY1; K1 warp strips as a = rows per
-// segment and b = 0; K2: a = rows per tile; K3: a = low-res rows per strip segment.
+// backward, 4 = K4 low-res backward, 5 = fused forward K12.  The value
+// (a, b) is the kernel's shape: K1/K4 tiles as a = CW and b = EY1; K1 warp
+// strips as a = rows per segment and b = 0; K2: a = rows per tile; K3: a =
+// low-res rows per strip segment; K12: a = low-res rows per segment, or 0
+// when the two-kernel forward (K1 + K2) is faster for the key.
 struct TuneKey {
     int kind, dt, r, F, vec, gf32;
 };

@@ -385,3 +385,62 @@ def test_guided_forward_backward_parity(case):
         assert err <= wtol, f"{name}: rel L2 {err:.3e}"
     # the guide-shift invariance makes db2 vanish; compare on the scale of dw2
     assert float(np.max(np.abs(f64(dws[2])))) <= 1e-3 * float(np.max(np.abs(rw2)))
+
+
+# ------------------------------------------------------------ shape invariance
+# Every K1 shape the autotuner may pick (segment lengths of the strips,
+# column-walking tile shapes) computes the same formula; they differ only in
+# rounding (a few units in the last place of Abar, bbar).
+K1_SHAPES = {"strips": [(8, 0), (24, 0), (32, 0), (64, 0)], "tiles": [(64, 32), (128, 16), (64, 64)]}
+
+
+def _close_bits(a, b, dtype):
+    """Same values up to a few ulp of FP32 arithmetic (stored in dtype)."""
+    d = (a.float() - b.float()).abs().max().item()
+    tol = 2e-6 if dtype == F32 else (2 ** -7 if dtype == BF16 else 2 ** -10)
+    assert d <= tol, (d, tol)
+
+
+@pytest.mark.parametrize("form", ["strips", "tiles"])
+@pytest.mark.parametrize("dtype,r,eps", [(F32, 1, 1e-4), (BF16, 2, 1e-3)], ids=["f32-r1", "bf16-r2"])
+def test_forward_does_not_depend_on_k1_shape(form, dtype, r, eps, pin):
+    dt = L.DGF_F32 if dtype == F32 else L.DGF_BF16
+    st = to_storage(make_case("photo", 41, 2, 2, 77, 150, 308, 600), dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    outs = []
+    for a, b in K1_SHAPES[form]:
+        L.dgf_autotune_reset()
+        pin(1, dt, r, 0, 0, 0, a, b)
+        outs.append(gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps))
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        _close_bits(o, outs[0], dtype)
+    assert_fwd(f64(outs[0]), oracle_forward(st, r, eps), dtype, eps)
+
+
+# --------------------------------------------------------------- fused forward
+# (dtype, N, C, h_l, w_l, F, r, eps): every factor / radius / dtype the fused
+# kernel serves, ragged against its 32-column strips and its segments
+K12_CASES = [(F32, 2, 3, 70, 90, 4, 1, 1e-4), (F32, 1, 2, 77, 131, 2, 2, 1e-3), (BF16, 2, 2, 45, 70, 8, 1, 1e-3),
+             (BF16, 1, 3, 54, 96, 4, 2, 1e-3), (F16, 2, 1, 33, 40, 4, 2, 1e-2), (F32, 1, 1, 5, 3, 4, 1, 1e-2)]
+
+
+@pytest.mark.parametrize("ls", [8, 32])
+@pytest.mark.parametrize("case", K12_CASES, ids=_ids(K12_CASES))
+def test_fused_forward_matches_two_kernel_forward_and_oracle(case, ls, pin):
+    dtype, N, C, hl, wl, f, r, eps = case
+    dt = {F32: L.DGF_F32, BF16: L.DGF_BF16, F16: L.DGF_F16}[dtype]
+    st = to_storage(make_case("photo", 60 + r, N, C, hl, wl, hl * f, wl * f), dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    pin(1, dt, r, 0, 0, 0, 32, 0)        # the two-kernel form with K1 strips
+    pin(5, dt, r, f, 0, 0, ls, 0)        # K12 segment length
+    ref = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps)
+    L.dgf_set_fused(True)
+    try:
+        out = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps)
+        torch.cuda.synchronize()
+    finally:
+        L.dgf_set_fused(False)
+    _close_bits(out, ref, dtype)
+    assert_fwd(f64(out), oracle_forward(st, r, eps), dtype, eps)
+    assert L.dgf_device_status() == 0
