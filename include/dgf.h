@@ -192,6 +192,20 @@ void dgf_set_tma(int on);
  * saved Abar, bbar traffic; on small images it is the faster form. */
 void dgf_set_fused(int on);
 
+/* Allows (1) or forbids (0, default) the plane-group pipeline of dgf_forward
+ * and dgf_backward (no guidance transform, integer factor for the backward):
+ * a call with 2 or more planes splits them into 2 or 3 groups and runs the
+ * low-resolution kernels on a library stream of the greatest priority and
+ * the high-resolution kernels on a second library stream, both forked from
+ * and joined back to the caller's stream with events, so the low-resolution
+ * pass of one group overlaps the high-resolution pass of another.  The call
+ * stays asynchronous and stream-ordered on `stream` (and capturable in a
+ * CUDA graph).  Results are identical either way.  Off by default: on
+ * GB300 the low-resolution kernels are bound by the latency of their row
+ * walks, so a group's pass takes nearly as long as the whole call's, and the
+ * overlap does not pay for it.  No counterpart in the paper. */
+void dgf_set_pipeline(int on);
+
 /*
  * Options of the _opt entry points (NULL = the defaults of dgf_forward and
  * dgf_backward).

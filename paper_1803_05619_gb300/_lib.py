@@ -74,6 +74,7 @@ _SIGS = {
     "dgf_device_status": (_I, []),
     "dgf_set_tma": (None, [_I]),
     "dgf_set_fused": (None, [_I]),
+    "dgf_set_pipeline": (None, [_I]),
     "dgf_shutdown": (None, []),
     "dgf_autotune": (None, [_I]),
     "dgf_autotune_entries": (_I, []),
@@ -185,6 +186,10 @@ def dgf_set_tma(on: bool) -> None:
 
 def dgf_set_fused(on: bool) -> None:
     lib().dgf_set_fused(1 if on else 0)
+
+
+def dgf_set_pipeline(on: bool) -> None:
+    lib().dgf_set_pipeline(1 if on else 0)
 
 
 def dgf_shutdown() -> None:

@@ -658,6 +658,17 @@ static void tune_k3(dgf_dtype dt, const float2* coef, const void* R, const void*
     }
 }
 
+// Whether the autotuner's table already holds the backward's shapes for this key.
+static bool tune_has_low(dgf_dtype dt, int r, const Plan&) {
+    int a, b;
+    if (!low_fast_radius(r)) return true;
+    return tune_lookup(TuneKey{1, (int)dt, r, 0, 0, 0}, a, b) && tune_lookup(TuneKey{4, (int)dt, r, 0, 0, 0}, a, b);
+}
+static bool tune_has_k3(dgf_dtype dt, const Plan& p) {
+    int a, b;
+    return !p.k3_fast || tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b);
+}
+
 // The fused forward against the two-kernel forward with its tuned shapes:
 // records the fastest K12 segment length, or 0 when K1 + K2 win.
 static void tune_k12(dgf_dtype dt, const void* G, const void* P, float2* coef, const void* in, void* out,
@@ -797,6 +808,82 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
 using namespace dgf;
 
 // ====================================================================== ABI
+namespace dgf {
+// ----------------------------------------------------- plane-group pipeline
+// One call's planes in G groups on two streams forked from the caller's: the
+// low-resolution kernels (latency-bound, few warps per SM) on a stream of the
+// greatest priority, the high-resolution kernels (HBM-bound) on a stream of
+// the least, ordered per group by events.  The low-res pass of one group then
+// runs while the high-res pass of another streams from HBM, instead of
+// between them.  Every kernel sees exactly the planes and pointers it would
+// in the one-stream order, so the results are the same bits.  Off by default
+// (dgf_set_pipeline): the low-res walks are latency-bound, so a group's pass
+// is nearly as long as the whole call's and the overlap does not pay.
+constexpr int kPipeGroups = 3;
+struct PipePool {
+    int dev = -1;
+    cudaStream_t lo = nullptr, hi = nullptr;
+    cudaEvent_t fork = nullptr, join_lo = nullptr, join_hi = nullptr;
+    cudaEvent_t k1[kPipeGroups] = {}, k3[kPipeGroups] = {};
+};
+static std::mutex g_pipe_mu;
+static std::map<int, PipePool> g_pipe_pools;
+static bool g_pipeline = false;
+
+static cudaError_t pipe_pool(PipePool*& out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    PipePool& p = g_pipe_pools[dev];
+    if (p.dev < 0) {
+        int least = 0, greatest = 0;
+        if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithPriority(&p.lo, cudaStreamNonBlocking, greatest)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithPriority(&p.hi, cudaStreamNonBlocking, least)) != cudaSuccess) return e;
+        cudaEvent_t* evs[] = {&p.fork, &p.join_lo, &p.join_hi};
+        for (cudaEvent_t* ev : evs)
+            if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+        for (int g = 0; g < kPipeGroups; ++g) {
+            if ((e = cudaEventCreateWithFlags(&p.k1[g], cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&p.k3[g], cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        p.dev = dev;
+    }
+    out = &p;
+    return cudaSuccess;
+}
+
+// groups for a call of `planes` planes (1: no pipeline)
+static int pipe_groups(int planes) {
+    if (!g_pipeline) return 1;
+    return planes >= 6 ? 3 : (planes >= 2 ? 2 : 1);
+}
+
+static cudaError_t pipe_fork(PipePool& p, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaEventRecord(p.fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(p.lo, p.fork, 0)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(p.hi, p.fork, 0);
+}
+
+static cudaError_t pipe_join(PipePool& p, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaEventRecord(p.join_lo, p.lo)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(p.join_hi, p.hi)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, p.join_lo, 0)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, p.join_hi, 0);
+}
+
+template <typename Ptr>
+static Ptr* plane_off(Ptr* base, size_t elems) {
+    return base == nullptr ? nullptr : base + elems;
+}
+static const void* byte_off(const void* base, size_t bytes) {
+    return base == nullptr ? nullptr : static_cast<const char*>(base) + bytes;
+}
+static void* byte_off(void* base, size_t bytes) { return base == nullptr ? nullptr : static_cast<char*>(base) + bytes; }
+}  // namespace dgf
+
 extern "C" {
 
 size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt, const dgf_guide* g) {
@@ -837,14 +924,48 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
             if (e != cudaSuccess) return cuda_fail(e, "k12");
             return DGF_OK;
         }
-        if (tuning) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
-        e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
-        if (e != cudaSuccess) return cuda_fail(e, "k1");
-        if (tuning) tune_k2(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, s, p);
-        e = L.run("k2_hires_apply", [&] {
-            return launch_k2_plan(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, p, p.k2_strip ? p.k2_ls : p.k2_th, s);
-        });
-        if (e != cudaSuccess) return cuda_fail(e, "k2");
+        if (tuning) {
+            tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
+            tune_k2(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, s, p);
+        }
+        const int G = pipe_groups(planes);
+        if (G == 1) {
+            e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+            if (e != cudaSuccess) return cuda_fail(e, "k1");
+            e = L.run("k2_hires_apply", [&] {
+                return launch_k2_plan(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, p, p.k2_strip ? p.k2_ls : p.k2_th,
+                                      s);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "k2");
+            return DGF_OK;
+        }
+        // K1 of every group on the low-res stream, K2 of group g on the
+        // high-res stream once K1 of group g is done
+        std::lock_guard<std::mutex> lk(g_pipe_mu);
+        PipePool* pp = nullptr;
+        if ((e = pipe_pool(pp)) != cudaSuccess) return cuda_fail(e, "pipeline streams");
+        if ((e = pipe_fork(*pp, s)) != cudaSuccess) return cuda_fail(e, "pipeline fork");
+        const size_t es = esize(dt), lw = (size_t)h_l * w_l, hw = (size_t)h * w;
+        {
+            Launcher Llo(pp->lo), Lhi(pp->hi);
+            for (int gi = 0; gi < G; ++gi) {
+                const int p0 = gi * planes / G, n = (gi + 1) * planes / G - p0;
+                e = run_k1(Llo, dt, false, byte_off(I_l, p0 * lw * es), byte_off(p_l, p0 * lw * es), coef + p0 * lw, n,
+                           h_l, w_l, r, eps, p, pp->lo);
+                if (e != cudaSuccess) return cuda_fail(e, "k1");
+                if ((e = cudaEventRecord(pp->k1[gi], pp->lo)) != cudaSuccess) return cuda_fail(e, "pipeline event");
+            }
+            for (int gi = 0; gi < G; ++gi) {
+                const int p0 = gi * planes / G, n = (gi + 1) * planes / G - p0;
+                if ((e = cudaStreamWaitEvent(pp->hi, pp->k1[gi], 0)) != cudaSuccess) return cuda_fail(e, "pipeline wait");
+                e = Lhi.run("k2_hires_apply", [&] {
+                    return launch_k2_plan(dt, coef + p0 * lw, byte_off(I_h, p0 * hw * es), byte_off(O_h, p0 * hw * es), n,
+                                          h_l, w_l, h, w, p, p.k2_strip ? p.k2_ls : p.k2_th, pp->hi);
+                });
+                if (e != cudaSuccess) return cuda_fail(e, "k2");
+            }
+        }
+        if ((e = pipe_join(*pp, s)) != cudaSuccess) return cuda_fail(e, "pipeline join");
         return DGF_OK;
     }
     float* G_l = reinterpret_cast<float*>(ws + lay.gl);
@@ -916,6 +1037,75 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
     return DGF_OK;
 }
 
+// backward_plain with the planes in groups on the two pipeline streams:
+// K1 (low-res stream) -> K3 (high-res stream) -> K4 (low-res stream) per group.
+static dgf_status backward_pipelined(dgf_dtype dt, const void* dO_h, const void* p_l, const void* I_l,
+                                     const void* I_h, void* dp_l, void* dI_l, void* dI_h, int planes, int h_l, int w_l,
+                                     int h, int w, int r, float eps, const Plan& p, char* ws, const Layout& lay,
+                                     cudaStream_t s, int G) {
+    float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
+    float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
+    const bool need_k4 = dp_l != nullptr || dI_l != nullptr;
+    const bool use_stats = need_k4 && p.k1.fast == 2 && p.k4.fast == 2;
+    float4* stats = use_stats ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr;
+    const bool need_k1 = dI_h != nullptr || use_stats;
+    const size_t es = esize(dt), lw = (size_t)h_l * w_l, hw = (size_t)h * w;
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    PipePool* pp = nullptr;
+    cudaError_t e;
+    if ((e = pipe_pool(pp)) != cudaSuccess) return cuda_fail(e, "pipeline streams");
+    if ((e = pipe_fork(*pp, s)) != cudaSuccess) return cuda_fail(e, "pipeline fork");
+    {
+        Launcher Llo(pp->lo), Lhi(pp->hi);
+        auto grp = [&](int gi, int& p0, int& n) {
+            p0 = gi * planes / G;
+            n = (gi + 1) * planes / G - p0;
+        };
+        for (int gi = 0; gi < G; ++gi) {
+            int p0, n;
+            grp(gi, p0, n);
+            if (need_k1) {
+                e = run_k1(Llo, dt, false, byte_off(I_l, p0 * lw * es), byte_off(p_l, p0 * lw * es), coef + p0 * lw, n,
+                           h_l, w_l, r, eps, p, pp->lo, plane_off(stats, p0 * lw));
+                if (e != cudaSuccess) return cuda_fail(e, "k1");
+            }
+            if ((e = cudaEventRecord(pp->k1[gi], pp->lo)) != cudaSuccess) return cuda_fail(e, "pipeline event");
+        }
+        for (int gi = 0; gi < G; ++gi) {
+            int p0, n;
+            grp(gi, p0, n);
+            if ((e = cudaStreamWaitEvent(pp->hi, pp->k1[gi], 0)) != cudaSuccess) return cuda_fail(e, "pipeline wait");
+            const void* dO = byte_off(dO_h, p0 * hw * es);
+            const void* G_h = byte_off(I_h, p0 * hw * es);
+            void* dG_h = byte_off(dI_h, p0 * hw * es);
+            K3Maps maps;
+            const bool tma = make_k3_maps(maps, dO, G_h, dt, n, h, w, p.vec, p.F);
+            e = Lhi.run("k3_hires_bwd", [&] {
+                return launch_k3(dt, coef + p0 * lw, dO, G_h, dG_h, dcoef + p0 * lw, n, h_l, w_l, h, w, p.vec, p.F,
+                                 p.k3_lth, tma ? &maps : nullptr, status_ptr(), pp->hi);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "k3");
+            if ((e = cudaEventRecord(pp->k3[gi], pp->hi)) != cudaSuccess) return cuda_fail(e, "pipeline event");
+        }
+        if (need_k4) {
+            const float4* k4_stats = p.k4.fast == 2 ? stats : nullptr;
+            for (int gi = 0; gi < G; ++gi) {
+                int p0, n;
+                grp(gi, p0, n);
+                if ((e = cudaStreamWaitEvent(pp->lo, pp->k3[gi], 0)) != cudaSuccess) return cuda_fail(e, "pipeline wait");
+                e = Llo.run("k4_lowres_bwd", [&] {
+                    return run_k4(dt, false, byte_off(I_l, p0 * lw * es), byte_off(p_l, p0 * lw * es), dcoef + p0 * lw,
+                                  byte_off(dp_l, p0 * lw * es), byte_off(dI_l, p0 * lw * es), n, h_l, w_l, r, eps,
+                                  p.k4, pp->lo, plane_off(k4_stats, p0 * lw));
+                });
+                if (e != cudaSuccess) return cuda_fail(e, "k4");
+            }
+        }
+    }
+    if ((e = pipe_join(*pp, s)) != cudaSuccess) return cuda_fail(e, "pipeline join");
+    return DGF_OK;
+}
+
 static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l,
                                 void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w,
                                 int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
@@ -948,8 +1138,13 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
     if (g == nullptr) {
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
         const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab;
-        return backward_plain(L, dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws,
-                              lay, s, tuning);
+        const int G = p.k3_fast ? pipe_groups(planes) : 1;
+        const bool tuned = !tuning || (tune_has_low(dt, r, p) && tune_has_k3(dt, p));
+        if (G == 1 || !tuned)  // the first call of a key tunes (one stream), later calls pipeline
+            return backward_plain(L, dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws,
+                                  lay, s, tuning);
+        return backward_pipelined(dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws, lay,
+                                  s, G);
     }
     // with the guidance transform
     float* G_l = reinterpret_cast<float*>(ws + lay.gl);
@@ -1290,6 +1485,8 @@ extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
 
 extern "C" void dgf_set_fused(int on) { g_fused_allowed = on != 0; }
 
+extern "C" void dgf_set_pipeline(int on) { g_pipeline = on != 0; }
+
 extern "C" void dgf_autotune(int on) { tune_set_enabled(on != 0); }
 
 extern "C" int dgf_autotune_entries(void) { return tune_count(); }
@@ -1306,6 +1503,22 @@ extern "C" dgf_status dgf_autotune_pin(int kind, dgf_dtype dt, int r, int F, int
 extern "C" void dgf_autotune_reset(void) { tune_clear(); }
 
 extern "C" void dgf_shutdown(void) {
+    {
+        std::lock_guard<std::mutex> lk(g_pipe_mu);
+        for (auto& kv : g_pipe_pools) {
+            PipePool& p = kv.second;
+            if (p.lo) cudaStreamDestroy(p.lo);
+            if (p.hi) cudaStreamDestroy(p.hi);
+            cudaEvent_t evs[] = {p.fork, p.join_lo, p.join_hi};
+            for (cudaEvent_t ev : evs)
+                if (ev) cudaEventDestroy(ev);
+            for (int g = 0; g < kPipeGroups; ++g) {
+                if (p.k1[g]) cudaEventDestroy(p.k1[g]);
+                if (p.k3[g]) cudaEventDestroy(p.k3[g]);
+            }
+        }
+        g_pipe_pools.clear();
+    }
     {
         std::lock_guard<std::mutex> lk(g_bwd_mu);
         for (auto& kv : g_bwd_pools) {

@@ -165,6 +165,29 @@ __global__ void __launch_bounds__(kK4StripWarps * 32)
                                           dP ? dP + plane * hw : nullptr, dG ? dG + plane * hw : nullptr, s);
 }
 
+// Two-column K4 from saved statistics: warp w owns strip (w % nstrip) of the
+// two-column geometry (64 - 4R outputs) of segment (w / nstrip) % nseg.
+template <typename TG, typename TP, typename TD, int R>
+__global__ void __launch_bounds__(kK4StripWarps * 32)
+    k4_lowres_bwd_strip2_stats(const TG* __restrict__ G, const TP* __restrict__ P, const float2* __restrict__ dcoef,
+                               const float4* __restrict__ stats, TP* __restrict__ dP, TD* __restrict__ dG, int h,
+                               int w, int seg, int nstrip, int nseg, int planes, int mean) {
+    const int gw = blockIdx.x * kK4StripWarps + (threadIdx.x >> 5);
+    if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
+    const int strip = gw % nstrip, rest = gw / nstrip;
+    const int sg = rest % nseg, plane = rest / nseg;
+    StripGeom s;
+    s.h = h;
+    s.w = w;
+    s.x0 = strip * strip2_out_cols(R) - 2 * R;
+    s.y0 = sg * seg;
+    s.seg = seg;
+    s.mean = mean;
+    const size_t hw = (size_t)h * w;
+    lowres_bwd_strip2_stats<TG, TP, TD, R>(G + plane * hw, P + plane * hw, dcoef + plane * hw, stats + plane * hw,
+                                           dP ? dP + plane * hw : nullptr, dG ? dG + plane * hw : nullptr, s);
+}
+
 template <typename K>
 static inline cudaError_t fast_prep(K kernel, size_t smem) {
     if (smem > 48 * 1024)
@@ -230,9 +253,12 @@ static cudaError_t k4f_go(const void* G, const void* P, const float2* dcoef, voi
             const long long warps = (long long)nstrip * nseg * planes;
             const int ctas = (int)((warps + kK4StripWarps - 1) / kK4StripWarps);
             if (stats != nullptr) {
-                k4_lowres_bwd_strip_stats<TG, TP, TD, R><<<ctas, kK4StripWarps * 32, 0, s>>>(
+                const int nstrip2 = (w + strip2_out_cols(R) - 1) / strip2_out_cols(R);
+                const long long warps2 = (long long)nstrip2 * nseg * planes;
+                const int ctas2 = (int)((warps2 + kK4StripWarps - 1) / kK4StripWarps);
+                k4_lowres_bwd_strip2_stats<TG, TP, TD, R><<<ctas2, kK4StripWarps * 32, 0, s>>>(
                     static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef, stats, static_cast<TP*>(dP),
-                    static_cast<TD*>(dG), h, w, seg, nstrip, nseg, planes, c.mean);
+                    static_cast<TD*>(dG), h, w, seg, nstrip2, nseg, planes, c.mean);
                 return cudaGetLastError();
             }
             if (tma != nullptr && tma->enabled) {

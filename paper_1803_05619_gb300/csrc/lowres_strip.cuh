@@ -1,5 +1,6 @@
 // Low-resolution stage as warp-strip column walks (radius R = 1 or 2): the
-// shared pieces and the K4 strips (one column per lane); K1 strips hold two
+// shared pieces and the K4 strips that recompute the window statistics (one
+// column per lane); K1 and the K4 that reads saved statistics hold two
 // columns per lane (lowres_strip2.cuh).
 //
 // One warp owns a strip of 32 consecutive low-res columns and walks down a

@@ -1,4 +1,5 @@
-// K1 as warp strips with two low-res columns per lane (radius R = 1 or 2).
+// K1, and K4 from saved window statistics, as warp strips with two low-res
+// columns per lane (radius R = 1 or 2).
 //
 // Same walk as the one-column strips of lowres_strip.cuh (a warp walks down a
 // segment of rows; register rings of the last 2R + 1 rows; exactly centred
@@ -325,6 +326,234 @@ __device__ void coef_strip2(const TG* __restrict__ G, const TP* __restrict__ P, 
             strip2_k1_period<R, true>(q, ln, gv, pv, base, e_first, e_last, xa, coef, stats, s, eps2);
         else
             strip2_k1_period<R, false>(q, ln, gv, pv, base, e_first, e_last, xa, coef, stats, s, eps2);
+    }
+}
+
+// ------------------------------------------------------------------- K4
+// K4 from the window statistics the backward K1 pass saved, two columns per
+// lane in paired FP32 (the strip geometry of the two-column K1: 64 - 4R
+// outputs per strip, R lanes of halo per side for the two horizontal box
+// levels).  Per window m (row ce, columns xa, xa + 1): dA = f_mu^T(d Abar),
+// db = f_mu^T(d bbar) as box sums of d Abar / N, d bbar / N, then
+//   gamma = (dA - db mu) / (var + eps),  beta = -gamma A,
+// and four quantities whose box sums over the windows containing a pixel give
+//   dP = G' S0 + S2,   dG = P' S0 + 2 G' S1 - S3
+// (S0 = sum gamma / N, S1 = sum beta / N, S2 = sum (db - gamma mu') / N,
+// S3 = sum (gamma nu' + 2 beta mu' + db A) / N; primes are shifts by the
+// strip's constant, the mean of the segment's first output row).
+template <int R>
+struct Strip2BwdRing {
+    static constexpr int W = 2 * R + 1;
+    f32x2 hda[W], hdb[W];                  // row box sums of d Abar / N, d bbar / N (input rows)
+    f32x2 hq0[W], hq1[W], hq2[W], hq3[W];  // row box sums of the four window quantities (window rows)
+    f32x2 rg[W], rp[W];                    // raw G, P of the input rows
+};
+
+__device__ __forceinline__ f32x2 f2_neg(f32x2 v) { return v ^ 0x8000000080000000ull; }
+
+// Row box sum of the pair (v0, v1)'s horizontal windows.
+template <int R>
+__device__ __forceinline__ f32x2 strip2_hsum(float v0, float v1) {
+    constexpr int W = 2 * R + 1;
+    f32x2 Q[W];
+    strip2_pairs<R>(v0, v1, Q);
+    f32x2 s = Q[0];
+#pragma unroll
+    for (int k = 1; k < W; ++k) s = f2_add(s, Q[k]);
+    return s;
+}
+
+template <typename TP, typename TD, int R, bool INT>
+__device__ __forceinline__ void strip2_k4s_row(Strip2BwdRing<R>& z, const Strip2Lane<R>& ln, int U, float g0,
+                                               float g1, float p0, float p1, float2 d0, float2 d1, float4 st0,
+                                               float4 st1, int e, int e_first, int xa, TP* __restrict__ dP,
+                                               TD* __restrict__ dG, const StripGeom& s, f32x2 KG, f32x2 KP) {
+    constexpr int W = 2 * R + 1;
+    constexpr float kInvW2 = 1.f / (float)(W * W);
+    const int lane = threadIdx.x & 31;
+    const bool row_in = e >= 0 && e < s.h;
+    z.rg[U] = f2_pack(g0, g1);
+    z.rp[U] = f2_pack(p0, p1);
+    if (s.mean) {
+        // d Abar / N, d bbar / N at (e, xa), (e, xa + 1); zero outside the image
+        float i0 = kInvW2, i1 = kInvW2;
+        if (!INT) {
+            const int ny = min(e + R, s.h - 1) - max(e - R, 0) + 1;
+            i0 = (ln.xin[0] && row_in) ? inv_count(ln.nx_i[0] * ny) : 0.f;
+            i1 = (ln.xin[1] && row_in) ? inv_count(ln.nx_i[1] * ny) : 0.f;
+        }
+        z.hda[U] = strip2_hsum<R>(d0.x * i0, d1.x * i1);
+        z.hdb[U] = strip2_hsum<R>(d0.y * i0, d1.y * i1);
+    } else {
+        // no box mean of A, b: the window's own d Abar, d bbar (row e, read at row e - R below)
+        z.hda[U] = f2_pack(d0.x, d1.x);
+        z.hdb[U] = f2_pack(d0.y, d1.y);
+    }
+    const int ce = e - R;
+    f32x2 q0 = 0ull, q1 = 0ull, q2 = 0ull, q3 = 0ull;
+    if (INT || (ce >= 0 && ce < s.h && e - e_first >= 2 * R)) {
+        const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
+        f32x2 dA, db;
+        if (s.mean) {
+            dA = z.hda[ring_slot<W>(U, 0)];
+            db = z.hdb[ring_slot<W>(U, 0)];
+#pragma unroll
+            for (int j = 1; j < W; ++j) {  // oldest row first
+                dA = f2_add(dA, z.hda[ring_slot<W>(U, j)]);
+                db = f2_add(db, z.hdb[ring_slot<W>(U, j)]);
+            }
+        } else {
+            dA = z.hda[(U + W - R) % W];  // row ce = e - R
+            db = z.hdb[(U + W - R) % W];
+        }
+        const f32x2 mu = f2_pack(st0.x, st1.x), nu = f2_pack(st0.y, st1.y);
+        const f32x2 ive = f2_pack(st0.z, st1.z), A = f2_pack(st0.w, st1.w);
+        const f32x2 gamma = f2_mul(f2_fma(f2_neg(db), mu, dA), ive);
+        const f32x2 beta = f2_mul(f2_neg(gamma), A);
+        const f32x2 inn = INT ? f2_splat(kInvW2)
+                              : f2_pack(inv_count(ln.nx_i[0] * ny), inv_count(ln.nx_i[1] * ny));
+        const f32x2 mus = f2_sub(mu, KG), nus = f2_sub(nu, KP);
+        q0 = f2_mul(gamma, inn);
+        q1 = f2_mul(beta, inn);
+        q2 = f2_mul(f2_fma(f2_neg(gamma), mus, db), inn);
+        q3 = f2_mul(f2_fma(gamma, nus, f2_fma(f2_add(beta, beta), mus, f2_mul(db, A))), inn);
+        if (!INT) {  // windows of columns outside the image contribute nothing
+            q0 = f2_mul(q0, ln.xin2);
+            q1 = f2_mul(q1, ln.xin2);
+            q2 = f2_mul(q2, ln.xin2);
+            q3 = f2_mul(q3, ln.xin2);
+        }
+    }
+    {
+        float a[2];
+        f2_unpack(q0, a[0], a[1]);
+        z.hq0[U] = strip2_hsum<R>(a[0], a[1]);
+        f2_unpack(q1, a[0], a[1]);
+        z.hq1[U] = strip2_hsum<R>(a[0], a[1]);
+        f2_unpack(q2, a[0], a[1]);
+        z.hq2[U] = strip2_hsum<R>(a[0], a[1]);
+        f2_unpack(q3, a[0], a[1]);
+        z.hq3[U] = strip2_hsum<R>(a[0], a[1]);
+    }
+    const int co = ce - R;
+    const bool rows = e - e_first >= 4 * R && (INT || (co >= s.y0 && co < s.y0 + s.seg && co < s.h));
+    const bool w0 = rows && (INT ? (lane >= R && lane < 32 - R) : ln.out[0]);
+    const bool w1 = rows && (INT ? (lane >= R && lane < 32 - R) : ln.out[1]);
+    if (w0 || w1) {
+        const int k0 = ring_slot<W>(U, 0);
+        f32x2 S0 = z.hq0[k0], S1 = z.hq1[k0], S2 = z.hq2[k0], S3 = z.hq3[k0];
+#pragma unroll
+        for (int j = 1; j < W; ++j) {  // oldest row first
+            const int k = ring_slot<W>(U, j);
+            S0 = f2_add(S0, z.hq0[k]);
+            S1 = f2_add(S1, z.hq1[k]);
+            S2 = f2_add(S2, z.hq2[k]);
+            S3 = f2_add(S3, z.hq3[k]);
+        }
+        const int V = ring_slot<W>(U, 0);  // row co = e - 2R, the oldest in the ring
+        const f32x2 g = f2_sub(z.rg[V], KG), p = f2_sub(z.rp[V], KP);
+        float vp0, vp1, vg0, vg1;
+        f2_unpack(f2_fma(g, S0, S2), vp0, vp1);
+        f2_unpack(f2_fma(p, S0, f2_fma(f2_add(g, g), S1, f2_neg(S3))), vg0, vg1);
+        const size_t o = (size_t)co * s.w + xa;
+        if (dP != nullptr) {
+            if (w0) dP[o] = from_f32<TP>(vp0);
+            if (w1) dP[o + 1] = from_f32<TP>(vp1);
+        }
+        if (dG != nullptr) {
+            if (w0) dG[o] = from_f32<TD>(vg0);
+            if (w1) dG[o + 1] = from_f32<TD>(vg1);
+        }
+    }
+}
+
+// K4 for one strip segment from saved statistics, rows loaded one ring period ahead.
+template <typename TG, typename TP, typename TD, int R>
+__device__ void lowres_bwd_strip2_stats(const TG* __restrict__ G, const TP* __restrict__ P,
+                                        const float2* __restrict__ dcoef, const float4* __restrict__ stats,
+                                        TP* __restrict__ dP, TD* __restrict__ dG, const StripGeom& s) {
+    constexpr int W = 2 * R + 1;
+    const int lane = threadIdx.x & 31;
+    const int xa = s.x0 + 2 * lane;
+    const Strip2Lane<R> ln = strip2_lane<R>(xa, s.w);
+    // interior: every lane's columns and their windows inside the image
+    const bool cols_int = s.x0 >= R && s.x0 + 64 + R <= s.w;
+    Strip2BwdRing<R> z;
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+        z.hda[k] = z.hdb[k] = z.hq0[k] = z.hq1[k] = z.hq2[k] = z.hq3[k] = z.rg[k] = z.rp[k] = 0ull;
+    const int e_first = s.y0 - 2 * R;
+    const int e_last = min(s.y0 + s.seg, s.h) + 2 * R;
+    float gn[2][W], pn[2][W];
+    float2 dn[2][W];
+    float4 sn[2][W];
+    auto load = [&](int base) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const int e = base + u, ce = e - R;
+            const bool row = e >= 0 && e < s.h && e < e_last;
+            const bool srow = ce >= 0 && ce < s.h;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const bool ok = row && ln.xin[c];
+                const size_t o = (size_t)e * s.w + xa + c;
+                gn[c][u] = ok ? to_f32<TG>(G[o]) : 0.f;
+                pn[c][u] = ok ? to_f32<TP>(P[o]) : 0.f;
+                dn[c][u] = ok ? dcoef[o] : make_float2(0.f, 0.f);
+                sn[c][u] = (srow && ln.xin[c]) ? stats[(size_t)ce * s.w + xa + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    };
+    load(e_first);
+    // shift: mean of row y0 (the last row of the first period) over the output columns
+    f32x2 KG, KP;
+    {
+        float sg = 0.f, sp = 0.f, cn = 0.f;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (ln.out[c]) {
+                sg += gn[c][2 * R];
+                sp += pn[c][2 * R];
+                cn += 1.f;
+            }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sg += __shfl_xor_sync(0xffffffffu, sg, off);
+            sp += __shfl_xor_sync(0xffffffffu, sp, off);
+            cn += __shfl_xor_sync(0xffffffffu, cn, off);
+        }
+        KG = f2_splat(cn > 0.f ? sg / cn : 0.f);
+        KP = f2_splat(cn > 0.f ? sp / cn : 0.f);
+    }
+    for (int base = e_first; base < e_last; base += W) {
+        float gv[2][W], pv[2][W];
+        float2 dv[2][W];
+        float4 sv[2][W];
+#pragma unroll
+        for (int u = 0; u < W; ++u)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                gv[c][u] = gn[c][u];
+                pv[c][u] = pn[c][u];
+                dv[c][u] = dn[c][u];
+                sv[c][u] = sn[c][u];
+            }
+        if (base + W < e_last) load(base + W);  // next period in flight while this one computes
+        const bool row_int = cols_int && base >= 3 * R && base + W + R <= s.h && base + W <= e_last;
+        if (row_int) {
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+                strip2_k4s_row<TP, TD, R, true>(z, ln, u, gv[0][u], gv[1][u], pv[0][u], pv[1][u], dv[0][u], dv[1][u],
+                                                sv[0][u], sv[1][u], base + u, e_first, xa, dP, dG, s, KG, KP);
+        } else {
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (base + u >= e_last) break;  // uniform across the warp
+                strip2_k4s_row<TP, TD, R, false>(z, ln, u, gv[0][u], gv[1][u], pv[0][u], pv[1][u], dv[0][u],
+                                                 dv[1][u], sv[0][u], sv[1][u], base + u, e_first, xa, dP, dG, s, KG,
+                                                 KP);
+            }
+        }
     }
 }
 

@@ -444,3 +444,26 @@ def test_fused_forward_matches_two_kernel_forward_and_oracle(case, ls, pin):
     _close_bits(out, ref, dtype)
     assert_fwd(f64(out), oracle_forward(st, r, eps), dtype, eps)
     assert L.dgf_device_status() == 0
+
+
+# ------------------------------------------------------- plane-group pipeline
+@pytest.mark.parametrize("dtype,r,planes", [(F32, 1, (2, 3)), (BF16, 2, (1, 2)), (F32, 2, (1, 7))],
+                         ids=["f32-r1-6", "bf16-r2-2", "f32-r2-7"])
+def test_plane_group_pipeline_gives_the_same_bits(dtype, r, planes):
+    N, C = planes
+    st = to_storage(make_case("photo", 70 + r, N, C, 45, 70, 180, 280), dtype)
+    R = synth.upstream_grad(71, st["I_h"].shape).to(dtype).cuda()
+    g = {k: v.cuda() for k, v in st.items()}
+    res = []
+    for on in (False, True, True):  # the first pipelined call may tune on one stream
+        L.dgf_set_pipeline(on)
+        try:
+            out = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, 1e-3)
+            grads = gf_backward(R, g["p_l"], g["I_l"], g["I_h"], r, 1e-3)[:3]
+            torch.cuda.synchronize()
+        finally:
+            L.dgf_set_pipeline(False)
+        res.append((out, *grads))
+    for a, b in zip(res[0], res[2]):
+        assert torch.equal(a, b)
+    assert L.dgf_device_status() == 0
