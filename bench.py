@@ -477,8 +477,10 @@ def main():
         "stand-in, tone-curve target, N(0,1) upstream gradient)",
         "config": {"workload": main_name, "step": "forward+backward", "N": N, "C": C, "h_l": h_l, "w_l": w_l,
                    "h": h, "w": w, "r": spec["r"], "eps": spec["eps"],
-                   "l2": "inputs larger than L2 (each high-res tensor %d MB > 129 MB)"
-                         % (N * C * h * w * g["I_h"].element_size() // 10**6),
+                   "l2": "no flush: a step streams %d MB of high-res tensors (I_h, O_h, dO_h, dI_h of %d MB "
+                         "each) through the 129 MB L2"
+                         % (4 * N * C * h * w * g["I_h"].element_size() // 10**6,
+                            N * C * h * w * g["I_h"].element_size() // 10**6),
                    "parallelism": f"images sharded over {ws} GPU(s), no collective"},
         "fwd": {"value": round(ws * pix / (fwd_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
                 "ms_per_step": round(fwd_ms, 5)},
