@@ -291,9 +291,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def ncu_traffic(kernel, workload, field="dram_bytes_per_launch"):
+    """A per-launch figure (DRAM bytes, warp-instructions) from the committed
+    ncu summary, if it was taken on the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(p))
@@ -302,7 +302,14 @@ def ncu_traffic(kernel, workload):
     e = d.get(workload, {}).get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get(field)
+
+
+# Instruction-issue peak of the low-res kernels (bound by issue and by the
+# latency of their row walks, not by HBM): 152 SMs x 4 schedulers x one
+# warp-instruction per cycle x 2070 MHz maximum SM clock.
+ISSUE_PEAK = 152 * 4 * 2.07e9
+ISSUE_BOUND = ("k1_lowres_coef", "k4_lowres_bwd")
 
 
 def roofline(step, spec, steps, warmup, workload):
@@ -332,12 +339,28 @@ def roofline(step, spec, steps, warmup, workload):
         per_call = ms / calls
         per[k] = {"us_per_call": round(per_call * 1e3, 2), "launches_per_call": round(n / calls, 2),
                   "share": round(ms / total, 4), "gbs": round(ab / (per_call * 1e-3) / 1e9, 1) if ab else None}
+    for k, v in per.items():
+        wi = ncu_traffic(k, workload, "warp_instructions_per_launch")
+        if wi is not None and k in ISSUE_BOUND:
+            # ncu's count is per launch of the one-stream call: the call's issue rate
+            v["issue_frac"] = round(wi / (v["us_per_call"] * 1e-6) / ISSUE_PEAK, 4)
     top = max(prof, key=lambda k: prof[k][0])
     ms, n = prof[top]
     per_call_s = ms / (steps * CALLS_PER_STEP.get(top, 1)) * 1e-3
     ab = algorithmic_bytes(top, step.shape, esz)
     peak, src = peaks()
     ach = ab / per_call_s / 1e9
+    wi = ncu_traffic(top, workload, "warp_instructions_per_launch")
+    if top in ISSUE_BOUND and wi is not None:
+        # a low-res kernel dominates: its bound is instruction issue, not HBM
+        ach_i = wi / per_call_s
+        return {"kernel": top, "bound": "issue", "achieved": round(ach_i / 1e9, 2), "peak": round(ISSUE_PEAK / 1e9, 2),
+                "unit": "G warp-instructions/s", "frac": round(ach_i / ISSUE_PEAK, 4),
+                "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp-instruction/cycle x 2070 MHz",
+                "warp_instructions": wi, "hbm_gbs": round(ach, 1), "hbm_frac_of_measured": round(ach / peak, 4),
+                "traffic": ncu_traffic(top, workload), "algorithmic_bytes": ab,
+                "us_per_call": round(per_call_s * 1e6, 2), "launches_per_call": per[top]["launches_per_call"],
+                "kernels": per}
     return {"kernel": top, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "peak_source": src,
             "frac_of_nominal_8TBs": round(ach / NOMINAL_HBM_GBS, 4),
