@@ -612,7 +612,7 @@ static void tune_k2(dgf_dtype dt, const float2* coef, const void* in, void* out,
     if (tune_lookup(key, a, b)) return;
     float best = 1e30f;
     int bt = p.k2_strip ? p.k2_ls : p.k2_th;
-    const std::initializer_list<int> strip_cand = {4, 8, 16, 32}, tile_cand = {8, 16, 32, 64};
+    const std::initializer_list<int> strip_cand = {4, 6, 8, 12, 16, 24, 32}, tile_cand = {8, 16, 32, 64};
     for (int th : p.k2_strip ? strip_cand : tile_cand) {
         if (!p.k2_strip && k2_smem_bytes(p.vec, p.F, h_l, h, w_l, w, th) > smem_limit()) continue;
         const float ms = time_launch(s, [&] {
@@ -642,7 +642,7 @@ static void tune_k3(dgf_dtype dt, const float2* coef, const void* R, const void*
     int bl = p.k3_lth;
     K3Maps maps;
     const bool tma = make_k3_maps(maps, R, G, dt, planes, h, w, p.vec, p.F);
-    for (int lth : {8, 16, 32, 64}) {
+    for (int lth : {8, 12, 16, 20, 24, 32, 48, 64}) {  // intermediate lengths let a grid fill whole waves
         const float ms = time_launch(s, [&] {
             return launch_k3(dt, coef, R, G, dG, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, lth,
                              tma ? &maps : nullptr, status_ptr(), s);
