@@ -257,10 +257,6 @@ def time_loop(fn, steps, warmup, ws, device, clock=None):
 
 
 # --------------------------------------------------------------- roofline
-# calls of each kernel per forward+backward step (K1 runs in both passes)
-CALLS_PER_STEP = {"k1_lowres_coef": 2}
-
-
 def algorithmic_bytes(kernel, shape, esz):
     """Minimum DRAM bytes one launch must move (inputs read once, outputs written once)."""
     N, C, h_l, w_l, h, w = shape
@@ -330,14 +326,13 @@ def roofline(step, spec, steps, warmup, workload):
     esz = 4 if spec["dtype"] == "f32" else 2
     total = sum(v[0] for v in prof.values())
     per = {}
-    # a call may launch a kernel once per plane group (the plane-group
-    # pipeline); its time per call is the sum over the groups, and its
-    # algorithmic bytes are those of the whole call
+    # one launch per call (the plane-group pipeline, which would launch a
+    # kernel once per group, is off here); a kernel's algorithmic bytes are
+    # those of one call
     for k, (ms, n) in prof.items():
         ab = algorithmic_bytes(k, step.shape, esz)
-        calls = steps * CALLS_PER_STEP.get(k, 1)
-        per_call = ms / calls
-        per[k] = {"us_per_call": round(per_call * 1e3, 2), "launches_per_call": round(n / calls, 2),
+        per_call = ms / max(n, 1)
+        per[k] = {"us_per_call": round(per_call * 1e3, 2), "launches_per_step": round(n / steps, 2),
                   "share": round(ms / total, 4), "gbs": round(ab / (per_call * 1e-3) / 1e9, 1) if ab else None}
     for k, v in per.items():
         wi = ncu_traffic(k, workload, "warp_instructions_per_launch")
@@ -346,7 +341,7 @@ def roofline(step, spec, steps, warmup, workload):
             v["issue_frac"] = round(wi / (v["us_per_call"] * 1e-6) / ISSUE_PEAK, 4)
     top = max(prof, key=lambda k: prof[k][0])
     ms, n = prof[top]
-    per_call_s = ms / (steps * CALLS_PER_STEP.get(top, 1)) * 1e-3
+    per_call_s = ms / max(n, 1) * 1e-3
     ab = algorithmic_bytes(top, step.shape, esz)
     peak, src = peaks()
     ach = ab / per_call_s / 1e9
@@ -359,13 +354,13 @@ def roofline(step, spec, steps, warmup, workload):
                 "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp-instruction/cycle x 2070 MHz",
                 "warp_instructions": wi, "hbm_gbs": round(ach, 1), "hbm_frac_of_measured": round(ach / peak, 4),
                 "traffic": ncu_traffic(top, workload), "algorithmic_bytes": ab,
-                "us_per_call": round(per_call_s * 1e6, 2), "launches_per_call": per[top]["launches_per_call"],
+                "us_per_call": round(per_call_s * 1e6, 2), "launches_per_step": per[top]["launches_per_step"],
                 "kernels": per}
     return {"kernel": top, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "peak_source": src,
             "frac_of_nominal_8TBs": round(ach / NOMINAL_HBM_GBS, 4),
             "traffic": ncu_traffic(top, workload), "algorithmic_bytes": ab,
-            "us_per_call": round(per_call_s * 1e6, 2), "launches_per_call": per[top]["launches_per_call"],
+            "us_per_call": round(per_call_s * 1e6, 2), "launches_per_step": per[top]["launches_per_step"],
             "kernels": per}
 
 

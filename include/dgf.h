@@ -179,17 +179,17 @@ int dgf_device_status(void);
  * identical either way; this exists for testing the two paths. */
 void dgf_set_tma(int on);
 
-/* Allows (1) or forbids (0, default) the fused forward: for r in {1, 2}, the
+/* Allows (1, default) or forbids (0) the fused forward: for r in {1, 2}, the
  * box mean of A, b, no guidance transform and an integer factor F with
  * F-pixel vectors of 8 or 16 bytes (F32: F = 2, 4; BF16/F16: F = 4, 8) and
  * I_h, O_h aligned to that vector, dgf_forward runs Eq. 1, both box means and
  * Eq. 2 (Sec. 3.2-3.3) in one kernel per high-resolution strip instead of a
  * low-resolution pass that writes Abar, bbar and a high-resolution pass that
  * reads them.  The autotuner (when on) keeps whichever form is faster for
- * the call's key (its first call's sizes decide).  The two forms agree to the
- * last place or two of the FP32 arithmetic.  Off by default: on large images
- * the fused kernel's redundant low-resolution columns cost more than the
- * saved Abar, bbar traffic; on small images it is the faster form. */
+ * the call's key (its first call's sizes decide); untuned, the fused form
+ * serves r = 1 (at r = 2 on large images its redundant low-resolution
+ * columns cost more than the saved Abar, bbar traffic).  The two forms give
+ * identical bits. */
 void dgf_set_fused(int on);
 
 /* Allows (1) or forbids (0, default) the plane-group pipeline of dgf_forward

@@ -193,7 +193,7 @@ struct Plan {
     int k12_ls = 32;       // K12: low-res rows per segment
 };
 
-static bool g_fused_allowed = false;
+static bool g_fused_allowed = true;
 
 static bool aligned_to(std::initializer_list<const void*> ptrs, int bytes) {
     for (const void* p : ptrs)
@@ -296,9 +296,13 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     // fused forward: plain guide, box mean of A, b, r in {1, 2}, a factor with
     // one low-res cell per lane; a table entry a = 0 means the tuner found
     // K1 + K2 faster for this key
+    // (the fused kernel's K1 part is the strip walk: it stands in for the
+    // strip K1 + K2 pair only, so a tile-form K1 keeps the two kernels)
     p.k12_ok = g_fused_allowed && !gf32 && mean_ab && p.F > 0 && k12_supported(dt, r, p.F) &&
-               aligned_to(hires_ptrs, k12_vec_bytes(dt, p.F));
-    p.k12 = p.k12_ok;
+               aligned_to(hires_ptrs, k12_vec_bytes(dt, p.F)) && p.k1.fast == 2;
+    // untuned default: fused at r = 1, where it measured faster than K1 + K2
+    // on large images too (at r = 2 its redundant K1 columns cost more)
+    p.k12 = p.k12_ok && r == 1;
     if (p.k12_ok && tune_lookup(TuneKey{5, (int)dt, r, p.F, 0, 0}, a, b) && a >= 0 && a <= 256) {
         p.k12 = a > 0;
         if (a > 0) p.k12_ls = a;
@@ -915,7 +919,10 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
             // shapes of the two-kernel forward first: K12 is timed against it
             tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
             tune_k2(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, s, p);
-            tune_k12(dt, I_l, p_l, coef, I_h, O_h, planes, h_l, w_l, h, w, r, eps, s, p);
+            if (p.k1.fast == 2)
+                tune_k12(dt, I_l, p_l, coef, I_h, O_h, planes, h_l, w_l, h, w, r, eps, s, p);
+            else
+                p.k12_ok = p.k12 = false;  // the tuner chose K1 tiles
         }
         if (p.k12) {
             e = L.run("k12_fused_forward", [&] {

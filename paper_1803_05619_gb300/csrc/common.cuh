@@ -24,10 +24,16 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // ------------------------------------------------------ paired FP32
-// Two values per instruction: Blackwell's paired FP32 arithmetic (PTX
-// add/sub/mul/fma.rn.f32x2 on a 64-bit register pair).  Each half is the
-// scalar IEEE operation with round-to-nearest, so a pair gives exactly the
-// two scalar results.
+// Two values per register pair (a 64-bit f32x2: low half, high half), as the
+// two-column strips hold their columns.  The arithmetic on a pair is two
+// scalar round-to-nearest operations through the __fadd_rn / __fmul_rn /
+// __fmaf_rn intrinsics, which the compiler never contracts or reassociates:
+// every bit of a result is fixed by the source, whatever the surrounding
+// code.  (Blackwell's paired add/mul/fma.rn.f32x2 instructions were measured
+// to round differently depending on the code around them, which made the
+// low-res results depend on the strip and segment shapes the autotuner
+// picks; they are kept for the guidance transform's 1x1 convolutions as
+// f2x_mul / f2x_fma, where no such shape dependence arises.)
 typedef unsigned long long f32x2;
 __device__ __forceinline__ f32x2 f2_pack(float a, float b) {
     f32x2 r;
@@ -39,21 +45,37 @@ __device__ __forceinline__ void f2_unpack(f32x2 v, float& a, float& b) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
 }
 __device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
+    float a0, a1, b0, b1;
+    f2_unpack(a, a0, a1);
+    f2_unpack(b, b0, b1);
+    return f2_pack(__fadd_rn(a0, b0), __fadd_rn(a1, b1));
 }
 __device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
+    float a0, a1, b0, b1;
+    f2_unpack(a, a0, a1);
+    f2_unpack(b, b0, b1);
+    return f2_pack(__fsub_rn(a0, b0), __fsub_rn(a1, b1));
 }
 __device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    float a0, a1, b0, b1;
+    f2_unpack(a, a0, a1);
+    f2_unpack(b, b0, b1);
+    return f2_pack(__fmul_rn(a0, b0), __fmul_rn(a1, b1));
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    float a0, a1, b0, b1, c0, c1;
+    f2_unpack(a, a0, a1);
+    f2_unpack(b, b0, b1);
+    f2_unpack(c, c0, c1);
+    return f2_pack(__fmaf_rn(a0, b0, c0), __fmaf_rn(a1, b1, c1));
+}
+// Blackwell's paired instructions (one instruction for both halves).
+__device__ __forceinline__ f32x2 f2x_mul(f32x2 a, f32x2 b) {
     f32x2 d;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+__device__ __forceinline__ f32x2 f2x_fma(f32x2 a, f32x2 b, f32x2 c) {
     f32x2 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;

@@ -16,11 +16,12 @@
 // column pass per strip (64 columns walked for 34 used) plus 4R + 2 halo rows
 // per segment: extra arithmetic, no extra HBM bytes.
 //
-// Every step is the unfused kernels' arithmetic term for term; the output
-// equals the unfused forward's to the last place or two (the K1 walk runs on
-// other segment and strip offsets).  Off by default (dgf_set_fused): on the
-// large benchmark workloads the redundant K1 columns cost more than the saved
-// Abar, bbar round trip; on small images it is the faster form.
+// Every step is the unfused kernels' arithmetic term for term (the K1 walk's
+// sums run in row order and its pair arithmetic through non-contracting
+// intrinsics, so other segment and strip offsets do not move a bit): the
+// output equals the two-kernel forward's bit for bit.  Untuned, it serves
+// r = 1; at r = 2 on large images the redundant K1 columns cost more than the
+// saved Abar, bbar round trip, and the autotuner keeps the faster form.
 #include "common.cuh"
 #include "hires_strip.cuh"
 #include "kernels.h"

@@ -61,13 +61,13 @@ __device__ __forceinline__ void guide_eval2(const float (&xa)[3], const float (&
     f32x2 g0 = bb[0], g1 = bb[1], g2 = bb[2];
 #pragma unroll
     for (int k = 0; k < kHid; ++k) {
-        const f32x2 z = f2_fma(w1[k * 3 + 2], x2, f2_fma(w1[k * 3 + 1], x1, f2_mul(w1[k * 3 + 0], x0)));
+        const f32x2 z = f2x_fma(w1[k * 3 + 2], x2, f2x_fma(w1[k * 3 + 1], x1, f2x_mul(w1[k * 3 + 0], x0)));
         float za, zb;
         f2_unpack(z, za, zb);
         const f32x2 hk = f2_pack(lrelu(za, slope), lrelu(zb, slope));
-        g0 = f2_fma(w2[0 * kHid + k], hk, g0);
-        g1 = f2_fma(w2[1 * kHid + k], hk, g1);
-        g2 = f2_fma(w2[2 * kHid + k], hk, g2);
+        g0 = f2x_fma(w2[0 * kHid + k], hk, g0);
+        g1 = f2x_fma(w2[1 * kHid + k], hk, g1);
+        g2 = f2x_fma(w2[2 * kHid + k], hk, g2);
     }
     f2_unpack(g0, ga[0], gb[0]);
     f2_unpack(g1, ga[1], gb[1]);

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kK4StripWarps * 32)
     k4_lowres_bwd_strip_tma(const __grid_constant__ TmaTriple maps, TP* __restrict__ dP, TD* __restrict__ dG, int h,
                             int w, float eps, int seg, int nstrip, int nseg, int planes, uint32_t* status, int mean) {
     extern __shared__ __align__(1024) unsigned char k4ring[];
-    constexpr int NS = StripTmaCfg<R>::NS, RB = StripTmaCfg<R>::RB;
+    constexpr int NS = StripTmaCfg<R>::NS4, RB = StripTmaCfg<R>::RB;
     constexpr int SLOT = strip_box_bytes(R, (int)sizeof(TG), RB) + strip_box_bytes(R, (int)sizeof(TP), RB) +
                          align128i(RB * 2 * (32 + 2) * 4);
     const int warp = threadIdx.x >> 5;

@@ -16,10 +16,8 @@
 // A ring period whose rows and columns are all far enough from the image
 // border takes the interior form: every window is full, so the masks and
 // clipped counts drop out and the counts' reciprocals are constants (the
-// same correctly rounded values the clipped form reads from its table).  A
-// pixel's result can still differ in the last place between segmentations
-// (segment lengths, strip offsets), which is within every tolerance; the
-// same shape always gives the same bits.  The first periods of a segment,
+// same correctly rounded values the clipped form reads from its table), so a
+// pixel's result does not depend on which form produced it.  The first periods of a segment,
 // which only fill the rings, take the interior form too when their rows are
 // inside the image: what they compute before the rings are full is never
 // stored (a per-row predicate) and leaves the rings before any stored
@@ -184,6 +182,9 @@ template <int R>
 struct StripTmaCfg {
     static constexpr int RB = R == 1 ? 6 : 10;  // rows per block (2 ring periods)
     static constexpr int NS = 4;                // slots per warp
+    // K4's slots also hold d Abar, d bbar; at R = 2 three slots keep a CTA's
+    // ring under 56 KB, so four CTAs (16 warps) share an SM
+    static constexpr int NS4 = R == 1 ? 4 : 3;
 };
 
 __host__ __device__ constexpr int strip_box_cols(int esize) { return 32 + 16 / esize; }
@@ -374,7 +375,7 @@ template <typename TG, typename TP, typename TD, int R>
 __device__ void lowres_bwd_strip_tma(const TmaTriple* maps, int plane, TP* __restrict__ dP, TD* __restrict__ dG,
                                      const StripGeom& s, float eps, unsigned char* ring, uint64_t* bars,
                                      uint32_t* status) {
-    constexpr int W = 2 * R + 1, RB = StripTmaCfg<R>::RB, NS = StripTmaCfg<R>::NS, NP = RB / W;
+    constexpr int W = 2 * R + 1, RB = StripTmaCfg<R>::RB, NS = StripTmaCfg<R>::NS4, NP = RB / W;
     constexpr int UG = 16 / (int)sizeof(TG), UP = 16 / (int)sizeof(TP);
     constexpr int BXG = 32 + UG, BXP = 32 + UP, BXD = 2 * (32 + 2);  // d: float pairs
     constexpr int BG = strip_box_bytes(R, (int)sizeof(TG), RB), BP = strip_box_bytes(R, (int)sizeof(TP), RB);
@@ -487,11 +488,11 @@ __device__ void lowres_bwd_strip_tma(const TmaTriple* maps, int plane, TP* __res
 // shared memory of one CTA of K4 strips staged by TMA (kK4StripWarps warps)
 template <typename TG, typename TP, int R>
 __host__ __device__ constexpr int k4_strip_tma_smem() {
-    return kK4StripWarps * StripTmaCfg<R>::NS *
+    return kK4StripWarps * StripTmaCfg<R>::NS4 *
                (strip_box_bytes(R, (int)sizeof(TG), StripTmaCfg<R>::RB) +
                 strip_box_bytes(R, (int)sizeof(TP), StripTmaCfg<R>::RB) +
                 align128i(StripTmaCfg<R>::RB * 2 * (32 + 2) * 4)) +
-           kK4StripWarps * StripTmaCfg<R>::NS * 8;
+           kK4StripWarps * StripTmaCfg<R>::NS4 * 8;
 }
 
 // K4 strip from saved window statistics: the backward K1 pass wrote

@@ -8,9 +8,10 @@
 // shuffles from each neighbouring lane, so the shuffles, loads and loop
 // overhead are shared by two outputs, and the halo is R lanes per side
 // (2R columns) out of 32: 64 - 4R outputs per strip instead of 32 - 4R.
-// The two columns run in lock step as the halves of paired FP32
-// instructions (f32x2): per column the arithmetic is the one-column
-// walk's, term for term, at one instruction per pair.
+// The two columns run in lock step as the halves of f32x2 register pairs
+// (common.cuh): per column the arithmetic is the one-column walk's, term for
+// term, through non-contracting round-to-nearest intrinsics, so a column's
+// bits do not depend on the strip or segment that computed it.
 #pragma once
 
 #include <type_traits>
