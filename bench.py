@@ -268,6 +268,7 @@ def algorithmic_bytes(kernel, shape, esz):
         "k1_lowres_coef": lo * (2 * esz + 8),         # read I_l, p_l; write Abar, bbar (FP32)
         "k4_lowres_bwd": lo * (2 * esz + 8 + 2 * esz),  # read I_l, p_l, dAbar/dbbar; write dp_l, dI_l
         "k12_fused_forward": hi * 2 * esz + lo * 2 * esz,  # read I_h, I_l, p_l; write O_h (no Abar, bbar traffic)
+        "k13_fused_backward": hi * 3 * esz + lo * 2 * esz,  # read dO_h, I_h, I_l, p_l; write dI_h
     }.get(kernel)
 
 

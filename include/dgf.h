@@ -179,17 +179,22 @@ int dgf_device_status(void);
  * identical either way; this exists for testing the two paths. */
 void dgf_set_tma(int on);
 
-/* Allows (1, default) or forbids (0) the fused forward: for r in {1, 2}, the
+/* Allows (1, default) or forbids (0) the fused forward and backward: for r in {1, 2}, the
  * box mean of A, b, no guidance transform and an integer factor F with
  * F-pixel vectors of 8 or 16 bytes (F32: F = 2, 4; BF16/F16: F = 4, 8) and
  * I_h, O_h aligned to that vector, dgf_forward runs Eq. 1, both box means and
  * Eq. 2 (Sec. 3.2-3.3) in one kernel per high-resolution strip instead of a
  * low-resolution pass that writes Abar, bbar and a high-resolution pass that
- * reads them.  The autotuner (when on) keeps whichever form is faster for
- * the call's key (its first call's sizes decide); untuned, the fused form
- * serves r = 1 (at r = 2 on large images its redundant low-resolution
- * columns cost more than the saved Abar, bbar traffic).  The two forms give
- * identical bits. */
+ * reads them; likewise dgf_backward runs the backward's Eq. 1 pass and the
+ * transposed upsampler (Algorithm 1's first two lines) in one kernel per
+ * high-resolution strip for F32 F = 4 and BF16/F16 F = 8 with 16-byte
+ * aligned dO_h, I_h, dI_h, writing the window statistics the low-resolution
+ * backward reads.  The autotuner (when on) keeps whichever form is faster for
+ * the call's key (its first call's sizes decide); untuned, the fused forms
+ * serve r = 1 (at r = 2 on large images their redundant low-resolution
+ * columns cost more than the saved Abar, bbar traffic).  The fused and
+ * two-kernel forms give identical bits.  Either form needs the strip form
+ * of the low-resolution pass (a pinned tile form keeps the two kernels). */
 void dgf_set_fused(int on);
 
 /* Allows (1) or forbids (0, default) the plane-group pipeline of dgf_forward
@@ -298,6 +303,8 @@ void dgf_autotune_reset(void);
  *   kind 5 (fused forward, see dgf_set_fused): r = radius, F = factor,
  *     vec = guide_f32 = 0; a = low-res rows per segment (1 .. 256), or 0 to
  *     use the two-kernel forward for this key; b = 0.
+ *   kind 6 (fused backward K1 + K3): r = radius, F = factor, vec = elements
+ *     per vector, guide_f32 = 0; a as kind 5 (0: K1 and K3 as two kernels).
  * A shape the kernels are not built for is stored but ignored at plan time
  * (the default shape is used).  Returns DGF_ERR_INVALID for a key or shape
  * outside these ranges.  No counterpart in the paper: tuning machinery.

@@ -191,6 +191,9 @@ struct Plan {
     bool k12 = false;      // forward as the fused K12 kernel
     bool k12_ok = false;   // K12 can serve this call (the tuner may still prefer K1 + K2)
     int k12_ls = 32;       // K12: low-res rows per segment
+    bool k13 = false;      // backward K1 + K3 as the fused K13 kernel
+    bool k13_ok = false;
+    int k13_ls = 16;       // K13: low-res rows per segment
 };
 
 static bool g_fused_allowed = true;
@@ -306,6 +309,15 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     if (p.k12_ok && tune_lookup(TuneKey{5, (int)dt, r, p.F, 0, 0}, a, b) && a >= 0 && a <= 256) {
         p.k12 = a > 0;
         if (a > 0) p.k12_ls = a;
+    }
+    // fused backward K1 + K3: likewise for the strip K1 and the 16-byte K3
+    // strips with one low-res cell per lane
+    p.k13_ok = g_fused_allowed && !gf32 && mean_ab && p.k3_fast && k13_supported(dt, r, p.F, p.vec) &&
+               aligned_to(hires_ptrs, 16) && p.k1.fast == 2;
+    p.k13 = p.k13_ok && r == 1;
+    if (p.k13_ok && tune_lookup(TuneKey{6, (int)dt, r, p.F, p.vec, 0}, a, b) && a >= 0 && a <= 256) {
+        p.k13 = a > 0;
+        if (a > 0) p.k13_ls = a;
     }
     if (!mean_ab) {
         // the layer as printed (no box mean of A, b): warp strips for r in
@@ -706,6 +718,42 @@ static void tune_k12(dgf_dtype dt, const void* G, const void* P, float2* coef, c
     if (bl > 0) p.k12_ls = bl;
 }
 
+// The fused backward K13 against K1 (with the statistics when K4 reads them)
+// + K3 at their tuned shapes: records the fastest K13 segment length, or 0.
+static void tune_k13(dgf_dtype dt, const void* G, const void* P, float2* coef, float4* stats, const void* R,
+                     const void* Gh, void* dGh, float2* dcoef, int planes, int h_l, int w_l, int h, int w, int r,
+                     float eps, const K3Maps& maps, cudaStream_t s, Plan& p) {
+    if (!p.k13_ok) return;
+    TuneKey key{6, (int)dt, r, p.F, p.vec, 0};
+    int a, b;
+    if (tune_lookup(key, a, b)) return;
+    size_t landing = 0;
+    TmaPair tma = make_tma_pair(G, dt, P, dt, planes, h_l, w_l, r, p.k1, landing);
+    const size_t smem = k1_cfg_smem(p.k1, r, tma.enabled ? landing : 0);
+    float best = time_launch(s, [&] {
+        cudaError_t e = launch_k1(dt, false, G, P, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, status_ptr(),
+                                  stats, s);
+        if (e != cudaSuccess) return e;
+        return launch_k3(dt, coef, R, Gh, dGh, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, p.k3_lth, &maps,
+                         status_ptr(), s);
+    }, 3);
+    if (best <= 0.f) best = 1e30f;
+    int bl = 0;
+    for (int ls : {8, 12, 16, 24, 32}) {
+        const float ms = time_launch(s, [&] {
+            return launch_k13(dt, G, P, maps, dGh, dcoef, stats, planes, h_l, w_l, h, w, r, p.F, eps, ls,
+                              status_ptr(), s);
+        }, 3);
+        if (ms > 0.f && ms < best) {
+            best = ms;
+            bl = ls;
+        }
+    }
+    tune_store(key, bl, 0);
+    p.k13 = bl > 0;
+    if (bl > 0) p.k13_ls = bl;
+}
+
 static cudaError_t run_k1(Launcher& L, dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef,
                           int planes, int h_l, int w_l, int r, float eps, const Plan& p, cudaStream_t s,
                           float4* stats = nullptr) {
@@ -1008,11 +1056,33 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
     if (tuning && (dI_h != nullptr || need_k4)) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
     const bool use_stats = need_k4 && p.k1.fast == 2 && p.k4.fast == 2;
     float4* stats = use_stats ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr;
-    if (dI_h != nullptr || use_stats) {
+    bool fused = false;
+    if (p.k13_ok && p.k3_fast) {
+        // K1 + K3 as one kernel (the tuner, when on, times it against the pair)
+        K3Maps maps;
+        if (make_k3_maps(maps, dO_h, I_h, dt, planes, h, w, p.vec, p.F)) {
+            if (tuning) {
+                tune_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, s, p);
+                tune_k13(dt, I_l, p_l, coef, stats, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, r, eps, maps, s,
+                         p);
+            }
+            if (p.k13) {
+                e = L.run("k13_fused_backward", [&] {
+                    return launch_k13(dt, I_l, p_l, maps, dI_h, dcoef, stats, planes, h_l, w_l, h, w, r, p.F, eps,
+                                      p.k13_ls, status_ptr(), s);
+                });
+                if (e != cudaSuccess) return cuda_fail(e, "k13");
+                fused = true;
+            }
+        }
+    }
+    if (!fused && (dI_h != nullptr || use_stats)) {
         e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s, stats);
         if (e != cudaSuccess) return cuda_fail(e, "k1");
     }
-    if (p.k3_fast) {
+    if (fused) {
+        // K13 wrote d Abar, d bbar (and the statistics)
+    } else if (p.k3_fast) {
         if (tuning) tune_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, s, p);
         K3Maps maps;
         const bool tma = make_k3_maps(maps, dO_h, I_h, dt, planes, h, w, p.vec, p.F);
@@ -1500,8 +1570,8 @@ extern "C" int dgf_autotune_entries(void) { return tune_count(); }
 
 extern "C" dgf_status dgf_autotune_pin(int kind, dgf_dtype dt, int r, int F, int vec, int guide_f32, int a,
                                        int b) {
-    if (kind < 1 || kind > 5 || (int)dt < 0 || (int)dt > 2 || r < 0 || F < 0 || vec < 0 || a < 0 ||
-        (a == 0 && kind != 5) || a > 4096 || b < 0 || b > 4096 || (guide_f32 != 0 && guide_f32 != 1))
+    if (kind < 1 || kind > 6 || (int)dt < 0 || (int)dt > 2 || r < 0 || F < 0 || vec < 0 || a < 0 ||
+        (a == 0 && kind < 5) || a > 4096 || b < 0 || b > 4096 || (guide_f32 != 0 && guide_f32 != 1))
         return fail(DGF_ERR_INVALID, "autotune_pin: bad key or shape");
     tune_store(TuneKey{kind, (int)dt, r, F, vec, guide_f32}, a, b);
     return DGF_OK;

@@ -48,14 +48,21 @@ __host__ __device__ constexpr float k3s_lam(int k) {
                            : (float)(2 * (k % F) + 1 - F) / (float)(2 * F);
 }
 
+// Where K3 reads Abar of row ii, column jj from: the plane's coefficient array.
+struct AbarIn {
+    const float2* __restrict__ coef;
+    int w_l;
+    __device__ __forceinline__ float at(int ii, int jj) const {
+        return reinterpret_cast<const float*>(coef)[2 * ((size_t)ii * w_l + jj)];
+    }
+};
+
 // Abar of row ii at the lane's own K cells (columns clamped to the image).
-template <int VEC, int F>
-__device__ __forceinline__ void k3s_own(const float2* __restrict__ coef, int ii, int J, int w_l,
-                                        float (&own)[VEC / F]) {
+template <int VEC, int F, class Src>
+__device__ __forceinline__ void k3s_own(const Src& coef, int ii, int J, int w_l, float (&own)[VEC / F]) {
     constexpr int K = VEC / F;
-    const float* row = reinterpret_cast<const float*>(coef + (size_t)ii * w_l);
 #pragma unroll
-    for (int c = 0; c < K; ++c) own[c] = row[2 * clampi(J + c, 0, w_l - 1)];
+    for (int c = 0; c < K; ++c) own[c] = coef.at(ii, clampi(J + c, 0, w_l - 1));
 }
 
 // A row of Abar interpolated along x at the lane's VEC pixels, from the
@@ -122,9 +129,9 @@ __device__ __forceinline__ K3Lane k3s_lane(int strip, int w_l) {
 }
 
 // Block i begins: Abar rows i and i + 1 (clamped) along x.
-template <int VEC, int F>
-__device__ __forceinline__ void k3s_block_start(K3State<VEC, F>& st, const float2* __restrict__ coef, int i,
-                                                const K3Lane& L, int h_l, int w_l) {
+template <int VEC, int F, class Src>
+__device__ __forceinline__ void k3s_block_start(K3State<VEC, F>& st, const Src& coef, int i, const K3Lane& L,
+                                                int h_l, int w_l) {
 #pragma unroll
     for (int k = 0; k < VEC; ++k) st.Hlo[k] = st.Hhi[k];
     k3s_hrow_from<VEC, F>(st.own_next, L.J, w_l, st.Hhi);  // row min(i + 1, h_l - 1)
@@ -243,9 +250,9 @@ __device__ __forceinline__ void k3s_block_end(K3State<VEC, F>& st, int i, int ia
     }
 }
 
-template <int VEC, int F>
-__device__ __forceinline__ void k3s_init(K3State<VEC, F>& st, const float2* __restrict__ coef, int ib0,
-                                         const K3Lane& L, int h_l, int w_l) {
+template <int VEC, int F, class Src>
+__device__ __forceinline__ void k3s_init(K3State<VEC, F>& st, const Src& coef, int ib0, const K3Lane& L, int h_l,
+                                         int w_l) {
     constexpr int K = VEC / F;
     k3s_own<VEC, F>(coef, clampi(ib0, 0, h_l - 1), L.J, w_l, st.own_next);
     k3s_hrow_from<VEC, F>(st.own_next, L.J, w_l, st.Hhi);
@@ -275,14 +282,14 @@ __device__ void k3_strip(const float2* __restrict__ coef, const T* __restrict__ 
     for (int s = 0; s < P; ++s)
         k3s_load<T, VEC>(R, G, row_of(0, s), row_ok(0, s), L.x0, w, L.full, L.any, rr[s], gg[s]);
     K3State<VEC, F> st;
-    k3s_init<VEC, F>(st, coef, ib0, L, h_l, w_l);
+    k3s_init<VEC, F>(st, AbarIn{coef, w_l}, ib0, L, h_l, w_l);
     for (int pi = 0; pi < nper; ++pi) {
 #pragma unroll
         for (int s = 0; s < P; ++s) {
             const int t = s % F;
             const int i = ib0 + pi * NB + s / F;
             if (i > ilast) break;  // uniform: past the segment's last block
-            if (t == 0) k3s_block_start<VEC, F>(st, coef, i, L, h_l, w_l);
+            if (t == 0) k3s_block_start<VEC, F>(st, AbarIn{coef, w_l}, i, L, h_l, w_l);
             float r[VEC], g[VEC];
             unpack_vec<T, VEC>(rr[s], r);
             unpack_vec<T, VEC>(gg[s], g);
@@ -343,13 +350,13 @@ __device__ void k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps
     }
     __syncwarp();
     K3State<VEC, F> st;
-    k3s_init<VEC, F>(st, coef, ib0, L, h_l, w_l);
+    k3s_init<VEC, F>(st, AbarIn{coef, w_l}, ib0, L, h_l, w_l);
     int m = 0;
     bool ok = true;
     for (; m < nblk; ++m) {
         const int slot = m % NSB;
         const int i = ib0 + m;
-        k3s_block_start<VEC, F>(st, coef, i, L, h_l, w_l);
+        k3s_block_start<VEC, F>(st, AbarIn{coef, w_l}, i, L, h_l, w_l);
         if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NSB) & 1), kWaitLimit))) {
             ok = false;
             break;

@@ -77,6 +77,15 @@ int k12_vec_bytes(dgf_dtype dt, int F);
 cudaError_t launch_k12(dgf_dtype dt, const void* G, const void* P, const void* in, void* out, int planes, int h_l,
                        int w_l, int h, int w, int r, int F, float eps, int LS, cudaStream_t s);
 
+// Fused backward K1 + K3 (r in {1, 2}; K3 strips of 16-byte vectors with one
+// low-res cell per lane: F32 F = 4, BF16/F16 F = 8, vec == F); `maps` the K3
+// tensor maps of d O_h and the guide; stats: the window statistics of every
+// cell for K4 (or null).  LS = low-res rows per segment.
+bool k13_supported(dgf_dtype dt, int r, int F, int vec);
+cudaError_t launch_k13(dgf_dtype dt, const void* G, const void* P, const K3Maps& maps, void* dG, float2* dcoef,
+                       float4* stats, int planes, int h_l, int w_l, int h, int w, int r, int F, float eps, int LS,
+                       uint32_t* status, cudaStream_t s);
+
 // Guidance transform (Sec. 3.4): weights staged to constant memory first.
 constexpr int kMaxK6Blocks = 1024;   // rows of weight-gradient partials
 constexpr int kWGradPadded = 99;     // padded [dw1 16x3 | dw2 3x16 | db2 3]

@@ -90,11 +90,18 @@ __device__ __forceinline__ void strip2_pairs(float v0, float v1, f32x2 (&Q)[2 * 
 //   stage B: level 2 (box sums of A, b) and the output row e - 2R.
 // INT: interior ring period.  stats non-null: stage A also writes
 // (mu, nu, 1/(var + eps), A) for the segment's rows.
-template <int R, bool INT>
+// Where stage A puts a window's statistics when the caller owns them (the
+// fused backward); the default writes the segment's rows to `stats`.
+struct NoStatsOut {
+    __device__ __forceinline__ void put(int, int, float4) const {}
+};
+
+template <int R, bool INT, class SOut = NoStatsOut>
 __device__ __forceinline__ void strip2_k1_stage_a(Strip2Ring<R>& q, const Strip2Lane<R>& ln, int U, float g0,
                                                   float g1, float p0, float p1, int e, int e_first, int xa,
                                                   float2* __restrict__ coef, float4* __restrict__ stats,
-                                                  const StripGeom& s, f32x2 eps2, f32x2& A_out, f32x2& b_out) {
+                                                  const StripGeom& s, f32x2 eps2, f32x2& A_out, f32x2& b_out,
+                                                  const SOut* sout = nullptr) {
     constexpr int W = 2 * R + 1;
     constexpr float kInvW = 1.f / (float)W;
     constexpr float kInvW2 = 1.f / (float)(W * W);
@@ -171,7 +178,15 @@ __device__ __forceinline__ void strip2_k1_stage_a(Strip2Ring<R>& q, const Strip2
             b2 = f2_mul(b2, ln.xin2);
         }
         const bool seg_row = ce >= s.y0 && ce < s.y0 + s.seg;
-        if (stats != nullptr && seg_row) {
+        if (sout != nullptr) {
+            float mu0, mu1, nu0, nu1, i0, i1, a0, a1;
+            f2_unpack(mu, mu0, mu1);
+            f2_unpack(nu, nu0, nu1);
+            f2_unpack(ive, i0, i1);
+            f2_unpack(A2, a0, a1);
+            if (ln.out[0]) sout->put(ce, xa, make_float4(mu0, nu0, i0, a0));
+            if (ln.out[1]) sout->put(ce, xa + 1, make_float4(mu1, nu1, i1, a1));
+        } else if (stats != nullptr && seg_row) {
             float mu0, mu1, nu0, nu1, i0, i1, a0, a1;
             f2_unpack(mu, mu0, mu1);
             f2_unpack(nu, nu0, nu1);
@@ -263,20 +278,20 @@ __host__ __device__ constexpr int strip2_out_cols(int R) { return 64 - 4 * R; }
 // One ring period of the walk (rows base .. base + W - 1 with values gv, pv).
 // Stage B's results go to `out` when given (the fused forward's shared-memory
 // rows), else to the plane's coefficient array.
-template <int R, bool INT, class Out = CoefOut>
+template <int R, bool INT, class Out = CoefOut, class SOut = NoStatsOut>
 __device__ __forceinline__ void strip2_k1_period(Strip2Ring<R>& q, const Strip2Lane<R>& ln,
                                                  const float (&gv)[2][2 * R + 1], const float (&pv)[2][2 * R + 1],
                                                  int base, int e_first, int e_last, int xa, float2* __restrict__ coef,
                                                  float4* __restrict__ stats, const StripGeom& s, f32x2 eps2,
-                                                 const Out* out = nullptr) {
+                                                 const Out* out = nullptr, const SOut* sout = nullptr) {
     constexpr int W = 2 * R + 1;
 #pragma unroll
     for (int u = 0; u < W; ++u) {
         const int e = base + u;
         if (!INT && e >= e_last) break;  // uniform across the warp
         f32x2 A, b;
-        strip2_k1_stage_a<R, INT>(q, ln, u, gv[0][u], gv[1][u], pv[0][u], pv[1][u], e, e_first, xa, coef, stats,
-                                  s, eps2, A, b);
+        strip2_k1_stage_a<R, INT, SOut>(q, ln, u, gv[0][u], gv[1][u], pv[0][u], pv[1][u], e, e_first, xa, coef,
+                                        stats, s, eps2, A, b, sout);
         if constexpr (std::is_same<Out, CoefOut>::value)
             strip2_k1_stage_b<R, INT>(q, ln, u, e, e_first, xa, CoefOut{coef, s.w}, s, A, b);
         else

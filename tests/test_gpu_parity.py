@@ -476,3 +476,41 @@ def test_plane_group_pipeline_gives_the_same_bits(dtype, r, planes):
     for a, b in zip(res[0], res[2]):
         assert torch.equal(a, b)
     assert L.dgf_device_status() == 0
+
+
+# -------------------------------------------------------------- fused backward
+# (dtype, N, C, h_l, w_l, F, r, eps): the K3 strips the fused backward serves
+# (16-byte vectors, one low-res cell per lane), ragged against its 30-cell
+# strips and its segments
+K13_CASES = [(F32, 2, 3, 70, 90, 4, 1, 1e-4), (F32, 1, 2, 77, 131, 4, 2, 1e-3), (BF16, 2, 2, 45, 70, 8, 1, 1e-3),
+             (BF16, 1, 3, 54, 96, 8, 2, 1e-3), (F16, 1, 2, 33, 40, 8, 1, 1e-2), (F32, 1, 1, 5, 3, 4, 1, 1e-2)]
+
+
+@pytest.mark.parametrize("k4_form", ["strips", "tiles"])
+@pytest.mark.parametrize("ls", [8, 24])
+@pytest.mark.parametrize("case", K13_CASES, ids=_ids(K13_CASES))
+def test_fused_backward_equals_two_kernel_backward(case, ls, k4_form, pin):
+    dtype, N, C, hl, wl, f, r, eps = case
+    dt = {F32: L.DGF_F32, BF16: L.DGF_BF16, F16: L.DGF_F16}[dtype]
+    vec = 16 // (4 if dtype == F32 else 2)
+    st = to_storage(make_case("photo", 80 + r, N, C, hl, wl, hl * f, wl * f), dtype)
+    R = synth.upstream_grad(81, st["I_h"].shape).to(dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    pin(1, dt, r, 0, 0, 0, 32, 0)                 # K1 strips
+    if k4_form == "tiles":
+        pin(4, dt, r, 0, 0, 0, 64, 16)            # K4 recomputing its statistics: none saved
+    pin(6, dt, r, f, vec, 0, ls, 0)               # K13 segment length
+    L.dgf_set_fused(False)
+    try:
+        ref = gf_backward(R.cuda(), g["p_l"], g["I_l"], g["I_h"], r, eps)[:3]
+    finally:
+        L.dgf_set_fused(True)
+    out = gf_backward(R.cuda(), g["p_l"], g["I_l"], g["I_h"], r, eps)[:3]
+    torch.cuda.synchronize()
+    for a, b in zip(out, ref):
+        assert torch.equal(a, b)
+    rp, rIl, rIh = oracle_backward(R, st, r, eps)
+    assert_grad(f64(out[0]), rp, dtype, "dp_l")
+    assert_grad(f64(out[1]), rIl, dtype, "dI_l")
+    assert_grad(f64(out[2]), rIh, dtype, "dI_h")
+    assert L.dgf_device_status() == 0
