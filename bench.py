@@ -628,7 +628,8 @@ def bench_small(args, device):
     return {"workload": name, "us_fwd": round(ms_f * 1e3, 2), "us_fwd_bwd": round(ms_fb * 1e3, 2),
             "fwd_mpix_s": round(pix / (ms_f * 1e-3) / 1e6, 1), "fwd_bwd_mpix_s": round(pix / (ms_fb * 1e-3) / 1e6, 1),
             "us_fwd_bwd_graph": round(ms_g * 1e3, 2), "fwd_bwd_graph_mpix_s": round(pix / (ms_g * 1e-3) / 1e6, 1),
-            "bound": "launch latency (2 kernels forward, 3 backward; eager calls pay the host launch cost)"}
+            "bound": "launch latency (one kernel forward, two backward at r = 1; eager calls pay the host "
+                     "launch cost)"}
 
 
 def bench_paper_literal(args, device):

@@ -144,27 +144,6 @@ __global__ void __launch_bounds__(kK4StripWarps * 32)
                                         s, eps, ring, bars, status);
 }
 
-template <typename TG, typename TP, typename TD, int R>
-__global__ void __launch_bounds__(kK4StripWarps * 32)
-    k4_lowres_bwd_strip_stats(const TG* __restrict__ G, const TP* __restrict__ P, const float2* __restrict__ dcoef,
-                              const float4* __restrict__ stats, TP* __restrict__ dP, TD* __restrict__ dG, int h,
-                              int w, int seg, int nstrip, int nseg, int planes, int mean) {
-    const int gw = blockIdx.x * kK4StripWarps + (threadIdx.x >> 5);
-    if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
-    const int strip = gw % nstrip, rest = gw / nstrip;
-    const int sg = rest % nseg, plane = rest / nseg;
-    StripGeom s;
-    s.h = h;
-    s.w = w;
-    s.x0 = strip * (32 - 4 * R) - 2 * R;
-    s.y0 = sg * seg;
-    s.seg = seg;
-    s.mean = mean;
-    const size_t hw = (size_t)h * w;
-    lowres_bwd_strip_stats<TG, TP, TD, R>(G + plane * hw, P + plane * hw, dcoef + plane * hw, stats + plane * hw,
-                                          dP ? dP + plane * hw : nullptr, dG ? dG + plane * hw : nullptr, s);
-}
-
 // Two-column K4 from saved statistics: warp w owns strip (w % nstrip) of the
 // two-column geometry (64 - 4R outputs) of segment (w / nstrip) % nseg.
 template <typename TG, typename TP, typename TD, int R>

@@ -495,154 +495,4 @@ __host__ __device__ constexpr int k4_strip_tma_smem() {
            kK4StripWarps * StripTmaCfg<R>::NS4 * 8;
 }
 
-// K4 strip from saved window statistics: the backward K1 pass wrote
-// (mu, nu, 1/(var + eps), A) of every window, so this pass forms only the
-// box sums of d Abar / N, d bbar / N, the four window quantities and their
-// box sums (same arithmetic as lowres_bwd_strip, without the statistics).
-template <typename TG, typename TP, typename TD, int R, bool INT>
-__device__ __forceinline__ void strip_k4s_row(StripBwdRing<R>& z, const StripLane<R>& ln, int U, float gvu,
-                                              float pvu, float2 dvu, float4 st, int e, int e_first, int x,
-                                              TP* __restrict__ dP, TD* __restrict__ dG, const StripGeom& s, float KG,
-                                              float KP) {
-    constexpr int W = 2 * R + 1;
-    constexpr float kInvW2 = 1.f / (float)(W * W);
-    const int lane = threadIdx.x & 31;
-    const bool row_in = e >= 0 && e < s.h;
-    z.rg[U] = gvu;
-    z.rp[U] = pvu;
-    if (s.mean) {
-        // d Abar / N, d bbar / N at (e, x); zero outside the image
-        const float inn = INT ? kInvW2
-                              : ((ln.xin && row_in) ? inv_count(ln.nx * (min(e + R, s.h - 1) - max(e - R, 0) + 1))
-                                                    : 0.f);
-        z.hda[U] = hsum<R>(dvu.x * inn);
-        z.hdb[U] = hsum<R>(dvu.y * inn);
-    } else {
-        // no box mean of A, b: the window's own d Abar, d bbar (row e, read at row e - R below)
-        z.hda[U] = dvu.x;
-        z.hdb[U] = dvu.y;
-    }
-    const int ce = e - R;
-    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
-    if (INT || (ln.xin && ce >= 0 && ce < s.h && e - e_first >= 2 * R)) {
-        const int ny = INT ? W : min(ce + R, s.h - 1) - max(ce - R, 0) + 1;
-        float dA = 0.f, db = 0.f;
-        if (s.mean) {
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                dA += z.hda[ring_slot<W>(U, j)];
-                db += z.hdb[ring_slot<W>(U, j)];
-            }
-        } else {
-            dA = z.hda[(U + W - R) % W];  // row ce = e - R
-            db = z.hdb[(U + W - R) % W];
-        }
-        const float mu = st.x, nu = st.y, ive = st.z, A = st.w;
-        const float gamma = fmaf(-db, mu, dA) * ive;
-        const float beta = -gamma * A;
-        const float inn = INT ? kInvW2 : inv_count(ln.nx * ny);
-        const float mus = mu - KG, nus = nu - KP;
-        q0 = gamma * inn;
-        q1 = beta * inn;
-        q2 = fmaf(-gamma, mus, db) * inn;
-        q3 = fmaf(gamma, nus, fmaf(2.f * beta, mus, db * A)) * inn;
-    }
-    z.hq0[U] = hsum<R>(q0);
-    z.hq1[U] = hsum<R>(q1);
-    z.hq2[U] = hsum<R>(q2);
-    z.hq3[U] = hsum<R>(q3);
-    const int co = ce - R;
-    const bool write = INT ? (lane >= 2 * R && lane < 32 - 2 * R && e - e_first >= 4 * R)
-                           : (ln.out && co >= s.y0 && co < s.y0 + s.seg && co < s.h && e - e_first >= 4 * R);
-    if (write) {
-        float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            const int k = ring_slot<W>(U, j);
-            S0 += z.hq0[k];
-            S1 += z.hq1[k];
-            S2 += z.hq2[k];
-            S3 += z.hq3[k];
-        }
-        const int V = (U + 1) % W;  // row co = e - 2R sits in slot (U + 1) mod W
-        const float g = z.rg[V] - KG, p = z.rp[V] - KP;
-        const size_t o = (size_t)co * s.w + x;
-        if (dP != nullptr) dP[o] = from_f32<TP>(fmaf(g, S0, S2));
-        if (dG != nullptr) dG[o] = from_f32<TD>(fmaf(p, S0, fmaf(2.f * g, S1, -S3)));
-    }
-}
-
-template <typename TG, typename TP, typename TD, int R>
-__device__ void lowres_bwd_strip_stats(const TG* __restrict__ G, const TP* __restrict__ P,
-                                       const float2* __restrict__ dcoef, const float4* __restrict__ stats,
-                                       TP* __restrict__ dP, TD* __restrict__ dG, const StripGeom& s) {
-    constexpr int W = 2 * R + 1;
-    const int lane = threadIdx.x & 31;
-    const int x = s.x0 + lane;
-    const StripLane<R> ln = strip_lane<R>(x, s.w);
-    const bool cols_int = s.x0 >= R && s.x0 + 32 + R <= s.w;
-    StripBwdRing<R> z;
-#pragma unroll
-    for (int k = 0; k < W; ++k) z.hda[k] = z.hdb[k] = z.hq0[k] = z.hq1[k] = z.hq2[k] = z.hq3[k] = z.rg[k] = z.rp[k] = 0.f;
-    const int e_first = s.y0 - 2 * R;
-    const int e_last = min(s.y0 + s.seg, s.h) + 2 * R;
-    float gn[W], pn[W];
-    float2 dn[W];
-    float4 sn[W];
-    auto load = [&](int base) {
-#pragma unroll
-        for (int u = 0; u < W; ++u) {
-            const int e = base + u, ce = e - R;
-            const bool ok = ln.xin && e >= 0 && e < s.h && e < e_last;
-            const size_t o = (size_t)e * s.w + x;
-            gn[u] = ok ? to_f32<TG>(G[o]) : 0.f;
-            pn[u] = ok ? to_f32<TP>(P[o]) : 0.f;
-            dn[u] = ok ? dcoef[o] : make_float2(0.f, 0.f);
-            sn[u] = (ln.xin && ce >= 0 && ce < s.h) ? stats[(size_t)ce * s.w + x] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    load(e_first);
-    float KG, KP;
-    {
-        const bool use = ln.out;
-        float sg = use ? gn[2 * R] : 0.f, sp = use ? pn[2 * R] : 0.f, cn = use ? 1.f : 0.f;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            sg += __shfl_xor_sync(0xffffffffu, sg, off);
-            sp += __shfl_xor_sync(0xffffffffu, sp, off);
-            cn += __shfl_xor_sync(0xffffffffu, cn, off);
-        }
-        KG = cn > 0.f ? sg / cn : 0.f;
-        KP = cn > 0.f ? sp / cn : 0.f;
-    }
-    for (int base = e_first; base < e_last; base += W) {
-        float gv[W], pv[W];
-        float2 dv[W];
-        float4 sv[W];
-#pragma unroll
-        for (int u = 0; u < W; ++u) {
-            gv[u] = gn[u];
-            pv[u] = pn[u];
-            dv[u] = dn[u];
-            sv[u] = sn[u];
-        }
-        if (base + W < e_last) load(base + W);
-        const bool row_int = cols_int && base >= 3 * R && base + W + R <= s.h &&
-                             base + W <= e_last;
-        if (row_int) {
-#pragma unroll
-            for (int u = 0; u < W; ++u)
-                strip_k4s_row<TG, TP, TD, R, true>(z, ln, u, gv[u], pv[u], dv[u], sv[u], base + u, e_first, x, dP, dG,
-                                                   s, KG, KP);
-        } else {
-#pragma unroll
-            for (int u = 0; u < W; ++u) {
-                if (base + u >= e_last) break;  // uniform across the warp
-                strip_k4s_row<TG, TP, TD, R, false>(z, ln, u, gv[u], pv[u], dv[u], sv[u], base + u, e_first, x, dP,
-                                                    dG, s, KG, KP);
-            }
-        }
-    }
-}
-
 }  // namespace dgf
