@@ -366,9 +366,16 @@ def roofline(step, spec, steps, warmup, workload):
 
 
 # ------------------------------------------------------------- end to end
-def e2e(step, steps, warmup, device):
-    """Same step with host buffers: H2D of the inputs and D2H of every output inside the timed region."""
+def e2e(step, steps, warmup, device, groups=0):
+    """Same step on host buffers through dgf_host_step: every step copies its
+    inputs host -> device and all four results device -> host inside the
+    timed region, the copies pipelined with the kernels over plane groups.
+    Also times the unpipelined form (the copies, then the two device calls,
+    then the copies back, on one stream) for comparison."""
     import torch
+
+    from paper_1803_05619_gb300.layer import workspace
+    L = step.L
     g = step.g
     ins = [g["p_l"], g["I_l"], g["I_h"], g["R"]]
     outs = [step.O, step.dp, step.dIl, step.dIh]
@@ -376,19 +383,32 @@ def e2e(step, steps, warmup, device):
     h_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
     for h, t in zip(h_in, ins):
         h.copy_(t)
+    N, C, h_l, w_l, h, w = step.shape
+    nb = L.dgf_host_step_device_bytes(N, C, h_l, w_l, h, w, step.r, step.dt, groups)
+    buf = workspace(nb, device)
+    io = L.dgf_host_step_io(*(t.data_ptr() for t in h_in + h_out))
+    args = (ctypes.byref(io), N, C, h_l, w_l, h, w, step.r, ctypes.c_float(step.eps), step.dt, groups,
+            ctypes.c_void_p(buf.data_ptr()), buf.numel(), step.stream)
+    fn = L.lib().dgf_host_step
 
-    def once():
-        for h, t in zip(h_in, ins):
-            t.copy_(h, non_blocking=True)
+    def pipelined():
+        if fn(*args) != 0:
+            raise RuntimeError(L.dgf_last_error())
+
+    def serial():
+        for hb, t in zip(h_in, ins):
+            t.copy_(hb, non_blocking=True)
         step()
-        for h, t in zip(h_out, outs):
-            h.copy_(t, non_blocking=True)
+        for hb, t in zip(h_out, outs):
+            hb.copy_(t, non_blocking=True)
 
     n = max(3, min(steps, 50))
-    ms = time_loop(once, n, max(2, warmup // 4), 1, device)
+    ms = time_loop(pipelined, n, max(2, warmup // 4), 1, device)
+    ms_serial = time_loop(serial, n, max(2, warmup // 4), 1, device)
     bi = sum(t.numel() * t.element_size() for t in ins)
     bo = sum(t.numel() * t.element_size() for t in outs)
-    return ms, bi, bo, n
+    del buf
+    return ms, bi, bo, n, ms_serial
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -511,10 +531,15 @@ def main():
         print(json.dumps(line), flush=True)
     elif rank == 0:
         line["roofline"] = roofline(step, spec, min(args.steps, 200), args.warmup, MAIN)
-        e_ms, bi, bo, n_e2e = e2e(step, args.steps, args.warmup, device)
+        e_ms, bi, bo, n_e2e, e_serial = e2e(step, args.steps, args.warmup, device)
         line["e2e"] = {"value": round(pix / (e_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
                        "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": n_e2e,
-                       "ms_per_step": round(e_ms, 4)}
+                       "ms_per_step": round(e_ms, 4),
+                       "path": "dgf_host_step on pinned host buffers (copies both ways pipelined with the "
+                               "kernels over plane groups)",
+                       "unpipelined": {"value": round(pix / (e_serial * 1e-3) / 1e6, 2),
+                                       "ms_per_step": round(e_serial, 4),
+                                       "path": "copies in, dgf_forward + dgf_backward, copies out, one stream"}}
         if not args.no_extra:
             line["bf16_4k"] = bench_bf16_4k(args, device)
             line["batched_64_uneven"] = bench_batched_64(args, device)

@@ -337,6 +337,53 @@ dgf_status dgf_forward_noalloc(const void* p_l, const void* I_l, const void* I_h
                                dgf_dtype dt, dgf_stream_t stream);
 size_t dgf_noalloc_max_pairs(void);
 
+/*
+ * Forward and backward of one batch whose tensors live in HOST memory
+ * (Eq. 1-2 and Algorithm 1 as dgf_forward and dgf_backward compute them,
+ * identity guide, box mean of A and b).  The call copies the inputs to the
+ * device, runs the layer and copies the results back, pipelined over groups
+ * of planes: while group g's kernels run, group g + 1's inputs travel
+ * host -> device and group g - 1's results device -> host, on three
+ * library-owned streams forked from and joined back to `stream`.  Planes
+ * are independent, so every output plane holds the bits the device-memory
+ * calls give for it.  No counterpart in the paper (I/O machinery).
+ *   io:       host pointers (NCHW).  Inputs p_l, I_l (N x C x h_l x w_l) and
+ *             I_h (N x C x h x w) are required; dO_h (N x C x h x w) is
+ *             required when a gradient output is given.  Outputs, each
+ *             nullable (not wanted): O_h (forward), dp_l, dI_l, dI_h
+ *             (backward; with all three NULL the backward is not run).
+ *             Pinned memory (cudaHostAlloc / cudaHostRegister) lets the
+ *             copies overlap the kernels; pageable memory still works but
+ *             the driver stages it and the overlap is lost.
+ *   groups:   plane groups of the pipeline, 1 .. 16, or 0 for the default
+ *             (min(N*C, 6)); clamped to N*C.
+ *   device:   device memory of at least dgf_host_step_device_bytes(...)
+ *             bytes, 256-byte aligned: the device copies of the eight
+ *             tensors and the workspace of one group.  Owned by the caller;
+ *             its contents after the call are unspecified.
+ * The host buffers must stay valid, and the output buffers untouched, until
+ * `stream` reaches the end of the call (cudaStreamSynchronize(stream)).
+ * Errors as dgf_forward / dgf_backward; on an error in group g the groups
+ * before it have been issued and `stream` is still joined to every library
+ * stream.  Not under stream capture.
+ */
+typedef struct {
+    const void* p_l;
+    const void* I_l;
+    const void* I_h;
+    const void* dO_h;
+    void* O_h;
+    void* dp_l;
+    void* dI_l;
+    void* dI_h;
+} dgf_host_step_io;
+
+size_t dgf_host_step_device_bytes(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt,
+                                  int groups);
+dgf_status dgf_host_step(const dgf_host_step_io* io, int N, int C, int h_l, int w_l, int h, int w, int r,
+                         float eps, dgf_dtype dt, int groups, void* device, size_t device_bytes,
+                         dgf_stream_t stream);
+
 /* Releases cached graphs and tuning state (idempotent). */
 void dgf_shutdown(void);
 

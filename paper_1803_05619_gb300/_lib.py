@@ -42,6 +42,12 @@ class dgf_image_grad(ctypes.Structure):
                 ("h", ctypes.c_int), ("w", ctypes.c_int), ("r", ctypes.c_int), ("eps", ctypes.c_float)]
 
 
+class dgf_host_step_io(ctypes.Structure):
+    _fields_ = [("p_l", ctypes.c_void_p), ("I_l", ctypes.c_void_p), ("I_h", ctypes.c_void_p),
+                ("dO_h", ctypes.c_void_p), ("O_h", ctypes.c_void_p), ("dp_l", ctypes.c_void_p),
+                ("dI_l", ctypes.c_void_p), ("dI_h", ctypes.c_void_p)]
+
+
 class DGFError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
@@ -82,6 +88,9 @@ _SIGS = {
     "dgf_autotune_pin": (_I, [_I, _I, _I, _I, _I, _I, _I, _I]),
     "dgf_forward_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _F, _I, _P]),
     "dgf_noalloc_max_pairs": (_S, []),
+    "dgf_host_step_device_bytes": (_S, [_I, _I, _I, _I, _I, _I, _I, _I, _I]),
+    "dgf_host_step": (_I, [ctypes.POINTER(dgf_host_step_io), _I, _I, _I, _I, _I, _I, _I, _F, _I, _I, _P, _S,
+                           _P]),
 }
 
 
@@ -218,3 +227,11 @@ def dgf_forward_noalloc(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, st
 
 def dgf_noalloc_max_pairs() -> int:
     return lib().dgf_noalloc_max_pairs()
+
+
+def dgf_host_step_device_bytes(N, C, h_l, w_l, h, w, r, dt, groups) -> int:
+    return lib().dgf_host_step_device_bytes(N, C, h_l, w_l, h, w, r, dt, groups)
+
+
+def dgf_host_step(io, N, C, h_l, w_l, h, w, r, eps, dt, groups, device, device_bytes, stream) -> int:
+    return lib().dgf_host_step(io, N, C, h_l, w_l, h, w, r, eps, dt, groups, device, device_bytes, stream)

@@ -1453,6 +1453,54 @@ static cudaError_t bwd_pool(int dev, BwdPool*& out) {
     return cudaSuccess;
 }
 
+// Streams of dgf_host_step: host -> device copies, kernels, device -> host
+// copies, with one event per group and stage.
+constexpr int kHostMaxGroups = 16;
+struct HostPool {
+    int dev = -1;
+    cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t copied[kHostMaxGroups] = {}, done[kHostMaxGroups] = {};
+};
+std::mutex g_host_mu;
+std::map<int, HostPool> g_host_pools;
+
+static cudaError_t host_pool(int dev, HostPool*& out) {
+    HostPool& p = g_host_pools[dev];
+    if (p.dev < 0) {
+        cudaError_t e;
+        cudaStream_t* sts[] = {&p.in, &p.comp, &p.out};
+        for (cudaStream_t* st : sts)
+            if ((e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&p.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        for (int g = 0; g < kHostMaxGroups; ++g) {
+            if ((e = cudaEventCreateWithFlags(&p.copied[g], cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&p.done[g], cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        p.dev = dev;
+    }
+    out = &p;
+    return cudaSuccess;
+}
+
+static void host_pools_free() {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    for (auto& kv : g_host_pools) {
+        HostPool& p = kv.second;
+        cudaStream_t sts[] = {p.in, p.comp, p.out};
+        for (cudaStream_t st : sts)
+            if (st) cudaStreamDestroy(st);
+        if (p.fork) cudaEventDestroy(p.fork);
+        if (p.join) cudaEventDestroy(p.join);
+        for (int g = 0; g < kHostMaxGroups; ++g) {
+            if (p.copied[g]) cudaEventDestroy(p.copied[g]);
+            if (p.done[g]) cudaEventDestroy(p.done[g]);
+        }
+    }
+    g_host_pools.clear();
+}
+
 static dgf_status check_grad_images(const dgf_image_grad* imgs, int n, dgf_dtype dt, size_t* ws_total) {
     if ((int)dt < 0 || (int)dt > 2) return fail(DGF_ERR_INVALID, "dtype %d", (int)dt);
     if (n < 0 || n > DGF_MAX_BATCH) return fail(DGF_ERR_INVALID, "n = %d outside [0, %d]", n, DGF_MAX_BATCH);
@@ -1607,6 +1655,7 @@ extern "C" void dgf_shutdown(void) {
         }
         g_bwd_pools.clear();
     }
+    host_pools_free();
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (auto& kv : g_batch) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -1686,4 +1735,130 @@ extern "C" dgf_status dgf_forward_noalloc(const void* p_l, const void* I_l, cons
     e = launch_k2_plan(dt, coef, I_h, O_h, planes, h_l, w_l, h, w, p, p.k2_strip ? p.k2_ls : p.k2_th, s);
     if (e != cudaSuccess) return cuda_fail(e, "k2");
     return DGF_OK;
+}
+
+// ====================================================== host-memory batches
+// dgf_host_step: the planes of one batch in groups, each group's inputs
+// copied in on one stream, its forward and backward on a second and its
+// results copied out on a third, so copies in both directions overlap the
+// kernels of the neighbouring groups.  Each group runs dgf_forward and
+// dgf_backward on its planes (N = planes, C = 1: without a guidance
+// transform the planes are independent), in device copies that sit at the
+// planes' offsets of full-size device tensors.
+namespace dgf {
+
+struct HostLayout {
+    size_t off[8];  // p_l, I_l, I_h, dO_h, O_h, dp_l, dI_l, dI_h
+    size_t ws, total;
+};
+
+static int host_groups(int planes, int groups) {
+    int G = groups > 0 ? groups : 6;
+    G = std::min(G, kHostMaxGroups);
+    return std::max(1, std::min(G, planes));
+}
+
+static HostLayout host_layout(int N, int C, int h_l, int w_l, int h, int w, dgf_dtype dt, int G) {
+    HostLayout L;
+    const size_t planes = (size_t)N * C, esz = esize(dt);
+    const size_t lo = planes * h_l * w_l * esz, hi = planes * h * w * esz;
+    const size_t sizes[8] = {lo, lo, hi, hi, hi, lo, lo, hi};
+    size_t o = 0;
+    for (int k = 0; k < 8; ++k) {
+        L.off[k] = o;
+        o += align256(sizes[k]);
+    }
+    const int gmax = (int)((planes + G - 1) / G);
+    L.ws = o;
+    L.total = o + align256(layout(gmax, 1, h_l, w_l, false).total);
+    return L;
+}
+
+}  // namespace dgf
+
+extern "C" size_t dgf_host_step_device_bytes(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt,
+                                             int groups) {
+    if (check_sizes(N, C, h_l, w_l, h, w, r, 1.f, dt) != DGF_OK) return 0;
+    if (groups < 0 || groups > kHostMaxGroups) return 0;
+    return host_layout(N, C, h_l, w_l, h, w, dt, host_groups(std::max(N * C, 1), groups)).total;
+}
+
+extern "C" dgf_status dgf_host_step(const dgf_host_step_io* io, int N, int C, int h_l, int w_l, int h, int w,
+                                    int r, float eps, dgf_dtype dt, int groups, void* device, size_t device_bytes,
+                                    dgf_stream_t stream) {
+    dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
+    if (st != DGF_OK) return st;
+    if (io == nullptr) return fail(DGF_ERR_INVALID, "NULL io descriptor");
+    if (groups < 0 || groups > kHostMaxGroups)
+        return fail(DGF_ERR_INVALID, "groups = %d outside [0, %d]", groups, kHostMaxGroups);
+    const bool bwd = io->dp_l != nullptr || io->dI_l != nullptr || io->dI_h != nullptr;
+    if (io->p_l == nullptr || io->I_l == nullptr || io->I_h == nullptr || (bwd && io->dO_h == nullptr))
+        return fail(DGF_ERR_INVALID, "NULL host input pointer");
+    if (N == 0 || (io->O_h == nullptr && !bwd)) return DGF_OK;
+    const int planes = N * C;
+    const int G = host_groups(planes, groups);
+    const HostLayout lay = host_layout(N, C, h_l, w_l, h, w, dt, G);
+    if ((st = check_ws(device, device_bytes, lay.total)) != DGF_OK) return st;
+    if (stream_capturing(reinterpret_cast<cudaStream_t>(stream)))
+        return fail(DGF_ERR_UNSUPPORTED, "dgf_host_step under stream capture");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    HostPool* hp = nullptr;
+    if ((e = host_pool(dev, hp)) != cudaSuccess) return cuda_fail(e, "host-step streams");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(device);
+    const size_t esz = esize(dt);
+    const size_t lo_plane = (size_t)h_l * w_l * esz, hi_plane = (size_t)h * w * esz;
+    const size_t plane_bytes[8] = {lo_plane, lo_plane, hi_plane, hi_plane, hi_plane, lo_plane, lo_plane, hi_plane};
+    const void* hin[4] = {io->p_l, io->I_l, io->I_h, bwd ? io->dO_h : nullptr};
+    void* hout[4] = {io->O_h, io->dp_l, io->dI_l, io->dI_h};
+    void* ws = base + lay.ws;
+    const size_t ws_bytes = lay.total - lay.ws;
+
+    // fork: the three streams start after the caller's earlier work
+    if ((e = cudaEventRecord(hp->fork, s)) != cudaSuccess) return cuda_fail(e, "fork");
+    cudaStream_t sts[3] = {hp->in, hp->comp, hp->out};
+    for (cudaStream_t x : sts)
+        if ((e = cudaStreamWaitEvent(x, hp->fork, 0)) != cudaSuccess) return cuda_fail(e, "fork wait");
+    dgf_status result = DGF_OK;
+    for (int g = 0; g < G && result == DGF_OK; ++g) {
+        const int p0 = (int)((size_t)planes * g / G), p1 = (int)((size_t)planes * (g + 1) / G);
+        const int n = p1 - p0;
+        auto dptr = [&](int k) { return base + lay.off[k] + (size_t)p0 * plane_bytes[k]; };
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            if (hin[k] != nullptr)
+                e = cudaMemcpyAsync(dptr(k), static_cast<const char*>(hin[k]) + (size_t)p0 * plane_bytes[k],
+                                    (size_t)n * plane_bytes[k], cudaMemcpyHostToDevice, hp->in);
+        if (e == cudaSuccess) e = cudaEventRecord(hp->copied[g], hp->in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->comp, hp->copied[g], 0);
+        if (e != cudaSuccess) {
+            result = cuda_fail(e, "host-to-device copy");
+            break;
+        }
+        dgf_stream_t cs = reinterpret_cast<dgf_stream_t>(hp->comp);
+        if (io->O_h != nullptr)
+            result = forward_impl(dptr(0), dptr(1), dptr(2), dptr(4), n, 1, h_l, w_l, h, w, r, eps, dt, nullptr, ws,
+                                  ws_bytes, cs, true);
+        if (result == DGF_OK && bwd)
+            result = backward_impl(dptr(3), dptr(0), dptr(1), dptr(2), io->dp_l ? dptr(5) : nullptr,
+                                   io->dI_l ? dptr(6) : nullptr, io->dI_h ? dptr(7) : nullptr, nullptr, n, 1, h_l,
+                                   w_l, h, w, r, eps, dt, nullptr, ws, ws_bytes, cs, true);
+        if (result != DGF_OK) break;
+        if ((e = cudaEventRecord(hp->done[g], hp->comp)) == cudaSuccess)
+            e = cudaStreamWaitEvent(hp->out, hp->done[g], 0);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            if (hout[k] != nullptr)
+                e = cudaMemcpyAsync(static_cast<char*>(hout[k]) + (size_t)p0 * plane_bytes[4 + k], dptr(4 + k),
+                                    (size_t)n * plane_bytes[4 + k], cudaMemcpyDeviceToHost, hp->out);
+        if (e != cudaSuccess) result = cuda_fail(e, "device-to-host copy");
+    }
+    // join: the caller's stream waits for all three (also after an error)
+    for (cudaStream_t x : sts) {
+        cudaError_t ej = cudaEventRecord(hp->join, x);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, hp->join, 0);
+        if (ej != cudaSuccess && result == DGF_OK) result = cuda_fail(ej, "join");
+    }
+    return result;
 }

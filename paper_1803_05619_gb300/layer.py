@@ -132,6 +132,47 @@ def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=No
     return dp, dIl, dIh, dws
 
 
+def gf_step_host(p_l, I_l, I_h, dO_h, r: int, eps: float, out=None, groups: int = 0, device=None, buf=None,
+                 sync: bool = True):
+    """Forward and backward of a batch held in host memory (dgf_host_step).
+
+    p_l, I_l, I_h, dO_h: contiguous CPU tensors of one dtype (pinned memory
+    lets the copies overlap the kernels).  Returns host tensors
+    (O_h, dp_l, dI_l, dI_h), written into ``out`` when given (entries may
+    be None: not wanted).  ``buf``: a device byte tensor of at least
+    dgf_host_step_device_bytes bytes, 256-byte aligned, reused across calls
+    (allocated here when None).  With sync=False the outputs are complete
+    once the device's current stream has reached the end of the call, and
+    the inputs must stay alive until then.
+    """
+    for t in (p_l, I_l, I_h, dO_h):
+        if t is None or t.is_cuda or not t.is_contiguous():
+            raise ValueError("gf_step_host takes contiguous CPU tensors")
+        if t.dtype != I_h.dtype:
+            raise TypeError("p_l, I_l, I_h and dO_h must share one dtype")
+    dev = torch.device(device if device is not None else "cuda")
+    N, C, h_l, w_l, h, w = _sizes(p_l, I_h)
+    dt = dtype_code(I_h)
+    pin = I_h.is_pinned()
+    if out is None:
+        out = (torch.empty(I_h.shape, dtype=I_h.dtype, pin_memory=pin),
+               torch.empty(p_l.shape, dtype=p_l.dtype, pin_memory=pin),
+               torch.empty(p_l.shape, dtype=p_l.dtype, pin_memory=pin),
+               torch.empty(I_h.shape, dtype=I_h.dtype, pin_memory=pin))
+    nb = L.dgf_host_step_device_bytes(N, C, h_l, w_l, h, w, r, dt, groups)
+    if nb == 0:
+        raise ValueError("invalid sizes or groups for dgf_host_step")
+    if buf is None or buf.numel() < nb:
+        buf = workspace(nb, dev)
+    io = L.dgf_host_step_io(*(None if x is None else x.data_ptr() for x in (p_l, I_l, I_h, dO_h, *out)))
+    with torch.cuda.device(dev):
+        L.check(L.dgf_host_step(ctypes.byref(io), N, C, h_l, w_l, h, w, r, float(eps), dt, groups, _ptr(buf),
+                                buf.numel(), _stream(dev)))
+        if sync:
+            torch.cuda.current_stream(dev).synchronize()
+    return out
+
+
 def gf_forward_batched(images, out=None):
     """Uneven batch in one graph-replayed persistent launch per stage.
 

@@ -117,3 +117,28 @@ def test_batched_backward_validation(lib):
     assert L.dgf_backward_batched(arr, 3, L.DGF_F32, None, 0, None) == 1
     assert L.dgf_backward_batched(arr, 2, L.DGF_F32, None, 0, None) == 5  # workspace too small
     assert L.dgf_backward_batched(arr, 0, L.DGF_F32, None, 0, None) == 0
+
+
+def test_host_step_validation(lib):
+    """dgf_host_step's size query and argument checks run on the host, before any CUDA call."""
+    nb = L.dgf_host_step_device_bytes(2, 3, 16, 20, 64, 80, 1, L.DGF_F32, 0)
+    assert nb > 0 and nb % 256 == 0
+    # eight full-size device tensors at least
+    assert nb >= 4 * (2 * 3 * 64 * 80 * 4) + 4 * (2 * 3 * 16 * 20 * 4)
+    # more groups: a smaller per-group workspace
+    assert L.dgf_host_step_device_bytes(2, 3, 16, 20, 64, 80, 1, L.DGF_F32, 6) <= \
+        L.dgf_host_step_device_bytes(2, 3, 16, 20, 64, 80, 1, L.DGF_F32, 1)
+    assert L.dgf_host_step_device_bytes(2, 3, 16, 20, 64, 80, 1, L.DGF_F32, 17) == 0
+    assert L.dgf_host_step_device_bytes(2, 3, 16, 20, 64, 80, -1, L.DGF_F32, 0) == 0
+    io = L.dgf_host_step_io(16, 32, 48, 64, 80, 96, 112, 128)
+    assert L.dgf_host_step(None, 2, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 0, None, 0, None) == 1
+    assert L.dgf_host_step(ctypes.byref(io), 2, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 99, None, 0, None) == 1
+    assert L.dgf_host_step(ctypes.byref(io), 2, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 0, None, 0, None) == 5
+    no_dO = L.dgf_host_step_io(16, 32, 48, None, 80, 96, 112, 128)  # gradients wanted, no dO_h
+    assert L.dgf_host_step(ctypes.byref(no_dO), 2, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 0, None, 0, None) == 1
+    fwd_only = L.dgf_host_step_io(16, 32, 48, None, 80, None, None, None)
+    assert L.dgf_host_step(ctypes.byref(fwd_only), 2, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 0, None, 0,
+                           None) == 5
+    nothing = L.dgf_host_step_io(16, 32, 48, None, None, None, None, None)
+    assert L.dgf_host_step(ctypes.byref(nothing), 2, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 0, None, 0, None) == 0
+    assert L.dgf_host_step(ctypes.byref(io), 0, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 0, None, 0, None) == 0
