@@ -302,6 +302,9 @@ def ncu_traffic(kernel, workload, field="dram_bytes_per_launch"):
     return e.get(field)
 
 
+# FP32 FMA peak of the guidance kernels: 152 SMs x 128 FP32 lanes x 2 flops
+# x 2070 MHz maximum SM clock, in TFLOP/s.
+FP32_FMA_TFLOPS = round(152 * 128 * 2 * 2.07e9 / 1e12, 2)
 # Instruction-issue peak of the low-res kernels (bound by issue and by the
 # latency of their row walks, not by HBM): 152 SMs x 4 schedulers x one
 # warp-instruction per cycle x 2070 MHz maximum SM clock.
@@ -706,10 +709,24 @@ def bench_guided(args, device):
     finally:
         L.dgf_profile_enable(False)
     pix = 8 * 2048 * 2048
-    return {"workload": "guided_train_8x3x2048 (BF16, r=8, eps=1e-4, F: 3->15->3)",
-            "fwd_bwd_mpix_s": round(pix / (ms * 1e-3) / 1e6, 1), "ms_fwd_bwd": round(ms, 4),
-            "bound": "alu (FP32 FMA of the 1x1 convolutions)",
-            "kernels_avg_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in prof.items()}}
+    avg = {k: v[0] / v[1] * 1e3 for k, v in prof.items()}
+    out = {"workload": "guided_train_8x3x2048 (BF16, r=8, eps=1e-4, F: 3->15->3)",
+           "fwd_bwd_mpix_s": round(pix / (ms * 1e-3) / 1e6, 1), "ms_fwd_bwd": round(ms, 4),
+           "bound": "alu (FP32 FMA of the 1x1 convolutions)",
+           "kernels_avg_us": {k: round(v, 1) for k, v in avg.items()}}
+    if "k6_guide_bwd" in avg:
+        # K6 per high-res pixel: the hidden layer recomputed (3H FMA), d h = W2^T d G (3H),
+        # the two weight-gradient outer products (3H + 3H), d I = W1^T d z (3H) and
+        # d G = d O Abar_h + d G_l / f^2 (3): 15 H + 3 FMA, 2 flops each
+        hid = 15
+        flops = 2 * (15 * hid + 3) * pix
+        ach = flops / (avg["k6_guide_bwd"] * 1e-6) / 1e12
+        out["roofline"] = {"kernel": "k6_guide_bwd", "bound": "alu", "achieved": round(ach, 2),
+                           "peak": FP32_FMA_TFLOPS, "unit": "TFLOP/s", "frac": round(ach / FP32_FMA_TFLOPS, 4),
+                           "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (unit counts and "
+                                          "maximum SM clock)",
+                           "algorithmic_flops": flops, "us_per_call": round(avg["k6_guide_bwd"], 1)}
+    return out
 
 
 if __name__ == "__main__":

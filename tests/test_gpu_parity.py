@@ -355,6 +355,8 @@ GUIDED_CASES = [  # N, h_l, w_l, f, r, eps, dtype
     (1, 20, 30, 8, 2, 1e-4, BF16),
     (2, 16, 29, 8, 8, 1e-4, BF16),   # r = 8 as in the training configuration; ragged K3 tile
     (1, 26, 18, 4, 1, 1e-3, F16),
+    (1, 22, 26, 2, 1, 1e-3, F32),    # f = 2
+    (2, 18, 30, 2, 2, 1e-3, BF16),   # f = 2, 8-byte vectors
 ]
 
 
