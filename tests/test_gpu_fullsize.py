@@ -9,6 +9,9 @@ shapes chosen by the autotuner as in the benchmark.
   equal to its single call
 * the training step with the guidance transform, 8 x 3 x 256^2 -> 2048^2,
   r = 8, eps = 1e-4, BF16, weight gradients included
+* the plain FP32 step from pinned host memory (dgf_host_step, six plane
+  groups as in the end-to-end benchmark): every output bitwise equal to the
+  device calls
 """
 import numpy as np
 import pytest
@@ -17,7 +20,8 @@ import torch
 import oracle as O
 import synth
 from paper_1803_05619_gb300 import _lib as L
-from paper_1803_05619_gb300.layer import gf_backward, gf_backward_batched, gf_forward, gf_forward_batched
+from paper_1803_05619_gb300.layer import (gf_backward, gf_backward_batched, gf_forward, gf_forward_batched,
+                                          gf_step_host)
 from tests.helpers import assert_fwd, assert_grad, f64, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -53,6 +57,20 @@ def test_fp32_plain_fullsize():
         assert_grad(f64(dp[n, c]), rp[n, c], torch.float32, "dp_l")
         assert_grad(f64(dIl[n, c]), rIl[n, c], torch.float32, "dI_l")
         assert_grad(f64(dIh[n, c]), rIh[n, c], torch.float32, "dI_h")
+
+
+def test_host_step_fullsize():
+    N, C, hl, wl, f, r, eps = 4, 3, 512, 512, 4, 1, 1e-4
+    d = synth.blobs_tone_curve(0, N, C, hl, wl, f, device="cuda")
+    g = {k: v.float().cuda() for k, v in d.items()}
+    R = synth.upstream_grad(1, g["I_h"].shape).float().cuda()
+    out = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps)
+    dp, dIl, dIh, _ = gf_backward(R, g["p_l"], g["I_l"], g["I_h"], r, eps)
+    torch.cuda.synchronize()
+    h = {k: v.cpu().pin_memory() for k, v in g.items()}
+    res = gf_step_host(h["p_l"], h["I_l"], h["I_h"], R.cpu().pin_memory(), r, eps, groups=6)
+    for a, b in zip(res, (out, dp, dIl, dIh)):
+        assert torch.equal(a, b.cpu())
 
 
 def test_bf16_4k_fullsize():
