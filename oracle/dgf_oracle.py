@@ -19,6 +19,9 @@ What it computes (Wu et al., "Fast End-to-End Trainable Guided Filter"):
 * Sec. 3.4 - the guidance transform F: 1x1 conv, leaky ReLU (slope 0.2),
   1x1 conv, applied per pixel; with it the low-resolution guide is the
   f x f block mean of F(I_h).
+* Sec. 6.3 (DGF_b) - when the guide and the output differ in channel count,
+  F is the mean over the guide's channels (a grey guide), used for every
+  output channel.
 
 Readings of points the paper leaves open (each is also listed in the design
 notes): windows are clipped to the image and divided by the number of
@@ -54,6 +57,9 @@ __all__ = [
     "block_mean",
     "forward_guided",
     "backward_guided",
+    "grey_guide",
+    "forward_grey",
+    "backward_grey",
 ]
 
 
@@ -359,3 +365,49 @@ def backward_guided(R, p_l, I_h, w1, w2, b2, r: int, eps: float, slope: float = 
         dw1 += np.einsum("khw,chw->kc", dZ, I_h[n])
         dI[n] = np.einsum("kc,khw->chw", w1, dZ)
     return dp, dI, dw1, dw2, db2
+
+
+# --------------------------------------------------------------------------
+# Grey guide (DGF_b with differing channel counts, Sec. 6.3)
+# --------------------------------------------------------------------------
+
+def grey_guide(I, store=None) -> np.ndarray:
+    """(N, 1, h, w): the mean of an (N, n_I, h, w) guide over its channels.
+
+    ``store``: the storage type of the layer (a torch dtype) when it is
+    narrower than FP64; the grey guide is then rounded to it (through FP32,
+    round to nearest even), as the layer stores every guide it reads in its
+    storage type.
+    """
+    I = _f64(I)
+    G = I.mean(axis=1, keepdims=True)
+    if store is not None:
+        import torch
+        G = torch.from_numpy(G).to(torch.float32).to(store).double().numpy()
+    return G
+
+
+def forward_grey(p_l, I_l, I_h, r: int, eps: float, store=None, mean_ab: bool = True) -> np.ndarray:
+    """O_h (N, C, h, w) with the grey guide of I_l, I_h (N, n_I, ...) for every output channel."""
+    p_l = _f64(p_l)
+    C = p_l.shape[1]
+    G_l = np.repeat(grey_guide(I_l, store), C, axis=1)
+    G_h = np.repeat(grey_guide(I_h, store), C, axis=1)
+    return forward(p_l, G_l, G_h, r, eps, mean_ab=mean_ab)
+
+
+def backward_grey(R, p_l, I_l, I_h, r: int, eps: float, store=None, mean_ab: bool = True):
+    """(dp_l, dI_l, dI_h) of sum(O_h * R) with the grey guide.
+
+    The grey guide feeds every output channel, so its gradient is the sum of
+    the channels' guide gradients (Algorithm 1 per channel); the channel mean
+    hands 1 / n_I of it to each guide channel.
+    """
+    p_l, I_l, I_h = _f64(p_l), _f64(I_l), _f64(I_h)
+    C, n_in = p_l.shape[1], I_l.shape[1]
+    G_l = np.repeat(grey_guide(I_l, store), C, axis=1)
+    G_h = np.repeat(grey_guide(I_h, store), C, axis=1)
+    dp, dG_l, dG_h = backward(R, p_l, G_l, G_h, r, eps, mean_ab=mean_ab)
+    dI_l = np.repeat(dG_l.sum(axis=1, keepdims=True) / n_in, n_in, axis=1)
+    dI_h = np.repeat(dG_h.sum(axis=1, keepdims=True) / n_in, n_in, axis=1)
+    return dp, dI_l, dI_h

@@ -398,6 +398,76 @@ def test_paper_literal_guided_matches_torch():
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-10
 
 
+# ------------------------------------------------------------- grey guide
+
+def _grey_case(seed, N, n_in, C, hl, wl, h, w):
+    """Guide with n_in channels, target with C channels (independent draws)."""
+    g = synth.ragged_case(seed, N, n_in, hl, wl, h, w)
+    p = synth.ragged_case(seed + 1, N, C, hl, wl, h, w)["p_l"]
+    return p, g["I_l"], g["I_h"]
+
+
+def test_grey_guide_with_one_channel_is_the_plain_filter():
+    p, il, ih = _grey_case(40, 2, 1, 1, 6, 7, 18, 20)
+    assert np.array_equal(O.forward_grey(p, il, ih, 1, 1e-2), O.forward(p, il, ih, 1, 1e-2))
+    R = synth.upstream_grad(3, ih.shape)
+    for a, b in zip(O.backward_grey(R, p, il, ih, 1, 1e-2), O.backward(R, p, il, ih, 1, 1e-2)):
+        assert np.array_equal(a, b)
+
+
+def test_grey_guide_of_equal_channels_is_that_channel():
+    p, il, ih = _grey_case(41, 1, 1, 2, 5, 6, 20, 24)
+    il3, ih3 = il.repeat(1, 3, 1, 1), ih.repeat(1, 3, 1, 1)
+    got = O.forward_grey(p, il3, ih3, 2, 1e-3)
+    ref = O.forward(p, il.repeat(1, 2, 1, 1), ih.repeat(1, 2, 1, 1), 2, 1e-3)
+    assert np.max(np.abs(got - ref)) < 1e-14
+
+
+@pytest.mark.parametrize("n_in,C", [(3, 1), (1, 3), (3, 2)])
+def test_grey_forward_and_backward_match_torch(n_in, C):
+    p, il, ih = _grey_case(42, 2, n_in, C, 5, 6, 15, 17)
+    R = synth.upstream_grad(4, (2, C, 15, 17))
+    pt = p.clone().requires_grad_(True)
+    ilt = il.clone().requires_grad_(True)
+    iht = ih.clone().requires_grad_(True)
+    # the channel mean and its broadcast written with torch; autograd gives the adjoint
+    Gl = ilt.mean(dim=1, keepdim=True).expand(-1, C, -1, -1)
+    Gh = iht.mean(dim=1, keepdim=True).expand(-1, C, -1, -1)
+    out = TC.gf(pt, Gl, Gh, 1, 1e-2)
+    (out * R).sum().backward()
+    assert np.max(np.abs(O.forward_grey(p, il, ih, 1, 1e-2) - out.detach().numpy())) < 1e-12
+    got = O.backward_grey(R, p, il, ih, 1, 1e-2)
+    for a, b in zip(got, (pt.grad, ilt.grad, iht.grad)):
+        b = b.numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-10
+    if n_in != C:  # an adjoint that divides by the output channels instead is caught
+        wrong = got[2] * n_in / C
+        assert np.linalg.norm(wrong - iht.grad.numpy()) / np.linalg.norm(iht.grad.numpy()) > 0.1
+
+
+def test_grey_backward_finite_differences():
+    p, il, ih = _grey_case(43, 1, 3, 2, 4, 4, 12, 12)
+    p, il, ih = p.numpy().copy(), il.numpy().copy(), ih.numpy().copy()
+    R = synth.upstream_grad(5, (1, 2, 12, 12)).numpy()
+    _, dil, dih = O.backward_grey(R, p, il, ih, 1, 1e-2)
+
+    def loss():
+        return float((O.forward_grey(p, il, ih, 1, 1e-2) * R).sum())
+    assert _fd_check(loss, il, dil, n_probe=12) < 1e-6
+    assert _fd_check(loss, ih, dih, n_probe=12, seed=1) < 1e-6
+
+
+@pytest.mark.parametrize("store,ulp", [(torch.bfloat16, 2.0 ** -7), (torch.float16, 2.0 ** -10)])
+def test_grey_guide_stored_rounding(store, ulp):
+    """Rounded to the storage type: representable there, within half its ulp of the exact mean."""
+    I = torch.from_numpy(rng(44).uniform(0.0, 1.0, size=(2, 3, 9, 11))).to(store).double()
+    exact = I.numpy().mean(axis=1, keepdims=True)
+    G = O.grey_guide(I, store)
+    assert np.array_equal(torch.from_numpy(G).to(store).double().numpy(), G)
+    scale = 2.0 ** np.floor(np.log2(np.maximum(np.abs(exact), 1e-30)))
+    assert np.all(np.abs(G - exact) <= 0.5 * ulp * scale * (1 + 1e-6))
+
+
 # ------------------------------------------------ planted mistakes (pins bite)
 
 def test_pins_catch_a_dropped_mean_of_coefficients(monkeypatch):
