@@ -374,17 +374,23 @@ def backward_guided(R, p_l, I_h, w1, w2, b2, r: int, eps: float, slope: float = 
 def grey_guide(I, store=None) -> np.ndarray:
     """(N, 1, h, w): the mean of an (N, n_I, h, w) guide over its channels.
 
-    ``store``: the storage type of the layer (a torch dtype) when it is
-    narrower than FP64; the grey guide is then rounded to it (through FP32,
-    round to nearest even), as the layer stores every guide it reads in its
-    storage type.
+    ``store``: the storage type of the layer (a torch dtype).  The layer
+    stores every guide it reads in that type, so the grey guide is rounded
+    to it (round to nearest even); a rounding is a quantisation, taken here
+    in the precision the layer takes it in: the channels summed in order in
+    FP32, one FP32 division by n_I, then the rounding.  Without ``store``
+    the mean is exact (FP64).
     """
     I = _f64(I)
-    G = I.mean(axis=1, keepdims=True)
-    if store is not None:
-        import torch
-        G = torch.from_numpy(G).to(torch.float32).to(store).double().numpy()
-    return G
+    if store is None:
+        return I.mean(axis=1, keepdims=True)
+    import torch
+    I32 = I.astype(np.float32)
+    s = np.zeros(I32[:, :1].shape, dtype=np.float32)
+    for k in range(I32.shape[1]):
+        s = s + I32[:, k:k + 1]
+    G = s / np.float32(I32.shape[1])
+    return torch.from_numpy(G).to(store).double().numpy()
 
 
 def forward_grey(p_l, I_l, I_h, r: int, eps: float, store=None, mean_ab: bool = True) -> np.ndarray:
