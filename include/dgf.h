@@ -220,10 +220,29 @@ void dgf_set_pipeline(int on);
  *             and Algorithm 1 print it.  Uses the warp-strip kernels for
  *             r in {1, 2} and the generic tiles otherwise; shapes are not
  *             autotuned in this mode.
+ *   guide_channels = 0 (default) or C: the guide has the output's C
+ *             channels (F the identity);
+ *   guide_channels = n_I >= 1, n_I != C: the grey guide of Sec. 6.3 (DGF_b
+ *             with differing channel counts): I_l (N x n_I x h_l x w_l) and
+ *             I_h (N x n_I x h x w) are averaged over their channels, the
+ *             mean is rounded to dt and guides every one of the C output
+ *             channels; dI_l, dI_h then have n_I channels (each the sum of
+ *             the C channels' guide gradients / n_I).  Not with a guidance
+ *             transform (g != NULL) and not in the batched or host-memory
+ *             calls.  The workspace (dgf_workspace_size_opt) adds the grey
+ *             guide repeated over the C channels at both resolutions and its
+ *             gradients; two streaming passes form the guide before the
+ *             layer and two more its gradient after it.
  */
 typedef struct {
     int mean_ab;
+    int guide_channels;
 } dgf_options;
+
+/* Workspace bytes of the _opt calls for these options (NULL = the defaults;
+ * equals dgf_workspace_size then).  0 for invalid sizes or options. */
+size_t dgf_workspace_size_opt(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt,
+                              const dgf_guide* g, const dgf_options* opt);
 
 dgf_status dgf_forward_opt(const void* p_l, const void* I_l, const void* I_h, void* O_h,
                            int N, int C, int h_l, int w_l, int h, int w, int r, float eps,

@@ -32,7 +32,7 @@ class dgf_image(ctypes.Structure):
 
 
 class dgf_options(ctypes.Structure):
-    _fields_ = [("mean_ab", ctypes.c_int)]
+    _fields_ = [("mean_ab", ctypes.c_int), ("guide_channels", ctypes.c_int)]
 
 
 class dgf_image_grad(ctypes.Structure):
@@ -67,6 +67,8 @@ _SIGS = {
                              ctypes.POINTER(dgf_guide), _P, _S, _P, ctypes.POINTER(dgf_options)]),
     "dgf_backward_opt": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _F, _I,
                               ctypes.POINTER(dgf_guide), _P, _S, _P, ctypes.POINTER(dgf_options)]),
+    "dgf_workspace_size_opt": (_S, [_I, _I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(dgf_guide),
+                                    ctypes.POINTER(dgf_options)]),
     "dgf_workspace_size_batched": (_S, [ctypes.POINTER(dgf_image), _I, _I]),
     "dgf_forward_batched": (_I, [ctypes.POINTER(dgf_image), _I, _I, _P, _S, _P]),
     "dgf_workspace_size_batched_backward": (_S, [ctypes.POINTER(dgf_image_grad), _I, _I]),
@@ -141,6 +143,10 @@ def dgf_backward_opt(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, 
                      ws_bytes, stream, opt) -> int:
     return lib().dgf_backward_opt(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps,
                                   dt, g, ws, ws_bytes, stream, opt)
+
+
+def dgf_workspace_size_opt(N, C, h_l, w_l, h, w, r, dt, g, opt) -> int:
+    return lib().dgf_workspace_size_opt(N, C, h_l, w_l, h, w, r, dt, g, opt)
 
 
 def dgf_workspace_size_batched(imgs, n, dt) -> int:

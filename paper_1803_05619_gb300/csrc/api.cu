@@ -1267,11 +1267,78 @@ dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* 
     return forward_impl(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream, true);
 }
 
+// Grey guide (Sec. 6.3): the guide's channel count when it differs from the
+// output's C (its channel mean then guides every output channel); 0 when the
+// guide has the output's channels (F the identity).
+static int grey_channels(const dgf_options* opt, int C) {
+    if (opt == nullptr) return 0;
+    const int n = opt->guide_channels;
+    return (n == 0 || n == C) ? 0 : n;
+}
+
+// Workspace of a grey-guide call: the plain layout, then the grey guide at
+// both resolutions repeated over the C output channels, then their gradients.
+struct GreyLayout {
+    size_t gl, gh, dgl, dgh, total;
+};
+
+static GreyLayout grey_layout(int N, int C, int h_l, int w_l, int h, int w, dgf_dtype dt) {
+    GreyLayout L;
+    size_t off = layout(N, C, h_l, w_l, false).total;
+    const size_t lo = (size_t)N * C * h_l * w_l * esize(dt), hi = (size_t)N * C * h * w * esize(dt);
+    L.gl = off;
+    off += align256(lo);
+    L.gh = off;
+    off += align256(hi);
+    L.dgl = off;
+    off += align256(lo);
+    L.dgh = off;
+    off += align256(hi);
+    L.total = off;
+    return L;
+}
+
+static dgf_status check_grey(int n_in, int N, const dgf_guide* g) {
+    if (n_in < 1) return fail(DGF_ERR_INVALID, "guide_channels = %d < 0", n_in);
+    if ((long long)N * n_in > 65535) return fail(DGF_ERR_UNSUPPORTED, "N*guide_channels > 65535 planes");
+    if (g != nullptr) return fail(DGF_ERR_INVALID, "a grey guide and a guidance transform exclude each other");
+    return DGF_OK;
+}
+
+static dgf_status forward_grey(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
+                               int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
+                               void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab, int n_in) {
+    dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
+    if (st != DGF_OK) return st;
+    if ((st = check_grey(n_in, N, g)) != DGF_OK) return st;
+    if (N == 0) return DGF_OK;
+    if (p_l == nullptr || I_l == nullptr || I_h == nullptr || O_h == nullptr)
+        return fail(DGF_ERR_INVALID, "NULL input or output pointer");
+    const GreyLayout gl = grey_layout(N, C, h_l, w_l, h, w, dt);
+    if ((st = check_ws(workspace, ws_bytes, gl.total)) != DGF_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    Launcher L(s);
+    cudaError_t e = L.run("grey_guide", [&] {
+        return launch_grey_mean(dt, I_l, ws + gl.gl, N, n_in, C, (size_t)h_l * w_l, s);
+    });
+    if (e == cudaSuccess)
+        e = L.run("grey_guide", [&] { return launch_grey_mean(dt, I_h, ws + gl.gh, N, n_in, C, (size_t)h * w, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "grey guide");
+    return forward_impl(p_l, ws + gl.gl, ws + gl.gh, O_h, N, C, h_l, w_l, h, w, r, eps, dt, nullptr, workspace,
+                        ws_bytes, stream, mean_ab);
+}
+
 dgf_status dgf_forward_opt(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
                            int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
                            void* workspace, size_t ws_bytes, dgf_stream_t stream, const dgf_options* opt) {
+    const bool mean_ab = opt == nullptr || opt->mean_ab != 0;
+    const int n_in = grey_channels(opt, C);
+    if (n_in != 0)
+        return forward_grey(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream,
+                            mean_ab, n_in);
     return forward_impl(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream,
-                        opt == nullptr || opt->mean_ab != 0);
+                        mean_ab);
 }
 
 dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l, void* dI_l,
@@ -1281,12 +1348,70 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
                          ws_bytes, stream, true);
 }
 
+static dgf_status backward_grey(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l,
+                                void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w,
+                                int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
+                                size_t ws_bytes, dgf_stream_t stream, bool mean_ab, int n_in) {
+    dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
+    if (st != DGF_OK) return st;
+    if ((st = check_grey(n_in, N, g)) != DGF_OK) return st;
+    if (dW != nullptr) return fail(DGF_ERR_INVALID, "dW needs a guidance transform");
+    if (N == 0 || (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr)) return DGF_OK;
+    if (dO_h == nullptr || p_l == nullptr || I_l == nullptr || I_h == nullptr)
+        return fail(DGF_ERR_INVALID, "NULL input pointer");
+    const GreyLayout gl = grey_layout(N, C, h_l, w_l, h, w, dt);
+    if ((st = check_ws(workspace, ws_bytes, gl.total)) != DGF_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    {
+        Launcher L(s);
+        cudaError_t e = L.run("grey_guide", [&] {
+            return launch_grey_mean(dt, I_l, ws + gl.gl, N, n_in, C, (size_t)h_l * w_l, s);
+        });
+        if (e == cudaSuccess)
+            e = L.run("grey_guide",
+                      [&] { return launch_grey_mean(dt, I_h, ws + gl.gh, N, n_in, C, (size_t)h * w, s); });
+        if (e != cudaSuccess) return cuda_fail(e, "grey guide");
+    }
+    // Algorithm 1 per output channel with the repeated grey guide, its guide
+    // gradients into the workspace, then their sum over the channels / n_I
+    st = backward_impl(dO_h, p_l, ws + gl.gl, ws + gl.gh, dp_l, dI_l ? ws + gl.dgl : nullptr,
+                       dI_h ? ws + gl.dgh : nullptr, nullptr, N, C, h_l, w_l, h, w, r, eps, dt, nullptr, workspace,
+                       ws_bytes, stream, mean_ab);
+    if (st != DGF_OK) return st;
+    Launcher L(s);
+    cudaError_t e = cudaSuccess;
+    if (dI_l != nullptr)
+        e = L.run("grey_guide_adjoint", [&] {
+            return launch_grey_adjoint(dt, ws + gl.dgl, dI_l, N, n_in, C, (size_t)h_l * w_l, s);
+        });
+    if (e == cudaSuccess && dI_h != nullptr)
+        e = L.run("grey_guide_adjoint",
+                  [&] { return launch_grey_adjoint(dt, ws + gl.dgh, dI_h, N, n_in, C, (size_t)h * w, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "grey guide adjoint");
+    return DGF_OK;
+}
+
 dgf_status dgf_backward_opt(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l,
                             void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w, int r,
                             float eps, dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes,
                             dgf_stream_t stream, const dgf_options* opt) {
+    const bool mean_ab = opt == nullptr || opt->mean_ab != 0;
+    const int n_in = grey_channels(opt, C);
+    if (n_in != 0)
+        return backward_grey(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g,
+                             workspace, ws_bytes, stream, mean_ab, n_in);
     return backward_impl(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace,
-                         ws_bytes, stream, opt == nullptr || opt->mean_ab != 0);
+                         ws_bytes, stream, mean_ab);
+}
+
+size_t dgf_workspace_size_opt(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt, const dgf_guide* g,
+                              const dgf_options* opt) {
+    if (check_sizes(N, C, h_l, w_l, h, w, r, 1.f, dt) != DGF_OK) return 0;
+    const int n_in = grey_channels(opt, C);
+    if (n_in == 0) return layout(N, C, h_l, w_l, g != nullptr).total;
+    if (check_grey(n_in, N, g) != DGF_OK) return 0;
+    return grey_layout(N, C, h_l, w_l, h, w, dt).total;
 }
 
 extern "C" size_t dgf_workspace_size_batched(const dgf_image* imgs, int n, dgf_dtype dt) {

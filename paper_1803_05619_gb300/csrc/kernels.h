@@ -103,6 +103,15 @@ cudaError_t launch_k6(dgf_dtype dt, const float2* coef, const float* dG_l, const
                       cudaStream_t s);
 cudaError_t launch_wreduce(const float* partials, int nblocks, float* dW, int hidden, cudaStream_t s);
 
+// Grey guide (channel mean of an n_in-channel guide, Sec. 6.3): G (N x C
+// planes) = the mean of I's n_in planes of each image, repeated C times; and
+// its adjoint d I (N x n_in planes) = the sum of d G's C planes / n_in,
+// repeated n_in times.  `plane` = pixels per plane.
+cudaError_t launch_grey_mean(dgf_dtype dt, const void* I, void* G, int N, int n_in, int C, size_t plane,
+                             cudaStream_t s);
+cudaError_t launch_grey_adjoint(dgf_dtype dt, const void* dG, void* dI, int N, int n_in, int C, size_t plane,
+                                cudaStream_t s);
+
 // Column-walking low-resolution kernels, one translation unit per radius.
 template <int R>
 cudaError_t launch_k1_fast(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes,

@@ -64,12 +64,25 @@ def _guide_struct(w1, w2, b2, slope):
     return L.dgf_guide(w1.data_ptr(), w2.data_ptr(), b2.data_ptr(), hidden, float(slope))
 
 
-def _sizes(p_l, I_h):
-    N, C, h, w = I_h.shape
+def _sizes(p_l, I_h, grey_ok=False):
+    """(N, C, h_l, w_l, h, w) with C the output's channels; with grey_ok the
+    guide may have another channel count (its channel mean is the guide)."""
+    N, n_I, h, w = I_h.shape
     h_l, w_l = p_l.shape[2], p_l.shape[3]
-    if p_l.shape[0] != N or p_l.shape[1] != C:
+    C = p_l.shape[1]
+    if p_l.shape[0] != N or (C != n_I and not grey_ok):
         raise ValueError("p_l and I_h disagree on N or C")
     return N, C, h_l, w_l, h, w
+
+
+def _options(mean_ab, C, I_h, g):
+    """dgf_options for the call, or None for the defaults."""
+    n_I = I_h.shape[1]
+    if n_I != C and g is not None:
+        raise ValueError("a grey guide (guide channels != output channels) excludes the guidance transform")
+    if mean_ab and n_I == C:
+        return None
+    return L.dgf_options(1 if mean_ab else 0, n_I if n_I != C else 0)
 
 
 def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2, out=None,
@@ -77,22 +90,22 @@ def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slo
     """O_h of the fast guided filtering layer (Eq. 1-2, box mean of A and b;
     mean_ab=False: A_l, b_l upsampled directly, the layer as printed)."""
     dev = _check(p_l, I_l, I_h, w1, w2, b2)
-    N, C, h_l, w_l, h, w = _sizes(p_l, I_h)
+    N, C, h_l, w_l, h, w = _sizes(p_l, I_h, grey_ok=True)
     dt = dtype_code(I_h)
     if p_l.dtype != I_h.dtype or (I_l is not None and I_l.dtype != I_h.dtype):
         raise TypeError("p_l, I_l and I_h must share one dtype")
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
+    opt = _options(mean_ab, C, I_h, g)
     if out is None:
-        out = torch.empty_like(I_h)
-    nb = L.dgf_workspace_size(N, C, h_l, w_l, h, w, r, dt, gp)
-    ws = workspace(nb, dev)
+        out = torch.empty((N, C, h, w), dtype=I_h.dtype, device=I_h.device)
     with torch.cuda.device(dev):
-        if mean_ab:
+        if opt is None:
+            ws = workspace(L.dgf_workspace_size(N, C, h_l, w_l, h, w, r, dt, gp), dev)
             L.check(L.dgf_forward(_ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(out), N, C, h_l, w_l, h, w, r,
                                   float(eps), dt, gp, _ptr(ws), ws.numel(), _stream(dev)))
         else:
-            opt = L.dgf_options(0)
+            ws = workspace(L.dgf_workspace_size_opt(N, C, h_l, w_l, h, w, r, dt, gp, ctypes.byref(opt)), dev)
             L.check(L.dgf_forward_opt(_ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(out), N, C, h_l, w_l, h, w, r,
                                       float(eps), dt, gp, _ptr(ws), ws.numel(), _stream(dev), ctypes.byref(opt)))
     return out
@@ -102,26 +115,26 @@ def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=No
                 need_p=True, need_Il=True, need_Ih=True, need_w=True, mean_ab=True):
     """(dp_l, dI_l, dI_h, (dw1, dw2, db2)) by the library's adjoint kernels."""
     dev = _check(dO_h, p_l, I_l, I_h, w1, w2, b2)
-    N, C, h_l, w_l, h, w = _sizes(p_l, I_h)
+    N, C, h_l, w_l, h, w = _sizes(p_l, I_h, grey_ok=True)
     dt = dtype_code(I_h)
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
+    opt = _options(mean_ab, C, I_h, g)
     dO_h = dO_h.to(I_h.dtype).contiguous()
     dp = torch.empty_like(p_l) if need_p else None
-    dIl = torch.empty_like(p_l) if (need_Il and g is None) else None
+    dIl = torch.empty_like(I_l) if (need_Il and g is None) else None
     dIh = torch.empty_like(I_h) if need_Ih else None
     dW = None
     if g is not None and need_w:
         dW = torch.empty(6 * g.hidden + 3, dtype=torch.float32, device=dev)
-    nb = L.dgf_workspace_size(N, C, h_l, w_l, h, w, r, dt, gp)
-    ws = workspace(nb, dev)
     with torch.cuda.device(dev):
-        if mean_ab:
+        if opt is None:
+            ws = workspace(L.dgf_workspace_size(N, C, h_l, w_l, h, w, r, dt, gp), dev)
             L.check(L.dgf_backward(_ptr(dO_h), _ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(dp), _ptr(dIl),
                                    _ptr(dIh), _ptr(dW), N, C, h_l, w_l, h, w, r, float(eps), dt, gp,
                                    _ptr(ws), ws.numel(), _stream(dev)))
         else:
-            opt = L.dgf_options(0)
+            ws = workspace(L.dgf_workspace_size_opt(N, C, h_l, w_l, h, w, r, dt, gp, ctypes.byref(opt)), dev)
             L.check(L.dgf_backward_opt(_ptr(dO_h), _ptr(p_l), _ptr(I_l), _ptr(I_h), _ptr(dp), _ptr(dIl),
                                        _ptr(dIh), _ptr(dW), N, C, h_l, w_l, h, w, r, float(eps), dt, gp,
                                        _ptr(ws), ws.numel(), _stream(dev), ctypes.byref(opt)))

@@ -142,3 +142,31 @@ def test_host_step_validation(lib):
     nothing = L.dgf_host_step_io(16, 32, 48, None, None, None, None, None)
     assert L.dgf_host_step(ctypes.byref(nothing), 2, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 0, None, 0, None) == 0
     assert L.dgf_host_step(ctypes.byref(io), 0, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 0, None, 0, None) == 0
+
+
+def test_grey_guide_options_on_host(lib):
+    """Grey-guide options: workspace sizes and argument checks run on the host."""
+    plain = L.dgf_workspace_size(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None)
+    same = L.dgf_options(1, 1)  # guide_channels == C: the plain layer
+    assert L.dgf_workspace_size_opt(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None, ctypes.byref(same)) == plain
+    assert L.dgf_workspace_size_opt(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None, None) == plain
+    grey = L.dgf_options(1, 3)
+    nb = L.dgf_workspace_size_opt(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None, ctypes.byref(grey))
+    # the grey guide and its gradient at both resolutions, repeated over C = 1 output channel
+    assert nb >= plain + 2 * (2 * 64 * 80 * 2 + 2 * 16 * 20 * 2) and nb % 256 == 0
+    assert L.dgf_workspace_size_opt(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None,
+                                    ctypes.byref(L.dgf_options(1, -2))) == 0
+    gd = L.dgf_guide(16, 32, 48, 16, 0.2)
+    assert L.dgf_workspace_size_opt(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, ctypes.byref(gd),
+                                    ctypes.byref(grey)) == 0
+    ptr = ctypes.c_void_p(256)
+    st = L.dgf_forward_opt(ptr, ptr, ptr, ptr, 2, 1, 16, 20, 64, 80, 1, 1e-3, L.DGF_BF16, ctypes.byref(gd),
+                           None, 0, None, ctypes.byref(grey))
+    assert st == 1 and "exclude" in L.dgf_last_error()
+    st = L.dgf_forward_opt(ptr, ptr, ptr, ptr, 2, 1, 16, 20, 64, 80, 1, 1e-3, L.DGF_BF16, None,
+                           None, 0, None, ctypes.byref(grey))
+    assert st == 5  # workspace missing
+    dW = ctypes.c_void_p(512)
+    st = L.dgf_backward_opt(ptr, ptr, ptr, ptr, ptr, ptr, ptr, ctypes.cast(dW, ctypes.POINTER(ctypes.c_float)),
+                            2, 1, 16, 20, 64, 80, 1, 1e-3, L.DGF_BF16, None, None, 0, None, ctypes.byref(grey))
+    assert st == 1 and "dW" in L.dgf_last_error()

@@ -313,6 +313,39 @@ def test_paper_literal_variant_parity(case, dtype):
         assert not torch.equal(out, gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps))
 
 
+# grey guide (Sec. 6.3, DGF_b with differing channel counts): kind, N, guide
+# channels, output channels, h_l, w_l, h, w, r, eps, mean_ab
+GREY_CASES = [("photo", 2, 3, 1, 40, 50, 160, 200, 1, 1e-3, True),     # RGB guide, one output channel
+              ("photo", 1, 3, 1, 45, 70, 360, 560, 2, 1e-3, True),     # f = 8, r = 2
+              ("photo", 2, 1, 3, 30, 33, 120, 132, 1, 1e-2, True),     # one guide channel, three outputs
+              ("ragged", 1, 3, 2, 37, 53, 150, 211, 1, 1e-3, True),    # non-integer ratio, odd width
+              ("photo", 1, 3, 1, 20, 24, 80, 96, 1, 1e-3, False)]      # the layer as printed
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16, F16], ids=["f32", "bf16", "f16"])
+@pytest.mark.parametrize("case", GREY_CASES, ids=_ids(GREY_CASES))
+def test_grey_guide_parity(case, dtype):
+    kind, N, n_in, C, hl, wl, h, w, r, eps, mean_ab = case
+    gsrc = to_storage(make_case(kind, 400 + r, N, n_in, hl, wl, h, w), dtype)
+    psrc = to_storage(make_case(kind, 410 + r, N, C, hl, wl, h, w), dtype)
+    p_l, I_l, I_h = psrc["p_l"], gsrc["I_l"], gsrc["I_h"]
+    R = synth.upstream_grad(11, (N, C, h, w)).to(dtype)
+    out = gf_forward(p_l.cuda(), I_l.cuda(), I_h.cuda(), r, eps, mean_ab=mean_ab)
+    dp, dIl, dIh, _ = gf_backward(R.cuda(), p_l.cuda(), I_l.cuda(), I_h.cuda(), r, eps, mean_ab=mean_ab)
+    torch.cuda.synchronize()
+    assert out.shape == (N, C, h, w) and dIl.shape == I_l.shape and dIh.shape == I_h.shape
+    ref = O.forward_grey(f64(p_l), f64(I_l), f64(I_h), r, eps, store=dtype, mean_ab=mean_ab)
+    assert_fwd(f64(out), ref, dtype, eps)
+    rp, rIl, rIh = O.backward_grey(f64(R), f64(p_l), f64(I_l), f64(I_h), r, eps, store=dtype, mean_ab=mean_ab)
+    assert_grad(f64(dp), rp, dtype, "dp_l")
+    assert_grad(f64(dIl), rIl, dtype, "dI_l")
+    assert_grad(f64(dIh), rIh, dtype, "dI_h")
+    # every guide channel receives the same gradient
+    for k in range(1, n_in):
+        assert torch.equal(dIh[:, k], dIh[:, 0]) and torch.equal(dIl[:, k], dIl[:, 0])
+    assert L.dgf_device_status() == 0
+
+
 def test_paper_literal_guided_parity():
     N, C, hl, wl, f, r, eps = 1, 3, 24, 32, 4, 2, 1e-3
     st = {k: v.to(BF16) for k, v in synth.photo_like(61, N, C, hl, wl, f).items()}
