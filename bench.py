@@ -550,6 +550,7 @@ def main():
             line["guided_train_8x2048"] = bench_guided(args, device)
             line["small_fp32_1x1x256"] = bench_small(args, device)
             line["paper_literal_fp32_plain"] = bench_paper_literal(args, device)
+            line["grey_guide_fp32"] = bench_grey(args, device)
         if not args.no_oracle:
             reps = 15
             cv, csec = cpu_oracle(spec, reps=reps)
@@ -679,6 +680,55 @@ def bench_paper_literal(args, device):
     return {"workload": MAIN + " with mean_ab=0", "fwd_bwd_mpix_s": round(N * h * w / (ms * 1e-3) / 1e6, 1),
             "ms_fwd_bwd": round(ms, 4),
             "note": "through the Python binding (allocates outputs and workspace per call)"}
+
+
+def bench_grey(args, device):
+    """Grey guide (Sec. 6.3, DGF_b with differing channel counts): an RGB guide
+    and a one-channel output, FP32 4 x (3 -> 1) x 512^2 -> 2048^2, r = 1,
+    eps = 1e-4; forward and forward + backward through the library."""
+    import synth
+    from paper_1803_05619_gb300 import _lib as L
+    from paper_1803_05619_gb300.layer import gf_backward, gf_forward
+    N, n_in, C, hl, f, r, eps = 4, 3, 1, 512, 4, 1, 1e-4
+    gd = synth.blobs_tone_curve(31, N, n_in, hl, hl, f)
+    pd = synth.blobs_tone_curve(32, N, C, hl, hl, f)
+    p_l, I_l, I_h = (x.float().to(device) for x in (pd["p_l"], gd["I_l"], gd["I_h"]))
+    R = synth.upstream_grad(33, (N, C, hl * f, hl * f)).float().to(device)
+    h = w = hl * f
+
+    def fwd():
+        gf_forward(p_l, I_l, I_h, r, eps)
+
+    def step():
+        gf_forward(p_l, I_l, I_h, r, eps)
+        gf_backward(R, p_l, I_l, I_h, r, eps)
+
+    steps = max(10, min(args.steps // 10, 200))
+    fwd_ms = time_loop(fwd, steps, max(3, args.warmup // 4), 1, device)
+    ms = time_loop(step, steps, max(3, args.warmup // 4), 1, device)
+    L.dgf_profile_reset()
+    L.dgf_profile_enable(True)
+    try:
+        step()
+        import torch
+        torch.cuda.synchronize()
+        prof = L.dgf_profile_read()
+    finally:
+        L.dgf_profile_enable(False)
+    hi, lo = h * w * 4, hl * hl * 4
+    # algorithmic bytes: forward reads I_h (3 channels), I_l (3), p_l and writes O_h;
+    # backward reads dO_h, I_h (3), p_l, I_l (3) and writes dI_h (3), dp_l, dI_l (3)
+    fwd_b = N * (n_in * hi + n_in * lo + C * lo + C * hi)
+    bwd_b = N * (C * hi + n_in * hi + C * lo + n_in * lo + n_in * hi + C * lo + n_in * lo)
+    peak = peaks()[0]
+    return {"workload": "grey_guide_fp32_4x(3->1)x512->2048 (r=1, eps=1e-4)",
+            "fwd_mpix_s": round(N * h * w / (fwd_ms * 1e-3) / 1e6, 1), "ms_fwd": round(fwd_ms, 4),
+            "fwd_bwd_mpix_s": round(N * h * w / (ms * 1e-3) / 1e6, 1), "ms_fwd_bwd": round(ms, 4),
+            "fwd_frac_of_measured_hbm": round(fwd_b / (fwd_ms * 1e-3) / 1e9 / peak, 4),
+            "fwd_bwd_frac_of_measured_hbm": round((fwd_b + bwd_b) / (ms * 1e-3) / 1e9 / peak, 4),
+            "kernels_avg_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in prof.items()},
+            "note": "through the Python binding (allocates outputs and workspace per call); the grey guide "
+                    "is formed by a streaming pass before the layer and its gradient by one after it"}
 
 
 def bench_guided(args, device):
