@@ -19,6 +19,8 @@ What it computes (Wu et al., "Fast End-to-End Trainable Guided Filter"):
 * Sec. 3.4 - the guidance transform F: 1x1 conv, leaky ReLU (slope 0.2),
   1x1 conv, applied per pixel; with it the low-resolution guide is the
   f x f block mean of F(I_h).
+* Sec. 3.4, read literally - F applied to each resolution on its own:
+  G_l = F(I_l), G_h = F(I_h) (``forward_guided_separate``).
 * Sec. 6.3 (DGF_b) - when the guide and the output differ in channel count,
   F is the mean over the guide's channels (a grey guide), used for every
   output channel.
@@ -57,6 +59,8 @@ __all__ = [
     "block_mean",
     "forward_guided",
     "backward_guided",
+    "forward_guided_separate",
+    "backward_guided_separate",
     "grey_guide",
     "forward_grey",
     "backward_grey",
@@ -365,6 +369,64 @@ def backward_guided(R, p_l, I_h, w1, w2, b2, r: int, eps: float, slope: float = 
         dw1 += np.einsum("khw,chw->kc", dZ, I_h[n])
         dI[n] = np.einsum("kc,khw->chw", w1, dZ)
     return dp, dI, dw1, dw2, db2
+
+
+def forward_guided_separate(p_l, I_l, I_h, w1, w2, b2, r: int, eps: float, slope: float = 0.2,
+                            mean_ab: bool = True) -> np.ndarray:
+    """O_h with the transform applied to each guide: G_l = F(I_l), G_h = F(I_h)."""
+    p_l, I_l, I_h = _f64(p_l), _f64(I_l), _f64(I_h)
+    w1, w2, b2 = _f64(w1), _f64(w2), _f64(b2)
+    N, C = I_h.shape[:2]
+    out = np.full(I_h.shape, np.nan)
+    for n in range(N):
+        G_h, _ = guide_apply(I_h[n], w1, w2, b2, slope)
+        G_l, _ = guide_apply(I_l[n], w1, w2, b2, slope)
+        for c in range(C):
+            out[n, c] = forward_plane(p_l[n, c], G_l[c], G_h[c], r, eps, mean_ab)
+    return out
+
+
+def _guide_adjoint(I, Z, dG, w1, w2, slope):
+    """d I, d w1, d w2, d b2 of a loss through G = F(I), given d G (C, h, w)."""
+    H = np.where(Z > 0.0, Z, slope * Z)
+    dw2 = np.einsum("chw,khw->ck", dG, H)
+    db2 = dG.sum(axis=(1, 2))
+    dH = np.einsum("ck,chw->khw", w2, dG)
+    dZ = dH * np.where(Z > 0.0, 1.0, slope)
+    dw1 = np.einsum("khw,chw->kc", dZ, I)
+    dI = np.einsum("kc,khw->chw", w1, dZ)
+    return dI, dw1, dw2, db2
+
+
+def backward_guided_separate(R, p_l, I_l, I_h, w1, w2, b2, r: int, eps: float, slope: float = 0.2,
+                             mean_ab: bool = True):
+    """(dp_l, dI_l, dI_h, dw1, dw2, db2) of sum(O_h * R) with G_l = F(I_l), G_h = F(I_h).
+
+    Algorithm 1 per channel gives d G_l and d G_h; each goes back through the
+    transform of its own resolution (the last line, d I = d G . grad F), and
+    the weight gradients add the two resolutions' terms.
+    """
+    R, p_l, I_l, I_h = _f64(R), _f64(p_l), _f64(I_l), _f64(I_h)
+    w1, w2, b2 = _f64(w1), _f64(w2), _f64(b2)
+    N, C = I_h.shape[:2]
+    dp = np.full(p_l.shape, np.nan)
+    dIl = np.full(I_l.shape, np.nan)
+    dIh = np.full(I_h.shape, np.nan)
+    dw1, dw2, db2 = np.zeros_like(w1), np.zeros_like(w2), np.zeros_like(b2)
+    for n in range(N):
+        G_h, Z_h = guide_apply(I_h[n], w1, w2, b2, slope)
+        G_l, Z_l = guide_apply(I_l[n], w1, w2, b2, slope)
+        dG_l = np.zeros_like(G_l)
+        dG_h = np.zeros_like(G_h)
+        for c in range(C):
+            dp[n, c], dG_l[c], dG_h[c] = backward_plane(R[n, c], p_l[n, c], G_l[c], G_h[c], r, eps, mean_ab)
+        for I, Z, dG, dI in ((I_h[n], Z_h, dG_h, dIh), (I_l[n], Z_l, dG_l, dIl)):
+            gI, g1, g2, gb = _guide_adjoint(I, Z, dG, w1, w2, slope)
+            dI[n] = gI
+            dw1 += g1
+            dw2 += g2
+            db2 += gb
+    return dp, dIl, dIh, dw1, dw2, db2
 
 
 # --------------------------------------------------------------------------

@@ -326,6 +326,66 @@ def test_guided_backward_finite_differences():
     assert np.max(np.abs(db2)) < 1e-12  # guide-shift invariance
 
 
+# ------------------------------- the transform applied to each guide (F(I_l))
+
+@pytest.mark.parametrize("mean_ab", [True, False])
+def test_guided_separate_matches_torch(mean_ab):
+    N, C, f, hl, wl, r, eps = 2, 3, 4, 5, 4, 1, 1e-3
+    d = synth.photo_like(45, N, C, hl, wl, f)
+    g = synth.guide_weights(7)
+    R = synth.upstream_grad(8, d["I_h"].shape)
+    out = O.forward_guided_separate(d["p_l"], d["I_l"], d["I_h"], g["w1"], g["w2"], g["b2"], r, eps,
+                                    mean_ab=mean_ab)
+    ts = {k: v.clone().requires_grad_(True) for k, v in (("p", d["p_l"]), ("il", d["I_l"]), ("ih", d["I_h"]),
+                                                         ("w1", g["w1"]), ("w2", g["w2"]), ("b2", g["b2"]))}
+    ref = TC.gf_guided_separate(ts["p"], ts["il"], ts["ih"], ts["w1"], ts["w2"], ts["b2"], r, eps,
+                                mean_ab=mean_ab)
+    np.testing.assert_allclose(out, ref.detach().numpy(), rtol=0, atol=1e-12)
+    (ref * R).sum().backward()
+    got = O.backward_guided_separate(R, d["p_l"], d["I_l"], d["I_h"], g["w1"], g["w2"], g["b2"], r, eps,
+                                     mean_ab=mean_ab)
+    for a, k in zip(got[:5], ("p", "il", "ih", "w1", "w2")):
+        b = ts[k].grad.numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-10, k
+    # a constant added to both guides is absorbed by b, so d b2 vanishes here too
+    assert np.max(np.abs(got[5])) < 1e-12 and np.max(np.abs(ts["b2"].grad.numpy())) < 1e-12
+
+
+def test_guided_separate_equals_block_mean_form_on_blocky_guides():
+    """With I_h constant on every f x f block and I_l its block values, F(I_l) is the block mean of F(I_h)."""
+    N, C, f, hl, wl, r, eps = 1, 3, 4, 6, 5, 1, 1e-3
+    d = synth.photo_like(46, N, C, hl, wl, f)
+    I_l = d["I_l"]
+    I_h = I_l.repeat_interleave(f, dim=2).repeat_interleave(f, dim=3)
+    g = synth.guide_weights(9)
+    a = O.forward_guided_separate(d["p_l"], I_l, I_h, g["w1"], g["w2"], g["b2"], r, eps)
+    b = O.forward_guided(d["p_l"], I_h, g["w1"], g["w2"], g["b2"], r, eps)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_guided_separate_finite_differences():
+    C, f, hl, wl, r, eps = 3, 4, 4, 4, 1, 1e-2
+    d = synth.photo_like(47, 1, C, hl, wl, f)
+    Il, Ih = d["I_l"].numpy().copy(), d["I_h"].numpy().copy()
+    for seed in range(5, 200):  # away from the leaky-ReLU kink at both resolutions
+        g = {k: v.numpy().copy() for k, v in synth.guide_weights(seed).items()}
+        zh = O.guide_apply(Ih[0], g["w1"], g["w2"], g["b2"])[1]
+        zl = O.guide_apply(Il[0], g["w1"], g["w2"], g["b2"])[1]
+        if min(np.min(np.abs(zh)), np.min(np.abs(zl))) > 1e-4:
+            break
+    P = d["p_l"].numpy().copy()
+    R = synth.upstream_grad(10, Ih.shape).numpy()
+    _, dIl, dIh, dw1, dw2, _ = O.backward_guided_separate(R, P, Il, Ih, g["w1"], g["w2"], g["b2"], r, eps)
+
+    def loss():
+        return float(np.sum(O.forward_guided_separate(P, Il, Ih, g["w1"], g["w2"], g["b2"], r, eps) * R))
+
+    assert _fd_check(loss, Il, dIl) < 1e-6
+    assert _fd_check(loss, Ih, dIh, n_probe=32) < 1e-6
+    assert _fd_check(loss, g["w1"], dw1) < 1e-6
+    assert _fd_check(loss, g["w2"], dw2) < 1e-6
+
+
 # ---------------------------------- the layer as printed (no mean of A, b)
 
 @pytest.mark.parametrize("case", CASES)

@@ -58,3 +58,8 @@ def gf_guided(p_l, I_h, w1, w2, b2, r: int, eps: float, slope=0.2, mean_ab: bool
     G_h = guide(I_h, w1, w2, b2, slope)
     G_l = F.avg_pool2d(G_h, f, stride=f)
     return gf(p_l, G_l, G_h, r, eps, mean_ab)
+
+
+def gf_guided_separate(p_l, I_l, I_h, w1, w2, b2, r: int, eps: float, slope=0.2, mean_ab: bool = True):
+    """The transform applied to each guide on its own: G_l = F(I_l), G_h = F(I_h)."""
+    return gf(p_l, guide(I_l, w1, w2, b2, slope), guide(I_h, w1, w2, b2, slope), r, eps, mean_ab)
