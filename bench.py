@@ -777,6 +777,16 @@ def bench_guided(args, device):
                            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (unit counts and "
                                           "maximum SM clock)",
                            "algorithmic_flops": flops, "us_per_call": round(avg["k6_guide_bwd"], 1)}
+
+    # the same step with the transform applied to each guide on its own
+    # (G_l = F(I_l), I_l the block mean of I_h): K5L and K6L replace K5's
+    # high-res read and K6's low-res term
+    def step_low():
+        gf_forward(g["p_l"], g["I_l"], g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2, guide_low=True)
+        gf_backward(R, g["p_l"], g["I_l"], g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2, guide_low=True)
+
+    ms_low = time_loop(step_low, steps, max(3, args.warmup // 4), 1, device)
+    out["guide_low"] = {"fwd_bwd_mpix_s": round(pix / (ms_low * 1e-3) / 1e6, 1), "ms_fwd_bwd": round(ms_low, 4)}
     return out
 
 

@@ -233,10 +233,18 @@ void dgf_set_pipeline(int on);
  *             guide repeated over the C channels at both resolutions and its
  *             gradients; two streaming passes form the guide before the
  *             layer and two more its gradient after it.
+ *   guide_low = 0 (default): with a guidance transform (g != NULL) the
+ *             low-res guide is the f x f block mean of F(I_h) and I_l is not
+ *             read;
+ *   guide_low = 1: F applied to each guide on its own, G_l = F(I_l) and
+ *             G_h = F(I_h) (Sec. 3.4 read literally).  Needs g and I_l
+ *             (N x 3 x h_l x w_l); the backward may then return dI_l (through
+ *             F at low resolution), and dW adds the low-res pixels' terms.
  */
 typedef struct {
     int mean_ab;
     int guide_channels;
+    int guide_low;
 } dgf_options;
 
 /* Workspace bytes of the _opt calls for these options (NULL = the defaults;

@@ -32,7 +32,7 @@ class dgf_image(ctypes.Structure):
 
 
 class dgf_options(ctypes.Structure):
-    _fields_ = [("mean_ab", ctypes.c_int), ("guide_channels", ctypes.c_int)]
+    _fields_ = [("mean_ab", ctypes.c_int), ("guide_channels", ctypes.c_int), ("guide_low", ctypes.c_int)]
 
 
 class dgf_image_grad(ctypes.Structure):

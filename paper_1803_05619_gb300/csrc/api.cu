@@ -945,12 +945,14 @@ size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r, d
 
 static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
                                int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
-                               void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab) {
+                               void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab,
+                               bool guide_low = false) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
+    if (guide_low && g == nullptr) return fail(DGF_ERR_INVALID, "guide_low needs a guidance transform");
     if (N == 0) return DGF_OK;
-    if (p_l == nullptr || I_h == nullptr || O_h == nullptr || (g == nullptr && I_l == nullptr))
+    if (p_l == nullptr || I_h == nullptr || O_h == nullptr || ((g == nullptr || guide_low) && I_l == nullptr))
         return fail(DGF_ERR_INVALID, "NULL input or output pointer");
     const Layout lay = layout(N, C, h_l, w_l, g != nullptr);
     if ((st = check_ws(workspace, ws_bytes, lay.total)) != DGF_OK) return st;
@@ -1027,7 +1029,10 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
     if (!aligned16({I_h, O_h})) return fail(DGF_ERR_UNSUPPORTED, "guidance transform needs 16-byte aligned I_h, O_h");
     e = guide_upload(g->w1, g->w2, g->b2, g->hidden, s);
     if (e != cudaSuccess) return cuda_fail(e, "guide weights");
-    e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
+    if (guide_low)
+        e = L.run("k5_guide_low", [&] { return launch_k5_low(dt, I_l, G_l, N, h_l, w_l, g->slope, s); });
+    else
+        e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
     if (e != cudaSuccess) return cuda_fail(e, "k5");
     e = run_k1(L, dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
     if (e != cudaSuccess) return cuda_fail(e, "k1");
@@ -1186,11 +1191,13 @@ static dgf_status backward_pipelined(dgf_dtype dt, const void* dO_h, const void*
 static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l,
                                 void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w,
                                 int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
-                                size_t ws_bytes, dgf_stream_t stream, bool mean_ab) {
+                                size_t ws_bytes, dgf_stream_t stream, bool mean_ab, bool guide_low = false) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
-    if (g != nullptr && dI_l != nullptr) return fail(DGF_ERR_INVALID, "dI_l must be NULL with a guidance transform");
+    if (guide_low && g == nullptr) return fail(DGF_ERR_INVALID, "guide_low needs a guidance transform");
+    if (g != nullptr && dI_l != nullptr && !guide_low)
+        return fail(DGF_ERR_INVALID, "dI_l must be NULL with a guidance transform (unless guide_low)");
     if (g == nullptr && dW != nullptr) return fail(DGF_ERR_INVALID, "dW needs a guidance transform");
     if (N == 0) {
         if (g != nullptr && dW != nullptr) {
@@ -1200,7 +1207,7 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
         }
         return DGF_OK;
     }
-    if (dO_h == nullptr || p_l == nullptr || I_h == nullptr || (g == nullptr && I_l == nullptr))
+    if (dO_h == nullptr || p_l == nullptr || I_h == nullptr || ((g == nullptr || guide_low) && I_l == nullptr))
         return fail(DGF_ERR_INVALID, "NULL input pointer");
     const Layout lay = layout(N, C, h_l, w_l, g != nullptr);
     if ((st = check_ws(workspace, ws_bytes, lay.total)) != DGF_OK) return st;
@@ -1228,11 +1235,17 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
     float* dG_l = reinterpret_cast<float*>(ws + lay.dgl);
     float* partials = reinterpret_cast<float*>(ws + lay.partials);
     const bool need_hi = dI_h != nullptr || dW != nullptr;
+    // with F applied to I_l, d G_l goes back through F at low resolution (K6L)
+    // instead of into K6's d G_h
+    const bool need_lo = guide_low && (dI_l != nullptr || dW != nullptr);
     if (!aligned16({dO_h, I_h, dI_h}))
         return fail(DGF_ERR_UNSUPPORTED, "guidance transform needs 16-byte aligned dO_h, I_h, dI_h");
     e = guide_upload(g->w1, g->w2, g->b2, g->hidden, s);
     if (e != cudaSuccess) return cuda_fail(e, "guide weights");
-    e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
+    if (guide_low)
+        e = L.run("k5_guide_low", [&] { return launch_k5_low(dt, I_l, G_l, N, h_l, w_l, g->slope, s); });
+    else
+        e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
     if (e != cudaSuccess) return cuda_fail(e, "k5");
     e = run_k1(L, dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
     if (e != cudaSuccess) return cuda_fail(e, "k1");
@@ -1240,23 +1253,36 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
         return launch_k3_guided(dt, dO_h, I_h, dcoef, N, h_l, w_l, h, w, p.F, g->slope, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "k3g");
-    if (dp_l != nullptr || need_hi) {
+    const bool want_dgl = guide_low ? need_lo : need_hi;
+    if (dp_l != nullptr || want_dgl) {
         e = L.run("k4_lowres_bwd", [&] {
-            return run_k4(dt, true, G_l, p_l, dcoef, dp_l, need_hi ? dG_l : nullptr, planes, h_l, w_l, r, eps,
+            return run_k4(dt, true, G_l, p_l, dcoef, dp_l, want_dgl ? dG_l : nullptr, planes, h_l, w_l, r, eps,
                           p.k4, s);
         });
         if (e != cudaSuccess) return cuda_fail(e, "k4");
     }
+    int rows = 0;  // weight-gradient partial rows written
     if (need_hi) {
-        const int nb = k6_blocks(N, h, w);
         e = L.run("k6_guide_bwd", [&] {
-            return launch_k6(dt, coef, dG_l, dO_h, I_h, dI_h, partials, N, h_l, w_l, h, w, p.F, g->slope, s);
+            return launch_k6(dt, coef, guide_low ? nullptr : dG_l, dO_h, I_h, dI_h, partials, N, h_l, w_l, h, w,
+                             p.F, g->slope, s);
         });
         if (e != cudaSuccess) return cuda_fail(e, "k6");
-        if (dW != nullptr) {
-            e = L.run("k6_weight_reduce", [&] { return launch_wreduce(partials, nb, dW, g->hidden, s); });
-            if (e != cudaSuccess) return cuda_fail(e, "k6 reduce");
-        }
+        rows = k6_blocks(N, h, w);
+    }
+    if (need_lo) {
+        if (rows + k6_low_blocks(N, h_l, w_l) > kMaxK6Blocks)
+            return fail(DGF_ERR_UNSUPPORTED, "weight-gradient partial rows exceed %d", kMaxK6Blocks);
+        e = L.run("k6_guide_low", [&] {
+            return launch_k6_low(dt, dG_l, I_l, dI_l, partials + (size_t)rows * kWGradPadded, N, h_l, w_l,
+                                 g->slope, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k6l");
+        rows += k6_low_blocks(N, h_l, w_l);
+    }
+    if (dW != nullptr) {
+        e = L.run("k6_weight_reduce", [&] { return launch_wreduce(partials, rows, dW, g->hidden, s); });
+        if (e != cudaSuccess) return cuda_fail(e, "k6 reduce");
     }
     return DGF_OK;
 }
@@ -1338,7 +1364,7 @@ dgf_status dgf_forward_opt(const void* p_l, const void* I_l, const void* I_h, vo
         return forward_grey(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream,
                             mean_ab, n_in);
     return forward_impl(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream,
-                        mean_ab);
+                        mean_ab, opt != nullptr && opt->guide_low != 0);
 }
 
 dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l, void* dI_l,
@@ -1402,7 +1428,7 @@ dgf_status dgf_backward_opt(const void* dO_h, const void* p_l, const void* I_l, 
         return backward_grey(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g,
                              workspace, ws_bytes, stream, mean_ab, n_in);
     return backward_impl(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace,
-                         ws_bytes, stream, mean_ab);
+                         ws_bytes, stream, mean_ab, opt != nullptr && opt->guide_low != 0);
 }
 
 size_t dgf_workspace_size_opt(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt, const dgf_guide* g,

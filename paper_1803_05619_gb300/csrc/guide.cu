@@ -7,8 +7,14 @@
 //   K6  d G_h = d O_h * Abar_h + d G_l / f^2 (block mean transposed), chained
 //       through F to d I_h, plus the weight gradients     (backward; Algorithm
 //       1's last line, d I_h = d G_h . grad F)
+// With F applied to each guide on its own (G_l = F(I_l), the literal reading
+// of Sec. 3.4), K5L forms G_l per low-res pixel instead of K5, K6 takes no
+// d G_l term, and K6L chains d G_l through F at low resolution to d I_l and
+// adds its weight-gradient terms as further partial rows.
 // The hidden width is padded to 16 with zero weights, which leaves every
 // output unchanged and keeps all loops fully unrolled.
+#include <algorithm>
+
 #include "common.cuh"
 #include "hires.cuh"
 #include "kernels.h"
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) k6_guide_bwd(const float2* __rest
                 for (int c = 0; c < 3; ++c) {
                     const float* row = sA + (c * TH + i) * pitch;
                     const float A = lerp(row[cc[k]], row[cc[k] + 1], ll[k]);
-                    const float dl = dG_l[((size_t)n * 3 + c) * lw + (size_t)yl * w_l + xl];
+                    const float dl = dG_l != nullptr ? dG_l[((size_t)n * 3 + c) * lw + (size_t)yl * w_l + xl] : 0.f;
                     dg[c] = fmaf(r[c][k], A, dl * inv_ff);
                     gb2[c] += dg[c];
                 }
@@ -342,6 +348,85 @@ __global__ void __launch_bounds__(kThreads, 1) k6_guide_bwd(const float2* __rest
                 for (int c = 0; c < 3; ++c)
                     store_vec<T, VEC>(dI_h + ((size_t)n * 3 + c) * hw + (size_t)y * w + xs, o[c]);
             }
+        }
+    }
+    // block reduction of the 99 sums (fixed order), one partial row per CTA
+#pragma unroll
+    for (int k = 0; k < kWGrad; ++k) {
+        float v = k < 48 ? gw1[k] : (k < 96 ? gw2[k - 48] : gb2[k - 96]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kWGrad; k += kThreads) {
+        float s = 0.f;
+        for (int wi = 0; wi < kWarps; ++wi) s += red[wi][k];
+        partials[(size_t)blockIdx.x * kWGrad + k] = s;
+    }
+}
+
+// ------------------------------------------------------------------ K5L
+// G_l = F(I_l) per low-res pixel (the transform applied to the low-res guide).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k5_guide_low(const T* __restrict__ I_l, float* __restrict__ G_l,
+                                                         int N, size_t lw, float slope) {
+    const size_t total = (size_t)N * lw;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (size_t)gridDim.x * blockDim.x) {
+        const size_t n = v / lw, px = v - n * lw;
+        float x[3], g[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x[c] = to_f32<T>(I_l[(n * 3 + c) * lw + px]);
+        guide_eval(x, slope, g);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) G_l[(n * 3 + c) * lw + px] = g[c];
+    }
+}
+
+// ------------------------------------------------------------------ K6L
+// d G_l through F at low resolution: d I_l = W1^T d z and the weight-gradient
+// terms of the low-res pixels, one partial row per CTA (rows after K6's).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) k6_guide_low(const float* __restrict__ dG_l,
+                                                           const T* __restrict__ I_l, T* __restrict__ dI_l,
+                                                           float* __restrict__ partials, int N, size_t lw,
+                                                           float slope) {
+    __shared__ float red[kWarps][kWGrad];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float gw1[kHid * 3], gw2[3 * kHid], gb2[3];
+#pragma unroll
+    for (int k = 0; k < kHid * 3; ++k) gw1[k] = gw2[k] = 0.f;
+    gb2[0] = gb2[1] = gb2[2] = 0.f;
+    const size_t total = (size_t)N * lw;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (size_t)gridDim.x * blockDim.x) {
+        const size_t n = v / lw, px = v - n * lw;
+        float x[3], dg[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            x[c] = to_f32<T>(I_l[(n * 3 + c) * lw + px]);
+            dg[c] = dG_l[(n * 3 + c) * lw + px];
+            gb2[c] += dg[c];
+        }
+        float dx0 = 0.f, dx1 = 0.f, dx2 = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < kHid; ++kk) {
+            const float z = fmaf(c_w1[kk * 3 + 2], x[2], fmaf(c_w1[kk * 3 + 1], x[1], c_w1[kk * 3 + 0] * x[0]));
+            const float hk = lrelu(z, slope);
+            const float dh = fmaf(c_w2[2 * kHid + kk], dg[2], fmaf(c_w2[1 * kHid + kk], dg[1], c_w2[kk] * dg[0]));
+            const float dz = z > 0.f ? dh : slope * dh;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gw2[c * kHid + kk] = fmaf(dg[c], hk, gw2[c * kHid + kk]);
+            gw1[kk * 3 + 0] = fmaf(dz, x[0], gw1[kk * 3 + 0]);
+            gw1[kk * 3 + 1] = fmaf(dz, x[1], gw1[kk * 3 + 1]);
+            gw1[kk * 3 + 2] = fmaf(dz, x[2], gw1[kk * 3 + 2]);
+            dx0 = fmaf(c_w1[kk * 3 + 0], dz, dx0);
+            dx1 = fmaf(c_w1[kk * 3 + 1], dz, dx1);
+            dx2 = fmaf(c_w1[kk * 3 + 2], dz, dx2);
+        }
+        if (dI_l != nullptr) {
+            dI_l[(n * 3 + 0) * lw + px] = from_f32<T>(dx0);
+            dI_l[(n * 3 + 1) * lw + px] = from_f32<T>(dx1);
+            dI_l[(n * 3 + 2) * lw + px] = from_f32<T>(dx2);
         }
     }
     // block reduction of the 99 sums (fixed order), one partial row per CTA
@@ -423,6 +508,49 @@ cudaError_t launch_k5(dgf_dtype dt, const void* I_h, float* G_l, int N, int h_l,
         case DGF_F32: return k5_go<float>(I_h, G_l, N, h_l, w_l, h, w, F, slope, s);
         case DGF_BF16: return k5_go<__nv_bfloat16>(I_h, G_l, N, h_l, w_l, h, w, F, slope, s);
         case DGF_F16: return k5_go<__half>(I_h, G_l, N, h_l, w_l, h, w, F, slope, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t k5l_go(const void* I_l, float* G_l, int N, size_t lw, float slope, cudaStream_t s) {
+    const int blocks = (int)std::min<size_t>(((size_t)N * lw + kThreads - 1) / kThreads, (size_t)152 * 8);
+    k5_guide_low<T><<<blocks, kThreads, 0, s>>>(static_cast<const T*>(I_l), G_l, N, lw, slope);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_k5_low(dgf_dtype dt, const void* I_l, float* G_l, int N, int h_l, int w_l, float slope,
+                          cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    const size_t lw = (size_t)h_l * w_l;
+    switch (dt) {
+        case DGF_F32: return k5l_go<float>(I_l, G_l, N, lw, slope, s);
+        case DGF_BF16: return k5l_go<__nv_bfloat16>(I_l, G_l, N, lw, slope, s);
+        case DGF_F16: return k5l_go<__half>(I_l, G_l, N, lw, slope, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int k6_low_blocks(int N, int h_l, int w_l) {
+    const size_t px = (size_t)N * h_l * w_l;
+    return (int)std::max<size_t>(1, std::min<size_t>((px + kThreads - 1) / kThreads, (size_t)152));
+}
+
+template <typename T>
+static cudaError_t k6l_go(const float* dG_l, const void* I_l, void* dI_l, float* partials, int N, int h_l,
+                          int w_l, float slope, cudaStream_t s) {
+    k6_guide_low<T><<<k6_low_blocks(N, h_l, w_l), kThreads, 0, s>>>(
+        dG_l, static_cast<const T*>(I_l), static_cast<T*>(dI_l), partials, N, (size_t)h_l * w_l, slope);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_k6_low(dgf_dtype dt, const float* dG_l, const void* I_l, void* dI_l, float* partials, int N,
+                          int h_l, int w_l, float slope, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    switch (dt) {
+        case DGF_F32: return k6l_go<float>(dG_l, I_l, dI_l, partials, N, h_l, w_l, slope, s);
+        case DGF_BF16: return k6l_go<__nv_bfloat16>(dG_l, I_l, dI_l, partials, N, h_l, w_l, slope, s);
+        case DGF_F16: return k6l_go<__half>(dG_l, I_l, dI_l, partials, N, h_l, w_l, slope, s);
     }
     return cudaErrorInvalidValue;
 }

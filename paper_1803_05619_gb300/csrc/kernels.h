@@ -97,6 +97,14 @@ cudaError_t launch_k2_guided(dgf_dtype dt, const float2* coef, const void* I_h, 
                              int h_l, int w_l, int h, int w, int F, int TH, float slope, cudaStream_t s);
 cudaError_t launch_k3_guided(dgf_dtype dt, const void* R, const void* I_h, float2* dcoef, int N,
                              int h_l, int w_l, int h, int w, int F, float slope, cudaStream_t s);
+// F applied to the low-res guide itself (G_l = F(I_l), I_l: N x 3 x h_l x w_l):
+// K5L forms G_l (FP32); K6L chains d G_l through F to d I_l (nullable) and
+// writes k6_low_blocks(...) weight-gradient partial rows from `partials`.
+cudaError_t launch_k5_low(dgf_dtype dt, const void* I_l, float* G_l, int N, int h_l, int w_l, float slope,
+                          cudaStream_t s);
+int k6_low_blocks(int N, int h_l, int w_l);
+cudaError_t launch_k6_low(dgf_dtype dt, const float* dG_l, const void* I_l, void* dI_l, float* partials, int N,
+                          int h_l, int w_l, float slope, cudaStream_t s);
 int k6_blocks(int N, int h, int w);
 cudaError_t launch_k6(dgf_dtype dt, const float2* coef, const float* dG_l, const void* R, const void* I_h,
                       void* dI_h, float* partials, int N, int h_l, int w_l, int h, int w, int F, float slope,

@@ -75,20 +75,25 @@ def _sizes(p_l, I_h, grey_ok=False):
     return N, C, h_l, w_l, h, w
 
 
-def _options(mean_ab, C, I_h, g):
+def _options(mean_ab, C, I_h, g, guide_low=False):
     """dgf_options for the call, or None for the defaults."""
     n_I = I_h.shape[1]
     if n_I != C and g is not None:
         raise ValueError("a grey guide (guide channels != output channels) excludes the guidance transform")
-    if mean_ab and n_I == C:
+    if guide_low and g is None:
+        raise ValueError("guide_low applies the guidance transform to I_l: it needs the transform's weights")
+    if mean_ab and n_I == C and not guide_low:
         return None
-    return L.dgf_options(1 if mean_ab else 0, n_I if n_I != C else 0)
+    return L.dgf_options(1 if mean_ab else 0, n_I if n_I != C else 0, 1 if guide_low else 0)
 
 
 def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2, out=None,
-               mean_ab=True):
+               mean_ab=True, guide_low=False):
     """O_h of the fast guided filtering layer (Eq. 1-2, box mean of A and b;
-    mean_ab=False: A_l, b_l upsampled directly, the layer as printed)."""
+    mean_ab=False: A_l, b_l upsampled directly, the layer as printed; a guide
+    with another channel count than p_l: its channel mean guides every
+    channel; guide_low=True with the transform's weights: G_l = F(I_l)
+    instead of the block mean of F(I_h))."""
     dev = _check(p_l, I_l, I_h, w1, w2, b2)
     N, C, h_l, w_l, h, w = _sizes(p_l, I_h, grey_ok=True)
     dt = dtype_code(I_h)
@@ -96,7 +101,7 @@ def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slo
         raise TypeError("p_l, I_l and I_h must share one dtype")
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
-    opt = _options(mean_ab, C, I_h, g)
+    opt = _options(mean_ab, C, I_h, g, guide_low)
     if out is None:
         out = torch.empty((N, C, h, w), dtype=I_h.dtype, device=I_h.device)
     with torch.cuda.device(dev):
@@ -112,17 +117,17 @@ def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slo
 
 
 def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2,
-                need_p=True, need_Il=True, need_Ih=True, need_w=True, mean_ab=True):
+                need_p=True, need_Il=True, need_Ih=True, need_w=True, mean_ab=True, guide_low=False):
     """(dp_l, dI_l, dI_h, (dw1, dw2, db2)) by the library's adjoint kernels."""
     dev = _check(dO_h, p_l, I_l, I_h, w1, w2, b2)
     N, C, h_l, w_l, h, w = _sizes(p_l, I_h, grey_ok=True)
     dt = dtype_code(I_h)
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
-    opt = _options(mean_ab, C, I_h, g)
+    opt = _options(mean_ab, C, I_h, g, guide_low)
     dO_h = dO_h.to(I_h.dtype).contiguous()
     dp = torch.empty_like(p_l) if need_p else None
-    dIl = torch.empty_like(I_l) if (need_Il and g is None) else None
+    dIl = torch.empty_like(I_l) if (need_Il and (g is None or guide_low)) else None
     dIh = torch.empty_like(I_h) if need_Ih else None
     dW = None
     if g is not None and need_w:

@@ -170,3 +170,23 @@ def test_grey_guide_options_on_host(lib):
     st = L.dgf_backward_opt(ptr, ptr, ptr, ptr, ptr, ptr, ptr, ctypes.cast(dW, ctypes.POINTER(ctypes.c_float)),
                             2, 1, 16, 20, 64, 80, 1, 1e-3, L.DGF_BF16, None, None, 0, None, ctypes.byref(grey))
     assert st == 1 and "dW" in L.dgf_last_error()
+
+
+def test_guide_low_option_on_host(lib):
+    """guide_low needs a guidance transform and I_l; it admits dI_l with a transform."""
+    ptr = ctypes.c_void_p(256)
+    low = L.dgf_options(1, 0, 1)
+    st = L.dgf_forward_opt(ptr, ptr, ptr, ptr, 1, 3, 16, 16, 64, 64, 1, 1e-3, L.DGF_F32, None,
+                           None, 0, None, ctypes.byref(low))
+    assert st == 1 and "guide_low" in L.dgf_last_error()
+    gd = L.dgf_guide(16, 32, 48, 16, 0.2)
+    st = L.dgf_forward_opt(ptr, None, ptr, ptr, 1, 3, 16, 16, 64, 64, 1, 1e-3, L.DGF_F32, ctypes.byref(gd),
+                           None, 0, None, ctypes.byref(low))
+    assert st == 1  # I_l is read
+    # dI_l is rejected with a transform unless guide_low; with it the call gets as far as the workspace
+    st = L.dgf_backward(ptr, ptr, ptr, ptr, None, ptr, None, None, 1, 3, 16, 16, 64, 64, 1, 1e-3, L.DGF_F32,
+                        ctypes.byref(gd), None, 0, None)
+    assert st == 1 and "dI_l" in L.dgf_last_error()
+    st = L.dgf_backward_opt(ptr, ptr, ptr, ptr, None, ptr, None, None, 1, 3, 16, 16, 64, 64, 1, 1e-3, L.DGF_F32,
+                            ctypes.byref(gd), None, 0, None, ctypes.byref(low))
+    assert st == 5

@@ -422,6 +422,56 @@ def test_guided_forward_backward_parity(case):
     assert float(np.max(np.abs(f64(dws[2])))) <= 1e-3 * float(np.max(np.abs(rw2)))
 
 
+# the transform applied to each guide on its own (G_l = F(I_l), guide_low)
+GUIDED_LOW_CASES = [  # N, h_l, w_l, f, r, eps, dtype, mean_ab
+    (2, 24, 20, 4, 1, 1e-3, F32, True),
+    (1, 20, 30, 8, 2, 1e-4, BF16, True),
+    (1, 26, 18, 4, 1, 1e-3, F16, True),
+    (1, 16, 22, 4, 1, 1e-3, F32, False),
+]
+
+
+@pytest.mark.parametrize("case", GUIDED_LOW_CASES, ids=_ids(GUIDED_LOW_CASES))
+def test_guided_low_guide_parity(case):
+    N, hl, wl, f, r, eps, dtype, mean_ab = case
+    st = to_storage(synth.photo_like(70 + r, N, 3, hl, wl, f), dtype)
+    w = {k: v.float() for k, v in synth.guide_weights(13).items()}
+    R = synth.upstream_grad(14, st["I_h"].shape).to(dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    wc = {k: v.cuda() for k, v in w.items()}
+    args = (wc["w1"], wc["w2"], wc["b2"], 0.2)
+    out = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps, *args, mean_ab=mean_ab, guide_low=True)
+    dp, dIl, dIh, dws = gf_backward(R.cuda(), g["p_l"], g["I_l"], g["I_h"], r, eps, *args, mean_ab=mean_ab,
+                                    guide_low=True)
+    # d I_l alone (the low-res chain without K6) and d W alone give the same values
+    only_il = gf_backward(R.cuda(), g["p_l"], g["I_l"], g["I_h"], r, eps, *args, need_p=False, need_Ih=False,
+                          need_w=False, mean_ab=mean_ab, guide_low=True)[1]
+    only_w = gf_backward(R.cuda(), g["p_l"], g["I_l"], g["I_h"], r, eps, *args, need_p=False, need_Il=False,
+                         need_Ih=False, mean_ab=mean_ab, guide_low=True)[3]
+    torch.cuda.synchronize()
+    assert torch.equal(only_il, dIl)
+    for a, b in zip(only_w, dws):
+        assert torch.equal(a, b)
+    w64 = {k: v.double().numpy() for k, v in w.items()}
+    ref = O.forward_guided_separate(f64(st["p_l"]), f64(st["I_l"]), f64(st["I_h"]), w64["w1"], w64["w2"],
+                                    w64["b2"], r, eps, mean_ab=mean_ab)
+    assert_fwd(f64(out), ref, dtype, eps if dtype != F32 else max(eps, 1e-3))
+    rp, rIl, rIh, rw1, rw2, rb2 = O.backward_guided_separate(f64(R), f64(st["p_l"]), f64(st["I_l"]),
+                                                             f64(st["I_h"]), w64["w1"], w64["w2"], w64["b2"],
+                                                             r, eps, mean_ab=mean_ab)
+    assert_grad(f64(dp), rp, dtype, "dp_l")
+    assert_grad(f64(dIl), rIl, dtype, "dI_l")
+    assert_grad(f64(dIh), rIh, dtype, "dI_h")
+    wtol = 1e-3 if dtype == F32 else 2e-2
+    for got, refw, name in ((dws[0], rw1, "dw1"), (dws[1], rw2, "dw2")):
+        err = float(np.linalg.norm(f64(got) - refw) / np.linalg.norm(refw))
+        assert err <= wtol, f"{name}: rel L2 {err:.3e}"
+    assert float(np.max(np.abs(f64(dws[2])))) <= 1e-3 * float(np.max(np.abs(rw2)))
+    # and it is not the block-mean form
+    assert not torch.equal(out, gf_forward(g["p_l"], None, g["I_h"], r, eps, *args, mean_ab=mean_ab))
+    assert L.dgf_device_status() == 0
+
+
 # ------------------------------------------------------------ shape invariance
 # The K1 strips sum their register rings oldest row first and do their pair
 # arithmetic through non-contracting intrinsics, so every segment length the
