@@ -250,7 +250,9 @@ __global__ void __launch_bounds__(kThreads) k3_hires_bwd_guided(const T* __restr
 // Persistent over high-res tiles (TH rows x 32*VEC columns of one image);
 // each CTA keeps its weight-gradient sums in registers and writes one
 // partial row; a second kernel adds the partials in a fixed order.
-template <typename T, int VEC, int F>
+// LOW: whether d G_l / f^2 joins d G_h (the block-mean form of the low-res
+// guide); without it (G_l = F(I_l)) K6L takes d G_l instead.
+template <typename T, int VEC, int F, bool LOW>
 __global__ void __launch_bounds__(kThreads, 1) k6_guide_bwd(const float2* __restrict__ coef,
                                                            const float* __restrict__ dG_l,
                                                            const T* __restrict__ R, const T* __restrict__ I_h,
@@ -317,7 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1) k6_guide_bwd(const float2* __rest
                 for (int c = 0; c < 3; ++c) {
                     const float* row = sA + (c * TH + i) * pitch;
                     const float A = lerp(row[cc[k]], row[cc[k] + 1], ll[k]);
-                    const float dl = dG_l != nullptr ? dG_l[((size_t)n * 3 + c) * lw + (size_t)yl * w_l + xl] : 0.f;
+                    float dl = 0.f;
+                    if constexpr (LOW) dl = dG_l[((size_t)n * 3 + c) * lw + (size_t)yl * w_l + xl];
                     dg[c] = fmaf(r[c][k], A, dl * inv_ff);
                     gb2[c] += dg[c];
                 }
@@ -610,7 +613,7 @@ static cudaError_t k6_go(const float2* coef, const float* dG_l, const void* R, c
                          float* partials, int N, int h_l, int w_l, int h, int w, float slope, cudaStream_t s) {
     const int TH = 8;
     const size_t smem = (size_t)3 * TH * (32 * VEC / F + 2) * sizeof(float);
-    auto kern = k6_guide_bwd<T, VEC, F>;
+    auto kern = dG_l != nullptr ? k6_guide_bwd<T, VEC, F, true> : k6_guide_bwd<T, VEC, F, false>;
     cudaError_t e = prep(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<k6_blocks(N, h, w), kThreads, smem, s>>>(coef, dG_l, static_cast<const T*>(R),
