@@ -16,18 +16,21 @@
  * dgf_backward returns the gradients of Algorithm 1 (with respect to p_l,
  * I_l and I_h, extended through the box mean of A and b).  With a guidance
  * transform F (Sec. 3.4: 1x1 conv, leaky ReLU, 1x1 conv) the guides become
- * G_h = F(I_h) and G_l = the f x f block mean of G_h, and the weight
- * gradients are returned as well.
+ * G_h = F(I_h) and G_l = the f x f block mean of G_h (or F(I_l) with
+ * dgf_options.guide_low), and the weight gradients are returned as well.
+ * A guide whose channel count differs from the output's is replaced by its
+ * channel mean (dgf_options.guide_channels, Sec. 6.3).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
  * Layout:    every image tensor is NCHW, contiguous, planes back to back:
  *            element (n, c, y, x) of an N x C x H x W tensor is at
  *            ((n*C + c)*H + y)*W + x.
- * Memory:    every tensor pointer is DEVICE memory owned by the caller.  The
- *            library allocates no tensor memory; it uses the caller's
- *            workspace (dgf_workspace_size bytes, 256-byte aligned) for its
- *            FP32 intermediates.
+ * Memory:    every tensor pointer is DEVICE memory owned by the caller
+ *            (dgf_host_step alone takes HOST tensors).  The library
+ *            allocates no tensor memory; it uses the caller's workspace
+ *            (dgf_workspace_size bytes, or dgf_workspace_size_opt for the
+ *            _opt calls; 256-byte aligned) for its intermediates.
  * Precision: storage is FP32, BF16 or FP16 (dgf_dtype); every sum and every
  *            product is formed in FP32; stores round to nearest even.
  * Streams:   calls enqueue kernels on `stream` and return without waiting.
