@@ -298,7 +298,8 @@ class GuidedFilterTransformFn(torch.autograd.Function):
 
 
 class GuidedFilter(torch.nn.Module):
-    """Fast guided filtering layer, F = identity (DGF_b with n_I = n_O)."""
+    """Fast guided filtering layer without a learned transform (DGF_b): the
+    guide itself when it has the output's channels, else its channel mean."""
 
     def __init__(self, r: int = 1, eps: float = 1e-8):
         super().__init__()
