@@ -62,6 +62,23 @@ def parse():
     return ap.parse_args()
 
 
+DATA = ("synthetic (seeded; blobs+edges+noise photo stand-in, tone-curve target, N(0,1) upstream "
+        "gradient)")
+
+
+def workload_config(name, ws):
+    """The `config` of a workload's JSON line (the same for both arms)."""
+    spec = WORKLOADS[name]
+    N, C, h_l, w_l, f = spec["N"], spec["C"], spec["h_l"], spec["w_l"], spec["f"]
+    h, w = h_l * f, w_l * f
+    esz = 4 if spec["dtype"] == "f32" else 2
+    return {"workload": name, "step": "forward+backward", "N": N, "C": C, "h_l": h_l, "w_l": w_l, "h": h, "w": w,
+            "r": spec["r"], "eps": spec["eps"],
+            "l2": "no flush: a step streams %d MB of high-res tensors (I_h, O_h, dO_h, dI_h of %d MB each) "
+                  "through the 129 MB L2" % (4 * N * C * h * w * esz // 10**6, N * C * h * w * esz // 10**6),
+            "parallelism": f"images sharded over {ws} GPU(s), no collective"}
+
+
 # ------------------------------------------------------------------ inputs
 def make_inputs(spec, device, seed=0):
     import torch
@@ -188,7 +205,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
             time.sleep(0.5)
         except Exception:
@@ -206,6 +223,22 @@ class ClockSampler:
 
     def mark(self, which):
         setattr(self, which, time.time())
+
+    def samples_in_window(self):
+        return self.summary().get("samples", 0) if self.proc is not None else 0
+
+    def extend(self, fn, seconds=0.3):
+        """A timed loop too short for the sampling period: keep the same work
+        running for `seconds` right after it (untimed) and take the clocks
+        over the timed loop and that run together."""
+        import torch
+        t_end = time.time() + seconds
+        while time.time() < t_end:
+            for _ in range(20):
+                fn()
+            torch.cuda.synchronize()
+        self.mark("stop")
+        self.extended = seconds
 
     def summary(self):
         if self.proc is None:
@@ -230,8 +263,12 @@ class ClockSampler:
         sm = sorted(r[0] for r in rows)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows), "power_w_max": max(r[4] for r in rows)}
+        out = {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+               "samples": len(rows), "power_w_max": max(r[4] for r in rows), "period_ms": 10}
+        if getattr(self, "extended", None):
+            out["window"] = ("the timed loop plus %.1f s of the same step run right after it (the timed loop "
+                             "alone is shorter than a few sampling periods)" % self.extended)
+        return out
 
 
 def time_loop(fn, steps, warmup, ws, device, clock=None):
@@ -429,7 +466,9 @@ else:
 R = synth.upstream_grad(1, d["I_h"].shape).numpy()
 p, il, ih = (d[k].numpy() for k in ("p_l", "I_l", "I_h"))
 reps = int(spec.get("reps", 1))
-oracle.forward(p, il, ih, spec["r"], spec["eps"])  # warm-up
+for _ in range(int(spec.get("warmup", 1))):
+    oracle.forward(p, il, ih, spec["r"], spec["eps"])
+    oracle.backward(R, p, il, ih, spec["r"], spec["eps"])
 t0 = time.perf_counter()
 for _ in range(reps):
     oracle.forward(p, il, ih, spec["r"], spec["eps"])
@@ -439,13 +478,14 @@ print(json.dumps({{"seconds_per_plane": dt}}))
 """
 
 
-def cpu_oracle(spec, reps=1):
+def cpu_oracle(spec, reps=1, warmup=1):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     s = dict(spec)
     s["reps"] = reps
+    s["warmup"] = warmup
     code = ORACLE_SNIPPET.format(root=ROOT, spec=json.dumps(s))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
@@ -455,25 +495,175 @@ def cpu_oracle(spec, reps=1):
     return pix / sec / 1e6, sec
 
 
+ACCURACY_SNIPPET = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle
+manifest = json.load(open({manifest!r}))
+out = {{}}
+def err(got, ref):
+    got = np.asarray(got, np.float64); ref = np.asarray(ref, np.float64)
+    d = got - ref
+    nr = float(np.linalg.norm(ref))
+    return {{"max_abs": float(np.max(np.abs(d))) if d.size else 0.0,
+             "rel_l2": float(np.linalg.norm(d) / nr) if nr > 0 else float(np.linalg.norm(d))}}
+for case in manifest:
+    a = np.load(case["file"])
+    f = {{k: a[k].astype(np.float64) for k in a.files}}
+    r, eps = case["r"], case["eps"]
+    if case["kind"] == "plain":
+        ref = oracle.forward(f["p_l"], f["I_l"], f["I_h"], r, eps)
+        rp, rIl, rIh = oracle.backward(f["R"], f["p_l"], f["I_l"], f["I_h"], r, eps)
+        e = {{"O_h": err(f["O_h"], ref), "dp_l": err(f["dp_l"], rp), "dI_l": err(f["dI_l"], rIl),
+              "dI_h": err(f["dI_h"], rIh)}}
+    else:
+        ref = oracle.forward_guided(f["p_l"], f["I_h"], f["w1"], f["w2"], f["b2"], r, eps)
+        rp, rIh, rw1, rw2, rb2 = oracle.backward_guided(f["R"], f["p_l"], f["I_h"], f["w1"], f["w2"], f["b2"], r, eps)
+        e = {{"O_h": err(f["O_h"], ref), "dp_l": err(f["dp_l"], rp), "dI_h": err(f["dI_h"], rIh),
+              "dW": err(np.concatenate([f["dw1"].ravel(), f["dw2"].ravel()]),
+                        np.concatenate([rw1.ravel(), rw2.ravel()])),
+              "db2_max_abs": float(np.max(np.abs(f["db2"] - rb2)))}}
+    out[case["name"]] = {{"sample": case["sample"], "dtype": case["dtype"], **e}}
+print(json.dumps(out))
+"""
+
+
+def accuracy(device):
+    """Max-abs and relative-L2 error against the FP64 oracle of O_h and of every
+    gradient, per configuration, on the benchmark's own full-size inputs
+    (sampled planes or images; the oracle computes each sample completely).
+    Part of the CPU-baseline leg: the oracle runs in a subprocess on the host
+    cores, after every GPU number has been taken."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1803_05619_gb300.layer import gf_backward, gf_backward_batched, gf_forward, gf_forward_batched
+    tmp = tempfile.mkdtemp(prefix="dgf_acc_")
+    manifest = []
+
+    def npf(t):
+        return t.detach().float().cpu().numpy()
+
+    def plain(name, spec, g, out, plane, sample):
+        n, c = divmod(plane, spec["C"])
+        sl = lambda t: npf(t[n:n + 1, c:c + 1])  # noqa: E731
+        f = os.path.join(tmp, name + ".npz")
+        np.savez(f, p_l=sl(g["p_l"]), I_l=sl(g["I_l"]), I_h=sl(g["I_h"]), R=sl(g["R"]), O_h=sl(out[0]),
+                 dp_l=sl(out[1]), dI_l=sl(out[2]), dI_h=sl(out[3]))
+        manifest.append({"name": name, "kind": "plain", "file": f, "r": spec["r"], "eps": spec["eps"],
+                         "dtype": spec["dtype"], "sample": sample})
+
+    def run_plain(g, spec):
+        o = gf_forward(g["p_l"], g["I_l"], g["I_h"], spec["r"], spec["eps"])
+        dp, dil, dih, _ = gf_backward(g["R"], g["p_l"], g["I_l"], g["I_h"], spec["r"], spec["eps"])
+        return o, dp, dil, dih
+
+    # c1 (whole), c2 (plane 0 of 12)
+    for name, seed in (("fp32_small_1x1x256", 0), (MAIN, 0)):
+        spec = WORKLOADS[name]
+        g, _ = make_inputs(spec, device, seed=seed)
+        plain(name, spec, g, run_plain(g, spec), 0,
+              "the whole image" if name != MAIN else "plane (0, 0) of the 4 x 3 batch")
+        del g
+    # c3 in BF16 and the same inputs in FP32 (plane (1, 2) of the 2 x 3 batch)
+    spec = WORKLOADS["bf16_4k_2x3x3840x2160"]
+    g, _ = make_inputs(spec, device, seed=7)
+    plain("bf16_4k_2x3x3840x2160", spec, g, run_plain(g, spec), 5, "plane (1, 2) of the 2 x 3 batch")
+    g32 = {k: v.float() for k, v in g.items()}
+    spec32 = dict(spec, dtype="f32")
+    plain("bf16_4k_inputs_in_fp32", spec32, g32, run_plain(g32, spec32), 5,
+          "the BF16 inputs held in FP32: plane (1, 2)")
+    del g, g32
+    # c4: the smallest and a middle image of the 64, through the batched calls
+    specs = synth.mixed_sizes(seed=0, n=64)
+    order = sorted(range(len(specs)), key=lambda i: specs[i].h * specs[i].w)
+    for i in (order[0], order[len(order) // 2]):
+        s = specs[i]
+        d = synth.photo_like(1000 + i, 1, 3, s.h_l, s.w_l, s.f)
+        st = {k: v.to(torch.bfloat16)[0].to(device) for k, v in d.items()}
+        R = synth.upstream_grad(2000 + i, st["I_h"].shape).to(torch.bfloat16).to(device)
+        im = {"p_l": st["p_l"], "I_l": st["I_l"], "I_h": st["I_h"], "r": s.r, "eps": 1e-3}
+        o = gf_forward_batched([im])[0]
+        dp, dil, dih = gf_backward_batched([im], [R])[0]
+        gg = {k: v[None] for k, v in st.items()}
+        gg["R"] = R[None]
+        sp = {"C": 3, "r": s.r, "eps": 1e-3, "dtype": "bf16"}
+        for c in range(3):
+            plain(f"batched_64_uneven_img{i}_c{c}", sp, gg, (o[None], dp[None], dil[None], dih[None]), c,
+                  f"image {i} ({s.h}x{s.w}, f={s.f}, r={s.r}) channel {c}, batched calls")
+    # c5: image 0 of the guided training batch (its own call: the weight
+    # gradients then belong to that image alone)
+    d = synth.photo_like(21, 1, 3, 256, 256, 8)
+    g5 = {k: v.to(torch.bfloat16).to(device) for k, v in d.items()}
+    w = {k: v.float().to(device) for k, v in synth.guide_weights(22).items()}
+    R5 = synth.upstream_grad(23, (8, 3, 2048, 2048)).to(torch.bfloat16)[:1].to(device)
+    o5 = gf_forward(g5["p_l"], None, g5["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2)
+    dp5, _, dih5, dws = gf_backward(R5, g5["p_l"], None, g5["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2)
+    f = os.path.join(tmp, "guided.npz")
+    np.savez(f, p_l=npf(g5["p_l"]), I_h=npf(g5["I_h"]), R=npf(R5), O_h=npf(o5), dp_l=npf(dp5), dI_h=npf(dih5),
+             w1=npf(w["w1"]), w2=npf(w["w2"]), b2=npf(w["b2"]), dw1=npf(dws[0]), dw2=npf(dws[1]), db2=npf(dws[2]))
+    manifest.append({"name": "guided_train_8x2048", "kind": "guided", "file": f, "r": 8, "eps": 1e-4,
+                     "dtype": "bf16", "sample": "image 0 of the 8 (3 channels, weight gradients of that image)"})
+    torch.cuda.synchronize()
+    try:
+        return accuracy_oracle(manifest, tmp)
+    finally:
+        for c in manifest:
+            try:
+                os.remove(c["file"])
+            except OSError:
+                pass
+
+
+def accuracy_oracle(manifest, tmp):
+    """The oracle half of the accuracy leg: every case of `manifest` (npz files
+    of inputs and GPU outputs) against the FP64 oracle, in a subprocess on the
+    host cores."""
+    mpath = os.path.join(tmp, "manifest.json")
+    json.dump(manifest, open(mpath, "w"))
+    code = ACCURACY_SNIPPET.format(root=ROOT, manifest=mpath)
+    env = dict(os.environ)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    t0 = time.perf_counter()
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        return {"error": out.stderr[-1500:]}
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    res["_note"] = ("max_abs and rel_l2 = ||got - ref|| / ||ref|| against the FP64 oracle on the stored "
+                    "(rounded) inputs; oracle run on %d host cores in %.1f s" % (os.cpu_count() or 1,
+                                                                                 time.perf_counter() - t0))
+    return res
+
+
 def run_reference(args):
-    """--impl reference: the FP64 oracle on the host cores, same workload and metric."""
+    """--impl reference: the FP64 oracle on the host cores, same workload and metric.
+
+    A step is a bounded sample of the workload: one plane (1 of N C) forward +
+    backward, as the oracle stands (single-threaded numpy FP64); `value` is
+    that plane's pixels over its time, so it is the same metric.  The line's
+    steps, warmup and ms_per_step are what ran; the time a whole step of the
+    workload would take is given separately."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     spec = WORKLOADS[MAIN]
-    steps = max(1, min(args.steps, 30))  # each step ~0.6 s of CPU work; bounded to keep the run short
+    steps = max(1, min(args.steps, 30))  # each step ~0.8 s of CPU work; bounded to keep the run short
+    warmup = max(1, min(args.warmup, 5))
     t0 = time.perf_counter()
-    value, sec = cpu_oracle(spec, reps=steps)
+    value, sec = cpu_oracle(spec, reps=steps, warmup=warmup)
     wall = time.perf_counter() - t0
-    sample = (f"one plane (1 of {spec['N'] * spec['C']}) of {MAIN} per step: forward + backward, "
+    planes = spec["N"] * spec["C"]
+    sample = (f"one plane (1 of {planes}) of {MAIN} per step: forward + backward, "
               f"{spec['h_l']}x{spec['w_l']} -> {spec['h_l'] * spec['f']}x{spec['w_l'] * spec['f']}, "
               f"{sec:.2f} s per plane, single-threaded numpy FP64")
-    pix_total = spec["N"] * spec["h_l"] * spec["f"] * spec["w_l"] * spec["f"]
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpix/s",
-            "n_gpus": args.gpus, "steps": steps, "warmup": 1,
-            "ms_per_step": round(pix_total / value / 1e3, 3),
+            "n_gpus": args.gpus, "steps": steps, "warmup": warmup,
+            "ms_per_step": round(sec * 1e3, 3),
+            "ms_per_full_step_scaled": round(sec * 1e3 * planes, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": MAIN, **{k: spec[k] for k in spec}},
+            "data": DATA, "config": workload_config(MAIN, args.gpus),
             "cpu_baseline": {"value": round(value, 4), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
@@ -510,21 +700,16 @@ def main():
     per_step = L.dgf_launch_count() - n0
     with ClockSampler(local) as clk:
         ms = time_loop(step, args.steps, args.warmup, ws, device, clock=clk)
+        if clk.proc is not None and clk.samples_in_window() < 10:
+            clk.extend(step)
     launches = per_step * args.steps
     value = job_value(pix, ws, ms)
     fwd_ms = time_loop(step.forward, max(10, args.steps // 2), args.warmup, ws, device)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic (seeded; blobs+edges+noise photo "
-        "stand-in, tone-curve target, N(0,1) upstream gradient)",
-        "config": {"workload": main_name, "step": "forward+backward", "N": N, "C": C, "h_l": h_l, "w_l": w_l,
-                   "h": h, "w": w, "r": spec["r"], "eps": spec["eps"],
-                   "l2": "no flush: a step streams %d MB of high-res tensors (I_h, O_h, dO_h, dI_h of %d MB "
-                         "each) through the 129 MB L2"
-                         % (4 * N * C * h * w * g["I_h"].element_size() // 10**6,
-                            N * C * h * w * g["I_h"].element_size() // 10**6),
-                   "parallelism": f"images sharded over {ws} GPU(s), no collective"},
+        "vs_baseline": None, "dtype": spec["dtype"], "data": DATA,
+        "config": workload_config(main_name, ws),
         "fwd": {"value": round(ws * pix / (fwd_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
                 "ms_per_step": round(fwd_ms, 5)},
         "gpu_launches": int(launches),
@@ -552,6 +737,7 @@ def main():
             line["paper_literal_fp32_plain"] = bench_paper_literal(args, device)
             line["grey_guide_fp32"] = bench_grey(args, device)
         if not args.no_oracle:
+            line["errors"] = accuracy(device)
             reps = 15
             cv, csec = cpu_oracle(spec, reps=reps)
             line["cpu_baseline"] = {"value": round(cv, 4), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
@@ -683,7 +869,7 @@ def bench_paper_literal(args, device):
 
 
 def bench_grey(args, device):
-    """Grey guide (Sec. 6.3, DGF_b with differing channel counts): an RGB guide
+    """Grey guide (Sec. 4.2, DGF_b with differing channel counts): an RGB guide
     and a one-channel output, FP32 4 x (3 -> 1) x 512^2 -> 2048^2, r = 1,
     eps = 1e-4; forward and forward + backward through the library."""
     import synth

@@ -19,7 +19,7 @@
  * G_h = F(I_h) and G_l = the f x f block mean of G_h (or F(I_l) with
  * dgf_options.guide_low), and the weight gradients are returned as well.
  * A guide whose channel count differs from the output's is replaced by its
- * channel mean (dgf_options.guide_channels, Sec. 6.3).
+ * channel mean (dgf_options.guide_channels, Sec. 4.2, DGF_b).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -170,12 +170,32 @@ int dgf_profile_read(const char** names, double* total_ms, long long* launches, 
 long long dgf_launch_count(void);
 
 /*
- * Reads and clears the library's device status word on the current device
- * (synchronous).  0 = no device-side error since the last read;
- * bit 0 = a bounded wait for a TMA copy ran out (the result of that call is
- * invalid, DGF_ERR_TIMEOUT); -1 = the word could not be read.
+ * Device-side errors.  Every wait of a kernel for one of its TMA copies is
+ * bounded; when one runs out the kernel records bit 0 (a timeout) in the
+ * library's status word on its device, waits (again bounded) for its copies
+ * still in flight and stops, so that call's results are invalid.  The bit
+ * is sticky: it is mirrored into a pinned host word (set up by the first
+ * workspace call on the device, which must not come during a stream
+ * capture), and every later entry point call on that device returns
+ * DGF_ERR_TIMEOUT without launching anything until the bit is cleared.
+ * dgf_forward_noalloc allocates nothing, so it sees the mirror only once
+ * another entry point has set it up.
+ *
+ * dgf_device_status: reads the status word of the current device
+ * (synchronous): 0 = no device-side error recorded; bit 0 = a bounded wait
+ * ran out; -1 = the word could not be read.
+ * dgf_clear_device_status: clears the word and its host mirror
+ * (synchronous).
+ * dgf_set_wait_polls: polls of a kernel's first wait on a copy (default and
+ * maximum 2^22; the wait for copies still in flight after a timeout always
+ * polls 2^22 times, so every copy lands before its buffer is reused).  A
+ * test hook: 0 makes every first wait give up at once, which exercises the
+ * timeout path without starving any copy.  Synchronous.  No counterpart in
+ * the paper.
  */
 int dgf_device_status(void);
+dgf_status dgf_clear_device_status(void);
+dgf_status dgf_set_wait_polls(long long polls);
 
 /* Allows (1, default) or forbids (0) TMA staging of the low-resolution
  * tiles; with 0 every tile is staged with plain loads.  Results are
@@ -199,6 +219,17 @@ void dgf_set_tma(int on);
  * two-kernel forms give identical bits.  Either form needs the strip form
  * of the low-resolution pass (a pinned tile form keeps the two kernels). */
 void dgf_set_fused(int on);
+
+/* Allows (1, default) or forbids (0) the sliding-sum form of the
+ * low-resolution kernels for 16-bit storage (BF16/F16, r in {1, 2, 4, 8},
+ * the box mean of A, b): K1 (Eq. 1 and both box means, Sec. 3.2-3.3) and K4
+ * (Algorithm 1 at low resolution) with running window sums over data shifted
+ * by a per-strip constant, at a cost per pixel that does not grow with r.
+ * Forbidden, 16-bit calls use the exactly centred forms FP32 storage always
+ * uses.  The two agree within the 16-bit parity gates (the running sums
+ * round differently); the sliding form's bits depend on its segment length
+ * (autotune kinds 1 and 4) but not on the number of planes in a call. */
+void dgf_set_lowres_slide(int on);
 
 /* Allows (1) or forbids (0, default) the plane-group pipeline of dgf_forward
  * and dgf_backward (no guidance transform, integer factor for the backward):
@@ -225,17 +256,19 @@ void dgf_set_pipeline(int on);
  *             autotuned in this mode.
  *   guide_channels = 0 (default) or C: the guide has the output's C
  *             channels (F the identity);
- *   guide_channels = n_I >= 1, n_I != C: the grey guide of Sec. 6.3 (DGF_b
+ *   guide_channels = n_I >= 1, n_I != C: the grey guide of Sec. 4.2 (DGF_b
  *             with differing channel counts): I_l (N x n_I x h_l x w_l) and
- *             I_h (N x n_I x h x w) are averaged over their channels, the
- *             mean is rounded to dt and guides every one of the C output
- *             channels; dI_l, dI_h then have n_I channels (each the sum of
- *             the C channels' guide gradients / n_I).  Not with a guidance
- *             transform (g != NULL) and not in the batched or host-memory
- *             calls.  The workspace (dgf_workspace_size_opt) adds the grey
- *             guide repeated over the C channels at both resolutions and its
- *             gradients; two streaming passes form the guide before the
- *             layer and two more its gradient after it.
+ *             I_h (N x n_I x h x w) are averaged over their channels in FP32,
+ *             and that mean, held in FP32 (never rounded to dt), guides every
+ *             one of the C output channels; dI_l, dI_h then have n_I channels
+ *             (each the sum of the C channels' guide gradients / n_I).  Not
+ *             with a guidance transform (g != NULL) and not in the batched or
+ *             host-memory calls.  The workspace (dgf_workspace_size_opt) adds
+ *             the FP32 grey guide repeated over the C channels at both
+ *             resolutions and its gradients in dt; two streaming passes form
+ *             the guide before the layer and two more its gradient after it.
+ *             With 16-bit dt the high-resolution stage runs the general tile
+ *             kernels (the strip and fused forms read guides in dt).
  *   guide_low = 0 (default): with a guidance transform (g != NULL) the
  *             low-res guide is the f x f block mean of F(I_h) and I_l is not
  *             read;
@@ -309,9 +342,13 @@ dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dgf_dtype dt,
  * own buffers and keeps the fastest; that call synchronises its stream and
  * must not be under stream capture (tuning is skipped while capturing).
  * Chosen shapes are used by every later call with the same key, tuned or
- * not, and are saved to the file DGF_TUNE_CACHE names (if any); unreadable
- * lines in that file are ignored.  Results never depend on the shape beyond
- * FP32 rounding order.
+ * not, and are saved to the file DGF_TUNE_CACHE names (if any).  Each line
+ * of that file is keyed by this library's cache version and the device name;
+ * lines of another version or device are kept in the file but never used,
+ * and malformed, truncated or out-of-range lines are skipped one by one (a
+ * corrupt cache costs only a re-tune of the keys it held).  Results never
+ * depend on the shape beyond FP32 rounding order.
+ * dgf_autotune_entries: entries this device and library version would use.
  */
 void dgf_autotune(int on);
 int dgf_autotune_entries(void);
@@ -325,7 +362,11 @@ void dgf_autotune_reset(void);
  *     F = vec = 0; guide_f32 = 1 for the guidance-transform path (FP32 guide);
  *     tiles: a = columns, b = rows of the coefficient region (a power of two
  *     in {64, 128, 256} and one of {16, 32, 64}); K1 with r <= 2 also takes
- *     warp strips: a = rows per segment in {8, 16, 24, 32, 48, 64, 128}, b = 0.
+ *     warp strips: a = rows per segment in {8, 16, 24, 32, 48, 64, 128}, b = 0;
+ *     with 16-bit storage both also take the sliding-sum strips
+ *     (dgf_set_lowres_slide): a = output rows per segment in
+ *     {8, 12, 16, 24, 32, 48, 64} (at least 2 r), b = -V with V the
+ *     columns per lane (2, 4 or 8 for r <= 2; 4 for r in {4, 8}).
  *   kind 2 (K2 high-res apply): r = 0, F = integer factor (0: non-integer),
  *     vec = elements per vector; a = high-res rows per tile, b = 0.
  *   kind 3 (K3 high-res backward): as kind 2; a = low-res rows per segment

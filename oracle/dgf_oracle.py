@@ -21,7 +21,7 @@ What it computes (Wu et al., "Fast End-to-End Trainable Guided Filter"):
   f x f block mean of F(I_h).
 * Sec. 3.4, read literally - F applied to each resolution on its own:
   G_l = F(I_l), G_h = F(I_h) (``forward_guided_separate``).
-* Sec. 6.3 (DGF_b) - when the guide and the output differ in channel count,
+* Sec. 4.2 (DGF_b) - when the guide and the output differ in channel count,
   F is the mean over the guide's channels (a grey guide), used for every
   output channel.
 
@@ -430,41 +430,30 @@ def backward_guided_separate(R, p_l, I_l, I_h, w1, w2, b2, r: int, eps: float, s
 
 
 # --------------------------------------------------------------------------
-# Grey guide (DGF_b with differing channel counts, Sec. 6.3)
+# Grey guide (DGF_b with differing channel counts, Sec. 4.2)
 # --------------------------------------------------------------------------
 
-def grey_guide(I, store=None) -> np.ndarray:
-    """(N, 1, h, w): the mean of an (N, n_I, h, w) guide over its channels.
+def grey_guide(I) -> np.ndarray:
+    """(N, 1, h, w): the mean of an (N, n_I, h, w) guide along its channel axis.
 
-    ``store``: the storage type of the layer (a torch dtype).  The layer
-    stores every guide it reads in that type, so the grey guide is rounded
-    to it (round to nearest even); a rounding is a quantisation, taken here
-    in the precision the layer takes it in: the channels summed in order in
-    FP32, one FP32 division by n_I, then the rounding.  Without ``store``
-    the mean is exact (FP64).
+    Sec. 4.2 (DGF_b): when the guide and the output differ in channel count,
+    F turns the guide into a grey image by averaging along the channel axis.
+    The mean is exact (FP64); nothing about its storage or summation order
+    is part of the definition.
     """
-    I = _f64(I)
-    if store is None:
-        return I.mean(axis=1, keepdims=True)
-    import torch
-    I32 = I.astype(np.float32)
-    s = np.zeros(I32[:, :1].shape, dtype=np.float32)
-    for k in range(I32.shape[1]):
-        s = s + I32[:, k:k + 1]
-    G = s / np.float32(I32.shape[1])
-    return torch.from_numpy(G).to(store).double().numpy()
+    return _f64(I).mean(axis=1, keepdims=True)
 
 
-def forward_grey(p_l, I_l, I_h, r: int, eps: float, store=None, mean_ab: bool = True) -> np.ndarray:
+def forward_grey(p_l, I_l, I_h, r: int, eps: float, mean_ab: bool = True) -> np.ndarray:
     """O_h (N, C, h, w) with the grey guide of I_l, I_h (N, n_I, ...) for every output channel."""
     p_l = _f64(p_l)
     C = p_l.shape[1]
-    G_l = np.repeat(grey_guide(I_l, store), C, axis=1)
-    G_h = np.repeat(grey_guide(I_h, store), C, axis=1)
+    G_l = np.repeat(grey_guide(I_l), C, axis=1)
+    G_h = np.repeat(grey_guide(I_h), C, axis=1)
     return forward(p_l, G_l, G_h, r, eps, mean_ab=mean_ab)
 
 
-def backward_grey(R, p_l, I_l, I_h, r: int, eps: float, store=None, mean_ab: bool = True):
+def backward_grey(R, p_l, I_l, I_h, r: int, eps: float, mean_ab: bool = True):
     """(dp_l, dI_l, dI_h) of sum(O_h * R) with the grey guide.
 
     The grey guide feeds every output channel, so its gradient is the sum of
@@ -473,8 +462,8 @@ def backward_grey(R, p_l, I_l, I_h, r: int, eps: float, store=None, mean_ab: boo
     """
     p_l, I_l, I_h = _f64(p_l), _f64(I_l), _f64(I_h)
     C, n_in = p_l.shape[1], I_l.shape[1]
-    G_l = np.repeat(grey_guide(I_l, store), C, axis=1)
-    G_h = np.repeat(grey_guide(I_h, store), C, axis=1)
+    G_l = np.repeat(grey_guide(I_l), C, axis=1)
+    G_h = np.repeat(grey_guide(I_h), C, axis=1)
     dp, dG_l, dG_h = backward(R, p_l, G_l, G_h, r, eps, mean_ab=mean_ab)
     dI_l = np.repeat(dG_l.sum(axis=1, keepdims=True) / n_in, n_in, axis=1)
     dI_h = np.repeat(dG_h.sum(axis=1, keepdims=True) / n_in, n_in, axis=1)

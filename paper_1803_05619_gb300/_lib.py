@@ -80,8 +80,11 @@ _SIGS = {
                               ctypes.POINTER(ctypes.c_longlong), _I]),
     "dgf_launch_count": (ctypes.c_longlong, []),
     "dgf_device_status": (_I, []),
+    "dgf_clear_device_status": (_I, []),
+    "dgf_set_wait_polls": (_I, [ctypes.c_longlong]),
     "dgf_set_tma": (None, [_I]),
     "dgf_set_fused": (None, [_I]),
+    "dgf_set_lowres_slide": (None, [_I]),
     "dgf_set_pipeline": (None, [_I]),
     "dgf_shutdown": (None, []),
     "dgf_autotune": (None, [_I]),
@@ -195,12 +198,24 @@ def dgf_device_status() -> int:
     return lib().dgf_device_status()
 
 
+def dgf_clear_device_status() -> int:
+    return lib().dgf_clear_device_status()
+
+
+def dgf_set_wait_polls(polls: int) -> int:
+    return lib().dgf_set_wait_polls(int(polls))
+
+
 def dgf_set_tma(on: bool) -> None:
     lib().dgf_set_tma(1 if on else 0)
 
 
 def dgf_set_fused(on: bool) -> None:
     lib().dgf_set_fused(1 if on else 0)
+
+
+def dgf_set_lowres_slide(on: bool) -> None:
+    lib().dgf_set_lowres_slide(1 if on else 0)
 
 
 def dgf_set_pipeline(on: bool) -> None:

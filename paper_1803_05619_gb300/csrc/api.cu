@@ -40,6 +40,10 @@ static dgf_status fail(dgf_status s, const char* fmt, ...) {
 }
 
 static dgf_status cuda_fail(cudaError_t e, const char* what) {
+    // consume the runtime's record of a non-sticky error (a launch or
+    // attribute call the runtime refused), so that it is reported once, by
+    // this call, and not again by a later launch check
+    cudaGetLastError();
     return fail(DGF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -101,20 +105,83 @@ class Launcher {
 };
 
 // --------------------------------------------------------------- status word
-// Device-side error bits (bounded waits that ran out); read by dgf_device_status.
-__device__ uint32_t g_status_word;
+// The status block of tma.cuh, one per device: error bits, the polls of a
+// first wait on a copy, and the address of the pinned host word that
+// mirrors the error bits (set up by the first call of a workspace entry
+// point on the device).
+__device__ uint32_t g_status_block[4] = {0u, (uint32_t)kWaitLimit, 0u, 0u};
+
+// Device address of the status block on the current device, resolved once
+// per device under a lock (concurrent first calls from several host threads).
+static std::mutex g_status_mu;
+static uint32_t* g_status_dev[64] = {nullptr};
+static volatile uint32_t* g_status_host[64] = {nullptr};
 
 static uint32_t* status_ptr() {
-    static uint32_t* p[64] = {nullptr};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return nullptr;
-    if (p[dev] == nullptr) {
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (g_status_dev[dev] == nullptr) {
         void* a = nullptr;
-        if (cudaGetSymbolAddress(&a, g_status_word) != cudaSuccess) return nullptr;
-        p[dev] = static_cast<uint32_t*>(a);
+        if (cudaGetSymbolAddress(&a, g_status_block) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_status_dev[dev] = static_cast<uint32_t*>(a);
     }
-    return p[dev];
+    return g_status_dev[dev];
+}
+
+// The pinned host mirror of the current device's error bits: allocated and
+// published to the device block on the first call (a synchronous copy, so
+// that first call must not come during a stream capture).
+static void status_mirror_setup() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return;
+    uint32_t* blk = status_ptr();
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (blk == nullptr || g_status_host[dev] != nullptr) return;
+    // (a failure leaves no mirror and clears the runtime's last error, so
+    // the calls that follow see only their own errors)
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, 64, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    memset(h, 0, 64);
+    void* hd = nullptr;
+    if (cudaHostGetDevicePointer(&hd, h, 0) != cudaSuccess) {
+        cudaFreeHost(h);
+        cudaGetLastError();
+        return;
+    }
+    uint32_t bits = 0;  // bits a kernel recorded before the mirror existed
+    if (cudaMemcpy(&bits, blk, sizeof bits, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(blk + 2, &hd, sizeof hd, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFreeHost(h);
+        cudaGetLastError();
+        return;
+    }
+    static_cast<uint32_t*>(h)[0] = bits;
+    g_status_host[dev] = static_cast<volatile uint32_t*>(h);
+}
+
+// Every entry point starts here: an error a kernel recorded in an earlier
+// call on this device (visible in the host mirror without synchronising)
+// makes every later call fail until dgf_clear_device_status().
+static dgf_status entry_check(bool setup) {
+    if (setup) status_mirror_setup();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return DGF_OK;
+    volatile uint32_t* m = g_status_host[dev];
+    if (m != nullptr && *m != 0u)
+        return fail(DGF_ERR_TIMEOUT,
+                    "a bounded device wait ran out in an earlier call on this device (its results are "
+                    "invalid); dgf_clear_device_status() resets the error");
+    return DGF_OK;
 }
 
 // ------------------------------------------------------------------ sizes
@@ -257,11 +324,52 @@ static bool pick_lowres_tiles(int r, Plan& p) {
 // K3 strip segments: low-res rows per segment
 static int default_k3_lth(int) { return 32; }
 
-static std::vector<LowCfg> low_candidates(int r, bool k4);
-static bool in_candidates(const LowCfg& c, int r, bool k4) {
-    for (const LowCfg& x : low_candidates(r, k4))
+// Small planes: the strip kernels' segment length (rows per warp) is shrunk
+// until one plane alone gives a few warps per SM, so a small image is not
+// a handful of warps walking long row chains.  The rule looks at the plane
+// shape only, never at the number of planes in a call, so a plane's bits do
+// not depend on the call it is in (and every kernel it is applied to gives
+// the same bits at every segment length except K4, whose shift constant
+// comes from the segment's first row).
+static int g_sms = 0;
+static int sm_count() {
+    if (g_sms == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 152;
+        }
+        g_sms = v;
+    }
+    return g_sms;
+}
+static int fill_ls(int ls, int nstrip, int rows, int min_ls) {
+    const long long want = 4LL * sm_count();  // warps of one plane
+    while (ls > min_ls && (long long)nstrip * ((rows + ls - 1) / ls) < want) ls = std::max(min_ls, ls / 2);
+    return ls;
+}
+
+static std::vector<LowCfg> low_candidates(int r, bool k4, dgf_dtype dt);
+static bool in_candidates(const LowCfg& c, int r, bool k4, dgf_dtype dt) {
+    for (const LowCfg& x : low_candidates(r, k4, dt))
         if (x.fast == c.fast && x.a == c.a && x.b == c.b) return true;
     return false;
+}
+
+// Sliding-sum low-res strips for 16-bit storage (dgf_set_lowres_slide).
+static bool g_slide_allowed = true;
+
+// Table entries of the low-res kernels: b > 0 column-walking tiles (CW = a,
+// EY1 = b), b == 0 strips (a rows per segment), b < 0 sliding strips (a rows
+// per segment, -b columns per lane).
+static LowCfg low_from_table(int a, int b) {
+    if (b < 0) return LowCfg{3, a, -b};
+    return LowCfg{b == 0 ? 2 : 1, a, b};
+}
+static void low_to_table(const LowCfg& c, int& a, int& b) {
+    a = c.a;
+    b = c.fast == 3 ? -c.b : c.b;
 }
 
 // Shapes from the autotuner's table override the defaults (whether or not
@@ -272,6 +380,12 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     p.F = integer_factor(h_l, w_l, h, w);
     p.vec = pick_vec(dt, w, hires_ptrs);
     pick_lowres_tiles(r, p);
+    // 16-bit storage: the sliding-sum strips (FP32 storage keeps the
+    // exactly centred forms, which its tighter gates need)
+    if (g_slide_allowed && dt != DGF_F32 && slide_radius(r)) {
+        p.k1 = LowCfg{3, 0, slide_k1_v(r)};
+        p.k4 = LowCfg{3, 0, slide_k4_v(r)};
+    }
     p.k3_fast = p.F > 0 && k3_fast_ok(p.vec, p.F);
     p.k2_strip = p.F > 0 && k2_strip_ok(p.vec, p.F);
     p.k3_lth = default_k3_lth(p.F);
@@ -280,12 +394,12 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     // it is one of the shapes the kernels are built for
     if (low_fast_radius(r)) {
         if (tune_lookup(TuneKey{1, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b)) {
-            const LowCfg c{b == 0 ? 2 : 1, a, b};
-            if (in_candidates(c, r, false)) p.k1 = c;
+            const LowCfg c = low_from_table(a, b);
+            if (in_candidates(c, r, false, dt)) p.k1 = c;
         }
         if (tune_lookup(TuneKey{4, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b)) {
-            const LowCfg c{b == 0 ? 2 : 1, a, b};
-            if (in_candidates(c, r, true)) p.k4 = c;
+            const LowCfg c = low_from_table(a, b);
+            if (in_candidates(c, r, true, dt)) p.k4 = c;
         }
     }
     if (tune_lookup(TuneKey{2, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256) {
@@ -344,9 +458,14 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     return p;
 }
 
-static std::vector<LowCfg> low_candidates(int r, bool k4) {
+static std::vector<LowCfg> low_candidates(int r, bool k4, dgf_dtype dt) {
     std::vector<LowCfg> v;
     if (!low_fast_radius(r)) return v;
+    if (g_slide_allowed && dt != DGF_F32 && slide_radius(r))
+        for (int V : {2, 4, 8})
+            if (slide_v_built(r, V, k4))
+                for (int seg : {8, 12, 16, 24, 32, 48, 64})
+                    if (seg >= 2 * r) v.push_back(LowCfg{3, seg, V});
     if (r <= 2)
         for (int seg : {8, 16, 24, 32, 48, 64, 128}) v.push_back(LowCfg{2, seg, 0});
     static const int cws[] = {64, 128, 256};
@@ -432,6 +551,7 @@ static bool make_k3_maps(K3Maps& m, const void* R, const void* G, dgf_dtype dt, 
 // wider and the kernel computes the offset per tile.
 static bool k1_box(const LowCfg& c, int r, int esz, int& bx, int& by, int& off) {
     const int U = 16 / esz;
+    if (c.fast == 3) return false;  // the sliding strips read rows directly
     if (c.fast == 2) {
         // warp strips (two columns per lane): 64 columns plus one 16-byte
         // unit (the strip's first column is rounded down to it), whole
@@ -498,6 +618,8 @@ static bool make_k2_map(K2Map& m, const void* in, dgf_dtype dt, int planes, int 
 static cudaError_t launch_k2_plan(dgf_dtype dt, const float2* coef, const void* in, void* out, int planes, int h_l,
                                   int w_l, int h, int w, const Plan& p, int shape, cudaStream_t s) {
     if (p.k2_strip) {
+        const int K = p.vec / p.F;
+        shape = fill_ls(shape, (w_l + 32 * K - 1) / (32 * K), h_l, 2);
         K2Map map;
         const bool tma = make_k2_map(map, in, dt, planes, h, w, p.vec, p.F);
         return launch_k2_strip(dt, coef, in, out, planes, h_l, w_l, h, w, p.vec, p.F, shape, tma ? &map : nullptr,
@@ -525,9 +647,12 @@ static TmaTriple make_k4_maps(const void* G, dgf_dtype dg, const void* P, dgf_dt
 }
 
 // stats: window statistics saved by the backward K1 pass (strip forms), or null
+static LowCfg low_fill(LowCfg c, int r, int h_l, int w_l, bool k4);
+
 static cudaError_t run_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP,
-                          void* dG, int planes, int h_l, int w_l, int r, float eps, const LowCfg& c, cudaStream_t s,
+                          void* dG, int planes, int h_l, int w_l, int r, float eps, const LowCfg& c0, cudaStream_t s,
                           const float4* stats = nullptr) {
+    const LowCfg c = low_fill(c0, r, h_l, w_l, true);
     const TmaTriple tma = make_k4_maps(G, gf32 ? DGF_F32 : dt, P, dt, dcoef, planes, h_l, w_l, r, c);
     return launch_k4(dt, gf32, G, P, dcoef, dP, dG, planes, h_l, w_l, r, eps, c, &tma, status_ptr(), stats, s);
 }
@@ -580,7 +705,7 @@ static void tune_k1(dgf_dtype dt, bool gf32, const void* G, const void* P, float
     if (tune_lookup(key, a, b)) return;
     float best = 1e30f;
     LowCfg bc = p.k1;
-    for (const LowCfg& c : low_candidates(r, false)) {
+    for (const LowCfg& c : low_candidates(r, false, dt)) {
         size_t landing = 0;
         TmaPair tma = make_tma_pair(G, gf32 ? DGF_F32 : dt, P, dt, planes, h_l, w_l, r, c, landing);
         const size_t smem = k1_cfg_smem(c, r, tma.enabled ? landing : 0);
@@ -593,7 +718,9 @@ static void tune_k1(dgf_dtype dt, bool gf32, const void* G, const void* P, float
         }
     }
     if (best < 1e30f) {
-        tune_store(key, bc.a, bc.b);
+        int ta, tb;
+        low_to_table(bc, ta, tb);
+        tune_store(key, ta, tb);
         p.k1 = bc;
     }
 }
@@ -606,7 +733,7 @@ static void tune_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const
     if (tune_lookup(key, a, b)) return;
     float best = 1e30f;
     LowCfg bc = p.k4;
-    for (const LowCfg& c : low_candidates(r, true)) {
+    for (const LowCfg& c : low_candidates(r, true, dt)) {
         const float ms = time_launch(s, [&] {
             return run_k4(dt, gf32, G, P, dcoef, dP, dG, planes, h_l, w_l, r, eps, c, s, c.fast == 2 ? stats : nullptr);
         }, 3);
@@ -616,7 +743,9 @@ static void tune_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const
         }
     }
     if (best < 1e30f) {
-        tune_store(key, bc.a, bc.b);
+        int ta, tb;
+        low_to_table(bc, ta, tb);
+        tune_store(key, ta, tb);
         p.k4 = bc;
     }
 }
@@ -754,15 +883,25 @@ static void tune_k13(dgf_dtype dt, const void* G, const void* P, float2* coef, f
     if (bl > 0) p.k13_ls = bl;
 }
 
+// the strip forms' segment rows for this plane shape (fill_ls)
+static LowCfg low_fill(LowCfg c, int r, int h_l, int w_l, bool k4) {
+    if (c.fast == 2 && r >= 1) {
+        const int out = k4 ? 32 - 4 * r : 64 - 4 * r;
+        if (out > 0) c.a = fill_ls(c.a, (w_l + out - 1) / out, h_l, 4);
+    }
+    return c;
+}
+
 static cudaError_t run_k1(Launcher& L, dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef,
                           int planes, int h_l, int w_l, int r, float eps, const Plan& p, cudaStream_t s,
                           float4* stats = nullptr) {
+    const LowCfg c = low_fill(p.k1, r, h_l, w_l, false);
     size_t landing = 0;
-    TmaPair tma = make_tma_pair(G, gf32 ? DGF_F32 : dt, P, dt, planes, h_l, w_l, r, p.k1, landing);
-    const size_t smem = k1_cfg_smem(p.k1, r, tma.enabled ? landing : 0);
+    TmaPair tma = make_tma_pair(G, gf32 ? DGF_F32 : dt, P, dt, planes, h_l, w_l, r, c, landing);
+    const size_t smem = k1_cfg_smem(c, r, tma.enabled ? landing : 0);
     uint32_t* st = status_ptr();
     return L.run("k1_lowres_coef", [&] {
-        return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, p.k1, tma, smem, st, stats, s);
+        return launch_k1(dt, gf32, G, P, coef, planes, h_l, w_l, r, eps, c, tma, smem, st, stats, s);
     });
 }
 
@@ -824,9 +963,13 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
         // with fast taps for factors 4 and 8 only
         b.F = p.k2_strip ? p.F : ((p.F == 4 || p.F == 8) ? p.F : 0);
         b.vec = p.vec;
+        if (p.k1.fast == 3) {  // sliding strips: the single call's segment rows and columns per lane
+            if (p.k1.a == 0) p.k1.a = slide_auto_seg(im.h_l, im.r);
+            if (p.k1.b == 0) p.k1.b = slide_k1_v(im.r);
+        }
         b.k1_fast = p.k1.fast;
-        b.k1_ty = p.k1.fast ? p.k1.b : p.k1.a;  // tiles: EY1; generic: TY; strips: 0
-        b.k1_tx = p.k1.fast ? p.k1.a : p.k1.b;  // tiles: CW;  generic: TX; strips: rows per segment
+        b.k1_ty = p.k1.fast ? p.k1.b : p.k1.a;  // tiles: EY1; generic: TY; strips: 0; sliding: V
+        b.k1_tx = p.k1.fast ? p.k1.a : p.k1.b;  // tiles: CW;  generic: TX; strips, sliding: rows per segment
         low_grid(p.k1, im.r, im.h_l, im.w_l, b.k1_nx, b.k1_ny);
         if (p.k2_strip) {
             // work items of kWarps strip segments (one per warp); k2_th = low-res rows per segment
@@ -946,7 +1089,7 @@ size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r, d
 static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
                                int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
                                void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab,
-                               bool guide_low = false) {
+                               bool guide_low = false, bool guide_f32 = false) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
@@ -960,10 +1103,23 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
     char* ws = static_cast<char*>(workspace);
     float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
     const int planes = N * C;
-    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr, {I_h, O_h}, mean_ab);
+    // an FP32 guide over 16-bit data (the grey guide): FP32 guide reads in K1
+    // and the K2 tiles; the strip and fused forms read guides in dt
+    const bool gf = guide_f32 && dt != DGF_F32;
+    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr || gf, {I_h, O_h}, mean_ab);
     Launcher L(s);
     cudaError_t e;
-    const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab;
+    const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab && !gf;
+    if (gf) {
+        e = run_k1(L, dt, true, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+        if (e != cudaSuccess) return cuda_fail(e, "k1");
+        e = L.run("k2_hires_apply", [&] {
+            return launch_k2_guide_f32(dt, coef, static_cast<const float*>(I_h), O_h, planes, h_l, w_l, h, w, p.vec,
+                                       p.F, p.k2_th, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k2");
+        return DGF_OK;
+    }
     if (g == nullptr) {
         if (tuning && p.k12_ok) {
             // shapes of the two-kernel forward first: K12 is timed against it
@@ -975,8 +1131,9 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
                 p.k12_ok = p.k12 = false;  // the tuner chose K1 tiles
         }
         if (p.k12) {
+            const int ls = fill_ls(p.k12_ls, (w_l + 31) / 32, h_l, 2);
             e = L.run("k12_fused_forward", [&] {
-                return launch_k12(dt, I_l, p_l, I_h, O_h, planes, h_l, w_l, h, w, r, p.F, eps, p.k12_ls, s);
+                return launch_k12(dt, I_l, p_l, I_h, O_h, planes, h_l, w_l, h, w, r, p.F, eps, ls, s);
             });
             if (e != cudaSuccess) return cuda_fail(e, "k12");
             return DGF_OK;
@@ -1050,7 +1207,7 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
 static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, const void* p_l, const void* I_l,
                                  const void* I_h, void* dp_l, void* dI_l, void* dI_h, int planes, int h_l, int w_l,
                                  int h, int w, int r, float eps, Plan& p, char* ws, const Layout& lay, cudaStream_t s,
-                                 bool tuning) {
+                                 bool tuning, bool gf = false) {
     float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
     float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
     cudaError_t e;
@@ -1059,6 +1216,13 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
     // window's statistics for K4, which then skips recomputing them
     const bool need_k4 = dp_l != nullptr || dI_l != nullptr;
     if (tuning && (dI_h != nullptr || need_k4)) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
+    // K4's form decides whether the K1 pass saves statistics, so it is tuned
+    // before that pass, on whatever the workspace holds (timing only; the
+    // real K4 launch below overwrites its outputs): the first call of a key
+    // then runs exactly the kernels of every later call
+    if (tuning && need_k4)
+        tune_k4(dt, gf, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, s, p,
+                p.k1.fast == 2 ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr);
     const bool use_stats = need_k4 && p.k1.fast == 2 && p.k4.fast == 2;
     float4* stats = use_stats ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr;
     bool fused = false;
@@ -1072,9 +1236,10 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
                          p);
             }
             if (p.k13) {
+                const int ls = fill_ls(p.k13_ls, (w_l + 29) / 30, h_l, 2);
                 e = L.run("k13_fused_backward", [&] {
                     return launch_k13(dt, I_l, p_l, maps, dI_h, dcoef, stats, planes, h_l, w_l, h, w, r, p.F, eps,
-                                      p.k13_ls, status_ptr(), s);
+                                      ls, status_ptr(), s);
                 });
                 if (e != cudaSuccess) return cuda_fail(e, "k13");
                 fused = true;
@@ -1082,7 +1247,7 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
         }
     }
     if (!fused && (dI_h != nullptr || use_stats)) {
-        e = run_k1(L, dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s, stats);
+        e = run_k1(L, dt, gf, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s, stats);
         if (e != cudaSuccess) return cuda_fail(e, "k1");
     }
     if (fused) {
@@ -1092,7 +1257,8 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
         K3Maps maps;
         const bool tma = make_k3_maps(maps, dO_h, I_h, dt, planes, h, w, p.vec, p.F);
         e = L.run("k3_hires_bwd", [&] {
-            return launch_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F, p.k3_lth,
+            return launch_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F,
+                             fill_ls(p.k3_lth, (w_l + 30 * (p.vec / p.F) - 1) / (30 * (p.vec / p.F)), h_l, 2),
                              tma ? &maps : nullptr, status_ptr(), s);
         });
         if (e != cudaSuccess) return cuda_fail(e, "k3");
@@ -1104,15 +1270,14 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
             if (e != cudaSuccess) return cuda_fail(e, "k2 scale");
         }
         e = L.run("k3_gather_general", [&] {
-            return launch_k3_general(dt, dO_h, I_h, dcoef, planes, h_l, w_l, h, w, s);
+            return launch_k3_general(dt, dO_h, I_h, dcoef, planes, h_l, w_l, h, w, s, gf);
         });
         if (e != cudaSuccess) return cuda_fail(e, "k3 general");
     }
     if (need_k4) {
-        if (tuning) tune_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, s, p, stats);
         const float4* k4_stats = p.k4.fast == 2 ? stats : nullptr;
         e = L.run("k4_lowres_bwd", [&] {
-            return run_k4(dt, false, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4, s, k4_stats);
+            return run_k4(dt, gf, I_l, p_l, dcoef, dp_l, dI_l, planes, h_l, w_l, r, eps, p.k4, s, k4_stats);
         });
         if (e != cudaSuccess) return cuda_fail(e, "k4");
     }
@@ -1164,7 +1329,8 @@ static dgf_status backward_pipelined(dgf_dtype dt, const void* dO_h, const void*
             const bool tma = make_k3_maps(maps, dO, G_h, dt, n, h, w, p.vec, p.F);
             e = Lhi.run("k3_hires_bwd", [&] {
                 return launch_k3(dt, coef + p0 * lw, dO, G_h, dG_h, dcoef + p0 * lw, n, h_l, w_l, h, w, p.vec, p.F,
-                                 p.k3_lth, tma ? &maps : nullptr, status_ptr(), pp->hi);
+                                 fill_ls(p.k3_lth, (w_l + 30 * (p.vec / p.F) - 1) / (30 * (p.vec / p.F)), h_l, 2),
+                                 tma ? &maps : nullptr, status_ptr(), pp->hi);
             });
             if (e != cudaSuccess) return cuda_fail(e, "k3");
             if ((e = cudaEventRecord(pp->k3[gi], pp->hi)) != cudaSuccess) return cuda_fail(e, "pipeline event");
@@ -1191,7 +1357,8 @@ static dgf_status backward_pipelined(dgf_dtype dt, const void* dO_h, const void*
 static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l,
                                 void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w,
                                 int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
-                                size_t ws_bytes, dgf_stream_t stream, bool mean_ab, bool guide_low = false) {
+                                size_t ws_bytes, dgf_stream_t stream, bool mean_ab, bool guide_low = false,
+                                bool guide_f32 = false) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
@@ -1216,9 +1383,19 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
     float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
     float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
     const int planes = N * C;
-    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr, {dO_h, I_h, dI_h}, mean_ab);
+    const bool gf = guide_f32 && dt != DGF_F32;  // FP32 guide over 16-bit data (the grey guide)
+    Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr || gf, {dO_h, I_h, dI_h}, mean_ab);
     Launcher L(s);
     cudaError_t e;
+    if (gf) {
+        // K1 and K4 read the FP32 guide; the high-res gradients come from the
+        // general K2 (d I_h = d O_h * Abar_h) and K3 gather (FP32 guide reads)
+        p.k3_fast = false;
+        p.k13_ok = p.k13 = false;
+        if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
+        return backward_plain(L, dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws,
+                              lay, s, false, true);
+    }
     if (g == nullptr) {
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
         const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab;
@@ -1290,10 +1467,11 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
 dgf_status dgf_forward(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
                        int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
                        size_t ws_bytes, dgf_stream_t stream) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
     return forward_impl(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream, true);
 }
 
-// Grey guide (Sec. 6.3): the guide's channel count when it differs from the
+// Grey guide (Sec. 4.2, DGF_b): the guide's channel count when it differs from the
 // output's C (its channel mean then guides every output channel); 0 when the
 // guide has the output's channels (F the identity).
 static int grey_channels(const dgf_options* opt, int C) {
@@ -1311,15 +1489,15 @@ struct GreyLayout {
 static GreyLayout grey_layout(int N, int C, int h_l, int w_l, int h, int w, dgf_dtype dt) {
     GreyLayout L;
     size_t off = layout(N, C, h_l, w_l, false).total;
-    const size_t lo = (size_t)N * C * h_l * w_l * esize(dt), hi = (size_t)N * C * h * w * esize(dt);
-    L.gl = off;
-    off += align256(lo);
+    const size_t lo = (size_t)N * C * h_l * w_l, hi = (size_t)N * C * h * w;
+    L.gl = off;  // the grey guides, FP32
+    off += align256(lo * 4);
     L.gh = off;
-    off += align256(hi);
-    L.dgl = off;
-    off += align256(lo);
+    off += align256(hi * 4);
+    L.dgl = off;  // their gradients per output channel: FP32 at low res (K4 with an FP32 guide), dt at high res
+    off += align256(lo * 4);
     L.dgh = off;
-    off += align256(hi);
+    off += align256(hi * esize(dt));
     L.total = off;
     return L;
 }
@@ -1345,19 +1523,22 @@ static dgf_status forward_grey(const void* p_l, const void* I_l, const void* I_h
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
     Launcher L(s);
+    float* Gl = reinterpret_cast<float*>(ws + gl.gl);
+    float* Gh = reinterpret_cast<float*>(ws + gl.gh);
     cudaError_t e = L.run("grey_guide", [&] {
-        return launch_grey_mean(dt, I_l, ws + gl.gl, N, n_in, C, (size_t)h_l * w_l, s);
+        return launch_grey_mean(dt, I_l, Gl, N, n_in, C, (size_t)h_l * w_l, s);
     });
     if (e == cudaSuccess)
-        e = L.run("grey_guide", [&] { return launch_grey_mean(dt, I_h, ws + gl.gh, N, n_in, C, (size_t)h * w, s); });
+        e = L.run("grey_guide", [&] { return launch_grey_mean(dt, I_h, Gh, N, n_in, C, (size_t)h * w, s); });
     if (e != cudaSuccess) return cuda_fail(e, "grey guide");
-    return forward_impl(p_l, ws + gl.gl, ws + gl.gh, O_h, N, C, h_l, w_l, h, w, r, eps, dt, nullptr, workspace,
-                        ws_bytes, stream, mean_ab);
+    return forward_impl(p_l, Gl, Gh, O_h, N, C, h_l, w_l, h, w, r, eps, dt, nullptr, workspace, ws_bytes, stream,
+                        mean_ab, false, true);
 }
 
 dgf_status dgf_forward_opt(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
                            int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
                            void* workspace, size_t ws_bytes, dgf_stream_t stream, const dgf_options* opt) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
     const bool mean_ab = opt == nullptr || opt->mean_ab != 0;
     const int n_in = grey_channels(opt, C);
     if (n_in != 0)
@@ -1370,6 +1551,7 @@ dgf_status dgf_forward_opt(const void* p_l, const void* I_l, const void* I_h, vo
 dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l, void* dI_l,
                         void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w, int r, float eps,
                         dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes, dgf_stream_t stream) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
     return backward_impl(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace,
                          ws_bytes, stream, true);
 }
@@ -1392,28 +1574,29 @@ static dgf_status backward_grey(const void* dO_h, const void* p_l, const void* I
     {
         Launcher L(s);
         cudaError_t e = L.run("grey_guide", [&] {
-            return launch_grey_mean(dt, I_l, ws + gl.gl, N, n_in, C, (size_t)h_l * w_l, s);
+            return launch_grey_mean(dt, I_l, reinterpret_cast<float*>(ws + gl.gl), N, n_in, C, (size_t)h_l * w_l, s);
         });
         if (e == cudaSuccess)
-            e = L.run("grey_guide",
-                      [&] { return launch_grey_mean(dt, I_h, ws + gl.gh, N, n_in, C, (size_t)h * w, s); });
+            e = L.run("grey_guide", [&] {
+                return launch_grey_mean(dt, I_h, reinterpret_cast<float*>(ws + gl.gh), N, n_in, C, (size_t)h * w, s);
+            });
         if (e != cudaSuccess) return cuda_fail(e, "grey guide");
     }
     // Algorithm 1 per output channel with the repeated grey guide, its guide
     // gradients into the workspace, then their sum over the channels / n_I
     st = backward_impl(dO_h, p_l, ws + gl.gl, ws + gl.gh, dp_l, dI_l ? ws + gl.dgl : nullptr,
                        dI_h ? ws + gl.dgh : nullptr, nullptr, N, C, h_l, w_l, h, w, r, eps, dt, nullptr, workspace,
-                       ws_bytes, stream, mean_ab);
+                       ws_bytes, stream, mean_ab, false, true);
     if (st != DGF_OK) return st;
     Launcher L(s);
     cudaError_t e = cudaSuccess;
     if (dI_l != nullptr)
         e = L.run("grey_guide_adjoint", [&] {
-            return launch_grey_adjoint(dt, ws + gl.dgl, dI_l, N, n_in, C, (size_t)h_l * w_l, s);
+            return launch_grey_adjoint(dt, true, ws + gl.dgl, dI_l, N, n_in, C, (size_t)h_l * w_l, s);
         });
     if (e == cudaSuccess && dI_h != nullptr)
         e = L.run("grey_guide_adjoint",
-                  [&] { return launch_grey_adjoint(dt, ws + gl.dgh, dI_h, N, n_in, C, (size_t)h * w, s); });
+                  [&] { return launch_grey_adjoint(dt, false, ws + gl.dgh, dI_h, N, n_in, C, (size_t)h * w, s); });
     if (e != cudaSuccess) return cuda_fail(e, "grey guide adjoint");
     return DGF_OK;
 }
@@ -1422,6 +1605,7 @@ dgf_status dgf_backward_opt(const void* dO_h, const void* p_l, const void* I_l, 
                             void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w, int r,
                             float eps, dgf_dtype dt, const dgf_guide* g, void* workspace, size_t ws_bytes,
                             dgf_stream_t stream, const dgf_options* opt) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
     const bool mean_ab = opt == nullptr || opt->mean_ab != 0;
     const int n_in = grey_channels(opt, C);
     if (n_in != 0)
@@ -1448,6 +1632,7 @@ extern "C" size_t dgf_workspace_size_batched(const dgf_image* imgs, int n, dgf_d
 
 extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtype dt, void* workspace,
                                           size_t ws_bytes, dgf_stream_t stream) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
     static thread_local BatchPrep prep;
     if ((int)dt < 0 || (int)dt > 2) return fail(DGF_ERR_INVALID, "dtype %d", (int)dt);
     dgf_status st = prepare_batch(imgs, n, dt, nullptr, prep);
@@ -1465,7 +1650,8 @@ extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtyp
     // specialised for its class, so it keeps the registers and occupancy of
     // the single-call kernel; its images keep their workspace slots.
     std::vector<int> c1, c2;
-    auto k1class = [](const BatchImage& im) { return im.r * 4 + im.k1_fast; };
+    // K1 class: radius, form and (sliding form) columns per lane
+    auto k1class = [](const BatchImage& im) { return (im.r * 4 + im.k1_fast) * 16 + (im.k1_fast == 3 ? im.k1_ty : 0); };
     auto k2class = [](const BatchImage& im) { return im.vec * 100 + im.F; };
     for (int i = 0; i < n; ++i) {
         const BatchImage& im = prep.bp.img[i];
@@ -1516,7 +1702,7 @@ extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtyp
     std::vector<std::array<void*, 1>> a2(c2.size());
     for (size_t q = 0; q < c1.size(); ++q) {
         void* f = nullptr;
-        if ((e = k1_batched_kernel(dt, c1[q] / 4, fast1[q], sm1[q], &f)) != cudaSuccess)
+        if ((e = k1_batched_kernel(dt, c1[q] / 64, fast1[q], sm1[q], &f, c1[q] % 16)) != cudaSuccess)
             return cuda_fail(e, "k1 batched attr");
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, sm1[q]);
@@ -1681,6 +1867,7 @@ extern "C" size_t dgf_workspace_size_batched_backward(const dgf_image_grad* imgs
 
 extern "C" dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dgf_dtype dt, void* workspace,
                                            size_t ws_bytes, dgf_stream_t stream) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
     size_t total = 0;
     dgf_status st = check_grad_images(imgs, n, dt, &total);
     if (st != DGF_OK) return st;
@@ -1752,14 +1939,35 @@ extern "C" int dgf_device_status(void) {
     if (p == nullptr) return -1;
     uint32_t v = 0;
     if (cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
-    const uint32_t z = 0;
-    cudaMemcpy(p, &z, sizeof z, cudaMemcpyHostToDevice);
     return (int)v;
+}
+
+extern "C" dgf_status dgf_clear_device_status(void) {
+    uint32_t* p = status_ptr();
+    if (p == nullptr) return fail(DGF_ERR_CUDA, "status word unavailable");
+    const uint32_t z = 0;
+    cudaError_t e = cudaMemcpy(p, &z, sizeof z, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && g_status_host[dev] != nullptr) *g_status_host[dev] = 0u;
+    return DGF_OK;
+}
+
+extern "C" dgf_status dgf_set_wait_polls(long long polls) {
+    if (polls < 0 || polls > kWaitLimit) return fail(DGF_ERR_INVALID, "polls %lld not in [0, %lld]", polls, kWaitLimit);
+    uint32_t* p = status_ptr();
+    if (p == nullptr) return fail(DGF_ERR_CUDA, "status word unavailable");
+    const uint32_t v = (uint32_t)polls;
+    cudaError_t e = cudaMemcpy(p + 1, &v, sizeof v, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "set wait polls");
+    return DGF_OK;
 }
 
 extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
 
 extern "C" void dgf_set_fused(int on) { g_fused_allowed = on != 0; }
+extern "C" void dgf_set_lowres_slide(int on) { g_slide_allowed = on != 0; }
 
 extern "C" void dgf_set_pipeline(int on) { g_pipeline = on != 0; }
 
@@ -1769,8 +1977,9 @@ extern "C" int dgf_autotune_entries(void) { return tune_count(); }
 
 extern "C" dgf_status dgf_autotune_pin(int kind, dgf_dtype dt, int r, int F, int vec, int guide_f32, int a,
                                        int b) {
+    const int bmin = (kind == 1 || kind == 4) ? -8 : 0;  // b < 0: sliding strips with -b columns per lane
     if (kind < 1 || kind > 6 || (int)dt < 0 || (int)dt > 2 || r < 0 || F < 0 || vec < 0 || a < 0 ||
-        (a == 0 && kind < 5) || a > 4096 || b < 0 || b > 4096 || (guide_f32 != 0 && guide_f32 != 1))
+        (a == 0 && kind < 5) || a > 4096 || b < bmin || b > 4096 || (guide_f32 != 0 && guide_f32 != 1))
         return fail(DGF_ERR_INVALID, "autotune_pin: bad key or shape");
     tune_store(TuneKey{kind, (int)dt, r, F, vec, guide_f32}, a, b);
     return DGF_OK;
@@ -1858,6 +2067,7 @@ extern "C" size_t dgf_noalloc_max_pairs(void) { return kNoAllocPairs; }
 extern "C" dgf_status dgf_forward_noalloc(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N,
                                           int C, int h_l, int w_l, int h, int w, int r, float eps, dgf_dtype dt,
                                           dgf_stream_t stream) {
+    if (dgf_status st0 = entry_check(false); st0 != DGF_OK) return st0;
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if (N == 0) return DGF_OK;
@@ -1937,6 +2147,7 @@ extern "C" size_t dgf_host_step_device_bytes(int N, int C, int h_l, int w_l, int
 extern "C" dgf_status dgf_host_step(const dgf_host_step_io* io, int N, int C, int h_l, int w_l, int h, int w,
                                     int r, float eps, dgf_dtype dt, int groups, void* device, size_t device_bytes,
                                     dgf_stream_t stream) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if (io == nullptr) return fail(DGF_ERR_INVALID, "NULL io descriptor");

@@ -2,5 +2,5 @@
 #include "batch_k1.cuh"
 
 namespace dgf {
-template cudaError_t k1_batched_kernel_t<float>(int, int, size_t, void**);
+template cudaError_t k1_batched_kernel_t<float>(int, int, size_t, void**, int);
 }  // namespace dgf

@@ -356,7 +356,7 @@ __device__ void k13_strip(const T* __restrict__ G, const T* __restrict__ P, cons
         while (step < nblk && min(ib0 + step + 2, h_l - 1) <= have) {
             const int m = step, slot = m % NSB, i = ib0 + m;
             k3s_block_start<VEC, F>(st, src, i, L, h_l, w_l);
-            if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NSB) & 1), kWaitLimit))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NSB) & 1), first_wait_limit(status)))) {
                 ok = false;
                 return;
             }
@@ -419,7 +419,7 @@ __device__ void k13_strip(const T* __restrict__ G, const T* __restrict__ P, cons
     }
     if (!ok) {
         // record the timeout, then wait (bounded) for the copies still in flight
-        if (lane == 0) atomicOr(status, kStatusTimeout);
+        if (lane == 0) status_fail(status, kStatusTimeout);
         for (int qb = step; qb < nblk && qb < step + NSB; ++qb)
             mbar_wait(bar_s + 8u * (qb % NSB), (uint32_t)((qb / NSB) & 1), kWaitLimit);
     }

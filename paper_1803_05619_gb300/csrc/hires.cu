@@ -10,13 +10,13 @@
 
 namespace dgf {
 
-template <typename T, int VEC, int F, int MODE>
-__global__ void __launch_bounds__(kThreads) k2_apply(const float2* __restrict__ coef, const T* __restrict__ in,
+template <typename T, int VEC, int F, int MODE, typename TI = T>
+__global__ void __launch_bounds__(kThreads) k2_apply(const float2* __restrict__ coef, const TI* __restrict__ in,
                                                      T* __restrict__ out, int h_l, int w_l, int h, int w,
                                                      int TH, int pitch) {
     extern __shared__ __align__(128) float2 sAB[];
     const size_t plane = blockIdx.z;
-    apply_tile<T, VEC, F, MODE>(coef + plane * h_l * w_l, in + plane * h * w, out + plane * h * w, h_l,
+    apply_tile<T, VEC, F, MODE, TI>(coef + plane * h_l * w_l, in + plane * h * w, out + plane * h * w, h_l,
                                 w_l, h, w, blockIdx.y * TH, blockIdx.x * 32 * VEC, TH, pitch, sAB);
 }
 
@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(K3Tma<T, VEC, F>::WPC * 32)
 // One thread per low-res (i, j): sum over the high-res rows/columns whose
 // (clamped) taps include it.  Slow but exact for every size; the fast tile
 // above covers integer factors.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k3_gather_general(const T* __restrict__ R, const T* __restrict__ G,
+template <typename T, typename TG = T>
+__global__ void __launch_bounds__(kThreads) k3_gather_general(const T* __restrict__ R, const TG* __restrict__ G,
                                                               float2* __restrict__ dcoef, int h_l, int w_l,
                                                               int h, int w) {
     const size_t plane = blockIdx.z;
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kThreads) k3_gather_general(const T* __restric
             const float wx = (b0 == j ? 1.f - tx.lam : 0.f) + (b1 == j ? tx.lam : 0.f);
             if (wx == 0.f) continue;
             const float r = to_f32<T>(R[(size_t)y * w + x]);
-            ru = fmaf(wx, r * to_f32<T>(G[(size_t)y * w + x]), ru);
+            ru = fmaf(wx, r * to_f32<TG>(G[(size_t)y * w + x]), ru);
             rv = fmaf(wx, r, rv);
         }
         su = fmaf(wy, ru, su);
@@ -234,35 +234,35 @@ static cudaError_t k2s_go(const float2* coef, const void* in, void* out, int pla
     return cudaGetLastError();
 }
 
-template <typename T, int VEC, int F, int MODE>
+template <typename T, int VEC, int F, int MODE, typename TI = T>
 static cudaError_t k2_go(const float2* coef, const void* in, void* out, int planes, int h_l, int w_l,
                          int h, int w, int TH, cudaStream_t s) {
     const int pitch = k2_pitch(VEC, F, w_l, w);
     const size_t smem = k2_smem_bytes(VEC, F, h_l, h, w_l, w, TH);
-    auto kern = k2_apply<T, VEC, F, MODE>;
+    auto kern = k2_apply<T, VEC, F, MODE, TI>;
     cudaError_t e = prep(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((w + 32 * VEC - 1) / (32 * VEC), (h + TH - 1) / TH, planes);
-    kern<<<grid, kThreads, smem, s>>>(coef, static_cast<const T*>(in), static_cast<T*>(out), h_l, w_l, h,
+    kern<<<grid, kThreads, smem, s>>>(coef, static_cast<const TI*>(in), static_cast<T*>(out), h_l, w_l, h,
                                       w, TH, pitch);
     return cudaGetLastError();
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, typename TI = T>
 static cudaError_t k2_dispatch(const float2* coef, const void* in, void* out, int planes, int h_l,
                                int w_l, int h, int w, int vec, int F, int TH, cudaStream_t s) {
     constexpr int VW = 16 / sizeof(T), VH = 8 / sizeof(T);
     if (vec == VW) {
-        if (F == 4) return k2_go<T, VW, 4, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
-        if (F == 8) return k2_go<T, VW, 8, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
-        return k2_go<T, VW, 0, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        if (F == 4) return k2_go<T, VW, 4, MODE, TI>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        if (F == 8) return k2_go<T, VW, 8, MODE, TI>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        return k2_go<T, VW, 0, MODE, TI>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
     }
     if (vec == VH) {
-        if (F == 4) return k2_go<T, VH, 4, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
-        if (F == 8) return k2_go<T, VH, 8, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
-        return k2_go<T, VH, 0, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        if (F == 4) return k2_go<T, VH, 4, MODE, TI>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        if (F == 8) return k2_go<T, VH, 8, MODE, TI>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+        return k2_go<T, VH, 0, MODE, TI>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
     }
-    return k2_go<T, 1, 0, MODE>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
+    return k2_go<T, 1, 0, MODE, TI>(coef, in, out, planes, h_l, w_l, h, w, TH, s);
 }
 
 template <typename T>
@@ -306,6 +306,20 @@ cudaError_t launch_k2(dgf_dtype dt, int mode, const float2* coef, const void* in
         case DGF_F16:
             return mode == 0 ? k2_dispatch<__half, 0>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s)
                              : k2_dispatch<__half, 1>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// K2 tiles (MODE 0) reading an FP32 guide while storing O_h in the 16-bit
+// type dt (a grey guide held in FP32 over 16-bit data).
+cudaError_t launch_k2_guide_f32(dgf_dtype dt, const float2* coef, const float* in, void* out, int planes, int h_l,
+                                int w_l, int h, int w, int vec, int F, int TH, cudaStream_t s) {
+    if (planes == 0) return cudaSuccess;
+    switch (dt) {
+        case DGF_F32: return k2_dispatch<float, 0>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s);
+        case DGF_BF16:
+            return k2_dispatch<__nv_bfloat16, 0, float>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s);
+        case DGF_F16: return k2_dispatch<__half, 0, float>(coef, in, out, planes, h_l, w_l, h, w, vec, F, TH, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -365,22 +379,26 @@ cudaError_t launch_k3(dgf_dtype dt, const float2* coef, const void* R, const voi
     return cudaErrorInvalidValue;
 }
 
-template <typename T>
+template <typename T, typename TG = T>
 static cudaError_t k3g_go(const void* R, const void* G, float2* dcoef, int planes, int h_l, int w_l, int h,
                           int w, cudaStream_t s) {
     dim3 grid((w_l + 31) / 32, (h_l + kWarps - 1) / kWarps, planes);
-    k3_gather_general<T><<<grid, kThreads, 0, s>>>(static_cast<const T*>(R), static_cast<const T*>(G), dcoef,
-                                                   h_l, w_l, h, w);
+    k3_gather_general<T, TG><<<grid, kThreads, 0, s>>>(static_cast<const T*>(R), static_cast<const TG*>(G), dcoef,
+                                                       h_l, w_l, h, w);
     return cudaGetLastError();
 }
 
 cudaError_t launch_k3_general(dgf_dtype dt, const void* R, const void* G, float2* dcoef, int planes,
-                              int h_l, int w_l, int h, int w, cudaStream_t s) {
+                              int h_l, int w_l, int h, int w, cudaStream_t s, bool guide_f32) {
     if (planes == 0) return cudaSuccess;
     switch (dt) {
         case DGF_F32: return k3g_go<float>(R, G, dcoef, planes, h_l, w_l, h, w, s);
-        case DGF_BF16: return k3g_go<__nv_bfloat16>(R, G, dcoef, planes, h_l, w_l, h, w, s);
-        case DGF_F16: return k3g_go<__half>(R, G, dcoef, planes, h_l, w_l, h, w, s);
+        case DGF_BF16:
+            return guide_f32 ? k3g_go<__nv_bfloat16, float>(R, G, dcoef, planes, h_l, w_l, h, w, s)
+                             : k3g_go<__nv_bfloat16>(R, G, dcoef, planes, h_l, w_l, h, w, s);
+        case DGF_F16:
+            return guide_f32 ? k3g_go<__half, float>(R, G, dcoef, planes, h_l, w_l, h, w, s)
+                             : k3g_go<__half>(R, G, dcoef, planes, h_l, w_l, h, w, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -25,8 +25,10 @@ __device__ __forceinline__ void col_tap(int pos, int& c, float& lam) {
     lam = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
 }
 
-template <typename T, int VEC, int F, int MODE>
-__device__ void apply_tile(const float2* __restrict__ coef, const T* __restrict__ in,
+// TI: type of `in` (the guide in MODE 0, held in FP32 for a grey guide over
+// 16-bit data; d O_h in MODE 1); `out` is stored in T.
+template <typename T, int VEC, int F, int MODE, typename TI = T>
+__device__ void apply_tile(const float2* __restrict__ coef, const TI* __restrict__ in,
                            T* __restrict__ out, int h_l, int w_l, int h, int w, int Y0, int X0, int TH,
                            int pitch, float2* sAB) {
     constexpr int TW = 32 * VEC;
@@ -36,11 +38,11 @@ __device__ void apply_tile(const float2* __restrict__ coef, const T* __restrict_
     const int xs = X0 + lane * VEC;
     const bool col_ok = xs < w;
     // issue the first rows' loads before staging, so both latencies overlap
-    Vec<T, VEC> raw[U];
+    Vec<TI, VEC> raw[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int i = warp + u * kWarps, y = Y0 + i;
-        if (col_ok && i < TH && y < h) raw[u] = ldg_vec<T, VEC>(in + (size_t)y * w + xs);
+        if (col_ok && i < TH && y < h) raw[u] = ldg_vec<TI, VEC>(in + (size_t)y * w + xs);
     }
     int jlo;
     int ncol;
@@ -113,7 +115,7 @@ __device__ void apply_tile(const float2* __restrict__ coef, const T* __restrict_
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int i = i0 + u * kWarps, y = Y0 + i;
-                    if (i < TH && y < h) raw[u] = ldg_vec<T, VEC>(in + (size_t)y * w + xs);
+                    if (i < TH && y < h) raw[u] = ldg_vec<TI, VEC>(in + (size_t)y * w + xs);
                 }
             }
 #pragma unroll
@@ -121,7 +123,7 @@ __device__ void apply_tile(const float2* __restrict__ coef, const T* __restrict_
                 const int i = i0 + u * kWarps, y = Y0 + i;
                 if (i < TH && y < h) {
                     float g[VEC];
-                    unpack_vec<T, VEC>(raw[u], g);
+                    unpack_vec<TI, VEC>(raw[u], g);
                     const float2* row = sAB + i * pitch;
                     float o[VEC];
 #pragma unroll

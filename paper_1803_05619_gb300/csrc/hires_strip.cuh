@@ -357,7 +357,7 @@ __device__ void k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps
         const int slot = m % NSB;
         const int i = ib0 + m;
         k3s_block_start<VEC, F>(st, AbarIn{coef, w_l}, i, L, h_l, w_l);
-        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NSB) & 1), kWaitLimit))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NSB) & 1), first_wait_limit(status)))) {
             ok = false;
             break;
         }
@@ -380,7 +380,7 @@ __device__ void k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps
     }
     if (!ok) {
         // record the timeout, then wait (bounded) for the copies still in flight
-        if (lane == 0) atomicOr(status, kStatusTimeout);
+        if (lane == 0) status_fail(status, kStatusTimeout);
         for (int q = m; q < nblk && q < m + NSB; ++q)
             mbar_wait(bar_s + 8u * (q % NSB), (uint32_t)((q / NSB) & 1), kWaitLimit);
     }
@@ -532,7 +532,7 @@ __device__ void k2_strip_tma(const float2* __restrict__ coef, const CUtensorMap*
         const int slot = m % NSB;
         const int i = b0 + m;
         k2s_block<VEC, F>(q, CoefIn{coef, w_l}, i, L.J, h_l, w_l);
-        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NSB) & 1), kWaitLimit))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NSB) & 1), first_wait_limit(status)))) {
             ok = false;
             break;
         }
@@ -557,7 +557,7 @@ __device__ void k2_strip_tma(const float2* __restrict__ coef, const CUtensorMap*
         }
     }
     if (!ok) {
-        if (lane == 0) atomicOr(status, kStatusTimeout);
+        if (lane == 0) status_fail(status, kStatusTimeout);
         for (int qb = m; qb < nblk && qb < m + NSB; ++qb)
             mbar_wait(bar_s + 8u * (qb % NSB), (uint32_t)((qb / NSB) & 1), kWaitLimit);
     }

@@ -29,12 +29,48 @@ __host__ __device__ inline int k2_pitch(int vec, int F, int w_l, int w) {
 // Low-resolution tile configuration: fast = 1: column-walking tile kernels
 // (r in {1, 2, 4, 8}; a = CW columns, b = EY1 rows of the coefficient
 // region); fast = 2: warp-strip K1 (r in {1, 2}; a = rows per segment,
-// b = 0); fast = 0: generic tile kernels (a = TY, b = TX output tile).
+// b = 0); fast = 3: sliding-sum warp strips for 16-bit storage (r in
+// {1, 2, 4, 8}; a = output rows per segment, 0 = slide_auto_seg; b = columns
+// per lane V); fast = 0: generic tile kernels (a = TY, b = TX output tile).
 struct LowCfg {
     int fast;
     int a, b;
     int mean = 1;  // 1: box mean of A, b (fast guided filter); 0: A_l, b_l as Sec. 3.2 prints them
 };
+
+// Sliding-sum strips (lowres_slide.cuh): radii built, default columns per
+// lane, default output rows per segment (a function of the plane height and
+// r only, so a plane's bits do not depend on how many planes a call holds),
+// output columns per strip.
+bool slide_radius(int r);
+int slide_k1_v(int r);
+int slide_k4_v(int r);
+bool slide_v_built(int r, int V, bool k4);
+int slide_auto_seg(int h, int r);
+int slide_out_cols(int r, int V);
+size_t k1_slide_smem_bytes(int r, int V, int warps);
+template <int R>
+cudaError_t launch_k1_slide_r(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes, int h,
+                              int w, float eps, int S, int V, cudaStream_t s);
+template <int R>
+cudaError_t launch_k4_slide_r(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP,
+                              void* dG, int planes, int h, int w, float eps, int S, int V, cudaStream_t s);
+extern template cudaError_t launch_k1_slide_r<1>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
+                                                 float, int, int, cudaStream_t);
+extern template cudaError_t launch_k1_slide_r<2>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
+                                                 float, int, int, cudaStream_t);
+extern template cudaError_t launch_k1_slide_r<4>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
+                                                 float, int, int, cudaStream_t);
+extern template cudaError_t launch_k1_slide_r<8>(dgf_dtype, bool, const void*, const void*, float2*, int, int, int,
+                                                 float, int, int, cudaStream_t);
+extern template cudaError_t launch_k4_slide_r<1>(dgf_dtype, bool, const void*, const void*, const float2*, void*,
+                                                 void*, int, int, int, float, int, int, cudaStream_t);
+extern template cudaError_t launch_k4_slide_r<2>(dgf_dtype, bool, const void*, const void*, const float2*, void*,
+                                                 void*, int, int, int, float, int, int, cudaStream_t);
+extern template cudaError_t launch_k4_slide_r<4>(dgf_dtype, bool, const void*, const void*, const float2*, void*,
+                                                 void*, int, int, int, float, int, int, cudaStream_t);
+extern template cudaError_t launch_k4_slide_r<8>(dgf_dtype, bool, const void*, const void*, const float2*, void*,
+                                                 void*, int, int, int, float, int, int, cudaStream_t);
 
 size_t k1_smem_bytes(int r, int TY, int TX);
 size_t k4_smem_bytes(int r, int TY, int TX);
@@ -66,8 +102,12 @@ cudaError_t launch_k2(dgf_dtype dt, int mode, const float2* coef, const void* in
 cudaError_t launch_k3(dgf_dtype dt, const float2* coef, const void* R, const void* G, void* dG,
                       float2* dcoef, int planes, int h_l, int w_l, int h, int w, int vec, int F, int LS,
                       const K3Maps* maps, uint32_t* status, cudaStream_t s);
+// guide_f32: G is FP32 while R is stored in dt (a grey guide over 16-bit data)
 cudaError_t launch_k3_general(dgf_dtype dt, const void* R, const void* G, float2* dcoef, int planes,
-                              int h_l, int w_l, int h, int w, cudaStream_t s);
+                              int h_l, int w_l, int h, int w, cudaStream_t s, bool guide_f32 = false);
+// K2 tiles (MODE 0) with an FP32 guide and O_h stored in dt
+cudaError_t launch_k2_guide_f32(dgf_dtype dt, const float2* coef, const float* in, void* out, int planes, int h_l,
+                                int w_l, int h, int w, int vec, int F, int TH, cudaStream_t s);
 
 // Fused forward (K1 + K2 in one kernel per high-res warp strip; r in {1, 2};
 // one low-res cell per lane: F-pixel vectors of 8 or 16 bytes).  LS =
@@ -111,14 +151,16 @@ cudaError_t launch_k6(dgf_dtype dt, const float2* coef, const float* dG_l, const
                       cudaStream_t s);
 cudaError_t launch_wreduce(const float* partials, int nblocks, float* dW, int hidden, cudaStream_t s);
 
-// Grey guide (channel mean of an n_in-channel guide, Sec. 6.3): G (N x C
-// planes) = the mean of I's n_in planes of each image, repeated C times; and
-// its adjoint d I (N x n_in planes) = the sum of d G's C planes / n_in,
-// repeated n_in times.  `plane` = pixels per plane.
-cudaError_t launch_grey_mean(dgf_dtype dt, const void* I, void* G, int N, int n_in, int C, size_t plane,
+// Grey guide (channel mean of an n_in-channel guide, Sec. 4.2, DGF_b): G
+// (N x C planes, FP32) = the mean of I's n_in planes of each image (stored in
+// dt), repeated C times; and its adjoint d I (N x n_in planes) = the sum of
+// d G's C planes / n_in, repeated n_in times (both in dt).  `plane` = pixels
+// per plane.
+cudaError_t launch_grey_mean(dgf_dtype dt, const void* I, float* G, int N, int n_in, int C, size_t plane,
                              cudaStream_t s);
-cudaError_t launch_grey_adjoint(dgf_dtype dt, const void* dG, void* dI, int N, int n_in, int C, size_t plane,
-                                cudaStream_t s);
+// src_f32: d G is FP32 (else stored in dt)
+cudaError_t launch_grey_adjoint(dgf_dtype dt, bool src_f32, const void* dG, void* dI, int N, int n_in, int C,
+                                size_t plane, cudaStream_t s);
 
 // Column-walking low-resolution kernels, one translation unit per radius.
 template <int R>
@@ -151,7 +193,8 @@ extern template cudaError_t launch_k4_fast<8>(dgf_dtype, bool, const void*, cons
                                               cudaStream_t);
 
 // Persistent batched kernels (function pointers for graph nodes).
-cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn);
+// V: columns per lane of the sliding form (mode 3), else ignored
+cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn, int V = 0);
 cudaError_t k2_batched_kernel(dgf_dtype dt, int vec, int F, size_t smem, void** fn);
 
 }  // namespace dgf

@@ -1,13 +1,74 @@
 // Low-resolution kernels: K1 (statistics -> A, b -> Abar, bbar) and K4
 // (recompute + Algorithm 1's low-resolution gradients).
+#include <algorithm>
+
 #include "batch.cuh"
 #include "kernels.h"
 #include "lowres_fast.cuh"
 #include "lowres_generic.cuh"
 #include "lowres_strip.cuh"
 #include "lowres_strip2.cuh"
+#include "lowres_slide.cuh"
 
 namespace dgf {
+
+bool slide_radius(int r) { return r == 1 || r == 2 || r == 4 || r == 8; }
+int slide_k1_v(int) { return 4; }
+int slide_k4_v(int) { return 4; }
+bool slide_v_built(int r, int V, bool) {
+    if (V == 2 || V == 8) return r <= 2;
+    return V == 4;
+}
+int slide_auto_seg(int h, int r) { return h <= 128 ? std::max(8, 2 * r) : std::max(16, 4 * r); }
+int slide_out_cols(int r, int V) {
+    const int hb = V * ((2 * r + V - 1) / V);
+    return 32 * V - 2 * hb;
+}
+// per-warp bytes of the sliding K1 for 16-bit G and P (the batched kernel's
+// types), taken from the device code's own constant
+template <int R, int V>
+static size_t k1_slide_warp16() {
+    return (size_t)k1_slide_warp_bytes<__nv_bfloat16, __nv_bfloat16, R, V>();
+}
+size_t k1_slide_smem_bytes(int r, int V, int warps) {
+    size_t b = 0;
+    if (V == 2 && r == 1) b = k1_slide_warp16<1, 2>();
+    if (V == 2 && r == 2) b = k1_slide_warp16<2, 2>();
+    if (V == 4 && r == 1) b = k1_slide_warp16<1, 4>();
+    if (V == 4 && r == 2) b = k1_slide_warp16<2, 4>();
+    if (V == 4 && r == 4) b = k1_slide_warp16<4, 4>();
+    if (V == 4 && r == 8) b = k1_slide_warp16<8, 4>();
+    if (V == 8 && r == 1) b = k1_slide_warp16<1, 8>();
+    if (V == 8 && r == 2) b = k1_slide_warp16<2, 8>();
+    return b * (size_t)warps;
+}
+
+static cudaError_t launch_k1_slide(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes,
+                                   int h, int w, int r, float eps, const LowCfg& c, cudaStream_t s) {
+    const int S = c.a > 0 ? c.a : slide_auto_seg(h, r);
+    const int V = c.b > 0 ? c.b : slide_k1_v(r);
+    switch (r) {
+        case 1: return launch_k1_slide_r<1>(dt, gf32, G, P, coef, planes, h, w, eps, S, V, s);
+        case 2: return launch_k1_slide_r<2>(dt, gf32, G, P, coef, planes, h, w, eps, S, V, s);
+        case 4: return launch_k1_slide_r<4>(dt, gf32, G, P, coef, planes, h, w, eps, S, V, s);
+        case 8: return launch_k1_slide_r<8>(dt, gf32, G, P, coef, planes, h, w, eps, S, V, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_k4_slide(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef,
+                                   void* dP, void* dG, int planes, int h, int w, int r, float eps, const LowCfg& c,
+                                   cudaStream_t s) {
+    const int S = c.a > 0 ? c.a : slide_auto_seg(h, r);
+    const int V = c.b > 0 ? c.b : slide_k4_v(r);
+    switch (r) {
+        case 1: return launch_k4_slide_r<1>(dt, gf32, G, P, dcoef, dP, dG, planes, h, w, eps, S, V, s);
+        case 2: return launch_k4_slide_r<2>(dt, gf32, G, P, dcoef, dP, dG, planes, h, w, eps, S, V, s);
+        case 4: return launch_k4_slide_r<4>(dt, gf32, G, P, dcoef, dP, dG, planes, h, w, eps, S, V, s);
+        case 8: return launch_k4_slide_r<8>(dt, gf32, G, P, dcoef, dP, dG, planes, h, w, eps, S, V, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 template <typename TG, typename TP>
 __global__ void __launch_bounds__(kThreads) k1_coef(const TG* __restrict__ G, const TP* __restrict__ P,
@@ -257,16 +318,25 @@ size_t k4_fast_smem_bytes(int r, int CW, int EY1) {
 }
 
 size_t k1_cfg_smem(const LowCfg& c, int r, size_t tma_landing) {
+    if (c.fast == 3) return k1_slide_smem_bytes(r, c.b > 0 ? c.b : slide_k1_v(r), kWarps);  // batched: 8 warps
     if (c.fast == 2) return 0;  // warp strips keep everything in registers
     return c.fast ? k1_fast_smem_bytes(r, c.a, c.b, tma_landing) : k1_smem_bytes(r, c.a, c.b);
 }
 
 size_t k4_cfg_smem(const LowCfg& c, int r) {
-    if (c.fast == 2) return 0;
+    if (c.fast == 2 || c.fast == 3) return 0;  // strips (the sliding form sizes its own ring at launch)
     return c.fast ? k4_fast_smem_bytes(r, c.a, c.b) : k4_smem_bytes(r, c.a, c.b);
 }
 
 void low_grid(const LowCfg& c, int r, int h, int w, int& gx, int& gy) {
+    if (c.fast == 3) {
+        // batched work items: kWarps strip segments (one per warp of a CTA)
+        const int V = c.b > 0 ? c.b : slide_k1_v(r), S = c.a > 0 ? c.a : slide_auto_seg(h, r);
+        const int nstrip = (w + slide_out_cols(r, V) - 1) / slide_out_cols(r, V), nseg = (h + S - 1) / S;
+        gx = (nstrip * nseg + kWarps - 1) / kWarps;
+        gy = 1;
+        return;
+    }
     if (c.fast == 2) {
         // work items of 8 warp strips (one CTA) per plane, in one row
         const int nstrip = (w + strip2_out_cols(r) - 1) / strip2_out_cols(r), nseg = (h + c.a - 1) / c.a;
@@ -309,6 +379,7 @@ cudaError_t launch_k1(dgf_dtype dt, bool guide_f32, const void* G, const void* P
                       int h, int w, int r, float eps, const LowCfg& c, const TmaPair& tma, size_t smem,
                       uint32_t* status, float4* stats, cudaStream_t s) {
     if (planes == 0) return cudaSuccess;
+    if (c.fast == 3) return launch_k1_slide(dt, guide_f32, G, P, coef, planes, h, w, r, eps, c, s);
     if (c.fast) {
         switch (r) {
             case 1: return launch_k1_fast<1>(dt, guide_f32, G, P, coef, planes, h, w, eps, c, tma, smem, status, stats, s);
@@ -350,6 +421,7 @@ cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P
                       void* dP, void* dG, int planes, int h, int w, int r, float eps, const LowCfg& c,
                       const TmaTriple* tma, uint32_t* status, const float4* stats, cudaStream_t s) {
     if (planes == 0) return cudaSuccess;
+    if (c.fast == 3) return launch_k4_slide(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, r, eps, c, s);
     if (c.fast) {
         switch (r) {
             case 1: return launch_k4_fast<1>(dt, guide_f32, G, P, dcoef, dP, dG, planes, h, w, eps, c, tma, status, stats, s);
@@ -375,13 +447,13 @@ cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P
 }
 
 template <typename T>
-cudaError_t k1_batched_kernel_t(int r, int mode, size_t smem, void** fn);
+cudaError_t k1_batched_kernel_t(int r, int mode, size_t smem, void** fn, int V);
 
-cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn) {
+cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn, int V) {
     switch (dt) {
-        case DGF_F32: return k1_batched_kernel_t<float>(r, mode, smem, fn);
-        case DGF_BF16: return k1_batched_kernel_t<__nv_bfloat16>(r, mode, smem, fn);
-        case DGF_F16: return k1_batched_kernel_t<__half>(r, mode, smem, fn);
+        case DGF_F32: return k1_batched_kernel_t<float>(r, mode, smem, fn, V);
+        case DGF_BF16: return k1_batched_kernel_t<__nv_bfloat16>(r, mode, smem, fn, V);
+        case DGF_F16: return k1_batched_kernel_t<__half>(r, mode, smem, fn, V);
     }
     return cudaErrorInvalidValue;
 }

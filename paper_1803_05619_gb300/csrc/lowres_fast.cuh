@@ -118,11 +118,12 @@ __device__ bool fast_stage_tma(const TmaPlane* ta, const TmaPlane* tb, int plane
         tma_load_3d(smem_u32(lb), &tb->map, xl - offb, yl, plane, b);
     }
     __syncthreads();
-    bool ok = mbar_wait(b, 0, kWaitLimit);
+    bool ok = mbar_wait(b, 0, first_wait_limit(status));
     if (!ok) {
-        atomicOr(status, kStatusTimeout);
-        mbar_wait(b, 0, kWaitLimit);
+        status_fail(status, kStatusTimeout);
+        mbar_wait(b, 0, kWaitLimit);  // the copies land before the buffers are reused
     }
+    ok = __syncthreads_and(ok) != 0;  // one decision for the whole CTA
     if (ok) {
         const TA* pa = reinterpret_cast<const TA*>(la);
         const TB* pb = reinterpret_cast<const TB*>(lb);

@@ -421,7 +421,7 @@ __device__ void lowres_bwd_strip_tma(const TmaTriple* maps, int plane, TP* __res
     bool ok = true;
     for (; m < nblk; ++m) {
         const int slot = m % NS;
-        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NS) & 1), kWaitLimit))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(bar_s + 8u * slot, (uint32_t)((m / NS) & 1), first_wait_limit(status)))) {
             ok = false;
             break;
         }
@@ -479,7 +479,7 @@ __device__ void lowres_bwd_strip_tma(const TmaTriple* maps, int plane, TP* __res
         }
     }
     if (!ok) {
-        if (lane == 0) atomicOr(status, kStatusTimeout);
+        if (lane == 0) status_fail(status, kStatusTimeout);
         for (int qb = m; qb < nblk && qb < m + NS; ++qb)
             mbar_wait(bar_s + 8u * (qb % NS), (uint32_t)((qb / NS) & 1), kWaitLimit);
     }

@@ -50,6 +50,32 @@ struct K2Map {
 constexpr long long kWaitLimit = 1LL << 22;  // try_wait polls before giving up
 constexpr uint32_t kStatusTimeout = 1u;
 
+// The library's status block (one per device, in api.cu), passed to the
+// kernels as `uint32_t* status`:
+//   status[0]      error bits (kStatusTimeout: a bounded wait ran out);
+//   status[1]      polls of a first wait on a copy (kWaitLimit unless a test
+//                  lowers it to make the wait run out); the second wait, for
+//                  the copies still in flight, always polls kWaitLimit times,
+//                  so every copy has landed before its shared memory is
+//                  reused or the kernel exits;
+//   status[2..3]   address of a pinned host word mirroring the error bits
+//                  (0 when the host has not set one up), written only when an
+//                  error is recorded, so the host sees it at its next call
+//                  without synchronising.
+__device__ __forceinline__ long long first_wait_limit(const uint32_t* status) {
+    return status != nullptr ? (long long)status[1] : kWaitLimit;
+}
+
+__device__ __forceinline__ void status_fail(uint32_t* status, uint32_t bits) {
+    if (status == nullptr) return;
+    atomicOr(status, bits);
+    uint32_t* host = *reinterpret_cast<uint32_t* const volatile*>(status + 2);
+    if (host != nullptr) {
+        *reinterpret_cast<volatile uint32_t*>(host) = bits;  // the only bit there is
+        __threadfence_system();
+    }
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -113,11 +139,12 @@ __device__ bool tma_stage_pair(const TmaPlane* ta, const TmaPlane* tb, int plane
         tma_load_3d(smem_u32(lb), &tb->map, t.tx0 - 2 * t.r - tb->off, ya, plane, b);
     }
     __syncthreads();
-    bool ok = mbar_wait(b, 0, kWaitLimit);
+    bool ok = mbar_wait(b, 0, first_wait_limit(status));
     if (!ok) {
-        atomicOr(status, kStatusTimeout);
-        mbar_wait(b, 0, kWaitLimit);
+        status_fail(status, kStatusTimeout);
+        mbar_wait(b, 0, kWaitLimit);  // the copies land before the buffers are reused
     }
+    ok = __syncthreads_and(ok) != 0;  // one decision for the whole CTA
     if (ok) {
         tma_unpack<TA>(la, ta, sA, t);
         tma_unpack<TB>(lb, tb, sB, t);

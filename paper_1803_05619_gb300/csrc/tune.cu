@@ -2,7 +2,10 @@
 // factor, vector width, guide type) it times every candidate shape on the
 // call's own buffers with CUDA events and keeps the fastest.  The choice is
 // cached in memory and, when DGF_TUNE_CACHE names a file, persisted there
-// as text lines "kind dt r F vec gf32 a b" keyed also by the device name.
+// as text lines "version/device kind dt r F vec gf32 a b": keyed also by the
+// device name and by the cache version of this library (kTuneVersion, raised
+// whenever the kernels' shapes or their encoding change), so entries written
+// by another build or for another GPU are never used.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -24,14 +27,31 @@ std::map<std::tuple<std::string, int, int, int, int, int, int>, std::pair<int, i
 bool g_loaded = false;
 int g_enabled = -1;  // -1: read DGF_AUTOTUNE on first use
 
+constexpr const char* kTuneVersion = "dgf2";
+
 std::string device_name() {
     int dev = 0;
     cudaDeviceProp p;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
-    std::string s = p.name;
+    std::string s = "unknown";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
+        s = p.name;
+    } else {
+        cudaGetLastError();  // no device here: leave no error behind for later calls
+    }
     for (auto& ch : s)
-        if (ch == ' ') ch = '_';
-    return s;
+        if (ch == ' ' || ch == '/') ch = '_';
+    return std::string(kTuneVersion) + "/" + s;
+}
+
+// a table entry the plan code can read: shapes are positive except b of the
+// low-res kernels (kinds 1, 4), where b < 0 names the sliding strips
+bool entry_ok(int kind, int dt, int r, int F, int vec, int gf32, int a, int b) {
+    if (kind < 1 || kind > 6 || dt < 0 || dt > 2 || r < 0 || r > 64 || F < 0 || F > 64 || vec < 0 || vec > 64)
+        return false;
+    if (gf32 != 0 && gf32 != 1) return false;
+    if (a < 0 || a > 4096 || (a == 0 && kind < 5)) return false;
+    const int bmin = (kind == 1 || kind == 4) ? -8 : 0;
+    return b >= bmin && b <= 4096;
 }
 
 std::tuple<std::string, int, int, int, int, int, int> full_key(const TuneKey& k) {
@@ -45,11 +65,16 @@ void load_locked() {
     if (path == nullptr || *path == 0) return;
     FILE* f = fopen(path, "r");
     if (f == nullptr) return;
-    char name[256];
+    char line[512], name[256];
     int kind, dt, r, F, vec, gf32, a, b;
-    // malformed or foreign lines are skipped: a corrupt cache only costs a re-tune
-    while (fscanf(f, "%255s %d %d %d %d %d %d %d %d", name, &kind, &dt, &r, &F, &vec, &gf32, &a, &b) == 9) {
-        if (a <= 0 || b < 0 || a > 4096 || b > 4096) continue;
+    // malformed, out-of-range or truncated lines are skipped one by one: a
+    // corrupt cache only costs a re-tune of the keys it held; lines of
+    // another version or device stay in the file but never match a key
+    while (fgets(line, sizeof line, f) != nullptr) {
+        char tail = 0;
+        const int n = sscanf(line, "%255s %d %d %d %d %d %d %d %d %c", name, &kind, &dt, &r, &F, &vec, &gf32, &a,
+                             &b, &tail);
+        if (n != 9 || !entry_ok(kind, dt, r, F, vec, gf32, a, b)) continue;
         g_table[std::make_tuple(std::string(name), kind, dt, r, F, vec, gf32)] = {a, b};
     }
     fclose(f);
@@ -109,10 +134,14 @@ void tune_clear() {
     g_loaded = true;
 }
 
+// entries this device and library version would use
 int tune_count() {
     std::lock_guard<std::mutex> lk(g_mu);
     load_locked();
-    return (int)g_table.size();
+    const std::string me = device_name();
+    int n = 0;
+    for (auto& kv : g_table) n += std::get<0>(kv.first) == me;
+    return n;
 }
 
 bool stream_capturing(cudaStream_t s) {

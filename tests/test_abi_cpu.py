@@ -152,8 +152,9 @@ def test_grey_guide_options_on_host(lib):
     assert L.dgf_workspace_size_opt(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None, None) == plain
     grey = L.dgf_options(1, 3)
     nb = L.dgf_workspace_size_opt(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None, ctypes.byref(grey))
-    # the grey guide and its gradient at both resolutions, repeated over C = 1 output channel
-    assert nb >= plain + 2 * (2 * 64 * 80 * 2 + 2 * 16 * 20 * 2) and nb % 256 == 0
+    # the FP32 grey guide at both resolutions, its FP32 low-res and BF16 high-res
+    # gradients, each repeated over C = 1 output channel
+    assert nb >= plain + 2 * 64 * 80 * 4 + 2 * 16 * 20 * 4 * 2 + 2 * 64 * 80 * 2 and nb % 256 == 0
     assert L.dgf_workspace_size_opt(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None,
                                     ctypes.byref(L.dgf_options(1, -2))) == 0
     gd = L.dgf_guide(16, 32, 48, 16, 0.2)
@@ -190,3 +191,36 @@ def test_guide_low_option_on_host(lib):
     st = L.dgf_backward_opt(ptr, ptr, ptr, ptr, None, ptr, None, None, 1, 3, 16, 16, 64, 64, 1, 1e-3, L.DGF_F32,
                             ctypes.byref(gd), None, 0, None, ctypes.byref(low))
     assert st == 5
+
+
+def test_autotune_cache_skips_corrupt_and_foreign_lines(lib, tmp_path):
+    """A corrupted or foreign cache file is ignored line by line (those keys
+    are re-tuned); valid lines of this library version and device are used,
+    and pinning a shape rewrites the file keeping the other lines."""
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    me = "dgf2/unknown"  # no device in the subprocess: the device name is "unknown"
+    cache.write_text(
+        f"{me} 1 1 2 0 0 0 16 -4\n"        # sliding K1 strips, BF16, r = 2: used
+        "garbage that is not an entry\n"
+        f"{me} 2 0 0 4 4 0 12 0\n"         # K2 strip segments: used
+        f"{me} 3 0 0 4 4 0 99999 0\n"      # out of range: skipped
+        f"{me} 1 1 2 0 0 0 16\n"           # truncated: skipped
+        f"{me} 4 1 2 0 0 0 16 -9\n"        # no such column width: skipped
+        "dgf1/unknown 1 1 1 0 0 0 32 0\n"  # another library version: never used
+        f"{me} 5 0 1 4 0 0 8 0 extra\n"    # trailing junk: skipped
+        "\x00\xff\n")
+    code = ("import ctypes, sys; L = ctypes.CDLL(sys.argv[1]); n = L.dgf_autotune_entries(); "
+            "pin = int(sys.argv[2]); st = L.dgf_autotune_pin(6, 1, 1, 8, 8, 0, 16, 0) if pin else 0; "
+            "print(n, st, L.dgf_autotune_entries())")
+    env = dict(os.environ, DGF_TUNE_CACHE=str(cache), CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code, B.OUT, "1"], capture_output=True, text=True, env=env,
+                         timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.split() == ["2", "0", "3"]
+    text = cache.read_text()
+    assert "dgf1/unknown 1 1 1 0 0 0 32 0" in text and f"{me} 6 1 1 8 8 0 16 0" in text
+    out = subprocess.run([sys.executable, "-c", code, B.OUT, "0"], capture_output=True, text=True, env=env,
+                         timeout=120)
+    assert out.stdout.split() == ["3", "0", "3"]

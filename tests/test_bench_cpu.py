@@ -57,3 +57,37 @@ def test_ncu_counters_follow_the_kernel_sources(tmp_path, monkeypatch):
     assert bench.ncu_traffic("k", "wl") == 123
     assert bench.ncu_traffic("old", "wl") is None      # taken on other kernel sources
     assert bench.ncu_traffic("missing", "wl") is None
+
+
+def test_accuracy_leg_reports_the_oracle_errors(tmp_path):
+    """The oracle half of bench.py's accuracy leg on tiny cases whose 'GPU'
+    outputs are the oracle's own plus a known perturbation."""
+    import numpy as np
+
+    import oracle
+    import synth
+    d = {k: v.numpy() for k, v in synth.photo_like(3, 1, 1, 8, 10, 4).items()}
+    R = synth.upstream_grad(4, d["I_h"].shape).numpy()
+    o = oracle.forward(d["p_l"], d["I_l"], d["I_h"], 1, 1e-3)
+    dp, dil, dih = oracle.backward(R, d["p_l"], d["I_l"], d["I_h"], 1, 1e-3)
+    o2 = o.copy()
+    o2[0, 0, 3, 5] += 1e-3
+    f = tmp_path / "plain.npz"
+    np.savez(f, p_l=d["p_l"], I_l=d["I_l"], I_h=d["I_h"], R=R, O_h=o2, dp_l=dp, dI_l=dil, dI_h=2 * dih)
+    dg = {k: v.numpy() for k, v in synth.photo_like(5, 1, 3, 4, 4, 4).items()}
+    w = {k: v.numpy() for k, v in synth.guide_weights(6).items()}
+    Rg = synth.upstream_grad(7, dg["I_h"].shape).numpy()
+    og = oracle.forward_guided(dg["p_l"], dg["I_h"], w["w1"], w["w2"], w["b2"], 2, 1e-3)
+    gp, gih, gw1, gw2, gb2 = oracle.backward_guided(Rg, dg["p_l"], dg["I_h"], w["w1"], w["w2"], w["b2"], 2, 1e-3)
+    fg = tmp_path / "guided.npz"
+    np.savez(fg, p_l=dg["p_l"], I_h=dg["I_h"], R=Rg, O_h=og, dp_l=gp, dI_h=gih, w1=w["w1"], w2=w["w2"],
+             b2=w["b2"], dw1=gw1, dw2=gw2, db2=gb2)
+    man = [{"name": "p", "kind": "plain", "file": str(f), "r": 1, "eps": 1e-3, "dtype": "f32", "sample": "all"},
+           {"name": "g", "kind": "guided", "file": str(fg), "r": 2, "eps": 1e-3, "dtype": "f32", "sample": "all"}]
+    res = bench.accuracy_oracle(man, str(tmp_path))
+    assert "error" not in res, res
+    assert res["p"]["O_h"]["max_abs"] == pytest.approx(1e-3, rel=1e-6)
+    assert res["p"]["dp_l"]["max_abs"] == 0.0 and res["p"]["dI_l"]["rel_l2"] == 0.0
+    assert res["p"]["dI_h"]["rel_l2"] == pytest.approx(1.0)
+    for k in ("O_h", "dp_l", "dI_h", "dW"):
+        assert res["g"][k]["max_abs"] < 1e-12

@@ -517,15 +517,18 @@ def test_grey_backward_finite_differences():
     assert _fd_check(loss, ih, dih, n_probe=12, seed=1) < 1e-6
 
 
-@pytest.mark.parametrize("store,ulp", [(torch.bfloat16, 2.0 ** -7), (torch.float16, 2.0 ** -10)])
-def test_grey_guide_stored_rounding(store, ulp):
-    """Rounded to the storage type: representable there, within half its ulp of the exact mean."""
-    I = torch.from_numpy(rng(44).uniform(0.0, 1.0, size=(2, 3, 9, 11))).to(store).double()
-    exact = I.numpy().mean(axis=1, keepdims=True)
-    G = O.grey_guide(I, store)
-    assert np.array_equal(torch.from_numpy(G).to(store).double().numpy(), G)
-    scale = 2.0 ** np.floor(np.log2(np.maximum(np.abs(exact), 1e-30)))
-    assert np.all(np.abs(G - exact) <= 0.5 * ulp * scale * (1 + 1e-6))
+def test_grey_guide_is_the_exact_channel_mean():
+    """Sec. 4.2: the grey guide is the average along the channel axis; brute
+    force over the channels, in exact rational arithmetic on dyadic inputs."""
+    from fractions import Fraction
+    x = rng(44).integers(0, 2 ** 20, size=(2, 3, 5, 6)) / 2.0 ** 20
+    G = O.grey_guide(x)
+    assert G.shape == (2, 1, 5, 6)
+    for n in range(2):
+        for y in range(5):
+            for xx in range(6):
+                exact = sum(Fraction(float(x[n, k, y, xx])) for k in range(3)) / 3
+                assert abs(Fraction(float(G[n, 0, y, xx])) - exact) <= Fraction(1, 2 ** 53)
 
 
 # ------------------------------------------------ planted mistakes (pins bite)
