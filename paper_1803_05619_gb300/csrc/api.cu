@@ -325,7 +325,7 @@ static bool pick_lowres_tiles(int r, Plan& p) {
 static int default_k3_lth(int) { return 32; }
 
 // Small planes: the strip kernels' segment length (rows per warp) is shrunk
-// until one plane alone gives a few warps per SM, so a small image is not
+// until one plane alone gives a warp per SM, so a small image is not
 // a handful of warps walking long row chains.  The rule looks at the plane
 // shape only, never at the number of planes in a call, so a plane's bits do
 // not depend on the call it is in (and every kernel it is applied to gives
@@ -345,7 +345,7 @@ static int sm_count() {
     return g_sms;
 }
 static int fill_ls(int ls, int nstrip, int rows, int min_ls) {
-    const long long want = 4LL * sm_count();  // warps of one plane
+    const long long want = sm_count();  // warps of one plane: one per SM
     while (ls > min_ls && (long long)nstrip * ((rows + ls - 1) / ls) < want) ls = std::max(min_ls, ls / 2);
     return ls;
 }

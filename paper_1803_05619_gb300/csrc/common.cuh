@@ -69,7 +69,28 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
     f2_unpack(c, c0, c1);
     return f2_pack(__fmaf_rn(a0, b0, c0), __fmaf_rn(a1, b1, c1));
 }
-// Blackwell's paired instructions (one instruction for both halves).
+// Blackwell's paired instructions (one instruction for both halves, each
+// half rounded to nearest as its scalar instruction would be).
+__device__ __forceinline__ f32x2 f2x_add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2x_sub(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float f2_lo(f32x2 v) {
+    float a, b;
+    f2_unpack(v, a, b);
+    return a;
+}
+__device__ __forceinline__ float f2_hi(f32x2 v) {
+    float a, b;
+    f2_unpack(v, a, b);
+    return b;
+}
 __device__ __forceinline__ f32x2 f2x_mul(f32x2 a, f32x2 b) {
     f32x2 d;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));

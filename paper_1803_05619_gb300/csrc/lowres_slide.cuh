@@ -51,34 +51,39 @@ struct SlideGeom {
 
 constexpr int kSlideWarps = 4;  // warps per CTA (independent strip segments)
 
-// Radius-R horizontal window sums of a row held V columns per lane:
-// out[j] = sum over k in [-R, R] of x at lane column j + k.  Lanes reach
-// their neighbours by shuffles; results are meaningful for strip columns
-// [R, 32 V - R) only (the others read across the warp's edge).
+// Radius-R horizontal window sums of a row held V columns per lane, on
+// pairs of quantities: out[j] = sum over k in [-R, R] of x at lane column
+// j + k.  Lanes reach their neighbours by shuffles (each half moves on its
+// own; the sums are paired instructions); results are meaningful for strip
+// columns [R, 32 V - R) only (the others read across the warp's edge).
 template <int R, int V>
-__device__ __forceinline__ void hbox(const float (&x)[V], float (&out)[V]) {
-    float T[V + 2 * R];
+__device__ __forceinline__ void hbox2(const f32x2 (&x)[V], f32x2 (&out)[V]) {
+    f32x2 T[V + 2 * R];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        const int o = -R + k;                   // column offset left of the lane
-        const int dl = -((-o + V - 1) / V);     // source lane offset (negative)
-        const int j = o - dl * V;               // column inside the source lane
-        T[k] = __shfl_up_sync(0xffffffffu, x[j], -dl);
+        const int o = -R + k;
+        const int dl = -((-o + V - 1) / V);
+        const int j = o - dl * V;
+        float a, b;
+        f2_unpack(x[j], a, b);
+        T[k] = f2_pack(__shfl_up_sync(0xffffffffu, a, -dl), __shfl_up_sync(0xffffffffu, b, -dl));
     }
 #pragma unroll
     for (int j = 0; j < V; ++j) T[R + j] = x[j];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int o = V + k;
-        T[R + V + k] = __shfl_down_sync(0xffffffffu, x[o % V], o / V);
+        float a, b;
+        f2_unpack(x[o % V], a, b);
+        T[R + V + k] = f2_pack(__shfl_down_sync(0xffffffffu, a, o / V), __shfl_down_sync(0xffffffffu, b, o / V));
     }
-    float s = T[0];
+    f32x2 s = T[0];
 #pragma unroll
-    for (int k = 1; k <= 2 * R; ++k) s += T[k];
+    for (int k = 1; k <= 2 * R; ++k) s = f2x_add(s, T[k]);
     out[0] = s;
 #pragma unroll
     for (int j = 1; j < V; ++j) {
-        s = (s + T[j + 2 * R]) - T[j - 1];
+        s = f2x_sub(f2x_add(s, T[j + 2 * R]), T[j - 1]);
         out[j] = s;
     }
 }
@@ -107,40 +112,11 @@ __device__ __forceinline__ void slide_load(const T* __restrict__ src, int e, int
     }
 }
 
-// d Abar, d bbar of row e at the lane's columns (zero outside the image).
-template <int V>
-__device__ __forceinline__ void slide_load_pairs(const float2* __restrict__ src, int e, int h, int w, int x0,
-                                                 bool vec, float (&a)[V], float (&b)[V]) {
-    if (e < 0 || e >= h) {
-#pragma unroll
-        for (int j = 0; j < V; ++j) a[j] = b[j] = 0.f;
-        return;
-    }
-    const float2* row = src + (size_t)e * w;
-    if (vec) {
-#pragma unroll
-        for (int j = 0; j < V; j += 2) {
-            const float4 q = *reinterpret_cast<const float4*>(row + x0 + j);
-            a[j] = q.x;
-            b[j] = q.y;
-            a[j + 1] = q.z;
-            b[j + 1] = q.w;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const int x = x0 + j;
-            const float2 q = (x >= 0 && x < w) ? row[x] : make_float2(0.f, 0.f);
-            a[j] = q.x;
-            b[j] = q.y;
-        }
-    }
-}
-
 // Per-lane column facts.
 template <int R, int V>
 struct SlideLane {
     float nx[V];     // clipped window width of each column (1 outside the image)
+    float inx[V];    // 1 / nx, correctly rounded
     float xin[V];    // 1 inside the image, else 0
     bool col_int;    // every column of the lane has the full width 2R + 1
     bool out;        // the lane's columns are strip outputs
@@ -162,6 +138,7 @@ __device__ __forceinline__ SlideLane<R, V> slide_lane(int x_base, int w, bool al
         L.xin[j] = in ? 1.f : 0.f;
         const int n = in ? min(x + R, w - 1) - max(x - R, 0) + 1 : 1;
         L.nx[j] = (float)n;
+        L.inx[j] = __frcp_rn((float)n);
         L.col_int = L.col_int && n == 2 * R + 1;
     }
     L.out = lane * V >= Gm::HB && lane * V < Gm::HB + Gm::OUTC;
@@ -169,16 +146,18 @@ __device__ __forceinline__ SlideLane<R, V> slide_lane(int x_base, int w, bool al
     return L;
 }
 
-__device__ __forceinline__ int slide_ny(int y, int h, int R) { return min(y + R, h - 1) - max(y - R, 0) + 1; }
 
-// 1 / (window count) for a window of ny rows at column j: a compile-time
-// constant for full windows, else the correctly rounded reciprocal.
+// 1 / (window count) of the window of ny rows at column j: the product of
+// the correctly rounded reciprocals of its width and height (one multiply
+// per pixel; iny = 1 / ny is formed once per row).  Every use of a count
+// in this file goes through it, so a term subtracted from a running sum is
+// scaled exactly as it was when it was added.
 template <int R, int V>
-__device__ __forceinline__ float slide_inv(const SlideLane<R, V>& L, int j, int ny) {
-    constexpr int W = 2 * R + 1;
-    constexpr float kInvW2 = 1.f / (float)(W * W);
-    if (L.col_int && ny == W) return kInvW2;
-    return __frcp_rn(L.nx[j] * (float)ny);
+__device__ __forceinline__ float slide_inv(const SlideLane<R, V>& L, int j, float iny) {
+    return L.inx[j] * iny;
+}
+__device__ __forceinline__ float slide_iny(int y, int h, int R) {
+    return __frcp_rn((float)(min(y + R, h - 1) - max(y - R, 0) + 1));
 }
 
 // Shift constant: mean over the strip's in-image columns of row y (the
@@ -293,122 +272,130 @@ __device__ void k1_slide_segment(const TG* __restrict__ G, const TP* __restrict_
         KG = slide_shift<TG, V>(g, L.xin);
         KP = slide_shift<TP, V>(p, L.xin);
     }
-    float vg[V], vp[V], vgg[V], vgp[V], va[V], vb[V];
+    // quantities held in pairs per column: (G', P') sums, (G'^2, G'P') sums,
+    // and the second pass's (A, b) sums
+    f32x2 a1[V], a2[V], ab[V];
+    // the shift and the column mask as one paired FMA: (G', P') = (G, P) xin - (K_G, K_P) xin
+    f32x2 xin2[V], nk[V];
 #pragma unroll
-    for (int j = 0; j < V; ++j) vg[j] = vp[j] = vgg[j] = vgp[j] = va[j] = vb[j] = 0.f;
+    for (int j = 0; j < V; ++j) {
+        a1[j] = a2[j] = ab[j] = f2_splat(0.f);
+        xin2[j] = f2_splat(L.xin[j]);
+        nk[j] = f2_pack(-KG * L.xin[j], -KP * L.xin[j]);
+    }
+    const f32x2 K2 = f2_pack(KG, KP);
     // input rows through the ring, D rows ahead (the leaving row is still there)
     constexpr int D = SlideStage<R>::D, NR = SlideStage<R>::NR;
     constexpr int SLOT = 32 * V * ((int)sizeof(TG) + (int)sizeof(TP));
     unsigned char* rin = reinterpret_cast<unsigned char*>(ring + W * (V / 2) * 32);
     const int og = lane * V * (int)sizeof(TG), op = 32 * V * (int)sizeof(TG) + lane * V * (int)sizeof(TP);
-    auto issue = [&](int tt) {  // row e0 + tt into its slot
-        unsigned char* sl = rin + (tt % NR) * SLOT;
+    auto issue = [&](int tt, int slot) {  // row e0 + tt into ring slot `slot`
+        unsigned char* sl = rin + slot * SLOT;
         stage_row<TG, V>(sl + og, G, e0 + tt, h, w, L.x0, aligned);
         stage_row<TP, V>(sl + op, P, e0 + tt, h, w, L.x0, aligned);
     };
+    // a staged row's shifted (G', P') pairs
+    auto shifted = [&](int slot, f32x2 (&sh)[V]) {
+        const unsigned char* sl = rin + slot * SLOT;
+        float g[V], p[V];
+        unstage_row<TG, V>(sl + og, g);
+        unstage_row<TP, V>(sl + op, p);
+#pragma unroll
+        for (int j = 0; j < V; ++j) sh[j] = f2x_fma(f2_pack(g[j], p[j]), xin2[j], nk[j]);
+    };
 #pragma unroll 1
     for (int tt = 0; tt < D; ++tt) {
-        if (tt < nrow) issue(tt);
+        if (tt < nrow) issue(tt, tt);
         cp_async_commit();
     }
-    int u = 0;  // ring slot of the second pass's newest row
+    auto wrap = [](int k) { return k + 1 == NR ? 0 : k + 1; };
+    int sn = 0, so = NR - W, sf = D;  // ring slots of rows t, t - W and t + D
+    int u = 0;  // second-pass ring slot of the newest window row
     for (int t = 0; t < nrow; ++t) {
         const int e = e0 + t;
-        if (t + D < nrow) issue(t + D);
+        if (t + D < nrow) issue(t + D, sf);
         cp_async_commit();
         cp_async_wait<D>();  // row e (and every older one) has landed
-        float g[V], p[V], go[V], po[V];
-        {
-            const unsigned char* sl = rin + (t % NR) * SLOT;
-            unstage_row<TG, V>(sl + og, g);
-            unstage_row<TP, V>(sl + op, p);
-        }
-        // first pass, vertical: add row e
-        const bool ein = e >= 0 && e < h;
-        if (ein) {
+        // first pass, vertical: add row e ...
+        if (e >= 0 && e < h) {
+            f32x2 sh[V];
+            shifted(sn, sh);
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                const float gs = (g[j] - KG) * L.xin[j], ps = (p[j] - KP) * L.xin[j];
-                vg[j] += gs;
-                vp[j] += ps;
-                vgg[j] += gs * gs;
-                vgp[j] += gs * ps;
+                a1[j] = f2x_add(a1[j], sh[j]);
+                a2[j] = f2x_add(a2[j], f2x_mul(f2_splat(f2_lo(sh[j])), sh[j]));
             }
         }
         // ... and subtract row e - W (zero when outside the image or before the walk)
         const int eo = e - W;
         if (t >= W && eo >= 0 && eo < h) {
-            const unsigned char* sl = rin + ((t - W) % NR) * SLOT;
-            unstage_row<TG, V>(sl + og, go);
-            unstage_row<TP, V>(sl + op, po);
+            f32x2 sh[V];
+            shifted(so, sh);
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                const float gs = (go[j] - KG) * L.xin[j], ps = (po[j] - KP) * L.xin[j];
-                vg[j] -= gs;
-                vp[j] -= ps;
-                vgg[j] -= gs * gs;
-                vgp[j] -= gs * ps;
+                a1[j] = f2x_sub(a1[j], sh[j]);
+                a2[j] = f2x_sub(a2[j], f2x_mul(f2_splat(f2_lo(sh[j])), sh[j]));
             }
         }
+        sn = wrap(sn);
+        so = wrap(so);
+        sf = wrap(sf);
         if (t < 2 * R) continue;  // uniform: the first pass's sums are not full yet
-        // first pass, horizontal, at window row c1 = e - R: statistics -> A, b
+        // first pass, horizontal, at window row c1 = e - R: statistics -> (A, b)
         const int c1 = e - R;
-        float sg[V], sp[V], sgg[V], sgp[V];
-        hbox<R, V>(vg, sg);
-        hbox<R, V>(vp, sp);
-        hbox<R, V>(vgg, sgg);
-        hbox<R, V>(vgp, sgp);
-        float A[V], B[V];
+        f32x2 s1[V], s2[V], nab[V];
+        hbox2<R, V>(a1, s1);
+        hbox2<R, V>(a2, s2);
         const bool c1in = c1 >= 0 && c1 < h;
-        const int ny1 = c1in ? slide_ny(c1, h, R) : 1;
+        const float iny1 = c1in ? slide_iny(c1, h, R) : 1.f;
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-            const float inv = slide_inv<R, V>(L, j, ny1);
-            const float mu = sg[j] * inv, nu = sp[j] * inv;
-            const float var = fmaxf(fmaf(-mu, mu, sgg[j] * inv), 0.f);
-            const float cov = fmaf(-mu, nu, sgp[j] * inv);
-            const float a = cov * rcp_approx(var + eps);
-            const float b = fmaf(-a, mu + KG, nu + KP);
-            const bool in = c1in && L.xin[j] != 0.f;
-            A[j] = in ? a : 0.f;
-            B[j] = in ? b : 0.f;
+            const f32x2 inv2 = f2_splat(slide_inv<R, V>(L, j, iny1));
+            const f32x2 m = f2x_mul(s1[j], inv2);                    // (mu', nu')
+            const f32x2 q = f2x_mul(s2[j], inv2);                    // (E[G'^2], E[G'P'])
+            const f32x2 vc = f2x_fma(f2_splat(-f2_lo(m)), m, q);     // (var, cov)
+            const float var = fmaxf(f2_lo(vc), 0.f);
+            const float a = f2_hi(vc) * rcp_approx(var + eps);
+            const f32x2 mk = f2x_add(m, K2);                         // (mu, nu)
+            const float b = fmaf(-a, f2_lo(mk), f2_hi(mk));
+            nab[j] = (c1in && L.xin[j] != 0.f) ? f2_pack(a, b) : f2_splat(0.f);
         }
-        // second pass, vertical: add row c1, subtract row c1 - W from the ring
+        // second pass, vertical: add window row c1, subtract row c1 - W from the ring
         float4* slot = ring + (size_t)u * (V / 2) * 32 + lane;
         if (t - 2 * R >= W) {
 #pragma unroll
             for (int j = 0; j < V; j += 2) {
                 const float4 o = slot[(j / 2) * 32];
-                va[j] = (va[j] + A[j]) - o.x;
-                vb[j] = (vb[j] + B[j]) - o.y;
-                va[j + 1] = (va[j + 1] + A[j + 1]) - o.z;
-                vb[j + 1] = (vb[j + 1] + B[j + 1]) - o.w;
+                ab[j] = f2x_sub(f2x_add(ab[j], nab[j]), f2_pack(o.x, o.y));
+                ab[j + 1] = f2x_sub(f2x_add(ab[j + 1], nab[j + 1]), f2_pack(o.z, o.w));
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                va[j] += A[j];
-                vb[j] += B[j];
-            }
+            for (int j = 0; j < V; ++j) ab[j] = f2x_add(ab[j], nab[j]);
         }
 #pragma unroll
-        for (int j = 0; j < V; j += 2) slot[(j / 2) * 32] = make_float4(A[j], B[j], A[j + 1], B[j + 1]);
+        for (int j = 0; j < V; j += 2) {
+            float a0, b0, a1v, b1v;
+            f2_unpack(nab[j], a0, b0);
+            f2_unpack(nab[j + 1], a1v, b1v);
+            slot[(j / 2) * 32] = make_float4(a0, b0, a1v, b1v);
+        }
         u = (u + 1 == W) ? 0 : u + 1;
         if (t < 4 * R) continue;  // uniform: the second pass's sums are not full yet
         // second pass, horizontal, at output row c2 = e - 2R
         const int c2 = e - 2 * R;
-        float sa[V], sb[V];
-        hbox<R, V>(va, sa);
-        hbox<R, V>(vb, sb);
+        f32x2 sab[V];
+        hbox2<R, V>(ab, sab);
         if (L.out) {
-            const int ny2 = slide_ny(c2, h, R);
+            const float iny2 = slide_iny(c2, h, R);
             float2* orow = coef + (size_t)c2 * w;
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 const int x = L.x0 + j;
                 if (x < w) {
-                    const float inv = slide_inv<R, V>(L, j, ny2);
-                    orow[x] = make_float2(sa[j] * inv, sb[j] * inv);
+                    float A, B;
+                    f2_unpack(f2x_mul(sab[j], f2_splat(slide_inv<R, V>(L, j, iny2))), A, B);
+                    orow[x] = make_float2(A, B);
                 }
             }
         }
@@ -454,23 +441,15 @@ __device__ void k4_slide_segment(const TG* __restrict__ G, const TP* __restrict_
         KG = slide_shift<TG, V>(g, L.xin);
         KP = slide_shift<TP, V>(p, L.xin);
     }
-    float vg[V], vp[V], vgg[V], vgp[V], vda[V], vdb[V], w0[V], w1[V], w2[V], w3[V];
+    // pairs per column: (G', P'), (G'^2, G'P') and (d Abar / N, d bbar / N)
+    // sums of the first pass; (q0, q1), (q2, q3) sums of the second
+    f32x2 a1[V], a2[V], a3[V], w01[V], w23[V], xin2[V], nk[V];
 #pragma unroll
-    for (int j = 0; j < V; ++j) vg[j] = vp[j] = vgg[j] = vgp[j] = vda[j] = vdb[j] = w0[j] = w1[j] = w2[j] = w3[j] = 0.f;
-    // the first pass's terms of row e at the lane's columns (zero outside),
-    // from its raw values
-    auto terms = [&](int e, const float (&g)[V], const float (&p)[V], float (&gs)[V], float (&ps)[V],
-                     float (&da)[V], float (&db)[V]) {
-        const int ny = slide_ny(e, h, R);
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            gs[j] = (g[j] - KG) * L.xin[j];
-            ps[j] = (p[j] - KP) * L.xin[j];
-            const float inv = slide_inv<R, V>(L, j, ny);
-            da[j] *= inv;
-            db[j] *= inv;
-        }
-    };
+    for (int j = 0; j < V; ++j) {
+        a1[j] = a2[j] = a3[j] = w01[j] = w23[j] = f2_splat(0.f);
+        xin2[j] = f2_splat(L.xin[j]);
+        nk[j] = f2_pack(-KG * L.xin[j], -KP * L.xin[j]);
+    }
     // input rows through the ring, D rows ahead (the leaving row and the
     // output row are still there)
     constexpr int D = SlideStage<R, true>::D, NR = SlideStage<R, true>::NR;
@@ -479,136 +458,136 @@ __device__ void k4_slide_segment(const TG* __restrict__ G, const TP* __restrict_
     unsigned char* rin = reinterpret_cast<unsigned char*>(ring + W * V * 32);
     const int og = lane * V * (int)sizeof(TG), od = BG + lane * V * 8, op = BG + BD + lane * V * (int)sizeof(TP);
     const float* dflat = reinterpret_cast<const float*>(dcoef);
-    auto issue = [&](int tt) {  // row e0 + tt into its slot
-        unsigned char* sl = rin + (tt % NR) * SLOT;
+    auto issue = [&](int tt, int slot) {  // row e0 + tt into ring slot `slot`
+        unsigned char* sl = rin + slot * SLOT;
         stage_row<TG, V>(sl + og, G, e0 + tt, h, w, L.x0, async);
         stage_row<float, 2 * V>(sl + od, dflat, e0 + tt, h, 2 * w, 2 * L.x0, async);
         stage_row<TP, V>(sl + op, P, e0 + tt, h, w, L.x0, async);
     };
-    auto unstage = [&](int tt, float (&g)[V], float (&p)[V], float (&da)[V], float (&db)[V]) {
-        const unsigned char* sl = rin + (tt % NR) * SLOT;
+    // a staged row's first-pass terms: (G', P') and (d Abar, d bbar) / N of
+    // each pixel's own window
+    auto terms = [&](int slot, int e, f32x2 (&sh)[V], f32x2 (&dd)[V]) {
+        const unsigned char* sl = rin + slot * SLOT;
+        float g[V], p[V], abv[2 * V];
         unstage_row<TG, V>(sl + og, g);
         unstage_row<TP, V>(sl + op, p);
-        float ab[2 * V];
-        unstage_row<float, 2 * V>(sl + od, ab);
+        unstage_row<float, 2 * V>(sl + od, abv);
+        const float iny = slide_iny(e, h, R);
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-            da[j] = ab[2 * j];
-            db[j] = ab[2 * j + 1];
+            sh[j] = f2x_fma(f2_pack(g[j], p[j]), xin2[j], nk[j]);
+            dd[j] = f2x_mul(f2_pack(abv[2 * j], abv[2 * j + 1]), f2_splat(slide_inv<R, V>(L, j, iny)));
         }
     };
 #pragma unroll 1
     for (int tt = 0; tt < D; ++tt) {
-        if (tt < nrow) issue(tt);
+        if (tt < nrow) issue(tt, tt);
         cp_async_commit();
     }
+    auto wrap = [](int k) { return k + 1 == NR ? 0 : k + 1; };
+    int sn = 0, so = NR - W, sc = NR - 2 * R, sf = D;  // ring slots of rows t, t - W, t - 2R and t + D
     int u = 0;
     for (int t = 0; t < nrow; ++t) {
         const int e = e0 + t;
-        if (t + D < nrow) issue(t + D);
+        if (t + D < nrow) issue(t + D, sf);
         cp_async_commit();
         cp_async_wait<D>();  // row e (and every older one) has landed
-        float g[V], p[V], da[V], db[V];
-        unstage(t, g, p, da, db);
         if (e >= 0 && e < h) {
-            float gs[V], ps[V];
-            terms(e, g, p, gs, ps, da, db);
+            f32x2 sh[V], dd[V];
+            terms(sn, e, sh, dd);
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                vg[j] += gs[j];
-                vp[j] += ps[j];
-                vgg[j] += gs[j] * gs[j];
-                vgp[j] += gs[j] * ps[j];
-                vda[j] += da[j];
-                vdb[j] += db[j];
+                a1[j] = f2x_add(a1[j], sh[j]);
+                a2[j] = f2x_add(a2[j], f2x_mul(f2_splat(f2_lo(sh[j])), sh[j]));
+                a3[j] = f2x_add(a3[j], dd[j]);
             }
         }
         const int eo = e - W;
         if (t >= W && eo >= 0 && eo < h) {
-            float go[V], po[V], ao[V], bo[V], gs[V], ps[V];
-            unstage(t - W, go, po, ao, bo);
-            terms(eo, go, po, gs, ps, ao, bo);
+            f32x2 sh[V], dd[V];
+            terms(so, eo, sh, dd);
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                vg[j] -= gs[j];
-                vp[j] -= ps[j];
-                vgg[j] -= gs[j] * gs[j];
-                vgp[j] -= gs[j] * ps[j];
-                vda[j] -= ao[j];
-                vdb[j] -= bo[j];
+                a1[j] = f2x_sub(a1[j], sh[j]);
+                a2[j] = f2x_sub(a2[j], f2x_mul(f2_splat(f2_lo(sh[j])), sh[j]));
+                a3[j] = f2x_sub(a3[j], dd[j]);
             }
         }
+        const int sc_now = sc;
+        sn = wrap(sn);
+        so = wrap(so);
+        sc = wrap(sc);
+        sf = wrap(sf);
         if (t < 2 * R) continue;  // uniform
         const int c1 = e - R;
-        float sg[V], sp[V], sgg[V], sgp[V], sda[V], sdb[V];
-        hbox<R, V>(vg, sg);
-        hbox<R, V>(vp, sp);
-        hbox<R, V>(vgg, sgg);
-        hbox<R, V>(vgp, sgp);
-        hbox<R, V>(vda, sda);
-        hbox<R, V>(vdb, sdb);
-        float q0[V], q1[V], q2[V], q3[V];
+        f32x2 s1[V], s2[V], s3[V];
+        hbox2<R, V>(a1, s1);
+        hbox2<R, V>(a2, s2);
+        hbox2<R, V>(a3, s3);
+        f32x2 q01[V], q23[V];
         const bool c1in = c1 >= 0 && c1 < h;
-        const int ny1 = c1in ? slide_ny(c1, h, R) : 1;
+        const float iny1 = c1in ? slide_iny(c1, h, R) : 1.f;
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-            const float inv = slide_inv<R, V>(L, j, ny1);
-            const float mus = sg[j] * inv, nus = sp[j] * inv;
-            const float var = fmaxf(fmaf(-mus, mus, sgg[j] * inv), 0.f);
-            const float cov = fmaf(-mus, nus, sgp[j] * inv);
-            const float ive = rcp_approx(var + eps);
-            const float A = cov * ive;
-            const float dA = sda[j], db = sdb[j];
+            const f32x2 inv2 = f2_splat(slide_inv<R, V>(L, j, iny1));
+            const f32x2 m = f2x_mul(s1[j], inv2);                    // (mu', nu')
+            const f32x2 q = f2x_mul(s2[j], inv2);                    // (E[G'^2], E[G'P'])
+            const f32x2 vc = f2x_fma(f2_splat(-f2_lo(m)), m, q);     // (var, cov)
+            const float mus = f2_lo(m), nus = f2_hi(m);
+            const float ive = rcp_approx(fmaxf(f2_lo(vc), 0.f) + eps);
+            const float A = f2_hi(vc) * ive;
+            const float dA = f2_lo(s3[j]), db = f2_hi(s3[j]);
             const float gamma = fmaf(-db, mus + KG, dA) * ive;
             const float beta = -gamma * A;
             const bool in = c1in && L.xin[j] != 0.f;
-            q0[j] = in ? gamma * inv : 0.f;
-            q1[j] = in ? beta * inv : 0.f;
-            q2[j] = in ? fmaf(-gamma, mus, db) * inv : 0.f;
-            q3[j] = in ? fmaf(gamma, nus, fmaf(2.f * beta, mus, db * A)) * inv : 0.f;
+            const f32x2 g01 = f2x_mul(f2_pack(gamma, beta), inv2);
+            const f32x2 g23 = f2x_mul(f2_pack(fmaf(-gamma, mus, db), fmaf(gamma, nus, fmaf(2.f * beta, mus, db * A))),
+                                      inv2);
+            q01[j] = in ? g01 : f2_splat(0.f);
+            q23[j] = in ? g23 : f2_splat(0.f);
         }
         float4* slot = ring + (size_t)u * V * 32 + lane;
         if (t - 2 * R >= W) {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 const float4 o = slot[j * 32];
-                w0[j] = (w0[j] + q0[j]) - o.x;
-                w1[j] = (w1[j] + q1[j]) - o.y;
-                w2[j] = (w2[j] + q2[j]) - o.z;
-                w3[j] = (w3[j] + q3[j]) - o.w;
+                w01[j] = f2x_sub(f2x_add(w01[j], q01[j]), f2_pack(o.x, o.y));
+                w23[j] = f2x_sub(f2x_add(w23[j], q23[j]), f2_pack(o.z, o.w));
             }
         } else {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                w0[j] += q0[j];
-                w1[j] += q1[j];
-                w2[j] += q2[j];
-                w3[j] += q3[j];
+                w01[j] = f2x_add(w01[j], q01[j]);
+                w23[j] = f2x_add(w23[j], q23[j]);
             }
         }
 #pragma unroll
-        for (int j = 0; j < V; ++j) slot[j * 32] = make_float4(q0[j], q1[j], q2[j], q3[j]);
+        for (int j = 0; j < V; ++j) {
+            float x0, x1, x2, x3;
+            f2_unpack(q01[j], x0, x1);
+            f2_unpack(q23[j], x2, x3);
+            slot[j * 32] = make_float4(x0, x1, x2, x3);
+        }
         u = (u + 1 == W) ? 0 : u + 1;
         if (t < 4 * R) continue;  // uniform
-        const int c2 = e - 2 * R;
-        float S0[V], S1[V], S2[V], S3[V];
-        hbox<R, V>(w0, S0);
-        hbox<R, V>(w1, S1);
-        hbox<R, V>(w2, S2);
-        hbox<R, V>(w3, S3);
+        f32x2 S01[V], S23[V];
+        hbox2<R, V>(w01, S01);
+        hbox2<R, V>(w23, S23);
         if (L.out) {
+            const int c2 = e - 2 * R;
+            const unsigned char* sl = rin + sc_now * SLOT;  // row c2 = e - 2R
             float gc[V], pc[V];
-            {
-                const unsigned char* sl = rin + ((t - 2 * R) % NR) * SLOT;  // row c2
-                unstage_row<TG, V>(sl + og, gc);
-                unstage_row<TP, V>(sl + op, pc);
-            }
+            unstage_row<TG, V>(sl + og, gc);
+            unstage_row<TP, V>(sl + op, pc);
             float outp[V], outg[V];
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 const float gs = gc[j] - KG, ps = pc[j] - KP;
-                outp[j] = fmaf(gs, S0[j], S2[j]);
-                outg[j] = fmaf(ps, S0[j], fmaf(2.f * gs, S1[j], -S3[j]));
+                float S0, S1, S2, S3;
+                f2_unpack(S01[j], S0, S1);
+                f2_unpack(S23[j], S2, S3);
+                f2_unpack(f2x_fma(f2_pack(gs, ps), f2_splat(S0), f2_pack(S2, fmaf(2.f * gs, S1, -S3))), outp[j],
+                          outg[j]);
             }
             const size_t o = (size_t)c2 * w + L.x0;
             if (L.vec) {
