@@ -147,6 +147,11 @@ size_t dgf_workspace_size_batched(const dgf_image* imgs, int n, dgf_dtype dt);
  * dgf_forward computes it with the same tile configuration, so results are
  * bitwise identical to per-image calls.  n <= DGF_MAX_BATCH.
  * The image table is read on the host during the call; it need not outlive it.
+ * The workspace (dgf_workspace_size_batched) holds each image's
+ * coefficients and a tensor map per image for the TMA-staged high-res
+ * strips (16-byte vectors), copied into it on `stream` from host memory
+ * before the graph runs (under stream capture the strips read with plain
+ * loads instead: the same bits).
  */
 #define DGF_MAX_BATCH 128
 dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtype dt,
@@ -230,6 +235,11 @@ void dgf_set_fused(int on);
  * round differently); the sliding form's bits depend on its segment length
  * (autotune kinds 1 and 4) but not on the number of planes in a call. */
 void dgf_set_lowres_slide(int on);
+
+/* Allows (1, default) or forbids (0) the one-graph form of
+ * dgf_backward_batched; forbidden, every batch runs the per-image chains.
+ * Both give the same bits. */
+void dgf_set_batched_graph_backward(int on);
 
 /* Allows (1) or forbids (0, default) the plane-group pipeline of dgf_forward
  * and dgf_backward (no guidance transform, integer factor for the backward):
@@ -318,10 +328,17 @@ typedef struct {
 /*
  * Batched backward over images of different sizes, radii and factors
  * (Algorithm 1 per image, as dgf_backward with N = 1 and no guidance
- * transform).  Each image's chain of kernels is exactly its single call's,
- * so the gradients equal the single calls' bit for bit; the chains run
- * concurrently on library-owned streams forked from and joined back to
- * `stream` (the call is ordered on `stream` like any other).
+ * transform).  With 16-bit storage, when every image's single call would run
+ * the sliding low-res kernels and the strip K3 (the default for integer
+ * factors 2, 4, 8 and radii 1, 2, 4, 8), the whole batch is one CUDA graph
+ * of persistent kernels (dgf_set_batched_graph_backward): K1 nodes (one per
+ * radius and lane width, images that want d I_h only) -> K3 nodes (one per
+ * vector width and factor) -> K4 nodes (one per radius and lane width), each
+ * node walking a flat list of every image's strip segments.  Otherwise each
+ * image's chain of kernels runs on library-owned streams forked from and
+ * joined back to `stream`.  Either way every image runs exactly its single
+ * call's arithmetic, so the gradients equal the single calls' bit for bit
+ * (the call is ordered on `stream` like any other).
  *   imgs:       n descriptors (host memory), 0 <= n <= DGF_MAX_BATCH;
  *               all tensors device memory in `dt`, NCHW with N = 1.
  *   workspace:  device memory of at least

@@ -85,6 +85,7 @@ _SIGS = {
     "dgf_set_tma": (None, [_I]),
     "dgf_set_fused": (None, [_I]),
     "dgf_set_lowres_slide": (None, [_I]),
+    "dgf_set_batched_graph_backward": (None, [_I]),
     "dgf_set_pipeline": (None, [_I]),
     "dgf_shutdown": (None, []),
     "dgf_autotune": (None, [_I]),
@@ -216,6 +217,10 @@ def dgf_set_fused(on: bool) -> None:
 
 def dgf_set_lowres_slide(on: bool) -> None:
     lib().dgf_set_lowres_slide(1 if on else 0)
+
+
+def dgf_set_batched_graph_backward(on: bool) -> None:
+    lib().dgf_set_batched_graph_backward(1 if on else 0)
 
 
 def dgf_set_pipeline(on: bool) -> None:

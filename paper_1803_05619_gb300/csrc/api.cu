@@ -359,6 +359,9 @@ static bool in_candidates(const LowCfg& c, int r, bool k4, dgf_dtype dt) {
 
 // Sliding-sum low-res strips for 16-bit storage (dgf_set_lowres_slide).
 static bool g_slide_allowed = true;
+// Batched backward as one graph of persistent kernels where it applies
+// (dgf_set_batched_graph_backward).
+static bool g_batched_graph_bwd = true;
 
 // Table entries of the low-res kernels: b > 0 column-walking tiles (CW = a,
 // EY1 = b), b == 0 strips (a rows per segment), b < 0 sliding strips (a rows
@@ -920,12 +923,13 @@ struct BatchGraph {
 };
 
 std::mutex g_batch_mu;
-// key: device, dtype, K1 classes (radius), K2 classes (vector width * 100 + factor)
+// key: device, dtype, K1 classes (radius, form, lane width), K2 classes (staging, vector width, factor)
 std::map<std::tuple<int, int, std::vector<int>, std::vector<int>>, BatchGraph> g_batch;
 
 struct BatchPrep {
     BatchParams bp;
     size_t smem1 = 0, smem2 = 0;
+    size_t maps = 0;  // workspace offset of the K2 tensor maps (one per image)
     size_t ws = 0;
 };
 
@@ -993,6 +997,8 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
     }
     bp.k1_total = bp.k1_start[n];
     bp.k2_total = bp.k2_start[n];
+    out.maps = off;
+    if (n > 0) off += align256((size_t)n * sizeof(K2Map));
     out.ws = off;
     return DGF_OK;
 }
@@ -1650,13 +1656,35 @@ extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtyp
     // specialised for its class, so it keeps the registers and occupancy of
     // the single-call kernel; its images keep their workspace slots.
     std::vector<int> c1, c2;
+    // K2 strips of 16-byte vectors are staged by TMA as in the single call:
+    // tensor maps of I_h in the workspace's map region, copied there on the
+    // stream ahead of the graph
+    static thread_local std::vector<K2Map> k2maps;
+    k2maps.assign(n, K2Map{});
+    std::vector<char> tma2(n, 0);
+    K2Map* maps_dev = reinterpret_cast<K2Map*>(static_cast<char*>(workspace) + prep.maps);
+    // (a capture cannot hold the maps' copy from pageable host memory: the
+    // plain-load strips then serve; the same bits)
+    const bool capturing = stream_capturing(s);
+    bool any_map = false;
+    for (int i = 0; i < n && !capturing; ++i) {
+        const BatchImage& im = prep.bp.img[i];
+        void* f = nullptr;
+        size_t sm = 0;
+        int th = 0;
+        tma2[i] = im.F > 0 && k2_strip_ok(im.vec, im.F) &&
+                  make_k2_map(k2maps[i], im.I_h, dt, im.C, im.h, im.w, im.vec, im.F) &&
+                  k2_batched_tma_kernel(dt, im.vec, im.F, &f, &sm, &th) == cudaSuccess;
+        any_map = any_map || tma2[i];
+    }
     // K1 class: radius, form and (sliding form) columns per lane
     auto k1class = [](const BatchImage& im) { return (im.r * 4 + im.k1_fast) * 16 + (im.k1_fast == 3 ? im.k1_ty : 0); };
-    auto k2class = [](const BatchImage& im) { return im.vec * 100 + im.F; };
+    // K2 class: staging, vector width, factor
+    auto k2class = [&](int i) { return (tma2[i] ? 10000 : 0) + prep.bp.img[i].vec * 100 + prep.bp.img[i].F; };
     for (int i = 0; i < n; ++i) {
         const BatchImage& im = prep.bp.img[i];
         if (std::find(c1.begin(), c1.end(), k1class(im)) == c1.end()) c1.push_back(k1class(im));
-        if (std::find(c2.begin(), c2.end(), k2class(im)) == c2.end()) c2.push_back(k2class(im));
+        if (std::find(c2.begin(), c2.end(), k2class(i)) == c2.end()) c2.push_back(k2class(i));
     }
     std::sort(c1.begin(), c1.end());
     std::sort(c2.begin(), c2.end());
@@ -1680,51 +1708,98 @@ extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtyp
         }
         b.k1_total = b.k1_start[b.n];
     }
+    std::vector<void*> f2(c2.size(), nullptr);
+    std::vector<int> th2(c2.size(), kThreads), occ2(c2.size(), 0);
+    cudaError_t e;
     for (size_t q = 0; q < c2.size(); ++q) {
         BatchParams& b = bp2[q];
         memset(&b, 0, sizeof b);
-        for (int i = 0; i < n; ++i) {
-            const BatchImage& im = prep.bp.img[i];
-            if (k2class(im) != c2[q]) continue;
-            const int j = b.n++;
-            b.img[j] = im;
-            b.k2_start[j + 1] = b.k2_start[j] + im.k2_nx * im.k2_ny * im.C;
-            sm2[q] = std::max(sm2[q], (im.F > 0 && k2_strip_ok(im.vec, im.F))
-                                          ? k2_strip_batched_smem((int)esize(dt), im.vec, im.F)
-                                          : k2_smem_bytes(im.vec, im.F, im.h_l, im.h, im.w_l, im.w, im.k2_th));
+        const bool tma = c2[q] >= 10000;
+        const int vec = c2[q] % 10000 / 100, F = c2[q] % 100;
+        std::vector<int> members;
+        for (int i = 0; i < n; ++i)
+            if (k2class(i) == c2[q]) members.push_back(i);
+        if (tma) {
+            // one segment length for the class (the strip walk's bits do not
+            // depend on it): whole waves of CTA slots, few halo rows
+            if ((e = k2_batched_tma_kernel(dt, vec, F, &f2[q], &sm2[q], &th2[q])) != cudaSuccess)
+                return cuda_fail(e, "k2 batched tma");
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2[q], f2[q], th2[q], sm2[q]);
+            const double slots = (double)sms * std::max(occ2[q], 1);
+            const int wpc = th2[q] / 32, OUT = 32 * (vec / F);
+            auto items = [&](int ls) {
+                long long t = 0;
+                for (int i : members) {
+                    const BatchImage& im = prep.bp.img[i];
+                    const int nstrip = (im.w_l + OUT - 1) / OUT, nseg = (im.h_l + ls - 1) / ls;
+                    t += (long long)((nstrip * nseg + wpc - 1) / wpc) * im.C;
+                }
+                return t;
+            };
+            int ls = 32;
+            double best = 1e30;
+            for (int c = 8; c <= 64; ++c) {
+                const double waves = (double)items(c) / slots, eff = waves / std::ceil(waves);
+                const double cost = (c + 0.25) / c / eff;
+                if (cost < best - 1e-9) {
+                    best = cost;
+                    ls = c;
+                }
+            }
+            for (int i : members) {
+                const int j = b.n++;
+                b.img[j] = prep.bp.img[i];
+                BatchImage& im = b.img[j];
+                const int nstrip = (im.w_l + OUT - 1) / OUT, nseg = (im.h_l + ls - 1) / ls;
+                im.k2_th = ls;
+                im.k2_nx = (nstrip * nseg + wpc - 1) / wpc;
+                im.k2_ny = 1;
+                im.k2_map = maps_dev + i;
+                b.k2_start[j + 1] = b.k2_start[j] + im.k2_nx * im.C;
+            }
+        } else {
+            for (int i : members) {
+                const BatchImage& im = prep.bp.img[i];
+                const int j = b.n++;
+                b.img[j] = im;
+                b.k2_start[j + 1] = b.k2_start[j] + im.k2_nx * im.k2_ny * im.C;
+                sm2[q] = std::max(sm2[q], (im.F > 0 && k2_strip_ok(im.vec, im.F))
+                                              ? k2_strip_batched_smem((int)esize(dt), im.vec, im.F)
+                                              : k2_smem_bytes(im.vec, im.F, im.h_l, im.h, im.w_l, im.w, im.k2_th));
+            }
+            if ((e = k2_batched_kernel(dt, vec, F, sm2[q], &f2[q])) != cudaSuccess)
+                return cuda_fail(e, "k2 batched attr");
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2[q], f2[q], kThreads, sm2[q]);
         }
         b.k2_total = b.k2_start[b.n];
     }
     uint32_t* stw = status_ptr();
-    cudaError_t e;
     std::vector<cudaKernelNodeParams> p1(c1.size()), p2(c2.size());
-    std::vector<std::array<void*, 2>> a1(c1.size());
-    std::vector<std::array<void*, 1>> a2(c2.size());
+    std::vector<std::array<void*, 2>> a1(c1.size()), a2(c2.size());
     for (size_t q = 0; q < c1.size(); ++q) {
         void* f = nullptr;
-        if ((e = k1_batched_kernel(dt, c1[q] / 64, fast1[q], sm1[q], &f, c1[q] % 16)) != cudaSuccess)
+        int threads = kThreads;
+        if ((e = k1_batched_kernel(dt, c1[q] / 64, fast1[q], sm1[q], &f, c1[q] % 16, &threads)) != cudaSuccess)
             return cuda_fail(e, "k1 batched attr");
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, sm1[q]);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, threads, sm1[q]);
         a1[q] = {&bp1[q], &stw};
         p1[q] = cudaKernelNodeParams{};
         p1[q].func = f;
-        p1[q].gridDim = dim3(std::max(1, std::min(bp1[q].k1_total, sms * std::max(occ, 1))));
-        p1[q].blockDim = dim3(kThreads);
+        // the sliding form takes one work item per CTA (the whole list), the
+        // others loop over it
+        p1[q].gridDim = dim3(std::max(1, fast1[q] == 3 ? bp1[q].k1_total
+                                                       : std::min(bp1[q].k1_total, sms * std::max(occ, 1))));
+        p1[q].blockDim = dim3(threads);
         p1[q].sharedMemBytes = (unsigned)sm1[q];
         p1[q].kernelParams = a1[q].data();
     }
     for (size_t q = 0; q < c2.size(); ++q) {
-        void* f = nullptr;
-        if ((e = k2_batched_kernel(dt, c2[q] / 100, c2[q] % 100, sm2[q], &f)) != cudaSuccess)
-            return cuda_fail(e, "k2 batched attr");
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, sm2[q]);
-        a2[q] = {&bp2[q]};
+        a2[q] = {&bp2[q], &stw};
         p2[q] = cudaKernelNodeParams{};
-        p2[q].func = f;
-        p2[q].gridDim = dim3(std::max(1, std::min(bp2[q].k2_total, sms * std::max(occ, 1))));
-        p2[q].blockDim = dim3(kThreads);
+        p2[q].func = f2[q];
+        p2[q].gridDim = dim3(std::max(1, std::min(bp2[q].k2_total, sms * std::max(occ2[q], 1))));
+        p2[q].blockDim = dim3(th2[q]);
         p2[q].sharedMemBytes = (unsigned)sm2[q];
         p2[q].kernelParams = a2[q].data();
     }
@@ -1750,6 +1825,10 @@ extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtyp
             if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n2[q], &p2[q])) != cudaSuccess)
                 return cuda_fail(e, "graph update k2");
     }
+    if (any_map &&
+        (e = cudaMemcpyAsync(maps_dev, k2maps.data(), (size_t)n * sizeof(K2Map), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+        return cuda_fail(e, "k2 maps");
     Launcher L(s);
     e = L.run("batched_graph(k1,k2)", [&] {
         g_launches.fetch_add((long long)(c1.size() + c2.size()) - 1);  // every node of the replay
@@ -1854,9 +1933,307 @@ static dgf_status check_grad_images(const dgf_image_grad* imgs, int n, dgf_dtype
             return fail(DGF_ERR_INVALID, "image %d: NULL input pointer", i);
         off += align256(layout(1, im.C, im.h_l, im.w_l, false).total);
     }
+    // 16-bit storage: the K3 tensor maps of the one-graph form
+    if (dt != DGF_F32 && n > 0) off += align256((size_t)n * sizeof(K3Maps));
     *ws_total = off;
     return DGF_OK;
 }
+}  // namespace dgf
+
+// ------------------------------------------------ batched backward as a graph
+// For 16-bit storage, when every image's backward runs the sliding K1/K4 and
+// the strip K3: one CUDA graph of persistent kernels, one per node class,
+// K1 classes (radius, columns per lane) -> K3 classes (vector width,
+// factor) -> K4 classes (radius, columns per lane); every edge is a stage
+// boundary and each image keeps its workspace slot.  Each image runs its
+// single call's arithmetic (same segment lengths for the sliding kernels; the
+// K3 walk gives the same bits at any segment length), so the results equal
+// the single calls bit for bit.
+namespace dgf {
+
+struct BwdGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> n1, n3, n4;
+};
+static std::mutex g_bwdg_mu;
+static std::map<std::tuple<int, int, std::vector<int>, std::vector<int>, std::vector<int>>, BwdGraph> g_bwdg;
+
+static dgf_status backward_batched_graph(const dgf_image_grad* imgs, int n, dgf_dtype dt, char* ws, cudaStream_t s,
+                                         bool& done) {
+    done = false;
+    if (dt == DGF_F32 || n <= 0 || stream_capturing(s)) return DGF_OK;
+    struct Item {
+        Plan p;
+        int S1, V1, S4, V4;
+        bool k4, tma;
+        int k3c;  // K3 class: vector width, factor, staging
+    };
+    std::vector<Item> it(n);
+    // K3 tensor maps (the single call's TMA staging) go to the workspace's map
+    // region, copied there on the stream ahead of the graph
+    static thread_local std::vector<K3Maps> maps;
+    maps.assign(n, K3Maps{});
+    std::vector<size_t> off(n);
+    size_t o = 0;
+    for (int i = 0; i < n; ++i) {
+        const dgf_image_grad& im = imgs[i];
+        off[i] = o;
+        o += align256(layout(1, im.C, im.h_l, im.w_l, false).total);
+        Item& t = it[i];
+        t.p = make_plan(dt, im.h_l, im.w_l, im.h, im.w, im.r, false, {im.dO_h, im.I_h, im.dI_h});
+        const Plan& p = t.p;
+        if (p.k1.fast != 3 || p.k4.fast != 3 || !p.k3_fast || p.F <= 0) return DGF_OK;
+        void* f = nullptr;
+        size_t sm3 = 0;
+        int th3 = 0;
+        t.tma = make_k3_maps(maps[i], im.dO_h, im.I_h, dt, im.C, im.h, im.w, p.vec, p.F);
+        t.k3c = (t.tma ? 10000 : 0) + p.vec * 100 + p.F;
+        if (k3_batched_kernel(dt, p.vec, p.F, t.tma, &f, &sm3, &th3) != cudaSuccess) return DGF_OK;
+        t.S1 = p.k1.a > 0 ? p.k1.a : slide_auto_seg(im.h_l, im.r);
+        t.V1 = p.k1.b > 0 ? p.k1.b : slide_k1_v(im.r);
+        t.S4 = p.k4.a > 0 ? p.k4.a : slide_auto_seg(im.h_l, im.r);
+        t.V4 = p.k4.b > 0 ? p.k4.b : slide_k4_v(im.r);
+        t.k4 = im.dp_l != nullptr || im.dI_l != nullptr;
+        size_t sm4 = 0;
+        int th4 = 0;
+        if (t.k4 && k4_batched_kernel(dt, im.r, t.V4, &f, &sm4, &th4) != cudaSuccess) return DGF_OK;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = sm_count();
+    // node classes
+    std::vector<int> c1, c3, c4;
+    auto add = [](std::vector<int>& v, int k) {
+        if (std::find(v.begin(), v.end(), k) == v.end()) v.push_back(k);
+    };
+    // as in the single call, K1 runs only for the images that want d I_h
+    // (d Abar and d bbar do not depend on the coefficients)
+    for (int i = 0; i < n; ++i) {
+        const dgf_image_grad& im = imgs[i];
+        if (im.dp_l == nullptr && im.dI_l == nullptr && im.dI_h == nullptr) continue;
+        if (im.dI_h != nullptr) add(c1, im.r * 16 + it[i].V1);
+        add(c3, it[i].k3c);
+        if (it[i].k4) add(c4, im.r * 16 + it[i].V4);
+    }
+    if (c3.empty()) {
+        done = true;
+        return DGF_OK;
+    }
+    std::sort(c1.begin(), c1.end());
+    std::sort(c3.begin(), c3.end());
+    std::sort(c4.begin(), c4.end());
+    static thread_local std::vector<BatchParams> bp1;
+    static thread_local std::vector<BwdParams> bp3, bp4;
+    bp1.resize(c1.size());
+    bp3.resize(c3.size());
+    bp4.resize(c4.size());
+    std::vector<cudaKernelNodeParams> p1(c1.size()), p3(c3.size()), p4(c4.size());
+    std::vector<std::array<void*, 2>> a1(c1.size()), a3(c3.size());
+    std::vector<std::array<void*, 1>> a4(c4.size());
+    uint32_t* stw = status_ptr();
+    cudaError_t e;
+    auto bwd_image = [&](int i, BwdImage& b) {
+        const dgf_image_grad& im = imgs[i];
+        const Layout lay = layout(1, im.C, im.h_l, im.w_l, false);
+        memset(&b, 0, sizeof b);
+        b.dO = im.dO_h;
+        b.p_l = im.p_l;
+        b.I_l = im.I_l;
+        b.I_h = im.I_h;
+        b.dp = im.dp_l;
+        b.dIl = im.dI_l;
+        b.dIh = im.dI_h;
+        b.coef = reinterpret_cast<const float2*>(ws + off[i] + lay.coef);
+        b.dcoef = reinterpret_cast<float2*>(ws + off[i] + lay.dcoef);
+        b.C = im.C;
+        b.h_l = im.h_l;
+        b.w_l = im.w_l;
+        b.h = im.h;
+        b.w = im.w;
+        b.eps = im.eps;
+    };
+    for (size_t q = 0; q < c1.size(); ++q) {  // K1: the forward's persistent sliding K1
+        BatchParams& b = bp1[q];
+        memset(&b, 0, sizeof b);
+        const int r = c1[q] / 16, V = c1[q] % 16;
+        size_t smem = 0;
+        for (int i = 0; i < n; ++i) {
+            const dgf_image_grad& im = imgs[i];
+            if (im.dI_h == nullptr || im.r * 16 + it[i].V1 != c1[q]) continue;
+            const int j = b.n++;
+            BatchImage& bi = b.img[j];
+            bi.p_l = im.p_l;
+            bi.I_l = im.I_l;
+            bi.I_h = im.I_h;
+            bi.coef = reinterpret_cast<float2*>(ws + off[i] + layout(1, im.C, im.h_l, im.w_l, false).coef);
+            bi.C = im.C;
+            bi.h_l = im.h_l;
+            bi.w_l = im.w_l;
+            bi.h = im.h;
+            bi.w = im.w;
+            bi.r = im.r;
+            bi.eps = im.eps;
+            bi.k1_fast = 3;
+            bi.k1_ty = V;
+            bi.k1_tx = it[i].S1;
+            const LowCfg c{3, it[i].S1, V};
+            low_grid(c, im.r, im.h_l, im.w_l, bi.k1_nx, bi.k1_ny);
+            b.k1_start[j + 1] = b.k1_start[j] + bi.k1_nx * bi.k1_ny * im.C;
+            smem = std::max(smem, k1_cfg_smem(c, im.r, 0));
+        }
+        b.k1_total = b.k1_start[b.n];
+        void* f = nullptr;
+        int threads = kThreads;
+        if ((e = k1_batched_kernel(dt, r, 3, smem, &f, V, &threads)) != cudaSuccess)
+            return cuda_fail(e, "k1 batched attr");
+        a1[q] = {&bp1[q], &stw};
+        p1[q] = cudaKernelNodeParams{};
+        p1[q].func = f;
+        p1[q].gridDim = dim3(std::max(1, b.k1_total));  // one work item per CTA
+        p1[q].blockDim = dim3(threads);
+        p1[q].sharedMemBytes = (unsigned)smem;
+        p1[q].kernelParams = a1[q].data();
+    }
+    K3Maps* maps_dev = reinterpret_cast<K3Maps*>(ws + o);
+    for (size_t q = 0; q < c3.size(); ++q) {  // K3 strips
+        BwdParams& b = bp3[q];
+        memset(&b, 0, sizeof b);
+        const bool tma = c3[q] >= 10000;
+        const int vec = c3[q] % 10000 / 100, F = c3[q] % 100, OUT = 30 * (vec / F);
+        void* f = nullptr;
+        size_t smem = 0;
+        int threads = 0;
+        if ((e = k3_batched_kernel(dt, vec, F, tma, &f, &smem, &threads)) != cudaSuccess)
+            return cuda_fail(e, "k3 batched");
+        const int wpc = threads / 32;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, threads, smem);
+        const double slots = (double)sms * std::max(occ, 1);
+        // one segment length for the class (the walk's bits do not depend on
+        // it), chosen like the single call's: whole waves of CTA slots, few
+        // halo blocks
+        std::vector<int> members;
+        for (int i = 0; i < n; ++i) {
+            const dgf_image_grad& im = imgs[i];
+            if (im.dp_l == nullptr && im.dI_l == nullptr && im.dI_h == nullptr) continue;
+            if (it[i].k3c == c3[q]) members.push_back(i);
+        }
+        auto items = [&](int ls) {
+            long long t = 0;
+            for (int i : members) {
+                const dgf_image_grad& im = imgs[i];
+                const int nstrip = (im.w_l + OUT - 1) / OUT, nseg = (im.h_l + ls - 1) / ls;
+                t += (long long)((nstrip * nseg + wpc - 1) / wpc) * im.C;
+            }
+            return t;
+        };
+        int ls = 32;
+        double best = 1e30;
+        for (int c = 8; c <= 64; ++c) {
+            const double waves = (double)items(c) / slots, eff = waves / std::ceil(waves);
+            const double cost = (c + 1.0) / c / eff;
+            if (cost < best - 1e-9) {
+                best = cost;
+                ls = c;
+            }
+        }
+        for (int i : members) {
+            const dgf_image_grad& im = imgs[i];
+            const int j = b.n++;
+            bwd_image(i, b.img[j]);
+            b.img[j].k3_ls = ls;
+            const int nstrip = (im.w_l + OUT - 1) / OUT, nseg = (im.h_l + ls - 1) / ls;
+            b.img[j].k3_nx = (nstrip * nseg + wpc - 1) / wpc;
+            b.img[j].k3_maps = tma ? maps_dev + i : nullptr;
+            b.start[j + 1] = b.start[j] + b.img[j].k3_nx * im.C;
+        }
+        b.total = b.start[b.n];
+        a3[q] = {&bp3[q], &stw};
+        p3[q] = cudaKernelNodeParams{};
+        p3[q].func = f;
+        p3[q].gridDim = dim3(std::max(1, b.total));  // one work item per CTA
+        p3[q].blockDim = dim3(threads);
+        p3[q].sharedMemBytes = (unsigned)smem;
+        p3[q].kernelParams = a3[q].data();
+    }
+    for (size_t q = 0; q < c4.size(); ++q) {  // sliding K4
+        BwdParams& b = bp4[q];
+        memset(&b, 0, sizeof b);
+        const int r = c4[q] / 16, V = c4[q] % 16;
+        void* f = nullptr;
+        size_t smem = 0;
+        int threads = 0;
+        if ((e = k4_batched_kernel(dt, r, V, &f, &smem, &threads)) != cudaSuccess) return cuda_fail(e, "k4 batched");
+        const int wpc = threads / 32, outc = slide_out_cols(r, V);
+        for (int i = 0; i < n; ++i) {
+            const dgf_image_grad& im = imgs[i];
+            if (!it[i].k4 || im.r * 16 + it[i].V4 != c4[q]) continue;
+            const int j = b.n++;
+            bwd_image(i, b.img[j]);
+            BwdImage& bi = b.img[j];
+            bi.k4_S = it[i].S4;
+            const int nstrip = (im.w_l + outc - 1) / outc, nseg = (im.h_l + bi.k4_S - 1) / bi.k4_S;
+            bi.k4_nx = (nstrip * nseg + wpc - 1) / wpc;
+            const size_t a = (size_t)V * 2;  // bytes of V 16-bit elements
+            auto al = [a](const void* ptr) { return ptr == nullptr || reinterpret_cast<uintptr_t>(ptr) % a == 0; };
+            bi.k4_aligned = im.w_l % V == 0 && al(im.I_l) && al(im.p_l) && al(im.dp_l) && al(im.dI_l);
+            bi.k4_pairs = im.w_l % 2 == 0 && reinterpret_cast<uintptr_t>(bi.dcoef) % 16 == 0;
+            b.start[j + 1] = b.start[j] + bi.k4_nx * im.C;
+        }
+        b.total = b.start[b.n];
+        a4[q] = {&bp4[q]};
+        p4[q] = cudaKernelNodeParams{};
+        p4[q].func = f;
+        p4[q].gridDim = dim3(std::max(1, b.total));  // one work item per CTA
+        p4[q].blockDim = dim3(threads);
+        p4[q].sharedMemBytes = (unsigned)smem;
+        p4[q].kernelParams = a4[q].data();
+    }
+    std::lock_guard<std::mutex> lk(g_bwdg_mu);
+    BwdGraph& bg = g_bwdg[std::make_tuple(dev, (int)dt, c1, c3, c4)];
+    if (bg.exec == nullptr) {
+        if ((e = cudaGraphCreate(&bg.graph, 0)) != cudaSuccess) return cuda_fail(e, "graph create");
+        bg.n1.resize(c1.size());
+        bg.n3.resize(c3.size());
+        bg.n4.resize(c4.size());
+        for (size_t q = 0; q < c1.size(); ++q)
+            if ((e = cudaGraphAddKernelNode(&bg.n1[q], bg.graph, nullptr, 0, &p1[q])) != cudaSuccess)
+                return cuda_fail(e, "graph node k1");
+        for (size_t q = 0; q < c3.size(); ++q)
+            if ((e = cudaGraphAddKernelNode(&bg.n3[q], bg.graph, bg.n1.data(), bg.n1.size(), &p3[q])) != cudaSuccess)
+                return cuda_fail(e, "graph node k3");
+        for (size_t q = 0; q < c4.size(); ++q)
+            if ((e = cudaGraphAddKernelNode(&bg.n4[q], bg.graph, bg.n3.data(), bg.n3.size(), &p4[q])) != cudaSuccess)
+                return cuda_fail(e, "graph node k4");
+        if ((e = cudaGraphInstantiate(&bg.exec, bg.graph, 0)) != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    } else {
+        for (size_t q = 0; q < c1.size(); ++q)
+            if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n1[q], &p1[q])) != cudaSuccess)
+                return cuda_fail(e, "graph update k1");
+        for (size_t q = 0; q < c3.size(); ++q)
+            if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n3[q], &p3[q])) != cudaSuccess)
+                return cuda_fail(e, "graph update k3");
+        for (size_t q = 0; q < c4.size(); ++q)
+            if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n4[q], &p4[q])) != cudaSuccess)
+                return cuda_fail(e, "graph update k4");
+    }
+    bool any_map = false;
+    for (int i = 0; i < n; ++i) any_map = any_map || it[i].tma;
+    if (any_map &&
+        (e = cudaMemcpyAsync(maps_dev, maps.data(), (size_t)n * sizeof(K3Maps), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+        return cuda_fail(e, "k3 maps");
+    Launcher L(s);
+    e = L.run("batched_bwd_graph(k1,k3,k4)", [&] {
+        g_launches.fetch_add((long long)(c1.size() + c3.size() + c4.size()) - 1);  // every node of the replay
+        return cudaGraphLaunch(bg.exec, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    done = true;
+    return DGF_OK;
+}
+
 }  // namespace dgf
 
 extern "C" size_t dgf_workspace_size_batched_backward(const dgf_image_grad* imgs, int n, dgf_dtype dt) {
@@ -1874,6 +2251,11 @@ extern "C" dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dg
     if (n == 0) return DGF_OK;
     if ((st = check_ws(workspace, ws_bytes, total)) != DGF_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    bool done = false;
+    if (g_batched_graph_bwd) {
+        st = backward_batched_graph(imgs, n, dt, static_cast<char*>(workspace), s, done);
+        if (st != DGF_OK || done) return st;
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_bwd_mu);
@@ -1968,6 +2350,7 @@ extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
 
 extern "C" void dgf_set_fused(int on) { g_fused_allowed = on != 0; }
 extern "C" void dgf_set_lowres_slide(int on) { g_slide_allowed = on != 0; }
+extern "C" void dgf_set_batched_graph_backward(int on) { g_batched_graph_bwd = on != 0; }
 
 extern "C" void dgf_set_pipeline(int on) { g_pipeline = on != 0; }
 

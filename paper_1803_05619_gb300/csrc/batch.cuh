@@ -22,6 +22,7 @@ struct BatchImage {
     int k2_th;        // high-res rows per tile
     int k1_nx, k1_ny; // low-res tiles per plane
     int k2_nx, k2_ny; // high-res tiles per plane
+    const void* k2_map; // K2Map of I_h in device memory (TMA-staged strips), or null
 };
 
 struct BatchParams {
@@ -33,6 +34,35 @@ struct BatchParams {
 };
 
 static_assert(sizeof(BatchParams) < 32000, "kernel parameter limit");
+
+// One image of the batched backward (16-bit storage): its K3 strip walk and
+// sliding K4 work lists.
+struct BwdImage {
+    const void* dO;       // d O_h (C planes)
+    const void* p_l;      // P
+    const void* I_l;      // G_l
+    const void* I_h;      // G_h
+    void* dp;             // d p_l (nullable)
+    void* dIl;            // d I_l (nullable)
+    void* dIh;            // d I_h (nullable)
+    const float2* coef;   // Abar, bbar (from the K1 stage)
+    float2* dcoef;        // d Abar, d bbar (K3 writes, K4 reads)
+    int C, h_l, w_l, h, w;
+    float eps;
+    int k3_ls, k3_nx;     // K3: low-res rows per segment; work items per plane
+    int k4_S, k4_nx;      // K4: output rows per segment; work items per plane
+    int k4_aligned, k4_pairs;
+    const void* k3_maps;  // K3Maps of d O_h and G_h in device memory (TMA staging), or null: plain loads
+};
+
+struct BwdParams {
+    int n;
+    int total;
+    int start[DGF_MAX_BATCH + 1];  // prefix sums of work items (all planes) per image
+    BwdImage img[DGF_MAX_BATCH];
+};
+
+static_assert(sizeof(BwdParams) < 32000, "kernel parameter limit");
 
 // image owning flat tile t: largest i with start[i] <= t
 __device__ __forceinline__ int batch_find(const int* start, int n, int t) {

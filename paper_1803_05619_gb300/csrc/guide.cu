@@ -35,23 +35,40 @@ __device__ __forceinline__ float lrelu(float z, float slope) { return z > 0.f ? 
 // constant bank.
 constexpr int kWPairs = kHid * 3 + 3 * kHid + 3;
 __constant__ f32x2 c_wx2[kWPairs];  // [w1 (k, c) | w2 (c, k) | b2]
-__device__ f32x2 g_wx2_stage[kWPairs];
+// ... and as pairs of neighbouring hidden units {w[k], w[k + 1]} (k even),
+// so K6 works on two hidden units per paired instruction
+constexpr int kHP = kHid / 2;
+constexpr int kHidPairs = kHP * 3 + 3 * kHP;
+__constant__ f32x2 c_wh[kHidPairs];  // [w1 (k / 2, c) | w2 (c, k / 2)]
+__device__ f32x2 g_wx2_stage[kWPairs + kHidPairs];
 
 __global__ void k_splat_weights(const float* __restrict__ w1, const float* __restrict__ w2,
                                 const float* __restrict__ b2, int hidden) {
     const int i = threadIdx.x;
-    if (i >= kWPairs) return;
-    float v = 0.f;
-    if (i < kHid * 3) {
-        const int k = i / 3, c = i - 3 * k;
-        v = k < hidden ? w1[k * 3 + c] : 0.f;
-    } else if (i < 2 * kHid * 3) {
-        const int c = (i - kHid * 3) / kHid, k = (i - kHid * 3) - c * kHid;
-        v = k < hidden ? w2[c * hidden + k] : 0.f;
-    } else {
-        v = b2[i - 2 * kHid * 3];
+    auto W1 = [&](int k, int c) { return k < hidden ? w1[k * 3 + c] : 0.f; };
+    auto W2 = [&](int c, int k) { return k < hidden ? w2[c * hidden + k] : 0.f; };
+    if (i < kWPairs) {
+        float v = 0.f;
+        if (i < kHid * 3) {
+            const int k = i / 3, c = i - 3 * k;
+            v = W1(k, c);
+        } else if (i < 2 * kHid * 3) {
+            const int c = (i - kHid * 3) / kHid, k = (i - kHid * 3) - c * kHid;
+            v = W2(c, k);
+        } else {
+            v = b2[i - 2 * kHid * 3];
+        }
+        g_wx2_stage[i] = f2_pack(v, v);
+    } else if (i < kWPairs + kHidPairs) {
+        const int j = i - kWPairs;
+        if (j < kHP * 3) {
+            const int q = j / 3, c = j - 3 * q;
+            g_wx2_stage[i] = f2_pack(W1(2 * q, c), W1(2 * q + 1, c));
+        } else {
+            const int c = (j - kHP * 3) / kHP, q = (j - kHP * 3) - c * kHP;
+            g_wx2_stage[i] = f2_pack(W2(c, 2 * q), W2(c, 2 * q + 1));
+        }
     }
-    g_wx2_stage[i] = f2_pack(v, v);
 }
 
 // guide_eval for two pixels (a, b) at once; per pixel the same operations in
@@ -268,10 +285,15 @@ __global__ void __launch_bounds__(kThreads, 1) k6_guide_bwd(const float2* __rest
     const int total = tiles_x * tiles_y * N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float inv_ff = 1.f / (float)(F * F);
-    float gw1[kHid * 3], gw2[3 * kHid], gb2[3];
+    // weight-gradient sums, two hidden units per register pair: gw1[q * 3 + c]
+    // holds units (2q, 2q + 1) of input channel c, gw2[c * kHP + q] likewise
+    f32x2 gw1[kHP * 3], gw2[3 * kHP];
+    float gb2[3];
 #pragma unroll
-    for (int k = 0; k < kHid * 3; ++k) gw1[k] = gw2[k] = 0.f;
+    for (int k = 0; k < kHP * 3; ++k) gw1[k] = gw2[k] = f2_splat(0.f);
     gb2[0] = gb2[1] = gb2[2] = 0.f;
+    const f32x2* W1p = c_wh;
+    const f32x2* W2p = c_wh + kHP * 3;
     int cc[VEC];
     float ll[VEC];
 #pragma unroll
@@ -324,27 +346,34 @@ __global__ void __launch_bounds__(kThreads, 1) k6_guide_bwd(const float2* __rest
                     dg[c] = fmaf(r[c][k], A, dl * inv_ff);
                     gb2[c] += dg[c];
                 }
-                float dx0 = 0.f, dx1 = 0.f, dx2 = 0.f;
+                // two hidden units per paired instruction: z, the leaky ReLU
+                // factor m (1 or slope: h = z m and d z = d h m), d h = W2^T d G,
+                // the two weight-gradient outer products and d I = W1^T d z
+                const f32x2 xs0 = f2_splat(x[0][k]), xs1 = f2_splat(x[1][k]), xs2 = f2_splat(x[2][k]);
+                const f32x2 d0 = f2_splat(dg[0]), d1 = f2_splat(dg[1]), d2 = f2_splat(dg[2]);
+                f32x2 dx0 = f2_splat(0.f), dx1 = f2_splat(0.f), dx2 = f2_splat(0.f);
 #pragma unroll
-                for (int kk = 0; kk < kHid; ++kk) {
-                    const float z = fmaf(c_w1[kk * 3 + 2], x[2][k],
-                                         fmaf(c_w1[kk * 3 + 1], x[1][k], c_w1[kk * 3 + 0] * x[0][k]));
-                    const float hk = lrelu(z, slope);
-                    const float dh = fmaf(c_w2[2 * kHid + kk], dg[2],
-                                          fmaf(c_w2[1 * kHid + kk], dg[1], c_w2[kk] * dg[0]));
-                    const float dz = z > 0.f ? dh : slope * dh;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) gw2[c * kHid + kk] = fmaf(dg[c], hk, gw2[c * kHid + kk]);
-                    gw1[kk * 3 + 0] = fmaf(dz, x[0][k], gw1[kk * 3 + 0]);
-                    gw1[kk * 3 + 1] = fmaf(dz, x[1][k], gw1[kk * 3 + 1]);
-                    gw1[kk * 3 + 2] = fmaf(dz, x[2][k], gw1[kk * 3 + 2]);
-                    dx0 = fmaf(c_w1[kk * 3 + 0], dz, dx0);
-                    dx1 = fmaf(c_w1[kk * 3 + 1], dz, dx1);
-                    dx2 = fmaf(c_w1[kk * 3 + 2], dz, dx2);
+                for (int q = 0; q < kHP; ++q) {
+                    const f32x2 z = f2x_fma(W1p[q * 3 + 2], xs2, f2x_fma(W1p[q * 3 + 1], xs1, f2x_mul(W1p[q * 3 + 0], xs0)));
+                    float za, zb;
+                    f2_unpack(z, za, zb);
+                    const f32x2 m = f2_pack(za > 0.f ? 1.f : slope, zb > 0.f ? 1.f : slope);
+                    const f32x2 hk = f2x_mul(z, m);
+                    const f32x2 dh = f2x_fma(W2p[2 * kHP + q], d2, f2x_fma(W2p[kHP + q], d1, f2x_mul(W2p[q], d0)));
+                    const f32x2 dz = f2x_mul(dh, m);
+                    gw2[0 * kHP + q] = f2x_fma(d0, hk, gw2[0 * kHP + q]);
+                    gw2[1 * kHP + q] = f2x_fma(d1, hk, gw2[1 * kHP + q]);
+                    gw2[2 * kHP + q] = f2x_fma(d2, hk, gw2[2 * kHP + q]);
+                    gw1[q * 3 + 0] = f2x_fma(dz, xs0, gw1[q * 3 + 0]);
+                    gw1[q * 3 + 1] = f2x_fma(dz, xs1, gw1[q * 3 + 1]);
+                    gw1[q * 3 + 2] = f2x_fma(dz, xs2, gw1[q * 3 + 2]);
+                    dx0 = f2x_fma(W1p[q * 3 + 0], dz, dx0);
+                    dx1 = f2x_fma(W1p[q * 3 + 1], dz, dx1);
+                    dx2 = f2x_fma(W1p[q * 3 + 2], dz, dx2);
                 }
-                o[0][k] = dx0;
-                o[1][k] = dx1;
-                o[2][k] = dx2;
+                o[0][k] = f2_lo(dx0) + f2_hi(dx0);  // even and odd hidden units
+                o[1][k] = f2_lo(dx1) + f2_hi(dx1);
+                o[2][k] = f2_lo(dx2) + f2_hi(dx2);
             }
             if (dI_h != nullptr) {
 #pragma unroll
@@ -356,7 +385,16 @@ __global__ void __launch_bounds__(kThreads, 1) k6_guide_bwd(const float2* __rest
     // block reduction of the 99 sums (fixed order), one partial row per CTA
 #pragma unroll
     for (int k = 0; k < kWGrad; ++k) {
-        float v = k < 48 ? gw1[k] : (k < 96 ? gw2[k - 48] : gb2[k - 96]);
+        float v;
+        if (k < kHid * 3) {  // w1 (unit kk, channel c)
+            const int kk = k / 3, c = k - 3 * kk;
+            v = (kk & 1) ? f2_hi(gw1[(kk >> 1) * 3 + c]) : f2_lo(gw1[(kk >> 1) * 3 + c]);
+        } else if (k < 2 * kHid * 3) {  // w2 (channel c, unit kk)
+            const int c = (k - kHid * 3) / kHid, kk = (k - kHid * 3) - c * kHid;
+            v = (kk & 1) ? f2_hi(gw2[c * kHP + (kk >> 1)]) : f2_lo(gw2[c * kHP + (kk >> 1)]);
+        } else {
+            v = gb2[k - 2 * kHid * 3];
+        }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         if (lane == 0) red[warp][k] = v;
@@ -489,11 +527,14 @@ cudaError_t guide_upload(const float* w1, const float* w2, const float* b2, int 
     }
     e = cudaMemcpyToSymbolAsync(c_b2, b2, sizeof(float) * 3, 0, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
-    k_splat_weights<<<1, 128, 0, s>>>(w1, w2, b2, hidden);
+    k_splat_weights<<<1, 160, 0, s>>>(w1, w2, b2, hidden);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     void* stage = nullptr;
     if ((e = cudaGetSymbolAddress(&stage, g_wx2_stage)) != cudaSuccess) return e;
-    return cudaMemcpyToSymbolAsync(c_wx2, stage, sizeof(f32x2) * kWPairs, 0, cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyToSymbolAsync(c_wx2, stage, sizeof(f32x2) * kWPairs, 0, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbolAsync(c_wh, static_cast<f32x2*>(stage) + kWPairs, sizeof(f32x2) * kHidPairs, 0,
+                                   cudaMemcpyDeviceToDevice, s);
 }
 
 template <typename T>

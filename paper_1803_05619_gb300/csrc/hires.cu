@@ -1,6 +1,10 @@
 // High-resolution kernels: K2 (bilinear upsampling of Abar, bbar and the
 // affine step, Eq. 2) and K3 (the transposed upsampler of Algorithm 1's
 // first two lines as a gather, plus d I_h = d O_h * Abar_h).
+#include <cmath>
+#include <map>
+#include <mutex>
+
 #include "batch.cuh"
 #include "common.cuh"
 #include "hires.cuh"
@@ -169,11 +173,43 @@ __device__ __forceinline__ void apply_batched_tile(const BatchImage& im, int loc
 // One persistent kernel per (storage type, vector width, factor) class:
 // each graph node walks the flat tile list of the images of its class.
 template <typename T, int VEC, int F>
-__global__ void __launch_bounds__(kThreads) k2_apply_batched(const __grid_constant__ BatchParams bp) {
+__global__ void __launch_bounds__(kThreads) k2_apply_batched(const __grid_constant__ BatchParams bp, uint32_t*) {
     extern __shared__ __align__(128) float2 sAB[];
     for (int tile = blockIdx.x; tile < bp.k2_total; tile += gridDim.x) {
         const int i = batch_find(bp.k2_start, bp.n, tile);
         apply_batched_tile<T, VEC, F>(bp.img[i], tile - bp.k2_start[i], sAB);
+    }
+}
+
+// K2 strips staged by TMA (16-byte vectors; every image of the class has a
+// tensor map of I_h in device memory): a work item is WPC strip segments of
+// one plane, one per warp, each with its own slot ring (k2_th = LS).
+template <typename T, int VEC, int F>
+__global__ void __launch_bounds__(K2Tma<T, VEC, F>::WPC * 32)
+    k2_strip_batched_tma(const __grid_constant__ BatchParams bp, uint32_t* status) {
+    extern __shared__ __align__(1024) unsigned char k2bring[];
+    using B = K2Tma<T, VEC, F>;
+    const int warp = threadIdx.x >> 5;
+    unsigned char* ring = k2bring + (size_t)warp * B::NSB * B::SLOT;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(k2bring + (size_t)B::WPC * B::NSB * B::SLOT) + warp * B::NSB;
+    for (int tile = blockIdx.x; tile < bp.k2_total; tile += gridDim.x) {
+        const int i = batch_find(bp.k2_start, bp.n, tile);
+        const BatchImage& im = bp.img[i];
+        const int local = tile - bp.k2_start[i];
+        const int nstrip = (im.w_l + 32 * (VEC / F) - 1) / (32 * (VEC / F));
+        const int nseg = (im.h_l + im.k2_th - 1) / im.k2_th;
+        const int plane = local / im.k2_nx;
+        const int item = (local - plane * im.k2_nx) * B::WPC + warp;
+        if (item >= nstrip * nseg) continue;  // warp-uniform; no barrier follows
+        const int strip = item % nstrip, sg = item / nstrip;
+        const CUtensorMap* map = static_cast<const CUtensorMap*>(im.k2_map);
+        if ((threadIdx.x & 31) == 0) tensormap_acquire(map);
+        __syncwarp();
+        const size_t hw = (size_t)im.h * im.w, lw = (size_t)im.h_l * im.w_l;
+        if (!k2_strip_tma<T, VEC, F>(im.coef + plane * lw, map, static_cast<T*>(im.O_h) + plane * hw, im.h_l, im.w_l,
+                                     im.h, im.w, strip, sg * im.k2_th, min(sg * im.k2_th + im.k2_th, im.h_l), plane,
+                                     ring, bars, status))
+            return;  // timeout recorded; this warp stops
     }
 }
 
@@ -207,28 +243,84 @@ size_t k2_strip_batched_smem(int esize, int vec, int F) {
     return (size_t)kWarps * nsb * (32 * vec) * F * esize;
 }
 
+// Segment length near `ls` whose grid fills whole waves of the kernel's
+// resident CTA slots, so no SM idles through a last partial wave (the strip
+// kernels give the same bits at every segment length).  `halo`: extra
+// low-res rows a segment walks besides its own.
+static std::mutex g_occ_mu;
+static std::map<const void*, int> g_occ;  // resident CTAs per SM, per kernel
+static int g_occ_sms = 0;
+
+template <typename K>
+static int wave_fit_ls(K kern, int threads, size_t smem, int ls, int nstrip, int rows, int planes, int wpc,
+                       float halo) {
+    int occ = 0, sms = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        if (g_occ_sms == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&g_occ_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                g_occ_sms = 152;
+            }
+        }
+        sms = g_occ_sms;
+        auto it = g_occ.find((const void*)kern);
+        if (it == g_occ.end()) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) {
+                cudaGetLastError();
+                occ = 0;
+            }
+            g_occ[(const void*)kern] = occ;
+        } else {
+            occ = it->second;
+        }
+    }
+    if (occ <= 0 || ls < 2) return ls;
+    const double slots = (double)occ * sms;
+    int best = ls;
+    double best_cost = 1e30;
+    for (int c = std::max(2, ls / 2); c <= ls + ls / 2; ++c) {
+        const long long ctas = ((long long)nstrip * ((rows + c - 1) / c) * planes + wpc - 1) / wpc;
+        const double waves = (double)ctas / slots;
+        const double eff = waves / std::ceil(waves);
+        const double cost = (c + halo) / (double)c / eff;
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    return best;
+}
+
 template <typename T, int VEC, int F>
 static cudaError_t k2s_go(const float2* coef, const void* in, void* out, int planes, int h_l, int w_l, int h, int w,
                           int LS, const K2Map* map, uint32_t* status, cudaStream_t s) {
-    const int nstrip = (w_l + 32 * (VEC / F) - 1) / (32 * (VEC / F)), nseg = (h_l + LS - 1) / LS;
-    const long long warps = (long long)nstrip * nseg * planes;
+    const int nstrip = (w_l + 32 * (VEC / F) - 1) / (32 * (VEC / F));
     if constexpr (VEC * sizeof(T) == 16) {
         if (map != nullptr) {
             using B = K2Tma<T, VEC, F>;
             auto kern = k2_apply_strip_tma<T, VEC, F>;
             cudaError_t e = prep(kern, B::CTA_BYTES);
             if (e != cudaSuccess) return e;
+            LS = wave_fit_ls(kern, B::WPC * 32, B::CTA_BYTES, LS, nstrip, h_l, planes, B::WPC, 0.25f);
+            const int nseg = (h_l + LS - 1) / LS;
+            const long long warps = (long long)nstrip * nseg * planes;
             const int ctas = (int)((warps + B::WPC - 1) / B::WPC);
             kern<<<ctas, B::WPC * 32, B::CTA_BYTES, s>>>(coef, *map, static_cast<T*>(out), h_l, w_l, h, w, LS, nstrip,
                                                           nseg, planes, status);
             return cudaGetLastError();
         }
     }
-    const int ctas = (int)((warps + kWarps - 1) / kWarps);
     constexpr size_t smem = kWarps * K2Async<T, VEC, F>::WARP_BYTES;
     auto kern = k2_apply_strip<T, VEC, F>;
     cudaError_t e = prep(kern, smem);
     if (e != cudaSuccess) return e;
+    LS = wave_fit_ls(kern, kThreads, smem, LS, nstrip, h_l, planes, kWarps, 0.25f);
+    const int nseg = (h_l + LS - 1) / LS;
+    const long long warps = (long long)nstrip * nseg * planes;
+    const int ctas = (int)((warps + kWarps - 1) / kWarps);
     kern<<<ctas, kThreads, smem, s>>>(coef, static_cast<const T*>(in), static_cast<T*>(out), h_l, w_l, h, w, LS,
                                       nstrip, nseg, planes);
     return cudaGetLastError();
@@ -329,20 +421,25 @@ static cudaError_t k3_go(const float2* coef, const void* R, const void* G, void*
                          int planes, int h_l, int w_l, int h, int w, int LS, const K3Maps* maps, uint32_t* status,
                          cudaStream_t s) {
     constexpr int OUT = K3Strip<VEC, F>::OUT;
-    const int nstrip = (w_l + OUT - 1) / OUT, nseg = (h_l + LS - 1) / LS;
-    const long long warps = (long long)nstrip * nseg * planes;
+    const int nstrip = (w_l + OUT - 1) / OUT;
     if constexpr (VEC * sizeof(T) == 16) {
         if (maps != nullptr) {
             using B = K3Tma<T, VEC, F>;
             auto kern = k3_hires_bwd_tma<T, VEC, F>;
             cudaError_t e = prep(kern, B::CTA_BYTES);
             if (e != cudaSuccess) return e;
+            LS = wave_fit_ls(kern, B::WPC * 32, B::CTA_BYTES, LS, nstrip, h_l, planes, B::WPC, 1.f);
+            const int nseg = (h_l + LS - 1) / LS;
+            const long long warps = (long long)nstrip * nseg * planes;
             const int ctas = (int)((warps + B::WPC - 1) / B::WPC);
             kern<<<ctas, B::WPC * 32, B::CTA_BYTES, s>>>(coef, *maps, static_cast<T*>(dG), dcoef, h_l, w_l, h, w,
                                                           LS, nstrip, nseg, planes, status);
             return cudaGetLastError();
         }
     }
+    LS = wave_fit_ls(k3_hires_bwd<T, VEC, F>, kThreads, 0, LS, nstrip, h_l, planes, kWarps, 1.f);
+    const int nseg = (h_l + LS - 1) / LS;
+    const long long warps = (long long)nstrip * nseg * planes;
     const int ctas = (int)((warps + kWarps - 1) / kWarps);
     k3_hires_bwd<T, VEC, F><<<ctas, kThreads, 0, s>>>(coef, static_cast<const T*>(R), static_cast<const T*>(G),
                                                       static_cast<T*>(dG), dcoef, h_l, w_l, h, w, LS, nstrip, nseg,
@@ -425,6 +522,36 @@ static cudaError_t k2b_dispatch(int vec, int F, size_t smem, void** fn) {
         return k2b_get<T, VH, 0>(smem, fn);
     }
     return k2b_get<T, 1, 0>(smem, fn);
+}
+
+template <typename T, int VEC, int F>
+static cudaError_t k2bt_get(void** fn, size_t* smem, int* threads) {
+    using B = K2Tma<T, VEC, F>;
+    *fn = (void*)k2_strip_batched_tma<T, VEC, F>;
+    *smem = B::CTA_BYTES;
+    *threads = B::WPC * 32;
+    return prep(k2_strip_batched_tma<T, VEC, F>, B::CTA_BYTES);
+}
+
+template <typename T>
+static cudaError_t k2bt_dispatch(int vec, int F, void** fn, size_t* smem, int* threads) {
+    constexpr int VW = 16 / sizeof(T);
+    if (vec == VW) {
+        if (F == 2) return k2bt_get<T, VW, 2>(fn, smem, threads);
+        if (F == 4) return k2bt_get<T, VW, 4>(fn, smem, threads);
+        if constexpr (VW >= 8)
+            if (F == 8) return k2bt_get<T, VW, 8>(fn, smem, threads);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t k2_batched_tma_kernel(dgf_dtype dt, int vec, int F, void** fn, size_t* smem, int* threads) {
+    switch (dt) {
+        case DGF_F32: return k2bt_dispatch<float>(vec, F, fn, smem, threads);
+        case DGF_BF16: return k2bt_dispatch<__nv_bfloat16>(vec, F, fn, smem, threads);
+        case DGF_F16: return k2bt_dispatch<__half>(vec, F, fn, smem, threads);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t k2_batched_kernel(dgf_dtype dt, int vec, int F, size_t smem, void** fn) {

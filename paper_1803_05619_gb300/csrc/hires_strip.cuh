@@ -100,12 +100,14 @@ __device__ __forceinline__ void k3s_load(const T* __restrict__ R, const T* __res
 
 // Per-lane state of a strip walk: Abar rows i, i + 1 along x at the lane's
 // pixels, and the accumulators of d Abar, d bbar rows i (lo) and i + 1 (hi).
-template <int VEC, int F>
+// PD: blocks ahead that the Abar cells are loaded (the fused backward,
+// whose Abar rows are produced as it walks, uses 1).
+template <int VEC, int F, int PD = 1>
 struct K3State {
     static constexpr int K = VEC / F;
     float Hlo[VEC], Hhi[VEC];
     float alu[K], alv[K], ahu[K], ahv[K];
-    float own_next[K];  // Abar cells of the next block's second tap row, loaded a block ahead
+    float own_next[PD][K];  // Abar cells of the next PD blocks' second tap rows, oldest first
 };
 
 struct K3Lane {
@@ -128,19 +130,24 @@ __device__ __forceinline__ K3Lane k3s_lane(int strip, int w_l) {
     return L;
 }
 
-// Block i begins: Abar rows i and i + 1 (clamped) along x.
-template <int VEC, int F, class Src>
-__device__ __forceinline__ void k3s_block_start(K3State<VEC, F>& st, const Src& coef, int i, const K3Lane& L,
+// Block i begins: Abar rows i and i + 1 (clamped) along x; the cells of row
+// i + 1 + PD are loaded for later blocks.
+template <int VEC, int F, int PD, class Src>
+__device__ __forceinline__ void k3s_block_start(K3State<VEC, F, PD>& st, const Src& coef, int i, const K3Lane& L,
                                                 int h_l, int w_l) {
 #pragma unroll
     for (int k = 0; k < VEC; ++k) st.Hlo[k] = st.Hhi[k];
-    k3s_hrow_from<VEC, F>(st.own_next, L.J, w_l, st.Hhi);  // row min(i + 1, h_l - 1)
-    k3s_own<VEC, F>(coef, min(i + 2, h_l - 1), L.J, w_l, st.own_next);
+    k3s_hrow_from<VEC, F>(st.own_next[0], L.J, w_l, st.Hhi);  // row min(i + 1, h_l - 1)
+#pragma unroll
+    for (int d = 0; d + 1 < PD; ++d)
+#pragma unroll
+        for (int c = 0; c < VEC / F; ++c) st.own_next[d][c] = st.own_next[d + 1][c];
+    k3s_own<VEC, F>(coef, min(i + 1 + PD, h_l - 1), L.J, w_l, st.own_next[PD - 1]);
 }
 
 // High-res row y = F i + F/2 + t of block i (t compile-time after unrolling).
-template <typename T, int VEC, int F>
-__device__ __forceinline__ void k3s_row(K3State<VEC, F>& st, const float (&r)[VEC], const float (&g)[VEC], int t,
+template <typename T, int VEC, int F, int PD>
+__device__ __forceinline__ void k3s_row(K3State<VEC, F, PD>& st, const float (&r)[VEC], const float (&g)[VEC], int t,
                                         int i, int ia, const K3Lane& L, T* __restrict__ dG, int h, int w) {
     constexpr int K = VEC / F;
     const int y = F * i + F / 2 + t;
@@ -197,8 +204,8 @@ __device__ __forceinline__ void k3s_row(K3State<VEC, F>& st, const float (&r)[VE
 
 // Block i done: row i of d Abar, d bbar is complete; write it (rows this
 // segment owns) and move the accumulators down one row.
-template <int VEC, int F>
-__device__ __forceinline__ void k3s_block_end(K3State<VEC, F>& st, int i, int ia, const K3Lane& L, int h_l,
+template <int VEC, int F, int PD>
+__device__ __forceinline__ void k3s_block_end(K3State<VEC, F, PD>& st, int i, int ia, const K3Lane& L, int h_l,
                                               int w_l, float2* __restrict__ dcoef) {
     constexpr int K = VEC / F;
     if (i == -1) {  // virtual row -1 folds into row 0
@@ -250,13 +257,14 @@ __device__ __forceinline__ void k3s_block_end(K3State<VEC, F>& st, int i, int ia
     }
 }
 
-template <int VEC, int F, class Src>
-__device__ __forceinline__ void k3s_init(K3State<VEC, F>& st, const Src& coef, int ib0, const K3Lane& L, int h_l,
+template <int VEC, int F, int PD, class Src>
+__device__ __forceinline__ void k3s_init(K3State<VEC, F, PD>& st, const Src& coef, int ib0, const K3Lane& L, int h_l,
                                          int w_l) {
     constexpr int K = VEC / F;
-    k3s_own<VEC, F>(coef, clampi(ib0, 0, h_l - 1), L.J, w_l, st.own_next);
-    k3s_hrow_from<VEC, F>(st.own_next, L.J, w_l, st.Hhi);
-    k3s_own<VEC, F>(coef, min(max(ib0, -1) + 1, h_l - 1), L.J, w_l, st.own_next);
+    k3s_own<VEC, F>(coef, clampi(ib0, 0, h_l - 1), L.J, w_l, st.own_next[0]);
+    k3s_hrow_from<VEC, F>(st.own_next[0], L.J, w_l, st.Hhi);
+#pragma unroll
+    for (int d = 0; d < PD; ++d) k3s_own<VEC, F>(coef, min(max(ib0, -1) + 1 + d, h_l - 1), L.J, w_l, st.own_next[d]);
 #pragma unroll
     for (int c = 0; c < K; ++c) st.alu[c] = st.alv[c] = st.ahu[c] = st.ahv[c] = 0.f;
 }
@@ -320,8 +328,12 @@ struct K3Tma {
 };
 
 
+// Returns false after a timeout (recorded in the status word); the warp's
+// copies have then landed or been waited for (bounded).  On success the slot
+// barriers are invalidated, so a persistent warp can call it again with the
+// same ring.
 template <typename T, int VEC, int F>
-__device__ void k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps, T* __restrict__ dG,
+__device__ bool k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps, T* __restrict__ dG,
                              float2* __restrict__ dcoef, int h_l, int w_l, int h, int w, int strip, int ia, int ib,
                              int plane, unsigned char* ring, uint64_t* bars, uint32_t* status) {
     using B = K3Tma<T, VEC, F>;
@@ -342,10 +354,12 @@ __device__ void k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps
         tma_load_3d(dst, &maps->r, xs, y, plane, bar);
         tma_load_3d(dst + (uint32_t)B::BOX_BYTES, &maps->g, xs, y, plane, bar);
     };
+    __syncwarp();  // a previous walk's reads of the ring are done
     if (lane == 0) {
         for (int s = 0; s < NSB; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         for (int m = 0; m < min(NSB, nblk); ++m) issue(m);
     }
     __syncwarp();
@@ -383,7 +397,12 @@ __device__ void k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps
         if (lane == 0) status_fail(status, kStatusTimeout);
         for (int q = m; q < nblk && q < m + NSB; ++q)
             mbar_wait(bar_s + 8u * (q % NSB), (uint32_t)((q / NSB) & 1), kWaitLimit);
+        return false;
     }
+    __syncwarp();  // every lane has passed its last wait
+    if (lane == 0)
+        for (int s = 0; s < NSB; ++s) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar_s + 8u * s) : "memory");
+    return true;
 }
 
 // ------------------------------------------------------------- K2 strip
@@ -396,11 +415,13 @@ __device__ void k3_strip_tma(const float2* __restrict__ coef, const K3Maps* maps
 // (no halo).  Rows reach the lanes through per-warp shared-memory slots,
 // filled by TMA (16-byte vectors, single calls) or by per-lane asynchronous
 // copies.
-template <int VEC, int F>
+// PD: blocks ahead that the coefficient taps are loaded (the fused forward,
+// whose coefficient rows are produced as it walks, uses 1).
+template <int VEC, int F, int PD = 1>
 struct K2Rows {
     float A1[VEC], B1[VEC];       // row i + 1 (the block's second tap row) along x
     float DA[VEC], DB[VEC];       // row i + 1 minus row i
-    float2 next[VEC / F + 2];     // tap columns of the next block's second row, loaded a block ahead
+    float2 next[PD][VEC / F + 2]; // tap columns of the next PD blocks' second rows, oldest first
 };
 
 // Where K2 reads (Abar, bbar) of row ii, column jj from: the plane's
@@ -428,20 +449,27 @@ __device__ __forceinline__ void k2s_hrow_from(const float2 (&tp)[VEC / F + 2], f
     }
 }
 
-// Before the first block b0: row clamp(b0) becomes the "second tap" row.
-template <int VEC, int F, class Src>
-__device__ __forceinline__ void k2s_init(K2Rows<VEC, F>& q, const Src& coef, int b0, int J, int h_l, int w_l) {
-    k2s_taps<VEC, F>(coef, clampi(b0, 0, h_l - 1), J, w_l, q.next);
-    k2s_hrow_from<VEC, F>(q.next, q.A1, q.B1);
-    k2s_taps<VEC, F>(coef, min(max(b0, -1) + 1, h_l - 1), J, w_l, q.next);
+// Before the first block b0: row clamp(b0) becomes the "second tap" row;
+// the taps of rows b0 + 1 .. b0 + PD (clamped) are loaded ahead.
+template <int VEC, int F, int PD, class Src>
+__device__ __forceinline__ void k2s_init(K2Rows<VEC, F, PD>& q, const Src& coef, int b0, int J, int h_l, int w_l) {
+    k2s_taps<VEC, F>(coef, clampi(b0, 0, h_l - 1), J, w_l, q.next[0]);
+    k2s_hrow_from<VEC, F>(q.next[0], q.A1, q.B1);
+#pragma unroll
+    for (int d = 0; d < PD; ++d) k2s_taps<VEC, F>(coef, min(max(b0, -1) + 1 + d, h_l - 1), J, w_l, q.next[d]);
 }
 
-// Block i begins: taps rows clamp(i) (the previous second row) and clamp(i + 1).
-template <int VEC, int F, class Src>
-__device__ __forceinline__ void k2s_block(K2Rows<VEC, F>& q, const Src& coef, int i, int J, int h_l, int w_l) {
+// Block i begins: taps rows clamp(i) (the previous second row) and clamp(i + 1);
+// the taps of row i + 1 + PD are loaded for later blocks.
+template <int VEC, int F, int PD, class Src>
+__device__ __forceinline__ void k2s_block(K2Rows<VEC, F, PD>& q, const Src& coef, int i, int J, int h_l, int w_l) {
     float a[VEC], b[VEC];
-    k2s_hrow_from<VEC, F>(q.next, a, b);  // row min(i + 1, h_l - 1)
-    k2s_taps<VEC, F>(coef, min(i + 2, h_l - 1), J, w_l, q.next);
+    k2s_hrow_from<VEC, F>(q.next[0], a, b);  // row min(i + 1, h_l - 1)
+#pragma unroll
+    for (int d = 0; d + 1 < PD; ++d)
+#pragma unroll
+        for (int c = 0; c < VEC / F + 2; ++c) q.next[d][c] = q.next[d + 1][c];
+    k2s_taps<VEC, F>(coef, min(i + 1 + PD, h_l - 1), J, w_l, q.next[PD - 1]);
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
         q.DA[k] = a[k] - q.A1[k];
@@ -453,8 +481,8 @@ __device__ __forceinline__ void k2s_block(K2Rows<VEC, F>& q, const Src& coef, in
 
 // O_h at row t of the block: lerp along y written from the second row,
 // A1 + (lam_y - 1) DA with lam_y = (2t + 1) / 2F.
-template <int VEC, int F>
-__device__ __forceinline__ void k2s_row(const K2Rows<VEC, F>& q, const float (&g)[VEC], int t, float (&o)[VEC]) {
+template <int VEC, int F, int PD>
+__device__ __forceinline__ void k2s_row(const K2Rows<VEC, F, PD>& q, const float (&g)[VEC], int t, float (&o)[VEC]) {
     const float lm1 = (float)(2 * t + 1 - 2 * F) / (float)(2 * F);
 #pragma unroll
     for (int k = 0; k < VEC; ++k) o[k] = fmaf(fmaf(lm1, q.DA[k], q.A1[k]), g[k], fmaf(lm1, q.DB[k], q.B1[k]));
@@ -497,8 +525,11 @@ struct K2Tma {
 };
 
 // Same walk with the input rows staged per block by TMA (16-byte vectors).
+// Returns false after a timeout (recorded in the status word); on success
+// the slot barriers are invalidated, so a persistent warp can call it again
+// with the same ring.
 template <typename T, int VEC, int F>
-__device__ void k2_strip_tma(const float2* __restrict__ coef, const CUtensorMap* map, T* __restrict__ out, int h_l,
+__device__ bool k2_strip_tma(const float2* __restrict__ coef, const CUtensorMap* map, T* __restrict__ out, int h_l,
                              int w_l, int h, int w, int strip, int ia, int ib, int plane, unsigned char* ring,
                              uint64_t* bars, uint32_t* status) {
     using B = K2Tma<T, VEC, F>;
@@ -517,10 +548,12 @@ __device__ void k2_strip_tma(const float2* __restrict__ coef, const CUtensorMap*
                      : "memory");
         tma_load_3d(ring_s + (uint32_t)(slot * B::SLOT), map, xs, F * (b0 + m) + H0, plane, bar);
     };
+    __syncwarp();  // a previous walk's reads of the ring are done
     if (lane == 0) {
         for (int s = 0; s < NSB; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         for (int m = 0; m < min(NSB, nblk); ++m) issue(m);
     }
     __syncwarp();
@@ -560,7 +593,12 @@ __device__ void k2_strip_tma(const float2* __restrict__ coef, const CUtensorMap*
         if (lane == 0) status_fail(status, kStatusTimeout);
         for (int qb = m; qb < nblk && qb < m + NSB; ++qb)
             mbar_wait(bar_s + 8u * (qb % NSB), (uint32_t)((qb / NSB) & 1), kWaitLimit);
+        return false;
     }
+    __syncwarp();  // every lane has passed its last wait
+    if (lane == 0)
+        for (int s = 0; s < NSB; ++s) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar_s + 8u * s) : "memory");
+    return true;
 }
 
 // Same walk with the input rows staged by per-lane asynchronous copies

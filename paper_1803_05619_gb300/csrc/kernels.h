@@ -192,9 +192,23 @@ extern template cudaError_t launch_k4_fast<8>(dgf_dtype, bool, const void*, cons
                                               int, int, int, float, const LowCfg&, const TmaTriple*, uint32_t*, const float4*,
                                               cudaStream_t);
 
+// Persistent kernels of the batched backward (batch_bwd.cuh), 16-bit storage:
+// K3 strips per (vector width, factor, TMA staging or plain loads); sliding K4 per (radius, columns per
+// lane), with the dynamic shared memory and threads of its CTA.
+cudaError_t k3_batched_kernel(dgf_dtype dt, int vec, int F, bool tma, void** fn, size_t* smem, int* threads);
+cudaError_t k4_batched_kernel(dgf_dtype dt, int r, int V, void** fn, size_t* smem, int* threads);
+int slide_out_cols(int r, int V);
+
 // Persistent batched kernels (function pointers for graph nodes).
-// V: columns per lane of the sliding form (mode 3), else ignored
-cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn, int V = 0);
+// V: columns per lane of the sliding form (mode 3), else ignored; threads:
+// the CTA size of the kernel (the sliding form's single-call warps per CTA,
+// else kThreads), if not null
+cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn, int V = 0,
+                              int* threads = nullptr);
+int k1_slide_batched_wpc(int r, int V);
 cudaError_t k2_batched_kernel(dgf_dtype dt, int vec, int F, size_t smem, void** fn);
+// K2 strips staged by TMA (16-byte vectors, integer F dividing vec): the
+// kernel, its dynamic shared memory and threads per CTA
+cudaError_t k2_batched_tma_kernel(dgf_dtype dt, int vec, int F, void** fn, size_t* smem, int* threads);
 
 }  // namespace dgf

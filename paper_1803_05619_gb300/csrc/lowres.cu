@@ -24,24 +24,33 @@ int slide_out_cols(int r, int V) {
     const int hb = V * ((2 * r + V - 1) / V);
     return 32 * V - 2 * hb;
 }
-// per-warp bytes of the sliding K1 for 16-bit G and P (the batched kernel's
-// types), taken from the device code's own constant
+// per-warp bytes and warps per CTA of the sliding K1 for 16-bit G and P
+// (the batched kernel's types), taken from the device code's own constants
 template <int R, int V>
 static size_t k1_slide_warp16() {
     return (size_t)k1_slide_warp_bytes<__nv_bfloat16, __nv_bfloat16, R, V>();
 }
+template <int R, int V>
+static int k1_slide_wpc16() {
+    return slide_wpc<k1_slide_warp_bytes<__nv_bfloat16, __nv_bfloat16, R, V>()>();
+}
+#define DGF_SLIDE_K1_SHAPES(X) X(1, 2) X(2, 2) X(1, 4) X(2, 4) X(4, 4) X(8, 4) X(1, 8) X(2, 8)
 size_t k1_slide_smem_bytes(int r, int V, int warps) {
     size_t b = 0;
-    if (V == 2 && r == 1) b = k1_slide_warp16<1, 2>();
-    if (V == 2 && r == 2) b = k1_slide_warp16<2, 2>();
-    if (V == 4 && r == 1) b = k1_slide_warp16<1, 4>();
-    if (V == 4 && r == 2) b = k1_slide_warp16<2, 4>();
-    if (V == 4 && r == 4) b = k1_slide_warp16<4, 4>();
-    if (V == 4 && r == 8) b = k1_slide_warp16<8, 4>();
-    if (V == 8 && r == 1) b = k1_slide_warp16<1, 8>();
-    if (V == 8 && r == 2) b = k1_slide_warp16<2, 8>();
+#define DGF_X(RR, VV) \
+    if (r == RR && V == VV) b = k1_slide_warp16<RR, VV>();
+    DGF_SLIDE_K1_SHAPES(DGF_X)
+#undef DGF_X
     return b * (size_t)warps;
 }
+int k1_slide_batched_wpc(int r, int V) {
+#define DGF_X(RR, VV) \
+    if (r == RR && V == VV) return k1_slide_wpc16<RR, VV>();
+    DGF_SLIDE_K1_SHAPES(DGF_X)
+#undef DGF_X
+    return kWarps;
+}
+#undef DGF_SLIDE_K1_SHAPES
 
 static cudaError_t launch_k1_slide(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes,
                                    int h, int w, int r, float eps, const LowCfg& c, cudaStream_t s) {
@@ -318,7 +327,10 @@ size_t k4_fast_smem_bytes(int r, int CW, int EY1) {
 }
 
 size_t k1_cfg_smem(const LowCfg& c, int r, size_t tma_landing) {
-    if (c.fast == 3) return k1_slide_smem_bytes(r, c.b > 0 ? c.b : slide_k1_v(r), kWarps);  // batched: 8 warps
+    if (c.fast == 3) {  // batched: the single call's warps per CTA
+        const int V = c.b > 0 ? c.b : slide_k1_v(r);
+        return k1_slide_smem_bytes(r, V, k1_slide_batched_wpc(r, V));
+    }
     if (c.fast == 2) return 0;  // warp strips keep everything in registers
     return c.fast ? k1_fast_smem_bytes(r, c.a, c.b, tma_landing) : k1_smem_bytes(r, c.a, c.b);
 }
@@ -330,10 +342,12 @@ size_t k4_cfg_smem(const LowCfg& c, int r) {
 
 void low_grid(const LowCfg& c, int r, int h, int w, int& gx, int& gy) {
     if (c.fast == 3) {
-        // batched work items: kWarps strip segments (one per warp of a CTA)
+        // batched work items: one strip segment per warp of a CTA (the single
+        // call's warps per CTA)
         const int V = c.b > 0 ? c.b : slide_k1_v(r), S = c.a > 0 ? c.a : slide_auto_seg(h, r);
         const int nstrip = (w + slide_out_cols(r, V) - 1) / slide_out_cols(r, V), nseg = (h + S - 1) / S;
-        gx = (nstrip * nseg + kWarps - 1) / kWarps;
+        const int wpc = k1_slide_batched_wpc(r, V);
+        gx = (nstrip * nseg + wpc - 1) / wpc;
         gy = 1;
         return;
     }
@@ -447,13 +461,13 @@ cudaError_t launch_k4(dgf_dtype dt, bool guide_f32, const void* G, const void* P
 }
 
 template <typename T>
-cudaError_t k1_batched_kernel_t(int r, int mode, size_t smem, void** fn, int V);
+cudaError_t k1_batched_kernel_t(int r, int mode, size_t smem, void** fn, int V, int* threads);
 
-cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn, int V) {
+cudaError_t k1_batched_kernel(dgf_dtype dt, int r, int mode, size_t smem, void** fn, int V, int* threads) {
     switch (dt) {
-        case DGF_F32: return k1_batched_kernel_t<float>(r, mode, smem, fn, V);
-        case DGF_BF16: return k1_batched_kernel_t<__nv_bfloat16>(r, mode, smem, fn, V);
-        case DGF_F16: return k1_batched_kernel_t<__half>(r, mode, smem, fn, V);
+        case DGF_F32: return k1_batched_kernel_t<float>(r, mode, smem, fn, V, threads);
+        case DGF_BF16: return k1_batched_kernel_t<__nv_bfloat16>(r, mode, smem, fn, V, threads);
+        case DGF_F16: return k1_batched_kernel_t<__half>(r, mode, smem, fn, V, threads);
     }
     return cudaErrorInvalidValue;
 }

@@ -51,6 +51,25 @@ struct SlideGeom {
 
 constexpr int kSlideWarps = 4;  // warps per CTA (independent strip segments)
 
+// Warps per CTA (1 .. kSlideWarps): the count that keeps the most warps'
+// rings resident on an SM (228 KB of shared memory, 1 KB reserved per CTA,
+// at most 227 KB per CTA); the larger count on a tie.
+template <int WARP_BYTES>
+constexpr int slide_wpc() {
+    int best = 1, most = 0;
+    for (int wpc = 1; wpc <= kSlideWarps; ++wpc) {
+        const int cta = wpc * WARP_BYTES + 1024;
+        if (cta > 227 * 1024 + 1024) break;
+        const int warps = (228 * 1024 / cta) * wpc;
+        if (warps >= most) {
+            most = warps;
+            best = wpc;
+        }
+    }
+    return best;
+}
+
+
 // Radius-R horizontal window sums of a row held V columns per lane, on
 // pairs of quantities: out[j] = sum over k in [-R, R] of x at lane column
 // j + k.  Lanes reach their neighbours by shuffles (each half moves on its
@@ -183,7 +202,7 @@ __device__ __forceinline__ float slide_shift(const float (&v)[V], const float (&
 // Asynchronous copy of BYTES (4, 8 or 16) from global to shared memory; the
 // bytes past `src_bytes` are zero-filled (src_bytes = 0: no read at all).
 template <int BYTES>
-__device__ __forceinline__ void cp_async_zfill(uint32_t dst, const void* src, uint32_t src_bytes) {
+__device__ __forceinline__ void slide_cp_async(uint32_t dst, const void* src, uint32_t src_bytes) {
     static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
     if constexpr (BYTES == 16)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
@@ -193,9 +212,9 @@ __device__ __forceinline__ void cp_async_zfill(uint32_t dst, const void* src, ui
                      "r"(src_bytes)
                      : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void slide_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
-__device__ __forceinline__ void cp_async_wait() {
+__device__ __forceinline__ void slide_cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
@@ -225,7 +244,7 @@ __device__ __forceinline__ void stage_row(unsigned char* dst, const T* __restric
         const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
 #pragma unroll
         for (int c = 0; c < BYTES / CH; ++c)
-            cp_async_zfill<CH>(d + c * CH, reinterpret_cast<const char*>(p) + c * CH, in ? CH : 0);
+            slide_cp_async<CH>(d + c * CH, reinterpret_cast<const char*>(p) + c * CH, in ? CH : 0);
     } else {
         Vec<T, V> v;
 #pragma unroll
@@ -254,10 +273,12 @@ __host__ __device__ constexpr int k1_slide_warp_bytes() {
     return (2 * R + 1) * 32 * V * 8 + SlideStage<R>::NR * 32 * V * ((int)sizeof(TG) + (int)sizeof(TP));
 }
 
-template <typename TG, typename TP, int R, int V>
-__device__ void k1_slide_segment(const TG* __restrict__ G, const TP* __restrict__ P, float2* __restrict__ coef,
-                                 int h, int w, float eps, int x_base, int y0, int S, bool aligned,
-                                 float4* __restrict__ ring) {
+// AL: rows are V-element aligned (w a multiple of V, aligned bases): the
+// lanes stage them by asynchronous copies, else by plain loads.
+template <typename TG, typename TP, int R, int V, bool AL>
+__device__ void k1_slide_segment_t(const TG* __restrict__ G, const TP* __restrict__ P, float2* __restrict__ coef,
+                                   int h, int w, float eps, int x_base, int y0, int S, float4* __restrict__ ring) {
+    constexpr bool aligned = AL;
     using Gm = SlideGeom<R, V>;
     constexpr int W = Gm::W;
     const int lane = threadIdx.x & 31;
@@ -306,7 +327,7 @@ __device__ void k1_slide_segment(const TG* __restrict__ G, const TP* __restrict_
 #pragma unroll 1
     for (int tt = 0; tt < D; ++tt) {
         if (tt < nrow) issue(tt, tt);
-        cp_async_commit();
+        slide_cp_commit();
     }
     auto wrap = [](int k) { return k + 1 == NR ? 0 : k + 1; };
     int sn = 0, so = NR - W, sf = D;  // ring slots of rows t, t - W and t + D
@@ -314,8 +335,8 @@ __device__ void k1_slide_segment(const TG* __restrict__ G, const TP* __restrict_
     for (int t = 0; t < nrow; ++t) {
         const int e = e0 + t;
         if (t + D < nrow) issue(t + D, sf);
-        cp_async_commit();
-        cp_async_wait<D>();  // row e (and every older one) has landed
+        slide_cp_commit();
+        slide_cp_wait<D>();  // row e (and every older one) has landed
         // first pass, vertical: add row e ...
         if (e >= 0 && e < h) {
             f32x2 sh[V];
@@ -400,7 +421,19 @@ __device__ void k1_slide_segment(const TG* __restrict__ G, const TP* __restrict_
             }
         }
     }
-    cp_async_wait<0>();  // the last groups are empty; nothing is left in flight
+    slide_cp_wait<0>();  // the last groups are empty; nothing is left in flight
+}
+
+// The segment with the row alignment as a compile-time choice (two
+// specialised walks).
+template <typename TG, typename TP, int R, int V>
+__device__ __forceinline__ void k1_slide_segment(const TG* __restrict__ G, const TP* __restrict__ P,
+                                                 float2* __restrict__ coef, int h, int w, float eps, int x_base,
+                                                 int y0, int S, bool aligned, float4* __restrict__ ring) {
+    if (aligned)
+        k1_slide_segment_t<TG, TP, R, V, true>(G, P, coef, h, w, eps, x_base, y0, S, ring);
+    else
+        k1_slide_segment_t<TG, TP, R, V, false>(G, P, coef, h, w, eps, x_base, y0, S, ring);
 }
 
 // ------------------------------------------------------------------- K4
@@ -482,7 +515,7 @@ __device__ void k4_slide_segment(const TG* __restrict__ G, const TP* __restrict_
 #pragma unroll 1
     for (int tt = 0; tt < D; ++tt) {
         if (tt < nrow) issue(tt, tt);
-        cp_async_commit();
+        slide_cp_commit();
     }
     auto wrap = [](int k) { return k + 1 == NR ? 0 : k + 1; };
     int sn = 0, so = NR - W, sc = NR - 2 * R, sf = D;  // ring slots of rows t, t - W, t - 2R and t + D
@@ -490,8 +523,8 @@ __device__ void k4_slide_segment(const TG* __restrict__ G, const TP* __restrict_
     for (int t = 0; t < nrow; ++t) {
         const int e = e0 + t;
         if (t + D < nrow) issue(t + D, sf);
-        cp_async_commit();
-        cp_async_wait<D>();  // row e (and every older one) has landed
+        slide_cp_commit();
+        slide_cp_wait<D>();  // row e (and every older one) has landed
         if (e >= 0 && e < h) {
             f32x2 sh[V], dd[V];
             terms(sn, e, sh, dd);
@@ -604,7 +637,7 @@ __device__ void k4_slide_segment(const TG* __restrict__ G, const TP* __restrict_
             }
         }
     }
-    cp_async_wait<0>();  // the last groups are empty; nothing is left in flight
+    slide_cp_wait<0>();  // the last groups are empty; nothing is left in flight
 }
 
 }  // namespace dgf

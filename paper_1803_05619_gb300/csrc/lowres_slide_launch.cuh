@@ -9,64 +9,48 @@
 
 namespace dgf {
 
-// Warp w of the grid owns strip (w % nstrip) of segment (w / nstrip) % nseg
-// (S output rows) of plane w / (nstrip nseg); the warps of a CTA are
-// independent (no barrier), each with its own shared-memory ring.
-// Warps per CTA (1 .. kSlideWarps): the count that keeps the most warps'
-// rings resident on an SM (228 KB of shared memory, 1 KB reserved per CTA,
-// at most 227 KB per CTA); the larger count on a tie.
-template <int WARP_BYTES>
-constexpr int slide_wpc() {
-    int best = 1, most = 0;
-    for (int wpc = 1; wpc <= kSlideWarps; ++wpc) {
-        const int cta = wpc * WARP_BYTES + 1024;
-        if (cta > 227 * 1024 + 1024) break;
-        const int warps = (228 * 1024 / cta) * wpc;
-        if (warps >= most) {
-            most = warps;
-            best = wpc;
-        }
-    }
-    return best;
-}
-
+// CTA b of plane b / nx owns WPC consecutive strip segments of that plane
+// (segment item k: strip k % nstrip, S output rows from (k / nstrip) S), one
+// per warp; the warps of a CTA are independent (no barrier), each with its
+// own shared-memory ring.
 template <typename TG, typename TP, int R, int V>
 __global__ void __launch_bounds__(slide_wpc<k1_slide_warp_bytes<TG, TP, R, V>()>() * 32)
     k1_slide(const TG* __restrict__ G, const TP* __restrict__ P, float2* __restrict__ coef, int h, int w, float eps,
-             int S, int nstrip, int nseg, int planes, int aligned) {
+             int S, int nx, int aligned) {
     extern __shared__ __align__(16) float4 k1slring[];
     using Gm = SlideGeom<R, V>;
     constexpr int WPC = slide_wpc<k1_slide_warp_bytes<TG, TP, R, V>()>();
     const int warp = threadIdx.x >> 5;
-    const int gw = blockIdx.x * WPC + warp;
-    if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
-    const int strip = gw % nstrip, rest = gw / nstrip;
-    const int sg = rest % nseg, plane = rest / nseg;
+    const int plane = blockIdx.x / nx;
+    const int item = (blockIdx.x - plane * nx) * WPC + warp;
+    const int nstrip = (w + Gm::OUTC - 1) / Gm::OUTC, nseg = (h + S - 1) / S;
+    if (item >= nstrip * nseg) return;  // whole warp leaves together
     const size_t hw = (size_t)h * w;
     float4* ring = k1slring + (size_t)warp * (k1_slide_warp_bytes<TG, TP, R, V>() / 16);
     k1_slide_segment<TG, TP, R, V>(G + plane * hw, P + plane * hw, coef + plane * hw, h, w, eps,
-                                   strip * Gm::OUTC - Gm::HB, sg * S, S, aligned != 0, ring);
+                                   (item % nstrip) * Gm::OUTC - Gm::HB, (item / nstrip) * S, S, aligned != 0, ring);
 }
 
+// K4: the same decomposition as K1.
 template <typename TG, typename TP, typename TD, int R, int V>
 __global__ void __launch_bounds__(slide_wpc<k4_slide_warp_bytes<TG, TP, R, V>()>() * 32)
     k4_slide(const TG* __restrict__ G, const TP* __restrict__ P, const float2* __restrict__ dcoef,
-             TP* __restrict__ dP, TD* __restrict__ dG, int h, int w, float eps, int S, int nstrip, int nseg,
-             int planes, int aligned, int aligned_pairs) {
+             TP* __restrict__ dP, TD* __restrict__ dG, int h, int w, float eps, int S, int nx, int aligned,
+             int aligned_pairs) {
     extern __shared__ __align__(16) float4 k4slring[];
     using Gm = SlideGeom<R, V>;
     constexpr int WPC = slide_wpc<k4_slide_warp_bytes<TG, TP, R, V>()>();
     const int warp = threadIdx.x >> 5;
-    const int gw = blockIdx.x * WPC + warp;
-    if (gw >= nstrip * nseg * planes) return;
-    const int strip = gw % nstrip, rest = gw / nstrip;
-    const int sg = rest % nseg, plane = rest / nseg;
+    const int plane = blockIdx.x / nx;
+    const int item = (blockIdx.x - plane * nx) * WPC + warp;
+    const int nstrip = (w + Gm::OUTC - 1) / Gm::OUTC, nseg = (h + S - 1) / S;
+    if (item >= nstrip * nseg) return;  // whole warp leaves together
     const size_t hw = (size_t)h * w;
     float4* ring = k4slring + (size_t)warp * (k4_slide_warp_bytes<TG, TP, R, V>() / 16);
     k4_slide_segment<TG, TP, TD, R, V>(G + plane * hw, P + plane * hw, dcoef + plane * hw,
                                        dP ? dP + plane * hw : nullptr, dG ? dG + plane * hw : nullptr, h, w, eps,
-                                       strip * Gm::OUTC - Gm::HB, sg * S, S, aligned != 0, aligned_pairs != 0,
-                                       ring);
+                                       (item % nstrip) * Gm::OUTC - Gm::HB, (item / nstrip) * S, S, aligned != 0,
+                                       aligned_pairs != 0, ring);
 }
 
 template <typename TG, typename TP, int R, int V>
@@ -105,16 +89,17 @@ static cudaError_t k1_slide_go(const void* G, const void* P, float2* coef, int p
                                int S, cudaStream_t s) {
     using Gm = SlideGeom<R, V>;
     const int nstrip = (w + Gm::OUTC - 1) / Gm::OUTC, nseg = (h + S - 1) / S;
-    const long long warps = (long long)nstrip * nseg * planes;
     constexpr int WPC = k1_slide_wpc<TG, TP, R, V>();
-    const int ctas = (int)((warps + WPC - 1) / WPC);
+    const int nx = (nstrip * nseg + WPC - 1) / WPC;  // CTAs per plane
+    const long long ctas = (long long)nx * planes;
+    if (ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
     constexpr size_t smem = k1_slide_smem<TG, TP, R, V>();
     auto kern = k1_slide<TG, TP, R, V>;
     cudaError_t e = slide_prep(kern, smem);
     if (e != cudaSuccess) return e;
     const int aligned = w % V == 0 && slide_ptr_aligned(G, V * sizeof(TG)) && slide_ptr_aligned(P, V * sizeof(TP));
-    kern<<<ctas, WPC * 32, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), coef, h, w, eps,
-                                              S, nstrip, nseg, planes, aligned);
+    kern<<<(unsigned)ctas, WPC * 32, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), coef, h, w,
+                                                 eps, S, nx, aligned);
     return cudaGetLastError();
 }
 
@@ -123,9 +108,10 @@ static cudaError_t k4_slide_go(const void* G, const void* P, const float2* dcoef
                                int h, int w, float eps, int S, cudaStream_t s) {
     using Gm = SlideGeom<R, V>;
     const int nstrip = (w + Gm::OUTC - 1) / Gm::OUTC, nseg = (h + S - 1) / S;
-    const long long warps = (long long)nstrip * nseg * planes;
     constexpr int WPC = k4_slide_wpc<TG, TP, R, V>();
-    const int ctas = (int)((warps + WPC - 1) / WPC);
+    const int nx = (nstrip * nseg + WPC - 1) / WPC;  // CTAs per plane
+    const long long ctas = (long long)nx * planes;
+    if (ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
     constexpr size_t smem = k4_slide_smem<TG, TP, R, V>();
     auto kern = k4_slide<TG, TP, TD, R, V>;
     cudaError_t e = slide_prep(kern, smem);
@@ -133,9 +119,9 @@ static cudaError_t k4_slide_go(const void* G, const void* P, const float2* dcoef
     const int aligned = w % V == 0 && slide_ptr_aligned(G, V * sizeof(TG)) && slide_ptr_aligned(P, V * sizeof(TP)) &&
                         slide_ptr_aligned(dP, V * sizeof(TP)) && slide_ptr_aligned(dG, V * sizeof(TD));
     const int aligned_pairs = w % 2 == 0 && slide_ptr_aligned(dcoef, 16);
-    kern<<<ctas, WPC * 32, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef,
-                                              static_cast<TP*>(dP), static_cast<TD*>(dG), h, w, eps, S, nstrip, nseg,
-                                              planes, aligned, aligned_pairs);
+    kern<<<(unsigned)ctas, WPC * 32, smem, s>>>(static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef,
+                                                 static_cast<TP*>(dP), static_cast<TD*>(dG), h, w, eps, S, nx,
+                                                 aligned, aligned_pairs);
     return cudaGetLastError();
 }
 

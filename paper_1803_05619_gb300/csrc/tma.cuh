@@ -95,6 +95,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long lon
     return false;
 }
 
+// Before a tensor map written by a host copy into global memory is used:
+// acquire it into the tensor-map proxy (system scope: the writer was a copy
+// from the host).
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
                                             uint32_t bar) {
     asm volatile(

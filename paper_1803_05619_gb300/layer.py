@@ -222,11 +222,12 @@ def gf_forward_batched(images, out=None):
 
 
 def gf_backward_batched(images, grads):
-    """Batched backward (Algorithm 1 per image, chains run concurrently).
+    """Batched backward (Algorithm 1 per image, one graph or concurrent chains).
 
     ``images``: list of dicts with p_l, I_l, I_h (C x h x w tensors, one
-    dtype), r, eps; ``grads``: the matching list of d O_h.  Returns a list
-    of (dp_l, dI_l, dI_h) per image.
+    dtype), r, eps, and optionally need_p / need_Il / need_Ih (default
+    True); ``grads``: the matching list of d O_h.  Returns a list of
+    (dp_l, dI_l, dI_h) per image, None where not wanted.
     """
     n = len(images)
     if n == 0:
@@ -239,12 +240,15 @@ def gf_backward_batched(images, grads):
         _check(im["p_l"], im["I_l"], im["I_h"])
         if R.dtype != im["I_h"].dtype or R.shape != im["I_h"].shape or not R.is_contiguous():
             raise ValueError("d O_h must match I_h in shape, dtype and layout")
-        dp, dIl, dIh = torch.empty_like(im["p_l"]), torch.empty_like(im["I_l"]), torch.empty_like(im["I_h"])
+        dp = torch.empty_like(im["p_l"]) if im.get("need_p", True) else None
+        dIl = torch.empty_like(im["I_l"]) if im.get("need_Il", True) else None
+        dIh = torch.empty_like(im["I_h"]) if im.get("need_Ih", True) else None
         outs.append((dp, dIl, dIh))
         C, h, w = im["I_h"].shape
         h_l, w_l = im["p_l"].shape[1:]
         arr[i] = L.dgf_image_grad(R.data_ptr(), im["p_l"].data_ptr(), im["I_l"].data_ptr(), im["I_h"].data_ptr(),
-                                  dp.data_ptr(), dIl.data_ptr(), dIh.data_ptr(), C, h_l, w_l, h, w, int(im["r"]),
+                                  *(None if t is None else t.data_ptr() for t in (dp, dIl, dIh)),
+                                  C, h_l, w_l, h, w, int(im["r"]),
                                   float(im["eps"]))
     nb = L.dgf_workspace_size_batched_backward(arr, n, dt)
     if nb == 0:
