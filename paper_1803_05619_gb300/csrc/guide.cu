@@ -264,9 +264,11 @@ __global__ void __launch_bounds__(kThreads) k3_hires_bwd_guided(const T* __restr
 }
 
 // ------------------------------------------------------------------- K6
-// Persistent over high-res tiles (TH rows x 32*VEC columns of one image);
-// each CTA keeps its weight-gradient sums in registers and writes one
-// partial row; a second kernel adds the partials in a fixed order.
+// Persistent over high-res tiles (TH rows x 32*VEC columns of one image), one
+// CTA per SM (the 99 weight-gradient sums live in registers); each warp
+// walks its rows of a tile with the next row's packed inputs already in
+// flight.  Each CTA writes one partial row of the sums; a second kernel adds
+// the partials in a fixed order.
 // LOW: whether d G_l / f^2 joins d G_h (the block-mean form of the low-res
 // guide); without it (G_l = F(I_l)) K6L takes d G_l instead.
 template <typename T, int VEC, int F, bool LOW>
@@ -294,10 +296,9 @@ __global__ void __launch_bounds__(kThreads, 1) k6_guide_bwd(const float2* __rest
     gb2[0] = gb2[1] = gb2[2] = 0.f;
     const f32x2* W1p = c_wh;
     const f32x2* W2p = c_wh + kHP * 3;
-    int cc[VEC];
-    float ll[VEC];
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) col_tap<F>(lane * VEC + k, cc[k], ll[k]);
+    static_assert(VEC % F == 0, "a lane's pixels cover whole low-res cells");
+    constexpr int KC = VEC / F;  // low-res cells per lane
+    using VT = Vec<T, VEC>;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int n = tile / (tiles_x * tiles_y);
         const int tl = tile - n * tiles_x * tiles_y;
@@ -323,62 +324,91 @@ __global__ void __launch_bounds__(kThreads, 1) k6_guide_bwd(const float2* __rest
         __syncthreads();
         const int xs = X0 + lane * VEC;
         if (xs >= w) continue;
+        // rows of this warp: i = warp, warp + kWarps, ...; each row's packed
+        // input vectors are loaded one row ahead
+        const T* xb = I_h + (size_t)n * 3 * hw + xs;
+        const T* rb = R + (size_t)n * 3 * hw + xs;
+        VT xv[3], rv[3];
+        if (warp < TH && Y0 + warp < h) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xv[c] = ldg_vec<T, VEC>(xb + c * hw + (size_t)(Y0 + warp) * w);
+                rv[c] = ldg_vec<T, VEC>(rb + c * hw + (size_t)(Y0 + warp) * w);
+            }
+        }
         for (int i = warp; i < TH; i += kWarps) {
             const int y = Y0 + i;
             if (y >= h) break;
-            float x[3][VEC], r[3][VEC], o[3][VEC];
+            const int yn = y + kWarps;
+            VT xn[3], rn[3];
+            if (i + kWarps < TH && yn < h) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                load_vec<T, VEC>(I_h + ((size_t)n * 3 + c) * hw + (size_t)y * w + xs, x[c]);
-                load_vec<T, VEC>(R + ((size_t)n * 3 + c) * hw + (size_t)y * w + xs, r[c]);
+                for (int c = 0; c < 3; ++c) {
+                    xn[c] = ldg_vec<T, VEC>(xb + c * hw + (size_t)yn * w);
+                    rn[c] = ldg_vec<T, VEC>(rb + c * hw + (size_t)yn * w);
+                }
             }
             const int yl = y / F;
+            float dl[3][KC];  // d G_l of the lane's low-res cells on row yl
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int kc = 0; kc < KC; ++kc)
+                    dl[c][kc] = LOW ? dG_l[((size_t)n * 3 + c) * lw + (size_t)yl * w_l + xs / F + kc] : 0.f;
+            VT ov[3];
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
-                const int xl = (xs + k) / F;
-                float dg[3];
+                // bilinear tap along x of pixel lane * VEC + k of the tile
+                const int q = k % F, t2 = 2 * q + 1 - F;
+                const int c0 = lane * KC + k / F + (t2 >= 0 ? 1 : 0);
+                const float lamx = (float)(t2 < 0 ? t2 + 2 * F : t2) / (float)(2 * F);
+                float dg[3], xk[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const float* row = sA + (c * TH + i) * pitch;
-                    const float A = lerp(row[cc[k]], row[cc[k] + 1], ll[k]);
-                    float dl = 0.f;
-                    if constexpr (LOW) dl = dG_l[((size_t)n * 3 + c) * lw + (size_t)yl * w_l + xl];
-                    dg[c] = fmaf(r[c][k], A, dl * inv_ff);
+                    const float A = lerp(row[c0], row[c0 + 1], lamx);
+                    xk[c] = to_f32<T>(xv[c].v[k]);
+                    dg[c] = fmaf(to_f32<T>(rv[c].v[k]), A, dl[c][k / F] * inv_ff);
                     gb2[c] += dg[c];
                 }
                 // two hidden units per paired instruction: z, the leaky ReLU
                 // factor m (1 or slope: h = z m and d z = d h m), d h = W2^T d G,
                 // the two weight-gradient outer products and d I = W1^T d z
-                const f32x2 xs0 = f2_splat(x[0][k]), xs1 = f2_splat(x[1][k]), xs2 = f2_splat(x[2][k]);
+                const f32x2 xs0 = f2_splat(xk[0]), xs1 = f2_splat(xk[1]), xs2 = f2_splat(xk[2]);
                 const f32x2 d0 = f2_splat(dg[0]), d1 = f2_splat(dg[1]), d2 = f2_splat(dg[2]);
                 f32x2 dx0 = f2_splat(0.f), dx1 = f2_splat(0.f), dx2 = f2_splat(0.f);
 #pragma unroll
-                for (int q = 0; q < kHP; ++q) {
-                    const f32x2 z = f2x_fma(W1p[q * 3 + 2], xs2, f2x_fma(W1p[q * 3 + 1], xs1, f2x_mul(W1p[q * 3 + 0], xs0)));
+                for (int q2 = 0; q2 < kHP; ++q2) {
+                    const f32x2 z = f2x_fma(W1p[q2 * 3 + 2], xs2, f2x_fma(W1p[q2 * 3 + 1], xs1, f2x_mul(W1p[q2 * 3 + 0], xs0)));
                     float za, zb;
                     f2_unpack(z, za, zb);
                     const f32x2 m = f2_pack(za > 0.f ? 1.f : slope, zb > 0.f ? 1.f : slope);
                     const f32x2 hk = f2x_mul(z, m);
-                    const f32x2 dh = f2x_fma(W2p[2 * kHP + q], d2, f2x_fma(W2p[kHP + q], d1, f2x_mul(W2p[q], d0)));
+                    const f32x2 dh = f2x_fma(W2p[2 * kHP + q2], d2, f2x_fma(W2p[kHP + q2], d1, f2x_mul(W2p[q2], d0)));
                     const f32x2 dz = f2x_mul(dh, m);
-                    gw2[0 * kHP + q] = f2x_fma(d0, hk, gw2[0 * kHP + q]);
-                    gw2[1 * kHP + q] = f2x_fma(d1, hk, gw2[1 * kHP + q]);
-                    gw2[2 * kHP + q] = f2x_fma(d2, hk, gw2[2 * kHP + q]);
-                    gw1[q * 3 + 0] = f2x_fma(dz, xs0, gw1[q * 3 + 0]);
-                    gw1[q * 3 + 1] = f2x_fma(dz, xs1, gw1[q * 3 + 1]);
-                    gw1[q * 3 + 2] = f2x_fma(dz, xs2, gw1[q * 3 + 2]);
-                    dx0 = f2x_fma(W1p[q * 3 + 0], dz, dx0);
-                    dx1 = f2x_fma(W1p[q * 3 + 1], dz, dx1);
-                    dx2 = f2x_fma(W1p[q * 3 + 2], dz, dx2);
+                    gw2[0 * kHP + q2] = f2x_fma(d0, hk, gw2[0 * kHP + q2]);
+                    gw2[1 * kHP + q2] = f2x_fma(d1, hk, gw2[1 * kHP + q2]);
+                    gw2[2 * kHP + q2] = f2x_fma(d2, hk, gw2[2 * kHP + q2]);
+                    gw1[q2 * 3 + 0] = f2x_fma(dz, xs0, gw1[q2 * 3 + 0]);
+                    gw1[q2 * 3 + 1] = f2x_fma(dz, xs1, gw1[q2 * 3 + 1]);
+                    gw1[q2 * 3 + 2] = f2x_fma(dz, xs2, gw1[q2 * 3 + 2]);
+                    dx0 = f2x_fma(W1p[q2 * 3 + 0], dz, dx0);
+                    dx1 = f2x_fma(W1p[q2 * 3 + 1], dz, dx1);
+                    dx2 = f2x_fma(W1p[q2 * 3 + 2], dz, dx2);
                 }
-                o[0][k] = f2_lo(dx0) + f2_hi(dx0);  // even and odd hidden units
-                o[1][k] = f2_lo(dx1) + f2_hi(dx1);
-                o[2][k] = f2_lo(dx2) + f2_hi(dx2);
+                ov[0].v[k] = from_f32<T>(f2_lo(dx0) + f2_hi(dx0));  // even and odd hidden units
+                ov[1].v[k] = from_f32<T>(f2_lo(dx1) + f2_hi(dx1));
+                ov[2].v[k] = from_f32<T>(f2_lo(dx2) + f2_hi(dx2));
             }
             if (dI_h != nullptr) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    store_vec<T, VEC>(dI_h + ((size_t)n * 3 + c) * hw + (size_t)y * w + xs, o[c]);
+                    *reinterpret_cast<VT*>(dI_h + ((size_t)n * 3 + c) * hw + (size_t)y * w + xs) = ov[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xv[c] = xn[c];
+                rv[c] = rn[c];
             }
         }
     }
@@ -646,13 +676,13 @@ static int sm_count() {
 
 int k6_blocks(int N, int h, int w) {
     (void)N; (void)h; (void)w;
-    return std::min(2 * sm_count(), kMaxK6Blocks);
+    return std::min(sm_count(), kMaxK6Blocks);  // one CTA per SM (its registers allow no second)
 }
 
 template <typename T, int VEC, int F>
 static cudaError_t k6_go(const float2* coef, const float* dG_l, const void* R, const void* I_h, void* dI_h,
                          float* partials, int N, int h_l, int w_l, int h, int w, float slope, cudaStream_t s) {
-    const int TH = 8;
+    const int TH = 32;
     const size_t smem = (size_t)3 * TH * (32 * VEC / F + 2) * sizeof(float);
     auto kern = dG_l != nullptr ? k6_guide_bwd<T, VEC, F, true> : k6_guide_bwd<T, VEC, F, false>;
     cudaError_t e = prep(kern, smem);
