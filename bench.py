@@ -142,6 +142,24 @@ class Step:
         self.backward()
 
 
+def step_graph(g, spec, device):
+    """One forward+backward step (a Step of its own, on a side stream)
+    captured in a CUDA graph; replay() runs it on the current stream."""
+    import torch
+    cap = torch.cuda.Stream(device)
+    torch.cuda.synchronize(device)
+    with torch.cuda.stream(cap):
+        gstep = Step(g, spec, device)
+        gstep()  # shapes already tuned by the eager calls: this call tunes nothing
+    torch.cuda.synchronize(device)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        gstep()
+    torch.cuda.synchronize(device)
+    graph.keep = gstep  # its outputs and workspace must outlive the graph
+    return graph
+
+
 class BatchedStep:
     """Pre-marshalled dgf_forward_batched + dgf_backward_batched over a list of
     images (dicts of C x h x w tensors with r, eps) and their upstream
@@ -748,10 +766,16 @@ def main():
     n0 = L.dgf_launch_count()
     step()
     per_step = L.dgf_launch_count() - n0
+    # eager calls first (these also tune the shapes), then the same step
+    # captured once in a CUDA graph and replayed: the timed figure, as a
+    # training loop that captures its step runs it (the kernels and their
+    # launch order are those of the eager calls; only host launch gaps go)
+    ms_eager = time_loop(step, args.steps, args.warmup, ws, device)
+    graph = step_graph(g, spec, device)
     with ClockSampler(local) as clk:
-        ms = time_loop(step, args.steps, args.warmup, ws, device, clock=clk)
+        ms = time_loop(graph.replay, args.steps, args.warmup, ws, device, clock=clk)
         if clk.proc is not None and clk.samples_in_window() < 10:
-            clk.extend(step)
+            clk.extend(graph.replay)
     launches = per_step * args.steps
     value = job_value(pix, ws, ms)
     fwd_ms = time_loop(step.forward, max(10, args.steps // 2), args.warmup, ws, device)
@@ -760,8 +784,12 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": spec["dtype"], "data": DATA,
         "config": workload_config(main_name, ws),
+        "timed": "one forward+backward step (dgf_forward + dgf_backward) captured in a CUDA graph, replayed "
+                 "per step",
+        "eager": {"value": round(job_value(pix, ws, ms_eager), 2), "unit": "Mpix/s",
+                  "ms_per_step": round(ms_eager, 5), "path": "the same calls issued from the host every step"},
         "fwd": {"value": round(ws * pix / (fwd_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
-                "ms_per_step": round(fwd_ms, 5)},
+                "ms_per_step": round(fwd_ms, 5), "path": "eager dgf_forward"},
         "gpu_launches": int(launches),
         "autotuned_shapes": L.dgf_autotune_entries(),
         "clocks": clk.summary(),
@@ -813,6 +841,8 @@ def bench_bf16_4k(args, device):
     pix = N * h * w
     steps = max(20, min(args.steps, 1000))
     ms = time_loop(step, steps, args.warmup, 1, device)
+    graph = step_graph(g, spec, device)
+    ms_graph = time_loop(graph.replay, steps, args.warmup, 1, device)
     fwd_ms = time_loop(step.forward, steps, args.warmup, 1, device)
     images = [{"p_l": g["p_l"][i], "I_l": g["I_l"][i], "I_h": g["I_h"][i], "r": spec["r"],
                "eps": spec["eps"]} for i in range(N)]
@@ -834,6 +864,10 @@ def bench_bf16_4k(args, device):
                 "target_frac_of_nominal_8TBs": 0.70},
             "ms_fwd_bwd": round(ms, 5), "fwd_bwd_frac_of_nominal_8TBs": round(
                 fb_bytes / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4),
+            "graph_fwd_bwd": {"path": "the single-call step captured in a CUDA graph and replayed",
+                              "mpix_s": round(pix / (ms_graph * 1e-3) / 1e6, 2), "ms": round(ms_graph, 5),
+                              "frac_of_nominal_8TBs": round(fb_bytes / (ms_graph * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4),
+                              "frac_of_measured_hbm": round(fb_bytes / (ms_graph * 1e-3) / 1e9 / peak, 4)},
             "fwd_bwd_algorithmic_bytes": fb_bytes, "roofline": rl}
 
 
@@ -871,8 +905,9 @@ def bench_batched_64(args, device):
 
 
 def bench_small(args, device):
-    """The smallest configuration (1 x 1 x 64^2 -> 256^2, FP32, r = 1): bound by
-    launch latency, so reported as microseconds per call and Mpix/s."""
+    """The smallest configuration (1 x 1 x 64^2 -> 256^2, FP32, r = 1): a few
+    CTAs per kernel, bound by latency, so reported as microseconds per call
+    (eager and graph-replayed) and Mpix/s."""
     name = "fp32_small_1x1x256"
     spec = WORKLOADS[name]
     import torch
@@ -894,8 +929,9 @@ def bench_small(args, device):
     return {"workload": name, "us_fwd": round(ms_f * 1e3, 2), "us_fwd_bwd": round(ms_fb * 1e3, 2),
             "fwd_mpix_s": round(pix / (ms_f * 1e-3) / 1e6, 1), "fwd_bwd_mpix_s": round(pix / (ms_fb * 1e-3) / 1e6, 1),
             "us_fwd_bwd_graph": round(ms_g * 1e3, 2), "fwd_bwd_graph_mpix_s": round(pix / (ms_g * 1e-3) / 1e6, 1),
-            "bound": "launch latency (one kernel forward, two backward at r = 1; eager calls pay the host "
-                     "launch cost)"}
+            "bound": "latency of the kernels' row walks: one plane of 64 x 64 low-res pixels gives each kernel "
+                     "a grid of a few CTAs (far under one wave), so device time is a walk's serial latency, "
+                     "and eager calls add the host launch cost on top (the graph-replayed figure has none)"}
 
 
 def bench_paper_literal(args, device):
