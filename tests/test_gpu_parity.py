@@ -4,6 +4,8 @@ Sizes span several tiles of every kernel and end in ragged tails; the
 cases cover integer factors 2, 4, 8, non-integer ratios, odd widths (scalar
 path), r from 0 to 16, FP32/BF16/FP16 storage.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -284,6 +286,60 @@ def test_deterministic():
     assert torch.equal(o1, o2)
     for x, y in zip(a[:3], b[:3]):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("dtype,r,f", [(F32, 1, 4), (BF16, 2, 4), (F16, 4, 8)], ids=["f32-r1", "bf16-r2", "f16-r4"])
+def test_graph_captured_step_matches_eager(dtype, r, f):
+    """A forward + backward step captured in a CUDA graph (as bench.py times
+    it) and replayed gives the eager calls' bits, replay after replay, also
+    after the inputs change in place."""
+    st = to_storage(make_case("photo", 40 + r, 2, 3, 48, 64, 48 * f, 64 * f), dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    R = synth.upstream_grad(41, st["I_h"].shape).to(dtype).cuda()
+    outs = {"O": torch.empty_like(g["I_h"]), "dp": torch.empty_like(g["p_l"]),
+            "dIl": torch.empty_like(g["I_l"]), "dIh": torch.empty_like(g["I_h"])}
+    N, C, h_l, w_l = g["p_l"].shape
+    h, w = g["I_h"].shape[2:]
+    dt = {F32: L.DGF_F32, BF16: L.DGF_BF16, F16: L.DGF_F16}[dtype]
+    lib = L.lib()
+    nb = L.dgf_workspace_size(N, C, h_l, w_l, h, w, r, dt, None)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    cap = torch.cuda.Stream()
+
+    def step():
+        s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        L.check(lib.dgf_forward(P(g["p_l"]), P(g["I_l"]), P(g["I_h"]), P(outs["O"]), N, C, h_l, w_l, h, w, r,
+                                ctypes.c_float(1e-3), dt, None, P(ws), ws.numel(), s))
+        L.check(lib.dgf_backward(P(R), P(g["p_l"]), P(g["I_l"]), P(g["I_h"]), P(outs["dp"]), P(outs["dIl"]),
+                                 P(outs["dIh"]), None, N, C, h_l, w_l, h, w, r, ctypes.c_float(1e-3), dt, None,
+                                 P(ws), ws.numel(), s))
+
+    with torch.cuda.stream(cap):
+        step()
+    torch.cuda.synchronize()
+    eager = {k: v.clone() for k, v in outs.items()}
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        step()
+    for v in outs.values():
+        v.zero_()
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        for k in outs:
+            assert torch.equal(outs[k], eager[k]), k
+    # new input values in the same buffers: the replay computes them
+    g["p_l"].copy_(g["p_l"].flip(-1))
+    with torch.cuda.stream(cap):
+        step()
+    torch.cuda.synchronize()
+    eager2 = {k: v.clone() for k, v in outs.items()}
+    graph.replay()
+    torch.cuda.synchronize()
+    for k in outs:
+        assert torch.equal(outs[k], eager2[k]), k
+    assert not torch.equal(eager2["O"], eager["O"])
 
 
 def test_guard_regions_untouched():
