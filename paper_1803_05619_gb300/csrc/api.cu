@@ -1117,6 +1117,9 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
     cudaError_t e;
     const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab && !gf;
     if (gf) {
+        // K1 over the FP32 grey guide: its own tuning key (guide_f32 = 1)
+        if (tune_enabled() && !stream_capturing(s) && mean_ab)
+            tune_k1(dt, true, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
         e = run_k1(L, dt, true, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
         if (e != cudaSuccess) return cuda_fail(e, "k1");
         e = L.run("k2_hires_apply", [&] {
@@ -1197,6 +1200,9 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
     else
         e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
     if (e != cudaSuccess) return cuda_fail(e, "k5");
+    // K1 over the FP32 low-res guide: its own tuning key (guide_f32 = 1)
+    if (tune_enabled() && !stream_capturing(s) && mean_ab)
+        tune_k1(dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
     e = run_k1(L, dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
     if (e != cudaSuccess) return cuda_fail(e, "k1");
     e = L.run("k2_hires_apply_guided", [&] {
@@ -1221,7 +1227,7 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
     // both low-res stages in strip form the K1 pass also keeps each
     // window's statistics for K4, which then skips recomputing them
     const bool need_k4 = dp_l != nullptr || dI_l != nullptr;
-    if (tuning && (dI_h != nullptr || need_k4)) tune_k1(dt, false, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
+    if (tuning && (dI_h != nullptr || need_k4)) tune_k1(dt, gf, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
     // K4's form decides whether the K1 pass saves statistics, so it is tuned
     // before that pass, on whatever the workspace holds (timing only; the
     // real K4 launch below overwrites its outputs): the first call of a key
@@ -1400,7 +1406,7 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
         p.k13_ok = p.k13 = false;
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
         return backward_plain(L, dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws,
-                              lay, s, false, true);
+                              lay, s, tune_enabled() && !stream_capturing(s) && mean_ab, true);
     }
     if (g == nullptr) {
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
@@ -1430,6 +1436,8 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
     else
         e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
     if (e != cudaSuccess) return cuda_fail(e, "k5");
+    const bool gtune = tune_enabled() && !stream_capturing(s) && mean_ab;
+    if (gtune) tune_k1(dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
     e = run_k1(L, dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
     if (e != cudaSuccess) return cuda_fail(e, "k1");
     e = L.run("k3_hires_bwd_guided", [&] {
@@ -1438,6 +1446,8 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
     if (e != cudaSuccess) return cuda_fail(e, "k3g");
     const bool want_dgl = guide_low ? need_lo : need_hi;
     if (dp_l != nullptr || want_dgl) {
+        // timing only: the K4 launch below overwrites what the candidates wrote
+        if (gtune) tune_k4(dt, true, G_l, p_l, dcoef, dp_l, want_dgl ? dG_l : nullptr, planes, h_l, w_l, r, eps, s, p);
         e = L.run("k4_lowres_bwd", [&] {
             return run_k4(dt, true, G_l, p_l, dcoef, dp_l, want_dgl ? dG_l : nullptr, planes, h_l, w_l, r, eps,
                           p.k4, s);
