@@ -102,9 +102,11 @@ typedef struct {
 
 /*
  * Bytes of workspace that dgf_forward and dgf_backward need for these sizes
- * (the larger of the two; FP32 Abar/bbar, their gradients, the low-res
- * guide when g != NULL, and weight-gradient partials).  Returns 0 for
- * invalid sizes.  Pure host function.
+ * (the larger of the two; FP32 Abar/bbar, their gradients, the window
+ * statistics; when g != NULL also the low-res guide, weight-gradient
+ * partials and F(I_h) in FP32, N x 3 x h x w, which the forward computes
+ * once for the block mean and reads back for Eq. 2).  Returns 0 for invalid
+ * sizes.  Pure host function.
  */
 size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r,
                           dgf_dtype dt, const dgf_guide* g);

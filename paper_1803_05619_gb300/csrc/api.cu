@@ -191,10 +191,12 @@ static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr int kMaxRadius = 16;
 
 struct Layout {
-    size_t coef, dcoef, stats, gl, dgl, partials, total;
+    size_t coef, dcoef, stats, gl, dgl, partials, gh, total;
 };
 
-static Layout layout(int N, int C, int h_l, int w_l, bool guided) {
+// hi: high-res pixel-channels (N C h w): with the guidance transform the
+// forward keeps F(I_h) there in FP32 (K5 writes it, K2 reads it).
+static Layout layout(int N, int C, int h_l, int w_l, bool guided, size_t hi = 0) {
     const size_t lo = (size_t)N * C * h_l * w_l;
     Layout L{};
     size_t off = 0;
@@ -211,6 +213,8 @@ static Layout layout(int N, int C, int h_l, int w_l, bool guided) {
         off += align256(lo * sizeof(float));
         L.partials = off;
         off += align256((size_t)kMaxK6Blocks * kWGradPadded * sizeof(float));
+        L.gh = off;
+        off += align256(hi * sizeof(float));
     }
     L.total = off;
     return L;
@@ -1128,7 +1132,7 @@ extern "C" {
 
 size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt, const dgf_guide* g) {
     if (check_sizes(N, C, h_l, w_l, h, w, r, 1.f, dt) != DGF_OK) return 0;
-    return layout(N, C, h_l, w_l, g != nullptr).total;
+    return layout(N, C, h_l, w_l, g != nullptr, (size_t)N * C * h * w).total;
 }
 
 static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
@@ -1142,7 +1146,7 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
     if (N == 0) return DGF_OK;
     if (p_l == nullptr || I_h == nullptr || O_h == nullptr || ((g == nullptr || guide_low) && I_l == nullptr))
         return fail(DGF_ERR_INVALID, "NULL input or output pointer");
-    const Layout lay = layout(N, C, h_l, w_l, g != nullptr);
+    const Layout lay = layout(N, C, h_l, w_l, g != nullptr, (size_t)N * C * h * w);
     if ((st = check_ws(workspace, ws_bytes, lay.total)) != DGF_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
@@ -1231,19 +1235,30 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
         return DGF_OK;
     }
     float* G_l = reinterpret_cast<float*>(ws + lay.gl);
+    // with G_l the block mean of F(I_h), K5 also keeps F(I_h) in FP32 and K2
+    // reads that guide instead of evaluating F again per pixel
+    float* G_h = guide_low ? nullptr : reinterpret_cast<float*>(ws + lay.gh);
     if (!aligned16({I_h, O_h})) return fail(DGF_ERR_UNSUPPORTED, "guidance transform needs 16-byte aligned I_h, O_h");
     e = guide_upload(g->w1, g->w2, g->b2, g->hidden, s);
     if (e != cudaSuccess) return cuda_fail(e, "guide weights");
     if (guide_low)
         e = L.run("k5_guide_low", [&] { return launch_k5_low(dt, I_l, G_l, N, h_l, w_l, g->slope, s); });
     else
-        e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
+        e = L.run("k5_guide_down",
+                  [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s, G_h); });
     if (e != cudaSuccess) return cuda_fail(e, "k5");
     // K1 over the FP32 low-res guide: its own tuning key (guide_f32 = 1)
     if (tune_enabled() && !stream_capturing(s) && mean_ab)
         tune_k1(dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
     e = run_k1(L, dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
     if (e != cudaSuccess) return cuda_fail(e, "k1");
+    if (G_h != nullptr) {
+        e = L.run("k2_hires_apply", [&] {
+            return launch_k2_guide_f32(dt, coef, G_h, O_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k2");
+        return DGF_OK;
+    }
     e = L.run("k2_hires_apply_guided", [&] {
         return launch_k2_guided(dt, coef, I_h, O_h, N, h_l, w_l, h, w, p.F, 8, g->slope, s);
     });
@@ -1427,7 +1442,7 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
     }
     if (dO_h == nullptr || p_l == nullptr || I_h == nullptr || ((g == nullptr || guide_low) && I_l == nullptr))
         return fail(DGF_ERR_INVALID, "NULL input pointer");
-    const Layout lay = layout(N, C, h_l, w_l, g != nullptr);
+    const Layout lay = layout(N, C, h_l, w_l, g != nullptr, (size_t)N * C * h * w);
     if ((st = check_ws(workspace, ws_bytes, lay.total)) != DGF_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
@@ -1674,7 +1689,7 @@ size_t dgf_workspace_size_opt(int N, int C, int h_l, int w_l, int h, int w, int 
                               const dgf_options* opt) {
     if (check_sizes(N, C, h_l, w_l, h, w, r, 1.f, dt) != DGF_OK) return 0;
     const int n_in = grey_channels(opt, C);
-    if (n_in == 0) return layout(N, C, h_l, w_l, g != nullptr).total;
+    if (n_in == 0) return layout(N, C, h_l, w_l, g != nullptr, (size_t)N * C * h * w).total;
     if (check_grey(n_in, N, g) != DGF_OK) return 0;
     return grey_layout(N, C, h_l, w_l, h, w, dt).total;
 }

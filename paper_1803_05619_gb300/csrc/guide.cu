@@ -151,6 +151,61 @@ __global__ void __launch_bounds__(kThreads) k5_guide_down(const T* __restrict__ 
     for (int c = 0; c < 3; ++c) G_l[(n * 3 + c) * lw + (size_t)i * w_l + j] = acc[c] / inv;
 }
 
+// K5 that also keeps F(I_h) (FP32) in G_h, for an even factor FF known at
+// compile time: a thread's FF pixels of a row arrive as one vector load per
+// channel, are evaluated in pairs and summed in the order of k5_guide_down
+// (so G_l has its bits), and each channel's FF values leave as one vector
+// store (I_h 16-byte aligned and w = FF w_l keep every vector aligned).
+template <typename T, int FF>
+__global__ void __launch_bounds__(kThreads) k5_guide_down_keep(const T* __restrict__ I_h, float* __restrict__ G_l,
+                                                               int h_l, int w_l, int h, int w, float slope,
+                                                               float* __restrict__ G_h) {
+    static_assert(FF % 2 == 0, "pixel pairs");
+    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int i = blockIdx.y;
+    const size_t n = blockIdx.z;
+    if (j >= w_l) return;
+    const size_t hw = (size_t)h * w;
+    const T* base = I_h + n * 3 * hw;
+    float* gbase = G_h + n * 3 * hw;
+    float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int dy = 0; dy < FF; ++dy) {
+        const size_t row = (size_t)(FF * i + dy) * w + (size_t)FF * j;
+        Vec<T, FF> in[3];  // the row's FF pixels of each channel, one vector load each
+#pragma unroll
+        for (int c = 0; c < 3; ++c) in[c] = *reinterpret_cast<const Vec<T, FF>*>(base + c * hw + row);
+        float gv[3][FF];
+#pragma unroll
+        for (int dx = 0; dx < FF; dx += 2) {
+            float xa[3], xb[3], ga[3], gb[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xa[c] = to_f32<T>(in[c].v[dx]);
+                xb[c] = to_f32<T>(in[c].v[dx + 1]);
+            }
+            guide_eval2(xa, xb, slope, ga, gb);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[c] += ga[c] + gb[c];
+                gv[c][dx] = ga[c];
+                gv[c][dx + 1] = gb[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Vec<float, FF> v;
+#pragma unroll
+            for (int k = 0; k < FF; ++k) v.v[k] = gv[c][k];
+            *reinterpret_cast<Vec<float, FF>*>(gbase + c * hw + row) = v;
+        }
+    }
+    const float inv = (float)(FF * FF);
+    const size_t lw = (size_t)h_l * w_l;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) G_l[(n * 3 + c) * lw + (size_t)i * w_l + j] = acc[c] / inv;
+}
+
 // ------------------------------------------------------------------ K2g
 template <typename T, int VEC, int F>
 __global__ void __launch_bounds__(kThreads) k2_apply_guided(const float2* __restrict__ coef,
@@ -569,19 +624,26 @@ cudaError_t guide_upload(const float* w1, const float* w2, const float* b2, int 
 
 template <typename T>
 static cudaError_t k5_go(const void* I_h, float* G_l, int N, int h_l, int w_l, int h, int w, int F,
-                         float slope, cudaStream_t s) {
+                         float slope, float* G_h, cudaStream_t s) {
     dim3 grid((w_l + kThreads - 1) / kThreads, h_l, N);
-    k5_guide_down<T><<<grid, kThreads, 0, s>>>(static_cast<const T*>(I_h), G_l, h_l, w_l, h, w, F, slope);
+    const T* in = static_cast<const T*>(I_h);
+    if (G_h != nullptr && F == 2) k5_guide_down_keep<T, 2><<<grid, kThreads, 0, s>>>(in, G_l, h_l, w_l, h, w, slope, G_h);
+    else if (G_h != nullptr && F == 4) k5_guide_down_keep<T, 4><<<grid, kThreads, 0, s>>>(in, G_l, h_l, w_l, h, w, slope, G_h);
+    else if (G_h != nullptr && F == 8) k5_guide_down_keep<T, 8><<<grid, kThreads, 0, s>>>(in, G_l, h_l, w_l, h, w, slope, G_h);
+    else k5_guide_down<T><<<grid, kThreads, 0, s>>>(in, G_l, h_l, w_l, h, w, F, slope);
     return cudaGetLastError();
 }
 
 cudaError_t launch_k5(dgf_dtype dt, const void* I_h, float* G_l, int N, int h_l, int w_l, int h, int w,
-                      int F, float slope, cudaStream_t s) {
+                      int F, float slope, cudaStream_t s, float* G_h) {
     if (N == 0) return cudaSuccess;
+    // the vector writes of G_h need a factor of 2, 4 or 8 (w = F w_l keeps every
+    // thread's FF floats aligned to FF floats)
+    if (G_h != nullptr && F != 2 && F != 4 && F != 8) return cudaErrorInvalidValue;
     switch (dt) {
-        case DGF_F32: return k5_go<float>(I_h, G_l, N, h_l, w_l, h, w, F, slope, s);
-        case DGF_BF16: return k5_go<__nv_bfloat16>(I_h, G_l, N, h_l, w_l, h, w, F, slope, s);
-        case DGF_F16: return k5_go<__half>(I_h, G_l, N, h_l, w_l, h, w, F, slope, s);
+        case DGF_F32: return k5_go<float>(I_h, G_l, N, h_l, w_l, h, w, F, slope, G_h, s);
+        case DGF_BF16: return k5_go<__nv_bfloat16>(I_h, G_l, N, h_l, w_l, h, w, F, slope, G_h, s);
+        case DGF_F16: return k5_go<__half>(I_h, G_l, N, h_l, w_l, h, w, F, slope, G_h, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -131,8 +131,9 @@ constexpr int kMaxK6Blocks = 1024;   // rows of weight-gradient partials
 constexpr int kWGradPadded = 99;     // padded [dw1 16x3 | dw2 3x16 | db2 3]
 cudaError_t guide_upload(const float* w1, const float* w2, const float* b2, int hidden, cudaStream_t s);
 bool guided_supported(dgf_dtype dt, int w, int F);
+// G_h (or null): F(I_h) of every high-res pixel, FP32, also written there
 cudaError_t launch_k5(dgf_dtype dt, const void* I_h, float* G_l, int N, int h_l, int w_l, int h, int w,
-                      int F, float slope, cudaStream_t s);
+                      int F, float slope, cudaStream_t s, float* G_h = nullptr);
 cudaError_t launch_k2_guided(dgf_dtype dt, const float2* coef, const void* I_h, void* O_h, int N,
                              int h_l, int w_l, int h, int w, int F, int TH, float slope, cudaStream_t s);
 cudaError_t launch_k3_guided(dgf_dtype dt, const void* R, const void* I_h, float2* dcoef, int N,
