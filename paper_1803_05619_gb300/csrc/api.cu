@@ -930,45 +930,6 @@ std::mutex g_batch_mu;
 // key: device, dtype, K1 classes (radius, form, lane width), K2 classes (staging, vector width, factor)
 std::map<std::tuple<int, int, std::vector<int>, std::vector<int>>, BatchGraph> g_batch;
 
-// Host-to-device copy of a batched call's tensor maps through pinned staging
-// buffers (a ring of four per device, each reused only after the copy made
-// from it four calls earlier has completed), so the copy is asynchronous:
-// a copy from pageable memory would make the host wait for the stream.
-static std::mutex g_stage_mu;
-struct StageRing {
-    void* buf[4] = {nullptr, nullptr, nullptr, nullptr};
-    size_t cap[4] = {0, 0, 0, 0};
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    bool used[4] = {false, false, false, false};
-    int next = 0;
-};
-static StageRing g_stage[64];
-
-static cudaError_t copy_staged(void* dst, const void* src, size_t bytes, cudaStream_t s) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_stage_mu);
-    StageRing& r = g_stage[dev];
-    const int k = r.next;
-    r.next = (k + 1) % 4;
-    cudaError_t e;
-    if (r.ev[k] == nullptr && (e = cudaEventCreateWithFlags(&r.ev[k], cudaEventDisableTiming)) != cudaSuccess) return e;
-    if (r.used[k] && (e = cudaEventSynchronize(r.ev[k])) != cudaSuccess) return e;  // its last copy is done
-    if (r.cap[k] < bytes) {
-        if (r.buf[k] != nullptr) cudaFreeHost(r.buf[k]);
-        r.buf[k] = nullptr;
-        r.cap[k] = 0;
-        const size_t cap = std::max(bytes, (size_t)DGF_MAX_BATCH * 256);
-        if ((e = cudaHostAlloc(&r.buf[k], cap, cudaHostAllocPortable)) != cudaSuccess) return e;
-        r.cap[k] = cap;
-    }
-    memcpy(r.buf[k], src, bytes);
-    if ((e = cudaMemcpyAsync(dst, r.buf[k], bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
-    r.used[k] = true;
-    return cudaEventRecord(r.ev[k], s);
-}
-
 struct BatchPrep {
     BatchParams bp;
     size_t smem1 = 0, smem2 = 0;
@@ -1889,7 +1850,9 @@ extern "C" dgf_status dgf_forward_batched(const dgf_image* imgs, int n, dgf_dtyp
             if ((e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.n2[q], &p2[q])) != cudaSuccess)
                 return cuda_fail(e, "graph update k2");
     }
-    if (any_map && (e = copy_staged(maps_dev, k2maps.data(), (size_t)n * sizeof(K2Map), s)) != cudaSuccess)
+    if (any_map &&
+        (e = cudaMemcpyAsync(maps_dev, k2maps.data(), (size_t)n * sizeof(K2Map), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
         return cuda_fail(e, "k2 maps");
     Launcher L(s);
     e = L.run("batched_graph(k1,k2)", [&] {
@@ -2282,7 +2245,9 @@ static dgf_status backward_batched_graph(const dgf_image_grad* imgs, int n, dgf_
     }
     bool any_map = false;
     for (int i = 0; i < n; ++i) any_map = any_map || it[i].tma;
-    if (any_map && (e = copy_staged(maps_dev, maps.data(), (size_t)n * sizeof(K3Maps), s)) != cudaSuccess)
+    if (any_map &&
+        (e = cudaMemcpyAsync(maps_dev, maps.data(), (size_t)n * sizeof(K3Maps), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
         return cuda_fail(e, "k3 maps");
     Launcher L(s);
     e = L.run("batched_bwd_graph(k1,k3,k4)", [&] {
@@ -2466,17 +2431,6 @@ extern "C" void dgf_shutdown(void) {
             if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
         }
         g_bwdg.clear();
-    }
-    {
-        std::lock_guard<std::mutex> lk(g_stage_mu);
-        for (StageRing& r : g_stage) {
-            for (int k = 0; k < 4; ++k) {
-                if (r.used[k] && r.ev[k]) cudaEventSynchronize(r.ev[k]);
-                if (r.ev[k]) cudaEventDestroy(r.ev[k]);
-                if (r.buf[k]) cudaFreeHost(r.buf[k]);
-            }
-            r = StageRing{};
-        }
     }
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (auto& kv : g_batch) {
