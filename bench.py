@@ -976,13 +976,35 @@ def bench_grey(args, device):
         gf_backward(R, p_l, I_l, I_h, r, eps)
 
     steps = max(10, min(args.steps // 10, 200))
+    # the streaming form (grey guide formed in the workspace at both
+    # resolutions, its gradient summed by a pass after the layer) for comparison
+    L.dgf_set_grey_fold(False)
+    try:
+        fwd_ms_s = time_loop(fwd, steps, max(3, args.warmup // 4), 1, device)
+        ms_s = time_loop(step, steps, max(3, args.warmup // 4), 1, device)
+    finally:
+        L.dgf_set_grey_fold(True)
     fwd_ms = time_loop(fwd, steps, max(3, args.warmup // 4), 1, device)
     ms = time_loop(step, steps, max(3, args.warmup // 4), 1, device)
+    # the same calls replayed from CUDA graphs (no host work between kernels)
+    import torch
+    graphs = {}
+    for name, fn in (("fwd", fwd), ("fwd_bwd", step)):
+        cap = torch.cuda.Stream(device)
+        torch.cuda.synchronize(device)
+        with torch.cuda.stream(cap):
+            fn()
+        torch.cuda.synchronize(device)
+        graphs[name] = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graphs[name], stream=cap):
+            fn()
+        torch.cuda.synchronize(device)
+    fwd_ms_g = time_loop(graphs["fwd"].replay, steps, 3, 1, device)
+    ms_g = time_loop(graphs["fwd_bwd"].replay, steps, 3, 1, device)
     L.dgf_profile_reset()
     L.dgf_profile_enable(True)
     try:
         step()
-        import torch
         torch.cuda.synchronize()
         prof = L.dgf_profile_read()
     finally:
@@ -998,9 +1020,18 @@ def bench_grey(args, device):
             "fwd_bwd_mpix_s": round(N * h * w / (ms * 1e-3) / 1e6, 1), "ms_fwd_bwd": round(ms, 4),
             "fwd_frac_of_measured_hbm": round(fwd_b / (fwd_ms * 1e-3) / 1e9 / peak, 4),
             "fwd_bwd_frac_of_measured_hbm": round((fwd_b + bwd_b) / (ms * 1e-3) / 1e9 / peak, 4),
+            "graph": {"ms_fwd": round(fwd_ms_g, 4), "ms_fwd_bwd": round(ms_g, 4),
+                      "fwd_bwd_mpix_s": round(N * h * w / (ms_g * 1e-3) / 1e6, 1),
+                      "fwd_frac_of_measured_hbm": round(fwd_b / (fwd_ms_g * 1e-3) / 1e9 / peak, 4),
+                      "fwd_bwd_frac_of_measured_hbm": round((fwd_b + bwd_b) / (ms_g * 1e-3) / 1e9 / peak, 4)},
             "kernels_avg_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in prof.items()},
-            "note": "through the Python binding (allocates outputs and workspace per call); the grey guide "
-                    "is formed by a streaming pass before the layer and its gradient by one after it"}
+            "streaming_form": {"ms_fwd": round(fwd_ms_s, 4), "ms_fwd_bwd": round(ms_s, 4)},
+            "note": "through the Python binding (allocates outputs and workspace per call); the high-res "
+                    "kernels form the grey guide from I_h's channels in registers (k2_grey_apply, "
+                    "k3_grey_bwd, which also writes dI_h); only the low-res guide and its gradient go "
+                    "through streaming passes (grey_guide, grey_guide_adjoint). streaming_form: the guide "
+                    "formed at both resolutions in the workspace before the layer and its gradient summed "
+                    "after it"}
 
 
 def bench_guided(args, device):

@@ -238,6 +238,15 @@ void dgf_set_fused(int on);
  * (autotune kinds 1 and 4) but not on the number of planes in a call. */
 void dgf_set_lowres_slide(int on);
 
+/* Allows (1, default) or forbids (0) the folded form of the grey guide
+ * (dgf_options.guide_channels, Sec. 4.2 DGF_b): the high-resolution kernels
+ * forming the channel mean of I_h in registers.  Forbidden, the grey guide
+ * is formed in the workspace at both resolutions by streaming passes and the
+ * layer runs on it.  Both forms form the mean the same way (FP32 sum over
+ * the channels in order, one division); the backward's dI_h differs in
+ * rounding (the folded form keeps the sum over output channels in FP32). */
+void dgf_set_grey_fold(int on);
+
 /* Allows (1, default) or forbids (0) the one-graph form of
  * dgf_backward_batched; forbidden, every batch runs the per-image chains.
  * Both give the same bits. */
@@ -275,12 +284,22 @@ void dgf_set_pipeline(int on);
  *             one of the C output channels; dI_l, dI_h then have n_I channels
  *             (each the sum of the C channels' guide gradients / n_I).  Not
  *             with a guidance transform (g != NULL) and not in the batched or
- *             host-memory calls.  The workspace (dgf_workspace_size_opt) adds
+ *             host-memory calls.  With an integer factor f in {2, 4, 8} and
+ *             I_h, O_h (dO_h, dI_h) aligned to the vectors of the
+ *             high-resolution tiles (16 bytes when w allows them, else 8;
+ *             FP32 f = 8 is not among them), the high-resolution kernels
+ *             read I_h's n_I channels and form the mean in registers: the
+ *             forward writes O_h for all C channels of a tile from one pass
+ *             over I_h, and the backward writes dI_h (from FP32 sums over
+ *             the C channels) in the same pass that gathers the low-res
+ *             gradients; only the low-res guide and its gradient go through
+ *             the workspace.  Otherwise two streaming passes form the guide
+ *             at both resolutions in the workspace before the layer and two
+ *             more sum its gradient after it (with 16-bit dt the high-
+ *             resolution stage then runs the general tile kernels).  The
+ *             workspace (dgf_workspace_size_opt) covers the second form:
  *             the FP32 grey guide repeated over the C channels at both
- *             resolutions and its gradients in dt; two streaming passes form
- *             the guide before the layer and two more its gradient after it.
- *             With 16-bit dt the high-resolution stage runs the general tile
- *             kernels (the strip and fused forms read guides in dt).
+ *             resolutions and its gradients.
  *   guide_low = 0 (default): with a guidance transform (g != NULL) the
  *             low-res guide is the f x f block mean of F(I_h) and I_l is not
  *             read;
@@ -353,6 +372,22 @@ typedef struct {
 size_t dgf_workspace_size_batched_backward(const dgf_image_grad* imgs, int n, dgf_dtype dt);
 dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dgf_dtype dt, void* workspace,
                                 size_t ws_bytes, dgf_stream_t stream);
+
+/*
+ * The batched calls with options (dgf_options; NULL = the defaults, the same
+ * as dgf_forward_batched / dgf_backward_batched).  Only mean_ab is taken:
+ * mean_ab = 0 runs every image as the layer Sec. 3.2 prints (A_l, b_l
+ * upsampled without their box mean; Algorithm 1 without f_mu^T), each image's
+ * kernel chain on one of the library streams forked from and joined back to
+ * `stream` (no graph of persistent kernels); each image's outputs hold the
+ * bits dgf_forward_opt / dgf_backward_opt give it with the same option.
+ * guide_channels != 0 or guide_low != 0: DGF_ERR_UNSUPPORTED.  Workspace as
+ * dgf_workspace_size_batched / dgf_workspace_size_batched_backward.
+ */
+dgf_status dgf_forward_batched_opt(const dgf_image* imgs, int n, dgf_dtype dt, void* workspace,
+                                   size_t ws_bytes, dgf_stream_t stream, const dgf_options* opt);
+dgf_status dgf_backward_batched_opt(const dgf_image_grad* imgs, int n, dgf_dtype dt, void* workspace,
+                                    size_t ws_bytes, dgf_stream_t stream, const dgf_options* opt);
 
 /*
  * Tile-shape autotuner.  When enabled (here, or DGF_AUTOTUNE=1 in the
@@ -473,6 +508,13 @@ size_t dgf_host_step_device_bytes(int N, int C, int h_l, int w_l, int h, int w, 
 dgf_status dgf_host_step(const dgf_host_step_io* io, int N, int C, int h_l, int w_l, int h, int w, int r,
                          float eps, dgf_dtype dt, int groups, void* device, size_t device_bytes,
                          dgf_stream_t stream);
+/* dgf_host_step with options (NULL = the defaults): only mean_ab is taken
+ * (mean_ab = 0: the layer as Sec. 3.2 prints it, every plane's outputs the
+ * bits of dgf_forward_opt / dgf_backward_opt with that option);
+ * guide_channels != 0 or guide_low != 0: DGF_ERR_UNSUPPORTED. */
+dgf_status dgf_host_step_opt(const dgf_host_step_io* io, int N, int C, int h_l, int w_l, int h, int w, int r,
+                             float eps, dgf_dtype dt, int groups, void* device, size_t device_bytes,
+                             dgf_stream_t stream, const dgf_options* opt);
 
 /* Releases cached graphs and tuning state (idempotent). */
 void dgf_shutdown(void);

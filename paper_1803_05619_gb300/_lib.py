@@ -73,6 +73,9 @@ _SIGS = {
     "dgf_forward_batched": (_I, [ctypes.POINTER(dgf_image), _I, _I, _P, _S, _P]),
     "dgf_workspace_size_batched_backward": (_S, [ctypes.POINTER(dgf_image_grad), _I, _I]),
     "dgf_backward_batched": (_I, [ctypes.POINTER(dgf_image_grad), _I, _I, _P, _S, _P]),
+    "dgf_forward_batched_opt": (_I, [ctypes.POINTER(dgf_image), _I, _I, _P, _S, _P, ctypes.POINTER(dgf_options)]),
+    "dgf_backward_batched_opt": (_I, [ctypes.POINTER(dgf_image_grad), _I, _I, _P, _S, _P,
+                                      ctypes.POINTER(dgf_options)]),
     "dgf_last_error": (ctypes.c_char_p, []),
     "dgf_profile_enable": (None, [_I]),
     "dgf_profile_reset": (None, []),
@@ -85,6 +88,7 @@ _SIGS = {
     "dgf_set_tma": (None, [_I]),
     "dgf_set_fused": (None, [_I]),
     "dgf_set_lowres_slide": (None, [_I]),
+    "dgf_set_grey_fold": (None, [_I]),
     "dgf_set_batched_graph_backward": (None, [_I]),
     "dgf_set_pipeline": (None, [_I]),
     "dgf_shutdown": (None, []),
@@ -97,6 +101,8 @@ _SIGS = {
     "dgf_host_step_device_bytes": (_S, [_I, _I, _I, _I, _I, _I, _I, _I, _I]),
     "dgf_host_step": (_I, [ctypes.POINTER(dgf_host_step_io), _I, _I, _I, _I, _I, _I, _I, _F, _I, _I, _P, _S,
                            _P]),
+    "dgf_host_step_opt": (_I, [ctypes.POINTER(dgf_host_step_io), _I, _I, _I, _I, _I, _I, _I, _F, _I, _I, _P,
+                               _S, _P, ctypes.POINTER(dgf_options)]),
 }
 
 
@@ -169,6 +175,14 @@ def dgf_backward_batched(imgs, n, dt, ws, ws_bytes, stream) -> int:
     return lib().dgf_backward_batched(imgs, n, dt, ws, ws_bytes, stream)
 
 
+def dgf_forward_batched_opt(imgs, n, dt, ws, ws_bytes, stream, opt) -> int:
+    return lib().dgf_forward_batched_opt(imgs, n, dt, ws, ws_bytes, stream, opt)
+
+
+def dgf_backward_batched_opt(imgs, n, dt, ws, ws_bytes, stream, opt) -> int:
+    return lib().dgf_backward_batched_opt(imgs, n, dt, ws, ws_bytes, stream, opt)
+
+
 def dgf_last_error() -> str:
     return lib().dgf_last_error().decode()
 
@@ -219,6 +233,10 @@ def dgf_set_lowres_slide(on: bool) -> None:
     lib().dgf_set_lowres_slide(1 if on else 0)
 
 
+def dgf_set_grey_fold(on: bool) -> None:
+    lib().dgf_set_grey_fold(1 if on else 0)
+
+
 def dgf_set_batched_graph_backward(on: bool) -> None:
     lib().dgf_set_batched_graph_backward(1 if on else 0)
 
@@ -261,3 +279,7 @@ def dgf_host_step_device_bytes(N, C, h_l, w_l, h, w, r, dt, groups) -> int:
 
 def dgf_host_step(io, N, C, h_l, w_l, h, w, r, eps, dt, groups, device, device_bytes, stream) -> int:
     return lib().dgf_host_step(io, N, C, h_l, w_l, h, w, r, eps, dt, groups, device, device_bytes, stream)
+
+
+def dgf_host_step_opt(io, N, C, h_l, w_l, h, w, r, eps, dt, groups, device, device_bytes, stream, opt) -> int:
+    return lib().dgf_host_step_opt(io, N, C, h_l, w_l, h, w, r, eps, dt, groups, device, device_bytes, stream, opt)

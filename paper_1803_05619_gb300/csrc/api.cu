@@ -1540,6 +1540,17 @@ static dgf_status check_grey(int n_in, int N, const dgf_guide* g) {
     return DGF_OK;
 }
 
+static bool g_grey_fold = true;
+
+// The folded grey-guide forms (the high-resolution guide formed in the
+// kernels' registers) serve an integer factor F in {2, 4, 8} with vector
+// access to the high-resolution tensors; their vector width, else 0.
+static int grey_fold(dgf_dtype dt, int C, int h_l, int w_l, int h, int w, std::initializer_list<const void*> ptrs) {
+    if (!g_grey_fold) return 0;
+    const int F = integer_factor(h_l, w_l, h, w);
+    return F > 0 ? grey_fold_vec(dt, F, C, w, ptrs) : 0;
+}
+
 static dgf_status forward_grey(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
                                int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
                                void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab, int n_in) {
@@ -1559,8 +1570,22 @@ static dgf_status forward_grey(const void* p_l, const void* I_l, const void* I_h
     cudaError_t e = L.run("grey_guide", [&] {
         return launch_grey_mean(dt, I_l, Gl, N, n_in, C, (size_t)h_l * w_l, s);
     });
-    if (e == cudaSuccess)
-        e = L.run("grey_guide", [&] { return launch_grey_mean(dt, I_h, Gh, N, n_in, C, (size_t)h * w, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "grey guide");
+    if (const int vec = grey_fold(dt, C, h_l, w_l, h, w, {I_h, O_h}); vec != 0) {
+        // K1 over the low-res grey guide (FP32), then K2 forming G_h itself
+        const int planes = N * C;
+        float2* coef = reinterpret_cast<float2*>(ws + layout(N, C, h_l, w_l, false).coef);
+        Plan p = make_plan(dt, h_l, w_l, h, w, r, true, {I_h, O_h}, mean_ab);
+        if (tune_enabled() && !stream_capturing(s) && mean_ab)
+            tune_k1(dt, true, Gl, p_l, coef, planes, h_l, w_l, r, eps, s, p);
+        e = run_k1(L, dt, true, Gl, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+        if (e != cudaSuccess) return cuda_fail(e, "k1");
+        e = L.run("k2_grey_apply",
+                  [&] { return launch_k2_grey(dt, coef, I_h, O_h, N, C, n_in, h_l, w_l, h, w, p.F, vec, s); });
+        if (e != cudaSuccess) return cuda_fail(e, "k2 grey");
+        return DGF_OK;
+    }
+    e = L.run("grey_guide", [&] { return launch_grey_mean(dt, I_h, Gh, N, n_in, C, (size_t)h * w, s); });
     if (e != cudaSuccess) return cuda_fail(e, "grey guide");
     return forward_impl(p_l, Gl, Gh, O_h, N, C, h_l, w_l, h, w, r, eps, dt, nullptr, workspace, ws_bytes, stream,
                         mean_ab, false, true);
@@ -1602,6 +1627,49 @@ static dgf_status backward_grey(const void* dO_h, const void* p_l, const void* I
     if ((st = check_ws(workspace, ws_bytes, gl.total)) != DGF_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
+    if (const int vec = grey_fold(dt, C, h_l, w_l, h, w, {dO_h, I_h, dI_h}); vec != 0) {
+        // the low-res grey guide (FP32); K1 (Abar, bbar, for d I_h only) ->
+        // K3 forming G_h itself and writing d I_h -> K4 (d p_l and d G_l per
+        // output channel) -> d I_l from the d G_l sums
+        Launcher L(s);
+        const int planes = N * C;
+        const Layout lay = layout(N, C, h_l, w_l, false);
+        float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
+        float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
+        float* Gl = reinterpret_cast<float*>(ws + gl.gl);
+        float* dGl = reinterpret_cast<float*>(ws + gl.dgl);
+        Plan p = make_plan(dt, h_l, w_l, h, w, r, true, {dO_h, I_h, dI_h}, mean_ab);
+        const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab;
+        const bool need_k4 = dp_l != nullptr || dI_l != nullptr;
+        cudaError_t e = L.run("grey_guide", [&] {
+            return launch_grey_mean(dt, I_l, Gl, N, n_in, C, (size_t)h_l * w_l, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "grey guide");
+        if (dI_h != nullptr) {
+            if (tuning) tune_k1(dt, true, Gl, p_l, coef, planes, h_l, w_l, r, eps, s, p);
+            e = run_k1(L, dt, true, Gl, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+            if (e != cudaSuccess) return cuda_fail(e, "k1");
+        }
+        e = L.run("k3_grey_bwd", [&] {
+            return launch_k3_grey(dt, dO_h, I_h, coef, dcoef, dI_h, N, C, n_in, h_l, w_l, h, w, p.F, vec, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k3 grey");
+        if (need_k4) {
+            // timing only: the K4 launch below overwrites what the candidates wrote
+            if (tuning) tune_k4(dt, true, Gl, p_l, dcoef, dp_l, dI_l ? dGl : nullptr, planes, h_l, w_l, r, eps, s, p);
+            e = L.run("k4_lowres_bwd", [&] {
+                return run_k4(dt, true, Gl, p_l, dcoef, dp_l, dI_l ? dGl : nullptr, planes, h_l, w_l, r, eps, p.k4, s);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "k4");
+        }
+        if (dI_l != nullptr) {
+            e = L.run("grey_guide_adjoint", [&] {
+                return launch_grey_adjoint(dt, true, dGl, dI_l, N, n_in, C, (size_t)h_l * w_l, s);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "grey guide adjoint");
+        }
+        return DGF_OK;
+    }
     {
         Launcher L(s);
         cudaError_t e = L.run("grey_guide", [&] {
@@ -2267,9 +2335,10 @@ extern "C" size_t dgf_workspace_size_batched_backward(const dgf_image_grad* imgs
     return total;
 }
 
-extern "C" dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dgf_dtype dt, void* workspace,
-                                           size_t ws_bytes, dgf_stream_t stream) {
-    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
+// The batched backward; mean_ab = false (the layer as printed, Sec. 3.2 and
+// Algorithm 1 without the box mean of A, b) runs every image's chain.
+static dgf_status backward_batched_impl(const dgf_image_grad* imgs, int n, dgf_dtype dt, void* workspace,
+                                        size_t ws_bytes, dgf_stream_t stream, bool mean_ab) {
     size_t total = 0;
     dgf_status st = check_grad_images(imgs, n, dt, &total);
     if (st != DGF_OK) return st;
@@ -2277,7 +2346,7 @@ extern "C" dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dg
     if ((st = check_ws(workspace, ws_bytes, total)) != DGF_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     bool done = false;
-    if (g_batched_graph_bwd) {
+    if (g_batched_graph_bwd && mean_ab) {
         st = backward_batched_graph(imgs, n, dt, static_cast<char*>(workspace), s, done);
         if (st != DGF_OK || done) return st;
     }
@@ -2297,7 +2366,7 @@ extern "C" dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dg
         const dgf_image_grad& im = imgs[i];
         cudaStream_t si = pool->st[i % ns];
         const Layout lay = layout(1, im.C, im.h_l, im.w_l, false);
-        Plan p = make_plan(dt, im.h_l, im.w_l, im.h, im.w, im.r, false, {im.dO_h, im.I_h, im.dI_h});
+        Plan p = make_plan(dt, im.h_l, im.w_l, im.h, im.w, im.r, false, {im.dO_h, im.I_h, im.dI_h}, mean_ab);
         if (im.dp_l != nullptr || im.dI_l != nullptr || im.dI_h != nullptr) {
             Launcher L(si);
             st = backward_plain(L, dt, im.dO_h, im.p_l, im.I_l, im.I_h, im.dp_l, im.dI_l, im.dI_h, im.C, im.h_l,
@@ -2311,6 +2380,81 @@ extern "C" dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dg
         if ((e = cudaStreamWaitEvent(s, pool->join[k], 0)) != cudaSuccess) return cuda_fail(e, "join wait");
     }
     return DGF_OK;
+}
+
+extern "C" dgf_status dgf_backward_batched(const dgf_image_grad* imgs, int n, dgf_dtype dt, void* workspace,
+                                           size_t ws_bytes, dgf_stream_t stream) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
+    return backward_batched_impl(imgs, n, dt, workspace, ws_bytes, stream, true);
+}
+
+// Options of the batched and host-memory calls: the box mean of A, b only.
+static dgf_status batch_options(const dgf_options* opt, bool& mean_ab) {
+    mean_ab = opt == nullptr || opt->mean_ab != 0;
+    if (opt != nullptr && (opt->guide_channels != 0 || opt->guide_low != 0))
+        return fail(DGF_ERR_UNSUPPORTED, "the batched and host-memory calls take the mean_ab option only");
+    return DGF_OK;
+}
+
+extern "C" dgf_status dgf_backward_batched_opt(const dgf_image_grad* imgs, int n, dgf_dtype dt, void* workspace,
+                                               size_t ws_bytes, dgf_stream_t stream, const dgf_options* opt) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
+    bool mean_ab = true;
+    if (dgf_status st = batch_options(opt, mean_ab); st != DGF_OK) return st;
+    return backward_batched_impl(imgs, n, dt, workspace, ws_bytes, stream, mean_ab);
+}
+
+// The layer as printed over a batch: each image's K1 (A, b without their box
+// mean) and K2 on one of the library streams, in the image's coefficient
+// slot of the batched workspace.
+static dgf_status forward_batched_chains(const dgf_image* imgs, int n, dgf_dtype dt, void* workspace,
+                                         size_t ws_bytes, dgf_stream_t stream) {
+    static thread_local BatchPrep prep;
+    if ((int)dt < 0 || (int)dt > 2) return fail(DGF_ERR_INVALID, "dtype %d", (int)dt);
+    dgf_status st = prepare_batch(imgs, n, dt, nullptr, prep);
+    if (st != DGF_OK) return st;
+    if (n == 0) return DGF_OK;
+    if ((st = check_ws(workspace, ws_bytes, prep.ws)) != DGF_OK) return st;
+    if ((st = prepare_batch(imgs, n, dt, static_cast<char*>(workspace), prep)) != DGF_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_bwd_mu);
+    BwdPool* pool = nullptr;
+    cudaError_t e = bwd_pool(dev, pool);
+    if (e != cudaSuccess) return cuda_fail(e, "batch stream pool");
+    const int ns = std::min(n, kBwdStreams);
+    if ((e = cudaEventRecord(pool->fork, s)) != cudaSuccess) return cuda_fail(e, "fork");
+    for (int k = 0; k < ns; ++k)
+        if ((e = cudaStreamWaitEvent(pool->st[k], pool->fork, 0)) != cudaSuccess) return cuda_fail(e, "fork wait");
+    for (int i = 0; i < n; ++i) {
+        const dgf_image& im = imgs[i];
+        cudaStream_t si = pool->st[i % ns];
+        float2* coef = prep.bp.img[i].coef;
+        Plan p = make_plan(dt, im.h_l, im.w_l, im.h, im.w, im.r, false, {im.I_h, im.O_h}, false);
+        Launcher L(si);
+        e = run_k1(L, dt, false, im.I_l, im.p_l, coef, im.C, im.h_l, im.w_l, im.r, im.eps, p, si);
+        if (e != cudaSuccess) return cuda_fail(e, "k1");
+        e = L.run("k2_hires_apply", [&] {
+            return launch_k2_plan(dt, coef, im.I_h, im.O_h, im.C, im.h_l, im.w_l, im.h, im.w, p,
+                                  p.k2_strip ? p.k2_ls : p.k2_th, si);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "k2");
+    }
+    for (int k = 0; k < ns; ++k) {
+        if ((e = cudaEventRecord(pool->join[k], pool->st[k])) != cudaSuccess) return cuda_fail(e, "join");
+        if ((e = cudaStreamWaitEvent(s, pool->join[k], 0)) != cudaSuccess) return cuda_fail(e, "join wait");
+    }
+    return DGF_OK;
+}
+
+extern "C" dgf_status dgf_forward_batched_opt(const dgf_image* imgs, int n, dgf_dtype dt, void* workspace,
+                                              size_t ws_bytes, dgf_stream_t stream, const dgf_options* opt) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
+    bool mean_ab = true;
+    if (dgf_status st = batch_options(opt, mean_ab); st != DGF_OK) return st;
+    if (mean_ab) return dgf_forward_batched(imgs, n, dt, workspace, ws_bytes, stream);
+    return forward_batched_chains(imgs, n, dt, workspace, ws_bytes, stream);
 }
 
 extern "C" const char* dgf_last_error(void) { return t_err.c_str(); }
@@ -2375,6 +2519,7 @@ extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
 
 extern "C" void dgf_set_fused(int on) { g_fused_allowed = on != 0; }
 extern "C" void dgf_set_lowres_slide(int on) { g_slide_allowed = on != 0; }
+extern "C" void dgf_set_grey_fold(int on) { g_grey_fold = on != 0; }
 extern "C" void dgf_set_batched_graph_backward(int on) { g_batched_graph_bwd = on != 0; }
 
 extern "C" void dgf_set_pipeline(int on) { g_pipeline = on != 0; }
@@ -2560,10 +2705,9 @@ extern "C" size_t dgf_host_step_device_bytes(int N, int C, int h_l, int w_l, int
     return host_layout(N, C, h_l, w_l, h, w, dt, host_groups(std::max(N * C, 1), groups)).total;
 }
 
-extern "C" dgf_status dgf_host_step(const dgf_host_step_io* io, int N, int C, int h_l, int w_l, int h, int w,
-                                    int r, float eps, dgf_dtype dt, int groups, void* device, size_t device_bytes,
-                                    dgf_stream_t stream) {
-    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
+static dgf_status host_step_impl(const dgf_host_step_io* io, int N, int C, int h_l, int w_l, int h, int w, int r,
+                                 float eps, dgf_dtype dt, int groups, void* device, size_t device_bytes,
+                                 dgf_stream_t stream, bool mean_ab) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if (io == nullptr) return fail(DGF_ERR_INVALID, "NULL io descriptor");
@@ -2618,11 +2762,11 @@ extern "C" dgf_status dgf_host_step(const dgf_host_step_io* io, int N, int C, in
         dgf_stream_t cs = reinterpret_cast<dgf_stream_t>(hp->comp);
         if (io->O_h != nullptr)
             result = forward_impl(dptr(0), dptr(1), dptr(2), dptr(4), n, 1, h_l, w_l, h, w, r, eps, dt, nullptr, ws,
-                                  ws_bytes, cs, true);
+                                  ws_bytes, cs, mean_ab);
         if (result == DGF_OK && bwd)
             result = backward_impl(dptr(3), dptr(0), dptr(1), dptr(2), io->dp_l ? dptr(5) : nullptr,
                                    io->dI_l ? dptr(6) : nullptr, io->dI_h ? dptr(7) : nullptr, nullptr, n, 1, h_l,
-                                   w_l, h, w, r, eps, dt, nullptr, ws, ws_bytes, cs, true);
+                                   w_l, h, w, r, eps, dt, nullptr, ws, ws_bytes, cs, mean_ab);
         if (result != DGF_OK) break;
         if ((e = cudaEventRecord(hp->done[g], hp->comp)) == cudaSuccess)
             e = cudaStreamWaitEvent(hp->out, hp->done[g], 0);
@@ -2639,4 +2783,20 @@ extern "C" dgf_status dgf_host_step(const dgf_host_step_io* io, int N, int C, in
         if (ej != cudaSuccess && result == DGF_OK) result = cuda_fail(ej, "join");
     }
     return result;
+}
+
+extern "C" dgf_status dgf_host_step(const dgf_host_step_io* io, int N, int C, int h_l, int w_l, int h, int w,
+                                    int r, float eps, dgf_dtype dt, int groups, void* device, size_t device_bytes,
+                                    dgf_stream_t stream) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
+    return host_step_impl(io, N, C, h_l, w_l, h, w, r, eps, dt, groups, device, device_bytes, stream, true);
+}
+
+extern "C" dgf_status dgf_host_step_opt(const dgf_host_step_io* io, int N, int C, int h_l, int w_l, int h, int w,
+                                        int r, float eps, dgf_dtype dt, int groups, void* device,
+                                        size_t device_bytes, dgf_stream_t stream, const dgf_options* opt) {
+    if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
+    bool mean_ab = true;
+    if (dgf_status st = batch_options(opt, mean_ab); st != DGF_OK) return st;
+    return host_step_impl(io, N, C, h_l, w_l, h, w, r, eps, dt, groups, device, device_bytes, stream, mean_ab);
 }

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <initializer_list>
 
 #include "../../include/dgf.h"
 
@@ -162,6 +163,18 @@ cudaError_t launch_grey_mean(dgf_dtype dt, const void* I, float* G, int N, int n
 // src_f32: d G is FP32 (else stored in dt)
 cudaError_t launch_grey_adjoint(dgf_dtype dt, bool src_f32, const void* dG, void* dI, int N, int n_in, int C,
                                 size_t plane, cudaStream_t s);
+// The high-resolution kernels with the grey guide formed in registers from
+// I_h's n_in channels (integer factor F; N images of C output channels).
+// grey_fold_vec: the vector width they use for these sizes and pointers, or
+// 0 when they do not serve them.  K2grey writes O_h; K3grey writes d Abar,
+// d bbar (dcoef) and, when dI_h is not null, d I_h (n_in planes per image)
+// from Abar (coef).
+int grey_fold_vec(dgf_dtype dt, int F, int C, int w, std::initializer_list<const void*> ptrs);
+cudaError_t launch_k2_grey(dgf_dtype dt, const float2* coef, const void* I_h, void* O_h, int N, int C, int n_in,
+                           int h_l, int w_l, int h, int w, int F, int vec, cudaStream_t s);
+cudaError_t launch_k3_grey(dgf_dtype dt, const void* R, const void* I_h, const float2* coef, float2* dcoef,
+                           void* dI_h, int N, int C, int n_in, int h_l, int w_l, int h, int w, int F, int vec,
+                           cudaStream_t s);
 
 // Column-walking low-resolution kernels, one translation unit per radius.
 template <int R>

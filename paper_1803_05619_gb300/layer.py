@@ -151,8 +151,9 @@ def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=No
 
 
 def gf_step_host(p_l, I_l, I_h, dO_h, r: int, eps: float, out=None, groups: int = 0, device=None, buf=None,
-                 sync: bool = True):
-    """Forward and backward of a batch held in host memory (dgf_host_step).
+                 sync: bool = True, mean_ab: bool = True):
+    """Forward and backward of a batch held in host memory (dgf_host_step;
+    mean_ab=False: the layer as printed, dgf_host_step_opt).
 
     p_l, I_l, I_h, dO_h: contiguous CPU tensors of one dtype (pinned memory
     lets the copies overlap the kernels).  Returns host tensors
@@ -184,18 +185,25 @@ def gf_step_host(p_l, I_l, I_h, dO_h, r: int, eps: float, out=None, groups: int 
         buf = workspace(nb, dev)
     io = L.dgf_host_step_io(*(None if x is None else x.data_ptr() for x in (p_l, I_l, I_h, dO_h, *out)))
     with torch.cuda.device(dev):
-        L.check(L.dgf_host_step(ctypes.byref(io), N, C, h_l, w_l, h, w, r, float(eps), dt, groups, _ptr(buf),
-                                buf.numel(), _stream(dev)))
+        if mean_ab:
+            L.check(L.dgf_host_step(ctypes.byref(io), N, C, h_l, w_l, h, w, r, float(eps), dt, groups, _ptr(buf),
+                                    buf.numel(), _stream(dev)))
+        else:
+            opt = L.dgf_options(0, 0, 0)
+            L.check(L.dgf_host_step_opt(ctypes.byref(io), N, C, h_l, w_l, h, w, r, float(eps), dt, groups,
+                                        _ptr(buf), buf.numel(), _stream(dev), ctypes.byref(opt)))
         if sync:
             torch.cuda.current_stream(dev).synchronize()
     return out
 
 
-def gf_forward_batched(images, out=None):
+def gf_forward_batched(images, out=None, mean_ab=True):
     """Uneven batch in one graph-replayed persistent launch per stage.
 
     ``images``: list of dicts with p_l, I_l, I_h (C x h x w tensors, one
-    dtype), r, eps.  Returns the list of O_h.
+    dtype), r, eps.  Returns the list of O_h.  mean_ab=False: the layer as
+    printed (dgf_forward_batched_opt; every image's kernels on library
+    streams).
     """
     n = len(images)
     if n == 0:
@@ -217,17 +225,22 @@ def gf_forward_batched(images, out=None):
         raise L.DGFError(1, L.dgf_last_error())
     ws = workspace(nb, dev)
     with torch.cuda.device(dev):
-        L.check(L.dgf_forward_batched(arr, n, dt, _ptr(ws), ws.numel(), _stream(dev)))
+        if mean_ab:
+            L.check(L.dgf_forward_batched(arr, n, dt, _ptr(ws), ws.numel(), _stream(dev)))
+        else:
+            opt = L.dgf_options(0, 0, 0)
+            L.check(L.dgf_forward_batched_opt(arr, n, dt, _ptr(ws), ws.numel(), _stream(dev), ctypes.byref(opt)))
     return outs
 
 
-def gf_backward_batched(images, grads):
+def gf_backward_batched(images, grads, mean_ab=True):
     """Batched backward (Algorithm 1 per image, one graph or concurrent chains).
 
     ``images``: list of dicts with p_l, I_l, I_h (C x h x w tensors, one
     dtype), r, eps, and optionally need_p / need_Il / need_Ih (default
     True); ``grads``: the matching list of d O_h.  Returns a list of
-    (dp_l, dI_l, dI_h) per image, None where not wanted.
+    (dp_l, dI_l, dI_h) per image, None where not wanted.  mean_ab=False:
+    Algorithm 1 as printed (dgf_backward_batched_opt).
     """
     n = len(images)
     if n == 0:
@@ -255,7 +268,11 @@ def gf_backward_batched(images, grads):
         raise L.DGFError(1, L.dgf_last_error())
     ws = workspace(nb, dev)
     with torch.cuda.device(dev):
-        L.check(L.dgf_backward_batched(arr, n, dt, _ptr(ws), ws.numel(), _stream(dev)))
+        if mean_ab:
+            L.check(L.dgf_backward_batched(arr, n, dt, _ptr(ws), ws.numel(), _stream(dev)))
+        else:
+            opt = L.dgf_options(0, 0, 0)
+            L.check(L.dgf_backward_batched_opt(arr, n, dt, _ptr(ws), ws.numel(), _stream(dev), ctypes.byref(opt)))
     return outs
 
 

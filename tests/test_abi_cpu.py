@@ -144,6 +144,28 @@ def test_host_step_validation(lib):
     assert L.dgf_host_step(ctypes.byref(io), 0, 3, 16, 20, 64, 80, 1, 1e-3, L.DGF_F32, 0, None, 0, None) == 0
 
 
+def test_batched_and_host_step_options_on_host(lib):
+    """The batched and host-memory calls take mean_ab only; their checks run on the host."""
+    arr = (L.dgf_image * 1)()
+    arr[0] = L.dgf_image(16, 32, 48, 64, 3, 8, 8, 32, 32, 1, 1e-3)
+    grads = (L.dgf_image_grad * 1)()
+    grads[0] = L.dgf_image_grad(16, 32, 48, 64, 80, 96, 112, 3, 8, 8, 32, 32, 1, 1e-3)
+    io = L.dgf_host_step_io(16, 32, 48, 64, 80, 96, 112, 128)
+    literal, grey, low = L.dgf_options(0, 0, 0), L.dgf_options(1, 1, 0), L.dgf_options(1, 0, 1)
+    for opt in (grey, low):
+        assert L.dgf_forward_batched_opt(arr, 1, L.DGF_F32, None, 0, None, ctypes.byref(opt)) == 2
+        assert L.dgf_backward_batched_opt(grads, 1, L.DGF_F32, None, 0, None, ctypes.byref(opt)) == 2
+        assert L.dgf_host_step_opt(ctypes.byref(io), 1, 3, 8, 8, 32, 32, 1, 1e-3, L.DGF_F32, 0, None, 0, None,
+                                   ctypes.byref(opt)) == 2
+    # mean_ab = 0 or no options: the size and workspace checks of the plain calls
+    for opt in (ctypes.byref(literal), None):
+        assert L.dgf_forward_batched_opt(arr, 1, L.DGF_F32, None, 0, None, opt) == 5
+        assert L.dgf_backward_batched_opt(grads, 1, L.DGF_F32, None, 0, None, opt) == 5
+        assert L.dgf_host_step_opt(ctypes.byref(io), 1, 3, 8, 8, 32, 32, 1, 1e-3, L.DGF_F32, 0, None, 0, None,
+                                   opt) == 5
+        assert L.dgf_forward_batched_opt(arr, 0, L.DGF_F32, None, 0, None, opt) == 0
+
+
 def test_grey_guide_options_on_host(lib):
     """Grey-guide options: workspace sizes and argument checks run on the host."""
     plain = L.dgf_workspace_size(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None)

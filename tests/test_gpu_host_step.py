@@ -86,3 +86,23 @@ def test_host_step_partial_outputs_and_buffer_reuse():
     for a, b in zip(outs[1:], ref):
         assert torch.equal(a, b)
     assert L.dgf_device_status() == 0
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
+def test_host_step_paper_literal_equals_device_calls(dtype):
+    # mean_ab = False (the layer as Sec. 3.2 prints it): every plane's outputs
+    # are those of the device calls with the same option
+    N, C, hl, wl, f, r, eps = 2, 2, 37, 45, 4, 2, 1e-3
+    st = to_storage(make_case("photo", 66, N, C, hl, wl, hl * f, wl * f), dtype)
+    R = synth.upstream_grad(67, st["I_h"].shape).to(dtype)
+    g = {k: v.cuda() for k, v in st.items()}
+    ref_O = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps, mean_ab=False)
+    ref = gf_backward(R.cuda(), g["p_l"], g["I_l"], g["I_h"], r, eps, mean_ab=False)[:3]
+    torch.cuda.synchronize()
+    h = {k: _host(v, True) for k, v in st.items()}
+    out = gf_step_host(h["p_l"], h["I_l"], h["I_h"], _host(R, True), r, eps, groups=3, mean_ab=False)
+    assert torch.equal(out[0], ref_O.cpu())
+    for a, b in zip(out[1:], ref):
+        assert torch.equal(a, b.cpu())
+    assert not torch.equal(out[0], gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps).cpu())
+    assert L.dgf_device_status() == 0

@@ -390,6 +390,42 @@ def test_batched_matches_single_bitwise(dtype, k1_form, pin):
 
 
 @pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
+def test_batched_paper_literal_matches_single_bitwise(dtype):
+    # mean_ab = False through the batched calls: each image's outputs are the
+    # single calls' with the same option (radii 1, 2, 4 and factors 4, 8)
+    specs = synth.mixed_sizes(seed=7, n=6, long_lo=96, long_hi=400)
+    images, grads, host = [], [], []
+    for i, s in enumerate(specs):
+        d = to_storage(synth.photo_like(80 + i, 1, 3, s.h_l, s.w_l, s.f), dtype)
+        R = synth.upstream_grad(95 + i, d["I_h"].shape).to(dtype)
+        host.append((d, R, s.r))
+        images.append({"p_l": d["p_l"][0].cuda(), "I_l": d["I_l"][0].cuda(), "I_h": d["I_h"][0].cuda(),
+                       "r": s.r, "eps": 1e-3})
+        grads.append(R[0].cuda())
+    outs = gf_forward_batched(images, mean_ab=False)
+    bouts = gf_backward_batched(images, grads, mean_ab=False)
+    torch.cuda.synchronize()
+    for im, R, o, b in zip(images, grads, outs, bouts):
+        single = gf_forward(im["p_l"][None], im["I_l"][None], im["I_h"][None], im["r"], im["eps"], mean_ab=False)
+        assert torch.equal(o, single[0])
+        sg = gf_backward(R[None], im["p_l"][None], im["I_l"][None], im["I_h"][None], im["r"], im["eps"],
+                         mean_ab=False)
+        for a, c in zip(b, sg[:3]):
+            assert torch.equal(a, c[0])
+    d, R, r = host[0]
+    ref = O.forward(f64(d["p_l"]), f64(d["I_l"]), f64(d["I_h"]), r, 1e-3, mean_ab=False)
+    assert_fwd(f64(outs[0])[None], ref, dtype, 1e-3)
+    rp, rIl, rIh = O.backward(f64(R), f64(d["p_l"]), f64(d["I_l"]), f64(d["I_h"]), r, 1e-3, mean_ab=False)
+    for got, want, name in zip(bouts[0], (rp, rIl, rIh), ("dp_l", "dI_l", "dI_h")):
+        assert_grad(f64(got)[None], want, dtype, name)
+    # the other options are refused
+    arr = (L.dgf_image * 1)()
+    opt = L.dgf_options(1, 2, 0)
+    assert L.dgf_forward_batched_opt(arr, 1, L.DGF_F32, None, 0, None, ctypes.byref(opt)) == 2  # DGF_ERR_UNSUPPORTED
+    assert L.dgf_device_status() == 0
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
 def test_batched_backward_matches_single_bitwise(dtype):
     specs = synth.mixed_sizes(seed=5, n=7, long_lo=96, long_hi=520)
     images, grads, host = [], [], []
@@ -511,6 +547,64 @@ def test_grey_guide_parity(case, dtype):
     # every guide channel receives the same gradient
     for k in range(1, n_in):
         assert torch.equal(dIh[:, k], dIh[:, 0]) and torch.equal(dIl[:, k], dIl[:, 0])
+    assert L.dgf_device_status() == 0
+
+
+# grey cases of the folded high-resolution kernels (integer factor 2, 4, 8;
+# partial tiles in both directions): kind, N, guide channels, output
+# channels, h_l, w_l, h, w, r, eps
+GREY_FOLD_CASES = [("photo", 2, 3, 1, 37, 62, 148, 248, 1, 1e-3),   # f = 4, RGB guide -> one channel
+                   ("photo", 1, 3, 1, 45, 70, 360, 560, 2, 1e-3),   # f = 8 (FP32: the streaming form)
+                   ("photo", 1, 2, 3, 33, 50, 66, 100, 1, 1e-3),    # f = 2, two guide channels -> three
+                   ("photo", 2, 4, 2, 20, 64, 80, 256, 4, 1e-3)]    # f = 4, r = 4, four -> two
+
+
+def _grey_run(p_l, I_l, I_h, R, r, eps):
+    L.dgf_profile_reset()
+    L.dgf_profile_enable(True)
+    try:
+        out = gf_forward(p_l, I_l, I_h, r, eps)
+        dp, dIl, dIh, _ = gf_backward(R, p_l, I_l, I_h, r, eps)
+        torch.cuda.synchronize()
+        names = set(L.dgf_profile_read().keys())
+    finally:
+        L.dgf_profile_enable(False)
+    return (out, dp, dIl, dIh), names
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16, F16], ids=["f32", "bf16", "f16"])
+@pytest.mark.parametrize("case", GREY_FOLD_CASES, ids=_ids(GREY_FOLD_CASES))
+def test_grey_fold_matches_oracle_and_streaming_form(case, dtype):
+    kind, N, n_in, C, hl, wl, h, w, r, eps = case
+    gsrc = to_storage(make_case(kind, 420 + r, N, n_in, hl, wl, h, w), dtype)
+    psrc = to_storage(make_case(kind, 430 + r, N, C, hl, wl, h, w), dtype)
+    p_l, I_l, I_h = (t.cuda() for t in (psrc["p_l"], gsrc["I_l"], gsrc["I_h"]))
+    R = synth.upstream_grad(13, (N, C, h, w)).to(dtype)
+    folded = not (dtype == F32 and h // hl == 8)
+    res, names = _grey_run(p_l, I_l, I_h, R.cuda(), r, eps)
+    assert ({"k2_grey_apply", "k3_grey_bwd"} <= names) == folded, names
+    out, dp, dIl, dIh = res
+    ref = O.forward_grey(f64(p_l), f64(I_l), f64(I_h), r, eps)
+    assert_fwd(f64(out), ref, dtype, eps)
+    rp, rIl, rIh = O.backward_grey(f64(R), f64(p_l), f64(I_l), f64(I_h), r, eps)
+    assert_grad(f64(dp), rp, dtype, "dp_l")
+    assert_grad(f64(dIl), rIl, dtype, "dI_l")
+    assert_grad(f64(dIh), rIh, dtype, "dI_h")
+    for k in range(1, n_in):
+        assert torch.equal(dIh[:, k], dIh[:, 0]) and torch.equal(dIl[:, k], dIl[:, 0])
+    assert L.dgf_device_status() == 0
+    # the streaming form (grey guide formed in the workspace) meets the same
+    # gates, and the two forms agree within them
+    L.dgf_set_grey_fold(False)
+    try:
+        res2, names2 = _grey_run(p_l, I_l, I_h, R.cuda(), r, eps)
+    finally:
+        L.dgf_set_grey_fold(True)
+    assert "k2_grey_apply" not in names2 and "k3_grey_bwd" not in names2
+    assert_fwd(f64(res2[0]), ref, dtype, eps)
+    assert_fwd(f64(out), f64(res2[0]), dtype, eps)
+    for a, b, ro, name in zip(res[1:], res2[1:], (rp, rIl, rIh), ("dp_l", "dI_l", "dI_h")):
+        assert_grad(f64(b), ro, dtype, name)
     assert L.dgf_device_status() == 0
 
 
