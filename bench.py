@@ -98,7 +98,7 @@ def make_inputs(spec, device, seed=0):
 class Step:
     """Pre-marshalled forward + backward calls through the C ABI."""
 
-    def __init__(self, g, spec, device):
+    def __init__(self, g, spec, device, keep_coef=True):
         import torch
 
         from paper_1803_05619_gb300 import _lib as L
@@ -124,8 +124,20 @@ class Step:
         self.bwd_args = (P(g["R"]), P(g["p_l"]), P(g["I_l"]), P(g["I_h"]), P(self.dp), P(self.dIl),
                          P(self.dIh), None, N, C, h_l, w_l, h, w, self.r, ctypes.c_float(self.eps), self.dt,
                          None, P(self.ws), self.ws.numel(), self.stream)
-        self._f = lib.dgf_forward
-        self._b = lib.dgf_backward
+        # the forward keeps its coefficients for the backward where the backward
+        # then skips work (as the layer's autograd function does)
+        self.keep_coef = keep_coef and L.dgf_backward_reuses_coef(N, C, h_l, w_l, h, w, self.r, self.dt, None,
+                                                                 None) == 1
+        if self.keep_coef:
+            self.coef = torch.empty(2 * N * C * h_l * w_l, dtype=torch.float32, device=device)
+            self.opt = L.dgf_options(1, 0, 0, self.coef.data_ptr())
+            self.fwd_args += (ctypes.byref(self.opt),)
+            self.bwd_args += (ctypes.byref(self.opt),)
+            self._f = lib.dgf_forward_opt
+            self._b = lib.dgf_backward_opt
+        else:
+            self._f = lib.dgf_forward
+            self._b = lib.dgf_backward
 
     def forward(self):
         st = self._f(*self.fwd_args)
@@ -183,11 +195,17 @@ class BatchedStep:
             o, dp = torch.empty_like(im["I_h"]), torch.empty_like(im["p_l"])
             dil, dih = torch.empty_like(im["I_l"]), torch.empty_like(im["I_h"])
             self.keep += [o, dp, dil, dih]
+            # coefficients kept from the forward where the backward then skips work
+            cf = None
+            if L.dgf_backward_reuses_coef(1, C, h_l, w_l, h, w, int(im["r"]), self.dt, None, None) == 1:
+                cf = torch.empty(2 * C * h_l * w_l, dtype=torch.float32, device=device)
+                self.keep.append(cf)
+            cp = None if cf is None else cf.data_ptr()
             self.fa[i] = L.dgf_image(im["p_l"].data_ptr(), im["I_l"].data_ptr(), im["I_h"].data_ptr(), o.data_ptr(),
-                                     C, h_l, w_l, h, w, int(im["r"]), float(im["eps"]))
+                                     C, h_l, w_l, h, w, int(im["r"]), float(im["eps"]), cp)
             self.ba[i] = L.dgf_image_grad(R.data_ptr(), im["p_l"].data_ptr(), im["I_l"].data_ptr(),
                                           im["I_h"].data_ptr(), dp.data_ptr(), dil.data_ptr(), dih.data_ptr(), C, h_l,
-                                          w_l, h, w, int(im["r"]), float(im["eps"]))
+                                          w_l, h, w, int(im["r"]), float(im["eps"]), cp)
         nf = L.dgf_workspace_size_batched(self.fa, n, self.dt)
         nb = L.dgf_workspace_size_batched_backward(self.ba, n, self.dt)
         self.wf, self.wb = workspace(nf, device), workspace(nb, device)
@@ -786,6 +804,7 @@ def main():
         "config": workload_config(main_name, ws),
         "timed": "one forward+backward step (dgf_forward + dgf_backward) captured in a CUDA graph, replayed "
                  "per step",
+        "coef_kept": bool(step.keep_coef),
         "eager": {"value": round(job_value(pix, ws, ms_eager), 2), "unit": "Mpix/s",
                   "ms_per_step": round(ms_eager, 5), "path": "the same calls issued from the host every step"},
         "fwd": {"value": round(ws * pix / (fwd_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
@@ -849,6 +868,9 @@ def bench_bf16_4k(args, device):
     bstep = BatchedStep(images, [g["R"][i] for i in range(N)], device)
     bat_ms = time_loop(bstep.forward, steps, args.warmup, 1, device)
     bat_fb_ms = time_loop(bstep, steps, args.warmup, 1, device)
+    # the same single-call step with the backward recomputing the coefficients
+    rstep = Step(g, spec, device, keep_coef=False)
+    ms_recompute = time_loop(rstep, steps, args.warmup, 1, device)
     rl = roofline(step, spec, min(steps, 200), args.warmup, name)
     esz = 2
     fb_bytes = pix * C * esz * (2 + 3) + N * C * h_l * w_l * esz * (2 + 2 + 2)
@@ -864,6 +886,8 @@ def bench_bf16_4k(args, device):
                 "target_frac_of_nominal_8TBs": 0.70},
             "ms_fwd_bwd": round(ms, 5), "fwd_bwd_frac_of_nominal_8TBs": round(
                 fb_bytes / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4),
+            "coef_kept": bool(step.keep_coef),
+            "ms_fwd_bwd_recomputing_coef": round(ms_recompute, 5),
             "graph_fwd_bwd": {"path": "the single-call step captured in a CUDA graph and replayed",
                               "mpix_s": round(pix / (ms_graph * 1e-3) / 1e6, 2), "ms": round(ms_graph, 5),
                               "frac_of_nominal_8TBs": round(fb_bytes / (ms_graph * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4),

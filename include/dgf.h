@@ -90,7 +90,10 @@ typedef struct {
     float slope;
 } dgf_guide;
 
-/* One image of a batched call (per-image sizes, radius, eps; C channels). */
+/* One image of a batched call (per-image sizes, radius, eps; C channels).
+ * coef: NULL, or C x h_l x w_l FP32 (Abar, bbar) pairs (8-byte aligned) the
+ * forward writes the image's coefficients to (as dgf_options.coef), for a
+ * batched backward that takes them (dgf_image_grad.coef). */
 typedef struct {
     const void* p_l; /* C x h_l x w_l */
     const void* I_l; /* C x h_l x w_l */
@@ -98,6 +101,7 @@ typedef struct {
     void* O_h;       /* C x h x w     */
     int C, h_l, w_l, h, w, r;
     float eps;
+    void* coef;
 } dgf_image;
 
 /*
@@ -307,12 +311,38 @@ void dgf_set_pipeline(int on);
  *             G_h = F(I_h) (Sec. 3.4 read literally).  Needs g and I_l
  *             (N x 3 x h_l x w_l); the backward may then return dI_l (through
  *             F at low resolution), and dW adds the low-res pixels' terms.
+ *   coef = NULL (default): the backward recomputes the coefficients of the
+ *             forward (Eq. 1 and the box mean) from its inputs;
+ *   coef != NULL: device memory of N x C x h_l x w_l FP32 pairs (Abar, bbar)
+ *             (A_l, b_l with mean_ab = 0), 8-byte aligned, owned by the
+ *             caller.  dgf_forward_opt writes the call's coefficients there
+ *             (with the fused forward kernel then off: the two-kernel form,
+ *             the same bits); dgf_backward_opt reads them as the forward's
+ *             (the intermediate values Algorithm 1 takes from the forward
+ *             pass) and skips its own low-resolution pass where that pass
+ *             produces nothing else (dgf_backward_reuses_coef tells when).
+ *             They must be what dgf_forward_opt wrote for the same inputs,
+ *             options and sizes; the backward's results are then the bits
+ *             it gives without them.
  */
 typedef struct {
     int mean_ab;
     int guide_channels;
     int guide_low;
+    void* coef;
 } dgf_options;
+
+/* 1 when dgf_backward_opt with these sizes and options (coef aside) skips
+ * work given the forward's coefficients (opt->coef): always with a guidance
+ * transform or a folded grey guide; without them when the backward's
+ * low-resolution pass would compute the coefficients alone (16-bit storage
+ * with the sliding-sum kernels); 0 when that pass also produces the window
+ * statistics the low-resolution backward reads (FP32 storage, r <= 2), where
+ * the saved coefficients would only cost the forward a write.  A hint for
+ * callers deciding whether to keep them: results are the same either way.
+ * Pure host function (reads the autotuner's table). */
+int dgf_backward_reuses_coef(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt,
+                             const dgf_guide* g, const dgf_options* opt);
 
 /* Workspace bytes of the _opt calls for these options (NULL = the defaults;
  * equals dgf_workspace_size then).  0 for invalid sizes or options. */
@@ -344,6 +374,7 @@ typedef struct {
     void* dI_h;
     int C, h_l, w_l, h, w, r;
     float eps;
+    const void* coef; /* NULL, or the image's coefficients from the forward (dgf_image.coef) */
 } dgf_image_grad;
 
 /*

@@ -28,18 +28,20 @@ class dgf_image(ctypes.Structure):
     _fields_ = [("p_l", ctypes.c_void_p), ("I_l", ctypes.c_void_p), ("I_h", ctypes.c_void_p),
                 ("O_h", ctypes.c_void_p), ("C", ctypes.c_int), ("h_l", ctypes.c_int),
                 ("w_l", ctypes.c_int), ("h", ctypes.c_int), ("w", ctypes.c_int), ("r", ctypes.c_int),
-                ("eps", ctypes.c_float)]
+                ("eps", ctypes.c_float), ("coef", ctypes.c_void_p)]
 
 
 class dgf_options(ctypes.Structure):
-    _fields_ = [("mean_ab", ctypes.c_int), ("guide_channels", ctypes.c_int), ("guide_low", ctypes.c_int)]
+    _fields_ = [("mean_ab", ctypes.c_int), ("guide_channels", ctypes.c_int), ("guide_low", ctypes.c_int),
+                ("coef", ctypes.c_void_p)]
 
 
 class dgf_image_grad(ctypes.Structure):
     _fields_ = [("dO_h", ctypes.c_void_p), ("p_l", ctypes.c_void_p), ("I_l", ctypes.c_void_p),
                 ("I_h", ctypes.c_void_p), ("dp_l", ctypes.c_void_p), ("dI_l", ctypes.c_void_p),
                 ("dI_h", ctypes.c_void_p), ("C", ctypes.c_int), ("h_l", ctypes.c_int), ("w_l", ctypes.c_int),
-                ("h", ctypes.c_int), ("w", ctypes.c_int), ("r", ctypes.c_int), ("eps", ctypes.c_float)]
+                ("h", ctypes.c_int), ("w", ctypes.c_int), ("r", ctypes.c_int), ("eps", ctypes.c_float),
+                ("coef", ctypes.c_void_p)]
 
 
 class dgf_host_step_io(ctypes.Structure):
@@ -69,6 +71,8 @@ _SIGS = {
                               ctypes.POINTER(dgf_guide), _P, _S, _P, ctypes.POINTER(dgf_options)]),
     "dgf_workspace_size_opt": (_S, [_I, _I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(dgf_guide),
                                     ctypes.POINTER(dgf_options)]),
+    "dgf_backward_reuses_coef": (_I, [_I, _I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(dgf_guide),
+                                      ctypes.POINTER(dgf_options)]),
     "dgf_workspace_size_batched": (_S, [ctypes.POINTER(dgf_image), _I, _I]),
     "dgf_forward_batched": (_I, [ctypes.POINTER(dgf_image), _I, _I, _P, _S, _P]),
     "dgf_workspace_size_batched_backward": (_S, [ctypes.POINTER(dgf_image_grad), _I, _I]),
@@ -157,6 +161,10 @@ def dgf_backward_opt(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, 
 
 def dgf_workspace_size_opt(N, C, h_l, w_l, h, w, r, dt, g, opt) -> int:
     return lib().dgf_workspace_size_opt(N, C, h_l, w_l, h, w, r, dt, g, opt)
+
+
+def dgf_backward_reuses_coef(N, C, h_l, w_l, h, w, r, dt, g, opt) -> int:
+    return lib().dgf_backward_reuses_coef(N, C, h_l, w_l, h, w, r, dt, g, opt)
 
 
 def dgf_workspace_size_batched(imgs, n, dt) -> int:

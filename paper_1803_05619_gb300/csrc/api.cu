@@ -954,6 +954,8 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
         if (ws_base != nullptr &&
             (im.p_l == nullptr || im.I_l == nullptr || im.I_h == nullptr || im.O_h == nullptr))
             return fail(DGF_ERR_INVALID, "image %d: NULL pointer", i);
+        if (reinterpret_cast<uintptr_t>(im.coef) % alignof(float2) != 0)
+            return fail(DGF_ERR_INVALID, "image %d: coef must be 8-byte aligned", i);
         BatchImage& b = bp.img[i];
         b.p_l = im.p_l;
         b.I_l = im.I_l;
@@ -991,7 +993,9 @@ dgf_status prepare_batch(const dgf_image* imgs, int n, dgf_dtype dt, char* ws_ba
             b.k2_nx = (im.w + 32 * b.vec - 1) / (32 * b.vec);
             b.k2_ny = (im.h + b.k2_th - 1) / b.k2_th;
         }
-        b.coef = ws_base ? reinterpret_cast<float2*>(ws_base + off) : nullptr;
+        // the image's coefficients: in the caller's buffer when it keeps them, else a workspace slot
+        b.coef = im.coef != nullptr ? static_cast<float2*>(im.coef)
+                                    : (ws_base ? reinterpret_cast<float2*>(ws_base + off) : nullptr);
         off += align256((size_t)im.C * im.h_l * im.w_l * sizeof(float2));
         bp.k1_start[i + 1] = bp.k1_start[i] + b.k1_nx * b.k1_ny * im.C;
         bp.k2_start[i + 1] = bp.k2_start[i] + b.k2_nx * b.k2_ny * im.C;
@@ -1099,7 +1103,7 @@ size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r, d
 static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
                                int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
                                void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab,
-                               bool guide_low = false, bool guide_f32 = false) {
+                               bool guide_low = false, bool guide_f32 = false, float2* coef_out = nullptr) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
@@ -1111,12 +1115,15 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
     if ((st = check_ws(workspace, ws_bytes, lay.total)) != DGF_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
-    float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
+    // the coefficients go to the caller's buffer when it keeps them for the
+    // backward (the fused forward never writes them: the two kernels then)
+    float2* coef = coef_out != nullptr ? coef_out : reinterpret_cast<float2*>(ws + lay.coef);
     const int planes = N * C;
     // an FP32 guide over 16-bit data (the grey guide): FP32 guide reads in K1
     // and the K2 tiles; the strip and fused forms read guides in dt
     const bool gf = guide_f32 && dt != DGF_F32;
     Plan p = make_plan(dt, h_l, w_l, h, w, r, g != nullptr || gf, {I_h, O_h}, mean_ab);
+    if (coef_out != nullptr) p.k12_ok = p.k12 = false;
     Launcher L(s);
     cudaError_t e;
     const bool tuning = tune_enabled() && !stream_capturing(s) && mean_ab && !gf;
@@ -1234,13 +1241,14 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
 static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, const void* p_l, const void* I_l,
                                  const void* I_h, void* dp_l, void* dI_l, void* dI_h, int planes, int h_l, int w_l,
                                  int h, int w, int r, float eps, Plan& p, char* ws, const Layout& lay, cudaStream_t s,
-                                 bool tuning, bool gf = false) {
+                                 bool tuning, bool gf = false, const float2* coef_in = nullptr) {
     float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
     float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
     cudaError_t e;
-    // coefficients are recomputed, not saved from the forward call; with
+    // coefficients are recomputed unless the forward's are given; with
     // both low-res stages in strip form the K1 pass also keeps each
-    // window's statistics for K4, which then skips recomputing them
+    // window's statistics for K4, which then skips recomputing them (and
+    // the K1 pass runs whether or not the coefficients are given)
     const bool need_k4 = dp_l != nullptr || dI_l != nullptr;
     if (tuning && (dI_h != nullptr || need_k4)) tune_k1(dt, gf, I_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
     // K4's form decides whether the K1 pass saves statistics, so it is tuned
@@ -1252,6 +1260,10 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
                 p.k1.fast == 2 ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr);
     const bool use_stats = need_k4 && p.k1.fast == 2 && p.k4.fast == 2;
     float4* stats = use_stats ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr;
+    // the forward's coefficients stand in for a K1 pass that would compute nothing else
+    const bool reuse = coef_in != nullptr && !use_stats;
+    if (reuse) p.k13_ok = p.k13 = false;
+    float2* cf = reuse ? const_cast<float2*>(coef_in) : coef;  // read only from here on
     bool fused = false;
     if (p.k13_ok && p.k3_fast) {
         // K1 + K3 as one kernel (the tuner, when on, times it against the pair)
@@ -1273,18 +1285,18 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
             }
         }
     }
-    if (!fused && (dI_h != nullptr || use_stats)) {
+    if (!fused && !reuse && (dI_h != nullptr || use_stats)) {
         e = run_k1(L, dt, gf, I_l, p_l, coef, planes, h_l, w_l, r, eps, p, s, stats);
         if (e != cudaSuccess) return cuda_fail(e, "k1");
     }
     if (fused) {
         // K13 wrote d Abar, d bbar (and the statistics)
     } else if (p.k3_fast) {
-        if (tuning) tune_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, s, p);
+        if (tuning) tune_k3(dt, cf, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, s, p);
         K3Maps maps;
         const bool tma = make_k3_maps(maps, dO_h, I_h, dt, planes, h, w, p.vec, p.F);
         e = L.run("k3_hires_bwd", [&] {
-            return launch_k3(dt, coef, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F,
+            return launch_k3(dt, cf, dO_h, I_h, dI_h, dcoef, planes, h_l, w_l, h, w, p.vec, p.F,
                              fill_ls(p.k3_lth, (w_l + 30 * (p.vec / p.F) - 1) / (30 * (p.vec / p.F)), h_l, 2),
                              tma ? &maps : nullptr, status_ptr(), s);
         });
@@ -1292,7 +1304,7 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
     } else {
         if (dI_h != nullptr) {
             e = L.run("k2_hires_scale", [&] {
-                return launch_k2(dt, 1, coef, dO_h, dI_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
+                return launch_k2(dt, 1, cf, dO_h, dI_h, planes, h_l, w_l, h, w, p.vec, p.F, p.k2_th, s);
             });
             if (e != cudaSuccess) return cuda_fail(e, "k2 scale");
         }
@@ -1316,13 +1328,15 @@ static dgf_status backward_plain(Launcher& L, dgf_dtype dt, const void* dO_h, co
 static dgf_status backward_pipelined(dgf_dtype dt, const void* dO_h, const void* p_l, const void* I_l,
                                      const void* I_h, void* dp_l, void* dI_l, void* dI_h, int planes, int h_l, int w_l,
                                      int h, int w, int r, float eps, const Plan& p, char* ws, const Layout& lay,
-                                     cudaStream_t s, int G) {
+                                     cudaStream_t s, int G, const float2* coef_in) {
     float2* coef = reinterpret_cast<float2*>(ws + lay.coef);
     float2* dcoef = reinterpret_cast<float2*>(ws + lay.dcoef);
     const bool need_k4 = dp_l != nullptr || dI_l != nullptr;
     const bool use_stats = need_k4 && p.k1.fast == 2 && p.k4.fast == 2;
     float4* stats = use_stats ? reinterpret_cast<float4*>(ws + lay.stats) : nullptr;
-    const bool need_k1 = dI_h != nullptr || use_stats;
+    const bool reuse = coef_in != nullptr && !use_stats;  // the forward's coefficients stand in for K1's
+    const float2* cf = reuse ? coef_in : coef;
+    const bool need_k1 = !reuse && (dI_h != nullptr || use_stats);
     const size_t es = esize(dt), lw = (size_t)h_l * w_l, hw = (size_t)h * w;
     std::lock_guard<std::mutex> lk(g_pipe_mu);
     PipePool* pp = nullptr;
@@ -1355,7 +1369,7 @@ static dgf_status backward_pipelined(dgf_dtype dt, const void* dO_h, const void*
             K3Maps maps;
             const bool tma = make_k3_maps(maps, dO, G_h, dt, n, h, w, p.vec, p.F);
             e = Lhi.run("k3_hires_bwd", [&] {
-                return launch_k3(dt, coef + p0 * lw, dO, G_h, dG_h, dcoef + p0 * lw, n, h_l, w_l, h, w, p.vec, p.F,
+                return launch_k3(dt, cf + p0 * lw, dO, G_h, dG_h, dcoef + p0 * lw, n, h_l, w_l, h, w, p.vec, p.F,
                                  fill_ls(p.k3_lth, (w_l + 30 * (p.vec / p.F) - 1) / (30 * (p.vec / p.F)), h_l, 2),
                                  tma ? &maps : nullptr, status_ptr(), pp->hi);
             });
@@ -1385,7 +1399,7 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
                                 void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w,
                                 int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
                                 size_t ws_bytes, dgf_stream_t stream, bool mean_ab, bool guide_low = false,
-                                bool guide_f32 = false) {
+                                bool guide_f32 = false, const float2* coef_in = nullptr) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_guide(g, C, h_l, w_l, h, w, dt)) != DGF_OK) return st;
@@ -1421,7 +1435,7 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
         p.k13_ok = p.k13 = false;
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
         return backward_plain(L, dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws,
-                              lay, s, tune_enabled() && !stream_capturing(s) && mean_ab, true);
+                              lay, s, tune_enabled() && !stream_capturing(s) && mean_ab, true, coef_in);
     }
     if (g == nullptr) {
         if (dp_l == nullptr && dI_l == nullptr && dI_h == nullptr) return DGF_OK;
@@ -1430,9 +1444,9 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
         const bool tuned = !tuning || (tune_has_low(dt, r, p) && tune_has_k3(dt, p));
         if (G == 1 || !tuned)  // the first call of a key tunes (one stream), later calls pipeline
             return backward_plain(L, dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws,
-                                  lay, s, tuning);
+                                  lay, s, tuning, false, coef_in);
         return backward_pipelined(dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws, lay,
-                                  s, G);
+                                  s, G, coef_in);
     }
     // with the guidance transform
     float* G_l = reinterpret_cast<float*>(ws + lay.gl);
@@ -1452,9 +1466,14 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
         e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
     if (e != cudaSuccess) return cuda_fail(e, "k5");
     const bool gtune = tune_enabled() && !stream_capturing(s) && mean_ab;
-    if (gtune) tune_k1(dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
-    e = run_k1(L, dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
-    if (e != cudaSuccess) return cuda_fail(e, "k1");
+    // Abar for K6: the forward's when given, else recomputed
+    if (coef_in != nullptr) {
+        coef = const_cast<float2*>(coef_in);  // read only from here on
+    } else {
+        if (gtune) tune_k1(dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, s, p);
+        e = run_k1(L, dt, true, G_l, p_l, coef, planes, h_l, w_l, r, eps, p, s);
+        if (e != cudaSuccess) return cuda_fail(e, "k1");
+    }
     e = L.run("k3_hires_bwd_guided", [&] {
         return launch_k3_guided(dt, dO_h, I_h, dcoef, N, h_l, w_l, h, w, p.F, g->slope, s);
     });
@@ -1553,7 +1572,8 @@ static int grey_fold(dgf_dtype dt, int C, int h_l, int w_l, int h, int w, std::i
 
 static dgf_status forward_grey(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
                                int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
-                               void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab, int n_in) {
+                               void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab, int n_in,
+                               float2* coef_out) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_grey(n_in, N, g)) != DGF_OK) return st;
@@ -1574,7 +1594,7 @@ static dgf_status forward_grey(const void* p_l, const void* I_l, const void* I_h
     if (const int vec = grey_fold(dt, C, h_l, w_l, h, w, {I_h, O_h}); vec != 0) {
         // K1 over the low-res grey guide (FP32), then K2 forming G_h itself
         const int planes = N * C;
-        float2* coef = reinterpret_cast<float2*>(ws + layout(N, C, h_l, w_l, false).coef);
+        float2* coef = coef_out != nullptr ? coef_out : reinterpret_cast<float2*>(ws + layout(N, C, h_l, w_l, false).coef);
         Plan p = make_plan(dt, h_l, w_l, h, w, r, true, {I_h, O_h}, mean_ab);
         if (tune_enabled() && !stream_capturing(s) && mean_ab)
             tune_k1(dt, true, Gl, p_l, coef, planes, h_l, w_l, r, eps, s, p);
@@ -1588,7 +1608,15 @@ static dgf_status forward_grey(const void* p_l, const void* I_l, const void* I_h
     e = L.run("grey_guide", [&] { return launch_grey_mean(dt, I_h, Gh, N, n_in, C, (size_t)h * w, s); });
     if (e != cudaSuccess) return cuda_fail(e, "grey guide");
     return forward_impl(p_l, Gl, Gh, O_h, N, C, h_l, w_l, h, w, r, eps, dt, nullptr, workspace, ws_bytes, stream,
-                        mean_ab, false, true);
+                        mean_ab, false, true, coef_out);
+}
+
+// opt->coef as the call's coefficient buffer: NULL, or 8-byte aligned
+static dgf_status opt_coef(const dgf_options* opt, float2*& coef) {
+    coef = opt != nullptr ? static_cast<float2*>(opt->coef) : nullptr;
+    if (reinterpret_cast<uintptr_t>(coef) % alignof(float2) != 0)
+        return fail(DGF_ERR_INVALID, "coef must be 8-byte aligned");
+    return DGF_OK;
 }
 
 dgf_status dgf_forward_opt(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
@@ -1597,11 +1625,13 @@ dgf_status dgf_forward_opt(const void* p_l, const void* I_l, const void* I_h, vo
     if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
     const bool mean_ab = opt == nullptr || opt->mean_ab != 0;
     const int n_in = grey_channels(opt, C);
+    float2* coef = nullptr;
+    if (dgf_status st = opt_coef(opt, coef); st != DGF_OK) return st;
     if (n_in != 0)
         return forward_grey(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream,
-                            mean_ab, n_in);
+                            mean_ab, n_in, coef);
     return forward_impl(p_l, I_l, I_h, O_h, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace, ws_bytes, stream,
-                        mean_ab, opt != nullptr && opt->guide_low != 0);
+                        mean_ab, opt != nullptr && opt->guide_low != 0, false, coef);
 }
 
 dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l, void* dI_l,
@@ -1615,7 +1645,8 @@ dgf_status dgf_backward(const void* dO_h, const void* p_l, const void* I_l, cons
 static dgf_status backward_grey(const void* dO_h, const void* p_l, const void* I_l, const void* I_h, void* dp_l,
                                 void* dI_l, void* dI_h, float* dW, int N, int C, int h_l, int w_l, int h, int w,
                                 int r, float eps, dgf_dtype dt, const dgf_guide* g, void* workspace,
-                                size_t ws_bytes, dgf_stream_t stream, bool mean_ab, int n_in) {
+                                size_t ws_bytes, dgf_stream_t stream, bool mean_ab, int n_in,
+                                const float2* coef_in) {
     dgf_status st = check_sizes(N, C, h_l, w_l, h, w, r, eps, dt);
     if (st != DGF_OK) return st;
     if ((st = check_grey(n_in, N, g)) != DGF_OK) return st;
@@ -1645,7 +1676,9 @@ static dgf_status backward_grey(const void* dO_h, const void* p_l, const void* I
             return launch_grey_mean(dt, I_l, Gl, N, n_in, C, (size_t)h_l * w_l, s);
         });
         if (e != cudaSuccess) return cuda_fail(e, "grey guide");
-        if (dI_h != nullptr) {
+        if (coef_in != nullptr) {
+            coef = const_cast<float2*>(coef_in);  // the forward's Abar: read only
+        } else if (dI_h != nullptr) {
             if (tuning) tune_k1(dt, true, Gl, p_l, coef, planes, h_l, w_l, r, eps, s, p);
             e = run_k1(L, dt, true, Gl, p_l, coef, planes, h_l, w_l, r, eps, p, s);
             if (e != cudaSuccess) return cuda_fail(e, "k1");
@@ -1685,7 +1718,7 @@ static dgf_status backward_grey(const void* dO_h, const void* p_l, const void* I
     // gradients into the workspace, then their sum over the channels / n_I
     st = backward_impl(dO_h, p_l, ws + gl.gl, ws + gl.gh, dp_l, dI_l ? ws + gl.dgl : nullptr,
                        dI_h ? ws + gl.dgh : nullptr, nullptr, N, C, h_l, w_l, h, w, r, eps, dt, nullptr, workspace,
-                       ws_bytes, stream, mean_ab, false, true);
+                       ws_bytes, stream, mean_ab, false, true, coef_in);
     if (st != DGF_OK) return st;
     Launcher L(s);
     cudaError_t e = cudaSuccess;
@@ -1707,11 +1740,13 @@ dgf_status dgf_backward_opt(const void* dO_h, const void* p_l, const void* I_l, 
     if (dgf_status st0 = entry_check(true); st0 != DGF_OK) return st0;
     const bool mean_ab = opt == nullptr || opt->mean_ab != 0;
     const int n_in = grey_channels(opt, C);
+    float2* coef = nullptr;
+    if (dgf_status st = opt_coef(opt, coef); st != DGF_OK) return st;
     if (n_in != 0)
         return backward_grey(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g,
-                             workspace, ws_bytes, stream, mean_ab, n_in);
+                             workspace, ws_bytes, stream, mean_ab, n_in, coef);
     return backward_impl(dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, dW, N, C, h_l, w_l, h, w, r, eps, dt, g, workspace,
-                         ws_bytes, stream, mean_ab, opt != nullptr && opt->guide_low != 0);
+                         ws_bytes, stream, mean_ab, opt != nullptr && opt->guide_low != 0, false, coef);
 }
 
 size_t dgf_workspace_size_opt(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt, const dgf_guide* g,
@@ -1721,6 +1756,19 @@ size_t dgf_workspace_size_opt(int N, int C, int h_l, int w_l, int h, int w, int 
     if (n_in == 0) return layout(N, C, h_l, w_l, g != nullptr, (size_t)N * C * h * w).total;
     if (check_grey(n_in, N, g) != DGF_OK) return 0;
     return grey_layout(N, C, h_l, w_l, h, w, dt).total;
+}
+
+int dgf_backward_reuses_coef(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt, const dgf_guide* g,
+                             const dgf_options* opt) {
+    if (check_sizes(N, C, h_l, w_l, h, w, r, 1.f, dt) != DGF_OK) return 0;
+    if (g != nullptr) return 1;  // its K1 pass computes Abar for K6 alone
+    const bool mean_ab = opt == nullptr || opt->mean_ab != 0;
+    const int n_in = grey_channels(opt, C);
+    if (n_in != 0 && grey_fold(dt, C, h_l, w_l, h, w, {}) != 0) return 1;
+    // the plain backward (and the grey guide's streaming form): its K1 pass
+    // also writes the window statistics when both low-res stages are strips
+    const Plan p = make_plan(dt, h_l, w_l, h, w, r, n_in != 0 && dt != DGF_F32, {}, mean_ab);
+    return (p.k1.fast == 2 && p.k4.fast == 2) ? 0 : 1;
 }
 
 extern "C" size_t dgf_workspace_size_batched(const dgf_image* imgs, int n, dgf_dtype dt) {
@@ -2024,6 +2072,8 @@ static dgf_status check_grad_images(const dgf_image_grad* imgs, int n, dgf_dtype
         }
         if (im.dO_h == nullptr || im.p_l == nullptr || im.I_l == nullptr || im.I_h == nullptr)
             return fail(DGF_ERR_INVALID, "image %d: NULL input pointer", i);
+        if (reinterpret_cast<uintptr_t>(im.coef) % alignof(float2) != 0)
+            return fail(DGF_ERR_INVALID, "image %d: coef must be 8-byte aligned", i);
         off += align256(layout(1, im.C, im.h_l, im.w_l, false).total);
     }
     // 16-bit storage: the K3 tensor maps of the one-graph form
@@ -2101,11 +2151,12 @@ static dgf_status backward_batched_graph(const dgf_image_grad* imgs, int n, dgf_
         if (std::find(v.begin(), v.end(), k) == v.end()) v.push_back(k);
     };
     // as in the single call, K1 runs only for the images that want d I_h
-    // (d Abar and d bbar do not depend on the coefficients)
+    // (d Abar and d bbar do not depend on the coefficients) and have not
+    // brought the forward's
     for (int i = 0; i < n; ++i) {
         const dgf_image_grad& im = imgs[i];
         if (im.dp_l == nullptr && im.dI_l == nullptr && im.dI_h == nullptr) continue;
-        if (im.dI_h != nullptr) add(c1, im.r * 16 + it[i].V1);
+        if (im.dI_h != nullptr && im.coef == nullptr) add(c1, im.r * 16 + it[i].V1);
         add(c3, it[i].k3c);
         if (it[i].k4) add(c4, im.r * 16 + it[i].V4);
     }
@@ -2137,7 +2188,8 @@ static dgf_status backward_batched_graph(const dgf_image_grad* imgs, int n, dgf_
         b.dp = im.dp_l;
         b.dIl = im.dI_l;
         b.dIh = im.dI_h;
-        b.coef = reinterpret_cast<const float2*>(ws + off[i] + lay.coef);
+        b.coef = im.coef != nullptr ? static_cast<const float2*>(im.coef)
+                                    : reinterpret_cast<const float2*>(ws + off[i] + lay.coef);
         b.dcoef = reinterpret_cast<float2*>(ws + off[i] + lay.dcoef);
         b.C = im.C;
         b.h_l = im.h_l;
@@ -2153,7 +2205,7 @@ static dgf_status backward_batched_graph(const dgf_image_grad* imgs, int n, dgf_
         size_t smem = 0;
         for (int i = 0; i < n; ++i) {
             const dgf_image_grad& im = imgs[i];
-            if (im.dI_h == nullptr || im.r * 16 + it[i].V1 != c1[q]) continue;
+            if (im.dI_h == nullptr || im.coef != nullptr || im.r * 16 + it[i].V1 != c1[q]) continue;
             const int j = b.n++;
             BatchImage& bi = b.img[j];
             bi.p_l = im.p_l;
@@ -2370,7 +2422,8 @@ static dgf_status backward_batched_impl(const dgf_image_grad* imgs, int n, dgf_d
         if (im.dp_l != nullptr || im.dI_l != nullptr || im.dI_h != nullptr) {
             Launcher L(si);
             st = backward_plain(L, dt, im.dO_h, im.p_l, im.I_l, im.I_h, im.dp_l, im.dI_l, im.dI_h, im.C, im.h_l,
-                                im.w_l, im.h, im.w, im.r, im.eps, p, ws + off, lay, si, false);
+                                im.w_l, im.h, im.w, im.r, im.eps, p, ws + off, lay, si, false, false,
+                                static_cast<const float2*>(im.coef));
             if (st != DGF_OK) return st;
         }
         off += align256(lay.total);

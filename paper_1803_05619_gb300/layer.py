@@ -75,25 +75,54 @@ def _sizes(p_l, I_h, grey_ok=False):
     return N, C, h_l, w_l, h, w
 
 
-def _options(mean_ab, C, I_h, g, guide_low=False):
+def _options(mean_ab, C, I_h, g, guide_low=False, coef=None):
     """dgf_options for the call, or None for the defaults."""
     n_I = I_h.shape[1]
     if n_I != C and g is not None:
         raise ValueError("a grey guide (guide channels != output channels) excludes the guidance transform")
     if guide_low and g is None:
         raise ValueError("guide_low applies the guidance transform to I_l: it needs the transform's weights")
-    if mean_ab and n_I == C and not guide_low:
+    if mean_ab and n_I == C and not guide_low and coef is None:
         return None
-    return L.dgf_options(1 if mean_ab else 0, n_I if n_I != C else 0, 1 if guide_low else 0)
+    return L.dgf_options(1 if mean_ab else 0, n_I if n_I != C else 0, 1 if guide_low else 0,
+                         None if coef is None else coef.data_ptr())
+
+
+def coef_buffer(p_l):
+    """A buffer for the coefficients (Abar, bbar) a forward call keeps for its
+    backward (FP32 pairs, N x C x h_l x w_l; see dgf_options.coef)."""
+    N, C, h_l, w_l = p_l.shape
+    return torch.empty((N, C, h_l, w_l, 2), dtype=torch.float32, device=p_l.device)
+
+
+def backward_reuses_coef(p_l, I_h, r, w1=None, mean_ab=True, guide_low=False) -> bool:
+    """Whether the backward skips work given the forward's coefficients
+    (dgf_backward_reuses_coef): the forward then keeps them."""
+    N, C, h_l, w_l, h, w = _sizes(p_l, I_h, grey_ok=True)
+    g = L.dgf_guide(None, None, None, w1.shape[0], 0.2) if w1 is not None else None
+    opt = _options(mean_ab, C, I_h, g, guide_low)
+    return bool(L.dgf_backward_reuses_coef(N, C, h_l, w_l, h, w, int(r), dtype_code(I_h),
+                                           ctypes.byref(g) if g is not None else None,
+                                           ctypes.byref(opt) if opt is not None else None))
+
+
+def _check_coef(coef, p_l):
+    if coef is None:
+        return
+    N, C, h_l, w_l = p_l.shape
+    if (coef.dtype != torch.float32 or not coef.is_cuda or not coef.is_contiguous()
+            or coef.numel() != 2 * N * C * h_l * w_l or coef.device != p_l.device):
+        raise ValueError("coef must be a contiguous float32 CUDA tensor of N x C x h_l x w_l pairs")
 
 
 def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2, out=None,
-               mean_ab=True, guide_low=False):
+               mean_ab=True, guide_low=False, coef=None):
     """O_h of the fast guided filtering layer (Eq. 1-2, box mean of A and b;
     mean_ab=False: A_l, b_l upsampled directly, the layer as printed; a guide
     with another channel count than p_l: its channel mean guides every
     channel; guide_low=True with the transform's weights: G_l = F(I_l)
-    instead of the block mean of F(I_h))."""
+    instead of the block mean of F(I_h); coef (coef_buffer): the call's
+    coefficients are written there for a backward that takes them)."""
     dev = _check(p_l, I_l, I_h, w1, w2, b2)
     N, C, h_l, w_l, h, w = _sizes(p_l, I_h, grey_ok=True)
     dt = dtype_code(I_h)
@@ -101,7 +130,8 @@ def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slo
         raise TypeError("p_l, I_l and I_h must share one dtype")
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
-    opt = _options(mean_ab, C, I_h, g, guide_low)
+    _check_coef(coef, p_l)
+    opt = _options(mean_ab, C, I_h, g, guide_low, coef)
     if out is None:
         out = torch.empty((N, C, h, w), dtype=I_h.dtype, device=I_h.device)
     with torch.cuda.device(dev):
@@ -117,14 +147,16 @@ def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slo
 
 
 def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2,
-                need_p=True, need_Il=True, need_Ih=True, need_w=True, mean_ab=True, guide_low=False):
-    """(dp_l, dI_l, dI_h, (dw1, dw2, db2)) by the library's adjoint kernels."""
+                need_p=True, need_Il=True, need_Ih=True, need_w=True, mean_ab=True, guide_low=False, coef=None):
+    """(dp_l, dI_l, dI_h, (dw1, dw2, db2)) by the library's adjoint kernels;
+    coef: the coefficients gf_forward kept for the same inputs and options."""
     dev = _check(dO_h, p_l, I_l, I_h, w1, w2, b2)
     N, C, h_l, w_l, h, w = _sizes(p_l, I_h, grey_ok=True)
     dt = dtype_code(I_h)
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
-    opt = _options(mean_ab, C, I_h, g, guide_low)
+    _check_coef(coef, p_l)
+    opt = _options(mean_ab, C, I_h, g, guide_low, coef)
     dO_h = dO_h.to(I_h.dtype).contiguous()
     dp = torch.empty_like(p_l) if need_p else None
     dIl = torch.empty_like(I_l) if (need_Il and (g is None or guide_low)) else None
@@ -201,9 +233,10 @@ def gf_forward_batched(images, out=None, mean_ab=True):
     """Uneven batch in one graph-replayed persistent launch per stage.
 
     ``images``: list of dicts with p_l, I_l, I_h (C x h x w tensors, one
-    dtype), r, eps.  Returns the list of O_h.  mean_ab=False: the layer as
-    printed (dgf_forward_batched_opt; every image's kernels on library
-    streams).
+    dtype), r, eps, and optionally coef (coef_buffer of p_l[None]: the
+    image's coefficients are written there).  Returns the list of O_h.
+    mean_ab=False: the layer as printed (dgf_forward_batched_opt; every
+    image's kernels on library streams).
     """
     n = len(images)
     if n == 0:
@@ -218,8 +251,11 @@ def gf_forward_batched(images, out=None, mean_ab=True):
         outs.append(o)
         C, h, w = im["I_h"].shape
         h_l, w_l = im["p_l"].shape[1:]
+        cf = im.get("coef")
+        _check_coef(cf, im["p_l"][None])
         arr[i] = L.dgf_image(im["p_l"].data_ptr(), im["I_l"].data_ptr(), im["I_h"].data_ptr(),
-                             o.data_ptr(), C, h_l, w_l, h, w, int(im["r"]), float(im["eps"]))
+                             o.data_ptr(), C, h_l, w_l, h, w, int(im["r"]), float(im["eps"]),
+                             None if cf is None else cf.data_ptr())
     nb = L.dgf_workspace_size_batched(arr, n, dt)
     if nb == 0:
         raise L.DGFError(1, L.dgf_last_error())
@@ -238,7 +274,8 @@ def gf_backward_batched(images, grads, mean_ab=True):
 
     ``images``: list of dicts with p_l, I_l, I_h (C x h x w tensors, one
     dtype), r, eps, and optionally need_p / need_Il / need_Ih (default
-    True); ``grads``: the matching list of d O_h.  Returns a list of
+    True) and coef (the coefficients the batched forward kept);
+    ``grads``: the matching list of d O_h.  Returns a list of
     (dp_l, dI_l, dI_h) per image, None where not wanted.  mean_ab=False:
     Algorithm 1 as printed (dgf_backward_batched_opt).
     """
@@ -259,10 +296,12 @@ def gf_backward_batched(images, grads, mean_ab=True):
         outs.append((dp, dIl, dIh))
         C, h, w = im["I_h"].shape
         h_l, w_l = im["p_l"].shape[1:]
+        cf = im.get("coef")
+        _check_coef(cf, im["p_l"][None])
         arr[i] = L.dgf_image_grad(R.data_ptr(), im["p_l"].data_ptr(), im["I_l"].data_ptr(), im["I_h"].data_ptr(),
                                   *(None if t is None else t.data_ptr() for t in (dp, dIl, dIh)),
                                   C, h_l, w_l, h, w, int(im["r"]),
-                                  float(im["eps"]))
+                                  float(im["eps"]), None if cf is None else cf.data_ptr())
     nb = L.dgf_workspace_size_batched_backward(arr, n, dt)
     if nb == 0:
         raise L.DGFError(1, L.dgf_last_error())
@@ -282,17 +321,19 @@ class GuidedFilterFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, p_l, I_l, I_h, r, eps):
         p_l, I_l, I_h = p_l.contiguous(), I_l.contiguous(), I_h.contiguous()
-        ctx.save_for_backward(p_l, I_l, I_h)
+        # the coefficients are kept for the backward where it then skips work
+        coef = coef_buffer(p_l) if backward_reuses_coef(p_l, I_h, r) else None
+        ctx.save_for_backward(p_l, I_l, I_h, coef)
         ctx.r, ctx.eps = r, eps
-        return gf_forward(p_l, I_l, I_h, r, eps)
+        return gf_forward(p_l, I_l, I_h, r, eps, coef=coef)
 
     @staticmethod
     def backward(ctx, dO_h):
-        p_l, I_l, I_h = ctx.saved_tensors
+        p_l, I_l, I_h, coef = ctx.saved_tensors
         dp, dIl, dIh, _ = gf_backward(dO_h.contiguous(), p_l, I_l, I_h, ctx.r, ctx.eps,
                                       need_p=ctx.needs_input_grad[0],
                                       need_Il=ctx.needs_input_grad[1],
-                                      need_Ih=ctx.needs_input_grad[2])
+                                      need_Ih=ctx.needs_input_grad[2], coef=coef)
         return dp, dIl, dIh, None, None
 
 
@@ -303,17 +344,18 @@ class GuidedFilterTransformFn(torch.autograd.Function):
     def forward(ctx, p_l, I_h, w1, w2, b2, r, eps, slope):
         p_l, I_h = p_l.contiguous(), I_h.contiguous()
         w1, w2, b2 = w1.contiguous(), w2.contiguous(), b2.contiguous()
-        ctx.save_for_backward(p_l, I_h, w1, w2, b2)
+        coef = coef_buffer(p_l)  # the guided backward always reuses them
+        ctx.save_for_backward(p_l, I_h, w1, w2, b2, coef)
         ctx.r, ctx.eps, ctx.slope = r, eps, slope
-        return gf_forward(p_l, None, I_h, r, eps, w1, w2, b2, slope)
+        return gf_forward(p_l, None, I_h, r, eps, w1, w2, b2, slope, coef=coef)
 
     @staticmethod
     def backward(ctx, dO_h):
-        p_l, I_h, w1, w2, b2 = ctx.saved_tensors
+        p_l, I_h, w1, w2, b2, coef = ctx.saved_tensors
         need_w = any(ctx.needs_input_grad[2:5])
         dp, _, dIh, dws = gf_backward(dO_h.contiguous(), p_l, None, I_h, ctx.r, ctx.eps, w1, w2, b2,
                                       ctx.slope, need_p=ctx.needs_input_grad[0], need_Il=False,
-                                      need_Ih=ctx.needs_input_grad[1], need_w=need_w)
+                                      need_Ih=ctx.needs_input_grad[1], need_w=need_w, coef=coef)
         dw1, dw2, db2 = dws if dws is not None else (None, None, None)
         return dp, dIh, dw1, dw2, db2, None, None, None
 

@@ -166,6 +166,34 @@ def test_batched_and_host_step_options_on_host(lib):
         assert L.dgf_forward_batched_opt(arr, 0, L.DGF_F32, None, 0, None, opt) == 0
 
 
+def test_coefficient_reuse_query_on_host(lib):
+    """dgf_backward_reuses_coef: where the backward's K1 pass computes the coefficients alone."""
+    q = L.dgf_backward_reuses_coef
+    # FP32 r = 1: the K1 strips also write the window statistics K4 reads
+    assert q(4, 3, 512, 512, 2048, 2048, 1, L.DGF_F32, None, None) == 0
+    # 16-bit storage, sliding sums: K1 computes the coefficients alone
+    assert q(2, 3, 540, 960, 2160, 3840, 2, L.DGF_BF16, None, None) == 1
+    assert q(1, 1, 64, 64, 256, 256, 8, L.DGF_F16, None, None) == 1
+    # with a guidance transform: always
+    g = L.dgf_guide(16, 32, 48, 15, 0.2)
+    assert q(8, 3, 256, 256, 2048, 2048, 8, L.DGF_BF16, ctypes.byref(g), None) == 1
+    # a folded grey guide: always
+    grey = L.dgf_options(1, 3, 0)
+    assert q(4, 1, 512, 512, 2048, 2048, 1, L.DGF_F32, None, ctypes.byref(grey)) == 1
+    # invalid sizes
+    assert q(1, 1, 64, 64, 256, 256, -1, L.DGF_F32, None, None) == 0
+    # a misaligned coefficient buffer is refused before anything runs
+    bad = L.dgf_options(1, 0, 0, 4)
+    assert L.dgf_forward_opt(16, 32, 48, 64, 1, 1, 8, 8, 32, 32, 1, 1e-3, L.DGF_F32, None, None, 0, None,
+                             ctypes.byref(bad)) == 1
+    assert "8-byte" in L.dgf_last_error()
+    assert L.dgf_backward_opt(16, 32, 48, 64, 80, 96, 112, None, 1, 1, 8, 8, 32, 32, 1, 1e-3, L.DGF_F32, None,
+                              None, 0, None, ctypes.byref(bad)) == 1
+    img = (L.dgf_image * 1)()
+    img[0] = L.dgf_image(16, 32, 48, 64, 3, 8, 8, 32, 32, 1, 1e-3, 4)
+    assert L.dgf_workspace_size_batched(img, 1, L.DGF_F32) == 0
+
+
 def test_grey_guide_options_on_host(lib):
     """Grey-guide options: workspace sizes and argument checks run on the host."""
     plain = L.dgf_workspace_size(2, 1, 16, 20, 64, 80, 1, L.DGF_BF16, None)

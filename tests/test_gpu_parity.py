@@ -902,3 +902,96 @@ def test_fused_backward_equals_two_kernel_backward(case, ls, k4_form, pin):
     assert_grad(f64(out[1]), rIl, dtype, "dI_l")
     assert_grad(f64(out[2]), rIh, dtype, "dI_h")
     assert L.dgf_device_status() == 0
+
+
+# the forward's coefficients kept for the backward (dgf_options.coef): kind,
+# N, C (output), guide channels, h_l, w_l, h, w, r, eps, dtype, mean_ab, reuses
+KEEP_CASES = [
+    ("photo", 2, 3, 3, 45, 70, 180, 280, 2, 1e-3, BF16, True, True),    # sliding K1/K4
+    ("photo", 1, 2, 2, 40, 36, 320, 288, 8, 1e-3, F16, True, True),     # f = 8, r = 8
+    ("photo", 1, 1, 1, 64, 64, 256, 256, 1, 1e-2, BF16, True, True),
+    ("photo", 2, 3, 3, 40, 50, 160, 200, 1, 1e-3, F32, True, False),    # FP32 r = 1: K13, statistics
+    ("photo", 1, 2, 2, 36, 60, 144, 240, 4, 1e-3, F32, True, True),     # FP32 tiles at r = 4
+    ("photo", 1, 2, 2, 30, 40, 120, 160, 2, 1e-3, BF16, False, False),  # the layer as printed: strips, statistics
+    ("ragged", 1, 2, 2, 37, 53, 150, 211, 1, 1e-3, BF16, True, True),   # non-integer ratio
+    ("photo", 2, 1, 3, 37, 62, 148, 248, 1, 1e-3, BF16, True, True),    # grey guide, folded
+    ("ragged", 1, 2, 3, 37, 53, 150, 211, 1, 1e-3, F16, True, True),    # grey guide, streaming form
+]
+
+
+@pytest.mark.parametrize("case", KEEP_CASES, ids=_ids(KEEP_CASES))
+@pytest.mark.parametrize("pipeline", [False, True], ids=["onestream", "pipeline"])
+def test_kept_coefficients_give_the_same_bits(case, pipeline):
+    kind, N, C, n_in, hl, wl, h, w, r, eps, dtype, mean_ab, reuses = case
+    gsrc = to_storage(make_case(kind, 440 + r, N, n_in, hl, wl, h, w), dtype)
+    psrc = to_storage(make_case(kind, 450 + r, N, C, hl, wl, h, w), dtype)
+    p_l, I_l, I_h = (t.cuda() for t in (psrc["p_l"], gsrc["I_l"], gsrc["I_h"]))
+    R = synth.upstream_grad(15, (N, C, h, w)).to(dtype).cuda()
+    from paper_1803_05619_gb300.layer import backward_reuses_coef, coef_buffer
+    assert backward_reuses_coef(p_l, I_h, r, mean_ab=mean_ab) == reuses
+    L.dgf_set_pipeline(pipeline)
+    try:
+        out = gf_forward(p_l, I_l, I_h, r, eps, mean_ab=mean_ab)
+        ref = gf_backward(R, p_l, I_l, I_h, r, eps, mean_ab=mean_ab)[:3]
+        cf = coef_buffer(p_l)
+        out_k = gf_forward(p_l, I_l, I_h, r, eps, mean_ab=mean_ab, coef=cf)
+        got = gf_backward(R, p_l, I_l, I_h, r, eps, mean_ab=mean_ab, coef=cf)[:3]
+        only_ih = gf_backward(R, p_l, I_l, I_h, r, eps, mean_ab=mean_ab, coef=cf, need_p=False,
+                              need_Il=False)[2]
+        torch.cuda.synchronize()
+    finally:
+        L.dgf_set_pipeline(False)
+    assert torch.equal(out_k, out)
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+    assert torch.equal(only_ih, ref[2])
+    assert L.dgf_device_status() == 0
+
+
+def test_kept_coefficients_guided():
+    # the guided backward takes Abar for K6 from the forward
+    N, hl, wl, f, r, eps = 1, 20, 30, 8, 2, 1e-4
+    st = {k: v.to(BF16).cuda() for k, v in synth.photo_like(73, N, 3, hl, wl, f).items()}
+    wc = {k: v.float().cuda() for k, v in synth.guide_weights(17).items()}
+    R = synth.upstream_grad(18, st["I_h"].shape).to(BF16).cuda()
+    args = (wc["w1"], wc["w2"], wc["b2"], 0.2)
+    from paper_1803_05619_gb300.layer import coef_buffer
+    out = gf_forward(st["p_l"], None, st["I_h"], r, eps, *args)
+    ref = gf_backward(R, st["p_l"], None, st["I_h"], r, eps, *args)
+    cf = coef_buffer(st["p_l"])
+    out_k = gf_forward(st["p_l"], None, st["I_h"], r, eps, *args, coef=cf)
+    got = gf_backward(R, st["p_l"], None, st["I_h"], r, eps, *args, coef=cf)
+    torch.cuda.synchronize()
+    assert torch.equal(out_k, out)
+    for k in (0, 2):
+        assert torch.equal(got[k], ref[k])
+    for a, b in zip(got[3], ref[3]):
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
+def test_kept_coefficients_batched(dtype):
+    # the batched forward writes each image's coefficients to its buffer and
+    # the batched backward takes them (the one-graph form skips those images'
+    # K1 work items): the bits of the calls without them
+    from paper_1803_05619_gb300.layer import coef_buffer
+    specs = synth.mixed_sizes(seed=9, n=5, long_lo=96, long_hi=400)
+    images, grads = [], []
+    for i, s in enumerate(specs):
+        d = to_storage(synth.photo_like(110 + i, 1, 3, s.h_l, s.w_l, s.f), dtype)
+        images.append({"p_l": d["p_l"][0].cuda(), "I_l": d["I_l"][0].cuda(), "I_h": d["I_h"][0].cuda(),
+                       "r": s.r, "eps": 1e-3})
+        grads.append(synth.upstream_grad(120 + i, d["I_h"].shape).to(dtype)[0].cuda())
+    outs = gf_forward_batched(images)
+    ref = gf_backward_batched(images, grads)
+    kept = [dict(im, coef=coef_buffer(im["p_l"][None])) for im in images]
+    kept[1]["coef"] = None  # one image recomputes them
+    outs_k = gf_forward_batched(kept)
+    got = gf_backward_batched(kept, grads)
+    torch.cuda.synchronize()
+    for a, b in zip(outs_k, outs):
+        assert torch.equal(a, b)
+    for ga, gb in zip(got, ref):
+        for a, b in zip(ga, gb):
+            assert torch.equal(a, b)
+    assert L.dgf_device_status() == 0
