@@ -129,7 +129,7 @@ class Step:
         self.keep_coef = keep_coef and L.dgf_backward_reuses_coef(N, C, h_l, w_l, h, w, self.r, self.dt, None,
                                                                  None) == 1
         if self.keep_coef:
-            self.coef = torch.empty(2 * N * C * h_l * w_l, dtype=torch.float32, device=device)
+            self.coef = torch.empty(L.dgf_coef_bytes(N, C, h_l, w_l, None) // 4, dtype=torch.float32, device=device)
             self.opt = L.dgf_options(1, 0, 0, self.coef.data_ptr())
             self.fwd_args += (ctypes.byref(self.opt),)
             self.bwd_args += (ctypes.byref(self.opt),)
@@ -984,7 +984,7 @@ def bench_grey(args, device):
     eps = 1e-4; forward and forward + backward through the library."""
     import synth
     from paper_1803_05619_gb300 import _lib as L
-    from paper_1803_05619_gb300.layer import gf_backward, gf_forward
+    from paper_1803_05619_gb300.layer import backward_reuses_coef, coef_buffer, gf_backward, gf_forward
     N, n_in, C, hl, f, r, eps = 4, 3, 1, 512, 4, 1, 1e-4
     gd = synth.blobs_tone_curve(31, N, n_in, hl, hl, f)
     pd = synth.blobs_tone_curve(32, N, C, hl, hl, f)
@@ -992,12 +992,15 @@ def bench_grey(args, device):
     R = synth.upstream_grad(33, (N, C, hl * f, hl * f)).float().to(device)
     h = w = hl * f
 
+    # the forward keeps Abar, bbar where the backward then skips work (the layer's autograd rule)
+    cf = coef_buffer(p_l) if backward_reuses_coef(p_l, I_h, r) else None
+
     def fwd():
-        gf_forward(p_l, I_l, I_h, r, eps)
+        gf_forward(p_l, I_l, I_h, r, eps, coef=cf)
 
     def step():
-        gf_forward(p_l, I_l, I_h, r, eps)
-        gf_backward(R, p_l, I_l, I_h, r, eps)
+        gf_forward(p_l, I_l, I_h, r, eps, coef=cf)
+        gf_backward(R, p_l, I_l, I_h, r, eps, coef=cf)
 
     steps = max(10, min(args.steps // 10, 200))
     # the streaming form (grey guide formed in the workspace at both
@@ -1050,6 +1053,7 @@ def bench_grey(args, device):
                       "fwd_bwd_frac_of_measured_hbm": round((fwd_b + bwd_b) / (ms_g * 1e-3) / 1e9 / peak, 4)},
             "kernels_avg_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in prof.items()},
             "streaming_form": {"ms_fwd": round(fwd_ms_s, 4), "ms_fwd_bwd": round(ms_s, 4)},
+            "coef_kept": cf is not None,
             "note": "through the Python binding (allocates outputs and workspace per call); the high-res "
                     "kernels form the grey guide from I_h's channels in registers (k2_grey_apply, "
                     "k3_grey_bwd, which also writes dI_h); only the low-res guide and its gradient go "
@@ -1065,17 +1069,20 @@ def bench_guided(args, device):
 
     import synth
     from paper_1803_05619_gb300 import _lib as L
-    from paper_1803_05619_gb300.layer import gf_backward, gf_forward
+    from paper_1803_05619_gb300.layer import coef_buffer, gf_backward, gf_forward
     d = synth.photo_like(21, 8, 3, 256, 256, 8)
     g = {k: v.to(torch.bfloat16).to(device) for k, v in d.items()}
     w = {k: v.float().to(device) for k, v in synth.guide_weights(22).items()}
     R = synth.upstream_grad(23, g["I_h"].shape).to(torch.bfloat16).to(device)
+    # the forward keeps Abar, bbar for the backward, as the layer's autograd function does
+    cf = coef_buffer(g["p_l"], guided=True)
 
-    def step():
-        gf_forward(g["p_l"], None, g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2)
-        gf_backward(R, g["p_l"], None, g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2)
+    def step(coef=cf):
+        gf_forward(g["p_l"], None, g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2, coef=coef)
+        gf_backward(R, g["p_l"], None, g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2, coef=coef)
 
     steps = max(10, min(args.steps // 10, 100))
+    ms_recompute = time_loop(lambda: step(None), steps, max(3, args.warmup // 4), 1, device)
     ms = time_loop(step, steps, max(3, args.warmup // 4), 1, device)
     L.dgf_profile_reset()
     L.dgf_profile_enable(True)
@@ -1090,6 +1097,7 @@ def bench_guided(args, device):
     avg = {k: v[0] / v[1] * 1e3 for k, v in prof.items()}
     out = {"workload": "guided_train_8x3x2048 (BF16, r=8, eps=1e-4, F: 3->15->3)",
            "fwd_bwd_mpix_s": round(pix / (ms * 1e-3) / 1e6, 1), "ms_fwd_bwd": round(ms, 4),
+           "coef_kept": True, "ms_fwd_bwd_recomputing_coef": round(ms_recompute, 4),
            "bound": "alu (FP32 FMA of the 1x1 convolutions)",
            "kernels_avg_us": {k: round(v, 1) for k, v in avg.items()}}
     if "k6_guide_bwd" in avg:
@@ -1109,8 +1117,9 @@ def bench_guided(args, device):
     # (G_l = F(I_l), I_l the block mean of I_h): K5L and K6L replace K5's
     # high-res read and K6's low-res term
     def step_low():
-        gf_forward(g["p_l"], g["I_l"], g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2, guide_low=True)
-        gf_backward(R, g["p_l"], g["I_l"], g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2, guide_low=True)
+        gf_forward(g["p_l"], g["I_l"], g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2, guide_low=True, coef=cf)
+        gf_backward(R, g["p_l"], g["I_l"], g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2, guide_low=True,
+                    coef=cf)
 
     ms_low = time_loop(step_low, steps, max(3, args.warmup // 4), 1, device)
     out["guide_low"] = {"fwd_bwd_mpix_s": round(pix / (ms_low * 1e-3) / 1e6, 1), "ms_fwd_bwd": round(ms_low, 4)}

@@ -313,17 +313,21 @@ void dgf_set_pipeline(int on);
  *             F at low resolution), and dW adds the low-res pixels' terms.
  *   coef = NULL (default): the backward recomputes the coefficients of the
  *             forward (Eq. 1 and the box mean) from its inputs;
- *   coef != NULL: device memory of N x C x h_l x w_l FP32 pairs (Abar, bbar)
- *             (A_l, b_l with mean_ab = 0), 8-byte aligned, owned by the
- *             caller.  dgf_forward_opt writes the call's coefficients there
- *             (with the fused forward kernel then off: the two-kernel form,
- *             the same bits); dgf_backward_opt reads them as the forward's
- *             (the intermediate values Algorithm 1 takes from the forward
- *             pass) and skips its own low-resolution pass where that pass
- *             produces nothing else (dgf_backward_reuses_coef tells when).
- *             They must be what dgf_forward_opt wrote for the same inputs,
- *             options and sizes; the backward's results are then the bits
- *             it gives without them.
+ *   coef != NULL: device memory of dgf_coef_bytes(...) bytes, 256-byte
+ *             aligned, owned by the caller: N x C x h_l x w_l FP32 pairs
+ *             (Abar, bbar) (A_l, b_l with mean_ab = 0) and, with a guidance
+ *             transform, from the next 256-byte boundary the low-res guide
+ *             G_l (N x 3 x h_l x w_l FP32).  dgf_forward_opt writes the
+ *             call's values there (with the fused forward kernel then off:
+ *             the two-kernel form, the same bits); dgf_backward_opt reads
+ *             them as the forward's (the intermediate values Algorithm 1
+ *             takes from the forward pass) and skips the passes that would
+ *             only recompute them: its low-resolution K1 pass where that
+ *             pass produces nothing else, and with a guidance transform also
+ *             the guide pass K5 (dgf_backward_reuses_coef tells when).  They
+ *             must be what dgf_forward_opt wrote for the same inputs,
+ *             weights, options and sizes; the backward's results are then
+ *             the bits it gives without them.
  */
 typedef struct {
     int mean_ab;
@@ -331,6 +335,11 @@ typedef struct {
     int guide_low;
     void* coef;
 } dgf_options;
+
+/* Bytes of the buffer dgf_options.coef points to for these sizes (g: with
+ * a guidance transform, which adds the low-res guide); 0 for invalid sizes.
+ * Pure host function. */
+size_t dgf_coef_bytes(int N, int C, int h_l, int w_l, const dgf_guide* g);
 
 /* 1 when dgf_backward_opt with these sizes and options (coef aside) skips
  * work given the forward's coefficients (opt->coef): always with a guidance

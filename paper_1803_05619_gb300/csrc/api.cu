@@ -1100,6 +1100,13 @@ size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r, d
     return layout(N, C, h_l, w_l, g != nullptr, (size_t)N * C * h * w).total;
 }
 
+// The kept values of a call (dgf_options.coef): N C h_l w_l (Abar, bbar)
+// pairs, then from the next 256-byte boundary the low-res guide of a
+// guidance transform (N x 3 planes, FP32; C = 3 there).
+static float* kept_guide(float2* coef, int planes, int h_l, int w_l) {
+    return reinterpret_cast<float*>(reinterpret_cast<char*>(coef) + align256((size_t)planes * h_l * w_l * sizeof(float2)));
+}
+
 static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
                                int w_l, int h, int w, int r, float eps, dgf_dtype dt, const dgf_guide* g,
                                void* workspace, size_t ws_bytes, dgf_stream_t stream, bool mean_ab,
@@ -1202,7 +1209,8 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
         if ((e = pipe_join(*pp, s)) != cudaSuccess) return cuda_fail(e, "pipeline join");
         return DGF_OK;
     }
-    float* G_l = reinterpret_cast<float*>(ws + lay.gl);
+    // G_l goes to the caller's buffer after the coefficients when it keeps them
+    float* G_l = coef_out != nullptr ? kept_guide(coef_out, planes, h_l, w_l) : reinterpret_cast<float*>(ws + lay.gl);
     // with G_l the block mean of F(I_h), K5 also keeps F(I_h) in FP32 and K2
     // reads that guide instead of evaluating F again per pixel
     float* G_h = guide_low ? nullptr : reinterpret_cast<float*>(ws + lay.gh);
@@ -1448,8 +1456,9 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
         return backward_pipelined(dt, dO_h, p_l, I_l, I_h, dp_l, dI_l, dI_h, planes, h_l, w_l, h, w, r, eps, p, ws, lay,
                                   s, G, coef_in);
     }
-    // with the guidance transform
-    float* G_l = reinterpret_cast<float*>(ws + lay.gl);
+    // with the guidance transform; G_l is the forward's when it kept it
+    float* G_l = coef_in != nullptr ? kept_guide(const_cast<float2*>(coef_in), planes, h_l, w_l)
+                                    : reinterpret_cast<float*>(ws + lay.gl);
     float* dG_l = reinterpret_cast<float*>(ws + lay.dgl);
     float* partials = reinterpret_cast<float*>(ws + lay.partials);
     const bool need_hi = dI_h != nullptr || dW != nullptr;
@@ -1460,7 +1469,9 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
         return fail(DGF_ERR_UNSUPPORTED, "guidance transform needs 16-byte aligned dO_h, I_h, dI_h");
     e = guide_upload(g->w1, g->w2, g->b2, g->hidden, s);
     if (e != cudaSuccess) return cuda_fail(e, "guide weights");
-    if (guide_low)
+    if (coef_in != nullptr)
+        e = cudaSuccess;  // G_l kept by the forward
+    else if (guide_low)
         e = L.run("k5_guide_low", [&] { return launch_k5_low(dt, I_l, G_l, N, h_l, w_l, g->slope, s); });
     else
         e = L.run("k5_guide_down", [&] { return launch_k5(dt, I_h, G_l, N, h_l, w_l, h, w, p.F, g->slope, s); });
@@ -1611,11 +1622,11 @@ static dgf_status forward_grey(const void* p_l, const void* I_l, const void* I_h
                         mean_ab, false, true, coef_out);
 }
 
-// opt->coef as the call's coefficient buffer: NULL, or 8-byte aligned
+// opt->coef as the call's buffer of kept values: NULL, or 256-byte aligned
 static dgf_status opt_coef(const dgf_options* opt, float2*& coef) {
     coef = opt != nullptr ? static_cast<float2*>(opt->coef) : nullptr;
-    if (reinterpret_cast<uintptr_t>(coef) % alignof(float2) != 0)
-        return fail(DGF_ERR_INVALID, "coef must be 8-byte aligned");
+    if (reinterpret_cast<uintptr_t>(coef) % 256 != 0)
+        return fail(DGF_ERR_INVALID, "coef must be 256-byte aligned");
     return DGF_OK;
 }
 
@@ -1756,6 +1767,12 @@ size_t dgf_workspace_size_opt(int N, int C, int h_l, int w_l, int h, int w, int 
     if (n_in == 0) return layout(N, C, h_l, w_l, g != nullptr, (size_t)N * C * h * w).total;
     if (check_grey(n_in, N, g) != DGF_OK) return 0;
     return grey_layout(N, C, h_l, w_l, h, w, dt).total;
+}
+
+size_t dgf_coef_bytes(int N, int C, int h_l, int w_l, const dgf_guide* g) {
+    if (N < 0 || C < 1 || h_l < 1 || w_l < 1 || (long long)N * C > 65535) return 0;
+    const size_t lo = (size_t)N * C * h_l * w_l;
+    return g == nullptr ? lo * sizeof(float2) : align256(lo * sizeof(float2)) + lo * sizeof(float);
 }
 
 int dgf_backward_reuses_coef(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt, const dgf_guide* g,

@@ -88,11 +88,14 @@ def _options(mean_ab, C, I_h, g, guide_low=False, coef=None):
                          None if coef is None else coef.data_ptr())
 
 
-def coef_buffer(p_l):
-    """A buffer for the coefficients (Abar, bbar) a forward call keeps for its
-    backward (FP32 pairs, N x C x h_l x w_l; see dgf_options.coef)."""
+def coef_buffer(p_l, guided=False):
+    """A buffer for the values a forward call keeps for its backward: the
+    coefficients (Abar, bbar) and, with the guidance transform (guided=True),
+    the low-res guide (dgf_options.coef, dgf_coef_bytes)."""
     N, C, h_l, w_l = p_l.shape
-    return torch.empty((N, C, h_l, w_l, 2), dtype=torch.float32, device=p_l.device)
+    g = L.dgf_guide(None, None, None, 1, 0.2) if guided else None
+    nb = L.dgf_coef_bytes(N, C, h_l, w_l, ctypes.byref(g) if g is not None else None)
+    return torch.empty((nb + 3) // 4, dtype=torch.float32, device=p_l.device)
 
 
 def backward_reuses_coef(p_l, I_h, r, w1=None, mean_ab=True, guide_low=False) -> bool:
@@ -106,13 +109,16 @@ def backward_reuses_coef(p_l, I_h, r, w1=None, mean_ab=True, guide_low=False) ->
                                            ctypes.byref(opt) if opt is not None else None))
 
 
-def _check_coef(coef, p_l):
+def _check_coef(coef, p_l, guided=False):
     if coef is None:
         return
     N, C, h_l, w_l = p_l.shape
+    g = L.dgf_guide(None, None, None, 1, 0.2) if guided else None
+    nb = L.dgf_coef_bytes(N, C, h_l, w_l, ctypes.byref(g) if g is not None else None)
     if (coef.dtype != torch.float32 or not coef.is_cuda or not coef.is_contiguous()
-            or coef.numel() != 2 * N * C * h_l * w_l or coef.device != p_l.device):
-        raise ValueError("coef must be a contiguous float32 CUDA tensor of N x C x h_l x w_l pairs")
+            or 4 * coef.numel() < nb or coef.device != p_l.device or coef.data_ptr() % 256 != 0):
+        raise ValueError("coef must be a contiguous, 256-byte aligned float32 CUDA tensor of "
+                         "dgf_coef_bytes bytes (coef_buffer)")
 
 
 def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slope=0.2, out=None,
@@ -130,7 +136,7 @@ def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slo
         raise TypeError("p_l, I_l and I_h must share one dtype")
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
-    _check_coef(coef, p_l)
+    _check_coef(coef, p_l, g is not None)
     opt = _options(mean_ab, C, I_h, g, guide_low, coef)
     if out is None:
         out = torch.empty((N, C, h, w), dtype=I_h.dtype, device=I_h.device)
@@ -155,7 +161,7 @@ def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=No
     dt = dtype_code(I_h)
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
-    _check_coef(coef, p_l)
+    _check_coef(coef, p_l, g is not None)
     opt = _options(mean_ab, C, I_h, g, guide_low, coef)
     dO_h = dO_h.to(I_h.dtype).contiguous()
     dp = torch.empty_like(p_l) if need_p else None
@@ -344,7 +350,7 @@ class GuidedFilterTransformFn(torch.autograd.Function):
     def forward(ctx, p_l, I_h, w1, w2, b2, r, eps, slope):
         p_l, I_h = p_l.contiguous(), I_h.contiguous()
         w1, w2, b2 = w1.contiguous(), w2.contiguous(), b2.contiguous()
-        coef = coef_buffer(p_l)  # the guided backward always reuses them
+        coef = coef_buffer(p_l, guided=True)  # the guided backward always reuses them
         ctx.save_for_backward(p_l, I_h, w1, w2, b2, coef)
         ctx.r, ctx.eps, ctx.slope = r, eps, slope
         return gf_forward(p_l, None, I_h, r, eps, w1, w2, b2, slope, coef=coef)

@@ -186,7 +186,11 @@ def test_coefficient_reuse_query_on_host(lib):
     bad = L.dgf_options(1, 0, 0, 4)
     assert L.dgf_forward_opt(16, 32, 48, 64, 1, 1, 8, 8, 32, 32, 1, 1e-3, L.DGF_F32, None, None, 0, None,
                              ctypes.byref(bad)) == 1
-    assert "8-byte" in L.dgf_last_error()
+    assert "aligned" in L.dgf_last_error()
+    # the kept values: the pairs, and with a guidance transform the low-res guide after them
+    assert L.dgf_coef_bytes(2, 3, 10, 13, None) == 2 * 3 * 10 * 13 * 8
+    assert L.dgf_coef_bytes(2, 3, 10, 13, ctypes.byref(g)) == 6400 + 2 * 3 * 10 * 13 * 4
+    assert L.dgf_coef_bytes(2, 0, 10, 13, None) == 0
     assert L.dgf_backward_opt(16, 32, 48, 64, 80, 96, 112, None, 1, 1, 8, 8, 32, 32, 1, 1e-3, L.DGF_F32, None,
                               None, 0, None, ctypes.byref(bad)) == 1
     img = (L.dgf_image * 1)()

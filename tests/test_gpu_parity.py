@@ -948,23 +948,34 @@ def test_kept_coefficients_give_the_same_bits(case, pipeline):
     assert L.dgf_device_status() == 0
 
 
-def test_kept_coefficients_guided():
-    # the guided backward takes Abar for K6 from the forward
-    N, hl, wl, f, r, eps = 1, 20, 30, 8, 2, 1e-4
-    st = {k: v.to(BF16).cuda() for k, v in synth.photo_like(73, N, 3, hl, wl, f).items()}
+@pytest.mark.parametrize("guide_low", [False, True], ids=["blockmean", "guide_low"])
+@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
+def test_kept_coefficients_guided(dtype, guide_low):
+    # the guided backward takes Abar (for K6) and G_l (for K4) from the
+    # forward: no K1 and no guide pass
+    N, hl, wl, f, r, eps = 2, 20, 30, 4, 2, 1e-4
+    st = {k: v.to(dtype).cuda() for k, v in synth.photo_like(73, N, 3, hl, wl, f).items()}
     wc = {k: v.float().cuda() for k, v in synth.guide_weights(17).items()}
-    R = synth.upstream_grad(18, st["I_h"].shape).to(BF16).cuda()
+    R = synth.upstream_grad(18, st["I_h"].shape).to(dtype).cuda()
     args = (wc["w1"], wc["w2"], wc["b2"], 0.2)
+    I_l = st["I_l"] if guide_low else None
     from paper_1803_05619_gb300.layer import coef_buffer
-    out = gf_forward(st["p_l"], None, st["I_h"], r, eps, *args)
-    ref = gf_backward(R, st["p_l"], None, st["I_h"], r, eps, *args)
-    cf = coef_buffer(st["p_l"])
-    out_k = gf_forward(st["p_l"], None, st["I_h"], r, eps, *args, coef=cf)
-    got = gf_backward(R, st["p_l"], None, st["I_h"], r, eps, *args, coef=cf)
-    torch.cuda.synchronize()
+    out = gf_forward(st["p_l"], I_l, st["I_h"], r, eps, *args, guide_low=guide_low)
+    ref = gf_backward(R, st["p_l"], I_l, st["I_h"], r, eps, *args, guide_low=guide_low)
+    cf = coef_buffer(st["p_l"], guided=True)
+    out_k = gf_forward(st["p_l"], I_l, st["I_h"], r, eps, *args, guide_low=guide_low, coef=cf)
+    L.dgf_profile_reset()
+    L.dgf_profile_enable(True)
+    try:
+        got = gf_backward(R, st["p_l"], I_l, st["I_h"], r, eps, *args, guide_low=guide_low, coef=cf)
+        torch.cuda.synchronize()
+        names = set(L.dgf_profile_read().keys())
+    finally:
+        L.dgf_profile_enable(False)
+    assert not names & {"k1_lowres_coef", "k5_guide_down", "k5_guide_low"}, names
     assert torch.equal(out_k, out)
-    for k in (0, 2):
-        assert torch.equal(got[k], ref[k])
+    for k in (0, 1, 2):
+        assert (got[k] is None and ref[k] is None) or torch.equal(got[k], ref[k])
     for a, b in zip(got[3], ref[3]):
         assert torch.equal(a, b)
 
