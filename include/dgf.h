@@ -251,6 +251,15 @@ void dgf_set_lowres_slide(int on);
  * rounding (the folded form keeps the sum over output channels in FP32). */
 void dgf_set_grey_fold(int on);
 
+/* Allows (1, default) or forbids (0) programmatic launches: the fused
+ * forward K12, the fused backward K13 and the low-resolution backward from
+ * saved statistics are launched so that they may start while the previous
+ * kernel of their stream finishes (CUDA programmatic dependent launch); each
+ * waits, before its first memory access, until that kernel has completed and
+ * its writes are visible, so only launch latency and the ramp of the grid
+ * overlap.  Results are identical either way.  No counterpart in the paper. */
+void dgf_set_programmatic_launch(int on);
+
 /* Allows (1, default) or forbids (0) the one-graph form of
  * dgf_backward_batched; forbidden, every batch runs the per-image chains.
  * Both give the same bits. */
@@ -432,7 +441,8 @@ dgf_status dgf_backward_batched_opt(const dgf_image_grad* imgs, int n, dgf_dtype
 /*
  * Tile-shape autotuner.  When enabled (here, or DGF_AUTOTUNE=1 in the
  * environment), the first call for a new key (kernel, storage type, radius
- * or factor, vector width) times each candidate tile shape on that call's
+ * or factor, vector width, guide type, and the size class of the low-res
+ * plane: under 128 x 128 pixels or larger) times each candidate tile shape on that call's
  * own buffers and keeps the fastest; that call synchronises its stream and
  * must not be under stream capture (tuning is skipped while capturing).
  * Chosen shapes are used by every later call with the same key, tuned or
@@ -450,7 +460,8 @@ void dgf_autotune_reset(void);
 
 /*
  * Pin one entry of the autotuner's table, as if tuning had chosen it: later
- * calls with that key use the shape (whether tuning is enabled or not).
+ * calls with that key use the shape (whether tuning is enabled or not), for
+ * planes of both size classes.
  * Keys and shapes as the table stores them:
  *   kind 1 (K1 low-res coefficients) and 4 (K4 low-res backward): r = radius,
  *     F = vec = 0; guide_f32 = 1 for the guidance-transform path (FP32 guide);

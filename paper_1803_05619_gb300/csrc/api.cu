@@ -265,9 +265,13 @@ struct Plan {
     bool k13 = false;      // backward K1 + K3 as the fused K13 kernel
     bool k13_ok = false;
     int k13_ls = 16;       // K13: low-res rows per segment
+    int sc = 0;            // the plane's size class in the autotuner's keys
 };
 
 static bool g_fused_allowed = true;
+
+std::atomic<bool> g_pdl{true};
+bool pdl_allowed() { return g_pdl.load(std::memory_order_relaxed); }
 
 static bool aligned_to(std::initializer_list<const void*> ptrs, int bytes) {
     for (const void* p : ptrs)
@@ -384,6 +388,7 @@ static void low_to_table(const LowCfg& c, int& a, int& b) {
 static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool gf32,
                       std::initializer_list<const void*> hires_ptrs, bool mean_ab = true) {
     Plan p;
+    p.sc = tune_size_class(h_l, w_l);
     p.F = integer_factor(h_l, w_l, h, w);
     p.vec = pick_vec(dt, w, hires_ptrs);
     pick_lowres_tiles(r, p);
@@ -400,22 +405,22 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     // a table entry (tuned, pinned or read from a cache file) is used only if
     // it is one of the shapes the kernels are built for
     if (low_fast_radius(r)) {
-        if (tune_lookup(TuneKey{1, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b)) {
+        if (tune_lookup(TuneKey{1, (int)dt, r, 0, 0, gf32 ? 1 : 0, p.sc}, a, b)) {
             const LowCfg c = low_from_table(a, b);
             if (in_candidates(c, r, false, dt)) p.k1 = c;
         }
-        if (tune_lookup(TuneKey{4, (int)dt, r, 0, 0, gf32 ? 1 : 0}, a, b)) {
+        if (tune_lookup(TuneKey{4, (int)dt, r, 0, 0, gf32 ? 1 : 0, p.sc}, a, b)) {
             const LowCfg c = low_from_table(a, b);
             if (in_candidates(c, r, true, dt)) p.k4 = c;
         }
     }
-    if (tune_lookup(TuneKey{2, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256) {
+    if (tune_lookup(TuneKey{2, (int)dt, 0, p.F, p.vec, 0, p.sc}, a, b) && a >= 1 && a <= 256) {
         if (p.k2_strip)
             p.k2_ls = a;
         else
             p.k2_th = a;
     }
-    if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b) && a >= 1 && a <= 256)
+    if (p.k3_fast && tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0, p.sc}, a, b) && a >= 1 && a <= 256)
         p.k3_lth = a;
     // fused forward: plain guide, box mean of A, b, r in {1, 2}, a factor with
     // one low-res cell per lane; a table entry a = 0 means the tuner found
@@ -427,7 +432,7 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     // untuned default: fused at r = 1, where it measured faster than K1 + K2
     // on large images too (at r = 2 its redundant K1 columns cost more)
     p.k12 = p.k12_ok && r == 1;
-    if (p.k12_ok && tune_lookup(TuneKey{5, (int)dt, r, p.F, 0, 0}, a, b) && a >= 0 && a <= 256) {
+    if (p.k12_ok && tune_lookup(TuneKey{5, (int)dt, r, p.F, 0, 0, p.sc}, a, b) && a >= 0 && a <= 256) {
         p.k12 = a > 0;
         if (a > 0) p.k12_ls = a;
     }
@@ -436,7 +441,7 @@ static Plan make_plan(dgf_dtype dt, int h_l, int w_l, int h, int w, int r, bool 
     p.k13_ok = g_fused_allowed && !gf32 && mean_ab && p.k3_fast && k13_supported(dt, r, p.F, p.vec) &&
                aligned_to(hires_ptrs, 16) && p.k1.fast == 2;
     p.k13 = p.k13_ok && r == 1;
-    if (p.k13_ok && tune_lookup(TuneKey{6, (int)dt, r, p.F, p.vec, 0}, a, b) && a >= 0 && a <= 256) {
+    if (p.k13_ok && tune_lookup(TuneKey{6, (int)dt, r, p.F, p.vec, 0, p.sc}, a, b) && a >= 0 && a <= 256) {
         p.k13 = a > 0;
         if (a > 0) p.k13_ls = a;
     }
@@ -707,7 +712,7 @@ static dgf_status check_ws(void* ws, size_t ws_bytes, size_t need) {
 // launch that follows overwrites every output) and records the fastest.
 static void tune_k1(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes, int h_l,
                     int w_l, int r, float eps, cudaStream_t s, Plan& p) {
-    TuneKey key{1, (int)dt, r, 0, 0, gf32 ? 1 : 0};
+    TuneKey key{1, (int)dt, r, 0, 0, gf32 ? 1 : 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
     float best = 1e30f;
@@ -735,7 +740,7 @@ static void tune_k1(dgf_dtype dt, bool gf32, const void* G, const void* P, float
 static void tune_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP, void* dG,
                     int planes, int h_l, int w_l, int r, float eps, cudaStream_t s, Plan& p,
                     const float4* stats = nullptr) {
-    TuneKey key{4, (int)dt, r, 0, 0, gf32 ? 1 : 0};
+    TuneKey key{4, (int)dt, r, 0, 0, gf32 ? 1 : 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
     float best = 1e30f;
@@ -759,7 +764,7 @@ static void tune_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const
 
 static void tune_k2(dgf_dtype dt, const float2* coef, const void* in, void* out, int planes, int h_l, int w_l,
                     int h, int w, cudaStream_t s, Plan& p) {
-    TuneKey key{2, (int)dt, 0, p.F, p.vec, 0};
+    TuneKey key{2, (int)dt, 0, p.F, p.vec, 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
     float best = 1e30f;
@@ -787,7 +792,7 @@ static void tune_k2(dgf_dtype dt, const float2* coef, const void* in, void* out,
 static void tune_k3(dgf_dtype dt, const float2* coef, const void* R, const void* G, void* dG, float2* dcoef,
                     int planes, int h_l, int w_l, int h, int w, cudaStream_t s, Plan& p) {
     if (!p.k3_fast) return;
-    TuneKey key{3, (int)dt, 0, p.F, p.vec, 0};
+    TuneKey key{3, (int)dt, 0, p.F, p.vec, 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
     float best = 1e30f;
@@ -811,14 +816,15 @@ static void tune_k3(dgf_dtype dt, const float2* coef, const void* R, const void*
 }
 
 // Whether the autotuner's table already holds the backward's shapes for this key.
-static bool tune_has_low(dgf_dtype dt, int r, const Plan&) {
+static bool tune_has_low(dgf_dtype dt, int r, const Plan& p) {
     int a, b;
     if (!low_fast_radius(r)) return true;
-    return tune_lookup(TuneKey{1, (int)dt, r, 0, 0, 0}, a, b) && tune_lookup(TuneKey{4, (int)dt, r, 0, 0, 0}, a, b);
+    return tune_lookup(TuneKey{1, (int)dt, r, 0, 0, 0, p.sc}, a, b) &&
+           tune_lookup(TuneKey{4, (int)dt, r, 0, 0, 0, p.sc}, a, b);
 }
 static bool tune_has_k3(dgf_dtype dt, const Plan& p) {
     int a, b;
-    return !p.k3_fast || tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0}, a, b);
+    return !p.k3_fast || tune_lookup(TuneKey{3, (int)dt, 0, p.F, p.vec, 0, p.sc}, a, b);
 }
 
 // The fused forward against the two-kernel forward with its tuned shapes:
@@ -826,7 +832,7 @@ static bool tune_has_k3(dgf_dtype dt, const Plan& p) {
 static void tune_k12(dgf_dtype dt, const void* G, const void* P, float2* coef, const void* in, void* out,
                      int planes, int h_l, int w_l, int h, int w, int r, float eps, cudaStream_t s, Plan& p) {
     if (!p.k12_ok) return;
-    TuneKey key{5, (int)dt, r, p.F, 0, 0};
+    TuneKey key{5, (int)dt, r, p.F, 0, 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
     size_t landing = 0;
@@ -860,7 +866,7 @@ static void tune_k13(dgf_dtype dt, const void* G, const void* P, float2* coef, f
                      const void* Gh, void* dGh, float2* dcoef, int planes, int h_l, int w_l, int h, int w, int r,
                      float eps, const K3Maps& maps, cudaStream_t s, Plan& p) {
     if (!p.k13_ok) return;
-    TuneKey key{6, (int)dt, r, p.F, p.vec, 0};
+    TuneKey key{6, (int)dt, r, p.F, p.vec, 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
     size_t landing = 0;
@@ -2590,6 +2596,7 @@ extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
 extern "C" void dgf_set_fused(int on) { g_fused_allowed = on != 0; }
 extern "C" void dgf_set_lowres_slide(int on) { g_slide_allowed = on != 0; }
 extern "C" void dgf_set_grey_fold(int on) { g_grey_fold = on != 0; }
+extern "C" void dgf_set_programmatic_launch(int on) { g_pdl = on != 0; }
 extern "C" void dgf_set_batched_graph_backward(int on) { g_batched_graph_bwd = on != 0; }
 
 extern "C" void dgf_set_pipeline(int on) { g_pipeline = on != 0; }
@@ -2604,7 +2611,9 @@ extern "C" dgf_status dgf_autotune_pin(int kind, dgf_dtype dt, int r, int F, int
     if (kind < 1 || kind > 6 || (int)dt < 0 || (int)dt > 2 || r < 0 || F < 0 || vec < 0 || a < 0 ||
         (a == 0 && kind < 5) || a > 4096 || b < bmin || b > 4096 || (guide_f32 != 0 && guide_f32 != 1))
         return fail(DGF_ERR_INVALID, "autotune_pin: bad key or shape");
-    tune_store(TuneKey{kind, (int)dt, r, F, vec, guide_f32}, a, b);
+    // a pin serves planes of both size classes
+    tune_store(TuneKey{kind, (int)dt, r, F, vec, guide_f32, 0}, a, b);
+    tune_store(TuneKey{kind, (int)dt, r, F, vec, guide_f32, 1}, a, b);
     return DGF_OK;
 }
 

@@ -2,7 +2,7 @@
 // factor, vector width, guide type) it times every candidate shape on the
 // call's own buffers with CUDA events and keeps the fastest.  The choice is
 // cached in memory and, when DGF_TUNE_CACHE names a file, persisted there
-// as text lines "version/device kind dt r F vec gf32 a b": keyed also by the
+// as text lines "version/device kind dt r F vec gf32 sc a b": keyed also by the
 // device name and by the cache version of this library (kTuneVersion, raised
 // whenever the kernels' shapes or their encoding change), so entries written
 // by another build or for another GPU are never used.
@@ -23,11 +23,12 @@ namespace dgf {
 namespace {
 
 std::mutex g_mu;
-std::map<std::tuple<std::string, int, int, int, int, int, int>, std::pair<int, int>> g_table;
+using FullKey = std::tuple<std::string, int, int, int, int, int, int, int>;
+std::map<FullKey, std::pair<int, int>> g_table;
 bool g_loaded = false;
 int g_enabled = -1;  // -1: read DGF_AUTOTUNE on first use
 
-constexpr const char* kTuneVersion = "dgf2";
+constexpr const char* kTuneVersion = "dgf3";
 
 std::string device_name() {
     int dev = 0;
@@ -45,17 +46,17 @@ std::string device_name() {
 
 // a table entry the plan code can read: shapes are positive except b of the
 // low-res kernels (kinds 1, 4), where b < 0 names the sliding strips
-bool entry_ok(int kind, int dt, int r, int F, int vec, int gf32, int a, int b) {
+bool entry_ok(int kind, int dt, int r, int F, int vec, int gf32, int sc, int a, int b) {
     if (kind < 1 || kind > 6 || dt < 0 || dt > 2 || r < 0 || r > 64 || F < 0 || F > 64 || vec < 0 || vec > 64)
         return false;
-    if (gf32 != 0 && gf32 != 1) return false;
+    if ((gf32 != 0 && gf32 != 1) || (sc != 0 && sc != 1)) return false;
     if (a < 0 || a > 4096 || (a == 0 && kind < 5)) return false;
     const int bmin = (kind == 1 || kind == 4) ? -8 : 0;
     return b >= bmin && b <= 4096;
 }
 
-std::tuple<std::string, int, int, int, int, int, int> full_key(const TuneKey& k) {
-    return std::make_tuple(device_name(), k.kind, k.dt, k.r, k.F, k.vec, k.gf32);
+FullKey full_key(const TuneKey& k) {
+    return std::make_tuple(device_name(), k.kind, k.dt, k.r, k.F, k.vec, k.gf32, k.sc);
 }
 
 void load_locked() {
@@ -66,16 +67,16 @@ void load_locked() {
     FILE* f = fopen(path, "r");
     if (f == nullptr) return;
     char line[512], name[256];
-    int kind, dt, r, F, vec, gf32, a, b;
+    int kind, dt, r, F, vec, gf32, sc, a, b;
     // malformed, out-of-range or truncated lines are skipped one by one: a
     // corrupt cache only costs a re-tune of the keys it held; lines of
     // another version or device stay in the file but never match a key
     while (fgets(line, sizeof line, f) != nullptr) {
         char tail = 0;
-        const int n = sscanf(line, "%255s %d %d %d %d %d %d %d %d %c", name, &kind, &dt, &r, &F, &vec, &gf32, &a,
-                             &b, &tail);
-        if (n != 9 || !entry_ok(kind, dt, r, F, vec, gf32, a, b)) continue;
-        g_table[std::make_tuple(std::string(name), kind, dt, r, F, vec, gf32)] = {a, b};
+        const int n = sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %c", name, &kind, &dt, &r, &F, &vec, &gf32,
+                             &sc, &a, &b, &tail);
+        if (n != 10 || !entry_ok(kind, dt, r, F, vec, gf32, sc, a, b)) continue;
+        g_table[std::make_tuple(std::string(name), kind, dt, r, F, vec, gf32, sc)] = {a, b};
     }
     fclose(f);
 }
@@ -88,8 +89,9 @@ void save_locked() {
     if (f == nullptr) return;
     for (auto& kv : g_table) {
         const auto& k = kv.first;
-        fprintf(f, "%s %d %d %d %d %d %d %d %d\n", std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k),
-                std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), kv.second.first, kv.second.second);
+        fprintf(f, "%s %d %d %d %d %d %d %d %d %d\n", std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k),
+                std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k), kv.second.first,
+                kv.second.second);
     }
     fclose(f);
     rename(tmp.c_str(), path);

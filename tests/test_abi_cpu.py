@@ -254,16 +254,18 @@ def test_autotune_cache_skips_corrupt_and_foreign_lines(lib, tmp_path):
     import subprocess
     import sys
     cache = tmp_path / "tune.txt"
-    me = "dgf2/unknown"  # no device in the subprocess: the device name is "unknown"
+    me = "dgf3/unknown"  # no device in the subprocess: the device name is "unknown"
     cache.write_text(
-        f"{me} 1 1 2 0 0 0 16 -4\n"        # sliding K1 strips, BF16, r = 2: used
+        f"{me} 1 1 2 0 0 0 0 16 -4\n"        # sliding K1 strips, BF16, r = 2, large planes: used
         "garbage that is not an entry\n"
-        f"{me} 2 0 0 4 4 0 12 0\n"         # K2 strip segments: used
-        f"{me} 3 0 0 4 4 0 99999 0\n"      # out of range: skipped
-        f"{me} 1 1 2 0 0 0 16\n"           # truncated: skipped
-        f"{me} 4 1 2 0 0 0 16 -9\n"        # no such column width: skipped
-        "dgf1/unknown 1 1 1 0 0 0 32 0\n"  # another library version: never used
-        f"{me} 5 0 1 4 0 0 8 0 extra\n"    # trailing junk: skipped
+        f"{me} 2 0 0 4 4 0 1 12 0\n"         # K2 strip segments, small planes: used
+        f"{me} 3 0 0 4 4 0 0 99999 0\n"      # out of range: skipped
+        f"{me} 1 1 2 0 0 0 0 16\n"           # truncated: skipped
+        f"{me} 4 1 2 0 0 0 0 16 -9\n"        # no such column width: skipped
+        f"{me} 4 1 2 0 0 0 2 16 -4\n"        # no such size class: skipped
+        "dgf2/unknown 1 1 1 0 0 0 32 0\n"    # the previous line format: skipped
+        "dgf1/unknown 1 1 1 0 0 0 0 32 0\n"  # another library version: kept, never used
+        f"{me} 5 0 1 4 0 0 0 8 0 extra\n"    # trailing junk: skipped
         "\x00\xff\n")
     code = ("import ctypes, sys; L = ctypes.CDLL(sys.argv[1]); n = L.dgf_autotune_entries(); "
             "pin = int(sys.argv[2]); st = L.dgf_autotune_pin(6, 1, 1, 8, 8, 0, 16, 0) if pin else 0; "
@@ -272,9 +274,11 @@ def test_autotune_cache_skips_corrupt_and_foreign_lines(lib, tmp_path):
     out = subprocess.run([sys.executable, "-c", code, B.OUT, "1"], capture_output=True, text=True, env=env,
                          timeout=120)
     assert out.returncode == 0, out.stderr
-    assert out.stdout.split() == ["2", "0", "3"]
+    # a pin serves both size classes: two entries
+    assert out.stdout.split() == ["2", "0", "4"]
     text = cache.read_text()
-    assert "dgf1/unknown 1 1 1 0 0 0 32 0" in text and f"{me} 6 1 1 8 8 0 16 0" in text
+    assert "dgf1/unknown 1 1 1 0 0 0 0 32 0" in text and "dgf2/unknown" not in text
+    assert f"{me} 6 1 1 8 8 0 0 16 0" in text and f"{me} 6 1 1 8 8 0 1 16 0" in text
     out = subprocess.run([sys.executable, "-c", code, B.OUT, "0"], capture_output=True, text=True, env=env,
                          timeout=120)
-    assert out.stdout.split() == ["3", "0", "3"]
+    assert out.stdout.split() == ["4", "0", "4"]
