@@ -251,15 +251,6 @@ void dgf_set_lowres_slide(int on);
  * rounding (the folded form keeps the sum over output channels in FP32). */
 void dgf_set_grey_fold(int on);
 
-/* Allows (1, default) or forbids (0) programmatic launches: the fused
- * forward K12, the fused backward K13 and the low-resolution backward from
- * saved statistics are launched so that they may start while the previous
- * kernel of their stream finishes (CUDA programmatic dependent launch); each
- * waits, before its first memory access, until that kernel has completed and
- * its writes are visible, so only launch latency and the ramp of the grid
- * overlap.  Results are identical either way.  No counterpart in the paper. */
-void dgf_set_programmatic_launch(int on);
-
 /* Allows (1, default) or forbids (0) the one-graph form of
  * dgf_backward_batched; forbidden, every batch runs the per-image chains.
  * Both give the same bits. */

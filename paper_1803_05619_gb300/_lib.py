@@ -94,7 +94,6 @@ _SIGS = {
     "dgf_set_fused": (None, [_I]),
     "dgf_set_lowres_slide": (None, [_I]),
     "dgf_set_grey_fold": (None, [_I]),
-    "dgf_set_programmatic_launch": (None, [_I]),
     "dgf_set_batched_graph_backward": (None, [_I]),
     "dgf_set_pipeline": (None, [_I]),
     "dgf_shutdown": (None, []),
@@ -249,10 +248,6 @@ def dgf_set_lowres_slide(on: bool) -> None:
 
 def dgf_set_grey_fold(on: bool) -> None:
     lib().dgf_set_grey_fold(1 if on else 0)
-
-
-def dgf_set_programmatic_launch(on: bool) -> None:
-    lib().dgf_set_programmatic_launch(1 if on else 0)
 
 
 def dgf_set_batched_graph_backward(on: bool) -> None:

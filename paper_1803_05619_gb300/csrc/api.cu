@@ -270,9 +270,6 @@ struct Plan {
 
 static bool g_fused_allowed = true;
 
-std::atomic<bool> g_pdl{true};
-bool pdl_allowed() { return g_pdl.load(std::memory_order_relaxed); }
-
 static bool aligned_to(std::initializer_list<const void*> ptrs, int bytes) {
     for (const void* p : ptrs)
         if (p != nullptr && reinterpret_cast<uintptr_t>(p) % (uintptr_t)bytes != 0) return false;
@@ -2596,7 +2593,6 @@ extern "C" void dgf_set_tma(int on) { g_tma_allowed = on != 0; }
 extern "C" void dgf_set_fused(int on) { g_fused_allowed = on != 0; }
 extern "C" void dgf_set_lowres_slide(int on) { g_slide_allowed = on != 0; }
 extern "C" void dgf_set_grey_fold(int on) { g_grey_fold = on != 0; }
-extern "C" void dgf_set_programmatic_launch(int on) { g_pdl = on != 0; }
 extern "C" void dgf_set_batched_graph_backward(int on) { g_batched_graph_bwd = on != 0; }
 
 extern "C" void dgf_set_pipeline(int on) { g_pipeline = on != 0; }

@@ -7,43 +7,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <utility>
-
 namespace dgf {
 
 constexpr int kThreads = 256;  // threads per CTA of every tiled kernel
 constexpr int kWarps = kThreads / 32;
-
-// ------------------------------------------------ programmatic launches
-// A kernel launched with launch_pdl may start while the previous kernel of
-// its stream is still running: before it reads anything that kernel wrote
-// it calls pdl_wait (which returns once every kernel it depends on has
-// completed and its memory operations are visible; a no-op when it was
-// launched without the attribute), and then pdl_trigger, which lets the
-// next kernel of the stream be scheduled once every CTA of this grid has
-// run it or exited.  So launch latency and the CTA ramp of the next kernel
-// overlap the tail of the current one, while no kernel ever reads data
-// before its producer has finished.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-bool pdl_allowed();  // dgf_set_programmatic_launch (api.cu)
-
-template <typename... KArgs, typename... Args>
-static inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                                     Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = pdl_allowed() ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
 
 // ------------------------------------------------------------ reciprocals
 // 1/x from the special-function unit (PTX rcp.approx.ftz.f32: relative error

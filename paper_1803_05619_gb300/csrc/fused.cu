@@ -201,8 +201,6 @@ __global__ void __launch_bounds__(kK12Warps * 32)
     k12_fused(const T* __restrict__ G, const T* __restrict__ P, const T* __restrict__ in, T* __restrict__ out,
               int h_l, int w_l, int h, int w, float eps, int LS, int nstrip, int nseg, int planes) {
     extern __shared__ __align__(128) unsigned char k12sm[];
-    pdl_wait();  // launched programmatically: the previous kernel's writes first
-    pdl_trigger();
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * kK12Warps + warp;
     if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
@@ -225,9 +223,10 @@ static cudaError_t k12_go(const void* G, const void* P, const void* in, void* ou
         if (e != cudaSuccess) return e;
     }
     const unsigned ctas = (unsigned)((warps + kK12Warps - 1) / kK12Warps);
-    return launch_pdl(kern, dim3(ctas), dim3(kK12Warps * 32), smem, s, static_cast<const T*>(G),
-                      static_cast<const T*>(P), static_cast<const T*>(in), static_cast<T*>(out), h_l, w_l, h, w, eps,
-                      LS, nstrip, nseg, planes);
+    kern<<<ctas, kK12Warps * 32, smem, s>>>(static_cast<const T*>(G), static_cast<const T*>(P),
+                                            static_cast<const T*>(in), static_cast<T*>(out), h_l, w_l, h, w, eps, LS,
+                                            nstrip, nseg, planes);
+    return cudaGetLastError();
 }
 
 template <typename T, int F>
@@ -433,8 +432,6 @@ __global__ void __launch_bounds__(kK13Warps * 32)
                   int w, float eps, int LS, int nstrip, int nseg, int planes, uint32_t* status) {
     extern __shared__ __align__(1024) unsigned char k13sm[];
     using C = K13Cfg<T, R, F>;
-    pdl_wait();  // launched programmatically: the previous kernel's writes first
-    pdl_trigger();
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * kK13Warps + warp;
     if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
@@ -461,9 +458,10 @@ static cudaError_t k13_go(const void* G, const void* P, const K3Maps& maps, void
         if (e != cudaSuccess) return e;
     }
     const unsigned ctas = (unsigned)((warps + kK13Warps - 1) / kK13Warps);
-    return launch_pdl(kern, dim3(ctas), dim3(kK13Warps * 32), C::CTA_BYTES, s, static_cast<const T*>(G),
-                      static_cast<const T*>(P), maps, static_cast<T*>(dG), dcoef, stats, h_l, w_l, h, w, eps, LS,
-                      nstrip, nseg, planes, status);
+    kern<<<ctas, kK13Warps * 32, C::CTA_BYTES, s>>>(static_cast<const T*>(G), static_cast<const T*>(P), maps,
+                                                     static_cast<T*>(dG), dcoef, stats, h_l, w_l, h, w, eps, LS,
+                                                     nstrip, nseg, planes, status);
+    return cudaGetLastError();
 }
 
 template <typename T, int F>

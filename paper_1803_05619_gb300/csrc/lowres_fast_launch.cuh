@@ -151,8 +151,6 @@ __global__ void __launch_bounds__(kK4StripWarps * 32)
     k4_lowres_bwd_strip2_stats(const TG* __restrict__ G, const TP* __restrict__ P, const float2* __restrict__ dcoef,
                                const float4* __restrict__ stats, TP* __restrict__ dP, TD* __restrict__ dG, int h,
                                int w, int seg, int nstrip, int nseg, int planes, int mean) {
-    pdl_wait();  // launched programmatically: the previous kernel's writes first
-    pdl_trigger();
     const int gw = blockIdx.x * kK4StripWarps + (threadIdx.x >> 5);
     if (gw >= nstrip * nseg * planes) return;  // whole warp leaves together
     const int strip = gw % nstrip, rest = gw / nstrip;
@@ -237,10 +235,10 @@ static cudaError_t k4f_go(const void* G, const void* P, const float2* dcoef, voi
                 const int nstrip2 = (w + strip2_out_cols(R) - 1) / strip2_out_cols(R);
                 const long long warps2 = (long long)nstrip2 * nseg * planes;
                 const int ctas2 = (int)((warps2 + kK4StripWarps - 1) / kK4StripWarps);
-                return launch_pdl(k4_lowres_bwd_strip2_stats<TG, TP, TD, R>, dim3(ctas2), dim3(kK4StripWarps * 32),
-                                  0, s, static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef, stats,
-                                  static_cast<TP*>(dP), static_cast<TD*>(dG), h, w, seg, nstrip2, nseg, planes,
-                                  c.mean);
+                k4_lowres_bwd_strip2_stats<TG, TP, TD, R><<<ctas2, kK4StripWarps * 32, 0, s>>>(
+                    static_cast<const TG*>(G), static_cast<const TP*>(P), dcoef, stats, static_cast<TP*>(dP),
+                    static_cast<TD*>(dG), h, w, seg, nstrip2, nseg, planes, c.mean);
+                return cudaGetLastError();
             }
             if (tma != nullptr && tma->enabled) {
                 constexpr int smem_t = k4_strip_tma_smem<TG, TP, R>();

@@ -1007,42 +1007,3 @@ def test_kept_coefficients_batched(dtype):
             assert torch.equal(a, b)
     assert L.dgf_device_status() == 0
 
-
-@pytest.mark.parametrize("dtype", [F32, BF16], ids=["f32", "bf16"])
-def test_programmatic_launch_gives_the_same_bits(dtype):
-    # the fused kernels and the K4 from saved statistics launched so that they
-    # may start early (each waits for its predecessor before any access) and
-    # launched plainly: the same outputs, eagerly and from a replayed graph
-    N, C, hl, wl, f, r, eps = 2, 3, 40, 50, 4 if dtype == F32 else 8, 1, 1e-3
-    st = to_storage(make_case("photo", 77, N, C, hl, wl, hl * f, wl * f), dtype)
-    R = synth.upstream_grad(78, st["I_h"].shape).to(dtype).cuda()
-    g = {k: v.cuda() for k, v in st.items()}
-    res = []
-    for on in (False, True):
-        L.dgf_set_programmatic_launch(on)
-        try:
-            out = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps)
-            grads = gf_backward(R, g["p_l"], g["I_l"], g["I_h"], r, eps)[:3]
-            s = torch.cuda.Stream()
-            s.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(s):
-                gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps)
-            torch.cuda.synchronize()
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph, stream=s):
-                gout = gf_forward(g["p_l"], g["I_l"], g["I_h"], r, eps)
-                ggrads = gf_backward(R, g["p_l"], g["I_l"], g["I_h"], r, eps)[:3]
-            for _ in range(3):
-                graph.replay()
-            torch.cuda.synchronize()
-        finally:
-            L.dgf_set_programmatic_launch(True)
-        assert torch.equal(gout, out)
-        for a, b in zip(ggrads, grads):
-            assert torch.equal(a, b)
-        res.append((out, grads))
-    assert torch.equal(res[0][0], res[1][0])
-    for a, b in zip(res[0][1], res[1][1]):
-        assert torch.equal(a, b)
-    assert_fwd(f64(res[1][0]), oracle_forward(st, r, eps), dtype, eps)
-    assert L.dgf_device_status() == 0
