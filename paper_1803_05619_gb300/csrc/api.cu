@@ -707,8 +707,14 @@ static dgf_status check_ws(void* ws, size_t ws_bytes, size_t need) {
 // ---------------------------------------------------------------- autotune
 // Each helper times its candidates on the call's own buffers (the real
 // launch that follows overwrites every output) and records the fastest.
+// Small planes (size class 1) are not tuned: their kernels are a few walks
+// bound by latency, which back-to-back timing of one kernel does not
+// measure (on a 64 x 64 plane it picked K1 tiles, which rule out the fused
+// kernels, and the step got slower); they keep the default shapes, with
+// segments shrunk until a plane gives a warp per SM, unless pinned.
 static void tune_k1(dgf_dtype dt, bool gf32, const void* G, const void* P, float2* coef, int planes, int h_l,
                     int w_l, int r, float eps, cudaStream_t s, Plan& p) {
+    if (p.sc != 0) return;  // small planes keep the default shapes
     TuneKey key{1, (int)dt, r, 0, 0, gf32 ? 1 : 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
@@ -737,6 +743,7 @@ static void tune_k1(dgf_dtype dt, bool gf32, const void* G, const void* P, float
 static void tune_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const float2* dcoef, void* dP, void* dG,
                     int planes, int h_l, int w_l, int r, float eps, cudaStream_t s, Plan& p,
                     const float4* stats = nullptr) {
+    if (p.sc != 0) return;  // small planes keep the default shapes
     TuneKey key{4, (int)dt, r, 0, 0, gf32 ? 1 : 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
@@ -761,6 +768,7 @@ static void tune_k4(dgf_dtype dt, bool gf32, const void* G, const void* P, const
 
 static void tune_k2(dgf_dtype dt, const float2* coef, const void* in, void* out, int planes, int h_l, int w_l,
                     int h, int w, cudaStream_t s, Plan& p) {
+    if (p.sc != 0) return;  // small planes keep the default shapes
     TuneKey key{2, (int)dt, 0, p.F, p.vec, 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
@@ -789,6 +797,7 @@ static void tune_k2(dgf_dtype dt, const float2* coef, const void* in, void* out,
 static void tune_k3(dgf_dtype dt, const float2* coef, const void* R, const void* G, void* dG, float2* dcoef,
                     int planes, int h_l, int w_l, int h, int w, cudaStream_t s, Plan& p) {
     if (!p.k3_fast) return;
+    if (p.sc != 0) return;  // small planes keep the default shapes
     TuneKey key{3, (int)dt, 0, p.F, p.vec, 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
@@ -829,6 +838,7 @@ static bool tune_has_k3(dgf_dtype dt, const Plan& p) {
 static void tune_k12(dgf_dtype dt, const void* G, const void* P, float2* coef, const void* in, void* out,
                      int planes, int h_l, int w_l, int h, int w, int r, float eps, cudaStream_t s, Plan& p) {
     if (!p.k12_ok) return;
+    if (p.sc != 0) return;  // small planes keep the default shapes
     TuneKey key{5, (int)dt, r, p.F, 0, 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
@@ -863,6 +873,7 @@ static void tune_k13(dgf_dtype dt, const void* G, const void* P, float2* coef, f
                      const void* Gh, void* dGh, float2* dcoef, int planes, int h_l, int w_l, int h, int w, int r,
                      float eps, const K3Maps& maps, cudaStream_t s, Plan& p) {
     if (!p.k13_ok) return;
+    if (p.sc != 0) return;  // small planes keep the default shapes
     TuneKey key{6, (int)dt, r, p.F, p.vec, 0, p.sc};
     int a, b;
     if (tune_lookup(key, a, b)) return;
