@@ -129,7 +129,8 @@ class Step:
         self.keep_coef = keep_coef and L.dgf_backward_reuses_coef(N, C, h_l, w_l, h, w, self.r, self.dt, None,
                                                                  None) == 1
         if self.keep_coef:
-            self.coef = torch.empty(L.dgf_coef_bytes(N, C, h_l, w_l, None) // 4, dtype=torch.float32, device=device)
+            self.coef = torch.empty(L.dgf_coef_bytes(N, C, h_l, w_l, h, w, None) // 4, dtype=torch.float32,
+                                    device=device)
             self.opt = L.dgf_options(1, 0, 0, self.coef.data_ptr())
             self.fwd_args += (ctypes.byref(self.opt),)
             self.bwd_args += (ctypes.byref(self.opt),)
@@ -993,7 +994,7 @@ def bench_grey(args, device):
     h = w = hl * f
 
     # the forward keeps Abar, bbar where the backward then skips work (the layer's autograd rule)
-    cf = coef_buffer(p_l) if backward_reuses_coef(p_l, I_h, r) else None
+    cf = coef_buffer(p_l, I_h) if backward_reuses_coef(p_l, I_h, r) else None
 
     def fwd():
         gf_forward(p_l, I_l, I_h, r, eps, coef=cf)
@@ -1075,7 +1076,7 @@ def bench_guided(args, device):
     w = {k: v.float().to(device) for k, v in synth.guide_weights(22).items()}
     R = synth.upstream_grad(23, g["I_h"].shape).to(torch.bfloat16).to(device)
     # the forward keeps Abar, bbar for the backward, as the layer's autograd function does
-    cf = coef_buffer(g["p_l"], guided=True)
+    cf = coef_buffer(g["p_l"], g["I_h"], guided=True)
 
     def step(coef=cf):
         gf_forward(g["p_l"], None, g["I_h"], 8, 1e-4, w["w1"], w["w2"], w["b2"], 0.2, coef=coef)

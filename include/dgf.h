@@ -316,15 +316,17 @@ void dgf_set_pipeline(int on);
  *   coef != NULL: device memory of dgf_coef_bytes(...) bytes, 256-byte
  *             aligned, owned by the caller: N x C x h_l x w_l FP32 pairs
  *             (Abar, bbar) (A_l, b_l with mean_ab = 0) and, with a guidance
- *             transform, from the next 256-byte boundary the low-res guide
- *             G_l (N x 3 x h_l x w_l FP32).  dgf_forward_opt writes the
- *             call's values there (with the fused forward kernel then off:
- *             the two-kernel form, the same bits); dgf_backward_opt reads
- *             them as the forward's (the intermediate values Algorithm 1
- *             takes from the forward pass) and skips the passes that would
- *             only recompute them: its low-resolution K1 pass where that
- *             pass produces nothing else, and with a guidance transform also
- *             the guide pass K5 (dgf_backward_reuses_coef tells when).  They
+ *             transform, from the next 256-byte boundaries the low-res guide
+ *             G_l (N x 3 x h_l x w_l FP32) and the high-res guide F(I_h)
+ *             (N x 3 x h x w FP32; not written with guide_low).
+ *             dgf_forward_opt writes the call's values there (with the fused
+ *             forward kernel then off: the two-kernel form, the same bits);
+ *             dgf_backward_opt reads them as the forward's (the intermediate
+ *             values Algorithm 1 takes from the forward pass) and skips the
+ *             work that would only recompute them: its low-resolution K1
+ *             pass where that pass produces nothing else, and with a
+ *             guidance transform also the guide pass K5 and the evaluation
+ *             of F per pixel in K3g (dgf_backward_reuses_coef tells when).  They
  *             must be what dgf_forward_opt wrote for the same inputs,
  *             weights, options and sizes; the backward's results are then
  *             the bits it gives without them.
@@ -337,9 +339,9 @@ typedef struct {
 } dgf_options;
 
 /* Bytes of the buffer dgf_options.coef points to for these sizes (g: with
- * a guidance transform, which adds the low-res guide); 0 for invalid sizes.
- * Pure host function. */
-size_t dgf_coef_bytes(int N, int C, int h_l, int w_l, const dgf_guide* g);
+ * a guidance transform, which adds the low-res and high-res guides); 0 for
+ * invalid sizes.  Pure host function. */
+size_t dgf_coef_bytes(int N, int C, int h_l, int w_l, int h, int w, const dgf_guide* g);
 
 /* 1 when dgf_backward_opt with these sizes and options (coef aside) skips
  * work given the forward's coefficients (opt->coef): always with a guidance

@@ -73,7 +73,7 @@ _SIGS = {
                                     ctypes.POINTER(dgf_options)]),
     "dgf_backward_reuses_coef": (_I, [_I, _I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(dgf_guide),
                                       ctypes.POINTER(dgf_options)]),
-    "dgf_coef_bytes": (_S, [_I, _I, _I, _I, ctypes.POINTER(dgf_guide)]),
+    "dgf_coef_bytes": (_S, [_I, _I, _I, _I, _I, _I, ctypes.POINTER(dgf_guide)]),
     "dgf_workspace_size_batched": (_S, [ctypes.POINTER(dgf_image), _I, _I]),
     "dgf_forward_batched": (_I, [ctypes.POINTER(dgf_image), _I, _I, _P, _S, _P]),
     "dgf_workspace_size_batched_backward": (_S, [ctypes.POINTER(dgf_image_grad), _I, _I]),
@@ -168,8 +168,8 @@ def dgf_backward_reuses_coef(N, C, h_l, w_l, h, w, r, dt, g, opt) -> int:
     return lib().dgf_backward_reuses_coef(N, C, h_l, w_l, h, w, r, dt, g, opt)
 
 
-def dgf_coef_bytes(N, C, h_l, w_l, g) -> int:
-    return lib().dgf_coef_bytes(N, C, h_l, w_l, g)
+def dgf_coef_bytes(N, C, h_l, w_l, h, w, g) -> int:
+    return lib().dgf_coef_bytes(N, C, h_l, w_l, h, w, g)
 
 
 def dgf_workspace_size_batched(imgs, n, dt) -> int:

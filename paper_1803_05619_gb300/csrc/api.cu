@@ -1115,10 +1115,15 @@ size_t dgf_workspace_size(int N, int C, int h_l, int w_l, int h, int w, int r, d
 }
 
 // The kept values of a call (dgf_options.coef): N C h_l w_l (Abar, bbar)
-// pairs, then from the next 256-byte boundary the low-res guide of a
-// guidance transform (N x 3 planes, FP32; C = 3 there).
+// pairs, then, with a guidance transform (C = 3), from the next 256-byte
+// boundaries the low-res guide G_l and the high-res guide F(I_h) (FP32).
 static float* kept_guide(float2* coef, int planes, int h_l, int w_l) {
     return reinterpret_cast<float*>(reinterpret_cast<char*>(coef) + align256((size_t)planes * h_l * w_l * sizeof(float2)));
+}
+static float* kept_guide_h(float2* coef, int planes, int h_l, int w_l) {
+    const size_t lo = (size_t)planes * h_l * w_l;
+    return reinterpret_cast<float*>(reinterpret_cast<char*>(coef) + align256(lo * sizeof(float2)) +
+                                    align256(lo * sizeof(float)));
 }
 
 static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h, void* O_h, int N, int C, int h_l,
@@ -1226,8 +1231,11 @@ static dgf_status forward_impl(const void* p_l, const void* I_l, const void* I_h
     // G_l goes to the caller's buffer after the coefficients when it keeps them
     float* G_l = coef_out != nullptr ? kept_guide(coef_out, planes, h_l, w_l) : reinterpret_cast<float*>(ws + lay.gl);
     // with G_l the block mean of F(I_h), K5 also keeps F(I_h) in FP32 and K2
-    // reads that guide instead of evaluating F again per pixel
-    float* G_h = guide_low ? nullptr : reinterpret_cast<float*>(ws + lay.gh);
+    // reads that guide instead of evaluating F again per pixel (kept for the
+    // backward's K3g when the caller keeps the forward's values)
+    float* G_h = guide_low ? nullptr
+                           : (coef_out != nullptr ? kept_guide_h(coef_out, planes, h_l, w_l)
+                                                  : reinterpret_cast<float*>(ws + lay.gh));
     if (!aligned16({I_h, O_h})) return fail(DGF_ERR_UNSUPPORTED, "guidance transform needs 16-byte aligned I_h, O_h");
     e = guide_upload(g->w1, g->w2, g->b2, g->hidden, s);
     if (e != cudaSuccess) return cuda_fail(e, "guide weights");
@@ -1500,7 +1508,10 @@ static dgf_status backward_impl(const void* dO_h, const void* p_l, const void* I
         if (e != cudaSuccess) return cuda_fail(e, "k1");
     }
     e = L.run("k3_hires_bwd_guided", [&] {
-        return launch_k3_guided(dt, dO_h, I_h, dcoef, N, h_l, w_l, h, w, p.F, g->slope, s);
+        return launch_k3_guided(dt, dO_h, I_h, dcoef, N, h_l, w_l, h, w, p.F, g->slope, s,
+                                (coef_in != nullptr && !guide_low)
+                                    ? kept_guide_h(const_cast<float2*>(coef_in), planes, h_l, w_l)
+                                    : nullptr);
     });
     if (e != cudaSuccess) return cuda_fail(e, "k3g");
     const bool want_dgl = guide_low ? need_lo : need_hi;
@@ -1783,10 +1794,11 @@ size_t dgf_workspace_size_opt(int N, int C, int h_l, int w_l, int h, int w, int 
     return grey_layout(N, C, h_l, w_l, h, w, dt).total;
 }
 
-size_t dgf_coef_bytes(int N, int C, int h_l, int w_l, const dgf_guide* g) {
-    if (N < 0 || C < 1 || h_l < 1 || w_l < 1 || (long long)N * C > 65535) return 0;
+size_t dgf_coef_bytes(int N, int C, int h_l, int w_l, int h, int w, const dgf_guide* g) {
+    if (N < 0 || C < 1 || h_l < 1 || w_l < 1 || h < h_l || w < w_l || (long long)N * C > 65535) return 0;
     const size_t lo = (size_t)N * C * h_l * w_l;
-    return g == nullptr ? lo * sizeof(float2) : align256(lo * sizeof(float2)) + lo * sizeof(float);
+    if (g == nullptr) return lo * sizeof(float2);
+    return align256(lo * sizeof(float2)) + align256(lo * sizeof(float)) + (size_t)N * C * h * w * sizeof(float);
 }
 
 int dgf_backward_reuses_coef(int N, int C, int h_l, int w_l, int h, int w, int r, dgf_dtype dt, const dgf_guide* g,

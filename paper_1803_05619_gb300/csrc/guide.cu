@@ -267,8 +267,11 @@ __global__ void __launch_bounds__(kThreads) k2_apply_guided(const float2* __rest
 }
 
 // ------------------------------------------------------------------ K3g
-template <typename T, int VEC, int F>
+// GH: G_h = F(I_h) is given in FP32 (the forward's K5 kept it: the same bits
+// guide_eval gives) and read instead of evaluating F per pixel.
+template <typename T, int VEC, int F, bool GH>
 __global__ void __launch_bounds__(kThreads) k3_hires_bwd_guided(const T* __restrict__ R, const T* __restrict__ I_h,
+                                                                const float* __restrict__ G_h,
                                                                 float2* __restrict__ dcoef, int h_l, int w_l,
                                                                 int h, int w, int LTH, float slope) {
     extern __shared__ __align__(128) float smem[];
@@ -287,12 +290,15 @@ __global__ void __launch_bounds__(kThreads) k3_hires_bwd_guided(const T* __restr
     for (int fr = warp; fr < FR; fr += kWarps) {
         const int y = yf0 + fr;
         const bool ok = col_ok && y >= 0 && y < h;
-        float r[3][VEC], x[3][VEC];
+        float r[3][VEC], x[3][VEC];  // x: I_h, or G_h itself with GH
         if (ok) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 load_vec<T, VEC>(R + (n * 3 + c) * hw + (size_t)y * w + xs, r[c]);
-                load_vec<T, VEC>(I_h + (n * 3 + c) * hw + (size_t)y * w + xs, x[c]);
+                if constexpr (GH)
+                    load_vec<float, VEC>(G_h + (n * 3 + c) * hw + (size_t)y * w + xs, x[c]);
+                else
+                    load_vec<T, VEC>(I_h + (n * 3 + c) * hw + (size_t)y * w + xs, x[c]);
             }
         } else {
 #pragma unroll
@@ -303,9 +309,15 @@ __global__ void __launch_bounds__(kThreads) k3_hires_bwd_guided(const T* __restr
         float u[3][VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) {
-            const float xi[3] = {x[0][k], x[1][k], x[2][k]};
             float g[3];
-            guide_eval(xi, slope, g);
+            if constexpr (GH) {
+                g[0] = x[0][k];
+                g[1] = x[1][k];
+                g[2] = x[2][k];
+            } else {
+                const float xi[3] = {x[0][k], x[1][k], x[2][k]};
+                guide_eval(xi, slope, g);
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) u[c][k] = ok ? r[c][k] * g[c] : 0.f;
         }
@@ -712,15 +724,15 @@ static cudaError_t k2g_go(const float2* coef, const void* I_h, void* O_h, int N,
 }
 
 template <typename T, int VEC, int F>
-static cudaError_t k3g_go(const void* R, const void* I_h, float2* dcoef, int N, int h_l, int w_l, int h,
-                          int w, int LTH, float slope, cudaStream_t s) {
+static cudaError_t k3g_go(const void* R, const void* I_h, const float* G_h, float2* dcoef, int N, int h_l, int w_l,
+                          int h, int w, int LTH, float slope, cudaStream_t s) {
     constexpr int LTW = K3Shape<VEC, F>::LTW, SXP = K3Shape<VEC, F>::SXP;
     const size_t smem = (size_t)3 * F * (LTH + 1) * SXP * sizeof(float2);
-    auto kern = k3_hires_bwd_guided<T, VEC, F>;
+    auto kern = G_h != nullptr ? k3_hires_bwd_guided<T, VEC, F, true> : k3_hires_bwd_guided<T, VEC, F, false>;
     cudaError_t e = prep(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((w_l + LTW - 1) / LTW, (h_l + LTH - 1) / LTH, N);
-    kern<<<grid, kThreads, smem, s>>>(static_cast<const T*>(R), static_cast<const T*>(I_h), dcoef, h_l, w_l,
+    kern<<<grid, kThreads, smem, s>>>(static_cast<const T*>(R), static_cast<const T*>(I_h), G_h, dcoef, h_l, w_l,
                                       h, w, LTH, slope);
     return cudaGetLastError();
 }
@@ -778,9 +790,9 @@ static cudaError_t k2g_d(const float2* coef, const void* I_h, void* O_h, int N, 
 }
 
 template <typename T>
-static cudaError_t k3g_d(const void* R, const void* I_h, float2* dcoef, int N, int h_l, int w_l, int h,
-                         int w, int vec, int F, int LTH, float slope, cudaStream_t s) {
-    DGF_GUIDED_DISPATCH(k3g_go, R, I_h, dcoef, N, h_l, w_l, h, w, LTH, slope, s);
+static cudaError_t k3g_d(const void* R, const void* I_h, const float* G_h, float2* dcoef, int N, int h_l, int w_l,
+                         int h, int w, int vec, int F, int LTH, float slope, cudaStream_t s) {
+    DGF_GUIDED_DISPATCH(k3g_go, R, I_h, G_h, dcoef, N, h_l, w_l, h, w, LTH, slope, s);
 }
 
 template <typename T>
@@ -811,14 +823,16 @@ cudaError_t launch_k2_guided(dgf_dtype dt, const float2* coef, const void* I_h, 
 }
 
 cudaError_t launch_k3_guided(dgf_dtype dt, const void* R, const void* I_h, float2* dcoef, int N, int h_l,
-                             int w_l, int h, int w, int F, float slope, cudaStream_t s) {
+                             int w_l, int h, int w, int F, float slope, cudaStream_t s, const float* G_h) {
     if (N == 0) return cudaSuccess;
     const int vec = guided_vec(dt, w);
+    // the FP32 guide's vectors (VEC floats) must be aligned as the loads need
+    if (G_h != nullptr && reinterpret_cast<uintptr_t>(G_h) % (vec * sizeof(float)) != 0) return cudaErrorInvalidValue;
     const int LTH = F >= 8 ? 4 : 8;
     switch (dt) {
-        case DGF_F32: return k3g_d<float>(R, I_h, dcoef, N, h_l, w_l, h, w, vec, F, LTH, slope, s);
-        case DGF_BF16: return k3g_d<__nv_bfloat16>(R, I_h, dcoef, N, h_l, w_l, h, w, vec, F, LTH, slope, s);
-        case DGF_F16: return k3g_d<__half>(R, I_h, dcoef, N, h_l, w_l, h, w, vec, F, LTH, slope, s);
+        case DGF_F32: return k3g_d<float>(R, I_h, G_h, dcoef, N, h_l, w_l, h, w, vec, F, LTH, slope, s);
+        case DGF_BF16: return k3g_d<__nv_bfloat16>(R, I_h, G_h, dcoef, N, h_l, w_l, h, w, vec, F, LTH, slope, s);
+        case DGF_F16: return k3g_d<__half>(R, I_h, G_h, dcoef, N, h_l, w_l, h, w, vec, F, LTH, slope, s);
     }
     return cudaErrorInvalidValue;
 }

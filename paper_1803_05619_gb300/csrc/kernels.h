@@ -137,8 +137,10 @@ cudaError_t launch_k5(dgf_dtype dt, const void* I_h, float* G_l, int N, int h_l,
                       int F, float slope, cudaStream_t s, float* G_h = nullptr);
 cudaError_t launch_k2_guided(dgf_dtype dt, const float2* coef, const void* I_h, void* O_h, int N,
                              int h_l, int w_l, int h, int w, int F, int TH, float slope, cudaStream_t s);
+// G_h (or null): F(I_h) in FP32 as the forward's K5 kept it, read instead of evaluating F
 cudaError_t launch_k3_guided(dgf_dtype dt, const void* R, const void* I_h, float2* dcoef, int N,
-                             int h_l, int w_l, int h, int w, int F, float slope, cudaStream_t s);
+                             int h_l, int w_l, int h, int w, int F, float slope, cudaStream_t s,
+                             const float* G_h = nullptr);
 // F applied to the low-res guide itself (G_l = F(I_l), I_l: N x 3 x h_l x w_l):
 // K5L forms G_l (FP32); K6L chains d G_l through F to d I_l (nullable) and
 // writes k6_low_blocks(...) weight-gradient partial rows from `partials`.

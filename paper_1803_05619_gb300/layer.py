@@ -88,13 +88,18 @@ def _options(mean_ab, C, I_h, g, guide_low=False, coef=None):
                          None if coef is None else coef.data_ptr())
 
 
-def coef_buffer(p_l, guided=False):
+def _coef_bytes(p_l, I_h, guided):
+    N, C, h_l, w_l = p_l.shape
+    h, w = I_h.shape[-2:]
+    g = L.dgf_guide(None, None, None, 1, 0.2) if guided else None
+    return L.dgf_coef_bytes(N, C, h_l, w_l, h, w, ctypes.byref(g) if g is not None else None)
+
+
+def coef_buffer(p_l, I_h, guided=False):
     """A buffer for the values a forward call keeps for its backward: the
     coefficients (Abar, bbar) and, with the guidance transform (guided=True),
-    the low-res guide (dgf_options.coef, dgf_coef_bytes)."""
-    N, C, h_l, w_l = p_l.shape
-    g = L.dgf_guide(None, None, None, 1, 0.2) if guided else None
-    nb = L.dgf_coef_bytes(N, C, h_l, w_l, ctypes.byref(g) if g is not None else None)
+    the low-res and high-res guides (dgf_options.coef, dgf_coef_bytes)."""
+    nb = _coef_bytes(p_l, I_h, guided)
     return torch.empty((nb + 3) // 4, dtype=torch.float32, device=p_l.device)
 
 
@@ -109,12 +114,10 @@ def backward_reuses_coef(p_l, I_h, r, w1=None, mean_ab=True, guide_low=False) ->
                                            ctypes.byref(opt) if opt is not None else None))
 
 
-def _check_coef(coef, p_l, guided=False):
+def _check_coef(coef, p_l, I_h, guided=False):
     if coef is None:
         return
-    N, C, h_l, w_l = p_l.shape
-    g = L.dgf_guide(None, None, None, 1, 0.2) if guided else None
-    nb = L.dgf_coef_bytes(N, C, h_l, w_l, ctypes.byref(g) if g is not None else None)
+    nb = _coef_bytes(p_l, I_h, guided)
     if (coef.dtype != torch.float32 or not coef.is_cuda or not coef.is_contiguous()
             or 4 * coef.numel() < nb or coef.device != p_l.device or coef.data_ptr() % 256 != 0):
         raise ValueError("coef must be a contiguous, 256-byte aligned float32 CUDA tensor of "
@@ -136,7 +139,7 @@ def gf_forward(p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=None, slo
         raise TypeError("p_l, I_l and I_h must share one dtype")
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
-    _check_coef(coef, p_l, g is not None)
+    _check_coef(coef, p_l, I_h, g is not None)
     opt = _options(mean_ab, C, I_h, g, guide_low, coef)
     if out is None:
         out = torch.empty((N, C, h, w), dtype=I_h.dtype, device=I_h.device)
@@ -161,7 +164,7 @@ def gf_backward(dO_h, p_l, I_l, I_h, r: int, eps: float, w1=None, w2=None, b2=No
     dt = dtype_code(I_h)
     g = _guide_struct(w1, w2, b2, slope)
     gp = ctypes.byref(g) if g is not None else None
-    _check_coef(coef, p_l, g is not None)
+    _check_coef(coef, p_l, I_h, g is not None)
     opt = _options(mean_ab, C, I_h, g, guide_low, coef)
     dO_h = dO_h.to(I_h.dtype).contiguous()
     dp = torch.empty_like(p_l) if need_p else None
@@ -239,7 +242,7 @@ def gf_forward_batched(images, out=None, mean_ab=True):
     """Uneven batch in one graph-replayed persistent launch per stage.
 
     ``images``: list of dicts with p_l, I_l, I_h (C x h x w tensors, one
-    dtype), r, eps, and optionally coef (coef_buffer of p_l[None]: the
+    dtype), r, eps, and optionally coef (coef_buffer(p_l[None], I_h[None]): the
     image's coefficients are written there).  Returns the list of O_h.
     mean_ab=False: the layer as printed (dgf_forward_batched_opt; every
     image's kernels on library streams).
@@ -258,7 +261,7 @@ def gf_forward_batched(images, out=None, mean_ab=True):
         C, h, w = im["I_h"].shape
         h_l, w_l = im["p_l"].shape[1:]
         cf = im.get("coef")
-        _check_coef(cf, im["p_l"][None])
+        _check_coef(cf, im["p_l"][None], im["I_h"][None])
         arr[i] = L.dgf_image(im["p_l"].data_ptr(), im["I_l"].data_ptr(), im["I_h"].data_ptr(),
                              o.data_ptr(), C, h_l, w_l, h, w, int(im["r"]), float(im["eps"]),
                              None if cf is None else cf.data_ptr())
@@ -303,7 +306,7 @@ def gf_backward_batched(images, grads, mean_ab=True):
         C, h, w = im["I_h"].shape
         h_l, w_l = im["p_l"].shape[1:]
         cf = im.get("coef")
-        _check_coef(cf, im["p_l"][None])
+        _check_coef(cf, im["p_l"][None], im["I_h"][None])
         arr[i] = L.dgf_image_grad(R.data_ptr(), im["p_l"].data_ptr(), im["I_l"].data_ptr(), im["I_h"].data_ptr(),
                                   *(None if t is None else t.data_ptr() for t in (dp, dIl, dIh)),
                                   C, h_l, w_l, h, w, int(im["r"]),
@@ -328,7 +331,7 @@ class GuidedFilterFn(torch.autograd.Function):
     def forward(ctx, p_l, I_l, I_h, r, eps):
         p_l, I_l, I_h = p_l.contiguous(), I_l.contiguous(), I_h.contiguous()
         # the coefficients are kept for the backward where it then skips work
-        coef = coef_buffer(p_l) if backward_reuses_coef(p_l, I_h, r) else None
+        coef = coef_buffer(p_l, I_h) if backward_reuses_coef(p_l, I_h, r) else None
         ctx.save_for_backward(p_l, I_l, I_h, coef)
         ctx.r, ctx.eps = r, eps
         return gf_forward(p_l, I_l, I_h, r, eps, coef=coef)
@@ -350,7 +353,7 @@ class GuidedFilterTransformFn(torch.autograd.Function):
     def forward(ctx, p_l, I_h, w1, w2, b2, r, eps, slope):
         p_l, I_h = p_l.contiguous(), I_h.contiguous()
         w1, w2, b2 = w1.contiguous(), w2.contiguous(), b2.contiguous()
-        coef = coef_buffer(p_l, guided=True)  # the guided backward always reuses them
+        coef = coef_buffer(p_l, I_h, guided=True)  # the guided backward always reuses them
         ctx.save_for_backward(p_l, I_h, w1, w2, b2, coef)
         ctx.r, ctx.eps, ctx.slope = r, eps, slope
         return gf_forward(p_l, None, I_h, r, eps, w1, w2, b2, slope, coef=coef)

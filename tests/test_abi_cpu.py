@@ -188,9 +188,10 @@ def test_coefficient_reuse_query_on_host(lib):
                              ctypes.byref(bad)) == 1
     assert "aligned" in L.dgf_last_error()
     # the kept values: the pairs, and with a guidance transform the low-res guide after them
-    assert L.dgf_coef_bytes(2, 3, 10, 13, None) == 2 * 3 * 10 * 13 * 8
-    assert L.dgf_coef_bytes(2, 3, 10, 13, ctypes.byref(g)) == 6400 + 2 * 3 * 10 * 13 * 4
-    assert L.dgf_coef_bytes(2, 0, 10, 13, None) == 0
+    assert L.dgf_coef_bytes(2, 3, 10, 13, 40, 52, None) == 2 * 3 * 10 * 13 * 8
+    # with a guidance transform: G_l and F(I_h) after the pairs, each from a 256-byte boundary
+    assert L.dgf_coef_bytes(2, 3, 10, 13, 40, 52, ctypes.byref(g)) == 6400 + 3328 + 2 * 3 * 40 * 52 * 4
+    assert L.dgf_coef_bytes(2, 0, 10, 13, 40, 52, None) == 0
     assert L.dgf_backward_opt(16, 32, 48, 64, 80, 96, 112, None, 1, 1, 8, 8, 32, 32, 1, 1e-3, L.DGF_F32, None,
                               None, 0, None, ctypes.byref(bad)) == 1
     img = (L.dgf_image * 1)()

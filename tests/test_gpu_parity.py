@@ -933,7 +933,7 @@ def test_kept_coefficients_give_the_same_bits(case, pipeline):
     try:
         out = gf_forward(p_l, I_l, I_h, r, eps, mean_ab=mean_ab)
         ref = gf_backward(R, p_l, I_l, I_h, r, eps, mean_ab=mean_ab)[:3]
-        cf = coef_buffer(p_l)
+        cf = coef_buffer(p_l, I_h)
         out_k = gf_forward(p_l, I_l, I_h, r, eps, mean_ab=mean_ab, coef=cf)
         got = gf_backward(R, p_l, I_l, I_h, r, eps, mean_ab=mean_ab, coef=cf)[:3]
         only_ih = gf_backward(R, p_l, I_l, I_h, r, eps, mean_ab=mean_ab, coef=cf, need_p=False,
@@ -962,7 +962,7 @@ def test_kept_coefficients_guided(dtype, guide_low):
     from paper_1803_05619_gb300.layer import coef_buffer
     out = gf_forward(st["p_l"], I_l, st["I_h"], r, eps, *args, guide_low=guide_low)
     ref = gf_backward(R, st["p_l"], I_l, st["I_h"], r, eps, *args, guide_low=guide_low)
-    cf = coef_buffer(st["p_l"], guided=True)
+    cf = coef_buffer(st["p_l"], st["I_h"], guided=True)
     out_k = gf_forward(st["p_l"], I_l, st["I_h"], r, eps, *args, guide_low=guide_low, coef=cf)
     L.dgf_profile_reset()
     L.dgf_profile_enable(True)
@@ -995,7 +995,7 @@ def test_kept_coefficients_batched(dtype):
         grads.append(synth.upstream_grad(120 + i, d["I_h"].shape).to(dtype)[0].cuda())
     outs = gf_forward_batched(images)
     ref = gf_backward_batched(images, grads)
-    kept = [dict(im, coef=coef_buffer(im["p_l"][None])) for im in images]
+    kept = [dict(im, coef=coef_buffer(im["p_l"][None], im["I_h"][None])) for im in images]
     kept[1]["coef"] = None  # one image recomputes them
     outs_k = gf_forward_batched(kept)
     got = gf_backward_batched(kept, grads)
